@@ -1,0 +1,313 @@
+"""FP64 CPU oracle for the unbinned NLL path of GooFit (arXiv:1311.1753).
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline``/``--impl reference`` legs of ``bench.py`` may import this package.
+The product library never loads it and shares no code with it.
+
+The arithmetic lives in ``oracle.c`` (plain C99, FP64, no FMA contraction); this
+module compiles it with gcc on first use and wraps it with ctypes.  Model objects
+mirror the paper's vocabulary (Sec. 2): observables with ranges, parameters, PDFs
+combined by sums and products (Sec. 3), and a three-body Dalitz amplitude model
+(Sec. 4).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+# Leaf and combinator codes, as in oracle.c.
+EXP, GAUSS, VOIGT, THRESH, POLY, ADD, PROD = 1, 2, 3, 4, 5, 10, 11
+MAXPAR, MAXCHILD = 16, 8
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into _build/liborc.so (gcc, -O2, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class OrcNode(C.Structure):
+    _fields_ = [("type", C.c_int32), ("obs", C.c_int32), ("npar", C.c_int32),
+                ("par", C.c_int32 * MAXPAR), ("nchild", C.c_int32), ("child", C.c_int32 * MAXCHILD)]
+
+
+class OrcModel(C.Structure):
+    _fields_ = [("nnodes", C.c_int32), ("root", C.c_int32), ("nodes", C.POINTER(OrcNode)),
+                ("nobs", C.c_int32), ("lo", C.POINTER(C.c_double)), ("hi", C.POINTER(C.c_double)),
+                ("nbins", C.c_int32)]
+
+
+class OrcDkin(C.Structure):
+    _fields_ = [("M", C.c_double), ("m1", C.c_double), ("m2", C.c_double), ("m3", C.c_double),
+                ("R", C.c_double)]
+
+
+class OrcRes(C.Structure):
+    _fields_ = [("channel", C.c_int32), ("spin", C.c_int32), ("p_m0", C.c_int32),
+                ("p_g0", C.c_int32), ("p_re", C.c_int32), ("p_im", C.c_int32)]
+
+
+_D = C.POINTER(C.c_double)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            so = C.CDLL(build())
+            so.orc_faddeeva.argtypes = [C.c_double, C.c_double, _D, _D]
+            so.orc_faddeeva_many.argtypes = [C.c_int64, _D, _D, _D, _D]
+            so.orc_norms.argtypes = [C.POINTER(OrcModel), _D, C.c_int, _D, _D]
+            so.orc_norms.restype = C.c_int
+            so.orc_logpdf.argtypes = [C.POINTER(OrcModel), _D, C.c_int, C.c_int64, C.POINTER(_D), _D]
+            so.orc_logpdf.restype = C.c_int
+            so.orc_nll.argtypes = [C.POINTER(OrcModel), _D, C.c_int, C.c_int64, C.POINTER(_D), _D, _D]
+            so.orc_nll.restype = C.c_int
+            so.orc_leaf_shape_many.argtypes = [C.POINTER(OrcNode), _D, C.c_int64, _D, _D]
+            so.orc_dalitz_inside.argtypes = [C.POINTER(OrcDkin), C.c_double, C.c_double]
+            so.orc_dalitz_inside_many.argtypes = [C.POINTER(OrcDkin), C.c_int64, _D, _D,
+                                                  C.POINTER(C.c_int8)]
+            so.orc_dalitz_amp_many.argtypes = [C.POINTER(OrcDkin), C.c_int, C.c_int, C.c_double,
+                                               C.c_double, C.c_int64, _D, _D, _D, _D, _D]
+            so.orc_dalitz_norm.argtypes = [C.POINTER(OrcDkin), C.c_int, C.POINTER(OrcRes), _D,
+                                           C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, _D,
+                                           _D, C.POINTER(C.c_int64)]
+            so.orc_dalitz_intensity.argtypes = [C.POINTER(OrcDkin), C.c_int, C.POINTER(OrcRes), _D,
+                                                C.c_int, C.c_double, C.c_double, C.c_int64, _D, _D,
+                                                _D, _D]
+            so.orc_dalitz_nll.argtypes = [C.POINTER(OrcDkin), C.c_int, C.POINTER(OrcRes), _D,
+                                          C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                                          C.c_int64, _D, _D, _D, _D]
+            so.orc_zemach_at.argtypes = [C.POINTER(OrcDkin), C.c_int, C.c_int, C.c_double,
+                                         C.c_double]
+            so.orc_zemach_at.restype = C.c_double
+            _lib = so
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def faddeeva(z) -> np.ndarray:
+    """w(z) = exp(-z^2) erfc(-iz) for Im z > 0 (pole-corrected trapezoidal rule)."""
+    z = np.asarray(z, dtype=np.complex128)
+    flat = z.ravel()
+    x, y = _f64(flat.real), _f64(flat.imag)
+    re, im = np.empty_like(x), np.empty_like(x)
+    lib().orc_faddeeva_many(len(x), _dp(x), _dp(y), _dp(re), _dp(im))
+    return (re + 1j * im).reshape(z.shape)
+
+
+class Model1D:
+    """A PDF tree over one or more observables (Sec. 2-3 of the paper).
+
+    Parameters are held in one flat array (fixed and free alike); nodes refer to
+    them by index, like GooFit's index arrays (Listing 3-4)."""
+
+    def __init__(self, obs_ranges, nbins: int = 10000):
+        self.lo = _f64([r[0] for r in obs_ranges])
+        self.hi = _f64([r[1] for r in obs_ranges])
+        self.nbins = int(nbins)
+        self.values: list[float] = []
+        self.nodes: list[OrcNode] = []
+        self.root = -1
+
+    # parameters -------------------------------------------------------------
+    def param(self, value: float) -> int:
+        self.values.append(float(value))
+        return len(self.values) - 1
+
+    @property
+    def p(self) -> np.ndarray:
+        return _f64(self.values)
+
+    # nodes ---------------------------------------------------------------------
+    def _node(self, typ, obs=0, pars=(), children=()) -> int:
+        nd = OrcNode()
+        nd.type, nd.obs, nd.npar, nd.nchild = typ, obs, len(pars), len(children)
+        assert len(pars) <= MAXPAR and len(children) <= MAXCHILD
+        for i, q in enumerate(pars):
+            nd.par[i] = q
+        for i, c in enumerate(children):
+            nd.child[i] = c
+        self.nodes.append(nd)
+        self.root = len(self.nodes) - 1
+        return self.root
+
+    def exp(self, obs, alpha):
+        return self._node(EXP, obs, [alpha])
+
+    def gauss(self, obs, mu, sigma):
+        return self._node(GAUSS, obs, [mu, sigma])
+
+    def voigt(self, obs, mu, sigma, width):
+        return self._node(VOIGT, obs, [mu, sigma, width])
+
+    def threshold(self, obs, x0, power, c):
+        return self._node(THRESH, obs, [x0, power, c])
+
+    def poly(self, obs, coefs):
+        return self._node(POLY, obs, list(coefs))
+
+    def add(self, children, fracs):
+        assert len(fracs) == len(children) - 1
+        return self._node(ADD, 0, list(fracs), list(children))
+
+    def prod(self, children):
+        return self._node(PROD, 0, [], list(children))
+
+    # evaluation -------------------------------------------------------------------
+    def _model(self):
+        arr = (OrcNode * len(self.nodes))(*self.nodes)
+        m = OrcModel(len(self.nodes), self.root, arr, len(self.lo), _dp(self.lo), _dp(self.hi),
+                     self.nbins)
+        return m, arr
+
+    def _cols(self, cols):
+        cols = [_f64(c) for c in cols]
+        ptrs = (_D * len(cols))(*[_dp(c) for c in cols])
+        return cols, ptrs
+
+    def norms(self, p=None):
+        p = self.p if p is None else _f64(p)
+        m, keep = self._model()
+        N = np.empty(len(self.nodes))
+        dN = np.empty(len(self.nodes) * len(p))
+        rc = lib().orc_norms(C.byref(m), _dp(p), len(p), _dp(N), _dp(dN))
+        assert rc == 0
+        return N, dN.reshape(len(self.nodes), len(p))
+
+    def logpdf(self, cols, p=None) -> np.ndarray:
+        p = self.p if p is None else _f64(p)
+        m, keep = self._model()
+        cols, ptrs = self._cols(cols)
+        out = np.empty(len(cols[0]))
+        rc = lib().orc_logpdf(C.byref(m), _dp(p), len(p), len(out), ptrs, _dp(out))
+        assert rc == 0
+        return out
+
+    def nll(self, cols, p=None, grad: bool = False):
+        p = self.p if p is None else _f64(p)
+        m, keep = self._model()
+        cols, ptrs = self._cols(cols)
+        out = np.zeros(1)
+        g = np.zeros(len(p)) if grad else None
+        rc = lib().orc_nll(C.byref(m), _dp(p), len(p), len(cols[0]), ptrs, _dp(out),
+                           _dp(g) if grad else None)
+        assert rc == 0
+        return (out[0], g) if grad else out[0]
+
+    def leaf_shape(self, node: int, x, p=None) -> np.ndarray:
+        p = self.p if p is None else _f64(p)
+        x = _f64(x)
+        out = np.empty_like(x)
+        lib().orc_leaf_shape_many(C.byref(self.nodes[node]), _dp(p), len(x), _dp(x), _dp(out))
+        return out
+
+
+class Dalitz:
+    """Three-body Dalitz amplitude model on (s12, s13) (Sec. 4 of the paper).
+
+    A = a_NR + sum_r c_r F_L S_L BW_r;  P = |A|^2 normalised on an nbx x nby
+    cell-centre grid over the kinematic region."""
+
+    def __init__(self, M, m1, m2, m3, R=1.5, nbx=512, nby=512):
+        self.kin = OrcDkin(M, m1, m2, m3, R)
+        self.nbx, self.nby = int(nbx), int(nby)
+        self.values: list[float] = []
+        self.res: list[OrcRes] = []
+
+    def param(self, value: float) -> int:
+        self.values.append(float(value))
+        return len(self.values) - 1
+
+    @property
+    def p(self) -> np.ndarray:
+        return _f64(self.values)
+
+    def resonance(self, channel, spin, m0, g0, re, im) -> int:
+        self.res.append(OrcRes(channel, spin, m0, g0, re, im))
+        return len(self.res) - 1
+
+    def box(self):
+        k = self.kin
+        return ((k.m1 + k.m2) ** 2, (k.M - k.m3) ** 2, (k.m1 + k.m3) ** 2, (k.M - k.m2) ** 2)
+
+    def _resarr(self):
+        return (OrcRes * max(1, len(self.res)))(*self.res)
+
+    def inside(self, s12, s13) -> np.ndarray:
+        s12, s13 = _f64(s12), _f64(s13)
+        out = np.empty(len(s12), dtype=np.int8)
+        lib().orc_dalitz_inside_many(C.byref(self.kin), len(s12), _dp(s12), _dp(s13),
+                                     out.ctypes.data_as(C.POINTER(C.c_int8)))
+        return out.astype(bool)
+
+    def amp(self, r: int, s12, s13, p=None, deriv: bool = False):
+        p = self.p if p is None else _f64(p)
+        rs = self.res[r]
+        s12, s13 = _f64(s12), _f64(s13)
+        re, im = np.empty_like(s12), np.empty_like(s12)
+        d = np.empty(4 * len(s12)) if deriv else None
+        lib().orc_dalitz_amp_many(C.byref(self.kin), rs.channel, rs.spin, p[rs.p_m0], p[rs.p_g0],
+                                  len(s12), _dp(s12), _dp(s13), _dp(re), _dp(im),
+                                  _dp(d) if deriv else None)
+        a = re + 1j * im
+        if deriv:
+            d = d.reshape(-1, 4)
+            return a, d[:, 0] + 1j * d[:, 1], d[:, 2] + 1j * d[:, 3]
+        return a
+
+    def zemach(self, channel: int, spin: int, s12: float, s13: float) -> float:
+        return lib().orc_zemach_at(C.byref(self.kin), channel, spin, s12, s13)
+
+    def norm(self, p=None, anr=1.0 + 0j, grad=False):
+        p = self.p if p is None else _f64(p)
+        N = np.zeros(1)
+        dN = np.zeros(len(p)) if grad else None
+        cnt = C.c_int64(0)
+        lib().orc_dalitz_norm(C.byref(self.kin), len(self.res), self._resarr(), _dp(p), len(p),
+                              anr.real, anr.imag, self.nbx, self.nby, _dp(N),
+                              _dp(dN) if grad else None, C.byref(cnt))
+        return (N[0], dN, cnt.value) if grad else (N[0], cnt.value)
+
+    def intensity(self, s12, s13, p=None, anr=1.0 + 0j, kappa=False):
+        p = self.p if p is None else _f64(p)
+        s12, s13 = _f64(s12), _f64(s13)
+        P = np.empty_like(s12)
+        K = np.empty_like(s12) if kappa else None
+        lib().orc_dalitz_intensity(C.byref(self.kin), len(self.res), self._resarr(), _dp(p), len(p),
+                                   anr.real, anr.imag, len(s12), _dp(s12), _dp(s13), _dp(P),
+                                   _dp(K) if kappa else None)
+        return (P, K) if kappa else P
+
+    def nll(self, s12, s13, p=None, anr=1.0 + 0j, grad=False):
+        p = self.p if p is None else _f64(p)
+        s12, s13 = _f64(s12), _f64(s13)
+        out = np.zeros(1)
+        g = np.zeros(len(p)) if grad else None
+        lib().orc_dalitz_nll(C.byref(self.kin), len(self.res), self._resarr(), _dp(p), len(p),
+                             anr.real, anr.imag, self.nbx, self.nby, len(s12), _dp(s12), _dp(s13),
+                             _dp(out), _dp(g) if grad else None)
+        return (out[0], g) if grad else out[0]

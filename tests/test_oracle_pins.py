@@ -1,0 +1,568 @@
+"""Pins of the CPU oracle against closed forms, library routines, invariants and
+finite differences (no GPU).  Each test names the fact that fixes the expected value;
+none of them re-types the oracle's own formula."""
+from __future__ import annotations
+
+import math
+
+import mpmath
+import numpy as np
+import pytest
+from scipy import integrate, optimize, special, stats
+
+import oracle
+from oracle import minimise
+from paper_1311_1753_gb300 import synth
+from tests import oracle_models as om
+
+RNG = np.random.Generator(np.random.PCG64(4242))
+
+
+# --------------------------------------------------------------------------------
+# Faddeeva function (Voigtian, the paper's BW (x) Gaussian of Sec. 4 "Zach's fit")
+# --------------------------------------------------------------------------------
+def _w_mp(z):
+    mpmath.mp.dps = 40
+    zz = mpmath.mpc(z.real, z.imag)
+    return complex(mpmath.exp(-zz * zz) * mpmath.erfc(-1j * zz))
+
+
+def test_faddeeva_vs_mpmath_config2_region():
+    # Config 2: y = Gamma/(2 sqrt2 sigma) ~ 0.094, Re z in [-14.2, 36.6]; widen both.
+    x = RNG.uniform(-16, 40, 300)
+    y = RNG.uniform(0.01, 0.3, 300)
+    z = x + 1j * y
+    w = oracle.faddeeva(z)
+    ref = np.array([_w_mp(v) for v in z])
+    assert np.max(np.abs(w - ref) / np.abs(ref)) < 1e-14
+    # Re w (the Voigtian itself) relative to itself, not to |w|
+    assert np.max(np.abs(w.real - ref.real) / np.abs(ref.real)) < 1e-12
+
+
+def _trap_bound(z, w):
+    # Rounding model of the pole-corrected trapezoid sum: the summand nearest the pole
+    # is ~ h/(pi y) and cancels against the correction term, so the relative error is
+    # a few ulps times (1 + h/(pi y |w|)), h = 0.4.
+    return 8 * 2.2e-16 * (1 + 0.4 / (math.pi * z.imag * np.abs(w)))
+
+
+def test_faddeeva_vs_mpmath_upper_half_plane():
+    x = RNG.uniform(-8, 8, 300)
+    y = 10 ** RNG.uniform(-3, 1.5, 300)
+    z = x + 1j * y
+    w = oracle.faddeeva(z)
+    ref = np.array([_w_mp(v) for v in z])
+    assert np.all(np.abs(w - ref) / np.abs(ref) < _trap_bound(z, ref))
+    big = z.imag > 0.05
+    assert np.max(np.abs(w - ref)[big] / np.abs(ref)[big]) < 1e-14
+
+
+def test_faddeeva_imaginary_axis_is_erfcx():
+    y = np.concatenate([10 ** np.linspace(-3, 2, 60)])
+    w = oracle.faddeeva(1j * y)
+    assert np.max(np.abs(w.imag)) < 1e-15
+    ref = special.erfcx(y)
+    assert np.all(np.abs(w.real / ref - 1) < _trap_bound(1j * y, ref))
+    assert np.max(np.abs(w.real / ref - 1)[y > 0.05]) < 1e-14
+
+
+def test_faddeeva_vs_scipy_wofz_grid():
+    x, y = np.meshgrid(np.linspace(-30, 30, 121), np.array([0.02, 0.0943, 0.5, 3.0, 9.0]))
+    z = (x + 1j * y).ravel()
+    w = oracle.faddeeva(z)
+    assert np.max(np.abs(w / special.wofz(z) - 1)) < 1e-13
+
+
+def test_faddeeva_symmetry_and_asymptote():
+    z = RNG.uniform(-10, 10, 50) + 1j * RNG.uniform(0.01, 5, 50)
+    # w(-conj z) = conj w(z)
+    assert np.max(np.abs(oracle.faddeeva(-np.conj(z)) - np.conj(oracle.faddeeva(z)))) < 1e-15
+    # large |z|: w ~ i/(sqrt(pi) z) (1 + 1/(2 z^2) + 3/(4 z^4) + 15/(8 z^6))
+    zl = np.array([35 + 0.1j, -33 + 0.05j, 31 + 2j, 40 + 0.0943j])
+    asym = 1j / (math.sqrt(math.pi) * zl) * (1 + 1 / (2 * zl**2) + 3 / (4 * zl**4)
+                                             + 15 / (8 * zl**6))
+    assert np.max(np.abs(oracle.faddeeva(zl) / asym - 1)) < 1e-9
+
+
+def test_faddeeva_real_axis_limit():
+    # Re w(x + i0) = exp(-x^2); approach the axis (off the trapezoid nodes x = 0.4 n).
+    x = np.array([0.13, 0.77, 1.51, 2.27, 3.03])
+    w = oracle.faddeeva(x + 1e-9j)
+    assert np.max(np.abs(w.real - np.exp(-x**2))) < 1e-8
+    # Im w(x) = 2/sqrt(pi) Dawson(x)
+    assert np.max(np.abs(w.imag - 2 / math.sqrt(math.pi) * special.dawsn(x))) < 1e-8
+
+
+# --------------------------------------------------------------------------------
+# Leaf PDFs and their normalisation
+# --------------------------------------------------------------------------------
+def _voigt_only(mu, s, w, lo, hi, nbins=10000):
+    m = oracle.Model1D([(lo, hi)], nbins=nbins)
+    v = m.voigt(0, m.param(mu), m.param(s), m.param(w))
+    return m, v
+
+
+def test_voigt_unit_integral_on_real_line():
+    mu, s, w = 0.1455, 3e-4, 8e-5
+    m, v = _voigt_only(mu, s, w, 0.0, 1.0)
+    f = lambda x: m.leaf_shape(v, np.array([x]))[0]
+    # Lorentzian tails: integrate in pieces around the peak, then add the analytic
+    # Cauchy tail beyond +-L (Gaussian part is negligible there).
+    L = 0.05
+    core = sum(integrate.quad(f, a, b, epsabs=0, epsrel=1e-12, limit=400)[0]
+               for a, b in [(mu - L, mu - 0.01), (mu - 0.01, mu), (mu, mu + 0.01),
+                            (mu + 0.01, mu + L)])
+    tail = 2 * (0.5 - math.atan(L / (w / 2)) / math.pi)
+    assert abs(core + tail - 1) < 2e-7
+
+
+def test_voigt_limits_lorentzian_and_gaussian():
+    x = np.linspace(-0.01, 0.01, 41)
+    # sigma -> 0: Cauchy with half-width Gamma/2
+    m, v = _voigt_only(0.0, 1e-9, 1e-3, -1, 1)
+    lor = stats.cauchy.pdf(x, 0.0, 0.5e-3)
+    assert np.max(np.abs(m.leaf_shape(v, x) / lor - 1)) < 1e-8
+    # Gamma -> 0: Gaussian
+    m, v = _voigt_only(0.0, 3e-3, 1e-12, -1, 1)
+    gau = stats.norm.pdf(x, 0.0, 3e-3)
+    assert np.max(np.abs(m.leaf_shape(v, x) / gau - 1)) < 1e-8
+
+
+def test_voigt_grid_norm_within_midpoint_bound():
+    lo, hi = synth.VOIGT_RANGE
+    mu, s, w = 0.1455, 3e-4, 8e-5
+    m, v = _voigt_only(mu, s, w, lo, hi, nbins=10000)
+    N, _ = m.norms()
+    f = lambda x: m.leaf_shape(v, np.array([x]))[0]
+    pts = [lo, mu - 0.003, mu - 0.0005, mu, mu + 0.0005, mu + 0.003, hi]
+    exact = sum(integrate.quad(f, a, b, epsabs=0, epsrel=1e-13, limit=400)[0]
+                for a, b in zip(pts[:-1], pts[1:]))
+    h = (hi - lo) / 10000
+    # |f''| is largest at the peak; bound it by a central difference there.
+    e = 1e-6
+    f2 = abs(f(mu + e) - 2 * f(mu) + f(mu - e)) / e**2
+    bound = (hi - lo) * h**2 * f2 / 24
+    assert abs(N[v] - exact) <= bound
+    assert abs(N[v] / exact - 1) < 1e-5
+
+
+def test_threshold_grid_norm_converges_to_incomplete_gamma():
+    lo, hi = synth.VOIGT_RANGE
+    c, p = 20.0, 0.5
+    D = hi - lo
+    exact = special.gammainc(p + 1, c * D) * special.gamma(p + 1) / c ** (p + 1)
+    errs = []
+    for nb in (1000, 10000, 100000):
+        m = oracle.Model1D([(lo, hi)], nbins=nb)
+        b = m.threshold(0, m.param(lo), m.param(p), m.param(c))
+        N, _ = m.norms()
+        errs.append(abs(N[b] - exact))
+    # midpoint rule on a sqrt endpoint singularity: error ~ h^{3/2}
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 25 < r1 < 40 and 25 < r2 < 40
+    assert errs[1] / exact < 1e-5
+
+
+def test_exponential_norm_closed_form_and_truth_values():
+    m, (a,) = om.exp_model(-1.0)
+    N, dN = m.norms()
+    # Int_0^10 e^{-x} dx = 1 - e^{-10}
+    assert abs(N[0] - (1 - math.exp(-10))) < 1e-15
+    assert abs(N[0] - 0.99995460) < 5e-9
+    # E[x] = d log N / d alpha = Int x e^{-x} / N
+    ex = integrate.quad(lambda x: x * math.exp(-x), 0, 10, epsabs=0, epsrel=1e-13)[0] / N[0]
+    assert abs(dN[0, a] / N[0] - ex) < 1e-13
+    assert abs(ex - 0.99954598) < 5e-9
+    # near alpha = 0 (series branch) against quadrature
+    for al in (1e-5, -3e-4, 0.0, 2.0, -7.5):
+        m2, _ = om.exp_model(al)
+        N2, dN2 = m2.norms()
+        q = integrate.quad(lambda x: math.exp(al * x), 0, 10, epsabs=0, epsrel=1e-13)[0]
+        qd = integrate.quad(lambda x: x * math.exp(al * x), 0, 10, epsabs=0, epsrel=1e-13)[0]
+        assert abs(N2[0] / q - 1) < 1e-13 and abs(dN2[0, 0] / qd - 1) < 1e-12
+
+
+def test_gaussian_norm_vs_normal_cdf():
+    for mu, s, lo, hi in [(0.3, 0.2, -1, 1), (5.0, 0.5, -1, 1), (-3, 0.4, 0, 2)]:
+        m = oracle.Model1D([(lo, hi)])
+        g = m.gauss(0, m.param(mu), m.param(s))
+        N, _ = m.norms()
+        if mu > hi:  # both limits in the lower tail: difference of CDFs
+            d = stats.norm.cdf(hi, mu, s) - stats.norm.cdf(lo, mu, s)
+        else:
+            d = stats.norm.sf(lo, mu, s) - stats.norm.sf(hi, mu, s)
+        ref = s * math.sqrt(2 * math.pi) * d
+        assert abs(N[g] / ref - 1) < 1e-12
+
+
+def test_poly_norm_vs_quadrature():
+    m = oracle.Model1D([(-1.0, 2.0)])
+    co = [m.param(v) for v in (2.0, 0.3, -0.1, 0.05)]
+    pn = m.poly(0, co)
+    N, _ = m.norms()
+    q = integrate.quad(lambda x: 2 + 0.3 * x - 0.1 * x**2 + 0.05 * x**3, -1, 2)[0]
+    assert abs(N[pn] / q - 1) < 1e-14
+
+
+# --------------------------------------------------------------------------------
+# Combinators (Sec. 3): AddPdf fractions, ProdPdf separability
+# --------------------------------------------------------------------------------
+def test_add_pdf_integrates_to_one_on_grid():
+    m, free = om.voigt_model(nbins=10000)
+    lo, hi = synth.VOIGT_RANGE
+    h = (hi - lo) / 10000
+    xb = lo + (np.arange(10000) + 0.5) * h
+    P = np.exp(m.logpdf([xb]))
+    assert abs(h * P.sum() - 1) < 1e-12
+
+
+def test_add_of_identical_children_ignores_fractions():
+    lo, hi = 0.0, 3.0
+    m = oracle.Model1D([(lo, hi)])
+    mu, s = m.param(1.2), m.param(0.4)
+    g1, g2, g3 = m.gauss(0, mu, s), m.gauss(0, mu, s), m.gauss(0, mu, s)
+    f1, f2 = m.param(0.3), m.param(0.45)
+    m.add([g1, g2, g3], [f1, f2])
+    x = RNG.uniform(lo, hi, 100)
+    single = oracle.Model1D([(lo, hi)])
+    single.gauss(0, single.param(1.2), single.param(0.4))
+    assert np.max(np.abs(m.logpdf([x]) - single.logpdf([x]))) < 1e-14
+
+
+def test_add_three_components_vs_scipy_mixture():
+    lo, hi = -2.0, 4.0
+    m = oracle.Model1D([(lo, hi)])
+    ga = m.gauss(0, m.param(0.5), m.param(0.3))
+    ex = m.exp(0, m.param(-0.7))
+    po = m.poly(0, [m.param(1.0), m.param(0.2)])
+    m.add([ga, ex, po], [m.param(0.25), m.param(0.5)])
+    x = RNG.uniform(lo, hi, 200)
+    gpdf = stats.truncnorm.pdf(x, (lo - 0.5) / 0.3, (hi - 0.5) / 0.3, 0.5, 0.3)
+    # truncated exponential and linear densities, normalised by scipy quadrature
+    en = integrate.quad(lambda t: math.exp(-0.7 * t), lo, hi)[0]
+    pn = integrate.quad(lambda t: 1 + 0.2 * t, lo, hi)[0]
+    ref = 0.25 * gpdf + 0.5 * np.exp(-0.7 * x) / en + 0.25 * (1 + 0.2 * x) / pn
+    assert np.max(np.abs(np.exp(m.logpdf([x])) / ref - 1)) < 1e-12
+
+
+def test_prod_pdf_is_separable():
+    # Listing 2: product of exponentials in x and y
+    m = oracle.Model1D([(0.0, 5.0), (0.0, 5.0)])
+    ex = m.exp(0, m.param(-2.4))
+    ey = m.exp(1, m.param(-1.1))
+    m.prod([ex, ey])
+    x = synth.exp_events(1000, -2.4, 0, 5, seed=1)
+    y = synth.exp_events(1000, -1.1, 0, 5, seed=2)
+    mx = oracle.Model1D([(0.0, 5.0)]); mx.exp(0, mx.param(-2.4))
+    my = oracle.Model1D([(0.0, 5.0)]); my.exp(0, my.param(-1.1))
+    assert abs(m.nll([x, y]) - (mx.nll([x]) + my.nll([y]))) < 1e-10
+
+
+# --------------------------------------------------------------------------------
+# Gradients against central finite differences
+# --------------------------------------------------------------------------------
+def _fd_check(fun, p, idx, rel=1e-6):
+    f0, g = fun(p)
+    for k in idx:
+        h = 1e-6 * max(1e-3, abs(p[k])) if abs(p[k]) > 0 else 1e-7
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (fun(pp)[0] - fun(pm)[0]) / (2 * h)
+        scale = max(abs(g[k]), 1e-6 * abs(f0) / max(abs(p[k]), 1e-12))
+        assert abs(fd - g[k]) <= rel * scale + 1e-7, (k, fd, g[k])
+
+
+def test_gradient_config1_fd():
+    m, free = om.exp_model(-1.3)
+    x = synth.exp_events(5000, -1.0)
+    _fd_check(lambda p: m.nll([x], p, grad=True), m.p, free)
+
+
+def test_gradient_config2_fd():
+    m, free = om.voigt_model(nbins=2000)
+    lo, hi = synth.VOIGT_RANGE
+    x = synth.voigt_threshold_events(3000, **synth.VOIGT_TRUTH, lo=lo, hi=hi)
+    p = m.p
+    p[free] *= np.array([1.00001, 1.02, 0.97, 1.05, 0.9])
+    _fd_check(lambda q: m.nll([x], q, grad=True), p, free + [4], rel=2e-6)
+    # x0 (fixed in the workload, free in general): the shape has a sqrt(x - x0) kink, so
+    # difference away from it -- events and grid midpoints stay > 1e-4 above x0.
+    m2, _ = om.voigt_model(nbins=2000)
+    xx = x[x > lo + 1e-3]
+    p2 = m2.p
+    p2[3] = lo - 1e-4
+    _fd_check(lambda q: m2.nll([xx], q, grad=True), p2, [3], rel=2e-6)
+
+
+def test_gradient_gauss_poly_prod_fd():
+    m = oracle.Model1D([(-1.0, 2.0), (0.0, 3.0)])
+    g = m.gauss(0, m.param(0.4), m.param(0.6))
+    po = m.poly(0, [m.param(1.0), m.param(0.3), m.param(0.1)])
+    a = m.add([g, po], [m.param(0.6)])
+    e = m.exp(1, m.param(-0.8))
+    m.prod([a, e])
+    x = RNG.uniform(-1, 2, 500)
+    y = RNG.uniform(0, 3, 500)
+    _fd_check(lambda q: m.nll([x, y], q, grad=True), m.p, list(range(len(m.values))))
+
+
+# --------------------------------------------------------------------------------
+# Dalitz kinematics and amplitudes (Sec. 4)
+# --------------------------------------------------------------------------------
+SPEC = om.load_dalitz_spec()
+KIN = SPEC["kin"]
+
+
+def _fourvectors(s12, s13):
+    """Daughter four-momenta in the parent rest frame from (s12, s13): particle 3 along
+    +z, particles 1 and 2 in the x-z plane (explicit construction, no invariant
+    bounds).  Returns None outside the physical region."""
+    M, m1, m2, m3 = KIN["M"], KIN["m1"], KIN["m2"], KIN["m3"]
+    s23 = M**2 + m1**2 + m2**2 + m3**2 - s12 - s13
+    E1 = (M**2 + m1**2 - s23) / (2 * M)
+    E2 = (M**2 + m2**2 - s13) / (2 * M)
+    E3 = (M**2 + m3**2 - s12) / (2 * M)
+    if min(E1 - m1, E2 - m2, E3 - m3) < 0:
+        return None
+    p1, p2, p3 = (math.sqrt(E**2 - m**2) for E, m in ((E1, m1), (E2, m2), (E3, m3)))
+    # p1 + p2 = -p3 (along -z); angle of p1 from law of cosines
+    c1 = (p2**2 - p1**2 - p3**2) / (2 * p1 * p3)
+    if abs(c1) > 1:
+        return None
+    s1 = math.sqrt(1 - c1 * c1)
+    P1 = np.array([E1, p1 * s1, 0.0, p1 * c1])
+    P3 = np.array([E3, 0.0, 0.0, p3])
+    P2 = np.array([M, 0, 0, 0]) - P1 - P3
+    return P1, P2, P3
+
+
+def _mdot(a, b):
+    return a[0] * b[0] - a[1:] @ b[1:]
+
+
+def _boost_to_rest(p, frame):
+    """Lorentz-boost four-vector p into the rest frame of four-vector ``frame``."""
+    m = math.sqrt(_mdot(frame, frame))
+    beta = frame[1:] / frame[0]
+    b2 = beta @ beta
+    g = frame[0] / m
+    bp = beta @ p[1:]
+    E = g * (p[0] - bp)
+    vec = p[1:] + ((g - 1) * bp / b2 - g * p[0]) * beta if b2 > 0 else p[1:]
+    return np.concatenate([[E], vec])
+
+
+def test_dalitz_region_matches_explicit_kinematics():
+    d = om.dalitz_from_spec(SPEC)
+    x0, x1, y0, y1 = d.box()
+    s12 = RNG.uniform(x0, x1, 4000)
+    s13 = RNG.uniform(y0, y1, 4000)
+    ins = d.inside(s12, s13)
+    phys = np.array([_fourvectors(a, b) is not None for a, b in zip(s12, s13)])
+    assert np.array_equal(ins, phys)
+    # the constructed vectors reproduce the invariants (sum rule included)
+    for a, b in zip(s12[ins][:50], s13[ins][:50]):
+        P1, P2, P3 = _fourvectors(a, b)
+        assert abs(_mdot(P1 + P2, P1 + P2) - a) < 1e-12
+        assert abs(_mdot(P1 + P3, P1 + P3) - b) < 1e-12
+
+
+def test_dalitz_area_converges_to_phase_space_integral():
+    M, m1, m2, m3 = KIN["M"], KIN["m1"], KIN["m2"], KIN["m3"]
+
+    def lam(a, b, c):
+        return a * a + b * b + c * c - 2 * a * b - 2 * a * c - 2 * b * c
+
+    # s13 range at fixed s12 from the Kallen function (textbook form, PDG kinematics)
+    def width(s12):
+        l1 = lam(s12, m1**2, m2**2)
+        l2 = lam(M**2, s12, m3**2)
+        return math.sqrt(max(l1, 0) * max(l2, 0)) / s12
+
+    area = integrate.quad(width, (m1 + m2) ** 2, (M - m3) ** 2, epsabs=0, epsrel=1e-12,
+                          limit=200)[0]
+    d = om.dalitz_from_spec(SPEC)
+    _, cnt = d.norm(anr=1.0 + 0j)
+    x0, x1, y0, y1 = d.box()
+    cell = (x1 - x0) * (y1 - y0) / (512 * 512)
+    assert cnt == 155812
+    assert abs(cnt * cell / area - 1) < 2e-3
+    assert abs(area - 5.02525) < 2e-3
+    # finer grids converge
+    d2 = om.dalitz_from_spec(SPEC, 2048, 2048)
+    _, cnt2 = d2.norm(anr=1.0 + 0j)
+    assert abs(cnt2 * cell / 16 / area - 1) < abs(cnt * cell / area - 1)
+
+
+def test_zemach_factors_vs_four_vectors():
+    d = om.dalitz_from_spec(SPEC)
+    x0, x1, y0, y1 = d.box()
+    n = 0
+    while n < 40:
+        a, b = RNG.uniform(x0, x1), RNG.uniform(y0, y1)
+        fv = _fourvectors(a, b)
+        if fv is None:
+            continue
+        n += 1
+        P = dict(zip((1, 2, 3), fv))
+        for ch, (ia, ib, ic) in enumerate([(1, 2, 3), (1, 3, 2), (2, 3, 1)]):
+            frame = P[ia] + P[ib]
+            qa = _boost_to_rest(P[ia], frame)[1:]
+            kc = _boost_to_rest(P[ic], frame)[1:]
+            kq = kc @ qa
+            k2, q2 = kc @ kc, qa @ qa
+            s1 = d.zemach(ch, 1, a, b)
+            s2 = d.zemach(ch, 2, a, b)
+            assert abs(s1 - 4 * kq) < 1e-10 * max(1, abs(s1))
+            assert abs(s2 - 16 * (kq * kq - k2 * q2 / 3)) < 1e-9 * max(1, abs(s2))
+
+
+def test_breit_wigner_at_pole():
+    d = om.dalitz_from_spec(SPEC)
+    # place a point with s12 = m0^2 for each channel-0 resonance: A_r / S_L = i/(m0 G0)
+    for r, res in enumerate(SPEC["resonances"]):
+        if res["channel"] != 0:
+            continue
+        s12 = res["m0"] ** 2
+        x0, x1, y0, y1 = d.box()
+        grid = np.linspace(y0, y1, 2001)
+        ins = d.inside(np.full_like(grid, s12), grid)
+        s13 = grid[ins][len(grid[ins]) // 3]
+        a = d.amp(r, np.array([s12]), np.array([s13]))[0]
+        S = d.zemach(0, res["spin"], s12, s13)
+        target = 1j / (res["m0"] * res["g0"])
+        assert abs(a / S - target) < 1e-12 * abs(target)
+
+
+def test_dalitz_only_nonresonant_gives_log_area():
+    d = om.dalitz_from_spec(SPEC)
+    p = d.p.copy()
+    p[2::4] = 0.0
+    p[3::4] = 0.0
+    s12 = np.array([0.5, 1.0, 1.3]); s13 = np.array([1.0, 0.9, 1.2])
+    assert d.inside(s12, s13).all()
+    N, cnt = d.norm(p)
+    x0, x1, y0, y1 = d.box()
+    area = cnt * (x1 - x0) * (y1 - y0) / 512**2
+    assert abs(d.nll(s12, s13, p) - 3 * math.log(area)) < 1e-12
+
+
+def test_dalitz_nll_invariant_under_common_rescaling():
+    d = om.dalitz_from_spec(SPEC, 128, 128)
+    s12, s13 = _inside_points(d, 300)
+    p = d.p.copy()
+    base = d.nll(s12, s13, p, anr=1.0 + 0j)
+    lam = 0.7 * np.exp(0.9j)
+    q = p.copy()
+    c = (p[2::4] + 1j * p[3::4]) * lam
+    q[2::4], q[3::4] = c.real, c.imag
+    assert abs(d.nll(s12, s13, q, anr=lam) - base) < 1e-10 * abs(base)
+
+
+def _inside_points(d, n, seed=7):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x0, x1, y0, y1 = d.box()
+    s12, s13 = rng.uniform(x0, x1, 4 * n), rng.uniform(y0, y1, 4 * n)
+    ins = d.inside(s12, s13)
+    return s12[ins][:n].copy(), s13[ins][:n].copy()
+
+
+def test_dalitz_gradient_fd():
+    d = om.dalitz_from_spec(SPEC, 96, 96)
+    s12, s13 = _inside_points(d, 200)
+    p = d.p.copy()
+    p[2::4] *= 1.05
+    p[1::4] *= 0.97
+    _fd_check(lambda q: d.nll(s12, s13, q, grad=True), p, list(range(len(p))), rel=1e-6)
+
+
+def test_dalitz_amplitude_derivatives_fd():
+    d = om.dalitz_from_spec(SPEC)
+    s12, s13 = _inside_points(d, 50)
+    for r, res in enumerate(SPEC["resonances"]):
+        a, dm, dg = d.amp(r, s12, s13, deriv=True)
+        for k, dd in ((4 * r, dm), (4 * r + 1, dg)):
+            h = 1e-7
+            pp, pm = d.p.copy(), d.p.copy()
+            pp[k] += h
+            pm[k] -= h
+            fd = (d.amp(r, s12, s13, pp) - d.amp(r, s12, s13, pm)) / (2 * h)
+            assert np.max(np.abs(fd - dd) / (np.abs(dd) + 1e-3 * np.abs(a))) < 1e-6
+
+
+def test_dalitz_fit_fractions_sum_without_interference():
+    # With resonances in distinct, non-overlapping... instead: the intensity integral is
+    # a Hermitian form c^H G c; check N(c) = sum_rs conj(c_r) G_rs c_s with G assembled
+    # from single and pairwise norms (polarisation identity).
+    d = om.dalitz_from_spec(SPEC, 64, 64)
+    p = d.p.copy()
+    R = len(SPEC["resonances"])
+    def N_of(cvec, anr):
+        q = p.copy()
+        q[2::4], q[3::4] = cvec.real, cvec.imag
+        return d.norm(q, anr=anr)[0]
+    G = np.zeros((R + 1, R + 1), complex)
+    basis = lambda i: (np.eye(R)[i - 1] if i > 0 else np.zeros(R)).astype(complex)
+    for i in range(R + 1):
+        for j in range(R + 1):
+            ci, cj = basis(i), basis(j)
+            ai, aj = (1.0 if i == 0 else 0.0), (1.0 if j == 0 else 0.0)
+            re = N_of(ci + cj, ai + aj) - N_of(ci - cj, ai - aj)
+            im = N_of(ci + 1j * cj, ai + 1j * aj) - N_of(ci - 1j * cj, ai - 1j * aj)
+            G[i, j] = (re - 1j * im) / 4
+    c = np.concatenate([[1.0], p[2::4] + 1j * p[3::4]])
+    assert np.allclose(G, G.conj().T, atol=1e-9)
+    assert abs((c.conj() @ G @ c).real / d.norm(p)[0] - 1) < 1e-12
+
+
+# --------------------------------------------------------------------------------
+# Minimiser
+# --------------------------------------------------------------------------------
+def test_minimiser_quadratic_bowl():
+    A = np.array([[4.0, 1.0, 0.5], [1.0, 3.0, 0.2], [0.5, 0.2, 2.0]])
+    x_star = np.array([0.3, -1.2, 2.0])
+    fg = lambda x: (0.5 * (x - x_star) @ A @ (x - x_star), A @ (x - x_star))
+    r = minimise.fit(fg, np.zeros(3), step=np.full(3, 0.5), tol=1e-16)
+    assert r.converged
+    assert np.max(np.abs(r.x - x_star)) < 1e-8
+    # f = NLL-like with up = 0.5: covariance = H^-1
+    assert np.max(np.abs(r.cov - np.linalg.inv(A))) < 1e-8
+
+
+def test_minimiser_rosenbrock_with_bounds():
+    def fg(x):
+        a, b = x
+        f = (1 - a) ** 2 + 100 * (b - a * a) ** 2
+        return f, np.array([-2 * (1 - a) - 400 * a * (b - a * a), 200 * (b - a * a)])
+    r = minimise.fit(fg, np.array([-1.2, 1.0]), step=np.array([0.1, 0.1]),
+                     lo=np.array([-5.0, -5.0]), hi=np.array([5.0, 5.0]), tol=1e-14)
+    assert r.converged and np.max(np.abs(r.x - 1)) < 1e-5
+
+
+def test_config1_fit_matches_mle_root_and_error():
+    m, (a,) = om.exp_model(-2.0)
+    x = synth.exp_events(100_000, -1.0)
+    mean = x.mean()
+
+    # stationarity: mean(x) = E_alpha[x] = Int x e^{a x} / Int e^{a x} (quadrature)
+    def ex(al):
+        num = integrate.quad(lambda t: t * math.exp(al * t), 0, 10, epsabs=0, epsrel=1e-13)[0]
+        den = integrate.quad(lambda t: math.exp(al * t), 0, 10, epsabs=0, epsrel=1e-13)[0]
+        return num / den - mean
+
+    root = optimize.brentq(ex, -1.5, -0.5, xtol=1e-15, rtol=1e-15)
+    fg = lambda q: m.nll([x], np.array([q[0]]), grad=True)
+    r = minimise.fit(fg, np.array([-2.0]), step=np.array([0.1]), lo=np.array([-10.0]),
+                     hi=np.array([10.0]))
+    assert r.converged
+    # sigma_alpha = 1/sqrt(n Var_alpha(x)), Var from quadrature
+    def var(al):
+        den = integrate.quad(lambda t: math.exp(al * t), 0, 10)[0]
+        m1 = integrate.quad(lambda t: t * math.exp(al * t), 0, 10)[0] / den
+        m2 = integrate.quad(lambda t: t * t * math.exp(al * t), 0, 10)[0] / den
+        return m2 - m1 * m1
+    sig = 1 / math.sqrt(len(x) * var(root))
+    assert abs(r.x[0] - root) < 1e-3 * sig
+    assert abs(r.err[0] / sig - 1) < 1e-3
+    assert abs(sig - 0.003169) < 2e-5
