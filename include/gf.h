@@ -1,0 +1,228 @@
+/*
+ * gf.h -- C ABI of the GB300 (sm_103a) unbinned maximum-likelihood engine.
+ *
+ * The calls follow the paper's statement of a fit (Andreassen et al., "GooFit: A
+ * library for massively parallelising maximum-likelihood fits", arXiv:1311.1753,
+ * Sec. 2): declare observables and fit parameters (Variable), build the PDF
+ * (GooPdf and its combinations, Sec. 3), load an unbinned dataset
+ * (UnbinnedDataSet / setData), evaluate the likelihood and fit (FitManager).
+ *
+ * Conventions for every call:
+ *  - Return value: GF_OK (0) or a negative GF_E* code; nothing aborts, and no GPU
+ *    error is raised on purpose.  gf_last_error() gives a message for the last failure
+ *    on a context.
+ *  - Pointers are plain host pointers unless the name says "_device"; arrays passed
+ *    in are copied, so the caller keeps ownership and may free them after the call.
+ *  - A context (gf_ctx) owns every object created through it (observables,
+ *    parameters, PDF nodes, device memory, CUDA stream).  A context is not
+ *    thread-safe: use one per host thread.
+ *  - Identifiers (observable, parameter, node) are small non-negative ints scoped
+ *    to their context.
+ */
+#ifndef GF_H
+#define GF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------- */
+#define GF_OK 0
+#define GF_EINVAL (-1)      /* bad argument, unknown id, cycle, event out of range   */
+#define GF_ENOMEM (-2)      /* host or device allocation failed                      */
+#define GF_ECUDA (-3)       /* a CUDA runtime call failed                            */
+#define GF_ENONFINITE (-4)  /* some P_i <= 0 or non-finite: nll set to +inf          */
+#define GF_ENOCONV (-5)     /* minimiser stopped without meeting the EDM tolerance   */
+#define GF_ETIMEOUT (-6)    /* a bounded wait ran out (server)                       */
+#define GF_ESTATE (-7)      /* call out of order (e.g. evaluate before gf_set_data)  */
+
+/* ---- precision modes -------------------------------------------------------------- */
+#define GF_FP64 0   /* every per-event and per-cell operation in FP64                   */
+#define GF_MIXED 1  /* per-event PDF/amplitude arithmetic in FP32; FP64 for the log-sum */
+                    /* across threads and blocks, the normalisation integrals and the   */
+                    /* Voigtian's Faddeeva function                                      */
+
+typedef struct gf_ctx gf_ctx;
+typedef struct gf_dataset gf_dataset;
+
+/* ---- context -------------------------------------------------------------------- */
+/* Create a context on CUDA device `device` with precision GF_FP64 or GF_MIXED.
+ * The context creates its own CUDA stream.  *out is NULL on failure. */
+int gf_create(gf_ctx** out, int device, int precision);
+/* Release every object, device buffer and stream of the context.  NULL is a no-op. */
+int gf_destroy(gf_ctx* ctx);
+/* Run all of the context's GPU work on `stream` (a cudaStream_t on the context's
+ * device, owned by the caller and alive until gf_destroy or another gf_set_stream);
+ * NULL returns to the context's own stream. */
+int gf_set_stream(gf_ctx* ctx, void* stream);
+/* Text for a status code (static storage). */
+const char* gf_strerror(int code);
+/* Copy the message of the context's last failure into buf (NUL-terminated). */
+int gf_last_error(gf_ctx* ctx, char* buf, size_t n);
+
+/* ---- variables (Sec. 2: the two uses of Variable) -------------------------------- */
+/* Observable with range [lo, hi] (Listing 1: Variable(name, lo, hi)); lo < hi. */
+int gf_observable(gf_ctx* ctx, const char* name, double lo, double hi, int* id);
+/* Fit parameter (Listing 1: Variable(name, init, step, lo, hi)).  lo < hi bounds the
+ * parameter with MINUIT's sine transform; lo == hi == 0 leaves it unbounded.  step is
+ * the minimiser's initial scale (> 0). */
+int gf_parameter(gf_ctx* ctx, const char* name, double init, double step, double lo, double hi,
+                 int* id);
+/* Fix (1) or release (0) a parameter.  Fixed parameters keep their value and are not
+ * part of theta. */
+int gf_set_fixed(gf_ctx* ctx, int par, int fixed);
+/* Set a parameter's current value (the start value of the next gf_fit). */
+int gf_set_value(gf_ctx* ctx, int par, double value);
+int gf_get_value(gf_ctx* ctx, int par, double* value);
+/* Number of free parameters and their ids in theta order (declaration order).
+ * ids may be NULL; otherwise it has room for *n entries. */
+int gf_free_params(gf_ctx* ctx, int* n, int* ids);
+
+/* ---- PDF nodes (Sec. 3, Listing 3-4) ---------------------------------------------
+ * Leaves are normalised on their observable's range: analytically where a closed form
+ * exists (exponential, Gaussian, polynomial), otherwise by the midpoint rule on the
+ * node's grid (default 10,000 bins; gf_set_norm_grid).  Arguments named after
+ * parameters are parameter ids. */
+/* e^{alpha x} (Listing 1, ExpPdf). */
+int gf_pdf_exp(gf_ctx* ctx, int obs, int alpha, int* node);
+/* exp(-(x-mu)^2/(2 sigma^2)) (Listing 3, GaussianPdf). */
+int gf_pdf_gauss(gf_ctx* ctx, int obs, int mu, int sigma, int* node);
+/* Voigtian: Breit-Wigner of FWHM `width` convolved with a Gaussian of std `sigma`
+ * (Sec. 4: the line shape of the D*+ width fit), Re w(z)/(sigma sqrt(2 pi)),
+ * z = (x - mu + i width/2)/(sigma sqrt 2). */
+int gf_pdf_voigt(gf_ctx* ctx, int obs, int mu, int sigma, int width, int* node);
+/* Threshold shape (x - x0)^power exp(-c (x - x0)) for x > x0, 0 below. */
+int gf_pdf_threshold(gf_ctx* ctx, int obs, int x0, int power, int c, int* node);
+/* Polynomial sum_k coef[k] x^k, ncoef <= 8. */
+int gf_pdf_poly(gf_ctx* ctx, int obs, int ncoef, const int* coefs, int* node);
+/* AddPdf (Sec. 3): sum_{k<n-1} f_k P_k + (1 - sum f) P_{n-1}; fracs has n-1 ids, n <= 8. */
+int gf_pdf_add(gf_ctx* ctx, int n, const int* nodes, const int* fracs, int* node);
+/* ProdPdf (Sec. 3, Listing 2): prod_k P_k; the factors must use distinct observables. */
+int gf_pdf_prod(gf_ctx* ctx, int n, const int* nodes, int* node);
+
+/* Three-body decay M -> 1 2 3 on the Dalitz plot (Sec. 4).  Observables are
+ * s12 = m12^2 and s13 = m13^2 (their declared ranges are ignored: the kinematic
+ * region decides).  Amplitude A = a_NR + sum_r c_r F_L S_L BW_r with a fixed
+ * non-resonant a_NR = 1, c_r = re + i im, relativistic Breit-Wigner
+ * BW = 1/(m0^2 - s - i m0 Gamma(m)), Gamma(m) = Gamma0 (q/q0)^{2L+1} (m0/m) F_L^2,
+ * Blatt-Weisskopf F_L at the resonance vertex with radius R, Zemach spin factors S_L;
+ * P = |A|^2, normalised on a grid of cell centres inside the region (512 x 512 by
+ * default). */
+typedef struct {
+  double M, m1, m2, m3; /* parent and daughter masses (GeV) */
+  double R;             /* Blatt-Weisskopf radius (GeV^-1) */
+} gf_dalitz_kin;
+typedef struct {
+  int channel;          /* 0: (12) bachelor 3; 1: (13) bachelor 2; 2: (23) bachelor 1 */
+  int spin;             /* 0, 1 or 2 */
+  int mass, width;      /* parameter ids of m0, Gamma0 */
+  int re, im;           /* parameter ids of the coefficient */
+} gf_resonance;
+int gf_pdf_dalitz(gf_ctx* ctx, int obs12, int obs13, const gf_dalitz_kin* kin, int nres,
+                  const gf_resonance* res, int* node);
+/* Grid of the node's numerical normalisation: nbins_x bins for a 1D leaf, or
+ * nbins_x x nbins_y cells for a Dalitz node. */
+int gf_set_norm_grid(gf_ctx* ctx, int node, int nbins_x, int nbins_y);
+/* 1 if (s12, s13) lies inside the kinematic region of the Dalitz node, else 0, for n
+ * points (host arrays). */
+int gf_dalitz_inside(gf_ctx* ctx, int node, int64_t n, const double* s12, const double* s13,
+                     int8_t* out);
+
+/* ---- data (Sec. 2: UnbinnedDataSet, addEvent, setData) ------------------------------ */
+/* Host-side dataset over nobs observables (ids copied). */
+int gf_dataset_create(gf_ctx* ctx, int nobs, const int* obs, gf_dataset** ds);
+/* Append n events given as one host column per observable (cols[k][i] is observable
+ * obs[k] of event i).  Any event outside an observable's range (or, for a Dalitz
+ * model's observables, outside the kinematic region at gf_set_data) makes the call
+ * fail with GF_EINVAL and adds nothing. */
+int gf_dataset_add_events(gf_dataset* ds, int64_t n, const double* const* cols);
+int64_t gf_dataset_size(const gf_dataset* ds);
+int gf_dataset_destroy(gf_dataset* ds);
+/* Compile the tree rooted at `root`, copy the dataset's columns to device memory
+ * (structure of arrays, 256-byte aligned, padded), and invalidate the normalisation
+ * caches.  The dataset stays owned by the caller. */
+int gf_set_data(gf_ctx* ctx, int root, const gf_dataset* ds);
+/* As gf_set_data, but the n events are already in device memory: dev_cols[k] is a
+ * device pointer to n doubles (observable obs[k]), 16-byte aligned, owned by the caller
+ * and alive while the context uses it.  Nothing is copied and no range check is made. */
+int gf_set_data_device(gf_ctx* ctx, int root, int nobs, const int* obs, int64_t n,
+                       const double* const* dev_cols);
+
+/* ---- evaluation (Sec. 2: evaluate and metric, summed over events) ------------------ */
+/* NLL(theta) = -sum_i log P(x_i; theta) with P normalised, at theta = the free
+ * parameters in gf_free_params order (external units).  Blocking: returns when the
+ * value is on the host.  Non-finite result: *nll = +inf, GF_ENONFINITE. */
+int gf_nll(gf_ctx* ctx, const double* theta, double* nll);
+/* NLL and its gradient over theta from the same event pass. */
+int gf_nll_grad(gf_ctx* ctx, const double* theta, double* nll, double* grad);
+/* Per-event log P_i at theta into out (host array of n doubles, event order). */
+int gf_logpdf(gf_ctx* ctx, const double* theta, double* out);
+/* Same into a device array of n doubles. */
+int gf_logpdf_device(gf_ctx* ctx, const double* theta, double* out_dev);
+/* The Dalitz node's normalisation Gram matrix G (row-major (nres+1)^2 complex as
+ * interleaved re, im; index 0 is a_NR) at theta: N = c^H G c.  Fit fractions follow
+ * as |c_r|^2 G_rr / N. */
+int gf_dalitz_gram(gf_ctx* ctx, const double* theta, double* G);
+
+/* ---- fit (Sec. 2: FitManager + Migrad, here a quasi-Newton of this library) -------- */
+typedef struct {
+  double tol;      /* EDM tolerance (default 1e-6 when <= 0) */
+  int max_calls;   /* evaluation budget (default 5000 when <= 0) */
+  int use_grad;    /* 1: fused analytic gradient; 0: central differences of gf_nll */
+  double up;       /* error definition (0.5 for a negative log-likelihood; <= 0 -> 0.5) */
+  int hesse;       /* 1: covariance from the Hessian by differences of the gradient */
+} gf_fit_opts;
+typedef struct {
+  double nll;      /* NLL at the minimum */
+  double edm;      /* estimated distance to minimum */
+  int n_calls;     /* likelihood evaluations */
+  int n_iter;      /* quasi-Newton iterations */
+  int status;      /* GF_OK or GF_ENOCONV */
+  double* theta;   /* caller-allocated, n_free: fitted values (external units) */
+  double* err;     /* caller-allocated, n_free, or NULL: parabolic errors */
+  double* cov;     /* caller-allocated, n_free^2, or NULL: covariance matrix */
+} gf_fit_result;
+/* Minimise from the parameters' current values; the fitted values become the current
+ * values.  Returns the same status as res->status. */
+int gf_fit(gf_ctx* ctx, const gf_fit_opts* opts, gf_fit_result* res);
+
+/* ---- fit server (continuous batching of many fits) ----------------------------------- */
+typedef struct gf_server gf_server;
+typedef struct {
+  int device;
+  int precision;        /* GF_FP64 or GF_MIXED for every admitted fit */
+  size_t mem_budget;    /* bytes of device memory the resident fits may hold */
+  int max_slots;        /* maximum number of fits resident at once */
+  double wait_timeout_s;/* bound on any internal wait (default 60 s) */
+} gf_server_opts;
+/* Start a server with its worker thread. */
+int gf_server_create(const gf_server_opts* opts, gf_server** out);
+/* Submit a fit: `model` is a context holding observables, parameters and the PDF
+ * tree (no data needed); `ds` the events; `root` the PDF node.  The server takes
+ * ownership of both (it destroys them when the fit is done); the request is admitted
+ * when a slot and enough of the memory budget are free.  ticket identifies it. */
+int gf_server_submit(gf_server* srv, gf_ctx* model, gf_dataset* ds, int root,
+                     const gf_fit_opts* opts, uint64_t* ticket);
+/* Non-blocking poll: *done = 1 when finished, then res is filled (caller arrays sized by
+ * gf_server_nfree), plus submit-to-done latency in seconds. */
+int gf_server_poll(gf_server* srv, uint64_t ticket, gf_fit_result* res, double* latency_s,
+                   int* done);
+int gf_server_nfree(gf_server* srv, uint64_t ticket, int* n);
+/* Wait until every submitted fit has finished (bounded by wait_timeout_s per fit). */
+int gf_server_drain(gf_server* srv);
+/* Counters: ticks run, GPU launches made, peak slots in use. */
+int gf_server_stats(gf_server* srv, int64_t* ticks, int64_t* launches, int* peak_slots);
+int gf_server_destroy(gf_server* srv);
+
+/* ---- introspection ----------------------------------------------------------------- */
+/* Device-side time of the last evaluation's kernels (ms, CUDA events) and the number of
+ * kernel launches it made. */
+int gf_last_eval_stats(gf_ctx* ctx, double* kernel_ms, int* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GF_H */

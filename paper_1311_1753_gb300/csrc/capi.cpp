@@ -1,0 +1,1193 @@
+// capi.cpp -- the C ABI (include/gf.h): contexts, variables, PDF nodes, datasets, the
+// PDF-tree compiler and the evaluation path.
+//
+// The paper's FitManager hands MINUIT a function that copies the parameters to the
+// device, runs the per-event evaluate/metric over all events and returns the reduced
+// sum (Sec. 2).  Here one evaluation is: one host->device copy of theta, one or two
+// kernel launches (normalisation, then the event stream whose last block finishes the
+// deterministic reduction), one device->host copy of 1 + n_free doubles.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+
+using namespace gfi;
+
+namespace gfi {
+
+int set_error(gf_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+static int cuda_fail(gf_ctx* ctx, cudaError_t e, const char* where) {
+  return set_error(ctx, GF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+// ---- Weideman coefficients --------------------------------------------------------------
+// a_n = (1/2pi) Int_{-pi}^{pi} f(theta) e^{-i n theta} d theta with
+// f = (L^2 + t^2) e^{-t^2}, t = L tan(theta/2): a periodic smooth function, so the
+// midpoint rule on M points converges faster than any power of 1/M.
+static void weideman_coeffs(int N, double L, double* a) {
+  const int M = 16 * N;
+  const double pi = 3.14159265358979323846;
+  for (int n = 0; n <= N; ++n) a[n] = 0.0;
+  for (int k = 0; k < M; ++k) {
+    const double th = -pi + 2.0 * pi * (k + 0.5) / M;
+    const double t = L * std::tan(0.5 * th);
+    const double f = (L * L + t * t) * std::exp(-t * t);
+    for (int n = 0; n <= N; ++n) a[n] += f * std::cos(n * th);
+  }
+  for (int n = 0; n <= N; ++n) a[n] /= M;
+}
+
+const WeidCoef& weideman() {
+  static WeidCoef W;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    W.L = std::pow(2.0, -0.25) * std::sqrt((double)kWeidN);
+    weideman_coeffs(kWeidN, W.L, W.a);
+    const double Lf = std::pow(2.0, -0.25) * std::sqrt((double)kWeidNf);
+    double af[kWeidNf + 1];
+    weideman_coeffs(kWeidNf, Lf, af);
+    W.Lf = (float)Lf;
+    for (int n = 0; n <= kWeidNf; ++n) W.af[n] = (float)af[n];
+  });
+  return W;
+}
+
+int nfree(const gf_ctx* ctx) {
+  int n = 0;
+  for (auto& p : ctx->pars) n += p.fixed ? 0 : 1;
+  return n;
+}
+
+}  // namespace gfi
+
+// ---- small helpers ------------------------------------------------------------------------------
+static bool valid_par(gf_ctx* c, int p) { return p >= 0 && p < (int)c->pars.size(); }
+static bool valid_obs(gf_ctx* c, int o) { return o >= 0 && o < (int)c->obs.size(); }
+static bool valid_node(gf_ctx* c, int n) { return n >= 0 && n < (int)c->nodes.size(); }
+
+static int add_node(gf_ctx* ctx, NodeDef&& nd, int* node) {
+  if (!node) return set_error(ctx, GF_EINVAL, "node output pointer is NULL");
+  ctx->nodes.push_back(std::move(nd));
+  *node = (int)ctx->nodes.size() - 1;
+  ctx->compiled = false;
+  return GF_OK;
+}
+
+static int leaf(gf_ctx* ctx, int type, int obs, std::vector<int> pars, int* node) {
+  if (!ctx) return GF_EINVAL;
+  if (!valid_obs(ctx, obs)) return set_error(ctx, GF_EINVAL, "unknown observable id");
+  for (int p : pars)
+    if (!valid_par(ctx, p)) return set_error(ctx, GF_EINVAL, "unknown parameter id");
+  NodeDef nd;
+  nd.type = type;
+  nd.obs = obs;
+  nd.pars = std::move(pars);
+  nd.nbx = (type == N_VOIGT || type == N_THRESH) ? 10000 : 0;
+  return add_node(ctx, std::move(nd), node);
+}
+
+// ---- device memory ------------------------------------------------------------------------------
+static void free_dev(gf_ctx* ctx) {
+  DevState& d = ctx->dev;
+  if (d.owns_cols)
+    for (double* p : d.cols) cudaFree(p);
+  d.cols.clear();
+  d.owns_cols = false;
+  cudaFree(d.theta);
+  cudaFree(d.derived);
+  cudaFree(d.partials);
+  cudaFree(d.partials2);
+  cudaFree(d.counters);
+  cudaFree(d.result);
+  cudaFree(d.norm_out);
+  cudaFree(d.inside);
+  cudaFree(d.grid_cols);
+  cudaFree(d.gram);
+  cudaFree(d.ev_cache);
+  cudaFree(d.fcols);
+  cudaFree(d.todo);
+  if (d.h_theta) cudaFreeHost(d.h_theta);
+  if (d.h_result) cudaFreeHost(d.h_result);
+  if (d.ev0) cudaEventDestroy(d.ev0);
+  if (d.ev1) cudaEventDestroy(d.ev1);
+  d = DevState();
+}
+
+// ---- C ABI: context -------------------------------------------------------------------------------
+extern "C" {
+
+int gf_create(gf_ctx** out, int device, int precision) {
+  if (!out) return GF_EINVAL;
+  *out = nullptr;
+  if (precision != GF_FP64 && precision != GF_MIXED) return GF_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return GF_ECUDA;
+  }
+  gf_ctx* ctx = new (std::nothrow) gf_ctx();
+  if (!ctx) return GF_ENOMEM;
+  ctx->device = device;
+  ctx->precision = precision;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return GF_ECUDA;
+  }
+  ctx->stream = ctx->own_stream;
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  weideman();
+  *out = ctx;
+  return GF_OK;
+}
+
+int gf_destroy(gf_ctx* ctx) {
+  if (!ctx) return GF_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_dev(ctx);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+  delete ctx;
+  return GF_OK;
+}
+
+int gf_set_stream(gf_ctx* ctx, void* stream) {
+  if (!ctx) return GF_EINVAL;
+  ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+  return GF_OK;
+}
+
+const char* gf_strerror(int code) {
+  switch (code) {
+    case GF_OK: return "ok";
+    case GF_EINVAL: return "invalid argument";
+    case GF_ENOMEM: return "out of memory";
+    case GF_ECUDA: return "CUDA runtime error";
+    case GF_ENONFINITE: return "non-finite likelihood (some P_i <= 0 or not finite)";
+    case GF_ENOCONV: return "minimiser did not converge";
+    case GF_ETIMEOUT: return "timed out";
+    case GF_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+int gf_last_error(gf_ctx* ctx, char* buf, size_t n) {
+  if (!ctx || !buf || n == 0) return GF_EINVAL;
+  std::snprintf(buf, n, "%s", ctx->err.c_str());
+  return GF_OK;
+}
+
+// ---- variables ---------------------------------------------------------------------------------------
+int gf_observable(gf_ctx* ctx, const char* name, double lo, double hi, int* id) {
+  if (!ctx || !id) return GF_EINVAL;
+  if (!(lo < hi) || !std::isfinite(lo) || !std::isfinite(hi))
+    return set_error(ctx, GF_EINVAL, "observable needs finite lo < hi");
+  ctx->obs.push_back({name ? name : "", lo, hi});
+  *id = (int)ctx->obs.size() - 1;
+  return GF_OK;
+}
+
+int gf_parameter(gf_ctx* ctx, const char* name, double init, double step, double lo, double hi,
+                 int* id) {
+  if (!ctx || !id) return GF_EINVAL;
+  if (!std::isfinite(init) || !(step > 0) || !std::isfinite(step))
+    return set_error(ctx, GF_EINVAL, "parameter needs a finite value and a step > 0");
+  if (!(lo == 0 && hi == 0)) {
+    if (!(lo < hi)) return set_error(ctx, GF_EINVAL, "parameter limits need lo < hi");
+    if (init < lo || init > hi) return set_error(ctx, GF_EINVAL, "initial value outside limits");
+  }
+  ctx->pars.push_back({name ? name : "", init, step, lo, hi, false});
+  *id = (int)ctx->pars.size() - 1;
+  ctx->compiled = false;
+  return GF_OK;
+}
+
+int gf_set_fixed(gf_ctx* ctx, int par, int fixed) {
+  if (!ctx || !valid_par(ctx, par)) return GF_EINVAL;
+  if (ctx->pars[par].fixed != (fixed != 0)) {
+    ctx->pars[par].fixed = fixed != 0;
+    ctx->compiled = false;
+  }
+  return GF_OK;
+}
+
+int gf_set_value(gf_ctx* ctx, int par, double value) {
+  if (!ctx || !valid_par(ctx, par) || !std::isfinite(value)) return GF_EINVAL;
+  const ParDef& p = ctx->pars[par];
+  if (!(p.lo == 0 && p.hi == 0) && (value < p.lo || value > p.hi))
+    return set_error(ctx, GF_EINVAL, "value outside the parameter's limits");
+  ctx->pars[par].value = value;
+  return GF_OK;
+}
+
+int gf_get_value(gf_ctx* ctx, int par, double* value) {
+  if (!ctx || !valid_par(ctx, par) || !value) return GF_EINVAL;
+  *value = ctx->pars[par].value;
+  return GF_OK;
+}
+
+int gf_free_params(gf_ctx* ctx, int* n, int* ids) {
+  if (!ctx || !n) return GF_EINVAL;
+  int k = 0;
+  for (int i = 0; i < (int)ctx->pars.size(); ++i)
+    if (!ctx->pars[i].fixed) {
+      if (ids) ids[k] = i;
+      ++k;
+    }
+  *n = k;
+  return GF_OK;
+}
+
+// ---- PDF nodes ----------------------------------------------------------------------------------------
+int gf_pdf_exp(gf_ctx* ctx, int obs, int alpha, int* node) {
+  return leaf(ctx, N_EXP, obs, {alpha}, node);
+}
+int gf_pdf_gauss(gf_ctx* ctx, int obs, int mu, int sigma, int* node) {
+  return leaf(ctx, N_GAUSS, obs, {mu, sigma}, node);
+}
+int gf_pdf_voigt(gf_ctx* ctx, int obs, int mu, int sigma, int width, int* node) {
+  return leaf(ctx, N_VOIGT, obs, {mu, sigma, width}, node);
+}
+int gf_pdf_threshold(gf_ctx* ctx, int obs, int x0, int power, int c, int* node) {
+  return leaf(ctx, N_THRESH, obs, {x0, power, c}, node);
+}
+int gf_pdf_poly(gf_ctx* ctx, int obs, int ncoef, const int* coefs, int* node) {
+  if (!ctx) return GF_EINVAL;
+  if (ncoef < 1 || ncoef > kMaxLocal || !coefs)
+    return set_error(ctx, GF_EINVAL, "polynomial needs 1..8 coefficients");
+  return leaf(ctx, N_POLY, obs, std::vector<int>(coefs, coefs + ncoef), node);
+}
+
+int gf_pdf_add(gf_ctx* ctx, int n, const int* nodes, const int* fracs, int* node) {
+  if (!ctx) return GF_EINVAL;
+  if (n < 2 || n > kMaxLocal || !nodes || !fracs)
+    return set_error(ctx, GF_EINVAL, "AddPdf needs 2..8 components and n-1 fractions");
+  NodeDef nd;
+  nd.type = N_ADD;
+  for (int k = 0; k < n; ++k) {
+    if (!valid_node(ctx, nodes[k]) || ctx->nodes[nodes[k]].type == N_DALITZ)
+      return set_error(ctx, GF_EINVAL, "AddPdf: unknown or non-1D component");
+    nd.children.push_back(nodes[k]);
+  }
+  for (int k = 0; k < n - 1; ++k) {
+    if (!valid_par(ctx, fracs[k])) return set_error(ctx, GF_EINVAL, "AddPdf: unknown fraction id");
+    nd.pars.push_back(fracs[k]);
+  }
+  return add_node(ctx, std::move(nd), node);
+}
+
+int gf_pdf_prod(gf_ctx* ctx, int n, const int* nodes, int* node) {
+  if (!ctx) return GF_EINVAL;
+  if (n < 2 || n > kMaxLocal || !nodes)
+    return set_error(ctx, GF_EINVAL, "ProdPdf needs 2..8 factors");
+  NodeDef nd;
+  nd.type = N_PROD;
+  for (int k = 0; k < n; ++k) {
+    if (!valid_node(ctx, nodes[k]) || ctx->nodes[nodes[k]].type == N_DALITZ)
+      return set_error(ctx, GF_EINVAL, "ProdPdf: unknown or non-1D factor");
+    nd.children.push_back(nodes[k]);
+  }
+  return add_node(ctx, std::move(nd), node);
+}
+
+int gf_pdf_dalitz(gf_ctx* ctx, int obs12, int obs13, const gf_dalitz_kin* kin, int nres,
+                  const gf_resonance* res, int* node) {
+  if (!ctx) return GF_EINVAL;
+  if (!valid_obs(ctx, obs12) || !valid_obs(ctx, obs13) || obs12 == obs13 || !kin)
+    return set_error(ctx, GF_EINVAL, "Dalitz: bad observables or kinematics");
+  if (nres < 0 || nres > kMaxRes || (nres > 0 && !res))
+    return set_error(ctx, GF_EINVAL, "Dalitz: 0..12 resonances");
+  if (!(kin->M > kin->m1 + kin->m2 + kin->m3) || !(kin->m1 > 0) || !(kin->m2 > 0) ||
+      !(kin->m3 > 0) || !(kin->R >= 0))
+    return set_error(ctx, GF_EINVAL, "Dalitz: masses must satisfy M > m1 + m2 + m3 > 0");
+  NodeDef nd;
+  nd.type = N_DALITZ;
+  nd.obs = obs12;
+  nd.obs2 = obs13;
+  nd.kin = *kin;
+  nd.nbx = 512;
+  nd.nby = 512;
+  for (int r = 0; r < nres; ++r) {
+    const gf_resonance& R = res[r];
+    if (R.channel < 0 || R.channel > 2 || R.spin < 0 || R.spin > 2 || !valid_par(ctx, R.mass) ||
+        !valid_par(ctx, R.width) || !valid_par(ctx, R.re) || !valid_par(ctx, R.im))
+      return set_error(ctx, GF_EINVAL, "Dalitz: bad resonance (channel 0..2, spin 0..2, ids)");
+    nd.res.push_back(R);
+  }
+  return add_node(ctx, std::move(nd), node);
+}
+
+int gf_set_norm_grid(gf_ctx* ctx, int node, int nbins_x, int nbins_y) {
+  if (!ctx || !valid_node(ctx, node)) return GF_EINVAL;
+  NodeDef& nd = ctx->nodes[node];
+  if (nd.type == N_DALITZ) {
+    if (nbins_x < 1 || nbins_y < 1 || (int64_t)nbins_x * nbins_y > (1 << 26))
+      return set_error(ctx, GF_EINVAL, "Dalitz grid: 1 <= nbx*nby <= 2^26");
+    nd.nby = nbins_y;
+  } else if (nd.type == N_VOIGT || nd.type == N_THRESH) {
+    if (nbins_x < 1 || nbins_x > (1 << 24)) return set_error(ctx, GF_EINVAL, "grid: 1..2^24 bins");
+  } else {
+    return set_error(ctx, GF_EINVAL, "node has an analytic normalisation");
+  }
+  nd.nbx = nbins_x;
+  ctx->compiled = false;
+  ctx->dev.gram_valid = false;
+  ctx->dev.mask_built = false;
+  return GF_OK;
+}
+
+}  // extern "C"
+
+// ---- Dalitz host-side geometry --------------------------------------------------------------------
+static void fill_channel(DalitzChannel& c, double M, double ma, double mb, double mc) {
+  c.ma2 = ma * ma;
+  c.mb2 = mb * mb;
+  c.mc2 = mc * mc;
+  c.thrA = (ma + mb) * (ma + mb);
+  c.thrB = (ma - mb) * (ma - mb);
+  c.k1 = (M * M - mc * mc) * (ma * ma - mb * mb);
+  c.a2c = 2 * M * M + 2 * mc * mc;
+  c.a2k = (M * M - mc * mc) * (M * M - mc * mc);
+}
+
+static void dalitz_geometry(const NodeDef& nd, DalitzPlan& D) {
+  const gf_dalitz_kin& k = nd.kin;
+  D.M = k.M;
+  D.m1 = k.m1;
+  D.m2 = k.m2;
+  D.m3 = k.m3;
+  D.M2 = k.M * k.M;
+  D.sum_m2 = D.M2 + k.m1 * k.m1 + k.m2 * k.m2 + k.m3 * k.m3;
+  D.R2 = k.R * k.R;
+  fill_channel(D.ch[0], k.M, k.m1, k.m2, k.m3);
+  fill_channel(D.ch[1], k.M, k.m1, k.m3, k.m2);
+  fill_channel(D.ch[2], k.M, k.m2, k.m3, k.m1);
+  D.nbx = nd.nbx;
+  D.nby = nd.nby;
+  D.x0 = (k.m1 + k.m2) * (k.m1 + k.m2);
+  D.hx = ((k.M - k.m3) * (k.M - k.m3) - D.x0) / nd.nbx;
+  D.y0 = (k.m1 + k.m3) * (k.m1 + k.m3);
+  D.hy = ((k.M - k.m2) * (k.M - k.m2) - D.y0) / nd.nby;
+}
+
+// Same region test as the device (|cos theta_12| <= 1 as S_1^2 <= a2 a3).
+static bool dalitz_inside_host(const DalitzPlan& D, double s12, double s13) {
+  const double s23 = D.sum_m2 - s12 - s13;
+  const DalitzChannel& c = D.ch[0];
+  if (!(s12 > c.thrA) || !(s13 > D.ch[1].thrA) || !(s23 > D.ch[2].thrA)) return false;
+  const double inv_s = 1.0 / s12;
+  const double S1 = s23 - s13 + c.k1 * inv_s;
+  const double a2 = s12 - c.a2c + c.a2k * inv_s;
+  const double a3 = (s12 - c.thrA) * (s12 - c.thrB) * inv_s;
+  return S1 * S1 <= a2 * a3;
+}
+
+extern "C" int gf_dalitz_inside(gf_ctx* ctx, int node, int64_t n, const double* s12,
+                                const double* s13, int8_t* out) {
+  if (!ctx || !valid_node(ctx, node) || ctx->nodes[node].type != N_DALITZ || n < 0 ||
+      (n > 0 && (!s12 || !s13 || !out)))
+    return GF_EINVAL;
+  DalitzPlan D{};
+  dalitz_geometry(ctx->nodes[node], D);
+  for (int64_t i = 0; i < n; ++i) out[i] = dalitz_inside_host(D, s12[i], s13[i]) ? 1 : 0;
+  return GF_OK;
+}
+
+// ---- the PDF-tree compiler (1D trees) ------------------------------------------------------------
+namespace {
+
+struct Compiler {
+  gf_ctx* ctx;
+  Program& P;
+  const std::vector<int>& col_of_obs;  // observable id -> dataset column, -1 if absent
+  std::string err;
+  int depth = 0, maxdepth = 0;
+
+  int need(int id) {
+    const NodeDef& nd = ctx->nodes[id];
+    if (nd.type != N_ADD && nd.type != N_PROD) return 1;
+    std::vector<int> nn;
+    for (int c : nd.children) nn.push_back(need(c));
+    std::sort(nn.rbegin(), nn.rend());
+    int m = 0;
+    for (size_t k = 0; k < nn.size(); ++k) m = std::max(m, nn[k] + (k > 0 ? 1 : 0));
+    return m;
+  }
+  std::vector<int> ordered(const NodeDef& nd) {
+    std::vector<int> idx(nd.children.size());
+    for (size_t k = 0; k < idx.size(); ++k) idx[k] = (int)k;
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int a, int b) { return need(nd.children[a]) > need(nd.children[b]); });
+    return idx;
+  }
+  bool emit(const Instr& I) {
+    if (P.n >= kMaxIns) { err = "PDF tree too large (more than 32 instructions)"; return false; }
+    P.ins[P.n++] = I;
+    if (I.op == OP_LEAF) depth++;
+    if (I.op == OP_MUL || I.op == OP_LMUL || I.op == OP_ADD) depth--;
+    maxdepth = std::max(maxdepth, depth);
+    return true;
+  }
+  int gidx(int par) const { return ctx->free_pos[par]; }
+
+  // returns 1 for log domain, 0 linear, -1 error
+  int walk(int id, std::vector<int>& obs_used) {
+    const NodeDef& nd = ctx->nodes[id];
+    if (nd.type >= N_EXP && nd.type <= N_POLY) {
+      if (P.nleaf >= kMaxLeaf) { err = "more than 16 leaves"; return -1; }
+      const int col = col_of_obs[nd.obs];
+      if (col < 0) { err = "the dataset lacks an observable used by the PDF"; return -1; }
+      obs_used.push_back(nd.obs);
+      LeafDesc& L = P.leaf[P.nleaf];
+      L = LeafDesc{};
+      L.kind = nd.type;  // N_EXP..N_POLY coincide with L_EXP..L_POLY
+      L.obs = col;
+      L.npar = (int)nd.pars.size();
+      for (int k = 0; k < L.npar; ++k) L.par[k] = nd.pars[k];
+      L.nbins = (nd.type == N_VOIGT || nd.type == N_THRESH) ? nd.nbx : 0;
+      L.lo = ctx->obs[nd.obs].lo;
+      L.hi = ctx->obs[nd.obs].hi;
+      Instr I{};
+      I.op = OP_LEAF;
+      I.kind = nd.type;
+      I.obs = col;
+      I.slot = P.nleaf;
+      I.npar = L.npar;
+      for (int k = 0; k < kMaxLocal; ++k) I.gidx[k] = k < L.npar ? gidx(L.par[k]) : -1;
+      P.nleaf++;
+      if (!emit(I)) return -1;
+      return (nd.type == N_EXP || nd.type == N_GAUSS) ? 1 : 0;
+    }
+    if (nd.type == N_PROD) {
+      // factors must use distinct observables (ProdPdf of Listing 2)
+      std::vector<std::vector<int>> used(nd.children.size());
+      std::vector<int> dom(nd.children.size());
+      bool all_log = true;
+      // decide the domain first: log if every factor is naturally log
+      for (int c : nd.children) all_log = all_log && natural_log(c);
+      auto ord = ordered(nd);
+      for (size_t k = 0; k < ord.size(); ++k) {
+        const int j = ord[k];
+        int d = walk(nd.children[j], used[j]);
+        if (d < 0) return -1;
+        if (!all_log && d == 1) {
+          Instr T{};
+          T.op = OP_TOLIN;
+          if (!emit(T)) return -1;
+        }
+        if (k > 0) {
+          Instr M{};
+          M.op = all_log ? OP_LMUL : OP_MUL;
+          if (!emit(M)) return -1;
+        }
+      }
+      for (size_t a = 0; a < used.size(); ++a)
+        for (size_t b = a + 1; b < used.size(); ++b)
+          for (int x : used[a])
+            for (int y : used[b])
+              if (x == y) { err = "ProdPdf factors share an observable"; return -1; }
+      for (auto& u : used) obs_used.insert(obs_used.end(), u.begin(), u.end());
+      return all_log ? 1 : 0;
+    }
+    if (nd.type == N_ADD) {
+      const int nc = (int)nd.children.size();
+      auto ord = ordered(nd);
+      for (int k = 0; k < nc; ++k) {
+        const int j = ord[k];
+        int d = walk(nd.children[j], obs_used);
+        if (d < 0) return -1;
+        if (d == 1) {
+          Instr T{};
+          T.op = OP_TOLIN;
+          if (!emit(T)) return -1;
+        }
+        if (P.ncoef >= kMaxCoef) { err = "more than 16 fraction coefficients"; return -1; }
+        CoefDesc& C = P.coef[P.ncoef];
+        C = CoefDesc{};
+        Instr S{};
+        S.op = OP_SCALE;
+        S.slot = P.ncoef;
+        if (j < nc - 1) {
+          C.sign = 1;
+          C.n = 1;
+          C.par[0] = nd.pars[j];
+        } else {
+          C.sign = -1;
+          C.n = nc - 1;
+          for (int q = 0; q < nc - 1; ++q) C.par[q] = nd.pars[q];
+        }
+        S.kind = C.sign;
+        S.npar = C.n;
+        for (int q = 0; q < kMaxLocal; ++q) S.gidx[q] = q < C.n ? gidx(C.par[q]) : -1;
+        P.ncoef++;
+        if (!emit(S)) return -1;
+        if (k > 0) {
+          Instr A{};
+          A.op = OP_ADD;
+          if (!emit(A)) return -1;
+        }
+      }
+      return 0;
+    }
+    err = "a Dalitz node can only be the root of its own PDF";
+    return -1;
+  }
+  bool natural_log(int id) {
+    const NodeDef& nd = ctx->nodes[id];
+    if (nd.type == N_EXP || nd.type == N_GAUSS) return true;
+    if (nd.type == N_PROD) {
+      for (int c : nd.children)
+        if (!natural_log(c)) return false;
+      return true;
+    }
+    return false;
+  }
+};
+
+bool has_cycle(gf_ctx* ctx, int id, std::vector<int>& state) {
+  if (state[id] == 1) return true;
+  if (state[id] == 2) return false;
+  state[id] = 1;
+  for (int c : ctx->nodes[id].children)
+    if (has_cycle(ctx, c, state)) return true;
+  state[id] = 2;
+  return false;
+}
+
+}  // namespace
+
+namespace gfi {
+
+int ensure_compiled(gf_ctx* ctx) {
+  if (ctx->compiled) return GF_OK;
+  if (ctx->root < 0 || !valid_node(ctx, ctx->root))
+    return set_error(ctx, GF_ESTATE, "no data set: call gf_set_data first");
+  ctx->free_ids.clear();
+  ctx->free_pos.assign(ctx->pars.size(), -1);
+  for (int i = 0; i < (int)ctx->pars.size(); ++i)
+    if (!ctx->pars[i].fixed) {
+      ctx->free_pos[i] = (int)ctx->free_ids.size();
+      ctx->free_ids.push_back(i);
+    }
+  const int nf = (int)ctx->free_ids.size();
+  std::vector<int> state(ctx->nodes.size(), 0);
+  if (has_cycle(ctx, ctx->root, state)) return set_error(ctx, GF_EINVAL, "PDF tree has a cycle");
+  const NodeDef& root = ctx->nodes[ctx->root];
+  DevState& d = ctx->dev;
+  std::vector<int> col_of_obs(ctx->obs.size(), -1);
+  for (int k = 0; k < (int)d.obs_ids.size(); ++k) col_of_obs[d.obs_ids[k]] = k;
+  if (root.type == N_DALITZ) {
+    ctx->is_dalitz = true;
+    DalitzPlan& D = ctx->dplan;
+    D = DalitzPlan{};
+    dalitz_geometry(root, D);
+    if (col_of_obs[root.obs] != 0 || col_of_obs[root.obs2] != 1)
+      return set_error(ctx, GF_EINVAL, "Dalitz data set must hold (s12, s13) as columns 0, 1");
+    if (nf > 4 * kMaxRes) return set_error(ctx, GF_EINVAL, "too many free parameters");
+    D.nres = (int)root.res.size();
+    D.nfree = nf;
+    int slot = 0;
+    for (int r = 0; r < D.nres; ++r) {
+      const gf_resonance& R = root.res[r];
+      DalitzRes& X = D.res[r];
+      X.channel = R.channel;
+      X.spin = R.spin;
+      X.p_m0 = R.mass;
+      X.p_g0 = R.width;
+      X.p_re = R.re;
+      X.p_im = R.im;
+      X.g_m0 = ctx->free_pos[R.mass];
+      X.g_g0 = ctx->free_pos[R.width];
+      X.g_re = ctx->free_pos[R.re];
+      X.g_im = ctx->free_pos[R.im];
+      X.ev_cached = (X.g_m0 < 0 && X.g_g0 < 0) ? slot++ : -1;
+      X.grid_col = r + 1;
+    }
+    ctx->has_grid = true;
+  } else {
+    ctx->is_dalitz = false;
+    Program& P = ctx->prog;
+    P = Program{};
+    P.nobs = (int)d.obs_ids.size();
+    if (nf > kMaxFree1D) return set_error(ctx, GF_EINVAL, "1D model: at most 24 free parameters");
+    P.nfree = nf;
+    Compiler C{ctx, P, col_of_obs};
+    std::vector<int> used;
+    const int dom = C.walk(ctx->root, used);
+    if (dom < 0) return set_error(ctx, GF_EINVAL, C.err);
+    if (C.maxdepth > kMaxStack)
+      return set_error(ctx, GF_EINVAL, "PDF tree needs a deeper evaluation stack than 4");
+    P.root_log = dom;
+    int blk = 0;
+    ctx->has_grid = false;
+    for (int l = 0; l < P.nleaf; ++l) {
+      LeafDesc& L = P.leaf[l];
+      if (L.nbins > 0) {
+        L.grid_first_block = blk;
+        L.grid_nblocks = (L.nbins + kThreads - 1) / kThreads;
+        blk += L.grid_nblocks;
+        ctx->has_grid = true;
+      }
+    }
+    P.ngrid_blocks = blk;
+  }
+  ctx->compiled = true;
+  return GF_OK;
+}
+
+}  // namespace gfi
+
+// ---- datasets ----------------------------------------------------------------------------------------------
+extern "C" {
+
+int gf_dataset_create(gf_ctx* ctx, int nobs, const int* obs, gf_dataset** ds) {
+  if (!ctx || !ds || nobs < 1 || nobs > kMaxObs || !obs) return GF_EINVAL;
+  *ds = nullptr;
+  for (int k = 0; k < nobs; ++k) {
+    if (!valid_obs(ctx, obs[k])) return set_error(ctx, GF_EINVAL, "unknown observable id");
+    for (int j = 0; j < k; ++j)
+      if (obs[j] == obs[k]) return set_error(ctx, GF_EINVAL, "observable listed twice");
+  }
+  gf_dataset* d = new (std::nothrow) gf_dataset();
+  if (!d) return GF_ENOMEM;
+  d->ctx = ctx;
+  d->obs.assign(obs, obs + nobs);
+  d->cols.resize(nobs);
+  *ds = d;
+  return GF_OK;
+}
+
+int gf_dataset_add_events(gf_dataset* ds, int64_t n, const double* const* cols) {
+  if (!ds || n < 0 || (n > 0 && !cols)) return GF_EINVAL;
+  gf_ctx* ctx = ds->ctx;
+  for (size_t k = 0; k < ds->obs.size(); ++k) {
+    if (n > 0 && !cols[k]) return set_error(ctx, GF_EINVAL, "NULL column");
+    const ObsDef& o = ctx->obs[ds->obs[k]];
+    for (int64_t i = 0; i < n; ++i) {
+      const double v = cols[k][i];
+      if (!(v >= o.lo && v <= o.hi))
+        return set_error(ctx, GF_EINVAL, "event " + std::to_string(i) + " outside the range of " +
+                                             o.name);
+    }
+  }
+  try {
+    for (size_t k = 0; k < ds->obs.size(); ++k) ds->cols[k].insert(ds->cols[k].end(), cols[k], cols[k] + n);
+  } catch (...) {
+    return set_error(ctx, GF_ENOMEM, "host allocation failed");
+  }
+  ds->n += n;
+  return GF_OK;
+}
+
+int64_t gf_dataset_size(const gf_dataset* ds) { return ds ? ds->n : -1; }
+
+int gf_dataset_destroy(gf_dataset* ds) {
+  delete ds;
+  return GF_OK;
+}
+
+}  // extern "C"
+
+// ---- device set-up ---------------------------------------------------------------------------------------
+static size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+namespace gfi {
+size_t device_bytes_for(const gf_ctx* ctx, int root, int64_t n) {
+  size_t b = 0;
+  const NodeDef& nd = ctx->nodes[root];
+  const size_t col = round_up((size_t)std::max<int64_t>(n, 1) * 8, 256);
+  if (nd.type == N_DALITZ) {
+    const size_t ncell = (size_t)nd.nbx * nd.nby;
+    const int nres = (int)nd.res.size();
+    b += 2 * col;
+    b += ncell + (size_t)(nres + 1) * ncell * 16;
+    int ncached = 0;
+    for (auto& R : nd.res)
+      if (ctx->pars[R.mass].fixed && ctx->pars[R.width].fixed) ++ncached;
+    b += (size_t)ncached * n * (ctx->precision == GF_MIXED ? 8 : 16);
+    if (ctx->precision == GF_MIXED) b += 3 * (size_t)n * 4;
+  } else {
+    b += col * 2;  // observables (typically 1-2)
+  }
+  return b + (4u << 20);  // work buffers
+}
+}  // namespace gfi
+
+static int alloc_work(gf_ctx* ctx) {
+  DevState& d = ctx->dev;
+  const int npar = (int)std::max<size_t>(ctx->pars.size(), 1);
+  if (!d.theta) CK(cudaMalloc(&d.theta, sizeof(double) * 64 * ((npar + 63) / 64)));
+  if (!d.derived) CK(cudaMalloc(&d.derived, sizeof(double) * (kMaxLeaf * kLeafRec + kMaxCoef)));
+  if (!d.counters) {
+    CK(cudaMalloc(&d.counters, sizeof(unsigned) * 4));
+    CK(cudaMemset(d.counters, 0, sizeof(unsigned) * 4));
+  }
+  if (!d.result) CK(cudaMalloc(&d.result, sizeof(double) * 64));
+  if (!d.norm_out) CK(cudaMalloc(&d.norm_out, sizeof(double) * 64));
+  if (!d.h_theta) CK(cudaMallocHost(&d.h_theta, sizeof(double) * 64 * ((npar + 63) / 64)));
+  if (!d.h_result) CK(cudaMallocHost(&d.h_result, sizeof(double) * 64));
+  if (!d.ev0) CK(cudaEventCreate(&d.ev0));
+  if (!d.ev1) CK(cudaEventCreate(&d.ev1));
+  return GF_OK;
+}
+
+static int grow(gf_ctx* ctx, double** p, size_t* cap, size_t need) {
+  if (*cap >= need) return GF_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  CK(cudaMalloc(p, need * sizeof(double)));
+  *cap = need;
+  return GF_OK;
+}
+
+// Shared tail of gf_set_data / gf_set_data_device once the columns are on the device.
+static int finish_set_data(gf_ctx* ctx) {
+  DevState& d = ctx->dev;
+  int rc = alloc_work(ctx);
+  if (rc) return rc;
+  rc = ensure_compiled(ctx);
+  if (rc) return rc;
+  // event-stream grid: a multiple of the SM count, capped by the work
+  int per_sm;
+  if (ctx->is_dalitz) {
+    per_sm = dalitz_blocks_per_sm(ctx->precision == GF_MIXED, true);
+  } else {
+    per_sm = events_1d_blocks_per_sm(true, events_1d_smem(ctx->prog, true, kThreads));
+  }
+  per_sm = std::max(1, std::min(per_sm, 8));
+  const int64_t items = ctx->is_dalitz ? d.n : (d.n + 1) / 2;
+  const int tpb = ctx->is_dalitz ? kThreads : kThreads1D;
+  const int64_t want = (items + tpb - 1) / tpb;
+  d.nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->sm_count * per_sm));
+  rc = grow(ctx, &d.partials, &d.partials_cap, (size_t)std::max(d.nblocks, 2048) * 64);
+  if (rc) return rc;
+  // norm-side partials: 1D grid blocks x 4, Gram chunks x groups x 16, cell blocks x 49
+  size_t need2 = (size_t)4096 * 64;
+  if (!ctx->is_dalitz) need2 = std::max(need2, (size_t)ctx->prog.ngrid_blocks * 4 + 64);
+  rc = grow(ctx, &d.partials2, &d.partials2_cap, need2);
+  if (rc) return rc;
+  if (ctx->is_dalitz) {
+    const DalitzPlan& D = ctx->dplan;
+    const size_t ncell = (size_t)D.nbx * D.nby;
+    cudaFree(d.inside);
+    cudaFree(d.grid_cols);
+    cudaFree(d.gram);
+    cudaFree(d.ev_cache);
+    cudaFree(d.fcols);
+    cudaFree(d.todo);
+    d.inside = nullptr; d.grid_cols = nullptr; d.gram = nullptr; d.ev_cache = nullptr;
+    d.fcols = nullptr; d.todo = nullptr;
+    CK(cudaMalloc(&d.inside, ncell));
+    CK(cudaMalloc(&d.grid_cols, (size_t)(D.nres + 1) * ncell * 16));
+    CK(cudaMalloc(&d.gram, sizeof(double) * 2 * (kMaxRes + 1) * (kMaxRes + 1)));
+    CK(cudaMalloc(&d.todo, sizeof(int) * kMaxRes));
+    int ncached = 0;
+    for (int r = 0; r < D.nres; ++r) ncached += D.res[r].ev_cached >= 0 ? 1 : 0;
+    const bool mixed = ctx->precision == GF_MIXED;
+    if (ncached > 0 && d.n > 0)
+      CK(cudaMalloc(&d.ev_cache, (size_t)ncached * d.n * (mixed ? 8 : 16)));
+    if (mixed && d.n > 0) {
+      CK(cudaMalloc(&d.fcols, 3 * (size_t)d.n * sizeof(float)));
+      // s12, s13, s23 in FP32 (s23 formed in FP64 first)
+      std::vector<float> tmp;  // converted on the host once at set-up
+      std::vector<double> a(d.n), b(d.n);
+      CK(cudaMemcpy(a.data(), d.cols[0], 8 * d.n, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(b.data(), d.cols[1], 8 * d.n, cudaMemcpyDeviceToHost));
+      tmp.resize(3 * (size_t)d.n);
+      for (int64_t i = 0; i < d.n; ++i) {
+        tmp[i] = (float)a[i];
+        tmp[d.n + i] = (float)b[i];
+        tmp[2 * d.n + i] = (float)(D.sum_m2 - a[i] - b[i]);
+      }
+      CK(cudaMemcpy(d.fcols, tmp.data(), tmp.size() * 4, cudaMemcpyHostToDevice));
+    }
+    d.ev_m0.assign(D.nres, NAN);
+    d.ev_g0.assign(D.nres, NAN);
+    d.col_m0.assign(D.nres, NAN);
+    d.col_g0.assign(D.nres, NAN);
+    d.gram_valid = false;
+    d.mask_built = false;
+  }
+  return GF_OK;
+}
+
+extern "C" int gf_set_data(gf_ctx* ctx, int root, const gf_dataset* ds) {
+  if (!ctx || !ds || ds->ctx != ctx || !valid_node(ctx, root)) return GF_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  const NodeDef& nd = ctx->nodes[root];
+  if (nd.type == N_DALITZ) {
+    // both observables as columns 0, 1 and every event inside the kinematic region
+    if (ds->obs.size() < 2 || ds->obs[0] != nd.obs || ds->obs[1] != nd.obs2)
+      return set_error(ctx, GF_EINVAL, "Dalitz data set must hold (s12, s13) as columns 0, 1");
+    DalitzPlan D{};
+    dalitz_geometry(nd, D);
+    for (int64_t i = 0; i < ds->n; ++i)
+      if (!dalitz_inside_host(D, ds->cols[0][i], ds->cols[1][i]))
+        return set_error(ctx, GF_EINVAL,
+                         "event " + std::to_string(i) + " outside the Dalitz kinematic region");
+  }
+  cudaStreamSynchronize(ctx->stream);
+  free_dev(ctx);
+  DevState& d = ctx->dev;
+  d.nobs = (int)ds->obs.size();
+  d.n = ds->n;
+  d.obs_ids = ds->obs;
+  d.owns_cols = true;
+  const size_t bytes = round_up((size_t)std::max<int64_t>(ds->n + 2, 2) * 8, 256);
+  for (int k = 0; k < d.nobs; ++k) {
+    double* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      free_dev(ctx);
+      return set_error(ctx, GF_ENOMEM, "device allocation of the event columns failed");
+    }
+    d.cols.push_back(p);
+    CK(cudaMemsetAsync(p, 0, bytes, ctx->stream));
+    if (ds->n > 0)
+      CK(cudaMemcpyAsync(p, ds->cols[k].data(), 8 * ds->n, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->root = root;
+  ctx->compiled = false;
+  return finish_set_data(ctx);
+}
+
+extern "C" int gf_set_data_device(gf_ctx* ctx, int root, int nobs, const int* obs, int64_t n,
+                                  const double* const* dev_cols) {
+  if (!ctx || !valid_node(ctx, root) || nobs < 1 || nobs > kMaxObs || !obs || n < 0 ||
+      !dev_cols)
+    return GF_EINVAL;
+  for (int k = 0; k < nobs; ++k) {
+    if (!valid_obs(ctx, obs[k]) || !dev_cols[k]) return GF_EINVAL;
+    if (reinterpret_cast<uintptr_t>(dev_cols[k]) % 16 != 0)
+      return set_error(ctx, GF_EINVAL, "device columns must be 16-byte aligned");
+  }
+  CK(cudaSetDevice(ctx->device));
+  cudaStreamSynchronize(ctx->stream);
+  free_dev(ctx);
+  DevState& d = ctx->dev;
+  d.nobs = nobs;
+  d.n = n;
+  d.obs_ids.assign(obs, obs + nobs);
+  d.owns_cols = false;
+  for (int k = 0; k < nobs; ++k) d.cols.push_back(const_cast<double*>(dev_cols[k]));
+  ctx->root = root;
+  ctx->compiled = false;
+  return finish_set_data(ctx);
+}
+
+// ---- evaluation ----------------------------------------------------------------------------------------------
+static int upload_theta(gf_ctx* ctx, const double* theta) {
+  DevState& d = ctx->dev;
+  const int np = (int)ctx->pars.size();
+  for (int i = 0; i < np; ++i) d.h_theta[i] = ctx->pars[i].value;
+  for (size_t k = 0; k < ctx->free_ids.size(); ++k) {
+    if (!std::isfinite(theta[k])) return set_error(ctx, GF_EINVAL, "non-finite theta");
+    d.h_theta[ctx->free_ids[k]] = theta[k];
+  }
+  if (np > 0)
+    CK(cudaMemcpyAsync(d.theta, d.h_theta, sizeof(double) * np, cudaMemcpyHostToDevice,
+                       ctx->stream));
+  return GF_OK;
+}
+
+static DalitzBufs dalitz_bufs(gf_ctx* ctx, double* out_logp) {
+  DevState& d = ctx->dev;
+  DalitzBufs B{};
+  B.s12 = d.cols[0];
+  B.s13 = d.cols[1];
+  B.sf = d.fcols;
+  B.n = d.n;
+  B.ev_cache = d.ev_cache;
+  B.grid_cols = d.grid_cols;
+  B.inside = d.inside;
+  B.gram = d.gram;
+  B.norm_out = d.norm_out;
+  B.partials = d.partials;
+  B.partials2 = d.partials2;
+  B.counter = d.counters;
+  B.counter2 = d.counters + 1;
+  B.result = d.result;
+  B.out_logp = out_logp;
+  return B;
+}
+
+// Dalitz caches: rebuild event / grid columns of fixed-shape resonances whose (m0,
+// Gamma0) differ from those the caches hold; decide the normalisation mode.
+static int dalitz_prepare(gf_ctx* ctx, int* norm_mode, int* launches) {
+  DevState& d = ctx->dev;
+  const DalitzPlan& D = ctx->dplan;
+  const bool mixed = ctx->precision == GF_MIXED;
+  if (!d.mask_built) {
+    CK(launch_dalitz_mask(D, d.inside, ctx->stream));
+    (*launches)++;
+    d.mask_built = true;
+  }
+  bool ev_stale = false;
+  std::vector<int> todo;
+  bool any_free_shape = false;
+  for (int r = 0; r < D.nres; ++r) {
+    const DalitzRes& R = D.res[r];
+    const double m0 = d.h_theta[R.p_m0], g0 = d.h_theta[R.p_g0];
+    if (R.ev_cached >= 0) {
+      if (!(d.ev_m0[r] == m0 && d.ev_g0[r] == g0)) ev_stale = true;
+      if (!(d.col_m0[r] == m0 && d.col_g0[r] == g0)) todo.push_back(r);
+    } else {
+      any_free_shape = true;
+    }
+  }
+  if (ev_stale && d.n > 0) {
+    CK(launch_dalitz_ev_cache(D, mixed, d.theta, d.cols[0], d.cols[1], d.n, d.ev_cache,
+                              ctx->stream));
+    (*launches)++;
+  }
+  for (int r = 0; r < D.nres; ++r)
+    if (D.res[r].ev_cached >= 0) {
+      d.ev_m0[r] = d.h_theta[D.res[r].p_m0];
+      d.ev_g0[r] = d.h_theta[D.res[r].p_g0];
+    }
+  if (!todo.empty()) {
+    CK(cudaMemcpyAsync(d.todo, todo.data(), sizeof(int) * todo.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(launch_dalitz_grid_cols(D, d.theta, d.todo, (int)todo.size(), d.grid_cols, d.inside,
+                               ctx->stream));
+    (*launches)++;
+    for (int r : todo) {
+      d.col_m0[r] = d.h_theta[D.res[r].p_m0];
+      d.col_g0[r] = d.h_theta[D.res[r].p_g0];
+    }
+    d.gram_valid = false;
+    // the todo buffer is read by the kernel: keep the host vector alive until then
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  if (!any_free_shape) {
+    if (!d.gram_valid) {
+      DalitzBufs B = dalitz_bufs(ctx, nullptr);
+      CK(launch_dalitz_gram(D, B, ctx->stream));
+      (*launches)++;
+      d.gram_valid = true;
+    }
+    *norm_mode = DN_GRAM;
+  } else {
+    *norm_mode = DN_DIRECT;
+  }
+  return GF_OK;
+}
+
+namespace gfi {
+
+int evaluate_async(gf_ctx* ctx, const double* theta, bool grad) {
+  int rc = ensure_compiled(ctx);
+  if (rc) return rc;
+  DevState& d = ctx->dev;
+  if (!d.theta) return set_error(ctx, GF_ESTATE, "no data set");
+  CK(cudaSetDevice(ctx->device));
+  rc = upload_theta(ctx, theta);
+  if (rc) return rc;
+  int launches = 0;
+  CK(cudaEventRecord(d.ev0, ctx->stream));
+  const int nf = (int)ctx->free_ids.size();
+  if (ctx->is_dalitz) {
+    int mode = DN_GRAM;
+    rc = dalitz_prepare(ctx, &mode, &launches);
+    if (rc) return rc;
+    DalitzBufs B = dalitz_bufs(ctx, nullptr);
+    const bool mixed = ctx->precision == GF_MIXED;
+    if (mode == DN_DIRECT) {
+      const int ncell_blocks = (int)std::min<int64_t>(
+          ((int64_t)ctx->dplan.nbx * ctx->dplan.nby + kThreads - 1) / kThreads,
+          (int64_t)ctx->sm_count * 4);
+      CK(launch_dalitz_norm_direct(ctx->dplan, mixed, grad, d.theta, B, ncell_blocks,
+                                   ctx->stream));
+      launches++;
+    }
+    CK(launch_dalitz_events(ctx->dplan, mixed, grad, false, mode, d.theta, B, d.nblocks,
+                            ctx->stream));
+    launches++;
+  } else {
+    const WeidCoef& W = weideman();
+    if (ctx->has_grid) {
+      CK(launch_norm_1d(ctx->prog, W, d.theta, d.partials2, d.counters + 1, d.derived,
+                        ctx->stream));
+      launches++;
+    }
+    Cols cols{};
+    for (int k = 0; k < d.nobs; ++k) cols.c[k] = d.cols[k];
+    CK(launch_events_1d(ctx->prog, W, cols, d.n, d.theta, d.derived, d.partials, d.counters,
+                        d.result, nullptr, grad, false, ctx->has_grid ? 0 : 1, d.nblocks,
+                        ctx->stream));
+    launches++;
+  }
+  CK(cudaEventRecord(d.ev1, ctx->stream));
+  CK(cudaMemcpyAsync(d.h_result, d.result, sizeof(double) * (1 + (grad ? nf : 0)),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  ctx->last_launches = launches;
+  return GF_OK;
+}
+
+int evaluate_finish(gf_ctx* ctx, double* nll, double* grad, bool grad_wanted) {
+  DevState& d = ctx->dev;
+  CK(cudaStreamSynchronize(ctx->stream));
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, d.ev0, d.ev1) == cudaSuccess) ctx->last_ms = ms;
+  const int nf = (int)ctx->free_ids.size();
+  double v = d.h_result[0];
+  bool finite = std::isfinite(v);
+  if (grad_wanted && grad)
+    for (int k = 0; k < nf; ++k) {
+      grad[k] = d.h_result[1 + k];
+      finite = finite && std::isfinite(grad[k]);
+    }
+  if (!finite) {
+    *nll = INFINITY;
+    return set_error(ctx, GF_ENONFINITE, "non-finite likelihood: some P_i <= 0 or not finite");
+  }
+  *nll = v;
+  return GF_OK;
+}
+
+int evaluate(gf_ctx* ctx, const double* theta, double* nll, double* grad) {
+  int rc = evaluate_async(ctx, theta, grad != nullptr);
+  if (rc) return rc;
+  return evaluate_finish(ctx, nll, grad, grad != nullptr);
+}
+
+}  // namespace gfi
+
+extern "C" {
+
+int gf_nll(gf_ctx* ctx, const double* theta, double* nll) {
+  if (!ctx || !nll) return GF_EINVAL;
+  int rc = ensure_compiled(ctx);
+  if (rc) return rc;
+  if (!theta && !ctx->free_ids.empty()) return GF_EINVAL;
+  return evaluate(ctx, theta, nll, nullptr);
+}
+
+int gf_nll_grad(gf_ctx* ctx, const double* theta, double* nll, double* grad) {
+  if (!ctx || !nll) return GF_EINVAL;
+  int rc = ensure_compiled(ctx);
+  if (rc) return rc;
+  if (!ctx->free_ids.empty() && (!theta || !grad)) return GF_EINVAL;
+  return evaluate(ctx, theta, nll, grad);
+}
+
+static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host) {
+  if (!ctx || !out) return GF_EINVAL;
+  int rc = ensure_compiled(ctx);
+  if (rc) return rc;
+  if (!theta && !ctx->free_ids.empty()) return GF_EINVAL;
+  DevState& d = ctx->dev;
+  CK(cudaSetDevice(ctx->device));
+  rc = upload_theta(ctx, theta);
+  if (rc) return rc;
+  double* dst = out;
+  if (host) CK(cudaMalloc(&dst, sizeof(double) * std::max<int64_t>(d.n, 1)));
+  int launches = 0;
+  if (ctx->is_dalitz) {
+    int mode = 0;
+    rc = dalitz_prepare(ctx, &mode, &launches);
+    if (rc == GF_OK) {
+      DalitzBufs B = dalitz_bufs(ctx, dst);
+      cudaError_t e = launch_dalitz_events(ctx->dplan, ctx->precision == GF_MIXED, false, true,
+                                           mode, d.theta, B, d.nblocks, ctx->stream);
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e, "launch_dalitz_events");
+    }
+  } else {
+    const WeidCoef& W = weideman();
+    if (ctx->has_grid) {
+      cudaError_t e = launch_norm_1d(ctx->prog, W, d.theta, d.partials2, d.counters + 1,
+                                     d.derived, ctx->stream);
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e, "launch_norm_1d");
+    }
+    Cols cols{};
+    for (int k = 0; k < d.nobs; ++k) cols.c[k] = d.cols[k];
+    if (rc == GF_OK) {
+      cudaError_t e = launch_events_1d(ctx->prog, W, cols, d.n, d.theta, d.derived, d.partials,
+                                       d.counters, d.result, dst, false, true,
+                                       ctx->has_grid ? 0 : 1, d.nblocks, ctx->stream);
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e, "launch_events_1d");
+    }
+  }
+  if (rc == GF_OK && host && d.n > 0) {
+    cudaError_t e = cudaMemcpyAsync(out, dst, sizeof(double) * d.n, cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "copy log P");
+  }
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (host) cudaFree(dst);
+  if (rc == GF_OK && e != cudaSuccess) rc = cuda_fail(ctx, e, "sync");
+  return rc;
+}
+
+int gf_logpdf(gf_ctx* ctx, const double* theta, double* out) {
+  return logpdf_impl(ctx, theta, out, true);
+}
+int gf_logpdf_device(gf_ctx* ctx, const double* theta, double* out_dev) {
+  return logpdf_impl(ctx, theta, out_dev, false);
+}
+
+int gf_dalitz_gram(gf_ctx* ctx, const double* theta, double* G) {
+  if (!ctx || !G) return GF_EINVAL;
+  int rc = ensure_compiled(ctx);
+  if (rc) return rc;
+  if (!ctx->is_dalitz) return set_error(ctx, GF_EINVAL, "root is not a Dalitz node");
+  if (!theta && !ctx->free_ids.empty()) return GF_EINVAL;
+  DevState& d = ctx->dev;
+  CK(cudaSetDevice(ctx->device));
+  rc = upload_theta(ctx, theta);
+  if (rc) return rc;
+  const DalitzPlan& D = ctx->dplan;
+  // columns of every resonance at this theta, then the Gram matrix
+  int launches = 0;
+  if (!d.mask_built) {
+    CK(launch_dalitz_mask(D, d.inside, ctx->stream));
+    d.mask_built = true;
+  }
+  std::vector<int> all(D.nres);
+  for (int r = 0; r < D.nres; ++r) all[r] = r;
+  CK(cudaMemcpyAsync(d.todo, all.data(), sizeof(int) * D.nres, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(launch_dalitz_grid_cols(D, d.theta, d.todo, D.nres, d.grid_cols, d.inside, ctx->stream));
+  DalitzBufs B = dalitz_bufs(ctx, nullptr);
+  CK(launch_dalitz_gram(D, B, ctx->stream));
+  const int K = D.nres + 1;
+  CK(cudaMemcpyAsync(G, d.gram, sizeof(double) * 2 * K * K, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int r = 0; r < D.nres; ++r) {
+    d.col_m0[r] = d.h_theta[D.res[r].p_m0];
+    d.col_g0[r] = d.h_theta[D.res[r].p_g0];
+  }
+  d.gram_valid = true;
+  (void)launches;
+  return GF_OK;
+}
+
+int gf_last_eval_stats(gf_ctx* ctx, double* kernel_ms, int* launches) {
+  if (!ctx) return GF_EINVAL;
+  if (kernel_ms) *kernel_ms = ctx->last_ms;
+  if (launches) *launches = ctx->last_launches;
+  return GF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// ctx.h -- the context object behind gf_ctx (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gf.h"
+#include "gf_internal.h"
+#include "launch.h"
+
+namespace gfi {
+
+enum NodeType { N_EXP = 1, N_GAUSS, N_VOIGT, N_THRESH, N_POLY, N_ADD = 10, N_PROD, N_DALITZ };
+
+struct ObsDef {
+  std::string name;
+  double lo, hi;
+};
+struct ParDef {
+  std::string name;
+  double value, step, lo, hi;
+  bool fixed;
+};
+struct NodeDef {
+  int type;
+  int obs = -1, obs2 = -1;
+  std::vector<int> pars;      // leaf parameters / ADD fractions
+  std::vector<int> children;  // ADD / PROD
+  int nbx = 10000, nby = 0;   // normalisation grid
+  gf_dalitz_kin kin{};
+  std::vector<gf_resonance> res;
+};
+
+// Device state of a compiled tree + dataset.
+struct DevState {
+  // data
+  int nobs = 0;
+  int64_t n = 0;
+  std::vector<int> obs_ids;           // dataset column k -> observable id
+  std::vector<double*> cols;          // device columns
+  bool owns_cols = false;
+  // common
+  double* theta = nullptr;            // all parameters (device)
+  double* derived = nullptr;
+  double* partials = nullptr;
+  double* partials2 = nullptr;
+  unsigned* counters = nullptr;       // [0] events, [1] norm
+  double* result = nullptr;           // [1 + nfree]
+  double* norm_out = nullptr;
+  double* h_theta = nullptr;          // pinned
+  double* h_result = nullptr;         // pinned
+  size_t partials_cap = 0, partials2_cap = 0;
+  int nblocks = 0;
+  // Dalitz
+  uint8_t* inside = nullptr;
+  double* grid_cols = nullptr;
+  double* gram = nullptr;
+  void* ev_cache = nullptr;
+  float* fcols = nullptr;
+  int* todo = nullptr;
+  std::vector<double> ev_m0, ev_g0;     // shapes the event cache was built with (NaN: none)
+  std::vector<double> col_m0, col_g0;   // shapes of the grid columns
+  bool gram_valid = false;
+  bool mask_built = false;
+  // timing
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+}  // namespace gfi
+
+struct gf_dataset {
+  gf_ctx* ctx;
+  std::vector<int> obs;
+  std::vector<std::vector<double>> cols;
+  int64_t n = 0;
+};
+
+struct gf_ctx {
+  int device = 0;
+  int precision = GF_FP64;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  std::vector<gfi::ObsDef> obs;
+  std::vector<gfi::ParDef> pars;
+  std::vector<gfi::NodeDef> nodes;
+  // compiled
+  int root = -1;
+  bool compiled = false;
+  bool is_dalitz = false;
+  bool has_grid = false;
+  gfi::Program prog{};
+  gfi::DalitzPlan dplan{};
+  std::vector<int> free_ids;     // theta position -> parameter id
+  std::vector<int> free_pos;     // parameter id -> theta position or -1
+  gfi::DevState dev;
+  int sm_count = 0;
+  double last_ms = 0.0;
+  int last_launches = 0;
+};
+
+namespace gfi {
+// capi.cpp internals used by fit.cpp and server.cpp
+int set_error(gf_ctx* ctx, int code, const std::string& msg);
+int ensure_compiled(gf_ctx* ctx);
+// Evaluate at theta (free params): nll always, grad if non-null.  Blocking.
+int evaluate(gf_ctx* ctx, const double* theta, double* nll, double* grad);
+// Enqueue an evaluation without waiting: the result lands in ctx->dev.h_result after the
+// stream reaches it (used by the server to overlap fits).
+int evaluate_async(gf_ctx* ctx, const double* theta, bool grad);
+int evaluate_finish(gf_ctx* ctx, double* nll, double* grad, bool grad_wanted);
+size_t device_bytes_for(const gf_ctx* ctx, int root, int64_t n);
+int nfree(const gf_ctx* ctx);
+const WeidCoef& weideman();
+}  // namespace gfi

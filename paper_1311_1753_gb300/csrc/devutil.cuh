@@ -1,0 +1,149 @@
+// devutil.cuh -- device helpers of the sm_103a kernels: deterministic block
+// reductions, the last-block completion pattern, and the Faddeeva function.
+#pragma once
+#include <cuda_runtime.h>
+#include "gf_internal.h"
+
+namespace gfi {
+
+constexpr double kInvSqrtPi = 0.56418958354775628695;  // 1/sqrt(pi)
+constexpr double kTwoInvSqrtPi = 1.12837916709551257390;
+constexpr double kSqrt2 = 1.41421356237309504880;
+constexpr double kSqrt2Pi = 2.50662827463100050242;
+
+// ---- compensated accumulation ------------------------------------------------------
+// FP64: plain sum (a thread adds O(100) terms).  FP32: Kahan pair, converted to FP64
+// when the thread hands its sum to the block reduction.
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct Acc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
+// ---- warp / block reductions in a fixed order (bitwise reproducible) -------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduce one value over the block; result valid in thread 0.  `red` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) r += red[w];
+  return r;
+}
+
+// Neumaier pair for the cross-block pass.
+struct Neu {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double v) {
+    double t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return s + c; }
+};
+
+// Block-wide fixed-order sum of partials[b * stride + k] over b < nblk, for each
+// k < m; writes out[k].  Called by every thread of one block.
+__device__ inline void reduce_partials(const double* partials, int nblk, int stride, int m,
+                                       double* out, double* red) {
+  for (int k = 0; k < m; ++k) {
+    Neu a;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) a.add(__ldcg(partials + (size_t)b * stride + k));
+    // fixed tree over threads: compensated values folded in by warp then by warp index
+    double v = a.get();
+    double r = block_sum(v, red);
+    if (threadIdx.x == 0) out[k] = r;
+    __syncthreads();
+  }
+}
+
+// Last-block pattern: every block publishes its partial, then bumps a counter; the
+// block that takes the last ticket sees every partial and finishes the reduction.
+// The counter is reset by that block, so the next launch starts from zero.
+__device__ __forceinline__ bool arrive_last(unsigned* counter, int* flag_smem) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(counter, 1u);
+    *flag_smem = (t == gridDim.x * gridDim.y - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  const bool last = *flag_smem != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// ---- Faddeeva function w(z) = exp(-z^2) erfc(-iz), Im z >= 0 ---------------------------
+// Weideman (1994), "Computation of the complex error function", SIAM J. Numer. Anal.
+// 31, 1497: expand (L^2 + t^2) e^{-t^2} in powers of Z(t) = (L + it)/(L - it), which maps
+// the real line onto the unit circle; integrating the Cauchy representation term by
+// term (residues at t = z and, for the constant term, t = iL) gives
+//   w(z) = 1/(sqrt(pi) (L - iz)) + 2/(L - iz)^2 sum_{n=1}^{N} a_n Z^{n-1},
+//   Z = (L + iz)/(L - iz),  L = 2^{-1/4} sqrt(N).
+// The a_n are Fourier coefficients computed on the host (WeidCoef).  N = 40 gives
+// |w| to ~2e-14 relative over the Voigtian's range of z.
+__device__ __forceinline__ void faddeeva(double x, double y, const WeidCoef& W, double& wr,
+                                         double& wi) {
+  const double L = W.L;
+  const double dr = L + y;                          // L - iz = (L + y) - i x
+  const double inv = 1.0 / fma(dr, dr, x * x);      // 1/|L - iz|^2
+  const double Zr = fma(L - y, dr, -x * x) * inv;   // Re Z
+  const double Zi = 2.0 * L * x * inv;              // Im Z
+  double pr = W.a[kWeidN], pi = 0.0;
+#pragma unroll
+  for (int n = kWeidN - 1; n >= 1; --n) {
+    const double t = fma(pr, Zr, fma(-pi, Zi, W.a[n]));
+    pi = fma(pr, Zi, pi * Zr);
+    pr = t;
+  }
+  const double ir = dr * inv, ii = x * inv;          // 1/(L - iz)
+  const double qr = fma(ir, ir, -ii * ii), qi = 2.0 * ir * ii;  // 1/(L - iz)^2
+  wr = fma(kInvSqrtPi, ir, 2.0 * fma(pr, qr, -pi * qi));
+  wi = fma(kInvSqrtPi, ii, 2.0 * fma(pr, qi, pi * qr));
+}
+
+__device__ __forceinline__ void faddeeva(float x, float y, const WeidCoef& W, float& wr,
+                                         float& wi) {
+  const float L = W.Lf;
+  const float dr = L + y;
+  const float inv = __frcp_rn(fmaf(dr, dr, x * x));
+  const float Zr = fmaf(L - y, dr, -x * x) * inv;
+  const float Zi = 2.f * L * x * inv;
+  float pr = W.af[kWeidNf], pi = 0.f;
+#pragma unroll
+  for (int n = kWeidNf - 1; n >= 1; --n) {
+    const float t = fmaf(pr, Zr, fmaf(-pi, Zi, W.af[n]));
+    pi = fmaf(pr, Zi, pi * Zr);
+    pr = t;
+  }
+  const float ir = dr * inv, ii = x * inv;
+  const float qr = fmaf(ir, ir, -ii * ii), qi = 2.f * ir * ii;
+  wr = fmaf((float)kInvSqrtPi, ir, 2.f * fmaf(pr, qr, -pi * qi));
+  wi = fmaf((float)kInvSqrtPi, ii, 2.f * fmaf(pr, qi, pi * qr));
+}
+
+}  // namespace gfi

@@ -1,0 +1,108 @@
+// gf_internal.h -- plans shared by the host-side PDF-tree compiler (capi.cpp) and the
+// sm_103a kernels (k_1d.cu, k_dalitz.cu).  Plain structs passed to kernels by value
+// (they land in the constant bank, so every warp reads the same instruction stream
+// with broadcast loads).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gfi {
+
+constexpr int kMaxIns = 32;     // instructions of a 1D program
+constexpr int kMaxObs = 8;      // observables of one dataset
+constexpr int kMaxLeaf = 16;    // leaves of a 1D program
+constexpr int kMaxCoef = 16;    // fraction coefficients of a 1D program
+constexpr int kMaxLocal = 8;    // parameters of one leaf
+constexpr int kLeafRec = 20;    // doubles per leaf record: invN, logN, dlogN[8], c[10]
+constexpr int kMaxFree1D = 24;  // free parameters of a 1D model with gradient
+constexpr int kMaxStack = 4;    // evaluation stack depth (Sethi-Ullman ordered)
+constexpr int kMaxRes = 12;     // resonances of a Dalitz model
+constexpr int kWeidN = 40;      // terms of the FP64 Faddeeva series
+constexpr int kWeidNf = 16;     // terms of the FP32 Faddeeva series
+constexpr int kThreads = 256;   // threads per block of the Dalitz and normalisation kernels
+constexpr int kThreads1D = 128; // threads per block of the 1D event kernel (its gradient
+                                // stack: 5 x nfree x 128 doubles of shared memory <= 123 KB)
+
+// Leaf kinds (shape functions; Sec. 2-3 of the paper and gf.h).
+enum Leaf : int32_t { L_EXP = 1, L_GAUSS = 2, L_VOIGT = 3, L_THRESH = 4, L_POLY = 5 };
+
+// Opcodes of the postfix (stack) program of a 1D PDF tree.  "log" values live in the
+// log domain, "lin" values in the linear domain; the compiler inserts TOLIN where a
+// linear consumer needs a log value.
+enum Op : int32_t {
+  OP_LEAF = 1,    // push the normalised leaf value (log domain for EXP/GAUSS)
+  OP_TOLIN = 2,   // s0 = exp(s0)
+  OP_MUL = 3,     // s0 = s1 * s0        (ProdPdf, linear)
+  OP_LMUL = 4,    // s0 = s1 + s0        (ProdPdf, log domain)
+  OP_SCALE = 5,   // s0 = coef[slot] * s0 (AddPdf fraction, or 1 - sum of fractions)
+  OP_ADD = 6,     // s0 = s1 + s0        (AddPdf)
+};
+
+struct Instr {
+  int32_t op;
+  int32_t kind;              // OP_LEAF: Leaf kind; OP_SCALE: +1 (coef = f) / -1 (1 - sum f)
+  int32_t obs;               // OP_LEAF: observable column
+  int32_t slot;              // OP_LEAF: leaf record; OP_SCALE: coefficient slot
+  int32_t npar;              // OP_LEAF: local parameters; OP_SCALE: fractions involved
+  int32_t gidx[kMaxLocal];   // free index (theta position) of each, -1 when fixed
+};
+
+struct LeafDesc {
+  int32_t kind, obs, npar, nbins;  // nbins > 0: midpoint-grid normalisation
+  int32_t par[kMaxLocal];          // indices into theta_all
+  double lo, hi;                   // observable range
+  int32_t grid_first_block;        // first block of this leaf in the norm grid launch
+  int32_t grid_nblocks;
+};
+
+struct CoefDesc {
+  int32_t sign, n;                 // sign +1: coef = theta[par[0]]; -1: 1 - sum theta[par[k]]
+  int32_t par[kMaxLocal];
+};
+
+struct Program {
+  int32_t n, nleaf, ncoef, nfree, nobs, root_log, ngrid_blocks, pad;
+  Instr ins[kMaxIns];
+  LeafDesc leaf[kMaxLeaf];
+  CoefDesc coef[kMaxCoef];
+};
+
+struct Cols {
+  const double* c[kMaxObs];
+};
+
+// Faddeeva coefficients (Weideman 1994 rational series), filled on the host.
+struct WeidCoef {
+  double L;
+  double a[kWeidN + 1];
+  float Lf;
+  float af[kWeidNf + 1];
+};
+
+// ---- Dalitz plan ------------------------------------------------------------------
+struct DalitzChannel {
+  double ma2, mb2, mc2;  // squared masses of a, b (resonance pair) and bachelor c
+  double thrA, thrB;     // (ma+mb)^2, (ma-mb)^2
+  double k1;             // (M^2 - mc^2)(ma^2 - mb^2)          (Zemach S_1 constant)
+  double a2c, a2k;       // a2 = s - a2c + a2k/s, a2c = 2M^2 + 2mc^2, a2k = (M^2-mc^2)^2
+};
+
+struct DalitzRes {
+  int32_t channel, spin;
+  int32_t p_m0, p_g0, p_re, p_im;  // theta_all indices
+  int32_t g_m0, g_g0, g_re, g_im;  // free indices or -1
+  int32_t ev_cached;               // per-event amplitude column available (cache slot or -1)
+  int32_t grid_col;                // grid column index (always r + 1; 0 is a_NR)
+};
+
+struct DalitzPlan {
+  double M2, sum_m2;  // M^2 and M^2 + m1^2 + m2^2 + m3^2
+  double R2;          // Blatt-Weisskopf radius squared
+  double m1, m2, m3, M;
+  DalitzChannel ch[3];
+  int32_t nres, nfree, nbx, nby;
+  double x0, hx, y0, hy;  // grid: s12 = x0 + (i + 1/2) hx, s13 = y0 + (j + 1/2) hy
+  DalitzRes res[kMaxRes];
+};
+
+}  // namespace gfi

@@ -1,0 +1,475 @@
+// k_1d.cu -- sm_103a kernels for PDF trees over one or more 1D observables
+// (Sec. 2-3 of the paper: per-event evaluate + metric, summed over events).
+//
+//  k_norm_1d    midpoint-grid normalisation integrals of the Voigtian / threshold leaves
+//               (and their parameter derivatives); its last block turns theta and the
+//               integrals into per-leaf records (1/N, log N, dlogN, shape constants).
+//  k_events_1d  the event stream: SoA columns read with 128-bit loads, the compiled
+//               postfix program evaluated per event (forward-mode gradient optional),
+//               -log P summed per thread, per block (warp shuffles), and across blocks
+//               by the last block in a fixed order.
+#include <cstdio>
+#include "devutil.cuh"
+#include "gf_internal.h"
+#include "launch.h"
+
+namespace gfi {
+
+// ---- shape functions (unnormalised r(x) and d r / d local parameter) ------------------
+// Voigtian: r = Re w(z)/(sigma sqrt(2 pi)), z = (x - mu)/(sigma sqrt 2) + i Gamma/(2 sigma sqrt 2).
+__device__ __forceinline__ double voigt_r(double x, double mu, double s, double G,
+                                          const WeidCoef& W, double* dr) {
+  const double c1 = 1.0 / (s * kSqrt2);
+  const double zr = (x - mu) * c1, zi = 0.5 * G * c1;
+  double wr, wi;
+  faddeeva(zr, zi, W, wr, wi);
+  const double pref = 1.0 / (s * kSqrt2Pi);
+  const double r = wr * pref;
+  if (dr) {
+    // w' = -2 z w + 2i/sqrt(pi)
+    const double dre = -2.0 * (zr * wr - zi * wi);
+    const double dim = -2.0 * (zr * wi + zi * wr) + kTwoInvSqrtPi;
+    dr[0] = -pref * c1 * dre;                               // d/dmu
+    dr[1] = -pref / s * (dre * zr - dim * zi) - r / s;      // d/dsigma
+    dr[2] = -pref * 0.5 * c1 * dim;                         // d/dGamma
+  }
+  return r;
+}
+
+// Threshold: r = (x - x0)^p e^{-c (x - x0)} for x > x0.
+__device__ __forceinline__ double thresh_r(double x, double x0, double p, double c, double* dr) {
+  const double t = x - x0;
+  if (!(t > 0.0)) {
+    if (dr) dr[0] = dr[1] = dr[2] = 0.0;
+    return 0.0;
+  }
+  const double lt = log(t);
+  const double r = exp(fma(p, lt, -c * t));
+  if (dr) {
+    dr[0] = r * (c - p / t);
+    dr[1] = r * lt;
+    dr[2] = -t * r;
+  }
+  return r;
+}
+
+// ---- leaf records ------------------------------------------------------------------------
+// rec[0] = 1/N, rec[1] = log N, rec[2 + k] = d log N / d par_k, rec[10 + j] = constants.
+__device__ void make_leaf_record(const LeafDesc& L, const double* th, double N, const double* dN,
+                                 double* rec) {
+  for (int k = 0; k < kLeafRec; ++k) rec[k] = 0.0;
+  const double lo = L.lo, hi = L.hi, D = hi - lo;
+  double* c = rec + 10;
+  switch (L.kind) {
+    case L_EXP: {
+      // N = e^{a lo} expm1(a D)/a;  d log N/da = lo + D phi(aD),
+      // phi(u) = 1/(1 - e^{-u}) - 1/u  (series 1/2 + u/12 - u^3/720 + u^5/30240 - u^7/1209600
+      // for |u| < 0.1, Bernoulli numbers).
+      const double a = th[L.par[0]];
+      const double u = a * D;
+      double logN, phi;
+      if (a == 0.0) {
+        logN = log(D);
+        phi = 0.5;
+      } else {
+        logN = a * lo + log(expm1(u) / a);
+        if (fabs(u) < 0.1) {
+          const double u2 = u * u;
+          phi = 0.5 + u * (1.0 / 12 + u2 * (-1.0 / 720 + u2 * (1.0 / 30240 - u2 / 1209600)));
+        } else {
+          phi = -1.0 / expm1(-u) - 1.0 / u;
+        }
+      }
+      rec[0] = exp(-logN);
+      rec[1] = logN;
+      rec[2] = lo + D * phi;
+      c[0] = a;
+      c[1] = -logN;
+      break;
+    }
+    case L_GAUSS: {
+      const double mu = th[L.par[0]], s = th[L.par[1]];
+      const double a = (lo - mu) / s, b = (hi - mu) / s;
+      double diff;  // Phi(b) - Phi(a)
+      if (a > 0.0) diff = 0.5 * (erfc(a / kSqrt2) - erfc(b / kSqrt2));
+      else if (b < 0.0) diff = 0.5 * (erfc(-b / kSqrt2) - erfc(-a / kSqrt2));
+      else diff = 0.5 * (erf(b / kSqrt2) - erf(a / kSqrt2));
+      const double n = s * kSqrt2Pi * diff;
+      const double ea = exp(-0.5 * a * a), eb = exp(-0.5 * b * b);
+      rec[0] = 1.0 / n;
+      rec[1] = log(n);
+      rec[2] = (ea - eb) / n;
+      rec[3] = (a * ea - b * eb) / n + 1.0 / s;
+      c[0] = mu;
+      c[1] = 1.0 / s;
+      c[2] = -rec[1];
+      break;
+    }
+    case L_VOIGT: {
+      const double mu = th[L.par[0]], s = th[L.par[1]], G = th[L.par[2]];
+      rec[0] = 1.0 / N;
+      rec[1] = log(N);
+      for (int k = 0; k < 3; ++k) rec[2 + k] = dN[k] / N;
+      c[0] = mu;
+      c[1] = 1.0 / (s * kSqrt2);
+      c[2] = 0.5 * G * c[1];
+      c[3] = 1.0 / (s * kSqrt2Pi * N);
+      c[4] = 1.0 / s;
+      break;
+    }
+    case L_THRESH: {
+      rec[0] = 1.0 / N;
+      rec[1] = log(N);
+      for (int k = 0; k < 3; ++k) rec[2 + k] = dN[k] / N;
+      c[0] = th[L.par[0]];
+      c[1] = th[L.par[1]];
+      c[2] = th[L.par[2]];
+      c[3] = 1.0 / N;
+      break;
+    }
+    case L_POLY: {
+      // N = Q(hi) - Q(lo), Q(x) = sum_k a_k x^{k+1}/(k+1)
+      double n = 0.0, phk = hi, plk = lo;
+      double ik[kMaxLocal];
+      for (int k = 0; k < L.npar; ++k) {
+        ik[k] = (phk - plk) / (k + 1);
+        n = fma(th[L.par[k]], ik[k], n);
+        phk *= hi;
+        plk *= lo;
+      }
+      rec[0] = 1.0 / n;
+      rec[1] = log(n);
+      for (int k = 0; k < L.npar; ++k) {
+        rec[2 + k] = ik[k] / n;
+        c[k] = th[L.par[k]] / n;
+      }
+      break;
+    }
+  }
+}
+
+__device__ inline void make_coefs(const Program& P, const double* th, double* coef) {
+  for (int j = 0; j < P.ncoef; ++j) {
+    const CoefDesc& C = P.coef[j];
+    if (C.sign > 0) {
+      coef[j] = th[C.par[0]];
+    } else {
+      double s = 1.0;
+      for (int k = 0; k < C.n; ++k) s -= th[C.par[k]];
+      coef[j] = s;
+    }
+  }
+}
+
+// ---- normalisation grid -----------------------------------------------------------------
+// One block per (grid leaf, chunk of kThreads bins): each thread takes one midpoint.
+// partials: [block][4] = (sum r, sum dr/dp0, dr/dp1, dr/dp2).
+__global__ void __launch_bounds__(kThreads) k_norm_1d(const Program P, const WeidCoef W,
+                                                      const double* __restrict__ theta,
+                                                      double* __restrict__ partials,
+                                                      unsigned* __restrict__ counter,
+                                                      double* __restrict__ derived) {
+  __shared__ double red[32];
+  __shared__ int last;
+  __shared__ double sums[kMaxLeaf][4];
+  // locate this block's leaf
+  int li = -1;
+  for (int l = 0; l < P.nleaf; ++l) {
+    const LeafDesc& L = P.leaf[l];
+    if (L.nbins > 0 && (int)blockIdx.x >= L.grid_first_block &&
+        (int)blockIdx.x < L.grid_first_block + L.grid_nblocks)
+      li = l;
+  }
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (li >= 0) {
+    const LeafDesc& L = P.leaf[li];
+    const int b = (blockIdx.x - L.grid_first_block) * blockDim.x + threadIdx.x;
+    if (b < L.nbins) {
+      const double h = (L.hi - L.lo) / L.nbins;
+      const double x = L.lo + (b + 0.5) * h;
+      double dr[3];
+      if (L.kind == L_VOIGT)
+        v[0] = voigt_r(x, theta[L.par[0]], theta[L.par[1]], theta[L.par[2]], W, dr);
+      else
+        v[0] = thresh_r(x, theta[L.par[0]], theta[L.par[1]], theta[L.par[2]], dr);
+      v[1] = dr[0];
+      v[2] = dr[1];
+      v[3] = dr[2];
+    }
+  }
+  for (int k = 0; k < 4; ++k) {
+    const double r = block_sum(v[k], red);
+    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 4 + k] = r;
+  }
+  if (!arrive_last(counter, &last)) return;
+  // last block: per leaf, fixed-order sum over its chunks, then every leaf record
+  for (int l = 0; l < P.nleaf; ++l) {
+    const LeafDesc& L = P.leaf[l];
+    if (L.nbins <= 0) continue;
+    for (int k = 0; k < 4; ++k) {
+      Neu a;
+      for (int b = threadIdx.x; b < L.grid_nblocks; b += blockDim.x)
+        a.add(__ldcg(partials + (size_t)(L.grid_first_block + b) * 4 + k));
+      const double r = block_sum(a.get(), red);
+      if (threadIdx.x == 0) sums[l][k] = r * (L.hi - L.lo) / L.nbins;
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < P.nleaf) {
+    const int l = threadIdx.x;
+    make_leaf_record(P.leaf[l], theta, sums[l][0], &sums[l][1], derived + l * kLeafRec);
+  }
+  if (threadIdx.x == 0) {
+    make_coefs(P, theta, derived + kMaxLeaf * kLeafRec);
+    *counter = 0u;
+  }
+}
+
+// ---- event-side leaf evaluation ------------------------------------------------------------
+// Returns the normalised leaf value (log domain for EXP and GAUSS).  With G, adds the
+// partials with respect to the leaf's free parameters into the gradient slot g (stride bd).
+template <bool G>
+__device__ __forceinline__ double eval_leaf(const Instr& I, const double* rec, double x,
+                                            const WeidCoef& W, double* g, int bd) {
+  const double* c = rec + 10;
+  switch (I.kind) {
+    case L_EXP: {
+      if (G && I.gidx[0] >= 0) g[I.gidx[0] * bd] += x - rec[2];
+      return fma(c[0], x, c[1]);
+    }
+    case L_GAUSS: {
+      const double u = (x - c[0]) * c[1];
+      if (G) {
+        if (I.gidx[0] >= 0) g[I.gidx[0] * bd] += u * c[1] - rec[2];
+        if (I.gidx[1] >= 0) g[I.gidx[1] * bd] += u * u * c[1] - rec[3];
+      }
+      return fma(-0.5 * u, u, c[2]);
+    }
+    case L_VOIGT: {
+      const double zr = (x - c[0]) * c[1], zi = c[2];
+      double wr, wi;
+      faddeeva(zr, zi, W, wr, wi);
+      const double l = c[3] * wr;
+      if (G) {
+        const double dre = -2.0 * (zr * wr - zi * wi);
+        const double dim = -2.0 * (zr * wi + zi * wr) + kTwoInvSqrtPi;
+        if (I.gidx[0] >= 0) g[I.gidx[0] * bd] += -c[3] * c[1] * dre - l * rec[2];
+        if (I.gidx[1] >= 0)
+          g[I.gidx[1] * bd] += -c[3] * c[4] * (dre * zr - dim * zi) - l * (c[4] + rec[3]);
+        if (I.gidx[2] >= 0) g[I.gidx[2] * bd] += -c[3] * 0.5 * c[1] * dim - l * rec[4];
+      }
+      return l;
+    }
+    case L_THRESH: {
+      const double t = x - c[0];
+      if (!(t > 0.0)) return 0.0;
+      double l, lt = 0.0;
+      if (c[1] == 0.5 && !(G && I.gidx[1] >= 0)) {
+        l = sqrt(t) * exp(-c[2] * t) * c[3];
+      } else {
+        lt = log(t);
+        l = exp(fma(c[1], lt, -c[2] * t)) * c[3];
+      }
+      if (G) {
+        if (I.gidx[0] >= 0) g[I.gidx[0] * bd] += l * (c[2] - c[1] / t - rec[2]);
+        if (I.gidx[1] >= 0) g[I.gidx[1] * bd] += l * (lt - rec[3]);
+        if (I.gidx[2] >= 0) g[I.gidx[2] * bd] += -l * (t + rec[4]);
+      }
+      return l;
+    }
+    case L_POLY: {
+      double l = 0.0;
+      for (int k = I.npar - 1; k >= 0; --k) l = fma(l, x, c[k]);
+      if (G) {
+        double xk = rec[0];
+        for (int k = 0; k < I.npar; ++k) {
+          if (I.gidx[k] >= 0) g[I.gidx[k] * bd] += xk - l * rec[2 + k];
+          xk *= x;
+        }
+      }
+      return l;
+    }
+  }
+  return 0.0;
+}
+
+// ---- event stream ------------------------------------------------------------------------
+// MODE 0: reduce -log P (and gradient) to result[0 .. nfree]; MODE 1: store log P_i.
+template <bool G, int MODE>
+__global__ void __launch_bounds__(kThreads1D) k_events_1d(
+    const Program P, const WeidCoef W, const Cols cols, const int64_t n,
+    const double* __restrict__ theta, const double* __restrict__ derived_g,
+    double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
+    double* __restrict__ out_logp, const int analytic_only) {
+  extern __shared__ double dyn[];  // G: (kMaxStack + 1) * nfree * blockDim doubles
+  __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
+  __shared__ double red[32];
+  __shared__ int last;
+  const int bd = blockDim.x, tid = threadIdx.x;
+  const int nf = P.nfree;
+  // leaf records: from the norm kernel, or (analytic leaves only) built here per block
+  if (analytic_only) {
+    if (tid < P.nleaf) make_leaf_record(P.leaf[tid], theta, 1.0, nullptr, rec + tid * kLeafRec);
+    if (tid == 0) make_coefs(P, theta, rec + kMaxLeaf * kLeafRec);
+  } else {
+    for (int k = tid; k < kMaxLeaf * kLeafRec + kMaxCoef; k += bd) rec[k] = derived_g[k];
+  }
+  __syncthreads();
+  const double* coef = rec + kMaxLeaf * kLeafRec;
+  double* gacc = dyn + (size_t)kMaxStack * nf * bd + tid;  // per-thread gradient sums
+  if (G)
+    for (int k = 0; k < nf; ++k) gacc[k * bd] = 0.0;
+  double acc = 0.0;
+
+  const int64_t npairs = (n + 1) >> 1;
+  const int64_t stride = (int64_t)gridDim.x * bd;
+  for (int64_t pr = (int64_t)blockIdx.x * bd + tid; pr < npairs; pr += stride) {
+    double2 xv[kMaxObs];
+    const bool full = 2 * pr + 1 < n;  // the last pair of an odd n holds one event
+#pragma unroll
+    for (int o = 0; o < kMaxObs; ++o)
+      if (o < P.nobs) {
+        if (full) {
+          xv[o] = __ldcs(reinterpret_cast<const double2*>(cols.c[o]) + pr);
+        } else {
+          xv[o].x = __ldcs(cols.c[o] + 2 * pr);
+          xv[o].y = 0.0;
+        }
+      }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int64_t i = 2 * pr + e;
+      if (i >= n) break;
+      double x[kMaxObs];
+#pragma unroll
+      for (int o = 0; o < kMaxObs; ++o) x[o] = e ? xv[o].y : xv[o].x;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int dep = 0;
+      for (int pc = 0; pc < P.n; ++pc) {
+        const Instr& I = P.ins[pc];
+        double* gt = dyn + (size_t)(dep - 1) * nf * bd + tid;  // gradient of s0
+        switch (I.op) {
+          case OP_LEAF: {
+            double* gn = dyn + (size_t)dep * nf * bd + tid;
+            if (G)
+              for (int k = 0; k < nf; ++k) gn[k * bd] = 0.0;
+            const double v = eval_leaf<G>(I, rec + I.slot * kLeafRec, x[I.obs], W, gn, bd);
+            s3 = s2; s2 = s1; s1 = s0; s0 = v;
+            ++dep;
+            break;
+          }
+          case OP_TOLIN: {
+            s0 = exp(s0);
+            if (G)
+              for (int k = 0; k < nf; ++k) gt[k * bd] *= s0;
+            break;
+          }
+          case OP_MUL: {
+            if (G) {
+              double* gb = gt - (size_t)nf * bd;
+              for (int k = 0; k < nf; ++k) gb[k * bd] = fma(gb[k * bd], s0, gt[k * bd] * s1);
+            }
+            s0 = s1 * s0; s1 = s2; s2 = s3;
+            --dep;
+            break;
+          }
+          case OP_LMUL:
+          case OP_ADD: {
+            if (G) {
+              double* gb = gt - (size_t)nf * bd;
+              for (int k = 0; k < nf; ++k) gb[k * bd] += gt[k * bd];
+            }
+            s0 = s1 + s0; s1 = s2; s2 = s3;
+            --dep;
+            break;
+          }
+          case OP_SCALE: {
+            const double cf = coef[I.slot];
+            if (G) {
+              for (int k = 0; k < nf; ++k) gt[k * bd] *= cf;
+              for (int j = 0; j < I.npar; ++j)
+                if (I.gidx[j] >= 0) gt[I.gidx[j] * bd] += I.kind * s0;
+            }
+            s0 *= cf;
+            break;
+          }
+        }
+      }
+      const double lp = P.root_log ? s0 : log(s0);
+      if (MODE == 1) {
+        out_logp[i] = lp;
+      } else {
+        acc -= lp;
+        if (G) {
+          const double* g0 = dyn + tid;
+          const double sc = P.root_log ? -1.0 : -1.0 / s0;
+          for (int k = 0; k < nf; ++k) gacc[k * bd] = fma(g0[k * bd], sc, gacc[k * bd]);
+        }
+      }
+    }
+  }
+  if (MODE == 1) return;
+
+  const int m = 1 + (G ? nf : 0);
+  const int stride_p = 1 + kMaxFree1D;
+  for (int k = 0; k < m; ++k) {
+    const double v = (k == 0) ? acc : gacc[(k - 1) * bd];
+    const double r = block_sum(v, red);
+    if (tid == 0) partials[(size_t)blockIdx.x * stride_p + k] = r;
+  }
+  if (!arrive_last(counter, &last)) return;
+  reduce_partials(partials, gridDim.x, stride_p, m, result, red);
+  if (tid == 0) *counter = 0u;
+}
+
+// ---- host launchers ---------------------------------------------------------------------------
+cudaError_t launch_norm_1d(const Program& P, const WeidCoef& W, const double* theta,
+                           double* partials, unsigned* counter, double* derived,
+                           cudaStream_t st) {
+  const int nb = P.ngrid_blocks > 0 ? P.ngrid_blocks : 1;
+  k_norm_1d<<<nb, kThreads, 0, st>>>(P, W, theta, partials, counter, derived);
+  return cudaGetLastError();
+}
+
+size_t events_1d_smem(const Program& P, bool grad, int threads) {
+  return grad ? (size_t)(kMaxStack + 1) * P.nfree * threads * sizeof(double) : 0;
+}
+
+cudaError_t launch_events_1d(const Program& P, const WeidCoef& W, const Cols& cols, int64_t n,
+                             const double* theta, const double* derived, double* partials,
+                             unsigned* counter, double* result, double* out_logp, bool grad,
+                             bool store, int analytic_only, int nblocks, cudaStream_t st) {
+  const int threads = kThreads1D;
+  const size_t smem = events_1d_smem(P, grad, threads);
+  if (store) {
+    k_events_1d<false, 1><<<nblocks, threads, 0, st>>>(P, W, cols, n, theta, derived, partials,
+                                                       counter, result, out_logp, analytic_only);
+  } else if (grad) {
+    static bool attr[64] = {false};  // opt in to > 48 KB dynamic shared memory, per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!attr[dev & 63]) {
+      cudaFuncSetAttribute(k_events_1d<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           200 * 1024);
+      attr[dev & 63] = true;
+    }
+    k_events_1d<true, 0><<<nblocks, threads, smem, st>>>(P, W, cols, n, theta, derived, partials,
+                                                         counter, result, out_logp, analytic_only);
+  } else {
+    k_events_1d<false, 0><<<nblocks, threads, 0, st>>>(P, W, cols, n, theta, derived, partials,
+                                                       counter, result, out_logp, analytic_only);
+  }
+  return cudaGetLastError();
+}
+
+int events_1d_blocks_per_sm(bool grad, size_t smem) {
+  int nb = 0;
+  if (grad)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_events_1d<true, 0>, kThreads1D, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_events_1d<false, 0>, kThreads1D, 0);
+  return nb > 0 ? nb : 1;
+}
+
+}  // namespace gfi

@@ -1,0 +1,639 @@
+// k_dalitz.cu -- sm_103a kernels of the three-body Dalitz amplitude model (Sec. 4 of
+// the paper: the D0 -> pi+ pi- pi0 analysis that drove GooFit's design).
+//
+//   A(s12, s13) = a_NR + sum_r c_r A_r,   A_r = F_L(q) S_L BW_r(s_ab),   P = |A|^2
+//   NLL = -sum_i log P_i + n log N,        N = dA sum_{cells inside} |A(cell centre)|^2
+//
+// Kernels:
+//   k_dalitz_mask      cell-centre-inside mask of the normalisation grid (set-up)
+//   k_dalitz_ev_cache  per-event A_r of resonances whose shape (m0, Gamma0) is fixed
+//   k_dalitz_grid_cols per-cell A_r of fixed-shape resonances (normalisation cache)
+//   k_dalitz_gram      Gram matrix G_rs = dA sum conj(A_r) A_s from the cached columns:
+//                      with every shape fixed, N = c^H G c costs O(K^2) per call
+//   k_dalitz_stream    the event pass (METRIC_NLL / METRIC_STORE) or the direct norm
+//                      pass over grid cells (METRIC_NORM) when some shape is free;
+//                      FP64 or FP32 amplitudes (T), optional fused gradient (G)
+#include "devutil.cuh"
+#include "gf_internal.h"
+#include "launch.h"
+
+namespace gfi {
+
+enum Metric { METRIC_NLL = 0, METRIC_STORE = 1, METRIC_NORM = 2 };
+
+template <typename T>
+struct C2 {
+  T r, i;
+};
+
+template <typename T>
+__device__ __forceinline__ T rsq(T x);
+template <>
+__device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
+template <>
+__device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+template <typename T>
+__device__ __forceinline__ T rcp(T x);
+template <>
+__device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
+template <>
+__device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }
+template <typename T>
+__device__ __forceinline__ T lg(T x);
+template <>
+__device__ __forceinline__ double lg<double>(double x) { return log(x); }
+template <>
+__device__ __forceinline__ float lg<float>(float x) { return logf(x); }
+
+// Per-call constants of one resonance, from theta (FP64 arithmetic, once per block).
+struct ResK {
+  double m0, m0sq, g0, cr, ci;
+  double K;       // Gamma0 m0 B_L(z0) / q0^{2L+1}:  Gamma(m) = K q^{2L+1} / (m B_L(z))
+  double sqrtB0;  // sqrt(B_L(z0)):                  F_L = sqrtB0 / sqrt(B_L(z))
+  double hF;      // (1/2) d log B_L(z0)/dm0:        dF/dm0 = F hF
+  double dlogK;   // d log K / dm0
+  double invg0;
+};
+
+__device__ __forceinline__ double barrier(int L, double z) {
+  return L == 0 ? 1.0 : (L == 1 ? 1.0 + z : fma(z, z + 3.0, 9.0));
+}
+__device__ __forceinline__ double barrier_dz(int L, double z) {
+  return L == 0 ? 0.0 : (L == 1 ? 1.0 : fma(2.0, z, 3.0));
+}
+
+__device__ void res_constants(const DalitzPlan& D, const DalitzRes& R, const double* th, ResK& k) {
+  const DalitzChannel& c = D.ch[R.channel];
+  const int L = R.spin;
+  const double m0 = th[R.p_m0], g0 = th[R.p_g0];
+  const double u = m0 * m0;
+  const double q02 = (u - c.thrA) * (u - c.thrB) / (4.0 * u);
+  const double z0 = q02 * D.R2;
+  const double B0 = barrier(L, z0);
+  const double q0 = sqrt(q02);
+  double q0p = q0;  // q0^{2L+1}
+  for (int j = 0; j < L; ++j) q0p *= q02;
+  k.m0 = m0;
+  k.m0sq = u;
+  k.g0 = g0;
+  k.cr = th[R.p_re];
+  k.ci = th[R.p_im];
+  k.K = g0 * m0 * B0 / q0p;
+  k.sqrtB0 = sqrt(B0);
+  // d q0^2/dm0 = (m0^4 - thrA thrB)/(2 m0^3)
+  const double dq02 = (u * u - c.thrA * c.thrB) / (2.0 * u * m0);
+  const double dlogB0 = barrier_dz(L, z0) * D.R2 * dq02 / B0;
+  k.hF = 0.5 * dlogB0;
+  k.dlogK = 1.0 / m0 + dlogB0 - (2 * L + 1) * 0.5 * dq02 / q02;
+  k.invg0 = 1.0 / g0;
+}
+
+// Per-event, per-channel kinematics (a, b = resonance pair; c = bachelor).
+template <typename T>
+struct ChanK {
+  T sab, minv, q, qp1, qp2;  // s_ab, 1/m, q, q^3, q^5
+  T rB1, iB1, rB2, iB2;      // 1/sqrt(B_1), 1/B_1, 1/sqrt(B_2), 1/B_2
+  T S1, S2;
+};
+
+template <typename T>
+__device__ __forceinline__ void chan_kin(const DalitzPlan& D, int ch, T s12, T s13, T s23,
+                                         ChanK<T>& k) {
+  const DalitzChannel& c = D.ch[ch];
+  T sab, sbc, sac;
+  if (ch == 0) { sab = s12; sbc = s23; sac = s13; }
+  else if (ch == 1) { sab = s13; sbc = s23; sac = s12; }
+  else { sab = s23; sbc = s13; sac = s12; }
+  const T rs = rsq<T>(sab);
+  const T inv_s = rs * rs;
+  k.sab = sab;
+  k.minv = rs;
+  T q2 = (sab - (T)c.thrA) * (sab - (T)c.thrB) * inv_s * (T)0.25;
+  q2 = q2 > (T)0 ? q2 : (T)0;
+  const T rq = q2 > (T)0 ? rsq<T>(q2) : (T)0;
+  k.q = q2 * rq;
+  k.qp1 = k.q * q2;
+  k.qp2 = k.qp1 * q2;
+  const T z = q2 * (T)D.R2;
+  const T B1 = (T)1 + z;
+  const T B2 = z * (z + (T)3) + (T)9;
+  k.rB1 = rsq<T>(B1);
+  k.iB1 = k.rB1 * k.rB1;
+  k.rB2 = rsq<T>(B2);
+  k.iB2 = k.rB2 * k.rB2;
+  k.S1 = sbc - sac + (T)c.k1 * inv_s;
+  const T a2 = sab - (T)c.a2c + (T)c.a2k * inv_s;
+  k.S2 = k.S1 * k.S1 - a2 * (T)4 * q2 * (T)(1.0 / 3.0);
+}
+
+// Breit-Wigner pieces of resonance r at an event: returns A_r, and (for the gradient)
+// FS = F_L S_L, BW, Gamma(m).
+template <typename T>
+__device__ __forceinline__ void res_amp(const DalitzRes& R, const ResK& k, const ChanK<T>& c,
+                                        C2<T>& A, T& FS, C2<T>& BW, T& Gm) {
+  const int L = R.spin;
+  T qpow, iB, F, S;
+  if (L == 0) { qpow = c.q; iB = (T)1; F = (T)1; S = (T)1; }
+  else if (L == 1) { qpow = c.qp1; iB = c.iB1; F = (T)k.sqrtB0 * c.rB1; S = c.S1; }
+  else { qpow = c.qp2; iB = c.iB2; F = (T)k.sqrtB0 * c.rB2; S = c.S2; }
+  Gm = (T)k.K * qpow * c.minv * iB;
+  const T m0 = (T)k.m0;
+  const T Dr = (T)k.m0sq - c.sab;
+  const T mG = m0 * Gm;
+  const T inv = rcp<T>(Dr * Dr + mG * mG);
+  BW.r = Dr * inv;
+  BW.i = mG * inv;
+  FS = F * S;
+  A.r = FS * BW.r;
+  A.i = FS * BW.i;
+}
+
+// Cached columns are double2 (FP64 plans, and the grid columns of every plan) or float2
+// (per-event columns of an FP32 plan); wide = 1 selects double2.
+template <typename T>
+__device__ __forceinline__ C2<T> load_cached(const void* base, int64_t stride, int slot,
+                                             int64_t i, int wide) {
+  if (wide) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(base) + (size_t)slot * stride + i);
+    return {(T)v.x, (T)v.y};
+  }
+  const float2 v = __ldg(reinterpret_cast<const float2*>(base) + (size_t)slot * stride + i);
+  return {(T)v.x, (T)v.y};
+}
+
+// ---- set-up kernels --------------------------------------------------------------------------
+// Inside test at a cell centre: |cos theta| <= 1 in the (12) rest frame, written as
+// S_1^2 <= a2 a3 (4 k.q)^2 <= (4|k|^2)(4|q|^2) for channel (12), together with both
+// invariant masses above threshold.
+__device__ __forceinline__ bool inside_region(const DalitzPlan& D, double s12, double s13) {
+  const double s23 = D.sum_m2 - s12 - s13;
+  const DalitzChannel& c = D.ch[0];
+  if (!(s12 > c.thrA) || !(s13 > D.ch[1].thrA) || !(s23 > D.ch[2].thrA)) return false;
+  const double inv_s = 1.0 / s12;
+  const double S1 = s23 - s13 + c.k1 * inv_s;
+  const double a2 = s12 - c.a2c + c.a2k * inv_s;
+  const double a3 = (s12 - c.thrA) * (s12 - c.thrB) * inv_s;
+  return S1 * S1 <= a2 * a3;
+}
+
+__global__ void k_dalitz_mask(const DalitzPlan D, uint8_t* inside) {
+  const int64_t ncell = (int64_t)D.nbx * D.nby;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncell;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(i / D.nby), iy = (int)(i % D.nby);
+    const double s12 = D.x0 + (ix + 0.5) * D.hx, s13 = D.y0 + (iy + 0.5) * D.hy;
+    inside[i] = inside_region(D, s12, s13) ? 1 : 0;
+  }
+}
+
+// Per-event amplitudes of the event-cached resonances, FP64 (double2) or FP32 (float2).
+template <typename T>
+__global__ void k_dalitz_ev_cache(const DalitzPlan D, const double* __restrict__ theta,
+                                  const double* __restrict__ s12, const double* __restrict__ s13,
+                                  int64_t n, void* __restrict__ cache) {
+  __shared__ ResK rk[kMaxRes];
+  if (threadIdx.x < D.nres) res_constants(D, D.res[threadIdx.x], theta, rk[threadIdx.x]);
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = s12[i], b = s13[i];
+    const double c = D.sum_m2 - a - b;
+    ChanK<double> ck[3];
+    for (int ch = 0; ch < 3; ++ch) chan_kin<double>(D, ch, a, b, c, ck[ch]);
+    for (int r = 0; r < D.nres; ++r) {
+      const DalitzRes& R = D.res[r];
+      if (R.ev_cached < 0) continue;
+      C2<double> A, BW;
+      double FS, Gm;
+      res_amp<double>(R, rk[r], ck[R.channel], A, FS, BW, Gm);
+      if (sizeof(T) == 8)
+        reinterpret_cast<double2*>(cache)[(size_t)R.ev_cached * n + i] = make_double2(A.r, A.i);
+      else
+        reinterpret_cast<float2*>(cache)[(size_t)R.ev_cached * n + i] =
+            make_float2((float)A.r, (float)A.i);
+    }
+  }
+}
+
+// Per-cell amplitudes (FP64) of the listed resonances; zero outside the region.
+__global__ void k_dalitz_grid_cols(const DalitzPlan D, const double* __restrict__ theta,
+                                   const int* __restrict__ todo, int ntodo,
+                                   double2* __restrict__ cols, const uint8_t* __restrict__ inside) {
+  __shared__ ResK rk[kMaxRes];
+  if (threadIdx.x < D.nres) res_constants(D, D.res[threadIdx.x], theta, rk[threadIdx.x]);
+  __syncthreads();
+  const int64_t ncell = (int64_t)D.nbx * D.nby;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncell;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool in = inside[i] != 0;
+    const int ix = (int)(i / D.nby), iy = (int)(i % D.nby);
+    const double a = D.x0 + (ix + 0.5) * D.hx, b = D.y0 + (iy + 0.5) * D.hy;
+    const double c = D.sum_m2 - a - b;
+    for (int t = 0; t < ntodo; ++t) {
+      const int r = todo[t];
+      const DalitzRes& R = D.res[r];
+      double2 v = make_double2(0.0, 0.0);
+      if (in) {
+        ChanK<double> ck;
+        chan_kin<double>(D, R.channel, a, b, c, ck);
+        C2<double> A, BW;
+        double FS, Gm;
+        res_amp<double>(R, rk[r], ck, A, FS, BW, Gm);
+        v = make_double2(A.r, A.i);
+      }
+      cols[(size_t)(r + 1) * ncell + i] = v;
+    }
+  }
+}
+
+// Gram matrix from the columns: block (chunk, entry group of 8 upper-triangle entries).
+// partials2[(chunk * ngroups + grp) * 16 + 2e + {0,1}] then the last block sums chunks.
+constexpr int kGramGroup = 8;
+__global__ void __launch_bounds__(kThreads) k_dalitz_gram(const DalitzPlan D,
+                                                          const double2* __restrict__ cols,
+                                                          const uint8_t* __restrict__ inside,
+                                                          double* __restrict__ partials,
+                                                          unsigned* __restrict__ counter,
+                                                          double* __restrict__ gram, int nchunks) {
+  __shared__ double red[32];
+  __shared__ int last;
+  const int K = D.nres + 1;
+  const int nent = K * (K + 1) / 2;
+  const int ngroups = (nent + kGramGroup - 1) / kGramGroup;
+  const int chunk = blockIdx.x, grp = blockIdx.y;
+  const int64_t ncell = (int64_t)D.nbx * D.nby;
+  const int64_t per = (ncell + nchunks - 1) / nchunks;
+  const int64_t beg = chunk * per, end = min(ncell, beg + per);
+  int er[kGramGroup], es[kGramGroup];
+  {
+    int e = 0, idx = 0;
+    for (int r = 0; r < K; ++r)
+      for (int s = r; s < K; ++s, ++idx)
+        if (idx >= grp * kGramGroup && idx < (grp + 1) * kGramGroup) {
+          er[e] = r;
+          es[e] = s;
+          ++e;
+        }
+    for (; e < kGramGroup; ++e) er[e] = es[e] = -1;
+  }
+  double ar[kGramGroup], ai[kGramGroup];
+#pragma unroll
+  for (int e = 0; e < kGramGroup; ++e) ar[e] = ai[e] = 0.0;
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    if (!inside[i]) continue;
+#pragma unroll
+    for (int e = 0; e < kGramGroup; ++e) {
+      if (er[e] < 0) continue;
+      const double2 x = er[e] == 0 ? make_double2(1.0, 0.0) : cols[(size_t)er[e] * ncell + i];
+      const double2 y = es[e] == 0 ? make_double2(1.0, 0.0) : cols[(size_t)es[e] * ncell + i];
+      // conj(x) y
+      ar[e] = fma(x.x, y.x, fma(x.y, y.y, ar[e]));
+      ai[e] = fma(x.x, y.y, fma(-x.y, y.x, ai[e]));
+    }
+  }
+  for (int e = 0; e < kGramGroup; ++e) {
+    const double r1 = block_sum(ar[e], red);
+    const double r2 = block_sum(ai[e], red);
+    if (threadIdx.x == 0) {
+      partials[((size_t)chunk * ngroups + grp) * 2 * kGramGroup + 2 * e] = r1;
+      partials[((size_t)chunk * ngroups + grp) * 2 * kGramGroup + 2 * e + 1] = r2;
+    }
+  }
+  if (!arrive_last(counter, &last)) return;
+  const double dA = D.hx * D.hy;
+  for (int g = 0; g < ngroups; ++g)
+    for (int e = 0; e < 2 * kGramGroup; ++e) {
+      Neu a;
+      for (int c = threadIdx.x; c < nchunks; c += blockDim.x)
+        a.add(__ldcg(partials + ((size_t)c * ngroups + g) * 2 * kGramGroup + e));
+      const double v = block_sum(a.get(), red);
+      if (threadIdx.x == 0) {
+        const int ent = g * kGramGroup + e / 2;
+        if (ent < nent) {
+          int idx = 0, rr = 0, ss = 0;
+          for (int r = 0; r < K; ++r)
+            for (int s = r; s < K; ++s, ++idx)
+              if (idx == ent) { rr = r; ss = s; }
+          const double val = v * dA;
+          // G_rs and G_sr = conj(G_rs)
+          const double im_part = (rr == ss) ? 0.0 : val;
+          gram[2 * (rr * K + ss) + (e & 1)] = (e & 1) ? im_part : val;
+          gram[2 * (ss * K + rr) + (e & 1)] = (e & 1) ? -im_part : val;
+        }
+      }
+      __syncthreads();
+    }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// ---- the stream kernel ------------------------------------------------------------------------
+// One pass over events (METRIC_NLL / METRIC_STORE) or over grid cells (METRIC_NORM).
+// Per item: kinematics of the three channels, every resonance either loaded from its
+// cache column or evaluated here, A = a_NR + sum c_r A_r, P = |A|^2; the metric is
+// -log P (events) or P dA (cells); with G the partials d/dtheta as well.
+// Shared memory: gacc[nfree][blockDim] per-thread gradient sums.
+template <typename T, bool G, int METRIC>
+__global__ void __launch_bounds__(kThreads) k_dalitz_stream(
+    const DalitzPlan D, const double* __restrict__ theta, const double* __restrict__ s12d,
+    const double* __restrict__ s13d, const float* __restrict__ sf, int64_t n,
+    const void* __restrict__ cache, int64_t cache_stride, int cache_wide,
+    const uint8_t* __restrict__ inside,
+    double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
+    double* __restrict__ out_logp, const double* __restrict__ norm_in, int norm_mode,
+    const double* __restrict__ gram) {
+  extern __shared__ double dyn[];
+  __shared__ ResK rk[kMaxRes];
+  __shared__ double red[32];
+  __shared__ int last;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int nf = D.nfree;
+  const int nres = D.nres;
+  if (tid < nres) res_constants(D, D.res[tid], theta, rk[tid]);
+  Acc<T>* gacc = reinterpret_cast<Acc<T>*>(dyn) + tid;
+  if (G)
+    for (int k = 0; k < nf; ++k) gacc[k * bd] = Acc<T>();
+  __syncthreads();
+  Acc<T> acc;
+  const int64_t nitems = (METRIC == METRIC_NORM) ? (int64_t)D.nbx * D.nby : n;
+
+  for (int64_t i = (int64_t)blockIdx.x * bd + tid; i < nitems; i += (int64_t)gridDim.x * bd) {
+    T a, b, c;
+    if (METRIC == METRIC_NORM) {
+      if (!inside[i]) continue;
+      const int ix = (int)(i / D.nby), iy = (int)(i % D.nby);
+      const double da = D.x0 + (ix + 0.5) * D.hx, db = D.y0 + (iy + 0.5) * D.hy;
+      a = (T)da;
+      b = (T)db;
+      c = (T)(D.sum_m2 - da - db);
+    } else if (sizeof(T) == 8) {
+      const double da = __ldcs(s12d + i), db = __ldcs(s13d + i);
+      a = (T)da;
+      b = (T)db;
+      c = (T)(D.sum_m2 - da - db);
+    } else {
+      a = (T)__ldcs(sf + i);
+      b = (T)__ldcs(sf + n + i);
+      c = (T)__ldcs(sf + 2 * n + i);
+    }
+    ChanK<T> ck[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) chan_kin<T>(D, ch, a, b, c, ck[ch]);
+    C2<T> Ar[kMaxRes], BW[kMaxRes];
+    T FS[kMaxRes], Gm[kMaxRes];
+    C2<T> At = {(T)1, (T)0};  // a_NR
+#pragma unroll
+    for (int r = 0; r < kMaxRes; ++r) {
+      if (r >= nres) break;
+      const DalitzRes& R = D.res[r];
+      if (R.ev_cached >= 0) {
+        Ar[r] = load_cached<T>(cache, cache_stride, R.ev_cached, i, cache_wide);
+      } else {
+        res_amp<T>(R, rk[r], ck[R.channel], Ar[r], FS[r], BW[r], Gm[r]);
+      }
+      const T cr = (T)rk[r].cr, ci = (T)rk[r].ci;
+      At.r += cr * Ar[r].r - ci * Ar[r].i;
+      At.i += cr * Ar[r].i + ci * Ar[r].r;
+    }
+    const T P = At.r * At.r + At.i * At.i;
+    if (METRIC == METRIC_STORE) {
+      out_logp[i] = (double)lg<T>(P);
+      continue;
+    }
+    if (METRIC == METRIC_NLL) acc.add(-lg<T>(P));
+    else acc.add(P);
+    if (G) {
+      // d P / d theta; events use d(-log P) = -(dP)/P, cells use dP
+      const T sc = (METRIC == METRIC_NLL) ? (T)(-2) / P : (T)2;
+#pragma unroll
+      for (int r = 0; r < kMaxRes; ++r) {
+        if (r >= nres) break;
+        const DalitzRes& R = D.res[r];
+        // conj(A) A_r
+        const T xr = At.r * Ar[r].r + At.i * Ar[r].i;
+        const T xi = At.r * Ar[r].i - At.i * Ar[r].r;
+        if (R.g_re >= 0) gacc[R.g_re * bd].add(sc * xr);
+        if (R.g_im >= 0) gacc[R.g_im * bd].add(-sc * xi);
+        if (R.ev_cached < 0 && (R.g_m0 >= 0 || R.g_g0 >= 0)) {
+          const T cr = (T)rk[r].cr, ci = (T)rk[r].ci;
+          // BW^2
+          const T b2r = BW[r].r * BW[r].r - BW[r].i * BW[r].i;
+          const T b2i = (T)2 * BW[r].r * BW[r].i;
+          // conj(A) c_r
+          const T yr = At.r * cr + At.i * ci;
+          const T yi = At.r * ci - At.i * cr;
+          if (R.g_m0 >= 0) {
+            // dA_r/dm0 = FS (hF BW - BW^2 dD),  dD = 2 m0 - i Gamma (1 + m0 dlogK)
+            const T dDr = (T)(2.0 * rk[r].m0);
+            const T dDi = -Gm[r] * (T)(1.0 + rk[r].m0 * rk[r].dlogK);
+            const T hF = (T)rk[r].hF;
+            const T dr = FS[r] * (hF * BW[r].r - (b2r * dDr - b2i * dDi));
+            const T di = FS[r] * (hF * BW[r].i - (b2r * dDi + b2i * dDr));
+            gacc[R.g_m0 * bd].add(sc * (yr * dr - yi * di));
+          }
+          if (R.g_g0 >= 0) {
+            // dA_r/dGamma0 = FS i m0 (Gamma/Gamma0) BW^2
+            const T f = FS[r] * (T)rk[r].m0 * Gm[r] * (T)rk[r].invg0;
+            const T dr = -f * b2i, di = f * b2r;
+            gacc[R.g_g0 * bd].add(sc * (yr * dr - yi * di));
+          }
+        }
+      }
+    }
+  }
+  if (METRIC == METRIC_STORE) return;
+
+  const int m = 1 + (G ? nf : 0);
+  const int stride_p = 1 + 2 * kMaxRes * 2;
+  for (int k = 0; k < m; ++k) {
+    const double v = (k == 0) ? acc.get() : gacc[(k - 1) * bd].get();
+    const double r = block_sum(v, red);
+    if (tid == 0) partials[(size_t)blockIdx.x * stride_p + k] = r;
+  }
+  if (!arrive_last(counter, &last)) return;
+  __shared__ double tot[1 + 4 * kMaxRes];
+  reduce_partials(partials, gridDim.x, stride_p, m, tot, red);
+  __syncthreads();
+  if (METRIC == METRIC_NORM) {
+    const double dA = D.hx * D.hy;
+    if (tid < m) result[tid] = tot[tid] * dA;
+  } else if (tid == 0) {
+    // combine with the normalisation: + n log N, + n dN/N
+    double N;
+    double dN[4 * kMaxRes];
+    for (int k = 0; k < nf; ++k) dN[k] = 0.0;
+    if (norm_mode == DN_GRAM) {
+      // N = c^H G c, c_0 = a_NR = 1;  v_k = sum_s G_ks c_s;  dN/dRe c_k = 2 Re v_k,
+      // dN/dIm c_k = 2 Im v_k
+      const int K = nres + 1;
+      double cr[kMaxRes + 1], ci[kMaxRes + 1];
+      cr[0] = 1.0;
+      ci[0] = 0.0;
+      for (int r = 0; r < nres; ++r) { cr[r + 1] = rk[r].cr; ci[r + 1] = rk[r].ci; }
+      N = 0.0;
+      for (int k = 0; k < K; ++k) {
+        double vr = 0.0, vi = 0.0;
+        for (int s = 0; s < K; ++s) {
+          const double gr = gram[2 * (k * K + s)], gi = gram[2 * (k * K + s) + 1];
+          vr += gr * cr[s] - gi * ci[s];
+          vi += gr * ci[s] + gi * cr[s];
+        }
+        N += cr[k] * vr + ci[k] * vi;  // Re(conj(c_k) v_k)
+        if (k > 0 && G) {
+          const DalitzRes& R = D.res[k - 1];
+          if (R.g_re >= 0) dN[R.g_re] += 2.0 * vr;
+          if (R.g_im >= 0) dN[R.g_im] += 2.0 * vi;
+        }
+      }
+    } else {
+      N = norm_in[0];
+      if (G)
+        for (int k = 0; k < nf; ++k) dN[k] = norm_in[1 + k];
+    }
+    const double nn = (double)n;
+    result[0] = tot[0] + nn * log(N);
+    if (G)
+      for (int k = 0; k < nf; ++k) result[1 + k] = tot[1 + k] + nn * dN[k] / N;
+  }
+  if (tid == 0) *counter = 0u;
+}
+
+// ---- host launchers ---------------------------------------------------------------------------
+static int grid_for(int64_t items, int threads, int cap) {
+  int64_t b = (items + threads - 1) / threads;
+  if (b < 1) b = 1;
+  return (int)(b < cap ? b : cap);
+}
+
+cudaError_t launch_dalitz_mask(const DalitzPlan& D, uint8_t* inside, cudaStream_t st) {
+  k_dalitz_mask<<<grid_for((int64_t)D.nbx * D.nby, 256, 4096), 256, 0, st>>>(D, inside);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dalitz_ev_cache(const DalitzPlan& D, bool mixed, const double* theta,
+                                   const double* s12, const double* s13, int64_t n,
+                                   void* ev_cache, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = grid_for(n, 256, 152 * 8);
+  if (mixed) k_dalitz_ev_cache<float><<<nb, 256, 0, st>>>(D, theta, s12, s13, n, ev_cache);
+  else k_dalitz_ev_cache<double><<<nb, 256, 0, st>>>(D, theta, s12, s13, n, ev_cache);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dalitz_grid_cols(const DalitzPlan& D, const double* theta, const int* todo,
+                                    int ntodo, void* grid_cols, const uint8_t* inside,
+                                    cudaStream_t st) {
+  if (ntodo <= 0) return cudaSuccess;
+  k_dalitz_grid_cols<<<grid_for((int64_t)D.nbx * D.nby, 256, 152 * 8), 256, 0, st>>>(
+      D, theta, todo, ntodo, reinterpret_cast<double2*>(grid_cols), inside);
+  return cudaGetLastError();
+}
+
+constexpr int kGramChunks = 304;
+cudaError_t launch_dalitz_gram(const DalitzPlan& D, const DalitzBufs& B, cudaStream_t st) {
+  const int K = D.nres + 1;
+  const int ngroups = (K * (K + 1) / 2 + kGramGroup - 1) / kGramGroup;
+  dim3 grid(kGramChunks, ngroups);
+  k_dalitz_gram<<<grid, kThreads, 0, st>>>(D, reinterpret_cast<const double2*>(B.grid_cols),
+                                          B.inside, B.partials2, B.counter2, B.gram, kGramChunks);
+  return cudaGetLastError();
+}
+
+template <typename T, bool G, int M>
+static cudaError_t launch_stream_t(const DalitzPlan& D, const double* theta, const DalitzBufs& B,
+                                   const void* cache, int64_t cstride, int cwide, double* partials,
+                                   unsigned* counter, double* result, int norm_mode, int nblocks,
+                                   cudaStream_t st) {
+  const size_t smem = G ? (size_t)D.nfree * kThreads * sizeof(Acc<T>) : 0;
+  static bool attr[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (G && !attr[dev & 63]) {
+    cudaFuncSetAttribute(k_dalitz_stream<T, G, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         160 * 1024);
+    attr[dev & 63] = true;
+  }
+  k_dalitz_stream<T, G, M><<<nblocks, kThreads, smem, st>>>(
+      D, theta, B.s12, B.s13, B.sf, B.n, cache, cstride, cwide, B.inside, partials, counter, result,
+      B.out_logp, B.norm_out, norm_mode, B.gram);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dalitz_norm_direct(const DalitzPlan& D, bool mixed, bool grad,
+                                      const double* theta, const DalitzBufs& B, int nblocks,
+                                      cudaStream_t st) {
+  const int64_t ncell = (int64_t)D.nbx * D.nby;
+  // cached grid columns: slot r -> column r + 1 (DalitzRes::grid_col); use ev_cached >= 0
+  // as "column valid" by passing a plan whose ev_cached points at grid columns.
+  DalitzPlan E = D;
+  for (int r = 0; r < E.nres; ++r) E.res[r].ev_cached = D.res[r].ev_cached >= 0 ? r + 1 : -1;
+  if (mixed) {
+    if (grad)
+      return launch_stream_t<float, true, METRIC_NORM>(E, theta, B, B.grid_cols, ncell, 1,
+                                                         B.partials2, B.counter2, B.norm_out, 0,
+                                                         nblocks, st);
+    return launch_stream_t<float, false, METRIC_NORM>(E, theta, B, B.grid_cols, ncell, 1,
+                                                        B.partials2, B.counter2, B.norm_out, 0,
+                                                        nblocks, st);
+  }
+  if (grad)
+    return launch_stream_t<double, true, METRIC_NORM>(E, theta, B, B.grid_cols, ncell, 1,
+                                                        B.partials2, B.counter2, B.norm_out, 0,
+                                                        nblocks, st);
+  return launch_stream_t<double, false, METRIC_NORM>(E, theta, B, B.grid_cols, ncell, 1,
+                                                       B.partials2, B.counter2, B.norm_out, 0,
+                                                       nblocks, st);
+}
+
+cudaError_t launch_dalitz_events(const DalitzPlan& D, bool mixed, bool grad, bool store,
+                                 int norm_mode, const double* theta, const DalitzBufs& B,
+                                 int nblocks, cudaStream_t st) {
+  const int64_t cs = B.n;
+  if (store) {
+    if (mixed)
+      return launch_stream_t<float, false, METRIC_STORE>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 1, B.partials,
+                                                           B.counter, B.result, norm_mode,
+                                                           nblocks, st);
+    return launch_stream_t<double, false, METRIC_STORE>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 1, B.partials,
+                                                          B.counter, B.result, norm_mode, nblocks,
+                                                          st);
+  }
+  if (mixed) {
+    if (grad)
+      return launch_stream_t<float, true, METRIC_NLL>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 1, B.partials,
+                                                        B.counter, B.result, norm_mode, nblocks,
+                                                        st);
+    return launch_stream_t<float, false, METRIC_NLL>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 1, B.partials,
+                                                       B.counter, B.result, norm_mode, nblocks,
+                                                       st);
+  }
+  if (grad)
+    return launch_stream_t<double, true, METRIC_NLL>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 1, B.partials,
+                                                       B.counter, B.result, norm_mode, nblocks,
+                                                       st);
+  return launch_stream_t<double, false, METRIC_NLL>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 1, B.partials,
+                                                      B.counter, B.result, norm_mode, nblocks, st);
+}
+
+int dalitz_blocks_per_sm(bool mixed, bool grad) {
+  int nb = 0;
+  // smem depends on nfree; size for the largest plan (4 kMaxRes free parameters)
+  const size_t smem = grad ? (size_t)4 * kMaxRes * kThreads * (mixed ? 8 : 8) : 0;
+  if (mixed) {
+    if (grad)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dalitz_stream<float, true, METRIC_NLL>,
+                                                    kThreads, smem);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dalitz_stream<float, false, METRIC_NLL>,
+                                                    kThreads, 0);
+  } else {
+    if (grad)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dalitz_stream<double, true, METRIC_NLL>,
+                                                    kThreads, smem);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &nb, k_dalitz_stream<double, false, METRIC_NLL>, kThreads, 0);
+  }
+  return nb > 0 ? nb : 1;
+}
+
+}  // namespace gfi

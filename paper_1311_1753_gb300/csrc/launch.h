@@ -1,0 +1,57 @@
+// launch.h -- host-side entry points of the kernel translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "gf_internal.h"
+
+namespace gfi {
+
+// k_1d.cu
+cudaError_t launch_norm_1d(const Program& P, const WeidCoef& W, const double* theta,
+                           double* partials, unsigned* counter, double* derived, cudaStream_t st);
+size_t events_1d_smem(const Program& P, bool grad, int threads);
+cudaError_t launch_events_1d(const Program& P, const WeidCoef& W, const Cols& cols, int64_t n,
+                             const double* theta, const double* derived, double* partials,
+                             unsigned* counter, double* result, double* out_logp, bool grad,
+                             bool store, int analytic_only, int nblocks, cudaStream_t st);
+int events_1d_blocks_per_sm(bool grad, size_t smem);
+
+// k_dalitz.cu
+struct DalitzBufs {
+  const double* s12;
+  const double* s13;
+  const float* sf;          // FP32 plans: s12, s13, s23 as three float columns [3][n]
+  int64_t n;
+  const void* ev_cache;     // [ncached][n] double2 (FP64) or float2 (mixed)
+  void* grid_cols;          // [nres + 1][nbx * nby] double2 (column 0 unused: a_NR = 1)
+  const uint8_t* inside;    // [nbx * nby] cell-centre-inside mask
+  double* gram;             // (nres + 1)^2 complex, interleaved
+  double* norm_out;         // [1 + nfree]: N, dN/dtheta (direct norm pass)
+  double* partials;         // per-block partials
+  double* partials2;        // per-block partials of the norm pass
+  unsigned* counter;
+  unsigned* counter2;
+  double* result;           // [1 + nfree]
+  double* out_logp;         // per-event log P (store mode)
+};
+// mode flags for the event launch
+enum DalitzNormMode { DN_GRAM = 0, DN_DIRECT = 1 };
+cudaError_t launch_dalitz_mask(const DalitzPlan& D, uint8_t* inside, cudaStream_t st);
+cudaError_t launch_dalitz_ev_cache(const DalitzPlan& D, bool mixed, const double* theta,
+                                   const double* s12, const double* s13, int64_t n,
+                                   void* ev_cache, cudaStream_t st);
+cudaError_t launch_dalitz_grid_cols(const DalitzPlan& D, const double* theta, const int* cols_todo,
+                                    int ncols, void* grid_cols, const uint8_t* inside,
+                                    cudaStream_t st);
+cudaError_t launch_dalitz_gram(const DalitzPlan& D, const DalitzBufs& B, cudaStream_t st);
+cudaError_t launch_dalitz_norm_direct(const DalitzPlan& D, bool mixed, bool grad,
+                                      const double* theta, const DalitzBufs& B, int nblocks,
+                                      cudaStream_t st);
+cudaError_t launch_dalitz_events(const DalitzPlan& D, bool mixed, bool grad, bool store,
+                                 int norm_mode, const double* theta, const DalitzBufs& B,
+                                 int nblocks, cudaStream_t st);
+int dalitz_blocks_per_sm(bool mixed, bool grad);
+constexpr int kGramEntries = (kMaxRes + 1) * (kMaxRes + 2) / 2;
+
+}  // namespace gfi

@@ -1,0 +1,301 @@
+// server.cpp -- continuous-batching fit server (toy / pull studies).
+//
+// Requests (a model context + its events) queue on submit.  The scheduler admits a
+// request when a slot is free and its device bytes fit in the memory budget, uploads its
+// events (they stay resident until the fit ends) and starts a host thread that owns the
+// fit's minimiser state.  Each minimiser step that needs NLL + gradient posts its theta
+// and waits.  A scheduler "tick" takes every posted evaluation, enqueues all of them on
+// the device back to back (each fit on its own stream, so their kernels overlap), then
+// collects the results and wakes the fits.  Requests that arrive while others run are
+// admitted at the next tick as slots and memory free up.  Every wait is bounded.
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/gf.h"
+#include "ctx.h"
+#include "fit.h"
+
+using namespace gfi;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+struct Req {
+  uint64_t ticket = 0;
+  gf_ctx* ctx = nullptr;
+  gf_dataset* ds = nullptr;
+  int root = -1;
+  gf_fit_opts opts{};
+  bool has_opts = false;
+  size_t bytes = 0;
+  Clock::time_point t_submit, t_done;
+  // evaluation hand-off
+  bool want = false, ready = false;
+  std::vector<double> theta, grad;
+  double f = 0.0;
+  int eval_rc = GF_OK;
+  // outcome
+  bool done = false;
+  MinResult result;
+  int nfree = 0;
+  std::thread th;
+};
+
+}  // namespace
+
+struct gf_server {
+  gf_server_opts opts{};
+  std::mutex mu;
+  std::condition_variable cv_sched, cv_fit;
+  std::deque<std::shared_ptr<Req>> pending;
+  std::vector<std::shared_ptr<Req>> active;
+  std::map<uint64_t, std::shared_ptr<Req>> all;
+  std::atomic<bool> stop{false};
+  std::thread sched;
+  uint64_t next_ticket = 1;
+  size_t used_bytes = 0;
+  int64_t ticks = 0, launches = 0;
+  int peak = 0;
+  int64_t unfinished = 0;
+};
+
+static void fit_thread(gf_server* S, std::shared_ptr<Req> R) {
+  const size_t n = R->ctx->free_ids.size();
+  std::vector<double> x0(n), step(n), lo(n), hi(n);
+  for (size_t k = 0; k < n; ++k) {
+    const ParDef& p = R->ctx->pars[R->ctx->free_ids[k]];
+    x0[k] = p.value;
+    step[k] = p.step;
+    lo[k] = p.lo;
+    hi[k] = p.hi;
+  }
+  MinOpts mo;
+  if (R->has_opts) {
+    if (R->opts.tol > 0) mo.tol = R->opts.tol;
+    if (R->opts.max_calls > 0) mo.max_calls = R->opts.max_calls;
+    if (R->opts.up > 0) mo.up = R->opts.up;
+    mo.hesse = R->opts.hesse != 0;
+  }
+  const double tmo = S->opts.wait_timeout_s > 0 ? S->opts.wait_timeout_s : 60.0;
+  FGFun fg = [&](const std::vector<double>& x, double& f, std::vector<double>& g) -> int {
+    std::unique_lock<std::mutex> lk(S->mu);
+    R->theta = x;
+    R->want = true;
+    R->ready = false;
+    S->cv_sched.notify_all();
+    if (!S->cv_fit.wait_for(lk, std::chrono::duration<double>(tmo),
+                            [&] { return R->ready || S->stop.load(); }))
+      return GF_ETIMEOUT;
+    if (!R->ready) return GF_ETIMEOUT;
+    f = R->f;
+    g = R->grad;
+    return R->eval_rc;
+  };
+  MinResult m = minimise(fg, x0, step, lo, hi, mo);
+  std::lock_guard<std::mutex> lk(S->mu);
+  R->result = std::move(m);
+  R->nfree = (int)n;
+  R->done = true;
+  R->t_done = Clock::now();
+  S->cv_sched.notify_all();
+}
+
+static void scheduler(gf_server* S) {
+  cudaSetDevice(S->opts.device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (!S->stop.load()) {
+    // retire finished fits: free their device memory and slot
+    for (size_t i = 0; i < S->active.size();) {
+      auto R = S->active[i];
+      if (R->done) {
+        lk.unlock();
+        if (R->th.joinable()) R->th.join();
+        gf_destroy(R->ctx);
+        R->ctx = nullptr;
+        gf_dataset_destroy(R->ds);
+        R->ds = nullptr;
+        lk.lock();
+        S->used_bytes -= R->bytes;
+        S->active.erase(S->active.begin() + i);
+        S->unfinished--;
+      } else {
+        ++i;
+      }
+    }
+    // admit
+    while (!S->pending.empty() && (int)S->active.size() < S->opts.max_slots) {
+      auto R = S->pending.front();
+      if (S->used_bytes + R->bytes > S->opts.mem_budget && !S->active.empty()) break;
+      S->pending.pop_front();
+      lk.unlock();
+      int rc = gf_set_data(R->ctx, R->root, R->ds);
+      lk.lock();
+      if (rc != GF_OK) {
+        R->result.status = rc;
+        R->done = true;
+        R->t_done = Clock::now();
+        S->unfinished--;
+        continue;
+      }
+      S->used_bytes += R->bytes;
+      S->active.push_back(R);
+      S->peak = std::max(S->peak, (int)S->active.size());
+      R->th = std::thread(fit_thread, S, R);
+    }
+    // tick: every fit waiting for an evaluation
+    std::vector<std::shared_ptr<Req>> batch;
+    for (auto& R : S->active)
+      if (R->want && !R->ready) batch.push_back(R);
+    if (batch.empty()) {
+      S->cv_sched.wait_for(lk, std::chrono::milliseconds(2));
+      continue;
+    }
+    for (auto& R : batch) R->want = false;
+    lk.unlock();
+    int64_t nl = 0;
+    for (auto& R : batch) {
+      R->eval_rc = evaluate_async(R->ctx, R->theta.data(), true);
+      nl += R->ctx->last_launches;
+    }
+    for (auto& R : batch) {
+      R->grad.assign(R->ctx->free_ids.size(), 0.0);
+      if (R->eval_rc == GF_OK) R->eval_rc = evaluate_finish(R->ctx, &R->f, R->grad.data(), true);
+      else R->f = INFINITY;
+    }
+    lk.lock();
+    S->ticks++;
+    S->launches += nl;
+    for (auto& R : batch) R->ready = true;
+    S->cv_fit.notify_all();
+  }
+}
+
+extern "C" {
+
+int gf_server_create(const gf_server_opts* opts, gf_server** out) {
+  if (!opts || !out || opts->max_slots < 1) return GF_EINVAL;
+  gf_server* S = new gf_server();
+  S->opts = *opts;
+  if (S->opts.wait_timeout_s <= 0) S->opts.wait_timeout_s = 60.0;
+  S->sched = std::thread(scheduler, S);
+  *out = S;
+  return GF_OK;
+}
+
+int gf_server_submit(gf_server* S, gf_ctx* model, gf_dataset* ds, int root,
+                     const gf_fit_opts* opts, uint64_t* ticket) {
+  if (!S || !model || !ds || !ticket || ds->ctx != model) return GF_EINVAL;
+  if (root < 0 || root >= (int)model->nodes.size()) return GF_EINVAL;
+  if (model->precision != S->opts.precision) return GF_EINVAL;
+  auto R = std::make_shared<Req>();
+  R->ctx = model;
+  R->ds = ds;
+  R->root = root;
+  if (opts) {
+    R->opts = *opts;
+    R->has_opts = true;
+  }
+  R->bytes = device_bytes_for(model, root, ds->n);
+  R->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (R->bytes > S->opts.mem_budget) return GF_ENOMEM;
+  R->ticket = S->next_ticket++;
+  *ticket = R->ticket;
+  S->pending.push_back(R);
+  S->all[R->ticket] = R;
+  S->unfinished++;
+  S->cv_sched.notify_all();
+  return GF_OK;
+}
+
+int gf_server_nfree(gf_server* S, uint64_t ticket, int* n) {
+  if (!S || !n) return GF_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) return GF_EINVAL;
+  auto& R = it->second;
+  if (R->done) *n = R->nfree;
+  else *n = R->ctx ? nfree(R->ctx) : 0;
+  return GF_OK;
+}
+
+int gf_server_poll(gf_server* S, uint64_t ticket, gf_fit_result* res, double* latency_s,
+                   int* done) {
+  if (!S || !done) return GF_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) return GF_EINVAL;
+  auto& R = it->second;
+  *done = R->done ? 1 : 0;
+  if (!R->done) return GF_OK;
+  const MinResult& m = R->result;
+  if (res) {
+    res->nll = m.fval;
+    res->edm = m.edm;
+    res->n_calls = m.calls;
+    res->n_iter = m.iters;
+    res->status = m.status;
+    for (size_t k = 0; k < m.x.size(); ++k) {
+      if (res->theta) res->theta[k] = m.x[k];
+      if (res->err && k < m.err.size()) res->err[k] = m.err[k];
+    }
+    if (res->cov)
+      for (size_t k = 0; k < m.cov.size(); ++k) res->cov[k] = m.cov[k];
+  }
+  if (latency_s)
+    *latency_s = std::chrono::duration<double>(R->t_done - R->t_submit).count();
+  return GF_OK;
+}
+
+int gf_server_drain(gf_server* S) {
+  if (!S) return GF_EINVAL;
+  std::unique_lock<std::mutex> lk(S->mu);
+  const double tmo = S->opts.wait_timeout_s;
+  while (S->unfinished > 0) {
+    const int64_t before = S->unfinished;
+    if (!S->cv_sched.wait_for(lk, std::chrono::duration<double>(tmo),
+                              [&] { return S->unfinished < before || S->unfinished == 0; }))
+      return GF_ETIMEOUT;
+  }
+  return GF_OK;
+}
+
+int gf_server_stats(gf_server* S, int64_t* ticks, int64_t* launches, int* peak_slots) {
+  if (!S) return GF_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (ticks) *ticks = S->ticks;
+  if (launches) *launches = S->launches;
+  if (peak_slots) *peak_slots = S->peak;
+  return GF_OK;
+}
+
+int gf_server_destroy(gf_server* S) {
+  if (!S) return GF_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->cv_sched.notify_all();
+    S->cv_fit.notify_all();
+  }
+  if (S->sched.joinable()) S->sched.join();
+  for (auto& kv : S->all) {
+    auto& R = kv.second;
+    if (R->th.joinable()) R->th.join();
+    if (R->ctx) gf_destroy(R->ctx);
+    if (R->ds) gf_dataset_destroy(R->ds);
+    R->ctx = nullptr;
+    R->ds = nullptr;
+  }
+  delete S;
+  return GF_OK;
+}
+
+}  // extern "C"

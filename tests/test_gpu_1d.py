@@ -1,0 +1,204 @@
+"""Parity of the sm_103a 1D path with the FP64 oracle (configs 1 and 2, generic trees).
+
+Tolerances: 1e-12 relative per event on P (|log P_gpu - log P_orc| <= 1e-12), 1e-9
+relative on the total NLL, gradients 1e-9 relative to the gradient's scale."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1311_1753_gb300 import synth
+from tests import oracle_models as om
+from tests import product_models as pm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gf():
+    from paper_1311_1753_gb300 import gf as _gf
+    return _gf
+
+
+def _theta(values, free):
+    return np.array([values[i] for i in free], dtype=float)
+
+
+def _grad_close(g_gpu, g_orc, n, rel=1e-9):
+    scale = np.maximum(np.abs(g_orc), 1e-6 * n)
+    assert np.all(np.abs(g_gpu - g_orc) <= rel * scale + 1e-9 * np.abs(g_orc).max()), (g_gpu, g_orc)
+
+
+# ---- config 1: exponential ------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 33, 257, 100_000, 1_000_003])
+def test_config1_exponential_parity(gf, n):
+    x = synth.exp_events(max(n, 1), -1.0)[:n]
+    ctx, root, obs = pm.exp_model(gf, -2.0)
+    ctx.set_data(root, obs, [x])
+    m, free = om.exp_model(-2.0)
+    for alpha in (-1.0, -2.0, 0.3, 1e-6, -9.5):
+        th = np.array([alpha])
+        p = m.p.copy(); p[free] = th
+        lg = ctx.logpdf(th)
+        if n:
+            lo = m.logpdf([x], p)
+            assert np.max(np.abs(lg - lo)) <= 1e-12 * np.maximum(1, np.abs(lo)).max()
+        f, g = ctx.nll_grad(th)
+        fo, go = m.nll([x], p, grad=True)
+        assert abs(f - fo) <= 1e-9 * max(1.0, abs(fo))
+        assert abs(ctx.nll(th) - f) <= 1e-12 * max(1.0, abs(f))
+        if n:
+            assert abs(g[0] - go[0]) <= 1e-9 * max(abs(go[0]), n * 1e-6)
+
+
+def test_config1_deterministic_bitwise(gf):
+    x = synth.exp_events(100_000, -1.0)
+    ctx, root, obs = pm.exp_model(gf)
+    ctx.set_data(root, obs, [x])
+    vals = {ctx.nll(np.array([-1.1])) for _ in range(5)}
+    assert len(vals) == 1
+
+
+# ---- config 2: Voigtian + threshold --------------------------------------------------------------------
+def _voigt_data(n, seed=synth.SEED_VOIGT):
+    lo, hi = synth.VOIGT_RANGE
+    return synth.voigt_threshold_events(n, **synth.VOIGT_TRUTH, lo=lo, hi=hi, seed=seed)
+
+
+@pytest.mark.parametrize("n", [1, 33, 4099, 200_000])
+def test_config2_voigt_parity(gf, n):
+    x = _voigt_data(n)
+    ctx, root, obs = pm.voigt_model(gf)
+    ctx.set_data(root, obs, [x])
+    m, free = om.voigt_model()
+    base = m.p.copy()
+    for scale in ([1, 1, 1, 1, 1], [1.00002, 1.05, 0.9, 1.1, 0.95]):
+        p = base.copy()
+        p[free] = base[free] * np.array(scale)
+        th = p[free]
+        lo_ = m.logpdf([x], p)
+        lg = ctx.logpdf(th)
+        assert np.max(np.abs(lg - lo_)) <= 1e-12 * max(1.0, np.abs(lo_).max()), np.max(np.abs(lg - lo_))
+        f, g = ctx.nll_grad(th)
+        fo, go = m.nll([x], p, grad=True)
+        assert abs(f - fo) <= 1e-9 * abs(fo)
+        _grad_close(g, go[free], n)
+
+
+def test_config2_free_shape_parameters(gf):
+    # x0 and power free as well (fixed in the workload, free in general)
+    x = _voigt_data(20_000)
+    ctx, root, obs = pm.voigt_model(gf, free_shape=True, nbins=2000)
+    ctx.set_data(root, obs, [x])
+    m, _ = om.voigt_model(nbins=2000)
+    p = m.p.copy()
+    p[3] = synth.VOIGT_RANGE[0] - 2e-4
+    p[4] = 0.6
+    th = p.copy()  # every parameter is free here, in creation order
+    f, g = ctx.nll_grad(th)
+    fo, go = m.nll([x], p, grad=True)
+    assert abs(f - fo) <= 1e-9 * abs(fo)
+    _grad_close(g, go, len(x), rel=1e-8)
+
+
+def test_config2_full_size_sampled(gf):
+    """10^7 events in the benchmark's launch shape: total NLL against the oracle's full
+    sum, and sampled per-event values."""
+    x = _voigt_data(10_000_000)
+    ctx, root, obs = pm.voigt_model(gf)
+    ctx.set_data(root, obs, [x])
+    m, free = om.voigt_model()
+    th = m.p[free]
+    f = ctx.nll(th)
+    fo = m.nll([x], m.p)
+    assert abs(f - fo) <= 1e-9 * abs(fo)
+    lg = ctx.logpdf(th)
+    idx = np.random.default_rng(0).choice(len(x), 20_000, replace=False)
+    lo_ = m.logpdf([x[idx]], m.p)
+    assert np.max(np.abs(lg[idx] - lo_)) <= 1e-12 * np.abs(lo_).max()
+
+
+# ---- generic trees (Sec. 3: sums, products, nesting) ----------------------------------------------------
+def _tree_models(gf):
+    """Depth-3 tree over two observables: PROD(ADD(gauss, poly, exp), ADD(exp, gauss))."""
+    ctx = gf.Context()
+    m = oracle.Model1D([(-1.0, 2.0), (0.0, 3.0)])
+    x = ctx.observable("x", -1.0, 2.0)
+    y = ctx.observable("y", 0.0, 3.0)
+    vals = [0.4, 0.6, 1.0, 0.3, 0.1, -0.7, 0.5, 0.2, -0.8, 1.5, 0.4, 0.35]
+    names = ["mu", "s", "a0", "a1", "a2", "ax", "f1", "f2", "ay", "muy", "sy", "fy"]
+    P = [ctx.parameter(nm, v, 0.01) for nm, v in zip(names, vals)]
+    O = [m.param(v) for v in vals]
+    g = ctx.gauss(x, P[0], P[1]); og = m.gauss(0, O[0], O[1])
+    po = ctx.poly(x, [P[2], P[3], P[4]]); opo = m.poly(0, [O[2], O[3], O[4]])
+    ex = ctx.exp(x, P[5]); oex = m.exp(0, O[5])
+    a1 = ctx.add([g, po, ex], [P[6], P[7]]); oa1 = m.add([og, opo, oex], [O[6], O[7]])
+    ey = ctx.exp(y, P[8]); oey = m.exp(1, O[8])
+    gy = ctx.gauss(y, P[9], P[10]); ogy = m.gauss(1, O[9], O[10])
+    a2 = ctx.add([ey, gy], [P[11]]); oa2 = m.add([oey, ogy], [O[11]])
+    root = ctx.prod([a1, a2]); m.prod([oa1, oa2])
+    return ctx, root, [x, y], m
+
+
+@pytest.mark.parametrize("n", [7, 5001])
+def test_nested_tree_parity(gf, n):
+    ctx, root, obs, m = _tree_models(gf)
+    rng = np.random.default_rng(3)
+    xs = rng.uniform(-1, 2, n)
+    ys = rng.uniform(0, 3, n)
+    ctx.set_data(root, obs, [xs, ys])
+    p = m.p.copy()
+    lo_ = m.logpdf([xs, ys], p)
+    lg = ctx.logpdf(p)
+    assert np.max(np.abs(lg - lo_)) <= 1e-12 * max(1.0, np.abs(lo_).max())
+    f, g = ctx.nll_grad(p)
+    fo, go = m.nll([xs, ys], p, grad=True)
+    assert abs(f - fo) <= 1e-9 * abs(fo)
+    _grad_close(g, go, n)
+
+
+def test_product_of_exponentials_listing2(gf):
+    ctx = gf.Context()
+    x = ctx.observable("x", 0.0, 5.0)
+    y = ctx.observable("y", 0.0, 5.0)
+    ax = ctx.parameter("ax", -2.4, 0.1, -10, 10)
+    ay = ctx.parameter("ay", -1.1, 0.1, -10, 10)
+    root = ctx.prod([ctx.exp(x, ax), ctx.exp(y, ay)])
+    xs = synth.exp_events(1000, -2.4, 0, 5, seed=1)
+    ys = synth.exp_events(1000, -1.1, 0, 5, seed=2)
+    ctx.set_data(root, [x, y], [xs, ys])
+    m = oracle.Model1D([(0.0, 5.0), (0.0, 5.0)])
+    m.prod([m.exp(0, m.param(-2.4)), m.exp(1, m.param(-1.1))])
+    f, g = ctx.nll_grad(np.array([-2.4, -1.1]))
+    fo, go = m.nll([xs, ys], grad=True)
+    assert abs(f - fo) <= 1e-9 * abs(fo)
+    _grad_close(g, go, 1000)
+
+
+# ---- edge cases and errors --------------------------------------------------------------------------------
+def test_nonfinite_is_reported(gf):
+    # a polynomial that goes negative inside the range -> log P undefined
+    ctx = gf.Context()
+    x = ctx.observable("x", -1.0, 1.0)
+    a0 = ctx.parameter("a0", 0.1, 0.01)
+    a1 = ctx.parameter("a1", 1.0, 0.01)
+    root = ctx.poly(x, [a0, a1])
+    ctx.set_data(root, [x], [np.array([-0.9, 0.5, 0.2])])
+    assert ctx.nll(np.array([0.1, 1.0])) == float("inf")
+
+
+def test_out_of_range_events_rejected(gf):
+    ctx, root, obs = pm.exp_model(gf)
+    with pytest.raises(gf.GFError):
+        ctx.set_data(root, obs, [np.array([1.0, 11.0])])
+
+
+def test_device_columns_from_torch(gf):
+    torch = pytest.importorskip("torch")
+    x = synth.exp_events(10_001, -1.0)
+    t = torch.tensor(x, dtype=torch.float64, device="cuda")
+    ctx, root, obs = pm.exp_model(gf)
+    ctx.set_data_device(root, obs, len(x), [t.data_ptr()], keep=t)
+    m, free = om.exp_model(-1.3)
+    assert abs(ctx.nll(np.array([-1.3])) - m.nll([x])) <= 1e-9 * abs(m.nll([x]))

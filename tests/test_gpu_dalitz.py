@@ -1,0 +1,138 @@
+"""Parity of the sm_103a Dalitz path with the FP64 oracle (configs 3 and 4).
+
+Per event: |P_gpu/P_orc - 1| <= 1e-12 kappa_i with the interference condition number
+kappa_i = (|a_NR| + sum_r |c_r A_r|)^2 / |A|^2.  Total NLL 1e-9 relative; gradients
+1e-9 relative to their scale.  FP32 (mixed) results: errors are measured and bounded
+loosely (1e-4 per event relative, 1e-6 relative on NLL)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_1311_1753_gb300 import synth
+from tests import oracle_models as om
+from tests import product_models as pm
+
+pytestmark = pytest.mark.gpu
+
+SPEC = om.load_dalitz_spec()
+
+
+@pytest.fixture(scope="module")
+def gf():
+    from paper_1311_1753_gb300 import gf as _gf
+    return _gf
+
+
+_cache = {}
+
+
+def _events(n, seed=synth.SEED_DALITZ_EVENTS):
+    key = (n, seed)
+    if key not in _cache:
+        d = om.dalitz_from_spec(SPEC)
+        _cache[key] = synth.dalitz_events(n, om.dalitz_accept(d, SPEC["envelope"]), seed)
+    return _cache[key]
+
+
+def _theta_all(spec):
+    out = []
+    for r in spec["resonances"]:
+        out += [r["m0"], r["g0"], r["re"], r["im"]]
+    return np.array(out)
+
+
+def _free_idx(nres, free_shapes, fixed_last=True):
+    idx = []
+    for r in range(nres):
+        if free_shapes and not (fixed_last and r == nres - 1):
+            idx += [4 * r, 4 * r + 1]
+        idx += [4 * r + 2, 4 * r + 3]
+    return idx
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 5000])
+@pytest.mark.parametrize("free_shapes", [False, True])
+def test_dalitz_fp64_parity(gf, n, free_shapes):
+    s12, s13 = _events(5000)
+    s12, s13 = s12[:n], s13[:n]
+    nres = len(SPEC["resonances"])
+    ctx, root, obs = pm.dalitz_model(gf, SPEC, free_shapes=free_shapes)
+    ctx.set_data(root, obs, [s12, s13])
+    d = om.dalitz_from_spec(SPEC)
+    p = _theta_all(SPEC)
+    free = _free_idx(nres, free_shapes)
+    rng = np.random.default_rng(11)
+    for trial in range(2):
+        q = p.copy()
+        if trial:
+            q[free] *= 1 + 0.03 * rng.standard_normal(len(free))
+        th = q[free]
+        lg = ctx.logpdf(th)
+        P, kap = d.intensity(s12, s13, q, kappa=True)
+        assert np.all(np.abs(np.exp(lg - np.log(P)) - 1) <= 1e-12 * kap), \
+            np.max(np.abs(np.exp(lg - np.log(P)) - 1) / kap)
+        f, g = ctx.nll_grad(th)
+        fo, go = d.nll(s12, s13, q, grad=True)
+        assert abs(f - fo) <= 1e-9 * max(1.0, abs(fo)), (f, fo)
+        go = go[free]
+        scale = np.maximum(np.abs(go), 1e-6 * max(n, 1))
+        assert np.all(np.abs(g - go) <= 1e-9 * scale + 1e-9 * np.abs(go).max()), (g, go)
+
+
+def test_dalitz_gram_matches_oracle_norm(gf):
+    nres = len(SPEC["resonances"])
+    ctx, root, obs = pm.dalitz_model(gf, SPEC)
+    s12, s13 = _events(100)
+    ctx.set_data(root, obs, [s12, s13])
+    th = _theta_all(SPEC)[_free_idx(nres, False)]
+    G = ctx.dalitz_gram(th, nres)
+    assert np.allclose(G, G.conj().T, rtol=0, atol=1e-12 * np.abs(G).max())
+    c = np.concatenate([[1.0], th[0::2] + 1j * th[1::2]])
+    N = (c.conj() @ G @ c).real
+    d = om.dalitz_from_spec(SPEC)
+    No, cnt = d.norm()
+    assert cnt == 155812
+    assert abs(N / No - 1) < 1e-12
+    # diagonal = per-resonance integrals of |A_r|^2 (fit-fraction denominators)
+    for r, res in enumerate(SPEC["resonances"]):
+        assert abs(G[r + 1, r + 1].real / res["G_rr"] - 1) < 1e-12
+
+
+def test_dalitz_full_size_sampled(gf):
+    """10^6 events (config 3) in the benchmark's launch shape: NLL against the oracle's
+    full sum, and sampled per-event values."""
+    nres = len(SPEC["resonances"])
+    s12, s13 = _events(1_000_000)
+    ctx, root, obs = pm.dalitz_model(gf, SPEC)
+    ctx.set_data(root, obs, [s12, s13])
+    d = om.dalitz_from_spec(SPEC)
+    p = _theta_all(SPEC)
+    th = p[_free_idx(nres, False)]
+    f = ctx.nll(th)
+    fo = d.nll(s12, s13, p)
+    assert abs(f - fo) <= 1e-9 * abs(fo)
+    lg = ctx.logpdf(th)
+    idx = np.random.default_rng(1).choice(len(s12), 5000, replace=False)
+    P, kap = d.intensity(s12[idx], s13[idx], p, kappa=True)
+    assert np.all(np.abs(np.exp(lg[idx] - np.log(P)) - 1) <= 1e-12 * kap)
+
+
+def test_dalitz_mixed_precision_errors(gf):
+    nres = len(SPEC["resonances"])
+    s12, s13 = _events(5000)
+    d = om.dalitz_from_spec(SPEC)
+    p = _theta_all(SPEC)
+    free = _free_idx(nres, True)
+    ctx, root, obs = pm.dalitz_model(gf, SPEC, precision=gf.GF_MIXED, free_shapes=True)
+    ctx.set_data(root, obs, [s12, s13])
+    th = p[free]
+    lg = ctx.logpdf(th)
+    P = d.intensity(s12, s13, p)
+    rel = np.abs(np.exp(lg - np.log(P)) - 1)
+    assert np.median(rel) < 1e-5 and np.quantile(rel, 0.99) < 1e-3
+    f, g = ctx.nll_grad(th)
+    fo, go = d.nll(s12, s13, p, grad=True)
+    assert abs(f - fo) <= 1e-6 * abs(fo)
+    go = go[free]
+    assert np.max(np.abs(g - go)) <= 1e-3 * np.abs(go).max() + 1e-2
