@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Benchmark of the unbinned-likelihood hot path on GB300.
+
+Headline workload (default): the 1D composite fit (Voigtian + threshold background on
+the D*+ - D0 mass-difference range, 10^7 FP64 events, 5 free parameters, 2 x 10,000-bin
+normalisation grids).  One step = one NLL + gradient evaluation (theta upload, grid
+normalisation, event pass with the fused gradient, deterministic reduction, result
+download), as a minimiser call makes it.  Metric: events x evaluations per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload voigt|exp|dalitz|dalitz-mixed] [--no-extra] [--fits] [--serve]
+
+N > 1 runs under torchrun: every rank evaluates its own data set (independent problems,
+weak scaling, no data-path collective); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1311_1753_gb300 import synth  # noqa: E402
+
+# Peaks: HBM from the driver's measurement; FP64 from the unit counts and the maximum
+# clock (152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz); FP32 likewise (x 128).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# Algorithmic FP64 flops per event of the config-2 event pass with the fused gradient,
+# counted from the source (FMA = 2, add/mul = 1; each exp, log, sqrt or division = 1):
+# Faddeeva series N = 40 (Horner 39 x 7 + 32 setup) = 305; Voigt value and 3 partials
+# 31; threshold value and partial 9; two fraction scalings with 5-wide gradients 14;
+# sum and gradient sum 6; log P, 1/P and the 5 gradient accumulations 12.
+FLOPS_PER_EVENT = {"voigt_grad": 377, "voigt": 318}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader",
+                                       "-i", str(index), "-lms", "200"],
+                                      stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return None
+        sm = [float(r[1].split()[0]) for r in rows if r[1].split()[0].replace(".", "").isdigit()]
+        mx = [float(r[2].split()[0]) for r in rows if r[2].split()[0].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---- workloads ------------------------------------------------------------------------------
+def voigt_workload(gf, n, seed, precision):
+    lo, hi = synth.VOIGT_RANGE
+    x = synth.voigt_threshold_events(n, **synth.VOIGT_TRUTH, lo=lo, hi=hi, seed=seed)
+    t = synth.VOIGT_TRUTH
+    ctx = gf.Context(0, precision)
+    xo = ctx.observable("dm", lo, hi)
+    mu = ctx.parameter("mu", t["mu"], 1e-5, 0.143, 0.148)
+    s = ctx.parameter("sigma", t["sigma"], 1e-5, 1e-5, 2e-3)
+    w = ctx.parameter("width", t["width"], 1e-5, 1e-6, 1e-3)
+    x0 = ctx.parameter("x0", t["x0"], 1e-4, fixed=True)
+    pw = ctx.parameter("power", t["power"], 0.01, fixed=True)
+    c = ctx.parameter("c", t["c"], 0.5, 0.0, 200.0)
+    f = ctx.parameter("frac", t["frac"], 0.01, 0.0, 1.0)
+    root = ctx.add([ctx.voigt(xo, mu, s, w), ctx.threshold(xo, x0, pw, c)], [f])
+    ctx.set_data(root, [xo], [x])
+    theta = np.array([t["mu"], t["sigma"], t["width"], t["c"], t["frac"]])
+    return ctx, root, [xo], [x], theta
+
+
+def exp_workload(gf, n, seed, precision):
+    x = synth.exp_events(n, -1.0, seed=seed)
+    ctx = gf.Context(0, precision)
+    xo = ctx.observable("x", 0.0, 10.0)
+    a = ctx.parameter("alpha", -2.0, 0.1, -10.0, 10.0)
+    root = ctx.exp(xo, a)
+    ctx.set_data(root, [xo], [x])
+    return ctx, root, [xo], [x], np.array([-1.0])
+
+
+def dalitz_spec():
+    with open(os.path.join(ROOT, "tests", "golden", f"dalitz_model_{synth.SEED_DALITZ_MODEL}.json")) as fh:
+        return json.load(fh)
+
+
+def dalitz_context(gf, spec, precision, free_shapes):
+    ctx = gf.Context(0, precision)
+    o12 = ctx.observable("s12", 0.0, 4.0)
+    o13 = ctx.observable("s13", 0.0, 4.0)
+    res, theta = [], []
+    nres = len(spec["resonances"])
+    for i, r in enumerate(spec["resonances"]):
+        shape_free = free_shapes and i != nres - 1
+        m0 = ctx.parameter(f"m0_{i}", r["m0"], 0.005, 0.4, 1.75, fixed=not shape_free)
+        g0 = ctx.parameter(f"g0_{i}", r["g0"], 0.005, 0.01, 0.6, fixed=not shape_free)
+        re = ctx.parameter(f"re_{i}", r["re"], 0.01)
+        im = ctx.parameter(f"im_{i}", r["im"], 0.01)
+        res.append(dict(channel=r["channel"], spin=r["spin"], mass=m0, width=g0, re=re, im=im))
+        theta += ([r["m0"], r["g0"]] if shape_free else []) + [r["re"], r["im"]]
+    root = ctx.dalitz(o12, o13, spec["kin"], res)
+    return ctx, root, [o12, o13], np.array(theta)
+
+
+def dalitz_events_gpu(gf, spec, n, seed):
+    """Accept-reject with the library's own density (normalised log P on the device)."""
+    gctx, groot, gobs, th = dalitz_context(gf, spec, gf.GF_FP64, False)
+    nres = len(spec["resonances"])
+
+    def accept(s12, s13, u):
+        ins = gctx.dalitz_inside(groot, s12, s13)
+        out = np.zeros(len(s12), dtype=bool)
+        idx = np.nonzero(ins)[0]
+        if len(idx):
+            gctx.set_data(groot, gobs, [s12[idx], s13[idx]])
+            lp = gctx.logpdf(th)
+            Gm = gctx.dalitz_gram(th, nres)
+            c = np.concatenate([[1.0], th[0::2] + 1j * th[1::2]])
+            N = float((c.conj() @ Gm @ c).real)
+            out[idx] = u[idx] * spec["envelope"] < np.exp(lp) * N
+        return out
+
+    s12, s13 = synth.dalitz_events(n, accept, seed, batch=1 << 22)
+    gctx.close()
+    return s12, s13
+
+
+def dalitz_workload(gf, n, seed, precision, free_shapes, data=None):
+    spec = dalitz_spec()
+    s12, s13 = data if data is not None else dalitz_events_gpu(gf, spec, n, seed)
+    ctx, root, obs, th = dalitz_context(gf, spec, precision, free_shapes)
+    ctx.set_data(root, obs, [s12, s13])
+    return ctx, root, obs, [s12, s13], th
+
+
+# ---- timing ---------------------------------------------------------------------------------------
+def time_steps(torch, ctx, thetas, steps, warmup, grad=True, flush=True):
+    """Per-step device time (CUDA events on the context's stream), L2 flushed between steps
+    with a 256 MB write; also the event-pass kernel's own time from the library."""
+    st = torch.cuda.Stream()
+    ctx.set_stream(st.cuda_stream)
+    buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for k in range(warmup):
+        (ctx.nll_grad if grad else ctx.nll)(thetas[k % len(thetas)])
+    torch.cuda.synchronize()
+    kern, launches, vals = [], 0, []
+    t0 = time.perf_counter()
+    for k in range(steps):
+        if flush:
+            with torch.cuda.stream(st):
+                buf.zero_()
+        ev[k][0].record(st)
+        r = (ctx.nll_grad if grad else ctx.nll)(thetas[k % len(thetas)])
+        ev[k][1].record(st)
+        vals.append(r[0] if grad else r)
+        tot, sk = ctx.last_eval_times()
+        kern.append(sk)
+        launches += ctx.last_eval_stats()[1]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ctx.set_stream(0)
+    return dict(step_ms=ms, kernel_ms=kern, launches=launches, wall_s=wall, values=vals)
+
+
+def e2e_steps(torch, ctx, cols, thetas, steps, warmup):
+    """Public-API step with host buffers: the step's events from pinned host memory
+    (gf_update_data), then NLL + gradient back to the host; wall clock per step."""
+    pinned = []
+    for shift in (0, 1):
+        p = [torch.from_numpy(np.ascontiguousarray(np.roll(c, shift))).pin_memory() for c in cols]
+        pinned.append(p)
+    n = len(cols[0])
+    for k in range(warmup):
+        ctx.update_data_ptrs(n, [t.data_ptr() for t in pinned[k % 2]])
+        ctx.nll_grad(thetas[k % len(thetas)])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        ctx.update_data_ptrs(n, [t.data_ptr() for t in pinned[k % 2]])
+        ctx.nll_grad(thetas[k % len(thetas)])
+    wall = time.perf_counter() - t0
+    return wall, 8 * n * len(cols)
+
+
+# ---- the oracle on the host cores ------------------------------------------------------------------
+def oracle_voigt_rate(n_sample, min_seconds=10.0, max_reps=50):
+    import oracle  # CPU baseline only
+    lo, hi = synth.VOIGT_RANGE
+    x = synth.voigt_threshold_events(n_sample, **synth.VOIGT_TRUTH, lo=lo, hi=hi)
+    t = synth.VOIGT_TRUTH
+    m = oracle.Model1D([synth.VOIGT_RANGE])
+    mu, s, w = m.param(t["mu"]), m.param(t["sigma"]), m.param(t["width"])
+    x0, pw, c, f = m.param(t["x0"]), m.param(t["power"]), m.param(t["c"]), m.param(t["frac"])
+    m.add([m.voigt(0, mu, s, w), m.threshold(0, x0, pw, c)], [f])
+    reps, t0 = 0, time.perf_counter()
+    while reps < max_reps:
+        m.nll([x], grad=True)
+        reps += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    el = time.perf_counter() - t0
+    return n_sample * reps / el, reps, el
+
+
+# ---- main -----------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="voigt",
+                    choices=["voigt", "exp", "dalitz", "dalitz-mixed"])
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--fits", action="store_true")
+    ap.add_argument("--serve", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    metric = "NLL+gradient evaluations: events x evals/s (1D composite, FP64)"
+    unit = "events*evals/s"
+
+    if args.impl == "reference":
+        # The reference arm is the FP64 CPU oracle on the host cores, on a bounded sample
+        # of the same workload per step; rank 0 only.
+        if rank != 0:
+            return 0
+        S = 200_000
+        rate_reps = []
+        for k in range(args.warmup + args.steps):
+            r, reps, el = oracle_voigt_rate(S, min_seconds=0.0, max_reps=1)
+            if k >= args.warmup:
+                rate_reps.append(el)
+        tot = sum(rate_reps)
+        value = S * args.steps / tot
+        out = {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": 0,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic",
+               "config": {"workload": "1D composite Voigtian + threshold, FP64, NLL+grad",
+                          "events_per_step": S, "full_workload_events": 10_000_000},
+               "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
+                                "sample": f"{S} events of the 10^7-event workload per step"},
+               "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return 0
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1311_1753_gb300 import gf
+
+    peaks = _peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    seed = synth.SEED_VOIGT + 1000 * rank
+
+    if args.workload == "voigt":
+        n = 10_000_000
+        ctx, root, obs, cols, th0 = voigt_workload(gf, n, seed, gf.GF_FP64)
+        flops_ev = FLOPS_PER_EVENT["voigt_grad"]
+        wl = "1D composite: Voigtian (mu,sigma,Gamma) + threshold (c) with fraction f, 10^7 FP64 events, 2 x 10,000-bin grid normalisation"
+    elif args.workload == "exp":
+        n = 100_000
+        ctx, root, obs, cols, th0 = exp_workload(gf, n, synth.SEED_EXP + rank, gf.GF_FP64)
+        flops_ev = 4
+        wl = "truncated exponential, 10^5 FP64 events, analytic normalisation"
+        metric = "NLL+gradient evaluations: events x evals/s (exponential, FP64)"
+    else:
+        mixed = args.workload == "dalitz-mixed"
+        n = 5_000_000 if mixed else 1_000_000
+        ctx, root, obs, cols, th0 = dalitz_workload(
+            gf, n, synth.SEED_DALITZ_BIG if mixed else synth.SEED_DALITZ_EVENTS,
+            gf.GF_MIXED if mixed else gf.GF_FP64, mixed)
+        flops_ev = None
+        wl = ("Dalitz 8 BW resonances, 5x10^6 events, 30 free, FP32 amplitudes + FP64 sums"
+              if mixed else "Dalitz 8 BW resonances, 10^6 FP64 events, 16 free coefficients")
+        metric = f"NLL+gradient evaluations: events x evals/s ({args.workload})"
+
+    rng = np.random.default_rng(5)
+    thetas = [th0 * (1 + 1e-4 * rng.standard_normal(len(th0))) for _ in range(8)]
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    res = time_steps(torch, ctx, thetas, args.steps, args.warmup)
+    clocks = clk.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    dev_s = sum(res["step_ms"]) / 1e3
+    if world > 1:
+        t = torch.tensor([dev_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dev_s = float(t.item())
+    value = n * args.steps * world / dev_s
+    kern_s = float(np.mean(res["kernel_ms"])) / 1e3
+
+    roofline = None
+    if flops_ev is not None:
+        ach = flops_ev * n / kern_s / 1e12
+        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                    "kernel": "k_events_1d<grad> (FP64 pipe)",
+                    "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts and max clock)",
+                    "kernel_ms": kern_s * 1e3,
+                    "algorithmic_flops_per_event": flops_ev,
+                    "hbm_frac_of_measured": (8 * n / kern_s / 1e9) / hbm_peak}
+
+    # end-to-end through the C ABI with host buffers
+    e2e = None
+    try:
+        wall, h2d = e2e_steps(torch, ctx, cols, thetas, max(3, args.steps // 2), 2)
+        ksteps = max(3, args.steps // 2)
+        e2e = {"value": n * ksteps / wall, "unit": unit,
+               "h2d_bytes_per_step": h2d + 8 * len(th0) + 0,
+               "d2h_bytes_per_step": 8 * (1 + len(th0)) + 4}
+    except Exception as e:  # report, do not hide
+        e2e = {"error": repr(e)[:200]}
+
+    extra = {}
+    if not args.no_extra and args.workload == "voigt" and rank == 0:
+        extra = run_extra(torch, gf, args)
+
+    cpu = None
+    if rank == 0 and world == 1:
+        rate, reps, el = oracle_voigt_rate(200_000, min_seconds=args.cpu_seconds)
+        cpu = {"value": rate, "unit": unit, "cores": 1, "kind": "oracle",
+               "sample": f"{reps} NLL+gradient evaluations over 200,000 events of the same workload ({el:.1f} s)"}
+
+    if rank == 0:
+        out = {"metric": metric, "value": value, "unit": unit, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": wl, "events": n, "free_params": len(th0),
+                          "l2": "flushed between steps (256 MB write)",
+                          "parallelism": f"replicas x{world} (independent data sets)"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+               "gpu_launches": res["launches"], "wall_s_timed_loop": res["wall_s"]}
+        if extra:
+            out["extra"] = extra
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_extra(torch, gf, args):
+    """Secondary measurements: configs 1, 3, 4 evaluation rates (and, on request, fit
+    times and the serving study)."""
+    out = {}
+    K = max(5, args.steps)
+    # config 1
+    ctx, root, obs, cols, th = exp_workload(gf, 100_000, synth.SEED_EXP, gf.GF_FP64)
+    r = time_steps(torch, ctx, [th * (1 + 1e-3 * k) for k in range(4)], 50, 5, flush=False)
+    out["config1_exp_1e5"] = {"events_x_evals_per_s": 1e5 * 50 / (sum(r["step_ms"]) / 1e3),
+                              "us_per_eval": 1e3 * float(np.mean(r["step_ms"])),
+                              "kernel_us": 1e3 * float(np.mean(r["kernel_ms"]))}
+    ctx.close()
+    # config 3 (FP64, 1e6 events, cached per-event amplitudes, Gram normalisation)
+    spec = dalitz_spec()
+    data = dalitz_events_gpu(gf, spec, 1_000_000, synth.SEED_DALITZ_EVENTS)
+    ctx, root, obs, cols, th = dalitz_workload(gf, 1_000_000, 0, gf.GF_FP64, False, data)
+    rng = np.random.default_rng(2)
+    ths = [th * (1 + 1e-3 * rng.standard_normal(len(th))) for _ in range(4)]
+    r = time_steps(torch, ctx, ths, K, 3)
+    out["config3_dalitz_fp64_1e6"] = {
+        "events_x_evals_per_s": 1e6 * K / (sum(r["step_ms"]) / 1e3),
+        "ms_per_eval": float(np.mean(r["step_ms"])), "kernel_ms": float(np.mean(r["kernel_ms"]))}
+    ctx.close()
+    # config 4 data: 5e6 events; mixed vs FP64 on the same data, 30 free parameters
+    data5 = dalitz_events_gpu(gf, spec, 5_000_000, synth.SEED_DALITZ_BIG)
+    for prec, name in ((gf.GF_MIXED, "mixed"), (gf.GF_FP64, "fp64")):
+        ctx, root, obs, cols, th = dalitz_workload(gf, 5_000_000, 0, prec, True, data5)
+        ths = [th * (1 + 1e-3 * rng.standard_normal(len(th))) for _ in range(4)]
+        r = time_steps(torch, ctx, ths, K, 3)
+        out[f"config4_dalitz_{name}_5e6"] = {
+            "events_x_evals_per_s": 5e6 * K / (sum(r["step_ms"]) / 1e3),
+            "ms_per_eval": float(np.mean(r["step_ms"])),
+            "kernel_ms": float(np.mean(r["kernel_ms"])), "free_params": len(th)}
+        ctx.close()
+    m, f = out["config4_dalitz_mixed_5e6"], out["config4_dalitz_fp64_5e6"]
+    out["config4_mixed_over_fp64_speedup"] = f["ms_per_eval"] / m["ms_per_eval"]
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -151,6 +151,13 @@ int gf_set_data(gf_ctx* ctx, int root, const gf_dataset* ds);
 int gf_set_data_device(gf_ctx* ctx, int root, int nobs, const int* obs, int64_t n,
                        const double* const* dev_cols);
 
+/* Replace the events of the loaded data set (same n, same observables) by new host
+ * columns (cols[k] has n doubles; pinned memory makes the copy asynchronous).  The copy
+ * is queued on the context's stream; the events are checked on the device against the
+ * observable ranges (Dalitz: the kinematic region) and the next evaluation returns
+ * GF_EINVAL if any is outside.  The per-event caches are rebuilt at that evaluation. */
+int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols);
+
 /* ---- evaluation (Sec. 2: evaluate and metric, summed over events) ------------------ */
 /* NLL(theta) = -sum_i log P(x_i; theta) with P normalised, at theta = the free
  * parameters in gf_free_params order (external units).  Blocking: returns when the
@@ -221,6 +228,9 @@ int gf_server_destroy(gf_server* srv);
 /* Device-side time of the last evaluation's kernels (ms, CUDA events) and the number of
  * kernel launches it made. */
 int gf_last_eval_stats(gf_ctx* ctx, double* kernel_ms, int* launches);
+/* Device time (ms) of the last evaluation: all its kernels, and the final stream kernel
+ * alone (the event pass, CUDA events on the context's stream). */
+int gf_last_eval_times(gf_ctx* ctx, double* total_ms, double* stream_ms);
 
 #ifdef __cplusplus
 }

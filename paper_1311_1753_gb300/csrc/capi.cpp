@@ -128,6 +128,8 @@ static void free_dev(gf_ctx* ctx) {
   if (d.h_result) cudaFreeHost(d.h_result);
   if (d.ev0) cudaEventDestroy(d.ev0);
   if (d.ev1) cudaEventDestroy(d.ev1);
+  if (d.evm) cudaEventDestroy(d.evm);
+  cudaFree(d.flag);
   d = DevState();
 }
 
@@ -747,6 +749,11 @@ static int alloc_work(gf_ctx* ctx) {
   if (!d.h_result) CK(cudaMallocHost(&d.h_result, sizeof(double) * 64));
   if (!d.ev0) CK(cudaEventCreate(&d.ev0));
   if (!d.ev1) CK(cudaEventCreate(&d.ev1));
+  if (!d.evm) CK(cudaEventCreate(&d.evm));
+  if (!d.flag) {
+    CK(cudaMalloc(&d.flag, sizeof(int)));
+    CK(cudaMemset(d.flag, 0, sizeof(int)));
+  }
   return GF_OK;
 }
 
@@ -808,18 +815,8 @@ static int finish_set_data(gf_ctx* ctx) {
       CK(cudaMalloc(&d.ev_cache, (size_t)ncached * d.n * (mixed ? 8 : 16)));
     if (mixed && d.n > 0) {
       CK(cudaMalloc(&d.fcols, 3 * (size_t)d.n * sizeof(float)));
-      // s12, s13, s23 in FP32 (s23 formed in FP64 first)
-      std::vector<float> tmp;  // converted on the host once at set-up
-      std::vector<double> a(d.n), b(d.n);
-      CK(cudaMemcpy(a.data(), d.cols[0], 8 * d.n, cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(b.data(), d.cols[1], 8 * d.n, cudaMemcpyDeviceToHost));
-      tmp.resize(3 * (size_t)d.n);
-      for (int64_t i = 0; i < d.n; ++i) {
-        tmp[i] = (float)a[i];
-        tmp[d.n + i] = (float)b[i];
-        tmp[2 * d.n + i] = (float)(D.sum_m2 - a[i] - b[i]);
-      }
-      CK(cudaMemcpy(d.fcols, tmp.data(), tmp.size() * 4, cudaMemcpyHostToDevice));
+      CK(launch_dalitz_fcols(D, d.cols[0], d.cols[1], d.n, d.fcols, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
     }
     d.ev_m0.assign(D.nres, NAN);
     d.ev_g0.assign(D.nres, NAN);
@@ -1021,6 +1018,7 @@ int evaluate_async(gf_ctx* ctx, const double* theta, bool grad) {
                                    ctx->stream));
       launches++;
     }
+    CK(cudaEventRecord(d.evm, ctx->stream));
     CK(launch_dalitz_events(ctx->dplan, mixed, grad, false, mode, d.theta, B, d.nblocks,
                             ctx->stream));
     launches++;
@@ -1033,6 +1031,7 @@ int evaluate_async(gf_ctx* ctx, const double* theta, bool grad) {
     }
     Cols cols{};
     for (int k = 0; k < d.nobs; ++k) cols.c[k] = d.cols[k];
+    CK(cudaEventRecord(d.evm, ctx->stream));
     CK(launch_events_1d(ctx->prog, W, cols, d.n, d.theta, d.derived, d.partials, d.counters,
                         d.result, nullptr, grad, false, ctx->has_grid ? 0 : 1, d.nblocks,
                         ctx->stream));
@@ -1040,6 +1039,9 @@ int evaluate_async(gf_ctx* ctx, const double* theta, bool grad) {
   }
   CK(cudaEventRecord(d.ev1, ctx->stream));
   CK(cudaMemcpyAsync(d.h_result, d.result, sizeof(double) * (1 + (grad ? nf : 0)),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  // data-check flag rides along in the last pinned slot
+  CK(cudaMemcpyAsync(reinterpret_cast<int*>(d.h_result + 63), d.flag, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->stream));
   ctx->last_launches = launches;
   return GF_OK;
@@ -1050,6 +1052,14 @@ int evaluate_finish(gf_ctx* ctx, double* nll, double* grad, bool grad_wanted) {
   CK(cudaStreamSynchronize(ctx->stream));
   float ms = 0.f;
   if (cudaEventElapsedTime(&ms, d.ev0, d.ev1) == cudaSuccess) ctx->last_ms = ms;
+  if (cudaEventElapsedTime(&ms, d.evm, d.ev1) == cudaSuccess) ctx->last_stream_ms = ms;
+  const int bad = *reinterpret_cast<const int*>(d.h_result + 63);
+  if (bad) {
+    *reinterpret_cast<int*>(d.h_result + 63) = 0;
+    CK(cudaMemset(d.flag, 0, sizeof(int)));
+    *nll = INFINITY;
+    return set_error(ctx, GF_EINVAL, "gf_update_data: an event lies outside its range/region");
+  }
   const int nf = (int)ctx->free_ids.size();
   double v = d.h_result[0];
   bool finite = std::isfinite(v);
@@ -1109,8 +1119,18 @@ static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host)
     rc = dalitz_prepare(ctx, &mode, &launches);
     if (rc == GF_OK) {
       DalitzBufs B = dalitz_bufs(ctx, dst);
-      cudaError_t e = launch_dalitz_events(ctx->dplan, ctx->precision == GF_MIXED, false, true,
-                                           mode, d.theta, B, d.nblocks, ctx->stream);
+      const bool mixed = ctx->precision == GF_MIXED;
+      cudaError_t e = cudaSuccess;
+      if (mode == DN_DIRECT) {
+        const int ncell_blocks = (int)std::min<int64_t>(
+            ((int64_t)ctx->dplan.nbx * ctx->dplan.nby + kThreads - 1) / kThreads,
+            (int64_t)ctx->sm_count * 4);
+        e = launch_dalitz_norm_direct(ctx->dplan, mixed, false, d.theta, B, ncell_blocks,
+                                      ctx->stream);
+      }
+      if (e == cudaSuccess)
+        e = launch_dalitz_events(ctx->dplan, mixed, false, true, mode, d.theta, B, d.nblocks,
+                                 ctx->stream);
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "launch_dalitz_events");
     }
   } else {
@@ -1180,6 +1200,45 @@ int gf_dalitz_gram(gf_ctx* ctx, const double* theta, double* G) {
   }
   d.gram_valid = true;
   (void)launches;
+  return GF_OK;
+}
+
+int gf_last_eval_times(gf_ctx* ctx, double* total_ms, double* stream_ms) {
+  if (!ctx) return GF_EINVAL;
+  if (total_ms) *total_ms = ctx->last_ms;
+  if (stream_ms) *stream_ms = ctx->last_stream_ms;
+  return GF_OK;
+}
+
+int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
+  if (!ctx || !cols) return GF_EINVAL;
+  DevState& d = ctx->dev;
+  if (!d.owns_cols || !d.theta) return set_error(ctx, GF_ESTATE, "no data set owned by the context");
+  if (n != d.n) return set_error(ctx, GF_EINVAL, "gf_update_data: n must equal the loaded size");
+  int rc = ensure_compiled(ctx);
+  if (rc) return rc;
+  CK(cudaSetDevice(ctx->device));
+  for (int k = 0; k < d.nobs; ++k) {
+    if (!cols[k]) return GF_EINVAL;
+    if (n > 0)
+      CK(cudaMemcpyAsync(d.cols[k], cols[k], sizeof(double) * n, cudaMemcpyHostToDevice,
+                         ctx->stream));
+  }
+  if (ctx->is_dalitz) {
+    CK(launch_dalitz_check(ctx->dplan, d.cols[0], d.cols[1], n, d.flag, ctx->stream));
+    if (d.fcols)
+      CK(launch_dalitz_fcols(ctx->dplan, d.cols[0], d.cols[1], n, d.fcols, ctx->stream));
+    for (auto& v : d.ev_m0) v = NAN;  // per-event caches hold the old events
+  } else {
+    Cols c{};
+    double lo[kMaxObs], hi[kMaxObs];
+    for (int k = 0; k < d.nobs; ++k) {
+      c.c[k] = d.cols[k];
+      lo[k] = ctx->obs[d.obs_ids[k]].lo;
+      hi[k] = ctx->obs[d.obs_ids[k]].hi;
+    }
+    CK(launch_check_range(c, d.nobs, n, lo, hi, d.flag, ctx->stream));
+  }
   return GF_OK;
 }
 

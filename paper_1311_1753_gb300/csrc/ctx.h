@@ -65,7 +65,8 @@ struct DevState {
   bool gram_valid = false;
   bool mask_built = false;
   // timing
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;  // eval start, stream kernel, end
+  int* flag = nullptr;                // device-side data check (0 = ok)
 };
 
 }  // namespace gfi
@@ -98,6 +99,7 @@ struct gf_ctx {
   gfi::DevState dev;
   int sm_count = 0;
   double last_ms = 0.0;
+  double last_stream_ms = 0.0;
   int last_launches = 0;
 };
 

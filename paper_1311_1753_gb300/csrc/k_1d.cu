@@ -423,6 +423,35 @@ __global__ void __launch_bounds__(kThreads1D) k_events_1d(
   if (tid == 0) *counter = 0u;
 }
 
+// ---- data check -------------------------------------------------------------------------------
+struct Range {
+  double lo[kMaxObs], hi[kMaxObs];
+};
+__global__ void k_check_range(const Cols cols, int nobs, int64_t n, const Range R, int* flag) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int o = 0; o < nobs; ++o) {
+      const double v = cols.c[o][i];
+      bad |= !(v >= R.lo[o] && v <= R.hi[o]);
+    }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+cudaError_t launch_check_range(const Cols& cols, int nobs, int64_t n, const double* lo,
+                               const double* hi, int* flag, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  Range R{};
+  for (int o = 0; o < nobs && o < kMaxObs; ++o) {
+    R.lo[o] = lo[o];
+    R.hi[o] = hi[o];
+  }
+  int64_t nb = (n + 255) / 256;
+  if (nb > 152 * 8) nb = 152 * 8;
+  k_check_range<<<(int)nb, 256, 0, st>>>(cols, nobs, n, R, flag);
+  return cudaGetLastError();
+}
+
 // ---- host launchers ---------------------------------------------------------------------------
 cudaError_t launch_norm_1d(const Program& P, const WeidCoef& W, const double* theta,
                            double* partials, unsigned* counter, double* derived,

@@ -186,6 +186,26 @@ __global__ void k_dalitz_mask(const DalitzPlan D, uint8_t* inside) {
   }
 }
 
+__global__ void k_dalitz_check(const DalitzPlan D, const double* __restrict__ s12,
+                               const double* __restrict__ s13, int64_t n, int* flag) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !inside_region(D, s12[i], s13[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+
+__global__ void k_dalitz_fcols(const DalitzPlan D, const double* __restrict__ s12,
+                               const double* __restrict__ s13, int64_t n, float* __restrict__ f) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = s12[i], b = s13[i];
+    f[i] = (float)a;
+    f[n + i] = (float)b;
+    f[2 * n + i] = (float)(D.sum_m2 - a - b);
+  }
+}
+
 // Per-event amplitudes of the event-cached resonances, FP64 (double2) or FP32 (float2).
 template <typename T>
 __global__ void k_dalitz_ev_cache(const DalitzPlan D, const double* __restrict__ theta,
@@ -349,9 +369,31 @@ __global__ void __launch_bounds__(kThreads) k_dalitz_stream(
   const int nf = D.nfree;
   const int nres = D.nres;
   if (tid < nres) res_constants(D, D.res[tid], theta, rk[tid]);
+  __shared__ double logN_s;
   Acc<T>* gacc = reinterpret_cast<Acc<T>*>(dyn) + tid;
   if (G)
     for (int k = 0; k < nf; ++k) gacc[k * bd] = Acc<T>();
+  __syncthreads();
+  if (METRIC == METRIC_STORE && tid == 0) {
+    // normalised log P: log |A|^2 - log N, N = c^H G c (Gram mode) or the direct pass
+    double N;
+    if (norm_mode == DN_GRAM) {
+      const int K = nres + 1;
+      double cr[kMaxRes + 1], ci[kMaxRes + 1];
+      cr[0] = 1.0;
+      ci[0] = 0.0;
+      for (int r = 0; r < nres; ++r) { cr[r + 1] = rk[r].cr; ci[r + 1] = rk[r].ci; }
+      N = 0.0;
+      for (int k = 0; k < K; ++k)
+        for (int s = 0; s < K; ++s) {
+          const double gr = gram[2 * (k * K + s)], gi = gram[2 * (k * K + s) + 1];
+          N += cr[k] * (gr * cr[s] - gi * ci[s]) + ci[k] * (gr * ci[s] + gi * cr[s]);
+        }
+    } else {
+      N = norm_in[0];
+    }
+    logN_s = log(N);
+  }
   __syncthreads();
   Acc<T> acc;
   const int64_t nitems = (METRIC == METRIC_NORM) ? (int64_t)D.nbx * D.nby : n;
@@ -396,7 +438,7 @@ __global__ void __launch_bounds__(kThreads) k_dalitz_stream(
     }
     const T P = At.r * At.r + At.i * At.i;
     if (METRIC == METRIC_STORE) {
-      out_logp[i] = (double)lg<T>(P);
+      out_logp[i] = (double)lg<T>(P) - logN_s;
       continue;
     }
     if (METRIC == METRIC_NLL) acc.add(-lg<T>(P));
@@ -506,6 +548,20 @@ static int grid_for(int64_t items, int threads, int cap) {
 
 cudaError_t launch_dalitz_mask(const DalitzPlan& D, uint8_t* inside, cudaStream_t st) {
   k_dalitz_mask<<<grid_for((int64_t)D.nbx * D.nby, 256, 4096), 256, 0, st>>>(D, inside);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dalitz_check(const DalitzPlan& D, const double* s12, const double* s13,
+                                int64_t n, int* flag, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_dalitz_check<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(D, s12, s13, n, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dalitz_fcols(const DalitzPlan& D, const double* s12, const double* s13,
+                                int64_t n, float* fcols, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_dalitz_fcols<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(D, s12, s13, n, fcols);
   return cudaGetLastError();
 }
 

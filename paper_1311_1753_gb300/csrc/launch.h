@@ -16,6 +16,9 @@ cudaError_t launch_events_1d(const Program& P, const WeidCoef& W, const Cols& co
                              unsigned* counter, double* result, double* out_logp, bool grad,
                              bool store, int analytic_only, int nblocks, cudaStream_t st);
 int events_1d_blocks_per_sm(bool grad, size_t smem);
+// flag := 1 if any event lies outside [lo[k], hi[k]] of its column
+cudaError_t launch_check_range(const Cols& cols, int nobs, int64_t n, const double* lo,
+                               const double* hi, int* flag, cudaStream_t st);
 
 // k_dalitz.cu
 struct DalitzBufs {
@@ -38,6 +41,12 @@ struct DalitzBufs {
 // mode flags for the event launch
 enum DalitzNormMode { DN_GRAM = 0, DN_DIRECT = 1 };
 cudaError_t launch_dalitz_mask(const DalitzPlan& D, uint8_t* inside, cudaStream_t st);
+// flag := 1 if any event lies outside the kinematic region
+cudaError_t launch_dalitz_check(const DalitzPlan& D, const double* s12, const double* s13,
+                                int64_t n, int* flag, cudaStream_t st);
+// FP32 columns s12, s13, s23 (s23 formed in FP64) for mixed-precision plans
+cudaError_t launch_dalitz_fcols(const DalitzPlan& D, const double* s12, const double* s13,
+                                int64_t n, float* fcols, cudaStream_t st);
 cudaError_t launch_dalitz_ev_cache(const DalitzPlan& D, bool mixed, const double* theta,
                                    const double* s12, const double* s13, int64_t n,
                                    void* ev_cache, cudaStream_t st);

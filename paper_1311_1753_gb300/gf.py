@@ -99,6 +99,8 @@ def _load():
         "gf_server_stats": ([vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _I], C.c_int),
         "gf_server_destroy": ([vp], C.c_int),
         "gf_last_eval_stats": ([vp, _D, _I], C.c_int),
+        "gf_last_eval_times": ([vp, _D, _D], C.c_int),
+        "gf_update_data": ([vp, C.c_int64, C.POINTER(_D)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -312,6 +314,21 @@ class Context:
 
     def set_stream(self, stream_ptr):
         self._ck(lib.gf_set_stream(self.h, C.c_void_p(stream_ptr)), "gf_set_stream")
+
+    def update_data(self, cols):
+        """Replace the loaded events (same n) from host columns; pinned arrays copy
+        asynchronously.  Pass arrays that stay alive until the next evaluation."""
+        ptrs = (_D * len(cols))(*[c.ctypes.data_as(_D) for c in cols])
+        self._ck(lib.gf_update_data(self.h, len(cols[0]), ptrs), "gf_update_data")
+
+    def update_data_ptrs(self, n, host_ptrs):
+        ptrs = (_D * len(host_ptrs))(*[C.cast(C.c_void_p(p), _D) for p in host_ptrs])
+        self._ck(lib.gf_update_data(self.h, n, ptrs), "gf_update_data")
+
+    def last_eval_times(self):
+        t, s = C.c_double(), C.c_double()
+        lib.gf_last_eval_times(self.h, C.byref(t), C.byref(s))
+        return t.value, s.value
 
     def last_eval_stats(self):
         ms = C.c_double()
