@@ -61,6 +61,10 @@ const WeidCoef& weideman() {
   std::call_once(once, [] {
     W.L = std::pow(2.0, -0.25) * std::sqrt((double)kWeidN);
     weideman_coeffs(kWeidN, W.L, W.a);
+    for (int n = 0; n <= kWeidN; ++n) {
+      W.ahi[n] = (float)W.a[n];
+      W.alo[n] = (float)(W.a[n] - (double)W.ahi[n]);
+    }
     const double Lf = std::pow(2.0, -0.25) * std::sqrt((double)kWeidNf);
     double af[kWeidNf + 1];
     weideman_coeffs(kWeidNf, Lf, af);
@@ -779,7 +783,7 @@ static int finish_set_data(gf_ctx* ctx) {
   if (ctx->is_dalitz) {
     per_sm = dalitz_blocks_per_sm(ctx->precision == GF_MIXED, true);
   } else {
-    per_sm = events_1d_blocks_per_sm(true, events_1d_smem(ctx->prog, true, kThreads));
+    per_sm = events_1d_blocks_per_sm(true, events_1d_smem(ctx->prog, true, kThreads1D));
   }
   per_sm = std::max(1, std::min(per_sm, 8));
   const int64_t items = ctx->is_dalitz ? d.n : (d.n + 1) / 2;

@@ -75,6 +75,7 @@ struct Cols {
 struct WeidCoef {
   double L;
   double a[kWeidN + 1];
+  float ahi[kWeidN + 1], alo[kWeidN + 1];  // a_n as double-float pairs (hi + lo)
   float Lf;
   float af[kWeidNf + 1];
 };

@@ -22,7 +22,7 @@ __device__ __forceinline__ double voigt_r(double x, double mu, double s, double 
   const double c1 = 1.0 / (s * kSqrt2);
   const double zr = (x - mu) * c1, zi = 0.5 * G * c1;
   double wr, wi;
-  faddeeva(zr, zi, W, wr, wi);
+  faddeeva_df(zr, zi, W, wr, wi);
   const double pref = 1.0 / (s * kSqrt2Pi);
   const double r = wr * pref;
   if (dr) {
@@ -249,7 +249,7 @@ __device__ __forceinline__ double eval_leaf(const Instr& I, const double* rec, d
     case L_VOIGT: {
       const double zr = (x - c[0]) * c[1], zi = c[2];
       double wr, wi;
-      faddeeva(zr, zi, W, wr, wi);
+      faddeeva_df(zr, zi, W, wr, wi);
       const double l = c[3] * wr;
       if (G) {
         const double dre = -2.0 * (zr * wr - zi * wi);
@@ -494,10 +494,14 @@ cudaError_t launch_events_1d(const Program& P, const WeidCoef& W, const Cols& co
 
 int events_1d_blocks_per_sm(bool grad, size_t smem) {
   int nb = 0;
-  if (grad)
+  if (grad) {
+    cudaFuncSetAttribute(k_events_1d<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_events_1d<true, 0>, kThreads1D, smem);
-  else
+  } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_events_1d<false, 0>, kThreads1D, 0);
+  }
+  cudaGetLastError();
   return nb > 0 ? nb : 1;
 }
 

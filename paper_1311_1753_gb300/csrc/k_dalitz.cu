@@ -37,7 +37,7 @@ __device__ __forceinline__ T rcp(T x);
 template <>
 __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
 template <>
-__device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
 template <typename T>
 __device__ __forceinline__ T lg(T x);
 template <>

@@ -54,7 +54,7 @@ struct Req {
 struct gf_server {
   gf_server_opts opts{};
   std::mutex mu;
-  std::condition_variable cv_sched, cv_fit;
+  std::condition_variable cv_sched, cv_fit, cv_drain;
   std::deque<std::shared_ptr<Req>> pending;
   std::vector<std::shared_ptr<Req>> active;
   std::map<uint64_t, std::shared_ptr<Req>> all;
@@ -126,6 +126,7 @@ static void scheduler(gf_server* S) {
         S->used_bytes -= R->bytes;
         S->active.erase(S->active.begin() + i);
         S->unfinished--;
+        S->cv_drain.notify_all();
       } else {
         ++i;
       }
@@ -143,6 +144,7 @@ static void scheduler(gf_server* S) {
         R->done = true;
         R->t_done = Clock::now();
         S->unfinished--;
+        S->cv_drain.notify_all();
         continue;
       }
       S->used_bytes += R->bytes;
@@ -261,7 +263,7 @@ int gf_server_drain(gf_server* S) {
   const double tmo = S->opts.wait_timeout_s;
   while (S->unfinished > 0) {
     const int64_t before = S->unfinished;
-    if (!S->cv_sched.wait_for(lk, std::chrono::duration<double>(tmo),
+    if (!S->cv_drain.wait_for(lk, std::chrono::duration<double>(tmo),
                               [&] { return S->unfinished < before || S->unfinished == 0; }))
       return GF_ETIMEOUT;
   }

@@ -111,3 +111,37 @@ def test_autograd_wrapper(gf):
     fo, go = m.nll([x], grad=True)
     assert abs(f.item() - fo) <= 1e-9 * abs(fo)
     assert abs(th.grad.item() - go[0]) <= 1e-9 * abs(go[0])
+
+
+def test_config4_mixed_fit_small(gf):
+    """Config 4's shape: 30 free parameters (7 masses and widths free), FP32 amplitudes with
+    FP64 sums and normalisation, fused gradient; against the oracle's FP64 fit."""
+    nres = len(SPEC["resonances"])
+    d = om.dalitz_from_spec(SPEC, 128, 128)
+    d_full = om.dalitz_from_spec(SPEC)
+    s12, s13 = synth.dalitz_events(20_000, om.dalitz_accept(d_full, SPEC["envelope"]), seed=78)
+    free = []
+    for r in range(nres):
+        if r != nres - 1:
+            free += [4 * r, 4 * r + 1]
+        free += [4 * r + 2, 4 * r + 3]
+    truth = d.p[free]
+    rng = np.random.default_rng(5)
+    start = truth * (1 + 0.01 * rng.standard_normal(len(truth)))
+    ctx, root, obs = pm.dalitz_model(gf, SPEC, precision=gf.GF_MIXED, free_shapes=True, nbx=128,
+                                     nby=128)
+    for k, pid in enumerate(ctx.free_params()):
+        ctx.set_value(pid, start[k])
+    ctx.set_data(root, obs, [s12, s13])
+    r = ctx.fit(tol=1e-5)
+    step = np.array([0.005 if k % 4 < 2 else 0.01 for k in free])
+    lo_b = np.array([0.4 if k % 4 == 0 else 0.01 if k % 4 == 1 else 0.0 for k in free])
+    hi_b = np.array([1.75 if k % 4 == 0 else 0.6 if k % 4 == 1 else 0.0 for k in free])
+    o = _oracle_fit(d, free, None, start, step, lo_b, hi_b,
+                    fun=lambda q: d.nll(s12, s13, q, grad=True))
+    assert o.converged
+    dev = (r["theta"] - o.x) / o.err
+    print("mixed fit: status", r["status"], "edm", r["edm"], "calls", r["n_calls"],
+          "max |dev|/sigma", np.abs(dev).max())
+    assert np.all(np.abs(dev) <= 0.01), dev
+    assert np.all(np.abs(r["err"] / o.err - 1) < 0.02)
