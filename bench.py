@@ -372,6 +372,10 @@ def main():
     extra = {}
     if not args.no_extra and args.workload == "voigt" and rank == 0:
         extra = run_extra(torch, gf, args)
+    if args.fits and rank == 0:
+        extra["fits"] = run_fits(torch, gf, args)
+    if args.serve and rank == 0:
+        extra["serve"] = run_serve(torch, gf, args)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -395,6 +399,136 @@ def main():
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def run_fits(torch, gf, args):
+    """Time-to-fit (gf_fit: BFGS + fused gradient + Hessian errors) per workload; config 4
+    in FP64 and in mixed precision (FP32 amplitudes, FP64 sums, FP64 refinement) on the
+    same data, with the deviation of the mixed fit from the FP64 fit in sigma units."""
+    out = {}
+
+    def timed_fit(ctx, start, tol):
+        for k, pid in enumerate(ctx.free_params()):
+            ctx.set_value(pid, start[k])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = ctx.fit(tol=tol)
+        torch.cuda.synchronize()
+        r["seconds"] = time.perf_counter() - t0
+        return r
+
+    ctx, root, obs, cols, th = exp_workload(gf, 100_000, synth.SEED_EXP, gf.GF_FP64)
+    r = timed_fit(ctx, np.array([-2.0]), 1e-8)
+    out["config1_fit"] = {"seconds": r["seconds"], "calls": r["n_calls"], "status": r["status"],
+                          "alpha": float(r["theta"][0]), "err": float(r["err"][0])}
+    ctx.close()
+    ctx, root, obs, cols, th = voigt_workload(gf, 10_000_000, synth.SEED_VOIGT, gf.GF_FP64)
+    r = timed_fit(ctx, th * np.array([1.0002, 1.1, 0.85, 1.1, 0.93]), 1e-6)
+    out["config2_fit_1e7"] = {"seconds": r["seconds"], "calls": r["n_calls"], "status": r["status"],
+                              "pull_vs_truth": ((r["theta"] - th) / r["err"]).tolist()}
+    ctx.close()
+    spec = dalitz_spec()
+    data = dalitz_events_gpu(gf, spec, 1_000_000, synth.SEED_DALITZ_EVENTS)
+    ctx, root, obs, cols, th = dalitz_workload(gf, 1_000_000, 0, gf.GF_FP64, False, data)
+    rng = np.random.default_rng(8)
+    r = timed_fit(ctx, th + 0.02 * rng.standard_normal(len(th)), 1e-6)
+    out["config3_fit_1e6"] = {"seconds": r["seconds"], "calls": r["n_calls"], "status": r["status"]}
+    ctx.close()
+    data5 = dalitz_events_gpu(gf, spec, 5_000_000, synth.SEED_DALITZ_BIG)
+    res = {}
+    for prec, name in ((gf.GF_FP64, "fp64"), (gf.GF_MIXED, "mixed")):
+        ctx, root, obs, cols, th = dalitz_workload(gf, 5_000_000, 0, prec, True, data5)
+        start = th * (1 + 0.01 * np.random.default_rng(9).standard_normal(len(th)))
+        res[name] = timed_fit(ctx, start, 1e-6)
+        ctx.close()
+    f, m = res["fp64"], res["mixed"]
+    out["config4_fit_5e6"] = {
+        "fp64": {"seconds": f["seconds"], "calls": f["n_calls"], "status": f["status"]},
+        "mixed": {"seconds": m["seconds"], "calls": m["n_calls"], "status": m["status"]},
+        "mixed_speedup": f["seconds"] / m["seconds"],
+        "max_abs_dev_mixed_vs_fp64_in_sigma": float(np.max(np.abs((m["theta"] - f["theta"]) / f["err"]))),
+        "max_rel_err_diff": float(np.max(np.abs(m["err"] / f["err"] - 1)))}
+    return out
+
+
+def run_serve(torch, gf, args, nreq=256):
+    """Pull study through the fit server: Poisson arrivals at 20/s, event counts
+    log-uniform in [1e4, 4e6], models 1D composite or Dalitz by a fair coin, each data set
+    drawn at the truth from its own seed; admission by a 150 GB device budget."""
+    kinds, counts, seeds = synth.serving_requests(nreq)
+    arrivals = synth.poisson_arrivals(nreq, 20.0)
+    spec = dalitz_spec()
+    lo, hi = synth.VOIGT_RANGE
+    t = synth.VOIGT_TRUTH
+    reqs = []
+    t_gen = time.perf_counter()
+    for j in range(nreq):
+        n = int(counts[j])
+        if kinds[j] == 0:
+            x = synth.voigt_threshold_events(n, **t, lo=lo, hi=hi, seed=int(seeds[j]))
+            reqs.append(("voigt", [x]))
+        else:
+            s12, s13 = dalitz_events_gpu(gf, spec, n, int(seeds[j]))
+            reqs.append(("dalitz", [s12, s13]))
+    t_gen = time.perf_counter() - t_gen
+    truth_v = np.array([t["mu"], t["sigma"], t["width"], t["c"], t["frac"]])
+    srv = gf.Server(precision=gf.GF_MIXED, mem_budget=150 << 30, max_slots=64,
+                    wait_timeout_s=600.0)
+    tickets, truths = [], []
+    t0 = time.perf_counter()
+    for j, (kind, cols) in enumerate(reqs):
+        while time.perf_counter() - t0 < arrivals[j]:
+            time.sleep(0.0005)
+        if kind == "voigt":
+            ctx, root, obs, _, _ = voigt_model_nodata(gf)
+            start = truth_v
+        else:
+            ctx, root, obs, th = dalitz_context(gf, spec, gf.GF_MIXED, False)
+            start = th
+        ds = ctx.make_dataset(obs, cols)
+        tickets.append(srv.submit(ctx, ds, root, tol=1e-6))
+        truths.append(start)
+    srv.drain()
+    t_all = time.perf_counter() - t0
+    lat, pulls_v, pulls_d, bad = [], [], [], 0
+    for j, tk in enumerate(tickets):
+        r = srv.poll(tk)
+        lat.append(r["latency"])
+        if r["status"] != 0:
+            bad += 1
+            continue
+        p = (r["theta"] - truths[j]) / r["err"]
+        (pulls_v if kinds[j] == 0 else pulls_d).append(p)
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    pv, pd = np.array(pulls_v), np.array(pulls_d)
+    return {"requests": nreq, "fits_per_s": nreq / t_all, "wall_s": t_all,
+            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+            "not_converged": bad, "ticks": st["ticks"], "launches": st["launches"],
+            "peak_slots": st["peak_slots"], "data_generation_s": t_gen,
+            "pull_1d_mean": pv.mean(0).tolist() if len(pv) else None,
+            "pull_1d_width": pv.std(0).tolist() if len(pv) else None,
+            "pull_dalitz_mean_avg": float(pd.mean()) if len(pd) else None,
+            "pull_dalitz_width_avg": float(pd.std(0).mean()) if len(pd) else None,
+            "pull_dalitz_width_range": [float(pd.std(0).min()), float(pd.std(0).max())] if len(pd) else None,
+            "precision": "mixed (FP32 amplitudes, FP64 sums; 1D path FP64) + FP64 refinement"}
+
+
+def voigt_model_nodata(gf):
+    lo, hi = synth.VOIGT_RANGE
+    t = synth.VOIGT_TRUTH
+    ctx = gf.Context(0, gf.GF_MIXED)
+    xo = ctx.observable("dm", lo, hi)
+    mu = ctx.parameter("mu", t["mu"], 1e-5, 0.143, 0.148)
+    s = ctx.parameter("sigma", t["sigma"], 1e-5, 1e-5, 2e-3)
+    w = ctx.parameter("width", t["width"], 1e-5, 1e-6, 1e-3)
+    x0 = ctx.parameter("x0", t["x0"], 1e-4, fixed=True)
+    pw = ctx.parameter("power", t["power"], 0.01, fixed=True)
+    c = ctx.parameter("c", t["c"], 0.5, 0.0, 200.0)
+    f = ctx.parameter("frac", t["frac"], 0.01, 0.0, 1.0)
+    root = ctx.add([ctx.voigt(xo, mu, s, w), ctx.threshold(xo, x0, pw, c)], [f])
+    return ctx, root, [xo], None, None
 
 
 def run_extra(torch, gf, args):

@@ -41,9 +41,9 @@ extern "C" {
 
 /* ---- precision modes -------------------------------------------------------------- */
 #define GF_FP64 0   /* every per-event and per-cell operation in FP64                   */
-#define GF_MIXED 1  /* per-event PDF/amplitude arithmetic in FP32; FP64 for the log-sum */
-                    /* across threads and blocks, the normalisation integrals and the   */
-                    /* Voigtian's Faddeeva function                                      */
+#define GF_MIXED 1  /* per-event amplitude arithmetic in FP32; FP64 for the log-sum      */
+                    /* across threads and blocks and for the normalisation integrals   */
+                    /* (1D trees evaluate in FP64 in either mode)                      */
 
 typedef struct gf_ctx gf_ctx;
 typedef struct gf_dataset gf_dataset;
@@ -181,6 +181,10 @@ typedef struct {
   int use_grad;    /* 1: fused analytic gradient; 0: central differences of gf_nll */
   double up;       /* error definition (0.5 for a negative log-likelihood; <= 0 -> 0.5) */
   int hesse;       /* 1: covariance from the Hessian by differences of the gradient */
+  int refine;      /* GF_MIXED contexts: 1 (default when opts is NULL) runs BFGS on the FP32
+                      likelihood to EDM < max(tol, 1e-3), then continues in FP64 from that
+                      point and inverse-Hessian estimate to EDM < tol; errors from the
+                      FP32 Hessian.  0: FP32 only. */
 } gf_fit_opts;
 typedef struct {
   double nll;      /* NLL at the minimum */

@@ -61,6 +61,8 @@ const WeidCoef& weideman() {
   std::call_once(once, [] {
     W.L = std::pow(2.0, -0.25) * std::sqrt((double)kWeidN);
     weideman_coeffs(kWeidN, W.L, W.a);
+    W.Lhi = (float)W.L;
+    W.Llo = (float)(W.L - (double)W.Lhi);
     for (int n = 0; n <= kWeidN; ++n) {
       W.ahi[n] = (float)W.a[n];
       W.alo[n] = (float)(W.a[n] - (double)W.ahi[n]);
@@ -126,6 +128,7 @@ static void free_dev(gf_ctx* ctx) {
   cudaFree(d.grid_cols);
   cudaFree(d.gram);
   cudaFree(d.ev_cache);
+  cudaFree(d.ev_cache64);
   cudaFree(d.fcols);
   cudaFree(d.todo);
   if (d.h_theta) cudaFreeHost(d.h_theta);
@@ -912,14 +915,14 @@ static int upload_theta(gf_ctx* ctx, const double* theta) {
   return GF_OK;
 }
 
-static DalitzBufs dalitz_bufs(gf_ctx* ctx, double* out_logp) {
+static DalitzBufs dalitz_bufs(gf_ctx* ctx, double* out_logp, bool mixed = true) {
   DevState& d = ctx->dev;
   DalitzBufs B{};
   B.s12 = d.cols[0];
   B.s13 = d.cols[1];
   B.sf = d.fcols;
   B.n = d.n;
-  B.ev_cache = d.ev_cache;
+  B.ev_cache = (ctx->precision == GF_MIXED && !mixed) ? d.ev_cache64 : d.ev_cache;
   B.grid_cols = d.grid_cols;
   B.inside = d.inside;
   B.gram = d.gram;
@@ -935,10 +938,24 @@ static DalitzBufs dalitz_bufs(gf_ctx* ctx, double* out_logp) {
 
 // Dalitz caches: rebuild event / grid columns of fixed-shape resonances whose (m0,
 // Gamma0) differ from those the caches hold; decide the normalisation mode.
-static int dalitz_prepare(gf_ctx* ctx, int* norm_mode, int* launches) {
+static int dalitz_prepare(gf_ctx* ctx, int* norm_mode, int* launches, bool mixed) {
   DevState& d = ctx->dev;
   const DalitzPlan& D = ctx->dplan;
-  const bool mixed = ctx->precision == GF_MIXED;
+  // the per-event cache matching the arithmetic of this evaluation: FP32 pairs for
+  // mixed evaluations, FP64 pairs otherwise (a mixed context keeps a second, FP64 cache
+  // for the refinement stage of its fits)
+  const bool second = ctx->precision == GF_MIXED && !mixed;
+  void*& cache = second ? d.ev_cache64 : d.ev_cache;
+  std::vector<double>& cm0 = second ? d.ev64_m0 : d.ev_m0;
+  std::vector<double>& cg0 = second ? d.ev64_g0 : d.ev_g0;
+  if (cm0.size() != (size_t)D.nres) {
+    cm0.assign(D.nres, NAN);
+    cg0.assign(D.nres, NAN);
+  }
+  int ncached = 0;
+  for (int r = 0; r < D.nres; ++r) ncached += D.res[r].ev_cached >= 0 ? 1 : 0;
+  if (second && !cache && ncached > 0 && d.n > 0)
+    CK(cudaMalloc(&cache, (size_t)ncached * d.n * 16));
   if (!d.mask_built) {
     CK(launch_dalitz_mask(D, d.inside, ctx->stream));
     (*launches)++;
@@ -951,21 +968,20 @@ static int dalitz_prepare(gf_ctx* ctx, int* norm_mode, int* launches) {
     const DalitzRes& R = D.res[r];
     const double m0 = d.h_theta[R.p_m0], g0 = d.h_theta[R.p_g0];
     if (R.ev_cached >= 0) {
-      if (!(d.ev_m0[r] == m0 && d.ev_g0[r] == g0)) ev_stale = true;
+      if (!(cm0[r] == m0 && cg0[r] == g0)) ev_stale = true;
       if (!(d.col_m0[r] == m0 && d.col_g0[r] == g0)) todo.push_back(r);
     } else {
       any_free_shape = true;
     }
   }
   if (ev_stale && d.n > 0) {
-    CK(launch_dalitz_ev_cache(D, mixed, d.theta, d.cols[0], d.cols[1], d.n, d.ev_cache,
-                              ctx->stream));
+    CK(launch_dalitz_ev_cache(D, mixed, d.theta, d.cols[0], d.cols[1], d.n, cache, ctx->stream));
     (*launches)++;
   }
   for (int r = 0; r < D.nres; ++r)
     if (D.res[r].ev_cached >= 0) {
-      d.ev_m0[r] = d.h_theta[D.res[r].p_m0];
-      d.ev_g0[r] = d.h_theta[D.res[r].p_g0];
+      cm0[r] = d.h_theta[D.res[r].p_m0];
+      cg0[r] = d.h_theta[D.res[r].p_g0];
     }
   if (!todo.empty()) {
     CK(cudaMemcpyAsync(d.todo, todo.data(), sizeof(int) * todo.size(), cudaMemcpyHostToDevice,
@@ -997,7 +1013,7 @@ static int dalitz_prepare(gf_ctx* ctx, int* norm_mode, int* launches) {
 
 namespace gfi {
 
-int evaluate_async(gf_ctx* ctx, const double* theta, bool grad) {
+int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64) {
   int rc = ensure_compiled(ctx);
   if (rc) return rc;
   DevState& d = ctx->dev;
@@ -1010,15 +1026,16 @@ int evaluate_async(gf_ctx* ctx, const double* theta, bool grad) {
   const int nf = (int)ctx->free_ids.size();
   if (ctx->is_dalitz) {
     int mode = DN_GRAM;
-    rc = dalitz_prepare(ctx, &mode, &launches);
+    const bool mixed = ctx->precision == GF_MIXED && !fp64;
+    rc = dalitz_prepare(ctx, &mode, &launches, mixed);
     if (rc) return rc;
-    DalitzBufs B = dalitz_bufs(ctx, nullptr);
-    const bool mixed = ctx->precision == GF_MIXED;
+    DalitzBufs B = dalitz_bufs(ctx, nullptr, mixed);
     if (mode == DN_DIRECT) {
       const int ncell_blocks = (int)std::min<int64_t>(
           ((int64_t)ctx->dplan.nbx * ctx->dplan.nby + kThreads - 1) / kThreads,
           (int64_t)ctx->sm_count * 4);
-      CK(launch_dalitz_norm_direct(ctx->dplan, mixed, grad, d.theta, B, ncell_blocks,
+      // the normalisation integral and its gradient in FP64 in every mode
+      CK(launch_dalitz_norm_direct(ctx->dplan, false, grad, d.theta, B, ncell_blocks,
                                    ctx->stream));
       launches++;
     }
@@ -1080,8 +1097,8 @@ int evaluate_finish(gf_ctx* ctx, double* nll, double* grad, bool grad_wanted) {
   return GF_OK;
 }
 
-int evaluate(gf_ctx* ctx, const double* theta, double* nll, double* grad) {
-  int rc = evaluate_async(ctx, theta, grad != nullptr);
+int evaluate(gf_ctx* ctx, const double* theta, double* nll, double* grad, bool fp64) {
+  int rc = evaluate_async(ctx, theta, grad != nullptr, fp64);
   if (rc) return rc;
   return evaluate_finish(ctx, nll, grad, grad != nullptr);
 }
@@ -1120,7 +1137,7 @@ static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host)
   int launches = 0;
   if (ctx->is_dalitz) {
     int mode = 0;
-    rc = dalitz_prepare(ctx, &mode, &launches);
+    rc = dalitz_prepare(ctx, &mode, &launches, ctx->precision == GF_MIXED);
     if (rc == GF_OK) {
       DalitzBufs B = dalitz_bufs(ctx, dst);
       const bool mixed = ctx->precision == GF_MIXED;
@@ -1129,7 +1146,7 @@ static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host)
         const int ncell_blocks = (int)std::min<int64_t>(
             ((int64_t)ctx->dplan.nbx * ctx->dplan.nby + kThreads - 1) / kThreads,
             (int64_t)ctx->sm_count * 4);
-        e = launch_dalitz_norm_direct(ctx->dplan, mixed, false, d.theta, B, ncell_blocks,
+        e = launch_dalitz_norm_direct(ctx->dplan, false, false, d.theta, B, ncell_blocks,
                                       ctx->stream);
       }
       if (e == cudaSuccess)
@@ -1233,6 +1250,7 @@ int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
     if (d.fcols)
       CK(launch_dalitz_fcols(ctx->dplan, d.cols[0], d.cols[1], n, d.fcols, ctx->stream));
     for (auto& v : d.ev_m0) v = NAN;  // per-event caches hold the old events
+    for (auto& v : d.ev64_m0) v = NAN;
   } else {
     Cols c{};
     double lo[kMaxObs], hi[kMaxObs];

@@ -58,9 +58,11 @@ struct DevState {
   double* grid_cols = nullptr;
   double* gram = nullptr;
   void* ev_cache = nullptr;
+  void* ev_cache64 = nullptr;           // FP64 per-event cache of a mixed context (refinement)
   float* fcols = nullptr;
   int* todo = nullptr;
   std::vector<double> ev_m0, ev_g0;     // shapes the event cache was built with (NaN: none)
+  std::vector<double> ev64_m0, ev64_g0; // same for ev_cache64
   std::vector<double> col_m0, col_g0;   // shapes of the grid columns
   bool gram_valid = false;
   bool mask_built = false;
@@ -108,10 +110,10 @@ namespace gfi {
 int set_error(gf_ctx* ctx, int code, const std::string& msg);
 int ensure_compiled(gf_ctx* ctx);
 // Evaluate at theta (free params): nll always, grad if non-null.  Blocking.
-int evaluate(gf_ctx* ctx, const double* theta, double* nll, double* grad);
+int evaluate(gf_ctx* ctx, const double* theta, double* nll, double* grad, bool fp64 = false);
 // Enqueue an evaluation without waiting: the result lands in ctx->dev.h_result after the
 // stream reaches it (used by the server to overlap fits).
-int evaluate_async(gf_ctx* ctx, const double* theta, bool grad);
+int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64 = false);
 int evaluate_finish(gf_ctx* ctx, double* nll, double* grad, bool grad_wanted);
 size_t device_bytes_for(const gf_ctx* ctx, int root, int64_t n);
 int nfree(const gf_ctx* ctx);

@@ -2,6 +2,7 @@
 // reductions, the last-block completion pattern, and the Faddeeva function.
 #pragma once
 #include <cuda_runtime.h>
+#include "df64.cuh"
 #include "gf_internal.h"
 
 namespace gfi {
@@ -104,88 +105,41 @@ __device__ __forceinline__ bool arrive_last(unsigned* counter, int* flag_smem) {
 // term (residues at t = z and, for the constant term, t = iL) gives
 //   w(z) = 1/(sqrt(pi) (L - iz)) + 2/(L - iz)^2 sum_{n=1}^{N} a_n Z^{n-1},
 //   Z = (L + iz)/(L - iz),  L = 2^{-1/4} sqrt(N).
-// The a_n are Fourier coefficients computed on the host (WeidCoef).  N = 40 gives
-// |w| to ~2e-14 relative over the Voigtian's range of z.
-__device__ __forceinline__ void faddeeva(double x, double y, const WeidCoef& W, double& wr,
-                                         double& wi) {
-  const double L = W.L;
-  const double dr = L + y;                          // L - iz = (L + y) - i x
-  const double inv = 1.0 / fma(dr, dr, x * x);      // 1/|L - iz|^2
-  const double Zr = fma(L - y, dr, -x * x) * inv;   // Re Z
-  const double Zi = 2.0 * L * x * inv;              // Im Z
-  double pr = W.a[kWeidN], pi = 0.0;
-#pragma unroll
-  for (int n = kWeidN - 1; n >= 1; --n) {
-    const double t = fma(pr, Zr, fma(-pi, Zi, W.a[n]));
-    pi = fma(pr, Zi, pi * Zr);
-    pr = t;
-  }
-  const double ir = dr * inv, ii = x * inv;          // 1/(L - iz)
-  const double qr = fma(ir, ir, -ii * ii), qi = 2.0 * ir * ii;  // 1/(L - iz)^2
-  wr = fma(kInvSqrtPi, ir, 2.0 * fma(pr, qr, -pi * qi));
-  wi = fma(kInvSqrtPi, ii, 2.0 * fma(pr, qi, pi * qr));
-}
-
-// ---- double-float arithmetic (unevaluated sums hi + lo of two floats) -------------------
-// Error-free transformations: Knuth's TwoSum, and the product error by one FMA (exact for
-// binary32).  __fadd_rn/__fmul_rn keep the compiler from contracting or reordering them.
-struct F2 {
-  float hi, lo;
-};
-__device__ __forceinline__ F2 two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ F2 fast_two_sum(float a, float b) {  // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-// a * b as an unnormalised pair (p, e): p = fl(a.hi b.hi), e = its error + cross terms
-__device__ __forceinline__ F2 df_mul_raw(F2 a, F2 b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  return {p, e};
-}
-__device__ __forceinline__ F2 split_double(double v) {
-  const float hi = __double2float_rn(v);
-  return {hi, __double2float_rn(v - (double)hi)};
-}
-
-// Weideman's series with the Horner recursion p <- p Z + a_n in double-float on the FP32
-// pipe (48-bit significands), the set-up (Z, 1/(L - iz)) and the final combination in
-// FP64.  GB300 issues FP32 at 61x the FP64 rate, so the 39 complex multiply-adds move off
-// the FP64 pipe; |w| stays within ~3e-14 relative over the Voigtian's range.
+// The a_n are Fourier coefficients computed on the host (WeidCoef).  N = 40 gives |w|
+// to ~2e-14 relative over the Voigtian's range of z.  FP64-accurate version: every step
+// in double-float on the FP32 pipe (inputs and outputs FP64).
 __device__ __forceinline__ void faddeeva_df(double x, double y, const WeidCoef& W, double& wr,
                                             double& wi) {
-  const double L = W.L;
-  const double dr = L + y;
-  const double inv = 1.0 / fma(dr, dr, x * x);
-  const F2 zr = split_double(fma(L - y, dr, -x * x) * inv);
-  const F2 zi = split_double(2.0 * L * x * inv);
+  const F2 X = df_from(x), Y = df_from(y);
+  const F2 L = {W.Lhi, W.Llo};
+  const F2 dr = df_add(L, Y);                                        // L - iz = dr - i x
+  const F2 x2 = df_mul(X, X);
+  const F2 inv = df_div(F2{1.f, 0.f}, df_add(df_mul(dr, dr), x2));   // 1/|L - iz|^2
+  const F2 zr = df_mul(df_sub(df_mul(df_sub(L, Y), dr), x2), inv);   // Re Z
+  const F2 zi = df_mul(df_mul_f(df_mul(L, X), 2.f), inv);            // Im Z
   F2 pr = {W.ahi[kWeidN], W.alo[kWeidN]}, pi = {0.f, 0.f};
 #pragma unroll
   for (int n = kWeidN - 1; n >= 1; --n) {
-    // real: pr zr - pi zi + a_n
+    // real: pr zr - pi zi + a_n ; imag: pr zi + pi zr
     const F2 t1 = df_mul_raw(pr, zr), t2 = df_mul_raw(pi, zi);
     const F2 s1 = two_sum(t1.hi, -t2.hi);
     const F2 s2 = two_sum(s1.hi, W.ahi[n]);
-    const float er = __fadd_rn(__fadd_rn(__fadd_rn(s1.lo, s2.lo), __fsub_rn(t1.lo, t2.lo)), W.alo[n]);
-    // imag: pr zi + pi zr
+    const float er =
+        __fadd_rn(__fadd_rn(__fadd_rn(s1.lo, s2.lo), __fsub_rn(t1.lo, t2.lo)), W.alo[n]);
     const F2 t3 = df_mul_raw(pr, zi), t4 = df_mul_raw(pi, zr);
     const F2 s3 = two_sum(t3.hi, t4.hi);
     const float ei = __fadd_rn(s3.lo, __fadd_rn(t3.lo, t4.lo));
     pr = fast_two_sum(s2.hi, er);
     pi = fast_two_sum(s3.hi, ei);
   }
-  const double Pr = (double)pr.hi + (double)pr.lo, Pi = (double)pi.hi + (double)pi.lo;
-  const double ir = dr * inv, ii = x * inv;
-  const double qr = fma(ir, ir, -ii * ii), qi = 2.0 * ir * ii;
-  wr = fma(kInvSqrtPi, ir, 2.0 * fma(Pr, qr, -Pi * qi));
-  wi = fma(kInvSqrtPi, ii, 2.0 * fma(Pr, qi, Pi * qr));
+  const F2 ir = df_mul(dr, inv), ii = df_mul(X, inv);                // 1/(L - iz)
+  const F2 qr = df_sub(df_mul(ir, ir), df_mul(ii, ii));              // 1/(L - iz)^2
+  const F2 qi = df_mul_f(df_mul(ir, ii), 2.f);
+  constexpr DFC c(kInvSqrtPi);
+  const F2 WR = df_add(df_mul(c, ir), df_mul_f(df_sub(df_mul(pr, qr), df_mul(pi, qi)), 2.f));
+  const F2 WI = df_add(df_mul(c, ii), df_mul_f(df_add(df_mul(pr, qi), df_mul(pi, qr)), 2.f));
+  wr = df_to(WR);
+  wi = df_to(WI);
 }
 
 __device__ __forceinline__ void faddeeva(float x, float y, const WeidCoef& W, float& wr,

@@ -86,13 +86,15 @@ MinResult minimise(const FGFun& fg, const std::vector<double>& x0, const std::ve
     res.calls = calls;
     return res;
   }
-  // V0 = diag(step_int^2)
+  // V0 = diag(step_int^2), or the caller's estimate
   std::vector<double> V(n * n, 0.0), sint(n);
   for (size_t k = 0; k < n; ++k) {
     const double d = std::max(std::fabs(B.der(k, u[k])), 1e-300);
     sint[k] = step[k] / d;
     V[k * n + k] = sint[k] * sint[k];
   }
+  const bool given_V = opt.V0 && opt.V0->size() == n * n;
+  if (given_V) V = *opt.V0;
   auto edm_of = [&](const std::vector<double>& gg) {
     double e = 0.0;
     for (size_t i = 0; i < n; ++i) {
@@ -125,6 +127,7 @@ MinResult minimise(const FGFun& fg, const std::vector<double>& x0, const std::ve
     }
     // strong-Wolfe line search along p
     const double c1 = 1e-4, c2 = 0.9;
+    const double fn = opt.f_noise;  // differences below the noise count as no change
     auto phi = [&](double a, double& fa, double& da, std::vector<double>& ga) -> int {
       for (size_t i = 0; i < n; ++i) un[i] = u[i] + a * p[i];
       int r = eval(un, fa, ga);
@@ -142,7 +145,7 @@ MinResult minimise(const FGFun& fg, const std::vector<double>& x0, const std::ve
       int r = phi(a, fa, da, ga);
       if (r != GF_OK && r != GF_ENONFINITE) { hard = true; rc = r; break; }
       if (r == GF_ENONFINITE) { a = 0.5 * (a_prev + a); continue; }
-      if (fa > f + c1 * a * d0 || (ls > 0 && fa >= f_prev)) {
+      if (fa > f + c1 * a * d0 + fn || (ls > 0 && fa >= f_prev + fn)) {
         // zoom in [a_prev, a]
         double alo = a_prev, flo = f_prev, dlo = d_prev, ahi = a, fhi = fa, dhi = da;
         for (int z = 0; z < 30 && calls < opt.max_calls; ++z) {
@@ -150,7 +153,7 @@ MinResult minimise(const FGFun& fg, const std::vector<double>& x0, const std::ve
           double ft, dt;
           int rz = phi(at, ft, dt, ga);
           if (rz != GF_OK && rz != GF_ENONFINITE) { hard = true; rc = rz; break; }
-          if (rz == GF_ENONFINITE || ft > f + c1 * at * d0 || ft >= flo) {
+          if (rz == GF_ENONFINITE || ft > f + c1 * at * d0 + fn || ft >= flo + fn) {
             ahi = at; fhi = (rz == GF_OK) ? ft : INFINITY; dhi = (rz == GF_OK) ? dt : 0.0;
             if (rz != GF_OK) { fhi = flo + 1.0; dhi = -dlo; }
           } else {
@@ -172,7 +175,7 @@ MinResult minimise(const FGFun& fg, const std::vector<double>& x0, const std::ve
           double ft, dt;
           int rz = phi(at, ft, dt, ga);
           if (rz != GF_OK && rz != GF_ENONFINITE) { hard = true; rc = rz; break; }
-          if (rz == GF_ENONFINITE || ft > f + c1 * at * d0 || ft >= flo) {
+          if (rz == GF_ENONFINITE || ft > f + c1 * at * d0 + fn || ft >= flo + fn) {
             ahi = at; fhi = (rz == GF_OK) ? ft : flo + 1.0; dhi = (rz == GF_OK) ? dt : -dlo;
           } else {
             if (std::fabs(dt) <= -c2 * d0) { a_ok = at; f_ok = ft; g_ok = ga; break; }
@@ -189,7 +192,7 @@ MinResult minimise(const FGFun& fg, const std::vector<double>& x0, const std::ve
       a *= 2.0;
     }
     if (hard) break;
-    if (a_ok <= 0 || !(f_ok < f)) {
+    if (a_ok <= 0 || !(f_ok < f + fn)) {
       if (++fail >= 2) break;
       std::fill(V.begin(), V.end(), 0.0);
       for (size_t k = 0; k < n; ++k) V[k * n + k] = sint[k] * sint[k];
@@ -202,7 +205,7 @@ MinResult minimise(const FGFun& fg, const std::vector<double>& x0, const std::ve
     }
     double sy = 0.0, yy = 0.0;
     for (size_t i = 0; i < n; ++i) { sy += s[i] * y[i]; yy += y[i] * y[i]; }
-    if (it == 0 && sy > 0) {
+    if (it == 0 && sy > 0 && !given_V) {
       // rescale the initial estimate (Nocedal & Wright, eq. 6.20)
       std::fill(V.begin(), V.end(), 0.0);
       for (size_t k = 0; k < n; ++k) V[k * n + k] = sy / yy;
@@ -239,60 +242,99 @@ MinResult minimise(const FGFun& fg, const std::vector<double>& x0, const std::ve
     return res;
   }
   res.status = converged ? GF_OK : GF_ENOCONV;
-  // errors: Hessian in external coordinates by central differences of the gradient
+  res.V = V;
   res.err.assign(n, 0.0);
   res.cov.assign(n * n, 0.0);
-  if (opt.hesse && n > 0) {
-    std::vector<double> H(n * n), gp(n), gm(n), xp(n);
-    bool ok = true;
-    for (size_t k = 0; k < n && ok; ++k) {
-      // step: 1% of the error estimate from V mapped to external units
-      double sig = std::sqrt(std::fabs(V[k * n + k])) * std::fabs(B.der(k, u[k]));
-      double h = sig > 0 ? 1e-2 * sig : 1e-6 * std::max(1.0, std::fabs(res.x[k]));
-      if (B.b(k)) h = std::min(h, 0.25 * std::min(res.x[k] - lo[k], hi[k] - res.x[k]) + 1e-300);
-      xp = res.x;
-      xp[k] += h;
-      double fp, fm;
-      ++calls;
-      if (fg(xp, fp, gp) != GF_OK) ok = false;
-      xp[k] = res.x[k] - h;
-      ++calls;
-      if (ok && fg(xp, fm, gm) != GF_OK) ok = false;
-      for (size_t i = 0; i < n && ok; ++i) H[i * n + k] = (gp[i] - gm[i]) / (2.0 * h);
-    }
-    if (ok) {
-      for (size_t i = 0; i < n; ++i)
-        for (size_t j = i + 1; j < n; ++j) {
-          const double m = 0.5 * (H[i * n + j] + H[j * n + i]);
-          H[i * n + j] = H[j * n + i] = m;
-        }
-      // invert by Gauss-Jordan with partial pivoting
-      std::vector<double> A = H, I(n * n, 0.0);
-      for (size_t k = 0; k < n; ++k) I[k * n + k] = 1.0;
-      for (size_t c = 0; c < n && ok; ++c) {
-        size_t piv = c;
-        for (size_t r = c + 1; r < n; ++r)
-          if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
-        if (A[piv * n + c] == 0.0) { ok = false; break; }
-        if (piv != c)
-          for (size_t j = 0; j < n; ++j) { std::swap(A[c * n + j], A[piv * n + j]); std::swap(I[c * n + j], I[piv * n + j]); }
-        const double d = 1.0 / A[c * n + c];
-        for (size_t j = 0; j < n; ++j) { A[c * n + j] *= d; I[c * n + j] *= d; }
-        for (size_t r = 0; r < n; ++r)
-          if (r != c) {
-            const double m = A[r * n + c];
-            if (m != 0.0)
-              for (size_t j = 0; j < n; ++j) { A[r * n + j] -= m * A[c * n + j]; I[r * n + j] -= m * I[c * n + j]; }
-          }
-      }
-      if (ok) {
-        for (size_t k = 0; k < n * n; ++k) res.cov[k] = 2.0 * opt.up * I[k];
-        for (size_t k = 0; k < n; ++k) res.err[k] = std::sqrt(std::fabs(res.cov[k * n + k]));
-      }
-    }
-  }
+  if (opt.hesse && n > 0) hesse(fg, res.x, V, lo, hi, opt.up, res.err, res.cov, &calls);
   res.calls = calls;
   return res;
+}
+
+bool hesse(const FGFun& fg, const std::vector<double>& x, const std::vector<double>& V,
+           const std::vector<double>& lo, const std::vector<double>& hi, double up,
+           std::vector<double>& err, std::vector<double>& cov, int* calls) {
+  const size_t n = x.size();
+  Bounds B{lo, hi};
+  std::vector<double> H(n * n), gp(n), gm(n), xp(n);
+  for (size_t k = 0; k < n; ++k) {
+    // step: 1% of the error estimate from V mapped to external units
+    const double u = B.inv(k, x[k]);
+    const double sig = std::sqrt(std::fabs(V[k * n + k])) * std::fabs(B.der(k, u));
+    double h = sig > 0 ? 1e-2 * sig : 1e-6 * std::max(1.0, std::fabs(x[k]));
+    if (B.b(k)) h = std::min(h, 0.25 * std::min(x[k] - lo[k], hi[k] - x[k]) + 1e-300);
+    xp = x;
+    xp[k] += h;
+    double fp, fm;
+    ++*calls;
+    if (fg(xp, fp, gp) != GF_OK) return false;
+    xp[k] = x[k] - h;
+    ++*calls;
+    if (fg(xp, fm, gm) != GF_OK) return false;
+    for (size_t i = 0; i < n; ++i) H[i * n + k] = (gp[i] - gm[i]) / (2.0 * h);
+  }
+  for (size_t i = 0; i < n; ++i)
+    for (size_t j = i + 1; j < n; ++j) {
+      const double m = 0.5 * (H[i * n + j] + H[j * n + i]);
+      H[i * n + j] = H[j * n + i] = m;
+    }
+  // invert by Gauss-Jordan with partial pivoting
+  std::vector<double> A = H, I(n * n, 0.0);
+  for (size_t k = 0; k < n; ++k) I[k * n + k] = 1.0;
+  for (size_t c = 0; c < n; ++c) {
+    size_t piv = c;
+    for (size_t r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0) return false;
+    if (piv != c)
+      for (size_t j = 0; j < n; ++j) {
+        std::swap(A[c * n + j], A[piv * n + j]);
+        std::swap(I[c * n + j], I[piv * n + j]);
+      }
+    const double d = 1.0 / A[c * n + c];
+    for (size_t j = 0; j < n; ++j) {
+      A[c * n + j] *= d;
+      I[c * n + j] *= d;
+    }
+    for (size_t r = 0; r < n; ++r)
+      if (r != c) {
+        const double m = A[r * n + c];
+        if (m != 0.0)
+          for (size_t j = 0; j < n; ++j) {
+            A[r * n + j] -= m * A[c * n + j];
+            I[r * n + j] -= m * I[c * n + j];
+          }
+      }
+  }
+  for (size_t k = 0; k < n * n; ++k) cov[k] = 2.0 * up * I[k];
+  for (size_t k = 0; k < n; ++k) err[k] = std::sqrt(std::fabs(cov[k * n + k]));
+  return true;
+}
+
+MinResult minimise_refined(const FGFun* fg_fast, const FGFun& fg_exact,
+                           const std::vector<double>& x0, const std::vector<double>& step,
+                           const std::vector<double>& lo, const std::vector<double>& hi,
+                           const MinOpts& opt) {
+  if (!fg_fast) return minimise(fg_exact, x0, step, lo, hi, opt);
+  MinOpts o1 = opt;
+  o1.tol = std::max(opt.tol, 1e-3);
+  o1.hesse = false;
+  o1.f_noise = opt.f_noise_fast;
+  MinResult r1 = minimise(*fg_fast, x0, step, lo, hi, o1);
+  if (r1.x.empty() || (r1.status != GF_OK && r1.status != GF_ENOCONV)) return r1;
+  MinOpts o2 = opt;
+  o2.hesse = false;
+  o2.f_noise = 0.0;
+  o2.max_calls = std::max(1, opt.max_calls - r1.calls);
+  o2.V0 = &r1.V;
+  MinResult r2 = minimise(fg_exact, r1.x, step, lo, hi, o2);
+  r2.calls += r1.calls;
+  r2.iters += r1.iters;
+  if (r2.x.empty()) return r2;
+  r2.err.assign(r2.x.size(), 0.0);
+  r2.cov.assign(r2.x.size() * r2.x.size(), 0.0);
+  if (opt.hesse && !r2.x.empty())
+    hesse(*fg_fast, r2.x, r2.V, lo, hi, opt.up, r2.err, r2.cov, &r2.calls);
+  return r2;
 }
 
 }  // namespace gfi
@@ -321,9 +363,10 @@ extern "C" int gf_fit(gf_ctx* ctx, const gf_fit_opts* opts, gf_fit_result* res) 
     lo[k] = p.lo;
     hi[k] = p.hi;
   }
-  FGFun fg = [&](const std::vector<double>& x, double& f, std::vector<double>& g) -> int {
-    if (use_grad) return evaluate(ctx, x.data(), &f, g.data());
-    int r = evaluate(ctx, x.data(), &f, nullptr);
+  auto make_fg = [&](bool fp64) -> FGFun {
+    return [&, fp64](const std::vector<double>& x, double& f, std::vector<double>& g) -> int {
+    if (use_grad) return evaluate(ctx, x.data(), &f, g.data(), fp64);
+    int r = evaluate(ctx, x.data(), &f, nullptr, fp64);
     if (r) return r;
     // central differences of the NLL, 2 n extra evaluations
     std::vector<double> xp = x;
@@ -331,17 +374,29 @@ extern "C" int gf_fit(gf_ctx* ctx, const gf_fit_opts* opts, gf_fit_result* res) 
       const double h = 1e-3 * step[k];
       double fp, fm;
       xp[k] = x[k] + h;
-      r = evaluate(ctx, xp.data(), &fp, nullptr);
+      r = evaluate(ctx, xp.data(), &fp, nullptr, fp64);
       if (r) return r;
       xp[k] = x[k] - h;
-      r = evaluate(ctx, xp.data(), &fm, nullptr);
+      r = evaluate(ctx, xp.data(), &fm, nullptr, fp64);
       if (r) return r;
       xp[k] = x[k];
       g[k] = (fp - fm) / (2 * h);
     }
     return GF_OK;
+    };
   };
-  MinResult m = minimise(fg, x0, step, lo, hi, mo);
+  // mixed contexts: FP32 BFGS, then an FP64 polish from the FP32 inverse Hessian
+  // (1D programs evaluate in FP64 in every context: nothing to refine)
+  const bool refine =
+      ctx->precision == GF_MIXED && ctx->is_dalitz && (!opts || opts->refine != 0);
+  // FP32 per-event log P carries ~2e-7 absolute rounding, so the FP32 NLL of n events is
+  // noisy at ~2e-7 sqrt(n): the line search of the FP32 stage ignores differences below
+  // a few times that
+  if (ctx->precision == GF_MIXED && ctx->is_dalitz)
+    mo.f_noise_fast = 1e-6 * std::sqrt((double)ctx->dev.n + 1.0);
+  FGFun fg_fast = make_fg(false), fg_exact = make_fg(ctx->precision == GF_MIXED);
+  MinResult m = refine ? minimise_refined(&fg_fast, fg_exact, x0, step, lo, hi, mo)
+                       : minimise(fg_fast, x0, step, lo, hi, mo);
   res->nll = m.fval;
   res->edm = m.edm;
   res->n_calls = m.calls;

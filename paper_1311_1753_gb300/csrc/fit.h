@@ -10,10 +10,14 @@ struct MinOpts {
   int max_calls = 5000;
   double up = 0.5;
   bool hesse = true;
+  const std::vector<double>* V0 = nullptr;  // starting inverse Hessian (internal coords)
+  double f_noise = 0.0;  // absolute noise of f: differences below it count as no change
+  double f_noise_fast = 0.0;  // the same for fg_fast of minimise_refined
 };
 
 struct MinResult {
   std::vector<double> x, err, cov;
+  std::vector<double> V;  // final inverse-Hessian estimate (internal coordinates)
   double fval = 0.0, edm = 0.0;
   int calls = 0, iters = 0;
   bool converged = false;
@@ -26,5 +30,19 @@ using FGFun = std::function<int(const std::vector<double>&, double&, std::vector
 MinResult minimise(const FGFun& fg, const std::vector<double>& x0, const std::vector<double>& step,
                    const std::vector<double>& lo, const std::vector<double>& hi,
                    const MinOpts& opt);
+
+// Parabolic errors at x: Hessian of f in external coordinates by central differences of
+// the gradient (steps from the internal inverse-Hessian estimate V), cov = 2 up H^-1.
+bool hesse(const FGFun& fg, const std::vector<double>& x, const std::vector<double>& V,
+           const std::vector<double>& lo, const std::vector<double>& hi, double up,
+           std::vector<double>& err, std::vector<double>& cov, int* calls);
+
+// A fit in two precisions: BFGS on fg_fast (FP32 amplitudes) to EDM < max(tol, 1e-3),
+// then BFGS on fg_exact (FP64) from that point and inverse Hessian to EDM < tol; errors
+// from the Hessian of fg_fast.  With fg_fast == nullptr it is a plain minimise().
+MinResult minimise_refined(const FGFun* fg_fast, const FGFun& fg_exact,
+                           const std::vector<double>& x0, const std::vector<double>& step,
+                           const std::vector<double>& lo, const std::vector<double>& hi,
+                           const MinOpts& opt);
 
 }  // namespace gfi

@@ -74,6 +74,7 @@ struct Cols {
 // Faddeeva coefficients (Weideman 1994 rational series), filled on the host.
 struct WeidCoef {
   double L;
+  float Lhi, Llo;                           // L as a double-float pair
   double a[kWeidN + 1];
   float ahi[kWeidN + 1], alo[kWeidN + 1];  // a_n as double-float pairs (hi + lo)
   float Lf;

@@ -266,10 +266,10 @@ __device__ __forceinline__ double eval_leaf(const Instr& I, const double* rec, d
       if (!(t > 0.0)) return 0.0;
       double l, lt = 0.0;
       if (c[1] == 0.5 && !(G && I.gidx[1] >= 0)) {
-        l = sqrt(t) * exp(-c[2] * t) * c[3];
+        l = sqrt(t) * df_exp(-c[2] * t) * c[3];
       } else {
-        lt = log(t);
-        l = exp(fma(c[1], lt, -c[2] * t)) * c[3];
+        lt = df_log(t);
+        l = df_exp(fma(c[1], lt, -c[2] * t)) * c[3];
       }
       if (G) {
         if (I.gidx[0] >= 0) g[I.gidx[0] * bd] += l * (c[2] - c[1] / t - rec[2]);
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(kThreads1D) k_events_1d(
           }
         }
       }
-      const double lp = P.root_log ? s0 : log(s0);
+      const double lp = P.root_log ? s0 : df_log(s0);
       if (MODE == 1) {
         out_logp[i] = lp;
       } else {

@@ -39,6 +39,7 @@ struct Req {
   Clock::time_point t_submit, t_done;
   // evaluation hand-off
   bool want = false, ready = false;
+  bool want64 = false;  // FP64 evaluation (refinement stage of a mixed-precision fit)
   std::vector<double> theta, grad;
   double f = 0.0;
   int eval_rc = GF_OK;
@@ -85,9 +86,11 @@ static void fit_thread(gf_server* S, std::shared_ptr<Req> R) {
     mo.hesse = R->opts.hesse != 0;
   }
   const double tmo = S->opts.wait_timeout_s > 0 ? S->opts.wait_timeout_s : 60.0;
-  FGFun fg = [&](const std::vector<double>& x, double& f, std::vector<double>& g) -> int {
+  auto make_fg = [&](bool fp64) -> FGFun {
+    return [&, fp64](const std::vector<double>& x, double& f, std::vector<double>& g) -> int {
     std::unique_lock<std::mutex> lk(S->mu);
     R->theta = x;
+    R->want64 = fp64;
     R->want = true;
     R->ready = false;
     S->cv_sched.notify_all();
@@ -98,8 +101,15 @@ static void fit_thread(gf_server* S, std::shared_ptr<Req> R) {
     f = R->f;
     g = R->grad;
     return R->eval_rc;
+    };
   };
-  MinResult m = minimise(fg, x0, step, lo, hi, mo);
+  const bool refine = R->ctx->precision == GF_MIXED && R->ctx->is_dalitz &&
+                      (!R->has_opts || R->opts.refine != 0);
+  if (R->ctx->precision == GF_MIXED && R->ctx->is_dalitz)
+    mo.f_noise_fast = 1e-6 * std::sqrt((double)R->ctx->dev.n + 1.0);
+  FGFun fg_fast = make_fg(false), fg_exact = make_fg(R->ctx->precision == GF_MIXED);
+  MinResult m = refine ? minimise_refined(&fg_fast, fg_exact, x0, step, lo, hi, mo)
+                       : minimise(fg_fast, x0, step, lo, hi, mo);
   std::lock_guard<std::mutex> lk(S->mu);
   R->result = std::move(m);
   R->nfree = (int)n;
@@ -164,7 +174,7 @@ static void scheduler(gf_server* S) {
     lk.unlock();
     int64_t nl = 0;
     for (auto& R : batch) {
-      R->eval_rc = evaluate_async(R->ctx, R->theta.data(), true);
+      R->eval_rc = evaluate_async(R->ctx, R->theta.data(), true, R->want64);
       nl += R->ctx->last_launches;
     }
     for (auto& R : batch) {

@@ -34,7 +34,7 @@ class Resonance(C.Structure):
 
 class FitOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_calls", C.c_int), ("use_grad", C.c_int),
-                ("up", C.c_double), ("hesse", C.c_int)]
+                ("up", C.c_double), ("hesse", C.c_int), ("refine", C.c_int)]
 
 
 class FitResult(C.Structure):
@@ -336,12 +336,13 @@ class Context:
         lib.gf_last_eval_stats(self.h, C.byref(ms), C.byref(nl))
         return ms.value, nl.value
 
-    def fit(self, tol=1e-6, max_calls=5000, use_grad=True, up=0.5, hesse=True):
+    def fit(self, tol=1e-6, max_calls=5000, use_grad=True, up=0.5, hesse=True, refine=True):
         nf = len(self.free_params())
         th = np.zeros(max(1, nf))
         err = np.zeros(max(1, nf))
         cov = np.zeros(max(1, nf * nf))
-        o = FitOpts(tol, max_calls, 1 if use_grad else 0, up, 1 if hesse else 0)
+        o = FitOpts(tol, max_calls, 1 if use_grad else 0, up, 1 if hesse else 0,
+                    1 if refine else 0)
         r = FitResult(0.0, 0.0, 0, 0, 0, _dp(th), _dp(err), _dp(cov))
         rc = lib.gf_fit(self.h, C.byref(o), C.byref(r))
         if rc not in (GF_OK, GF_ENOCONV):
@@ -361,9 +362,9 @@ class Server:
         if rc:
             raise GFError(rc, "gf_server_create")
 
-    def submit(self, ctx: Context, ds, root, tol=1e-6, max_calls=5000, hesse=True):
+    def submit(self, ctx: Context, ds, root, tol=1e-6, max_calls=5000, hesse=True, refine=True):
         t = C.c_uint64()
-        o = FitOpts(tol, max_calls, 1, 0.5, 1 if hesse else 0)
+        o = FitOpts(tol, max_calls, 1, 0.5, 1 if hesse else 0, 1 if refine else 0)
         rc = lib.gf_server_submit(self.h, ctx.h, ds, root, C.byref(o), C.byref(t))
         if rc:
             raise GFError(rc, "gf_server_submit")

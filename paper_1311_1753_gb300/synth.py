@@ -87,13 +87,21 @@ def dalitz_box(M=D0_MASS, m1=PIC_MASS, m2=PIC_MASS, m3=PI0_MASS):
 def dalitz_model_draw(seed: int = SEED_DALITZ_MODEL, nres: int = 8):
     """Seeded resonance list: mass in U(0.5, 1.7) GeV, width in U(0.05, 0.4) GeV, spin in
     U{0,1,2}, channel r mod 3, coefficient magnitude rho in U(0.5, 1.5) and phase in
-    U(-pi, pi).  The caller rescales the magnitudes by its own normalisation integrals."""
+    U(-pi, pi).  A draw whose mass lies within the sum of the widths of an earlier
+    resonance with the same channel and spin is redrawn (two such resonances are nearly
+    the same amplitude, which leaves their masses and widths without a unique fit).  The
+    caller rescales the magnitudes by its own normalisation integrals."""
     rng = _rng(seed)
     res = []
     for r in range(nres):
-        m0 = rng.uniform(0.5, 1.7)
-        g0 = rng.uniform(0.05, 0.4)
-        spin = int(rng.integers(0, 3))
+        while True:
+            m0 = rng.uniform(0.5, 1.7)
+            g0 = rng.uniform(0.05, 0.4)
+            spin = int(rng.integers(0, 3))
+            clash = any(q["channel"] == r % 3 and q["spin"] == spin
+                        and abs(q["m0"] - m0) < q["g0"] + g0 for q in res)
+            if not clash:
+                break
         rho = rng.uniform(0.5, 1.5)
         phi = rng.uniform(-math.pi, math.pi)
         res.append(dict(channel=r % 3, spin=spin, m0=m0, g0=g0, rho=rho, phi=phi))

@@ -133,7 +133,7 @@ def test_config4_mixed_fit_small(gf):
     for k, pid in enumerate(ctx.free_params()):
         ctx.set_value(pid, start[k])
     ctx.set_data(root, obs, [s12, s13])
-    r = ctx.fit(tol=1e-5)
+    r = ctx.fit(tol=1e-8)  # FP32 BFGS to EDM 1e-4, then the FP64 refinement to 1e-8
     step = np.array([0.005 if k % 4 < 2 else 0.01 for k in free])
     lo_b = np.array([0.4 if k % 4 == 0 else 0.01 if k % 4 == 1 else 0.0 for k in free])
     hi_b = np.array([1.75 if k % 4 == 0 else 0.6 if k % 4 == 1 else 0.0 for k in free])
