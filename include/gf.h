@@ -236,6 +236,31 @@ int gf_last_eval_stats(gf_ctx* ctx, double* kernel_ms, int* launches);
  * alone (the event pass, CUDA events on the context's stream). */
 int gf_last_eval_times(gf_ctx* ctx, double* total_ms, double* stream_ms);
 
+/* ---- allocation-free evaluation -------------------------------------------------------
+ * The paper has no counterpart to this call.  It is for callers that cannot call
+ * cudaMalloc: code whose device memory is handed out by a pool or framework that grants
+ * no extra buffers, or that must not grow the process's device footprint once running.
+ * gf_nll_noalloc computes the same NLL as gf_nll for the 1D PDF tree rooted at `root` of
+ * a context that holds only the model (gf_create and node declarations allocate no device
+ * memory; no gf_set_data is needed), over caller-owned device columns, and allocates
+ * nothing: its working buffers (theta, normalisation records, block partials, counters)
+ * are one static device array of 448 KiB compiled into the library, which every GPU that
+ * loads the library holds until the process exits.
+ *   obs[k], dev_cols[k]: observable id and device column of n doubles (16-byte aligned);
+ *   theta: host array of the free parameters (gf_free_params order);
+ *   nll_dev: one double in device memory, written when the context's stream reaches it
+ *            (the call returns after queueing; synchronise the stream before reading).
+ * Limits: at most 256 parameters and 64 observables in the context, 24 free parameters,
+ * 262,144 normalisation-grid bins in total; beyond them the call returns GF_EINVAL with a
+ * message (gf_last_error).  Dalitz nodes are not accepted.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current: make that first call before any stream capture.  Every call
+ * reuses the same array, which keeps the last call's contents (the call clears what must
+ * start at zero): calls whose GPU work overlaps -- other streams, other host threads --
+ * race on it and must be serialised by the caller. */
+int gf_nll_noalloc(gf_ctx* ctx, int root, int nobs, const int* obs, int64_t n,
+                   const double* const* dev_cols, const double* theta, double* nll_dev);
+
 #ifdef __cplusplus
 }
 #endif

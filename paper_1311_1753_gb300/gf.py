@@ -101,6 +101,7 @@ def _load():
         "gf_last_eval_stats": ([vp, _D, _I], C.c_int),
         "gf_last_eval_times": ([vp, _D, _D], C.c_int),
         "gf_update_data": ([vp, C.c_int64, C.POINTER(_D)], C.c_int),
+        "gf_nll_noalloc": ([vp, C.c_int, C.c_int, _I, C.c_int64, C.POINTER(vp), _D, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -324,6 +325,15 @@ class Context:
     def update_data_ptrs(self, n, host_ptrs):
         ptrs = (_D * len(host_ptrs))(*[C.cast(C.c_void_p(p), _D) for p in host_ptrs])
         self._ck(lib.gf_update_data(self.h, n, ptrs), "gf_update_data")
+
+    def nll_noalloc(self, root, obs, n, dev_ptrs, theta, out_dev_ptr):
+        """gf_nll_noalloc: NLL over caller-owned device columns into a caller-owned device
+        double, with no allocation (queued on the context's stream)."""
+        ids = (C.c_int * len(obs))(*obs)
+        ptrs = (C.c_void_p * len(dev_ptrs))(*dev_ptrs)
+        th = _f64(theta)
+        self._ck(lib.gf_nll_noalloc(self.h, root, len(obs), ids, n, ptrs, _dp(th),
+                                    C.c_void_p(out_dev_ptr)), "gf_nll_noalloc")
 
     def last_eval_times(self):
         t, s = C.c_double(), C.c_double()
