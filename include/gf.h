@@ -182,9 +182,10 @@ typedef struct {
   double up;       /* error definition (0.5 for a negative log-likelihood; <= 0 -> 0.5) */
   int hesse;       /* 1: covariance from the Hessian by differences of the gradient */
   int refine;      /* GF_MIXED contexts: 1 (default when opts is NULL) runs BFGS on the FP32
-                      likelihood to EDM < max(tol, 1e-3), then continues in FP64 from that
-                      point and inverse-Hessian estimate to EDM < tol; errors from the
-                      FP32 Hessian.  0: FP32 only. */
+                      likelihood to EDM < max(tol, 1) (or until its rounding noise stops
+                      the line search), then continues in FP64 from that point and
+                      inverse-Hessian estimate to EDM < tol; errors from the FP32
+                      Hessian.  0: FP32 only. */
 } gf_fit_opts;
 typedef struct {
   double nll;      /* NLL at the minimum */
@@ -195,6 +196,7 @@ typedef struct {
   double* theta;   /* caller-allocated, n_free: fitted values (external units) */
   double* err;     /* caller-allocated, n_free, or NULL: parabolic errors */
   double* cov;     /* caller-allocated, n_free^2, or NULL: covariance matrix */
+  int n_calls_fast; /* of n_calls, those made on the FP32 likelihood (refined fits) */
 } gf_fit_result;
 /* Minimise from the parameters' current values; the fitted values become the current
  * values.  Returns the same status as res->status. */

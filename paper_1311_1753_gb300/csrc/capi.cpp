@@ -137,6 +137,9 @@ static void free_dev(gf_ctx* ctx) {
   if (d.ev1) cudaEventDestroy(d.ev1);
   if (d.evm) cudaEventDestroy(d.evm);
   cudaFree(d.flag);
+  cudaFree(d.tick_desc);
+  for (auto& g : d.graph)
+    if (g) cudaGraphExecDestroy(g);
   d = DevState();
 }
 
@@ -588,6 +591,11 @@ namespace gfi {
 
 int ensure_compiled(gf_ctx* ctx) {
   if (ctx->compiled) return GF_OK;
+  for (auto& g : ctx->dev.graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
   if (ctx->root < 0 || !valid_node(ctx, ctx->root))
     return set_error(ctx, GF_ESTATE, "no data set: call gf_set_data first");
   ctx->free_ids.clear();
@@ -901,7 +909,7 @@ extern "C" int gf_set_data_device(gf_ctx* ctx, int root, int nobs, const int* ob
 }
 
 // ---- evaluation ----------------------------------------------------------------------------------------------
-static int upload_theta(gf_ctx* ctx, const double* theta) {
+static int fill_theta_host(gf_ctx* ctx, const double* theta) {
   DevState& d = ctx->dev;
   const int np = (int)ctx->pars.size();
   for (int i = 0; i < np; ++i) d.h_theta[i] = ctx->pars[i].value;
@@ -909,10 +917,45 @@ static int upload_theta(gf_ctx* ctx, const double* theta) {
     if (!std::isfinite(theta[k])) return set_error(ctx, GF_EINVAL, "non-finite theta");
     d.h_theta[ctx->free_ids[k]] = theta[k];
   }
+  return GF_OK;
+}
+
+static int upload_theta(gf_ctx* ctx, const double* theta) {
+  int rc = fill_theta_host(ctx, theta);
+  if (rc) return rc;
+  DevState& d = ctx->dev;
+  const int np = (int)ctx->pars.size();
   if (np > 0)
     CK(cudaMemcpyAsync(d.theta, d.h_theta, sizeof(double) * np, cudaMemcpyHostToDevice,
                        ctx->stream));
   return GF_OK;
+}
+
+// Dalitz: true when no cache needs (re)building for this evaluation (mask, per-event and
+// grid columns of fixed-shape resonances, Gram matrix); *direct: free shapes present.
+static bool dalitz_is_steady(gf_ctx* ctx, bool mixed, bool* direct) {
+  DevState& d = ctx->dev;
+  const DalitzPlan& D = ctx->dplan;
+  const bool second = ctx->precision == GF_MIXED && !mixed;
+  const std::vector<double>& cm0 = second ? d.ev64_m0 : d.ev_m0;
+  const std::vector<double>& cg0 = second ? d.ev64_g0 : d.ev_g0;
+  *direct = false;
+  if (!d.mask_built || cm0.size() != (size_t)D.nres || d.col_m0.size() != (size_t)D.nres)
+    return false;
+  int ncached = 0;
+  for (int r = 0; r < D.nres; ++r) {
+    const DalitzRes& R = D.res[r];
+    const double m0 = d.h_theta[R.p_m0], g0 = d.h_theta[R.p_g0];
+    if (R.ev_cached >= 0) {
+      ++ncached;
+      if (!(cm0[r] == m0 && cg0[r] == g0) || !(d.col_m0[r] == m0 && d.col_g0[r] == g0))
+        return false;
+    } else {
+      *direct = true;
+    }
+  }
+  if (second && ncached > 0 && !d.ev_cache64) return false;
+  return *direct || d.gram_valid;
 }
 
 static DalitzBufs dalitz_bufs(gf_ctx* ctx, double* out_logp, bool mixed = true) {
@@ -1013,22 +1056,19 @@ static int dalitz_prepare(gf_ctx* ctx, int* norm_mode, int* launches, bool mixed
 
 namespace gfi {
 
-int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64) {
-  int rc = ensure_compiled(ctx);
-  if (rc) return rc;
+// The evaluation after any cache maintenance: theta upload (if with_upload), the
+// normalisation and event kernels, the result and data-check downloads, timing events.
+static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool with_upload,
+                          int* launches) {
   DevState& d = ctx->dev;
-  if (!d.theta) return set_error(ctx, GF_ESTATE, "no data set");
-  CK(cudaSetDevice(ctx->device));
-  rc = upload_theta(ctx, theta);
-  if (rc) return rc;
-  int launches = 0;
-  CK(cudaEventRecord(d.ev0, ctx->stream));
   const int nf = (int)ctx->free_ids.size();
+  const int np = (int)ctx->pars.size();
+  if (with_upload && np > 0)
+    CK(cudaMemcpyAsync(d.theta, d.h_theta, sizeof(double) * np, cudaMemcpyHostToDevice,
+                       ctx->stream));
+  CK(cudaEventRecord(d.ev0, ctx->stream));
   if (ctx->is_dalitz) {
-    int mode = DN_GRAM;
     const bool mixed = ctx->precision == GF_MIXED && !fp64;
-    rc = dalitz_prepare(ctx, &mode, &launches, mixed);
-    if (rc) return rc;
     DalitzBufs B = dalitz_bufs(ctx, nullptr, mixed);
     if (mode == DN_DIRECT) {
       const int ncell_blocks = (int)std::min<int64_t>(
@@ -1037,18 +1077,18 @@ int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64) {
       // the normalisation integral and its gradient in FP64 in every mode
       CK(launch_dalitz_norm_direct(ctx->dplan, false, grad, d.theta, B, ncell_blocks,
                                    ctx->stream));
-      launches++;
+      (*launches)++;
     }
     CK(cudaEventRecord(d.evm, ctx->stream));
     CK(launch_dalitz_events(ctx->dplan, mixed, grad, false, mode, d.theta, B, d.nblocks,
                             ctx->stream));
-    launches++;
+    (*launches)++;
   } else {
     const WeidCoef& W = weideman();
     if (ctx->has_grid) {
       CK(launch_norm_1d(ctx->prog, W, d.theta, d.partials2, d.counters + 1, d.derived,
                         ctx->stream));
-      launches++;
+      (*launches)++;
     }
     Cols cols{};
     for (int k = 0; k < d.nobs; ++k) cols.c[k] = d.cols[k];
@@ -1056,7 +1096,7 @@ int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64) {
     CK(launch_events_1d(ctx->prog, W, cols, d.n, d.theta, d.derived, d.partials, d.counters,
                         d.result, nullptr, grad, false, ctx->has_grid ? 0 : 1, d.nblocks,
                         ctx->stream));
-    launches++;
+    (*launches)++;
   }
   CK(cudaEventRecord(d.ev1, ctx->stream));
   CK(cudaMemcpyAsync(d.h_result, d.result, sizeof(double) * (1 + (grad ? nf : 0)),
@@ -1064,6 +1104,57 @@ int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64) {
   // data-check flag rides along in the last pinned slot
   CK(cudaMemcpyAsync(reinterpret_cast<int*>(d.h_result + 63), d.flag, sizeof(int),
                      cudaMemcpyDeviceToHost, ctx->stream));
+  return GF_OK;
+}
+
+int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64) {
+  int rc = ensure_compiled(ctx);
+  if (rc) return rc;
+  DevState& d = ctx->dev;
+  if (!d.theta) return set_error(ctx, GF_ESTATE, "no data set");
+  CK(cudaSetDevice(ctx->device));
+  rc = fill_theta_host(ctx, theta);
+  if (rc) return rc;
+  // steady state: replay the evaluation graph of this (grad, fp64, normalisation mode)
+  bool direct = false;
+  const bool mixed = ctx->precision == GF_MIXED && !fp64;
+  const bool steady = !ctx->is_dalitz || dalitz_is_steady(ctx, mixed, &direct);
+  if (steady) {
+    const int key = (grad ? 1 : 0) | (fp64 ? 2 : 0) | (direct ? 4 : 0);
+    int launches = 0;
+    if (!d.graph[key]) {
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue_steady(ctx, grad, fp64, direct ? DN_DIRECT : DN_GRAM, true, &launches);
+      cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&d.graph[key], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        d.graph[key] = nullptr;
+        return cuda_fail(ctx, e, "cudaGraphInstantiate");
+      }
+    } else {
+      launches = (ctx->is_dalitz ? (direct ? 2 : 1) : (ctx->has_grid ? 2 : 1));
+    }
+    CK(cudaGraphLaunch(d.graph[key], ctx->stream));
+    ctx->last_launches = launches;
+    return GF_OK;
+  }
+  // cache maintenance first (Dalitz), then the evaluation
+  const int np = (int)ctx->pars.size();
+  if (np > 0)
+    CK(cudaMemcpyAsync(d.theta, d.h_theta, sizeof(double) * np, cudaMemcpyHostToDevice,
+                       ctx->stream));
+  int launches = 0, mode = DN_GRAM;
+  rc = dalitz_prepare(ctx, &mode, &launches, mixed);
+  if (rc) return rc;
+  rc = enqueue_steady(ctx, grad, fp64, mode, false, &launches);
+  if (rc) return rc;
   ctx->last_launches = launches;
   return GF_OK;
 }
@@ -1094,6 +1185,73 @@ int evaluate_finish(gf_ctx* ctx, double* nll, double* grad, bool grad_wanted) {
     return set_error(ctx, GF_ENONFINITE, "non-finite likelihood: some P_i <= 0 or not finite");
   }
   *nll = v;
+  return GF_OK;
+}
+
+void fill_theta_all(const gf_ctx* ctx, const double* theta, double* out) {
+  const int np = (int)ctx->pars.size();
+  for (int i = 0; i < np; ++i) out[i] = ctx->pars[i].value;
+  for (size_t k = 0; k < ctx->free_ids.size(); ++k) out[ctx->free_ids[k]] = theta[k];
+}
+
+int tick_prepare(gf_ctx* ctx) {
+  DevState& d = ctx->dev;
+  if (d.tick_desc) return d.tick_kind;
+  if (!ctx->compiled || !d.theta || d.n <= 0) return 0;
+  CK(cudaSetDevice(ctx->device));
+  if (!ctx->is_dalitz) {
+    Fit1D F{};
+    F.P = ctx->prog;
+    for (int k = 0; k < d.nobs; ++k) F.cols.c[k] = d.cols[k];
+    F.n = d.n;
+    F.derived = d.derived;
+    F.partials = d.partials;
+    F.partials_norm = d.partials2;
+    F.counter_ev = d.counters;
+    F.counter_norm = d.counters + 1;
+    F.analytic_only = ctx->has_grid ? 0 : 1;
+    CK(cudaMalloc(&d.tick_desc, sizeof(F)));
+    CK(cudaMemcpy(d.tick_desc, &F, sizeof(F), cudaMemcpyHostToDevice));
+    d.tick_kind = 1;
+    return 1;
+  }
+  // Dalitz: only with every shape fixed (Gram normalisation) and the caches built
+  const DalitzPlan& D = ctx->dplan;
+  for (int r = 0; r < D.nres; ++r)
+    if (D.res[r].ev_cached < 0) return 0;
+  if (!d.gram_valid) return 0;
+  const bool mixed = ctx->precision == GF_MIXED;
+  for (int r = 0; r < D.nres; ++r)
+    if (!(d.ev_m0.size() == (size_t)D.nres && d.ev_m0[r] == d.h_theta[D.res[r].p_m0])) return 0;
+  FitDz F{};
+  F.D = D;
+  F.s12 = d.cols[0];
+  F.s13 = d.cols[1];
+  F.sf = d.fcols;
+  F.n = d.n;
+  F.ev_cache = d.ev_cache;
+  F.gram = d.gram;
+  F.partials = d.partials;
+  F.counter = d.counters;
+  F.cache_wide = mixed ? 0 : 1;
+  CK(cudaMalloc(&d.tick_desc, sizeof(F)));
+  CK(cudaMemcpy(d.tick_desc, &F, sizeof(F), cudaMemcpyHostToDevice));
+  d.tick_kind = 2;
+  return 2;
+}
+
+int tick_finish(gf_ctx* ctx, const double* res, double* nll, double* grad) {
+  const int nf = (int)ctx->free_ids.size();
+  bool finite = std::isfinite(res[0]);
+  for (int k = 0; k < nf; ++k) {
+    grad[k] = res[1 + k];
+    finite = finite && std::isfinite(grad[k]);
+  }
+  if (!finite) {
+    *nll = INFINITY;
+    return set_error(ctx, GF_ENONFINITE, "non-finite likelihood: some P_i <= 0 or not finite");
+  }
+  *nll = res[0];
   return GF_OK;
 }
 

@@ -67,6 +67,9 @@ struct DevState {
   bool gram_valid = false;
   bool mask_built = false;
   // timing
+  cudaGraphExec_t graph[8] = {};      // steady-state evaluation graphs: grad | fp64 << 1 | direct << 2
+  void* tick_desc = nullptr;          // Fit1D / FitDz for batched ticks (device)
+  int tick_kind = 0;                  // 0: none, 1: 1D, 2: Dalitz (Gram normalisation)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;  // eval start, stream kernel, end
   int* flag = nullptr;                // device-side data check (0 = ok)
 };
@@ -116,6 +119,13 @@ int evaluate(gf_ctx* ctx, const double* theta, double* nll, double* grad, bool f
 int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64 = false);
 int evaluate_finish(gf_ctx* ctx, double* nll, double* grad, bool grad_wanted);
 size_t device_bytes_for(const gf_ctx* ctx, int root, int64_t n);
+// Batched ticks: build the context's device descriptor once it has been evaluated (returns
+// 0 if the context cannot join a batch: Dalitz with free shapes, or not evaluated yet);
+// theta_all for theta; the 1 + nfree results of a batched evaluation checked as in
+// evaluate_finish.
+int tick_prepare(gf_ctx* ctx);
+void fill_theta_all(const gf_ctx* ctx, const double* theta, double* out);
+int tick_finish(gf_ctx* ctx, const double* res, double* nll, double* grad);
 int nfree(const gf_ctx* ctx);
 const WeidCoef& weideman();
 }  // namespace gfi

@@ -85,17 +85,21 @@ __device__ inline void reduce_partials(const double* partials, int nblk, int str
 // Last-block pattern: every block publishes its partial, then bumps a counter; the
 // block that takes the last ticket sees every partial and finishes the reduction.
 // The counter is reset by that block, so the next launch starts from zero.
-__device__ __forceinline__ bool arrive_last(unsigned* counter, int* flag_smem) {
+__device__ __forceinline__ bool arrive_last_of(unsigned* counter, unsigned expected,
+                                               int* flag_smem) {
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned t = atomicAdd(counter, 1u);
-    *flag_smem = (t == gridDim.x * gridDim.y - 1) ? 1 : 0;
+    *flag_smem = (t == expected - 1) ? 1 : 0;
   }
   __syncthreads();
   const bool last = *flag_smem != 0;
   if (last) __threadfence();
   return last;
+}
+__device__ __forceinline__ bool arrive_last(unsigned* counter, int* flag_smem) {
+  return arrive_last_of(counter, gridDim.x * gridDim.y, flag_smem);
 }
 
 // ---- Faddeeva function w(z) = exp(-z^2) erfc(-iz), Im z >= 0 ---------------------------

@@ -127,7 +127,8 @@ MinResult minimise(const FGFun& fg, const std::vector<double>& x0, const std::ve
     }
     // strong-Wolfe line search along p
     const double c1 = 1e-4, c2 = 0.9;
-    const double fn = opt.f_noise;  // differences below the noise count as no change
+    const double fn = opt.f_noise_rel * std::fabs(f);  // differences below the noise
+                                                        // count as no change
     auto phi = [&](double a, double& fa, double& da, std::vector<double>& ga) -> int {
       for (size_t i = 0; i < n; ++i) un[i] = u[i] + a * p[i];
       int r = eval(un, fa, ga);
@@ -316,24 +317,49 @@ MinResult minimise_refined(const FGFun* fg_fast, const FGFun& fg_exact,
                            const MinOpts& opt) {
   if (!fg_fast) return minimise(fg_exact, x0, step, lo, hi, opt);
   MinOpts o1 = opt;
-  o1.tol = std::max(opt.tol, 1e-3);
+  o1.tol = std::max(opt.tol, 1.0);
   o1.hesse = false;
-  o1.f_noise = opt.f_noise_fast;
+  o1.f_noise_rel = opt.f_noise_rel_fast;
   MinResult r1 = minimise(*fg_fast, x0, step, lo, hi, o1);
   if (r1.x.empty() || (r1.status != GF_OK && r1.status != GF_ENOCONV)) return r1;
   MinOpts o2 = opt;
   o2.hesse = false;
-  o2.f_noise = 0.0;
+  o2.f_noise_rel = 0.0;
   o2.max_calls = std::max(1, opt.max_calls - r1.calls);
-  o2.V0 = &r1.V;
+  // curvature for the FP64 stage: the FP32 Hessian at the hand-over point, mapped to
+  // internal coordinates (V = D^-1 H_ext^-1 D^-1, D = dext/du); BFGS's own estimate
+  // after a few FP32 iterations is too rough for 30 parameters
+  const size_t n = r1.x.size();
+  std::vector<double> e1(n), c1(n * n), V0 = r1.V;
+  int hc1 = 0;
+  if (n > 0 && hesse(*fg_fast, r1.x, r1.V, lo, hi, opt.up, e1, c1, &hc1)) {
+    Bounds B{lo, hi};
+    std::vector<double> d(n);
+    for (size_t k = 0; k < n; ++k) d[k] = B.der(k, B.inv(k, r1.x[k]));
+    bool ok = true;
+    for (size_t i = 0; i < n && ok; ++i)
+      for (size_t j = 0; j < n; ++j) {
+        const double v = c1[i * n + j] / (2.0 * opt.up) / (d[i] * d[j]);
+        if (!std::isfinite(v)) ok = false;
+        V0[i * n + j] = v;
+      }
+    if (!ok) V0 = r1.V;
+  }
+  r1.calls += hc1;
+  o2.V0 = &V0;
   MinResult r2 = minimise(fg_exact, r1.x, step, lo, hi, o2);
+  r2.calls_fast = r1.calls;
   r2.calls += r1.calls;
   r2.iters += r1.iters;
   if (r2.x.empty()) return r2;
   r2.err.assign(r2.x.size(), 0.0);
   r2.cov.assign(r2.x.size() * r2.x.size(), 0.0);
-  if (opt.hesse && !r2.x.empty())
-    hesse(*fg_fast, r2.x, r2.V, lo, hi, opt.up, r2.err, r2.cov, &r2.calls);
+  if (opt.hesse && !r2.x.empty()) {
+    int hc = 0;
+    hesse(*fg_fast, r2.x, r2.V, lo, hi, opt.up, r2.err, r2.cov, &hc);
+    r2.calls += hc;
+    r2.calls_fast += hc;
+  }
   return r2;
 }
 
@@ -389,11 +415,6 @@ extern "C" int gf_fit(gf_ctx* ctx, const gf_fit_opts* opts, gf_fit_result* res) 
   // (1D programs evaluate in FP64 in every context: nothing to refine)
   const bool refine =
       ctx->precision == GF_MIXED && ctx->is_dalitz && (!opts || opts->refine != 0);
-  // FP32 per-event log P carries ~2e-7 absolute rounding, so the FP32 NLL of n events is
-  // noisy at ~2e-7 sqrt(n): the line search of the FP32 stage ignores differences below
-  // a few times that
-  if (ctx->precision == GF_MIXED && ctx->is_dalitz)
-    mo.f_noise_fast = 1e-6 * std::sqrt((double)ctx->dev.n + 1.0);
   FGFun fg_fast = make_fg(false), fg_exact = make_fg(ctx->precision == GF_MIXED);
   MinResult m = refine ? minimise_refined(&fg_fast, fg_exact, x0, step, lo, hi, mo)
                        : minimise(fg_fast, x0, step, lo, hi, mo);
@@ -401,6 +422,7 @@ extern "C" int gf_fit(gf_ctx* ctx, const gf_fit_opts* opts, gf_fit_result* res) 
   res->edm = m.edm;
   res->n_calls = m.calls;
   res->n_iter = m.iters;
+  res->n_calls_fast = m.calls_fast;
   res->status = m.status;
   if (!m.x.empty()) {
     for (size_t k = 0; k < n; ++k) {

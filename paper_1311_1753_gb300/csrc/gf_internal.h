@@ -107,4 +107,44 @@ struct DalitzPlan {
   DalitzRes res[kMaxRes];
 };
 
+// ---- batched evaluation of many fits (one fit-server tick) ----------------------------
+// Per-fit descriptors live in device memory; a tick's work list holds one TickItem per fit
+// per launch: items item0 .. item0 + nitems - 1 of the launch are that fit's virtual
+// blocks 0 .. nitems - 1, which process exactly the events of the fit's standalone
+// blocks, so its result is the same bits alone or in the batch.
+struct Fit1D {
+  Program P;
+  Cols cols;
+  int64_t n;
+  double* derived;
+  double* partials;
+  double* partials_norm;
+  unsigned* counter_ev;
+  unsigned* counter_norm;
+  int analytic_only;
+  int pad;
+};
+
+struct FitDz {
+  DalitzPlan D;
+  const double* s12;
+  const double* s13;
+  const float* sf;
+  int64_t n;
+  const void* ev_cache;
+  const double* gram;
+  double* partials;
+  unsigned* counter;
+  int cache_wide;
+  int pad;
+};
+
+struct TickItem {
+  const void* fit;       // Fit1D* or FitDz* (device)
+  const double* theta;   // this fit's theta_all for this tick (device)
+  double* result;        // its 1 + nfree results (device)
+  int item0;             // first item of this fit in the launch
+  int nitems;            // its virtual grid
+};
+
 }  // namespace gfi

@@ -164,26 +164,25 @@ __device__ inline void make_coefs(const Program& P, const double* th, double* co
 // ---- normalisation grid -----------------------------------------------------------------
 // One block per (grid leaf, chunk of kThreads bins): each thread takes one midpoint.
 // partials: [block][4] = (sum r, sum dr/dp0, dr/dp1, dr/dp2).
-__global__ void __launch_bounds__(kThreads) k_norm_1d(const Program P, const WeidCoef W,
-                                                      const double* __restrict__ theta,
-                                                      double* __restrict__ partials,
-                                                      unsigned* __restrict__ counter,
-                                                      double* __restrict__ derived) {
-  __shared__ double red[32];
-  __shared__ int last;
-  __shared__ double sums[kMaxLeaf][4];
+// Body of one (virtual) block vb of the vgrid blocks of a normalisation launch; the last
+// block to arrive finishes.  Shared scratch: red[32], *last, sums[kMaxLeaf][4].
+__device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& W,
+                                              const double* __restrict__ theta,
+                                              double* __restrict__ partials,
+                                              unsigned* __restrict__ counter,
+                                              double* __restrict__ derived, int vb, int vgrid,
+                                              double* red, int* last, double (*sums)[4]) {
   // locate this block's leaf
   int li = -1;
   for (int l = 0; l < P.nleaf; ++l) {
     const LeafDesc& L = P.leaf[l];
-    if (L.nbins > 0 && (int)blockIdx.x >= L.grid_first_block &&
-        (int)blockIdx.x < L.grid_first_block + L.grid_nblocks)
+    if (L.nbins > 0 && vb >= L.grid_first_block && vb < L.grid_first_block + L.grid_nblocks)
       li = l;
   }
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   if (li >= 0) {
     const LeafDesc& L = P.leaf[li];
-    const int b = (blockIdx.x - L.grid_first_block) * blockDim.x + threadIdx.x;
+    const int b = (vb - L.grid_first_block) * blockDim.x + threadIdx.x;
     if (b < L.nbins) {
       const double h = (L.hi - L.lo) / L.nbins;
       const double x = L.lo + (b + 0.5) * h;
@@ -199,9 +198,9 @@ __global__ void __launch_bounds__(kThreads) k_norm_1d(const Program P, const Wei
   }
   for (int k = 0; k < 4; ++k) {
     const double r = block_sum(v[k], red);
-    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * 4 + k] = r;
+    if (threadIdx.x == 0) partials[(size_t)vb * 4 + k] = r;
   }
-  if (!arrive_last(counter, &last)) return;
+  if (!arrive_last_of(counter, (unsigned)vgrid, last)) return;
   // last block: per leaf, fixed-order sum over its chunks, then every leaf record
   for (int l = 0; l < P.nleaf; ++l) {
     const LeafDesc& L = P.leaf[l];
@@ -224,6 +223,17 @@ __global__ void __launch_bounds__(kThreads) k_norm_1d(const Program P, const Wei
     make_coefs(P, theta, derived + kMaxLeaf * kLeafRec);
     *counter = 0u;
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_norm_1d(const Program P, const WeidCoef W,
+                                                      const double* __restrict__ theta,
+                                                      double* __restrict__ partials,
+                                                      unsigned* __restrict__ counter,
+                                                      double* __restrict__ derived) {
+  __shared__ double red[32];
+  __shared__ int last;
+  __shared__ double sums[kMaxLeaf][4];
+  norm_1d_block(P, W, theta, partials, counter, derived, blockIdx.x, gridDim.x, red, &last, sums);
 }
 
 // ---- event-side leaf evaluation ------------------------------------------------------------
@@ -296,16 +306,16 @@ __device__ __forceinline__ double eval_leaf(const Instr& I, const double* rec, d
 
 // ---- event stream ------------------------------------------------------------------------
 // MODE 0: reduce -log P (and gradient) to result[0 .. nfree]; MODE 1: store log P_i.
+// Body of one (virtual) block vb of the vgrid blocks of an event launch.  Shared
+// scratch: dyn (G: (kMaxStack + 1) nfree blockDim doubles), rec (leaf records), red[32],
+// *last.
 template <bool G, int MODE>
-__global__ void __launch_bounds__(kThreads1D) k_events_1d(
-    const Program P, const WeidCoef W, const Cols cols, const int64_t n,
+__device__ __forceinline__ void events_1d_block(
+    const Program& P, const WeidCoef& W, const Cols& cols, const int64_t n,
     const double* __restrict__ theta, const double* __restrict__ derived_g,
     double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
-    double* __restrict__ out_logp, const int analytic_only) {
-  extern __shared__ double dyn[];  // G: (kMaxStack + 1) * nfree * blockDim doubles
-  __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
-  __shared__ double red[32];
-  __shared__ int last;
+    double* __restrict__ out_logp, const int analytic_only, const int vb, const int vgrid,
+    double* dyn, double* rec, double* red, int* last) {
   const int bd = blockDim.x, tid = threadIdx.x;
   const int nf = P.nfree;
   // leaf records: from the norm kernel, or (analytic leaves only) built here per block
@@ -323,8 +333,8 @@ __global__ void __launch_bounds__(kThreads1D) k_events_1d(
   double acc = 0.0;
 
   const int64_t npairs = (n + 1) >> 1;
-  const int64_t stride = (int64_t)gridDim.x * bd;
-  for (int64_t pr = (int64_t)blockIdx.x * bd + tid; pr < npairs; pr += stride) {
+  const int64_t stride = (int64_t)vgrid * bd;
+  for (int64_t pr = (int64_t)vb * bd + tid; pr < npairs; pr += stride) {
     double2 xv[kMaxObs];
     const bool full = 2 * pr + 1 < n;  // the last pair of an odd n holds one event
 #pragma unroll
@@ -416,11 +426,93 @@ __global__ void __launch_bounds__(kThreads1D) k_events_1d(
   for (int k = 0; k < m; ++k) {
     const double v = (k == 0) ? acc : gacc[(k - 1) * bd];
     const double r = block_sum(v, red);
-    if (tid == 0) partials[(size_t)blockIdx.x * stride_p + k] = r;
+    if (tid == 0) partials[(size_t)vb * stride_p + k] = r;
   }
-  if (!arrive_last(counter, &last)) return;
-  reduce_partials(partials, gridDim.x, stride_p, m, result, red);
+  if (!arrive_last_of(counter, (unsigned)vgrid, last)) return;
+  reduce_partials(partials, vgrid, stride_p, m, result, red);
   if (tid == 0) *counter = 0u;
+}
+
+template <bool G, int MODE>
+__global__ void __launch_bounds__(kThreads1D) k_events_1d(
+    const Program P, const WeidCoef W, const Cols cols, const int64_t n,
+    const double* __restrict__ theta, const double* __restrict__ derived_g,
+    double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
+    double* __restrict__ out_logp, const int analytic_only) {
+  extern __shared__ double dyn[];  // G: (kMaxStack + 1) * nfree * blockDim doubles
+  __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
+  __shared__ double red[32];
+  __shared__ int last;
+  events_1d_block<G, MODE>(P, W, cols, n, theta, derived_g, partials, counter, result, out_logp,
+                           analytic_only, blockIdx.x, gridDim.x, dyn, rec, red, &last);
+}
+
+// ---- batched tick: every waiting 1D fit in one persistent launch -----------------------
+// Shared by the two tick kernels: find the item's fit and bring its program into shared
+// memory when it changes (blocks walk the items in increasing order).
+__device__ __forceinline__ const TickItem& tick_item(const TickItem* __restrict__ items, int nfits,
+                                                     int it, int& cur, Program& Ps) {
+  int f = 0;
+  while (f + 1 < nfits && items[f + 1].item0 <= it) ++f;
+  const TickItem& ti = items[f];
+  if (f != cur) {
+    __syncthreads();
+    const int* src = reinterpret_cast<const int*>(&static_cast<const Fit1D*>(ti.fit)->P);
+    int* dst = reinterpret_cast<int*>(&Ps);
+    for (int k = threadIdx.x; k < (int)(sizeof(Program) / 4); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    cur = f;
+  }
+  return ti;
+}
+
+// normalisation grids of every batched fit (kThreads threads: one bin per thread)
+__global__ void __launch_bounds__(kThreads) k_tick_norm_1d(const TickItem* __restrict__ items,
+                                                           int nfits, int total,
+                                                           const WeidCoef W) {
+  __shared__ Program Ps;
+  __shared__ double red[32];
+  __shared__ int last;
+  __shared__ double sums[kMaxLeaf][4];
+  int cur = -1;
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const TickItem& ti = tick_item(items, nfits, it, cur, Ps);
+    const Fit1D* F = static_cast<const Fit1D*>(ti.fit);
+    norm_1d_block(Ps, W, ti.theta, F->partials_norm, F->counter_norm, F->derived,
+                  it - ti.item0, ti.nitems, red, &last, sums);
+    __syncthreads();
+  }
+}
+
+// event passes (NLL + gradient) of every batched fit (kThreads1D threads, as standalone)
+__global__ void __launch_bounds__(kThreads1D) k_tick_events_1d(const TickItem* __restrict__ items,
+                                                               int nfits, int total,
+                                                               const WeidCoef W) {
+  extern __shared__ double dyn[];
+  __shared__ Program Ps;
+  __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
+  __shared__ double red[32];
+  __shared__ int last;
+  int cur = -1;
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    const TickItem& ti = tick_item(items, nfits, it, cur, Ps);
+    const Fit1D* F = static_cast<const Fit1D*>(ti.fit);
+    events_1d_block<true, 0>(Ps, W, F->cols, F->n, ti.theta, F->derived, F->partials,
+                             F->counter_ev, ti.result, nullptr, F->analytic_only, it - ti.item0,
+                             ti.nitems, dyn, rec, red, &last);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_tick_1d(bool norm, const TickItem* items, int nfits, int total,
+                           const WeidCoef& W, size_t smem, int grid, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  if (norm) {
+    k_tick_norm_1d<<<grid, kThreads, 0, st>>>(items, nfits, total, W);
+  } else {
+    k_tick_events_1d<<<grid, kThreads1D, smem, st>>>(items, nfits, total, W);
+  }
+  return cudaGetLastError();
 }
 
 // ---- data check -------------------------------------------------------------------------------
@@ -475,14 +567,6 @@ cudaError_t launch_events_1d(const Program& P, const WeidCoef& W, const Cols& co
     k_events_1d<false, 1><<<nblocks, threads, 0, st>>>(P, W, cols, n, theta, derived, partials,
                                                        counter, result, out_logp, analytic_only);
   } else if (grad) {
-    static bool attr[64] = {false};  // opt in to > 48 KB dynamic shared memory, per device
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (!attr[dev & 63]) {
-      cudaFuncSetAttribute(k_events_1d<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           200 * 1024);
-      attr[dev & 63] = true;
-    }
     k_events_1d<true, 0><<<nblocks, threads, smem, st>>>(P, W, cols, n, theta, derived, partials,
                                                          counter, result, out_logp, analytic_only);
   } else {
@@ -492,11 +576,19 @@ cudaError_t launch_events_1d(const Program& P, const WeidCoef& W, const Cols& co
   return cudaGetLastError();
 }
 
+// Opt the gradient kernels in to > 48 KB of dynamic shared memory on the current device
+// (outside any stream capture; called when a data set is loaded).
+void prepare_kernels_1d() {
+  cudaFuncSetAttribute(k_events_1d<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       200 * 1024);
+  cudaFuncSetAttribute(k_tick_events_1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       200 * 1024);
+}
+
 int events_1d_blocks_per_sm(bool grad, size_t smem) {
   int nb = 0;
   if (grad) {
-    cudaFuncSetAttribute(k_events_1d<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
+    prepare_kernels_1d();
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_events_1d<true, 0>, kThreads1D, smem);
   } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_events_1d<false, 0>, kThreads1D, 0);

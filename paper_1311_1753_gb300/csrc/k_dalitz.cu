@@ -150,6 +150,46 @@ __device__ __forceinline__ void res_amp(const DalitzRes& R, const ResK& k, const
 
 // Cached columns are double2 (FP64 plans, and the grid columns of every plan) or float2
 // (per-event columns of an FP32 plan); wide = 1 selects double2.
+// FP32 plans: the theta-dependent constants enter as hi + lo float pairs.  A constant
+// rounded once per call carries the same relative error into every event, so the FP32
+// likelihood would jump by ~n x 6e-8 whenever the rounding of m0, K, c_r ... flips as
+// theta moves; with the pairs it varies smoothly and only the per-event roundings
+// (independent across events) remain.
+struct ResKf {
+  float m0h, m0l, m0sqh, m0sql, Kh, Kl, sBh, sBl, crh, crl, cih, cil;
+};
+__device__ __forceinline__ void split_const(double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+__device__ __forceinline__ void make_resf(const ResK& k, ResKf& f) {
+  split_const(k.m0, f.m0h, f.m0l);
+  split_const(k.m0sq, f.m0sqh, f.m0sql);
+  split_const(k.K, f.Kh, f.Kl);
+  split_const(k.sqrtB0, f.sBh, f.sBl);
+  split_const(k.cr, f.crh, f.crl);
+  split_const(k.ci, f.cih, f.cil);
+}
+__device__ __forceinline__ void res_amp_f(const DalitzRes& R, const ResKf& k, const ChanK<float>& c,
+                                          C2<float>& A, float& FS, C2<float>& BW, float& Gm) {
+  const int L = R.spin;
+  float qpow, iB, rB, S;
+  if (L == 0) { qpow = c.q; iB = 1.f; rB = 1.f; S = 1.f; }
+  else if (L == 1) { qpow = c.qp1; iB = c.iB1; rB = c.rB1; S = c.S1; }
+  else { qpow = c.qp2; iB = c.iB2; rB = c.rB2; S = c.S2; }
+  const float g = qpow * c.minv * iB;
+  Gm = fmaf(k.Kh, g, k.Kl * g);
+  const float Dr = (k.m0sqh - c.sab) + k.m0sql;
+  const float mG = fmaf(k.m0h, Gm, k.m0l * Gm);
+  const float inv = __frcp_rn(fmaf(Dr, Dr, mG * mG));
+  BW.r = Dr * inv;
+  BW.i = mG * inv;
+  const float F = (L == 0) ? 1.f : fmaf(k.sBh, rB, k.sBl * rB);
+  FS = F * S;
+  A.r = FS * BW.r;
+  A.i = FS * BW.i;
+}
+
 template <typename T>
 __device__ __forceinline__ C2<T> load_cached(const void* base, int64_t stride, int slot,
                                              int64_t i, int wide) {
@@ -352,24 +392,36 @@ __global__ void __launch_bounds__(kThreads) k_dalitz_gram(const DalitzPlan D,
 // cache column or evaluated here, A = a_NR + sum c_r A_r, P = |A|^2; the metric is
 // -log P (events) or P dA (cells); with G the partials d/dtheta as well.
 // Shared memory: gacc[nfree][blockDim] per-thread gradient sums.
+// Shared scratch of one block (static part).
+struct DzShared {
+  ResK rk[kMaxRes];
+  ResKf rkf[kMaxRes];
+  double red[32];
+  double tot[1 + 4 * kMaxRes];
+  double logN;
+  int last;
+};
+
+// Body of one (virtual) block vb of the vgrid blocks of a stream launch.
 template <typename T, bool G, int METRIC>
-__global__ void __launch_bounds__(kThreads) k_dalitz_stream(
-    const DalitzPlan D, const double* __restrict__ theta, const double* __restrict__ s12d,
+__device__ __forceinline__ void dalitz_stream_block(
+    const DalitzPlan& D, const double* __restrict__ theta, const double* __restrict__ s12d,
     const double* __restrict__ s13d, const float* __restrict__ sf, int64_t n,
     const void* __restrict__ cache, int64_t cache_stride, int cache_wide,
     const uint8_t* __restrict__ inside,
     double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
     double* __restrict__ out_logp, const double* __restrict__ norm_in, int norm_mode,
-    const double* __restrict__ gram) {
-  extern __shared__ double dyn[];
-  __shared__ ResK rk[kMaxRes];
-  __shared__ double red[32];
-  __shared__ int last;
+    const double* __restrict__ gram, const int vb, const int vgrid, double* dyn, DzShared& sh) {
+  ResK* rk = sh.rk;
+  ResKf* rkf = sh.rkf;
+  double* red = sh.red;
   const int tid = threadIdx.x, bd = blockDim.x;
   const int nf = D.nfree;
   const int nres = D.nres;
-  if (tid < nres) res_constants(D, D.res[tid], theta, rk[tid]);
-  __shared__ double logN_s;
+  if (tid < nres) {
+    res_constants(D, D.res[tid], theta, rk[tid]);
+    make_resf(rk[tid], rkf[tid]);
+  }
   Acc<T>* gacc = reinterpret_cast<Acc<T>*>(dyn) + tid;
   if (G)
     for (int k = 0; k < nf; ++k) gacc[k * bd] = Acc<T>();
@@ -392,13 +444,13 @@ __global__ void __launch_bounds__(kThreads) k_dalitz_stream(
     } else {
       N = norm_in[0];
     }
-    logN_s = log(N);
+    sh.logN = log(N);
   }
   __syncthreads();
   Acc<T> acc;
   const int64_t nitems = (METRIC == METRIC_NORM) ? (int64_t)D.nbx * D.nby : n;
 
-  for (int64_t i = (int64_t)blockIdx.x * bd + tid; i < nitems; i += (int64_t)gridDim.x * bd) {
+  for (int64_t i = (int64_t)vb * bd + tid; i < nitems; i += (int64_t)vgrid * bd) {
     T a, b, c;
     if (METRIC == METRIC_NORM) {
       if (!inside[i]) continue;
@@ -429,16 +481,27 @@ __global__ void __launch_bounds__(kThreads) k_dalitz_stream(
       const DalitzRes& R = D.res[r];
       if (R.ev_cached >= 0) {
         Ar[r] = load_cached<T>(cache, cache_stride, R.ev_cached, i, cache_wide);
+      } else if constexpr (sizeof(T) == 4) {
+        res_amp_f(R, rkf[r], reinterpret_cast<const ChanK<float>&>(ck[R.channel]),
+                  reinterpret_cast<C2<float>&>(Ar[r]), reinterpret_cast<float&>(FS[r]),
+                  reinterpret_cast<C2<float>&>(BW[r]), reinterpret_cast<float&>(Gm[r]));
       } else {
         res_amp<T>(R, rk[r], ck[R.channel], Ar[r], FS[r], BW[r], Gm[r]);
       }
-      const T cr = (T)rk[r].cr, ci = (T)rk[r].ci;
-      At.r += cr * Ar[r].r - ci * Ar[r].i;
-      At.i += cr * Ar[r].i + ci * Ar[r].r;
+      if constexpr (sizeof(T) == 4) {
+        const ResKf& f = rkf[r];
+        const T ar = Ar[r].r, ai = Ar[r].i;
+        At.r += fmaf(f.crh, ar, -f.cih * ai) + fmaf(f.crl, ar, -f.cil * ai);
+        At.i += fmaf(f.crh, ai, f.cih * ar) + fmaf(f.crl, ai, f.cil * ar);
+      } else {
+        const T cr = (T)rk[r].cr, ci = (T)rk[r].ci;
+        At.r += cr * Ar[r].r - ci * Ar[r].i;
+        At.i += cr * Ar[r].i + ci * Ar[r].r;
+      }
     }
     const T P = At.r * At.r + At.i * At.i;
     if (METRIC == METRIC_STORE) {
-      out_logp[i] = (double)lg<T>(P) - logN_s;
+      out_logp[i] = (double)lg<T>(P) - sh.logN;
       continue;
     }
     if (METRIC == METRIC_NLL) acc.add(-lg<T>(P));
@@ -489,11 +552,11 @@ __global__ void __launch_bounds__(kThreads) k_dalitz_stream(
   for (int k = 0; k < m; ++k) {
     const double v = (k == 0) ? acc.get() : gacc[(k - 1) * bd].get();
     const double r = block_sum(v, red);
-    if (tid == 0) partials[(size_t)blockIdx.x * stride_p + k] = r;
+    if (tid == 0) partials[(size_t)vb * stride_p + k] = r;
   }
-  if (!arrive_last(counter, &last)) return;
-  __shared__ double tot[1 + 4 * kMaxRes];
-  reduce_partials(partials, gridDim.x, stride_p, m, tot, red);
+  if (!arrive_last_of(counter, (unsigned)vgrid, &sh.last)) return;
+  double* tot = sh.tot;
+  reduce_partials(partials, vgrid, stride_p, m, tot, red);
   __syncthreads();
   if (METRIC == METRIC_NORM) {
     const double dA = D.hx * D.hy;
@@ -537,6 +600,51 @@ __global__ void __launch_bounds__(kThreads) k_dalitz_stream(
       for (int k = 0; k < nf; ++k) result[1 + k] = tot[1 + k] + nn * dN[k] / N;
   }
   if (tid == 0) *counter = 0u;
+}
+
+template <typename T, bool G, int METRIC>
+__global__ void __launch_bounds__(kThreads) k_dalitz_stream(
+    const DalitzPlan D, const double* __restrict__ theta, const double* __restrict__ s12d,
+    const double* __restrict__ s13d, const float* __restrict__ sf, int64_t n,
+    const void* __restrict__ cache, int64_t cache_stride, int cache_wide,
+    const uint8_t* __restrict__ inside,
+    double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
+    double* __restrict__ out_logp, const double* __restrict__ norm_in, int norm_mode,
+    const double* __restrict__ gram) {
+  extern __shared__ double dyn[];
+  __shared__ DzShared sh;
+  dalitz_stream_block<T, G, METRIC>(D, theta, s12d, s13d, sf, n, cache, cache_stride, cache_wide,
+                                    inside, partials, counter, result, out_logp, norm_in,
+                                    norm_mode, gram, blockIdx.x, gridDim.x, dyn, sh);
+}
+
+// ---- batched tick: every waiting Dalitz fit (Gram normalisation) in one persistent launch
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_tick_dalitz(const TickItem* __restrict__ items,
+                                                          int nfits, int total) {
+  extern __shared__ double dyn[];
+  __shared__ DalitzPlan Ds;
+  __shared__ DzShared sh;
+  int cur = -1;
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    int f = 0;
+    while (f + 1 < nfits && items[f + 1].item0 <= it) ++f;
+    const TickItem ti = items[f];
+    const FitDz* F = static_cast<const FitDz*>(ti.fit);
+    if (f != cur) {  // this fit's plan into shared memory
+      __syncthreads();
+      const int* src = reinterpret_cast<const int*>(&F->D);
+      int* dst = reinterpret_cast<int*>(&Ds);
+      for (int k = threadIdx.x; k < (int)(sizeof(DalitzPlan) / 4); k += blockDim.x) dst[k] = src[k];
+      __syncthreads();
+      cur = f;
+    }
+    dalitz_stream_block<T, true, METRIC_NLL>(Ds, ti.theta, F->s12, F->s13, F->sf, F->n,
+                                             F->ev_cache, F->n, F->cache_wide, nullptr,
+                                             F->partials, F->counter, ti.result, nullptr, nullptr,
+                                             DN_GRAM, F->gram, it - ti.item0, ti.nitems, dyn, sh);
+    __syncthreads();
+  }
 }
 
 // ---- host launchers ---------------------------------------------------------------------------
@@ -668,6 +776,24 @@ cudaError_t launch_dalitz_events(const DalitzPlan& D, bool mixed, bool grad, boo
                                                        st);
   return launch_stream_t<double, false, METRIC_NLL>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 1, B.partials,
                                                       B.counter, B.result, norm_mode, nblocks, st);
+}
+
+cudaError_t launch_tick_dalitz(bool mixed, const TickItem* items, int nfits, int total,
+                               size_t smem, int grid, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  static bool attr[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!attr[dev & 63]) {
+    cudaFuncSetAttribute(k_tick_dalitz<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         160 * 1024);
+    cudaFuncSetAttribute(k_tick_dalitz<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         160 * 1024);
+    attr[dev & 63] = true;
+  }
+  if (mixed) k_tick_dalitz<float><<<grid, kThreads, smem, st>>>(items, nfits, total);
+  else k_tick_dalitz<double><<<grid, kThreads, smem, st>>>(items, nfits, total);
+  return cudaGetLastError();
 }
 
 int dalitz_blocks_per_sm(bool mixed, bool grad) {

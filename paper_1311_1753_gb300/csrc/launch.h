@@ -15,7 +15,11 @@ cudaError_t launch_events_1d(const Program& P, const WeidCoef& W, const Cols& co
                              const double* theta, const double* derived, double* partials,
                              unsigned* counter, double* result, double* out_logp, bool grad,
                              bool store, int analytic_only, int nblocks, cudaStream_t st);
-int events_1d_blocks_per_sm(bool grad, size_t smem);
+int events_1d_blocks_per_sm(bool grad, size_t smem);  // also opts in to large shared memory
+void prepare_kernels_1d();
+// batched fit-server tick (persistent launches over a work list of TickItems)
+cudaError_t launch_tick_1d(bool norm, const TickItem* items, int nfits, int total,
+                           const WeidCoef& W, size_t smem, int grid, cudaStream_t st);
 // flag := 1 if any event lies outside [lo[k], hi[k]] of its column
 cudaError_t launch_check_range(const Cols& cols, int nobs, int64_t n, const double* lo,
                                const double* hi, int* flag, cudaStream_t st);
@@ -61,6 +65,8 @@ cudaError_t launch_dalitz_events(const DalitzPlan& D, bool mixed, bool grad, boo
                                  int norm_mode, const double* theta, const DalitzBufs& B,
                                  int nblocks, cudaStream_t st);
 int dalitz_blocks_per_sm(bool mixed, bool grad);
+cudaError_t launch_tick_dalitz(bool mixed, const TickItem* items, int nfits, int total,
+                               size_t smem, int grid, cudaStream_t st);
 constexpr int kGramEntries = (kMaxRes + 1) * (kMaxRes + 2) / 2;
 
 }  // namespace gfi

@@ -22,6 +22,7 @@
 #include "../../include/gf.h"
 #include "ctx.h"
 #include "fit.h"
+#include "launch.h"
 
 using namespace gfi;
 using Clock = std::chrono::steady_clock;
@@ -40,6 +41,7 @@ struct Req {
   // evaluation hand-off
   bool want = false, ready = false;
   bool want64 = false;  // FP64 evaluation (refinement stage of a mixed-precision fit)
+  int evals = 0;        // evaluations done (the first one builds caches per fit)
   std::vector<double> theta, grad;
   double f = 0.0;
   int eval_rc = GF_OK;
@@ -52,8 +54,24 @@ struct Req {
 
 }  // namespace
 
+// Device and pinned buffers of the batched tick: the work lists of the three launches,
+// every batched fit's theta_all, and their results.
+struct TickBufs {
+  int cap_fits = 0, cap_par = 0;
+  TickItem* h_items = nullptr;  // [3][cap_fits]: 1D norm, 1D events, Dalitz events
+  double* h_theta = nullptr;    // [cap_fits][cap_par]
+  double* h_res = nullptr;      // [cap_fits][64]
+  void* d_block = nullptr;      // device mirror of items + theta
+  double* d_res = nullptr;
+  cudaStream_t st = nullptr;
+  size_t bytes_items() const { return sizeof(TickItem) * 3 * cap_fits; }
+  size_t bytes_theta() const { return sizeof(double) * (size_t)cap_fits * cap_par; }
+};
+
 struct gf_server {
   gf_server_opts opts{};
+  TickBufs tb;
+  int sm_count = 152;
   std::mutex mu;
   std::condition_variable cv_sched, cv_fit, cv_drain;
   std::deque<std::shared_ptr<Req>> pending;
@@ -105,8 +123,6 @@ static void fit_thread(gf_server* S, std::shared_ptr<Req> R) {
   };
   const bool refine = R->ctx->precision == GF_MIXED && R->ctx->is_dalitz &&
                       (!R->has_opts || R->opts.refine != 0);
-  if (R->ctx->precision == GF_MIXED && R->ctx->is_dalitz)
-    mo.f_noise_fast = 1e-6 * std::sqrt((double)R->ctx->dev.n + 1.0);
   FGFun fg_fast = make_fg(false), fg_exact = make_fg(R->ctx->precision == GF_MIXED);
   MinResult m = refine ? minimise_refined(&fg_fast, fg_exact, x0, step, lo, hi, mo)
                        : minimise(fg_fast, x0, step, lo, hi, mo);
@@ -116,6 +132,102 @@ static void fit_thread(gf_server* S, std::shared_ptr<Req> R) {
   R->done = true;
   R->t_done = Clock::now();
   S->cv_sched.notify_all();
+}
+
+// One batched tick for fits with a tick descriptor: one host-to-device copy of the work
+// lists and theta, the persistent launches (1D normalisation, 1D events, Dalitz events),
+// one device-to-host copy of the results.  Returns the number of kernel launches.
+static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
+  TickBufs& T = S->tb;
+  int maxpar = 1;
+  for (auto& R : fits) maxpar = std::max(maxpar, (int)R->ctx->pars.size());
+  const int nfit = (int)fits.size();
+  if (nfit > T.cap_fits || maxpar > T.cap_par) {  // (re)size the buffers
+    if (T.st) cudaStreamSynchronize(T.st);
+    cudaFreeHost(T.h_items);
+    cudaFreeHost(T.h_theta);
+    cudaFreeHost(T.h_res);
+    cudaFree(T.d_block);
+    cudaFree(T.d_res);
+    T.cap_fits = std::max(nfit, std::max(T.cap_fits, S->opts.max_slots));
+    T.cap_par = std::max(maxpar, std::max(T.cap_par, 64));
+    if (cudaMallocHost(&T.h_items, T.bytes_items()) != cudaSuccess ||
+        cudaMallocHost(&T.h_theta, T.bytes_theta()) != cudaSuccess ||
+        cudaMallocHost(&T.h_res, sizeof(double) * 64 * T.cap_fits) != cudaSuccess ||
+        cudaMalloc(&T.d_block, T.bytes_items() + T.bytes_theta()) != cudaSuccess ||
+        cudaMalloc(&T.d_res, sizeof(double) * 64 * T.cap_fits) != cudaSuccess) {
+      cudaGetLastError();
+      for (auto& R : fits) R->eval_rc = GF_ENOMEM;
+      T.cap_fits = T.cap_par = 0;
+      return 0;
+    }
+  }
+  if (!T.st) cudaStreamCreateWithFlags(&T.st, cudaStreamNonBlocking);
+  TickItem* it_norm = T.h_items;
+  TickItem* it_ev1 = T.h_items + T.cap_fits;
+  TickItem* it_dz = T.h_items + 2 * T.cap_fits;
+  TickItem* d_items = static_cast<TickItem*>(T.d_block);
+  double* d_theta = reinterpret_cast<double*>(static_cast<char*>(T.d_block) + T.bytes_items());
+  int n_norm = 0, n_ev1 = 0, n_dz = 0, tot_norm = 0, tot_ev1 = 0, tot_dz = 0;
+  int nf1 = 0, nfd = 0;
+  for (int j = 0; j < nfit; ++j) {
+    gf_ctx* c = fits[j]->ctx;
+    fill_theta_all(c, fits[j]->theta.data(), T.h_theta + (size_t)j * T.cap_par);
+    const double* th = d_theta + (size_t)j * T.cap_par;
+    double* res = T.d_res + 64 * j;
+    if (c->dev.tick_kind == 1) {
+      if (c->has_grid) {
+        it_norm[n_norm++] = TickItem{c->dev.tick_desc, th, res, tot_norm, c->prog.ngrid_blocks};
+        tot_norm += c->prog.ngrid_blocks;
+      }
+      it_ev1[n_ev1++] = TickItem{c->dev.tick_desc, th, res, tot_ev1, c->dev.nblocks};
+      tot_ev1 += c->dev.nblocks;
+      nf1 = std::max(nf1, (int)c->free_ids.size());
+    } else {
+      it_dz[n_dz++] = TickItem{c->dev.tick_desc, th, res, tot_dz, c->dev.nblocks};
+      tot_dz += c->dev.nblocks;
+      nfd = std::max(nfd, (int)c->free_ids.size());
+    }
+  }
+  cudaStream_t st = T.st;
+  int64_t nl = 0;
+  cudaError_t e = cudaMemcpyAsync(T.d_block, T.h_items, T.bytes_items() + 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_theta, T.h_theta, sizeof(double) * (size_t)nfit * T.cap_par,
+                        cudaMemcpyHostToDevice, st);
+  const WeidCoef& W = weideman();
+  const int grid = S->sm_count * 4;
+  if (e == cudaSuccess && n_norm) {
+    e = launch_tick_1d(true, d_items, n_norm, tot_norm, W, 0, grid, st);
+    ++nl;
+  }
+  if (e == cudaSuccess && n_ev1) {
+    const size_t smem = (size_t)(kMaxStack + 1) * nf1 * kThreads1D * sizeof(double);
+    e = launch_tick_1d(false, d_items + T.cap_fits, n_ev1, tot_ev1, W, smem, grid, st);
+    ++nl;
+  }
+  if (e == cudaSuccess && n_dz) {
+    const size_t smem = (size_t)nfd * kThreads * sizeof(double);
+    e = launch_tick_dalitz(S->opts.precision == GF_MIXED, d_items + 2 * T.cap_fits, n_dz, tot_dz,
+                           smem, S->sm_count * 2, st);
+    ++nl;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(T.h_res, T.d_res, sizeof(double) * 64 * nfit, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  for (int j = 0; j < nfit; ++j) {
+    auto& R = fits[j];
+    R->grad.assign(R->ctx->free_ids.size(), 0.0);
+    if (e != cudaSuccess) {
+      R->eval_rc = GF_ECUDA;
+      R->f = INFINITY;
+    } else {
+      R->eval_rc = tick_finish(R->ctx, T.h_res + 64 * j, &R->f, R->grad.data());
+    }
+    R->evals++;
+  }
+  if (e != cudaSuccess) cudaGetLastError();
+  return nl;
 }
 
 static void scheduler(gf_server* S) {
@@ -173,14 +285,24 @@ static void scheduler(gf_server* S) {
     for (auto& R : batch) R->want = false;
     lk.unlock();
     int64_t nl = 0;
+    // fits whose evaluation can join the batched launches: prepared, not an FP64
+    // refinement step, and their first evaluation done (it builds the caches)
+    std::vector<std::shared_ptr<Req>> batched, single;
     for (auto& R : batch) {
+      if (!R->want64 && R->evals > 0 && R->ctx->dev.tick_desc) batched.push_back(R);
+      else single.push_back(R);
+    }
+    for (auto& R : single) {
       R->eval_rc = evaluate_async(R->ctx, R->theta.data(), true, R->want64);
       nl += R->ctx->last_launches;
     }
-    for (auto& R : batch) {
+    if (!batched.empty()) nl += run_tick(S, batched);
+    for (auto& R : single) {
       R->grad.assign(R->ctx->free_ids.size(), 0.0);
       if (R->eval_rc == GF_OK) R->eval_rc = evaluate_finish(R->ctx, &R->f, R->grad.data(), true);
       else R->f = INFINITY;
+      R->evals++;
+      if (!R->ctx->dev.tick_desc) tick_prepare(R->ctx);
     }
     lk.lock();
     S->ticks++;
@@ -196,6 +318,7 @@ int gf_server_create(const gf_server_opts* opts, gf_server** out) {
   if (!opts || !out || opts->max_slots < 1) return GF_EINVAL;
   gf_server* S = new gf_server();
   S->opts = *opts;
+  cudaDeviceGetAttribute(&S->sm_count, cudaDevAttrMultiProcessorCount, opts->device);
   if (S->opts.wait_timeout_s <= 0) S->opts.wait_timeout_s = 60.0;
   S->sched = std::thread(scheduler, S);
   *out = S;
@@ -254,6 +377,7 @@ int gf_server_poll(gf_server* S, uint64_t ticket, gf_fit_result* res, double* la
     res->edm = m.edm;
     res->n_calls = m.calls;
     res->n_iter = m.iters;
+    res->n_calls_fast = m.calls_fast;
     res->status = m.status;
     for (size_t k = 0; k < m.x.size(); ++k) {
       if (res->theta) res->theta[k] = m.x[k];
@@ -298,6 +422,7 @@ int gf_server_destroy(gf_server* S) {
     S->cv_fit.notify_all();
   }
   if (S->sched.joinable()) S->sched.join();
+  if (S->tb.st) cudaStreamSynchronize(S->tb.st);
   for (auto& kv : S->all) {
     auto& R = kv.second;
     if (R->th.joinable()) R->th.join();
@@ -306,6 +431,12 @@ int gf_server_destroy(gf_server* S) {
     R->ctx = nullptr;
     R->ds = nullptr;
   }
+  cudaFreeHost(S->tb.h_items);
+  cudaFreeHost(S->tb.h_theta);
+  cudaFreeHost(S->tb.h_res);
+  cudaFree(S->tb.d_block);
+  cudaFree(S->tb.d_res);
+  if (S->tb.st) cudaStreamDestroy(S->tb.st);
   delete S;
   return GF_OK;
 }

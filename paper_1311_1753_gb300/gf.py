@@ -40,7 +40,7 @@ class FitOpts(C.Structure):
 class FitResult(C.Structure):
     _fields_ = [("nll", C.c_double), ("edm", C.c_double), ("n_calls", C.c_int),
                 ("n_iter", C.c_int), ("status", C.c_int), ("theta", _D), ("err", _D),
-                ("cov", _D)]
+                ("cov", _D), ("n_calls_fast", C.c_int)]
 
 
 class ServerOpts(C.Structure):
@@ -353,12 +353,13 @@ class Context:
         cov = np.zeros(max(1, nf * nf))
         o = FitOpts(tol, max_calls, 1 if use_grad else 0, up, 1 if hesse else 0,
                     1 if refine else 0)
-        r = FitResult(0.0, 0.0, 0, 0, 0, _dp(th), _dp(err), _dp(cov))
+        r = FitResult(0.0, 0.0, 0, 0, 0, _dp(th), _dp(err), _dp(cov), 0)
         rc = lib.gf_fit(self.h, C.byref(o), C.byref(r))
         if rc not in (GF_OK, GF_ENOCONV):
             self._ck(rc, "gf_fit")
         return dict(theta=th[:nf].copy(), err=err[:nf].copy(), cov=cov[: nf * nf].reshape(nf, nf),
-                    nll=r.nll, edm=r.edm, n_calls=r.n_calls, n_iter=r.n_iter, status=r.status)
+                    nll=r.nll, edm=r.edm, n_calls=r.n_calls, n_iter=r.n_iter, status=r.status,
+                    n_calls_fast=r.n_calls_fast)
 
 
 class Server:
@@ -388,7 +389,7 @@ class Server:
             raise GFError(rc, "gf_server_nfree")
         nf = max(1, n.value)
         th, err = np.zeros(nf), np.zeros(nf)
-        r = FitResult(0.0, 0.0, 0, 0, 0, _dp(th), _dp(err), None)
+        r = FitResult(0.0, 0.0, 0, 0, 0, _dp(th), _dp(err), None, 0)
         lat = C.c_double()
         done = C.c_int()
         rc = lib.gf_server_poll(self.h, ticket, C.byref(r), C.byref(lat), C.byref(done))
@@ -397,7 +398,8 @@ class Server:
         if not done.value:
             return None
         return dict(theta=th[: n.value].copy(), err=err[: n.value].copy(), nll=r.nll, edm=r.edm,
-                    n_calls=r.n_calls, status=r.status, latency=lat.value)
+                    n_calls=r.n_calls, n_calls_fast=r.n_calls_fast, status=r.status,
+                    latency=lat.value)
 
     def drain(self):
         rc = lib.gf_server_drain(self.h)
