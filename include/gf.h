@@ -237,6 +237,15 @@ int gf_last_eval_stats(gf_ctx* ctx, double* kernel_ms, int* launches);
 /* Device time (ms) of the last evaluation: all its kernels, and the final stream kernel
  * alone (the event pass, CUDA events on the context's stream). */
 int gf_last_eval_times(gf_ctx* ctx, double* total_ms, double* stream_ms);
+/* Whether the last evaluation replayed a captured CUDA graph (*replayed = 1) or launched
+ * its kernels one by one (0: the first evaluation of a kind, one that had cache work to
+ * do, or a context whose graph capture failed -- then why_not, if given, receives the
+ * reason, at most n bytes with the terminating NUL; the context then launches directly
+ * from there on, with the same results). */
+int gf_last_eval_graph(gf_ctx* ctx, int* replayed, char* why_not, size_t n);
+/* Turn the replay of captured evaluation graphs on (enable != 0, the default) or off (every
+ * evaluation launches its kernels one by one; the results are the same bits). */
+int gf_set_graphs(gf_ctx* ctx, int enable);
 
 /* ---- allocation-free evaluation -------------------------------------------------------
  * The paper has no counterpart to this call.  It is for callers that cannot call
@@ -245,9 +254,9 @@ int gf_last_eval_times(gf_ctx* ctx, double* total_ms, double* stream_ms);
  * gf_nll_noalloc computes the same NLL as gf_nll for the 1D PDF tree rooted at `root` of
  * a context that holds only the model (gf_create and node declarations allocate no device
  * memory; no gf_set_data is needed), over caller-owned device columns, and allocates
- * nothing: its working buffers (theta, normalisation records, block partials, counters)
- * are one static device array of 448 KiB compiled into the library, which every GPU that
- * loads the library holds until the process exits.
+ * nothing: its working buffers (theta, normalisation records, block partials, counters,
+ * the compiled program) are one static device array of 440 KiB compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
  *   obs[k], dev_cols[k]: observable id and device column of n doubles (16-byte aligned);
  *   theta: host array of the free parameters (gf_free_params order);
  *   nll_dev: one double in device memory, written when the context's stream reaches it

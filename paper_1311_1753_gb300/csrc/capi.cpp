@@ -29,6 +29,7 @@ int set_error(gf_ctx* ctx, int code, const std::string& msg) {
 }
 
 static int cuda_fail(gf_ctx* ctx, cudaError_t e, const char* where) {
+  cudaGetLastError();  // clear the (non-sticky) error so later calls do not report it
   return set_error(ctx, GF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
@@ -59,19 +60,15 @@ const WeidCoef& weideman() {
   static WeidCoef W;
   static std::once_flag once;
   std::call_once(once, [] {
-    W.L = std::pow(2.0, -0.25) * std::sqrt((double)kWeidN);
-    weideman_coeffs(kWeidN, W.L, W.a);
-    W.Lhi = (float)W.L;
-    W.Llo = (float)(W.L - (double)W.Lhi);
+    const double L = std::pow(2.0, -0.25) * std::sqrt((double)kWeidN);
+    double a[kWeidN + 1];
+    weideman_coeffs(kWeidN, L, a);
+    W.Lhi = (float)L;
+    W.Llo = (float)(L - (double)W.Lhi);
     for (int n = 0; n <= kWeidN; ++n) {
-      W.ahi[n] = (float)W.a[n];
-      W.alo[n] = (float)(W.a[n] - (double)W.ahi[n]);
+      W.ahi[n] = (float)a[n];
+      W.alo[n] = (float)(a[n] - (double)W.ahi[n]);
     }
-    const double Lf = std::pow(2.0, -0.25) * std::sqrt((double)kWeidNf);
-    double af[kWeidNf + 1];
-    weideman_coeffs(kWeidNf, Lf, af);
-    W.Lf = (float)Lf;
-    for (int n = 0; n <= kWeidNf; ++n) W.af[n] = (float)af[n];
   });
   return W;
 }
@@ -138,6 +135,7 @@ static void free_dev(gf_ctx* ctx) {
   if (d.evm) cudaEventDestroy(d.evm);
   cudaFree(d.flag);
   cudaFree(d.tick_desc);
+  cudaFree(d.prog);
   for (auto& g : d.graph)
     if (g) cudaGraphExecDestroy(g);
   d = DevState();
@@ -145,6 +143,21 @@ static void free_dev(gf_ctx* ctx) {
 
 // ---- C ABI: context -------------------------------------------------------------------------------
 extern "C" {
+
+namespace {
+// Kernel attributes are set once per device, with that device current, before any of the
+// context's work can be captured into a graph.
+std::mutex g_prep_mu;
+bool g_prepared[64] = {false};
+void prepare_device(int device) {
+  std::lock_guard<std::mutex> lk(g_prep_mu);
+  if (device < 0 || device >= 64 || g_prepared[device]) return;
+  gfi::prepare_kernels_1d();
+  gfi::prepare_kernels_dalitz();
+  cudaGetLastError();
+  g_prepared[device] = true;
+}
+}  // namespace
 
 int gf_create(gf_ctx** out, int device, int precision) {
   if (!out) return GF_EINVAL;
@@ -168,6 +181,7 @@ int gf_create(gf_ctx** out, int device, int precision) {
   ctx->stream = ctx->own_stream;
   cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
   weideman();
+  prepare_device(device);
   *out = ctx;
   return GF_OK;
 }
@@ -666,6 +680,10 @@ int ensure_compiled(gf_ctx* ctx) {
       }
     }
     P.ngrid_blocks = blk;
+    // the kernels read the program from device memory (it is too large for parameters)
+    DevState& dv = ctx->dev;
+    if (!dv.prog) CK(cudaMalloc(&dv.prog, sizeof(Program)));
+    CK(cudaMemcpy(dv.prog, &P, sizeof(Program), cudaMemcpyHostToDevice));
   }
   ctx->compiled = true;
   return GF_OK;
@@ -982,6 +1000,7 @@ static DalitzBufs dalitz_bufs(gf_ctx* ctx, double* out_logp, bool mixed = true) 
 // Dalitz caches: rebuild event / grid columns of fixed-shape resonances whose (m0,
 // Gamma0) differ from those the caches hold; decide the normalisation mode.
 static int dalitz_prepare(gf_ctx* ctx, int* norm_mode, int* launches, bool mixed) {
+  if (!ctx->is_dalitz) return set_error(ctx, GF_ESTATE, "dalitz_prepare on a 1D context");
   DevState& d = ctx->dev;
   const DalitzPlan& D = ctx->dplan;
   // the per-event cache matching the arithmetic of this evaluation: FP32 pairs for
@@ -1056,17 +1075,22 @@ static int dalitz_prepare(gf_ctx* ctx, int* norm_mode, int* launches, bool mixed
 
 namespace gfi {
 
-// The evaluation after any cache maintenance: theta upload (if with_upload), the
-// normalisation and event kernels, the result and data-check downloads, timing events.
-static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool with_upload,
+// The evaluation after any cache maintenance: the normalisation and event kernels, the
+// result and data-check downloads, timing events.  capturing: the stream is being
+// captured into a graph, which then also holds the theta upload from the pinned buffer.
+static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool capturing,
                           int* launches) {
   DevState& d = ctx->dev;
+  // Timing events: inside a stream capture a plain record only orders the capture and
+  // never records the event, so there they become external event-record nodes.
+  const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  const bool with_upload = capturing;
   const int nf = (int)ctx->free_ids.size();
   const int np = (int)ctx->pars.size();
   if (with_upload && np > 0)
     CK(cudaMemcpyAsync(d.theta, d.h_theta, sizeof(double) * np, cudaMemcpyHostToDevice,
                        ctx->stream));
-  CK(cudaEventRecord(d.ev0, ctx->stream));
+  CK(cudaEventRecordWithFlags(d.ev0, ctx->stream, evf));
   if (ctx->is_dalitz) {
     const bool mixed = ctx->precision == GF_MIXED && !fp64;
     DalitzBufs B = dalitz_bufs(ctx, nullptr, mixed);
@@ -1079,26 +1103,26 @@ static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool with
                                    ctx->stream));
       (*launches)++;
     }
-    CK(cudaEventRecord(d.evm, ctx->stream));
+    CK(cudaEventRecordWithFlags(d.evm, ctx->stream, evf));
     CK(launch_dalitz_events(ctx->dplan, mixed, grad, false, mode, d.theta, B, d.nblocks,
                             ctx->stream));
     (*launches)++;
   } else {
     const WeidCoef& W = weideman();
     if (ctx->has_grid) {
-      CK(launch_norm_1d(ctx->prog, W, d.theta, d.partials2, d.counters + 1, d.derived,
+      CK(launch_norm_1d(ctx->prog, d.prog, W, d.theta, d.partials2, d.counters + 1, d.derived,
                         ctx->stream));
       (*launches)++;
     }
     Cols cols{};
     for (int k = 0; k < d.nobs; ++k) cols.c[k] = d.cols[k];
-    CK(cudaEventRecord(d.evm, ctx->stream));
-    CK(launch_events_1d(ctx->prog, W, cols, d.n, d.theta, d.derived, d.partials, d.counters,
+    CK(cudaEventRecordWithFlags(d.evm, ctx->stream, evf));
+    CK(launch_events_1d(ctx->prog, d.prog, W, cols, d.n, d.theta, d.derived, d.partials, d.counters,
                         d.result, nullptr, grad, false, ctx->has_grid ? 0 : 1, d.nblocks,
                         ctx->stream));
     (*launches)++;
   }
-  CK(cudaEventRecord(d.ev1, ctx->stream));
+  CK(cudaEventRecordWithFlags(d.ev1, ctx->stream, evf));
   CK(cudaMemcpyAsync(d.h_result, d.result, sizeof(double) * (1 + (grad ? nf : 0)),
                      cudaMemcpyDeviceToHost, ctx->stream));
   // data-check flag rides along in the last pinned slot
@@ -1119,40 +1143,61 @@ int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64) {
   bool direct = false;
   const bool mixed = ctx->precision == GF_MIXED && !fp64;
   const bool steady = !ctx->is_dalitz || dalitz_is_steady(ctx, mixed, &direct);
-  if (steady) {
+  if (steady && ctx->graphs && !d.graph_off) {
     const int key = (grad ? 1 : 0) | (fp64 ? 2 : 0) | (direct ? 4 : 0);
     int launches = 0;
     if (!d.graph[key]) {
+      // capture once; if the capture or instantiation fails for any reason the context
+      // stops using graphs and this and later evaluations launch directly
       cudaGraph_t g = nullptr;
-      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      rc = enqueue_steady(ctx, grad, fp64, direct ? DN_DIRECT : DN_GRAM, true, &launches);
-      cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
-      if (rc) {
-        if (g) cudaGraphDestroy(g);
-        return rc;
-      }
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
-      e = cudaGraphInstantiate(&d.graph[key], g, 0);
-      cudaGraphDestroy(g);
+      cudaGraphExec_t ge = nullptr;
+      const std::string err_before = ctx->err;
+      std::string why;
+      cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) {
-        d.graph[key] = nullptr;
-        return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        why = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e);
+      } else {
+        const int rc_cap =
+            enqueue_steady(ctx, grad, fp64, direct ? DN_DIRECT : DN_GRAM, true, &launches);
+        e = cudaStreamEndCapture(ctx->stream, &g);
+        if (rc_cap != GF_OK) why = ctx->err;
+        else if (e != cudaSuccess || !g)
+          why = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
+        else if ((e = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess)
+          why = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+      }
+      if (g) cudaGraphDestroy(g);
+      if (!why.empty()) {
+        if (ge) cudaGraphExecDestroy(ge);
+        cudaGetLastError();
+        ctx->err = err_before;
+        d.graph_off = true;
+        d.graph_why = why;
+        launches = 0;
+      } else {
+        d.graph[key] = ge;
       }
     } else {
       launches = (ctx->is_dalitz ? (direct ? 2 : 1) : (ctx->has_grid ? 2 : 1));
     }
-    CK(cudaGraphLaunch(d.graph[key], ctx->stream));
-    ctx->last_launches = launches;
-    return GF_OK;
+    if (!d.graph_off) {
+      CK(cudaGraphLaunch(d.graph[key], ctx->stream));
+      ctx->last_launches = launches;
+      ctx->last_graph = true;
+      return GF_OK;
+    }
   }
+  ctx->last_graph = false;
   // cache maintenance first (Dalitz), then the evaluation
   const int np = (int)ctx->pars.size();
   if (np > 0)
     CK(cudaMemcpyAsync(d.theta, d.h_theta, sizeof(double) * np, cudaMemcpyHostToDevice,
                        ctx->stream));
   int launches = 0, mode = DN_GRAM;
-  rc = dalitz_prepare(ctx, &mode, &launches, mixed);
-  if (rc) return rc;
+  if (ctx->is_dalitz) {
+    rc = dalitz_prepare(ctx, &mode, &launches, mixed);
+    if (rc) return rc;
+  }
   rc = enqueue_steady(ctx, grad, fp64, mode, false, &launches);
   if (rc) return rc;
   ctx->last_launches = launches;
@@ -1163,8 +1208,13 @@ int evaluate_finish(gf_ctx* ctx, double* nll, double* grad, bool grad_wanted) {
   DevState& d = ctx->dev;
   CK(cudaStreamSynchronize(ctx->stream));
   float ms = 0.f;
+  // timings are informative: a failure makes them NaN and must not linger as the
+  // runtime's last error (the next launch check would report it)
+  ctx->last_ms = ctx->last_stream_ms = NAN;
   if (cudaEventElapsedTime(&ms, d.ev0, d.ev1) == cudaSuccess) ctx->last_ms = ms;
+  else cudaGetLastError();
   if (cudaEventElapsedTime(&ms, d.evm, d.ev1) == cudaSuccess) ctx->last_stream_ms = ms;
+  else cudaGetLastError();
   const int bad = *reinterpret_cast<const int*>(d.h_result + 63);
   if (bad) {
     *reinterpret_cast<int*>(d.h_result + 63) = 0;
@@ -1315,14 +1365,14 @@ static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host)
   } else {
     const WeidCoef& W = weideman();
     if (ctx->has_grid) {
-      cudaError_t e = launch_norm_1d(ctx->prog, W, d.theta, d.partials2, d.counters + 1,
+      cudaError_t e = launch_norm_1d(ctx->prog, d.prog, W, d.theta, d.partials2, d.counters + 1,
                                      d.derived, ctx->stream);
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "launch_norm_1d");
     }
     Cols cols{};
     for (int k = 0; k < d.nobs; ++k) cols.c[k] = d.cols[k];
     if (rc == GF_OK) {
-      cudaError_t e = launch_events_1d(ctx->prog, W, cols, d.n, d.theta, d.derived, d.partials,
+      cudaError_t e = launch_events_1d(ctx->prog, d.prog, W, cols, d.n, d.theta, d.derived, d.partials,
                                        d.counters, d.result, dst, false, true,
                                        ctx->has_grid ? 0 : 1, d.nblocks, ctx->stream);
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "launch_events_1d");
@@ -1419,6 +1469,19 @@ int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
     }
     CK(launch_check_range(c, d.nobs, n, lo, hi, d.flag, ctx->stream));
   }
+  return GF_OK;
+}
+
+int gf_set_graphs(gf_ctx* ctx, int enable) {
+  if (!ctx) return GF_EINVAL;
+  ctx->graphs = enable != 0;
+  return GF_OK;
+}
+
+int gf_last_eval_graph(gf_ctx* ctx, int* replayed, char* why_not, size_t n) {
+  if (!ctx) return GF_EINVAL;
+  if (replayed) *replayed = ctx->last_graph ? 1 : 0;
+  if (why_not && n > 0) std::snprintf(why_not, n, "%s", ctx->dev.graph_why.c_str());
   return GF_OK;
 }
 

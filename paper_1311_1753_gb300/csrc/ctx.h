@@ -43,6 +43,7 @@ struct DevState {
   bool owns_cols = false;
   // common
   double* theta = nullptr;            // all parameters (device)
+  Program* prog = nullptr;            // compiled 1D program (device)
   double* derived = nullptr;
   double* partials = nullptr;
   double* partials2 = nullptr;
@@ -68,6 +69,8 @@ struct DevState {
   bool mask_built = false;
   // timing
   cudaGraphExec_t graph[8] = {};      // steady-state evaluation graphs: grad | fp64 << 1 | direct << 2
+  bool graph_off = false;             // a capture failed: launch directly from then on
+  std::string graph_why;              // why (for gf_last_eval_graph)
   void* tick_desc = nullptr;          // Fit1D / FitDz for batched ticks (device)
   int tick_kind = 0;                  // 0: none, 1: 1D, 2: Dalitz (Gram normalisation)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;  // eval start, stream kernel, end
@@ -106,6 +109,8 @@ struct gf_ctx {
   double last_ms = 0.0;
   double last_stream_ms = 0.0;
   int last_launches = 0;
+  bool last_graph = false;  // the last evaluation replayed a captured graph
+  bool graphs = true;       // replay captured graphs of steady evaluations
 };
 
 namespace gfi {

@@ -110,20 +110,31 @@ __device__ __forceinline__ bool arrive_last(unsigned* counter, int* flag_smem) {
 //   w(z) = 1/(sqrt(pi) (L - iz)) + 2/(L - iz)^2 sum_{n=1}^{N} a_n Z^{n-1},
 //   Z = (L + iz)/(L - iz),  L = 2^{-1/4} sqrt(N).
 // The a_n are Fourier coefficients computed on the host (WeidCoef).  N = 40 gives |w|
-// to ~2e-14 relative over the Voigtian's range of z.  FP64-accurate version: every step
-// in double-float on the FP32 pipe (inputs and outputs FP64).
-__device__ __forceinline__ void faddeeva_df(double x, double y, const WeidCoef& W, double& wr,
-                                            double& wi) {
-  const F2 X = df_from(x), Y = df_from(y);
+// to ~2e-14 relative over the Voigtian's range of z.  FP64-accurate version on the FP32
+// pipe: every step in double-float, except the high-order terms n >= kWeidSplit, whose
+// coefficients are below 4e-9 (a_1 = 2.9): their partial sum is formed in plain float,
+// which changes w by < 1e-18 absolute (3e-14 relative to Re w at |Re z| = 37).
+constexpr int kWeidSplit = 24;
+__device__ __forceinline__ void faddeeva_f2(F2 X, F2 Y, const WeidCoef& W, F2& WR, F2& WI) {
   const F2 L = {W.Lhi, W.Llo};
   const F2 dr = df_add(L, Y);                                        // L - iz = dr - i x
   const F2 x2 = df_mul(X, X);
-  const F2 inv = df_div(F2{1.f, 0.f}, df_add(df_mul(dr, dr), x2));   // 1/|L - iz|^2
+  const F2 inv = df_rcp(df_add(df_mul(dr, dr), x2));                 // 1/|L - iz|^2
   const F2 zr = df_mul(df_sub(df_mul(df_sub(L, Y), dr), x2), inv);   // Re Z
   const F2 zi = df_mul(df_mul_f(df_mul(L, X), 2.f), inv);            // Im Z
-  F2 pr = {W.ahi[kWeidN], W.alo[kWeidN]}, pi = {0.f, 0.f};
+  // tail n = N .. kWeidSplit in float
+  float fr = W.ahi[kWeidN], fi = 0.f;
 #pragma unroll
-  for (int n = kWeidN - 1; n >= 1; --n) {
+  for (int n = kWeidN - 1; n >= kWeidSplit; --n) {
+    const float t = __fmaf_rn(fr, zr.hi, __fmaf_rn(-fi, zi.hi, W.ahi[n]));
+    fi = __fmaf_rn(fr, zi.hi, __fmul_rn(fi, zr.hi));
+    fr = t;
+  }
+  F2 pr = {fr, 0.f}, pi = {fi, 0.f};
+  // rolled: one copy of the step stays in the instruction cache (W sits in the constant
+  // bank, a __grid_constant__ kernel parameter, so W.ahi[n] is an indexed constant load)
+#pragma unroll 1
+  for (int n = kWeidSplit - 1; n >= 1; --n) {
     // real: pr zr - pi zi + a_n ; imag: pr zi + pi zr
     const F2 t1 = df_mul_raw(pr, zr), t2 = df_mul_raw(pi, zi);
     const F2 s1 = two_sum(t1.hi, -t2.hi);
@@ -140,30 +151,16 @@ __device__ __forceinline__ void faddeeva_df(double x, double y, const WeidCoef& 
   const F2 qr = df_sub(df_mul(ir, ir), df_mul(ii, ii));              // 1/(L - iz)^2
   const F2 qi = df_mul_f(df_mul(ir, ii), 2.f);
   constexpr DFC c(kInvSqrtPi);
-  const F2 WR = df_add(df_mul(c, ir), df_mul_f(df_sub(df_mul(pr, qr), df_mul(pi, qi)), 2.f));
-  const F2 WI = df_add(df_mul(c, ii), df_mul_f(df_add(df_mul(pr, qi), df_mul(pi, qr)), 2.f));
+  WR = df_add(df_mul(c, ir), df_mul_f(df_sub(df_mul(pr, qr), df_mul(pi, qi)), 2.f));
+  WI = df_add(df_mul(c, ii), df_mul_f(df_add(df_mul(pr, qi), df_mul(pi, qr)), 2.f));
+}
+// FP64 in and out (the normalisation grid)
+__device__ __forceinline__ void faddeeva_df(double x, double y, const WeidCoef& W, double& wr,
+                                            double& wi) {
+  F2 WR, WI;
+  faddeeva_f2(df_from(x), df_from(y), W, WR, WI);
   wr = df_to(WR);
   wi = df_to(WI);
-}
-
-__device__ __forceinline__ void faddeeva(float x, float y, const WeidCoef& W, float& wr,
-                                         float& wi) {
-  const float L = W.Lf;
-  const float dr = L + y;
-  const float inv = __frcp_rn(fmaf(dr, dr, x * x));
-  const float Zr = fmaf(L - y, dr, -x * x) * inv;
-  const float Zi = 2.f * L * x * inv;
-  float pr = W.af[kWeidNf], pi = 0.f;
-#pragma unroll
-  for (int n = kWeidNf - 1; n >= 1; --n) {
-    const float t = fmaf(pr, Zr, fmaf(-pi, Zi, W.af[n]));
-    pi = fmaf(pr, Zi, pi * Zr);
-    pr = t;
-  }
-  const float ir = dr * inv, ii = x * inv;
-  const float qr = fmaf(ir, ir, -ii * ii), qi = 2.f * ir * ii;
-  wr = fmaf((float)kInvSqrtPi, ir, 2.f * fmaf(pr, qr, -pi * qi));
-  wi = fmaf((float)kInvSqrtPi, ii, 2.f * fmaf(pr, qi, pi * qr));
 }
 
 }  // namespace gfi

@@ -61,12 +61,129 @@ __device__ __forceinline__ F2 df_from(double v) {
 }
 __device__ __forceinline__ double df_to(F2 a) { return (double)a.hi + (double)a.lo; }
 
+// d as a pair without FP64 conversions (integer pipe and a few FP32 operations): hi is d
+// rounded to 24 significant bits (round half up on the magnitude), lo the remainder
+// (at most 28 bits and a sign) rounded to 24, so hi + lo equals d to 2^-48 relative.
+// |d| outside [2^-74, 2^126) (and 0) takes the conversion path.
+__device__ __forceinline__ F2 df_split(double d) {
+  const long long b = __double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e < 949 || e > 1149) return df_from(d);
+  const unsigned sign = (unsigned)((unsigned long long)b >> 32) & 0x80000000u;
+  const unsigned up = (unsigned)(b >> 28) & 1u;  // top bit of the remainder: round up
+  const float hi = __uint_as_float((sign | ((unsigned)(e - 896) << 23) |
+                                    ((unsigned)(b >> 29) & 0x7fffffu)) + up);
+  // remainder below hi's last place, in units of d's last place: r - 2^29 if rounded up
+  const int r = (int)((unsigned)b & 0x1fffffffu) - (int)(up << 29);
+  const unsigned m = (unsigned)(r < 0 ? -r : r);  // < 2^29
+  // m exactly as two floats (each < 2^23, by the 2^23 + k trick), one rounding in the fma
+  const float ml = __fsub_rn(__uint_as_float(0x4b000000u | (m & 0x7fffffu)), 8388608.f);
+  const float mh = __fsub_rn(__uint_as_float(0x4b000000u | (m >> 23)), 8388608.f);
+  const float scale = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e - 1075)
+  const float lo = __fmul_rn(__fmaf_rn(mh, 8388608.f, ml), scale);
+  return {hi, ((r < 0) != (sign != 0)) ? -lo : lo};
+}
+
+__device__ __forceinline__ F2 df_add_f(F2 a, float b) {
+  const F2 s = two_sum(a.hi, b);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+// a b + c
+__device__ __forceinline__ F2 df_fma(F2 a, F2 b, F2 c) { return df_add(df_mul(a, b), c); }
+// 1 / a: the correctly rounded float reciprocal y and the pair y (1 + e + e^2),
+// e = 1 - a y (second-order Newton-Raphson step)
+__device__ __forceinline__ F2 df_rcp(F2 a) {
+  const float y = __frcp_rn(a.hi);
+  float e = __fmaf_rn(-a.hi, y, 1.f);
+  e = __fmaf_rn(-a.lo, y, e);
+  return fast_two_sum(y, __fmul_rn(y, __fmaf_rn(e, e, e)));
+}
+// sqrt(a), a > 0: the correctly rounded float root and one Newton step on the pair
+__device__ __forceinline__ F2 df_sqrt(F2 a) {
+  const float s = __fsqrt_rn(a.hi);
+  float e = __fmaf_rn(-s, s, a.hi);
+  e = __fadd_rn(e, a.lo);
+  return fast_two_sum(s, __fmul_rn(e, __fdiv_rn(0.5f, s)));
+}
+
 // Constant c as a df64 pair, formed at compile time.
 struct DFC {
   float hi, lo;
+  __host__ __device__ constexpr DFC() : hi(0.f), lo(0.f) {}
   __host__ __device__ constexpr DFC(double c) : hi((float)c), lo((float)(c - (double)(float)c)) {}
   __device__ __forceinline__ operator F2() const { return {hi, lo}; }
 };
+
+// Series coefficients as pairs in the constant bank (the loops over them stay rolled, so
+// the per-event code stays small enough for the instruction cache).
+static __constant__ DFC kLogSeries[11] = {1.0,      1.0 / 3,  1.0 / 5,  1.0 / 7,
+                                          1.0 / 9,  1.0 / 11, 1.0 / 13, 1.0 / 15,
+                                          1.0 / 17, 1.0 / 19, 1.0 / 21};  // atanh: 1/(2k+1)
+static __constant__ DFC kExpSeries[15] = {1.0,
+                                          1.0,
+                                          1.0 / 2,
+                                          1.0 / 6,
+                                          1.0 / 24,
+                                          1.0 / 120,
+                                          1.0 / 720,
+                                          1.0 / 5040,
+                                          1.0 / 40320,
+                                          1.0 / 362880,
+                                          1.0 / 3628800,
+                                          1.0 / 39916800,
+                                          1.0 / 479001600,
+                                          1.0 / 6227020800.0,
+                                          1.0 / 87178291200.0};  // 1/j!
+
+// ---- natural logarithm of a pair ------------------------------------------------------
+// a = m 2^e with m in [1/sqrt2, sqrt2) from hi's exponent bits (both parts scaled
+// exactly); log m = 2 atanh(s), s = (m - 1)/(m + 1), |s| <= 0.1716, odd series to s^21;
+// e ln2 with ln2 split so that e times its leading part is exact.  a <= 0, non-finite or
+// outside [2^-100, 2^125) goes to the float logf (-inf, NaN, inf or a low-accuracy value).
+__device__ __forceinline__ F2 df_log2(F2 a) {
+  if (!(a.hi >= 7.888609052210118e-31f && a.hi < 4.2535295865117308e37f))
+    return {logf(a.hi), 0.f};
+  unsigned hb = __float_as_uint(a.hi);
+  int e = (int)((hb >> 23) & 0xff) - 127;
+  if ((hb & 0x7fffffu) > 0x3504f3u) e += 1;  // mantissa above sqrt 2: use the next power
+  const float sc = __uint_as_float((unsigned)(127 - e) << 23);  // 2^-e, exact
+  const F2 m = {__fmul_rn(a.hi, sc), __fmul_rn(a.lo, sc)};
+  const F2 s = df_div(df_add_f(m, -1.f), df_add_f(m, 1.f));
+  const F2 s2 = df_mul(s, s);
+  F2 p = kLogSeries[10];
+#pragma unroll 1
+  for (int k = 9; k >= 0; --k) p = df_add(df_mul(p, s2), kLogSeries[k]);
+  const F2 lm = df_mul(df_mul_f(s, 2.f), p);
+  // ln2 = L1 + L2 + L3: L1 with 12 significant bits, so e L1 is exact for |e| < 2^12
+  const float L1 = 0.693115234375f;
+  constexpr DFC L23(0.69314718055994530942 - 0.693115234375);
+  const F2 el = df_add_f(df_mul_f(F2(L23), (float)e), __fmul_rn((float)e, L1));
+  return df_add(el, lm);
+}
+
+// ---- exponential of a pair --------------------------------------------------------------
+// u = k ln2 + r, k = rint(u / ln2) (-150 <= k <= 128), r = u - k L1 - k (L2 + L3) in pairs
+// with the split ln2 of df_log2, |r| <= 0.347; e^r by its Taylor series to r^14/14!; 2^k
+// applied in two exact steps.  Relative error ~1e-15 down to e^u ~ 2^-100; below that
+// the low part, then the high part, go subnormal, so the absolute error stays below
+// 2^-149.  u above 88.5 gives inf, below -104 gives 0.
+__device__ __forceinline__ F2 df_exp2(F2 u) {
+  if (!(u.hi < 88.5f)) return {u.hi != u.hi ? u.hi : INFINITY, 0.f};
+  if (!(u.hi > -104.0f)) return {0.f, 0.f};
+  const float k = rintf(__fmul_rn(u.hi, 1.44269504088896341f));
+  const float L1 = 0.693115234375f;
+  constexpr DFC L23(0.69314718055994530942 - 0.693115234375);
+  const F2 r = df_sub(df_add_f(u, -__fmul_rn(k, L1)), df_mul_f(F2(L23), k));
+  F2 p = kExpSeries[14];
+#pragma unroll 1
+  for (int j = 13; j >= 0; --j) p = df_add(df_mul(p, r), kExpSeries[j]);
+  // 2^k in two steps so that k = 128 or -150 stays representable
+  const int ki = (int)k;
+  const int k1 = ki / 2, k2 = ki - k1;
+  const float s1 = __uint_as_float((unsigned)(k1 + 127) << 23);
+  const float s2 = __uint_as_float((unsigned)(k2 + 127) << 23);
+  return {__fmul_rn(__fmul_rn(p.hi, s1), s2), __fmul_rn(__fmul_rn(p.lo, s1), s2)};
+}
 
 // ---- natural logarithm -----------------------------------------------------------------
 // x = m 2^e with m in [1/sqrt2, sqrt2) (exponent bits, integer pipe); log m = 2 atanh(s),
@@ -84,11 +201,9 @@ __device__ __forceinline__ double df_log(double x) {
   const F2 m = df_from(__longlong_as_double(b));
   const F2 s = df_div(df_add(m, F2{-1.f, 0.f}), df_add(m, F2{1.f, 0.f}));
   const F2 s2 = df_mul(s, s);
-  constexpr DFC c[11] = {1.0, 1.0 / 3, 1.0 / 5, 1.0 / 7, 1.0 / 9, 1.0 / 11,
-                         1.0 / 13, 1.0 / 15, 1.0 / 17, 1.0 / 19, 1.0 / 21};
-  F2 p = c[10];
-#pragma unroll
-  for (int k = 9; k >= 0; --k) p = df_add(df_mul(p, s2), c[k]);
+  F2 p = kLogSeries[10];
+#pragma unroll 1
+  for (int k = 9; k >= 0; --k) p = df_add(df_mul(p, s2), kLogSeries[k]);
   const double lm = df_to(df_mul(df_mul_f(s, 2.f), p));
   return fma((double)e, 0.69314718055994530942, lm);
 }
@@ -101,24 +216,9 @@ __device__ __forceinline__ double df_exp(double u) {
   if (!(u > -700.0 && u < 700.0)) return exp(u);
   const double k = rint(u * 1.4426950408889634074);
   const F2 r = df_from(fma(-k, 0.69314718055994530942, u));
-  constexpr DFC c[15] = {1.0,
-                         1.0,
-                         1.0 / 2,
-                         1.0 / 6,
-                         1.0 / 24,
-                         1.0 / 120,
-                         1.0 / 720,
-                         1.0 / 5040,
-                         1.0 / 40320,
-                         1.0 / 362880,
-                         1.0 / 3628800,
-                         1.0 / 39916800,
-                         1.0 / 479001600,
-                         1.0 / 6227020800.0,
-                         1.0 / 87178291200.0};
-  F2 p = c[14];
-#pragma unroll
-  for (int j = 13; j >= 0; --j) p = df_add(df_mul(p, r), c[j]);
+  F2 p = kExpSeries[14];
+#pragma unroll 1
+  for (int j = 13; j >= 0; --j) p = df_add(df_mul(p, r), kExpSeries[j]);
   const double v = df_to(p);
   return __longlong_as_double(__double_as_longlong(v) + ((long long)k << 52));
 }

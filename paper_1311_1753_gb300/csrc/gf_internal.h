@@ -71,14 +71,11 @@ struct Cols {
   const double* c[kMaxObs];
 };
 
-// Faddeeva coefficients (Weideman 1994 rational series), filled on the host.
+// Faddeeva coefficients (Weideman 1994 rational series) as double-float pairs, filled on
+// the host.  Kept small: it is a kernel parameter.
 struct WeidCoef {
-  double L;
   float Lhi, Llo;                           // L as a double-float pair
-  double a[kWeidN + 1];
-  float ahi[kWeidN + 1], alo[kWeidN + 1];  // a_n as double-float pairs (hi + lo)
-  float Lf;
-  float af[kWeidNf + 1];
+  float ahi[kWeidN + 1], alo[kWeidN + 1];   // a_n = ahi + alo
 };
 
 // ---- Dalitz plan ------------------------------------------------------------------

@@ -115,6 +115,11 @@ __device__ void make_leaf_record(const LeafDesc& L, const double* th, double N, 
       c[2] = 0.5 * G * c[1];
       c[3] = 1.0 / (s * kSqrt2Pi * N);
       c[4] = 1.0 / s;
+      // products the event-side gradient uses
+      c[5] = c[3] * c[1];
+      c[6] = c[3] * c[4];
+      c[7] = 0.5 * c[3] * c[1];
+      c[8] = c[4] + rec[3];
       break;
     }
     case L_THRESH: {
@@ -225,112 +230,274 @@ __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& 
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_norm_1d(const Program P, const WeidCoef W,
+// Copy the program into shared memory (every block, before its first use).
+__device__ __forceinline__ void load_program(const Program* __restrict__ src, Program& dst) {
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(&dst);
+  for (int k = threadIdx.x; k < (int)(sizeof(Program) / 4); k += blockDim.x) d[k] = __ldg(s + k);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) k_norm_1d(const Program* __restrict__ Pg,
+                                                      const __grid_constant__ WeidCoef W,
                                                       const double* __restrict__ theta,
                                                       double* __restrict__ partials,
                                                       unsigned* __restrict__ counter,
                                                       double* __restrict__ derived) {
+  __shared__ Program P;
   __shared__ double red[32];
   __shared__ int last;
   __shared__ double sums[kMaxLeaf][4];
+  load_program(Pg, P);
   norm_1d_block(P, W, theta, partials, counter, derived, blockIdx.x, gridDim.x, red, &last, sums);
 }
+
+// ---- event-side arithmetic ----------------------------------------------------------------
+// The per-event program runs in one of two arithmetics with the same code:
+//  ArF2  double-float pairs on the FP32 pipe (the normal path: FP64-accurate, no FP64
+//        instruction per event except the exact differences x - c of the data and a
+//        leaf constant);
+//  ArD   plain FP64, for the rare event whose density leaves the float exponent range
+//        (P < 2^-80 or > 2^125, or an intermediate that overflows), re-evaluated so that
+//        the result is the FP64 one.
+struct ArF2 {
+  using T = F2;
+  static __device__ __forceinline__ T zero() { return {0.f, 0.f}; }
+  static __device__ __forceinline__ T of(double x) { return df_split(x); }
+  static __device__ __forceinline__ T diff(double x, double c) { return df_split(x - c); }
+  static __device__ __forceinline__ T add(T a, T b) { return df_add(a, b); }
+  static __device__ __forceinline__ T sub(T a, T b) { return df_sub(a, b); }
+  static __device__ __forceinline__ T mul(T a, T b) { return df_mul(a, b); }
+  static __device__ __forceinline__ T mulf(T a, float b) { return df_mul_f(a, b); }
+  static __device__ __forceinline__ T neg(T a) { return df_neg(a); }
+  static __device__ __forceinline__ T rcp(T a) { return df_rcp(a); }
+  static __device__ __forceinline__ T sqrt_(T a) { return df_sqrt(a); }
+  static __device__ __forceinline__ T exp_(T a) { return df_exp2(a); }
+  static __device__ __forceinline__ T log_(T a) { return df_log2(a); }
+  static __device__ __forceinline__ bool pos(T a) { return a.hi > 0.f; }
+  static __device__ __forceinline__ T two_inv_sqrt_pi() { return DFC(kTwoInvSqrtPi); }
+  static __device__ __forceinline__ void faddeeva(T x, T y, const WeidCoef& W, T& wr, T& wi) {
+    faddeeva_f2(x, y, W, wr, wi);
+  }
+};
+struct ArD {
+  using T = double;
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ T of(double x) { return x; }
+  static __device__ __forceinline__ T diff(double x, double c) { return x - c; }
+  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+  static __device__ __forceinline__ T mulf(T a, float b) { return a * (double)b; }
+  static __device__ __forceinline__ T neg(T a) { return -a; }
+  static __device__ __forceinline__ T rcp(T a) { return 1.0 / a; }
+  static __device__ __forceinline__ T sqrt_(T a) { return sqrt(a); }
+  static __device__ __forceinline__ T exp_(T a) { return df_exp(a); }
+  static __device__ __forceinline__ T log_(T a) { return df_log(a); }
+  static __device__ __forceinline__ bool pos(T a) { return a > 0.0; }
+  static __device__ __forceinline__ T two_inv_sqrt_pi() { return kTwoInvSqrtPi; }
+  static __device__ __forceinline__ void faddeeva(T x, T y, const WeidCoef& W, T& wr, T& wi) {
+    faddeeva_df(x, y, W, wr, wi);
+  }
+};
 
 // ---- event-side leaf evaluation ------------------------------------------------------------
 // Returns the normalised leaf value (log domain for EXP and GAUSS).  With G, adds the
 // partials with respect to the leaf's free parameters into the gradient slot g (stride bd).
-template <bool G>
-__device__ __forceinline__ double eval_leaf(const Instr& I, const double* rec, double x,
-                                            const WeidCoef& W, double* g, int bd) {
-  const double* c = rec + 10;
+// rec: the leaf record in FP64 (its constant c0 = rec[10] enters the exact difference
+// x - c0); r: the same record in the arithmetic A.
+template <class A, bool G>
+__device__ __forceinline__ typename A::T eval_leaf(const Instr& I, const double* rec,
+                                                   const typename A::T* r, double x,
+                                                   const WeidCoef& W, typename A::T* g,
+                                                   int bd) {
+  using T = typename A::T;
+  const T* c = r + 10;
   switch (I.kind) {
     case L_EXP: {
-      if (G && I.gidx[0] >= 0) g[I.gidx[0] * bd] += x - rec[2];
-      return fma(c[0], x, c[1]);
+      const T X = A::of(x);
+      if (G && I.gidx[0] >= 0) g[I.gidx[0] * bd] = A::add(g[I.gidx[0] * bd], A::sub(X, r[2]));
+      return A::add(A::mul(c[0], X), c[1]);
     }
     case L_GAUSS: {
-      const double u = (x - c[0]) * c[1];
+      const T u = A::mul(A::diff(x, rec[10]), c[1]);
       if (G) {
-        if (I.gidx[0] >= 0) g[I.gidx[0] * bd] += u * c[1] - rec[2];
-        if (I.gidx[1] >= 0) g[I.gidx[1] * bd] += u * u * c[1] - rec[3];
+        const T uc = A::mul(u, c[1]);
+        if (I.gidx[0] >= 0) g[I.gidx[0] * bd] = A::add(g[I.gidx[0] * bd], A::sub(uc, r[2]));
+        if (I.gidx[1] >= 0)
+          g[I.gidx[1] * bd] = A::add(g[I.gidx[1] * bd], A::sub(A::mul(u, uc), r[3]));
       }
-      return fma(-0.5 * u, u, c[2]);
+      return A::add(A::mulf(A::mul(u, u), -0.5f), c[2]);
     }
     case L_VOIGT: {
-      const double zr = (x - c[0]) * c[1], zi = c[2];
-      double wr, wi;
-      faddeeva_df(zr, zi, W, wr, wi);
-      const double l = c[3] * wr;
+      const T zr = A::mul(A::diff(x, rec[10]), c[1]);
+      T wr, wi;
+      A::faddeeva(zr, c[2], W, wr, wi);
+      const T l = A::mul(c[3], wr);
       if (G) {
-        const double dre = -2.0 * (zr * wr - zi * wi);
-        const double dim = -2.0 * (zr * wi + zi * wr) + kTwoInvSqrtPi;
-        if (I.gidx[0] >= 0) g[I.gidx[0] * bd] += -c[3] * c[1] * dre - l * rec[2];
-        if (I.gidx[1] >= 0)
-          g[I.gidx[1] * bd] += -c[3] * c[4] * (dre * zr - dim * zi) - l * (c[4] + rec[3]);
-        if (I.gidx[2] >= 0) g[I.gidx[2] * bd] += -c[3] * 0.5 * c[1] * dim - l * rec[4];
+        // w' = -2 z w + 2i/sqrt(pi)
+        const T dre = A::mulf(A::sub(A::mul(zr, wr), A::mul(c[2], wi)), -2.f);
+        const T dim = A::add(A::mulf(A::add(A::mul(zr, wi), A::mul(c[2], wr)), -2.f),
+                             A::two_inv_sqrt_pi());
+        if (I.gidx[0] >= 0)
+          g[I.gidx[0] * bd] =
+              A::sub(g[I.gidx[0] * bd], A::add(A::mul(c[5], dre), A::mul(l, r[2])));
+        if (I.gidx[1] >= 0) {
+          const T q = A::sub(A::mul(dre, zr), A::mul(dim, c[2]));
+          g[I.gidx[1] * bd] =
+              A::sub(g[I.gidx[1] * bd], A::add(A::mul(c[6], q), A::mul(l, c[8])));
+        }
+        if (I.gidx[2] >= 0)
+          g[I.gidx[2] * bd] =
+              A::sub(g[I.gidx[2] * bd], A::add(A::mul(c[7], dim), A::mul(l, r[4])));
       }
       return l;
     }
     case L_THRESH: {
-      const double t = x - c[0];
-      if (!(t > 0.0)) return 0.0;
-      double l, lt = 0.0;
-      if (c[1] == 0.5 && !(G && I.gidx[1] >= 0)) {
-        l = sqrt(t) * df_exp(-c[2] * t) * c[3];
+      const T t = A::diff(x, rec[10]);
+      if (!A::pos(t)) return A::zero();
+      T l, lt = A::zero();
+      if (rec[11] == 0.5 && !(G && I.gidx[1] >= 0)) {
+        l = A::mul(A::mul(A::sqrt_(t), A::exp_(A::neg(A::mul(c[2], t)))), c[3]);
       } else {
-        lt = df_log(t);
-        l = df_exp(fma(c[1], lt, -c[2] * t)) * c[3];
+        lt = A::log_(t);
+        l = A::mul(A::exp_(A::sub(A::mul(c[1], lt), A::mul(c[2], t))), c[3]);
       }
       if (G) {
-        if (I.gidx[0] >= 0) g[I.gidx[0] * bd] += l * (c[2] - c[1] / t - rec[2]);
-        if (I.gidx[1] >= 0) g[I.gidx[1] * bd] += l * (lt - rec[3]);
-        if (I.gidx[2] >= 0) g[I.gidx[2] * bd] += -l * (t + rec[4]);
+        if (I.gidx[0] >= 0)
+          g[I.gidx[0] * bd] = A::add(
+              g[I.gidx[0] * bd], A::mul(l, A::sub(A::sub(c[2], A::mul(c[1], A::rcp(t))), r[2])));
+        if (I.gidx[1] >= 0)
+          g[I.gidx[1] * bd] = A::add(g[I.gidx[1] * bd], A::mul(l, A::sub(lt, r[3])));
+        if (I.gidx[2] >= 0)
+          g[I.gidx[2] * bd] = A::sub(g[I.gidx[2] * bd], A::mul(l, A::add(t, r[4])));
       }
       return l;
     }
     case L_POLY: {
-      double l = 0.0;
-      for (int k = I.npar - 1; k >= 0; --k) l = fma(l, x, c[k]);
+      const T X = A::of(x);
+      T l = A::zero();
+      for (int k = I.npar - 1; k >= 0; --k) l = A::add(A::mul(l, X), c[k]);
       if (G) {
-        double xk = rec[0];
+        T xk = r[0];
         for (int k = 0; k < I.npar; ++k) {
-          if (I.gidx[k] >= 0) g[I.gidx[k] * bd] += xk - l * rec[2 + k];
-          xk *= x;
+          if (I.gidx[k] >= 0)
+            g[I.gidx[k] * bd] = A::add(g[I.gidx[k] * bd], A::sub(xk, A::mul(l, r[2 + k])));
+          xk = A::mul(xk, X);
         }
       }
       return l;
     }
   }
-  return 0.0;
+  return A::zero();
+}
+
+// The compiled postfix program for one event: returns the root's value (log domain if
+// P.root_log) and, with G, leaves its gradient in stack level 0 of dyn (stride bd).
+template <class A, bool G>
+__device__ __forceinline__ typename A::T run_program(const Program& P, const double* rec,
+                                                     const typename A::T* rc, const double* x,
+                                                     const WeidCoef& W, typename A::T* dyn,
+                                                     int nf, int bd, int tid) {
+  using T = typename A::T;
+  const T* coef = rc + kMaxLeaf * kLeafRec;
+  T s0 = A::zero(), s1 = A::zero(), s2 = A::zero(), s3 = A::zero();
+  int dep = 0;
+  for (int pc = 0; pc < P.n; ++pc) {
+    const Instr& I = P.ins[pc];
+    T* gt = dyn + (size_t)(dep - 1) * nf * bd + tid;  // gradient of s0
+    switch (I.op) {
+      case OP_LEAF: {
+        T* gn = dyn + (size_t)dep * nf * bd + tid;
+        if (G)
+          for (int k = 0; k < nf; ++k) gn[k * bd] = A::zero();
+        const T v = eval_leaf<A, G>(I, rec + I.slot * kLeafRec, rc + I.slot * kLeafRec, x[I.obs],
+                                    W, gn, bd);
+        s3 = s2; s2 = s1; s1 = s0; s0 = v;
+        ++dep;
+        break;
+      }
+      case OP_TOLIN: {
+        s0 = A::exp_(s0);
+        if (G)
+          for (int k = 0; k < nf; ++k) gt[k * bd] = A::mul(gt[k * bd], s0);
+        break;
+      }
+      case OP_MUL: {
+        if (G) {
+          T* gb = gt - (size_t)nf * bd;
+          for (int k = 0; k < nf; ++k)
+            gb[k * bd] = A::add(A::mul(gb[k * bd], s0), A::mul(gt[k * bd], s1));
+        }
+        s0 = A::mul(s1, s0); s1 = s2; s2 = s3;
+        --dep;
+        break;
+      }
+      case OP_LMUL:
+      case OP_ADD: {
+        if (G) {
+          T* gb = gt - (size_t)nf * bd;
+          for (int k = 0; k < nf; ++k) gb[k * bd] = A::add(gb[k * bd], gt[k * bd]);
+        }
+        s0 = A::add(s1, s0); s1 = s2; s2 = s3;
+        --dep;
+        break;
+      }
+      case OP_SCALE: {
+        const T cf = coef[I.slot];
+        if (G) {
+          for (int k = 0; k < nf; ++k) gt[k * bd] = A::mul(gt[k * bd], cf);
+          for (int j = 0; j < I.npar; ++j)
+            if (I.gidx[j] >= 0)
+              gt[I.gidx[j] * bd] = A::add(gt[I.gidx[j] * bd], A::mulf(s0, (float)I.kind));
+        }
+        s0 = A::mul(s0, cf);
+        break;
+      }
+    }
+  }
+  return s0;
+}
+
+// The FP64 re-evaluation, out of line: it is rarely taken and keeps its code out of the
+// hot loop's instruction stream.
+template <bool G>
+__device__ __noinline__ double run_program_fp64(const Program& P, const double* rec,
+                                                const double* x, const WeidCoef& W, double* dyn,
+                                                int nf, int bd, int tid) {
+  return run_program<ArD, G>(P, rec, rec, x, W, dyn, nf, bd, tid);
 }
 
 // ---- event stream ------------------------------------------------------------------------
 // MODE 0: reduce -log P (and gradient) to result[0 .. nfree]; MODE 1: store log P_i.
 // Body of one (virtual) block vb of the vgrid blocks of an event launch.  Shared
-// scratch: dyn (G: (kMaxStack + 1) nfree blockDim doubles), rec (leaf records), red[32],
-// *last.
+// scratch: dyn (G: (kMaxStack + 1) nfree blockDim pairs/doubles), rec (leaf records in
+// FP64), rf (the same as pairs), red[32], *last.
 template <bool G, int MODE>
 __device__ __forceinline__ void events_1d_block(
     const Program& P, const WeidCoef& W, const Cols& cols, const int64_t n,
     const double* __restrict__ theta, const double* __restrict__ derived_g,
     double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
     double* __restrict__ out_logp, const int analytic_only, const int vb, const int vgrid,
-    double* dyn, double* rec, double* red, int* last) {
+    double* dyn, double* rec, F2* rf, double* red, int* last) {
   const int bd = blockDim.x, tid = threadIdx.x;
   const int nf = P.nfree;
+  constexpr int kRec = kMaxLeaf * kLeafRec + kMaxCoef;
   // leaf records: from the norm kernel, or (analytic leaves only) built here per block
   if (analytic_only) {
     if (tid < P.nleaf) make_leaf_record(P.leaf[tid], theta, 1.0, nullptr, rec + tid * kLeafRec);
     if (tid == 0) make_coefs(P, theta, rec + kMaxLeaf * kLeafRec);
   } else {
-    for (int k = tid; k < kMaxLeaf * kLeafRec + kMaxCoef; k += bd) rec[k] = derived_g[k];
+    for (int k = tid; k < kRec; k += bd) rec[k] = derived_g[k];
   }
   __syncthreads();
-  const double* coef = rec + kMaxLeaf * kLeafRec;
-  double* gacc = dyn + (size_t)kMaxStack * nf * bd + tid;  // per-thread gradient sums
+  for (int k = tid; k < kRec; k += bd) rf[k] = df_from(rec[k]);
+  __syncthreads();
+  F2* dynf = reinterpret_cast<F2*>(dyn);
+  F2* gacc = dynf + (size_t)kMaxStack * nf * bd + tid;  // per-thread gradient sums
   if (G)
-    for (int k = 0; k < nf; ++k) gacc[k * bd] = 0.0;
-  double acc = 0.0;
+    for (int k = 0; k < nf; ++k) gacc[k * bd] = F2{0.f, 0.f};
+  F2 acc = {0.f, 0.f};
 
   const int64_t npairs = (n + 1) >> 1;
   const int64_t stride = (int64_t)vgrid * bd;
@@ -354,67 +521,37 @@ __device__ __forceinline__ void events_1d_block(
       double x[kMaxObs];
 #pragma unroll
       for (int o = 0; o < kMaxObs; ++o) x[o] = e ? xv[o].y : xv[o].x;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int dep = 0;
-      for (int pc = 0; pc < P.n; ++pc) {
-        const Instr& I = P.ins[pc];
-        double* gt = dyn + (size_t)(dep - 1) * nf * bd + tid;  // gradient of s0
-        switch (I.op) {
-          case OP_LEAF: {
-            double* gn = dyn + (size_t)dep * nf * bd + tid;
-            if (G)
-              for (int k = 0; k < nf; ++k) gn[k * bd] = 0.0;
-            const double v = eval_leaf<G>(I, rec + I.slot * kLeafRec, x[I.obs], W, gn, bd);
-            s3 = s2; s2 = s1; s1 = s0; s0 = v;
-            ++dep;
-            break;
-          }
-          case OP_TOLIN: {
-            s0 = exp(s0);
-            if (G)
-              for (int k = 0; k < nf; ++k) gt[k * bd] *= s0;
-            break;
-          }
-          case OP_MUL: {
-            if (G) {
-              double* gb = gt - (size_t)nf * bd;
-              for (int k = 0; k < nf; ++k) gb[k * bd] = fma(gb[k * bd], s0, gt[k * bd] * s1);
-            }
-            s0 = s1 * s0; s1 = s2; s2 = s3;
-            --dep;
-            break;
-          }
-          case OP_LMUL:
-          case OP_ADD: {
-            if (G) {
-              double* gb = gt - (size_t)nf * bd;
-              for (int k = 0; k < nf; ++k) gb[k * bd] += gt[k * bd];
-            }
-            s0 = s1 + s0; s1 = s2; s2 = s3;
-            --dep;
-            break;
-          }
-          case OP_SCALE: {
-            const double cf = coef[I.slot];
-            if (G) {
-              for (int k = 0; k < nf; ++k) gt[k * bd] *= cf;
-              for (int j = 0; j < I.npar; ++j)
-                if (I.gidx[j] >= 0) gt[I.gidx[j] * bd] += I.kind * s0;
-            }
-            s0 *= cf;
-            break;
+      const F2 s = run_program<ArF2, G>(P, rec, rf, x, W, dynf, nf, bd, tid);
+      // P in [2^-80, 2^125): every term that underflowed on the way (absolute error below
+      // 2^-149 times a leaf constant) is negligible against P
+      const bool ok = P.root_log ? (fabsf(s.hi) < 3.0e38f)
+                                 : (s.hi >= 8.271806125530277e-25f && s.hi < 4.2535295865117308e37f);
+      if (ok) {
+        const F2 lp = P.root_log ? s : df_log2(s);
+        if (MODE == 1) {
+          out_logp[i] = df_to(lp);
+        } else {
+          acc = df_sub(acc, lp);
+          if (G) {
+            const F2 sc = P.root_log ? F2{-1.f, 0.f} : df_neg(df_rcp(s));
+            const F2* g0 = dynf + tid;
+            for (int k = 0; k < nf; ++k) gacc[k * bd] = df_add(gacc[k * bd], df_mul(g0[k * bd], sc));
           }
         }
-      }
-      const double lp = P.root_log ? s0 : df_log(s0);
-      if (MODE == 1) {
-        out_logp[i] = lp;
       } else {
-        acc -= lp;
-        if (G) {
-          const double* g0 = dyn + tid;
-          const double sc = P.root_log ? -1.0 : -1.0 / s0;
-          for (int k = 0; k < nf; ++k) gacc[k * bd] = fma(g0[k * bd], sc, gacc[k * bd]);
+        // outside the float exponent range: this event again in FP64
+        const double sd = run_program_fp64<G>(P, rec, x, W, dyn, nf, bd, tid);
+        const double lp = P.root_log ? sd : df_log(sd);
+        if (MODE == 1) {
+          out_logp[i] = lp;
+        } else {
+          acc = df_sub(acc, df_from(lp));
+          if (G) {
+            const double sc = P.root_log ? -1.0 : -1.0 / sd;
+            const double* g0 = dyn + tid;
+            for (int k = 0; k < nf; ++k)
+              gacc[k * bd] = df_add(gacc[k * bd], df_from(g0[k * bd] * sc));
+          }
         }
       }
     }
@@ -424,7 +561,7 @@ __device__ __forceinline__ void events_1d_block(
   const int m = 1 + (G ? nf : 0);
   const int stride_p = 1 + kMaxFree1D;
   for (int k = 0; k < m; ++k) {
-    const double v = (k == 0) ? acc : gacc[(k - 1) * bd];
+    const double v = (k == 0) ? df_to(acc) : df_to(gacc[(k - 1) * bd]);
     const double r = block_sum(v, red);
     if (tid == 0) partials[(size_t)vb * stride_p + k] = r;
   }
@@ -435,16 +572,19 @@ __device__ __forceinline__ void events_1d_block(
 
 template <bool G, int MODE>
 __global__ void __launch_bounds__(kThreads1D) k_events_1d(
-    const Program P, const WeidCoef W, const Cols cols, const int64_t n,
+    const Program* __restrict__ Pg, const __grid_constant__ WeidCoef W, const Cols cols, const int64_t n,
     const double* __restrict__ theta, const double* __restrict__ derived_g,
     double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
     double* __restrict__ out_logp, const int analytic_only) {
-  extern __shared__ double dyn[];  // G: (kMaxStack + 1) * nfree * blockDim doubles
+  extern __shared__ double dyn[];  // G: (kMaxStack + 1) * nfree * blockDim entries
+  __shared__ Program P;
   __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
+  __shared__ F2 rf[kMaxLeaf * kLeafRec + kMaxCoef];
   __shared__ double red[32];
   __shared__ int last;
+  load_program(Pg, P);
   events_1d_block<G, MODE>(P, W, cols, n, theta, derived_g, partials, counter, result, out_logp,
-                           analytic_only, blockIdx.x, gridDim.x, dyn, rec, red, &last);
+                           analytic_only, blockIdx.x, gridDim.x, dyn, rec, rf, red, &last);
 }
 
 // ---- batched tick: every waiting 1D fit in one persistent launch -----------------------
@@ -469,7 +609,7 @@ __device__ __forceinline__ const TickItem& tick_item(const TickItem* __restrict_
 // normalisation grids of every batched fit (kThreads threads: one bin per thread)
 __global__ void __launch_bounds__(kThreads) k_tick_norm_1d(const TickItem* __restrict__ items,
                                                            int nfits, int total,
-                                                           const WeidCoef W) {
+                                                           const __grid_constant__ WeidCoef W) {
   __shared__ Program Ps;
   __shared__ double red[32];
   __shared__ int last;
@@ -487,10 +627,11 @@ __global__ void __launch_bounds__(kThreads) k_tick_norm_1d(const TickItem* __res
 // event passes (NLL + gradient) of every batched fit (kThreads1D threads, as standalone)
 __global__ void __launch_bounds__(kThreads1D) k_tick_events_1d(const TickItem* __restrict__ items,
                                                                int nfits, int total,
-                                                               const WeidCoef W) {
+                                                               const __grid_constant__ WeidCoef W) {
   extern __shared__ double dyn[];
   __shared__ Program Ps;
   __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
+  __shared__ F2 rf[kMaxLeaf * kLeafRec + kMaxCoef];
   __shared__ double red[32];
   __shared__ int last;
   int cur = -1;
@@ -499,7 +640,7 @@ __global__ void __launch_bounds__(kThreads1D) k_tick_events_1d(const TickItem* _
     const Fit1D* F = static_cast<const Fit1D*>(ti.fit);
     events_1d_block<true, 0>(Ps, W, F->cols, F->n, ti.theta, F->derived, F->partials,
                              F->counter_ev, ti.result, nullptr, F->analytic_only, it - ti.item0,
-                             ti.nitems, dyn, rec, red, &last);
+                             ti.nitems, dyn, rec, rf, red, &last);
     __syncthreads();
   }
 }
@@ -545,11 +686,11 @@ cudaError_t launch_check_range(const Cols& cols, int nobs, int64_t n, const doub
 }
 
 // ---- host launchers ---------------------------------------------------------------------------
-cudaError_t launch_norm_1d(const Program& P, const WeidCoef& W, const double* theta,
-                           double* partials, unsigned* counter, double* derived,
-                           cudaStream_t st) {
+cudaError_t launch_norm_1d(const Program& P, const Program* prog, const WeidCoef& W,
+                           const double* theta, double* partials, unsigned* counter,
+                           double* derived, cudaStream_t st) {
   const int nb = P.ngrid_blocks > 0 ? P.ngrid_blocks : 1;
-  k_norm_1d<<<nb, kThreads, 0, st>>>(P, W, theta, partials, counter, derived);
+  k_norm_1d<<<nb, kThreads, 0, st>>>(prog, W, theta, partials, counter, derived);
   return cudaGetLastError();
 }
 
@@ -557,27 +698,28 @@ size_t events_1d_smem(const Program& P, bool grad, int threads) {
   return grad ? (size_t)(kMaxStack + 1) * P.nfree * threads * sizeof(double) : 0;
 }
 
-cudaError_t launch_events_1d(const Program& P, const WeidCoef& W, const Cols& cols, int64_t n,
+cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCoef& W,
+                             const Cols& cols, int64_t n,
                              const double* theta, const double* derived, double* partials,
                              unsigned* counter, double* result, double* out_logp, bool grad,
                              bool store, int analytic_only, int nblocks, cudaStream_t st) {
   const int threads = kThreads1D;
   const size_t smem = events_1d_smem(P, grad, threads);
   if (store) {
-    k_events_1d<false, 1><<<nblocks, threads, 0, st>>>(P, W, cols, n, theta, derived, partials,
+    k_events_1d<false, 1><<<nblocks, threads, 0, st>>>(prog, W, cols, n, theta, derived, partials,
                                                        counter, result, out_logp, analytic_only);
   } else if (grad) {
-    k_events_1d<true, 0><<<nblocks, threads, smem, st>>>(P, W, cols, n, theta, derived, partials,
+    k_events_1d<true, 0><<<nblocks, threads, smem, st>>>(prog, W, cols, n, theta, derived, partials,
                                                          counter, result, out_logp, analytic_only);
   } else {
-    k_events_1d<false, 0><<<nblocks, threads, 0, st>>>(P, W, cols, n, theta, derived, partials,
+    k_events_1d<false, 0><<<nblocks, threads, 0, st>>>(prog, W, cols, n, theta, derived, partials,
                                                        counter, result, out_logp, analytic_only);
   }
   return cudaGetLastError();
 }
 
-// Opt the gradient kernels in to > 48 KB of dynamic shared memory on the current device
-// (outside any stream capture; called when a data set is loaded).
+// Opt the gradient kernels in to > 48 KB of dynamic shared memory on the current device.
+// Called once per device when a context is created: never inside a stream capture.
 void prepare_kernels_1d() {
   cudaFuncSetAttribute(k_events_1d<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
@@ -588,7 +730,6 @@ void prepare_kernels_1d() {
 int events_1d_blocks_per_sm(bool grad, size_t smem) {
   int nb = 0;
   if (grad) {
-    prepare_kernels_1d();
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_events_1d<true, 0>, kThreads1D, smem);
   } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_events_1d<false, 0>, kThreads1D, 0);

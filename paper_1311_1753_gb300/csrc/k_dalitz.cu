@@ -654,7 +654,10 @@ static int grid_for(int64_t items, int threads, int cap) {
   return (int)(b < cap ? b : cap);
 }
 
+// Every launcher refuses (cudaErrorInvalidValue, nothing launched) a plan without a grid or
+// a missing buffer, so a call on the wrong kind of context cannot reach the device.
 cudaError_t launch_dalitz_mask(const DalitzPlan& D, uint8_t* inside, cudaStream_t st) {
+  if (!inside || D.nbx <= 0 || D.nby <= 0) return cudaErrorInvalidValue;
   k_dalitz_mask<<<grid_for((int64_t)D.nbx * D.nby, 256, 4096), 256, 0, st>>>(D, inside);
   return cudaGetLastError();
 }
@@ -677,6 +680,7 @@ cudaError_t launch_dalitz_ev_cache(const DalitzPlan& D, bool mixed, const double
                                    const double* s12, const double* s13, int64_t n,
                                    void* ev_cache, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  if (!theta || !s12 || !s13 || !ev_cache) return cudaErrorInvalidValue;
   const int nb = grid_for(n, 256, 152 * 8);
   if (mixed) k_dalitz_ev_cache<float><<<nb, 256, 0, st>>>(D, theta, s12, s13, n, ev_cache);
   else k_dalitz_ev_cache<double><<<nb, 256, 0, st>>>(D, theta, s12, s13, n, ev_cache);
@@ -687,6 +691,8 @@ cudaError_t launch_dalitz_grid_cols(const DalitzPlan& D, const double* theta, co
                                     int ntodo, void* grid_cols, const uint8_t* inside,
                                     cudaStream_t st) {
   if (ntodo <= 0) return cudaSuccess;
+  if (!theta || !todo || !grid_cols || !inside || D.nbx <= 0 || D.nby <= 0)
+    return cudaErrorInvalidValue;
   k_dalitz_grid_cols<<<grid_for((int64_t)D.nbx * D.nby, 256, 152 * 8), 256, 0, st>>>(
       D, theta, todo, ntodo, reinterpret_cast<double2*>(grid_cols), inside);
   return cudaGetLastError();
@@ -694,6 +700,9 @@ cudaError_t launch_dalitz_grid_cols(const DalitzPlan& D, const double* theta, co
 
 constexpr int kGramChunks = 304;
 cudaError_t launch_dalitz_gram(const DalitzPlan& D, const DalitzBufs& B, cudaStream_t st) {
+  if (!B.grid_cols || !B.inside || !B.partials2 || !B.counter2 || !B.gram || D.nbx <= 0 ||
+      D.nby <= 0)
+    return cudaErrorInvalidValue;
   const int K = D.nres + 1;
   const int ngroups = (K * (K + 1) / 2 + kGramGroup - 1) / kGramGroup;
   dim3 grid(kGramChunks, ngroups);
@@ -707,15 +716,10 @@ static cudaError_t launch_stream_t(const DalitzPlan& D, const double* theta, con
                                    const void* cache, int64_t cstride, int cwide, double* partials,
                                    unsigned* counter, double* result, int norm_mode, int nblocks,
                                    cudaStream_t st) {
+  if (!theta || !partials || !counter || (M != METRIC_STORE && !result) ||
+      (M == METRIC_STORE && !B.out_logp) || (B.n > 0 && (!B.s12 || !B.s13)))
+    return cudaErrorInvalidValue;
   const size_t smem = G ? (size_t)D.nfree * kThreads * sizeof(Acc<T>) : 0;
-  static bool attr[64] = {false};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (G && !attr[dev & 63]) {
-    cudaFuncSetAttribute(k_dalitz_stream<T, G, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         160 * 1024);
-    attr[dev & 63] = true;
-  }
   k_dalitz_stream<T, G, M><<<nblocks, kThreads, smem, st>>>(
       D, theta, B.s12, B.s13, B.sf, B.n, cache, cstride, cwide, B.inside, partials, counter, result,
       B.out_logp, B.norm_out, norm_mode, B.gram);
@@ -781,19 +785,25 @@ cudaError_t launch_dalitz_events(const DalitzPlan& D, bool mixed, bool grad, boo
 cudaError_t launch_tick_dalitz(bool mixed, const TickItem* items, int nfits, int total,
                                size_t smem, int grid, cudaStream_t st) {
   if (total <= 0) return cudaSuccess;
-  static bool attr[64] = {false};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (!attr[dev & 63]) {
-    cudaFuncSetAttribute(k_tick_dalitz<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         160 * 1024);
-    cudaFuncSetAttribute(k_tick_dalitz<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         160 * 1024);
-    attr[dev & 63] = true;
-  }
   if (mixed) k_tick_dalitz<float><<<grid, kThreads, smem, st>>>(items, nfits, total);
   else k_tick_dalitz<double><<<grid, kThreads, smem, st>>>(items, nfits, total);
   return cudaGetLastError();
+}
+
+// Opt the gradient kernels in to > 48 KB of dynamic shared memory on the current device.
+// Called once per device when a context is created: never inside a stream capture.
+void prepare_kernels_dalitz() {
+  const int lim = 160 * 1024;
+  cudaFuncSetAttribute(k_dalitz_stream<float, true, METRIC_NLL>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_dalitz_stream<float, true, METRIC_NORM>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_dalitz_stream<double, true, METRIC_NLL>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_dalitz_stream<double, true, METRIC_NORM>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_tick_dalitz<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_tick_dalitz<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 int dalitz_blocks_per_sm(bool mixed, bool grad) {

@@ -30,7 +30,8 @@ constexpr size_t kNADerived = kNATheta + kNAMaxPar;
 constexpr size_t kNAPartNorm = kNADerived + kMaxLeaf * kLeafRec + kMaxCoef;
 constexpr size_t kNAPartEv = kNAPartNorm + (size_t)kNAMaxGridBlocks * 4;
 constexpr size_t kNACounters = kNAPartEv + (size_t)kNAMaxEvBlocks * kNAStride;
-constexpr size_t kNADoubles = kNACounters + 2;  // two unsigned counters share one slot each
+constexpr size_t kNAProg = kNACounters + 2;  // two unsigned counters, one slot each
+constexpr size_t kNADoubles = kNAProg + (sizeof(Program) + 7) / 8;
 
 }  // namespace
 }  // namespace gfi
@@ -286,6 +287,7 @@ extern "C" int gf_nll_noalloc(gf_ctx* ctx, int root, int nobs, const int* obs, i
   double* d_pev = base + kNAPartEv;
   unsigned* d_cnt_ev = reinterpret_cast<unsigned*>(base + kNACounters);
   unsigned* d_cnt_norm = reinterpret_cast<unsigned*>(base + kNACounters + 1);
+  Program* d_prog = reinterpret_cast<Program*>(base + kNAProg);
 
   // event grid: same rule as the context path, capped by the scratch
   int per_sm = events_1d_blocks_per_sm(false, 0);
@@ -301,18 +303,22 @@ extern "C" int gf_nll_noalloc(gf_ctx* ctx, int root, int nobs, const int* obs, i
   // array keeps the previous call's contents
   if (cudaMemcpyAsync(d_theta, theta_all, sizeof(double) * (npar > 0 ? npar : 1),
                       cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(d_prog, &P, sizeof(Program), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemsetAsync(base + kNACounters, 0, 2 * sizeof(double), st) != cudaSuccess) {
     cudaGetLastError();
-    return set_error(ctx, GF_ECUDA, "gf_nll_noalloc: queueing theta / counters failed");
+    return set_error(ctx, GF_ECUDA, "gf_nll_noalloc: queueing theta / program / counters failed");
   }
   const WeidCoef& W = weideman();
   cudaError_t e = cudaSuccess;
-  if (has_grid) e = launch_norm_1d(P, W, d_theta, d_pnorm, d_cnt_norm, d_derived, st);
+  if (has_grid) e = launch_norm_1d(P, d_prog, W, d_theta, d_pnorm, d_cnt_norm, d_derived, st);
   Cols cols{};
   for (int k = 0; k < nobs; ++k) cols.c[k] = dev_cols[k];
   if (e == cudaSuccess)
-    e = launch_events_1d(P, W, cols, n, d_theta, d_derived, d_pev, d_cnt_ev, nll_dev, nullptr,
+    e = launch_events_1d(P, d_prog, W, cols, n, d_theta, d_derived, d_pev, d_cnt_ev, nll_dev, nullptr,
                          false, false, has_grid ? 0 : 1, (int)nb, st);
-  if (e != cudaSuccess) return set_error(ctx, GF_ECUDA, cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(ctx, GF_ECUDA, cudaGetErrorString(e));
+  }
   return GF_OK;
 }

@@ -8,15 +8,20 @@
 namespace gfi {
 
 // k_1d.cu
-cudaError_t launch_norm_1d(const Program& P, const WeidCoef& W, const double* theta,
-                           double* partials, unsigned* counter, double* derived, cudaStream_t st);
+// P: the host copy (grid sizes); prog: the same program in device memory (read by the
+// kernels, copied to shared memory per block)
+cudaError_t launch_norm_1d(const Program& P, const Program* prog, const WeidCoef& W,
+                           const double* theta, double* partials, unsigned* counter,
+                           double* derived, cudaStream_t st);
 size_t events_1d_smem(const Program& P, bool grad, int threads);
-cudaError_t launch_events_1d(const Program& P, const WeidCoef& W, const Cols& cols, int64_t n,
+cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCoef& W,
+                             const Cols& cols, int64_t n,
                              const double* theta, const double* derived, double* partials,
                              unsigned* counter, double* result, double* out_logp, bool grad,
                              bool store, int analytic_only, int nblocks, cudaStream_t st);
 int events_1d_blocks_per_sm(bool grad, size_t smem);  // also opts in to large shared memory
 void prepare_kernels_1d();
+void prepare_kernels_dalitz();
 // batched fit-server tick (persistent launches over a work list of TickItems)
 cudaError_t launch_tick_1d(bool norm, const TickItem* items, int nfits, int total,
                            const WeidCoef& W, size_t smem, int grid, cudaStream_t st);

@@ -100,6 +100,8 @@ def _load():
         "gf_server_destroy": ([vp], C.c_int),
         "gf_last_eval_stats": ([vp, _D, _I], C.c_int),
         "gf_last_eval_times": ([vp, _D, _D], C.c_int),
+        "gf_last_eval_graph": ([vp, _I, C.c_char_p, C.c_size_t], C.c_int),
+        "gf_set_graphs": ([vp, C.c_int], C.c_int),
         "gf_update_data": ([vp, C.c_int64, C.POINTER(_D)], C.c_int),
         "gf_nll_noalloc": ([vp, C.c_int, C.c_int, _I, C.c_int64, C.POINTER(vp), _D, vp], C.c_int),
     }
@@ -339,6 +341,17 @@ class Context:
         t, s = C.c_double(), C.c_double()
         lib.gf_last_eval_times(self.h, C.byref(t), C.byref(s))
         return t.value, s.value
+
+    def set_graphs(self, enable):
+        self._ck(lib.gf_set_graphs(self.h, 1 if enable else 0), "gf_set_graphs")
+
+    def last_eval_graph(self):
+        """(replayed, why_not): whether the last evaluation replayed a CUDA graph, and why
+        graphs are off for this context if a capture failed ("" otherwise)."""
+        r = C.c_int()
+        buf = C.create_string_buffer(512)
+        lib.gf_last_eval_graph(self.h, C.byref(r), buf, 512)
+        return bool(r.value), buf.value.decode()
 
     def last_eval_stats(self):
         ms = C.c_double()

@@ -176,6 +176,30 @@ def test_product_of_exponentials_listing2(gf):
     _grad_close(g, go, 1000)
 
 
+def test_densities_outside_float_range(gf):
+    """Events whose density falls below 2^-80 (here x > ~7.2: P down to e^-76) are
+    re-evaluated in FP64; the rest run in double-float pairs.  Both match the oracle."""
+    ctx = gf.Context()
+    x = ctx.observable("x", 0.0, 10.0)
+    a1 = ctx.parameter("a1", -9.5, 0.1)
+    a2 = ctx.parameter("a2", -8.0, 0.1)
+    f = ctx.parameter("f", 0.3, 0.01)
+    root = ctx.add([ctx.exp(x, a1), ctx.exp(x, a2)], [f])
+    m = oracle.Model1D([(0.0, 10.0)])
+    m.add([m.exp(0, m.param(-9.5)), m.exp(0, m.param(-8.0))], [m.param(0.3)])
+    xs = np.random.default_rng(11).uniform(0.0, 10.0, 2001)
+    ctx.set_data(root, [x], [xs])
+    th = np.array([-9.5, -8.0, 0.3])
+    lo_ = m.logpdf([xs], th)
+    assert lo_.min() < -70 and (lo_ > -50).sum() > 500  # both regimes present
+    lg = ctx.logpdf(th)
+    assert np.max(np.abs(lg - lo_)) <= 1e-12 * np.abs(lo_).max()
+    fg, gg = ctx.nll_grad(th)
+    fo, go = m.nll([xs], th, grad=True)
+    assert abs(fg - fo) <= 1e-9 * abs(fo)
+    _grad_close(gg, go, len(xs))
+
+
 # ---- edge cases and errors --------------------------------------------------------------------------------
 def test_nonfinite_is_reported(gf):
     # a polynomial that goes negative inside the range -> log P undefined
@@ -202,3 +226,26 @@ def test_device_columns_from_torch(gf):
     ctx.set_data_device(root, obs, len(x), [t.data_ptr()], keep=t)
     m, free = om.exp_model(-1.3)
     assert abs(ctx.nll(np.array([-1.3])) - m.nll([x])) <= 1e-9 * abs(m.nll([x]))
+
+
+def test_graph_replay_matches_direct_launches(gf):
+    """Steady evaluations replay a captured CUDA graph; with graphs off the same kernels
+    launch one by one.  Both give the same bits, for the NLL and the gradient."""
+    lo, hi = synth.VOIGT_RANGE
+    x = synth.voigt_threshold_events(100_003, **synth.VOIGT_TRUTH, lo=lo, hi=hi, seed=5)
+    t = synth.VOIGT_TRUTH
+    th0 = np.array([t["mu"], t["sigma"], t["width"], t["c"], t["frac"]])
+    a, ra, oa = pm.voigt_model(gf, nbins=2000)
+    b, rb, ob = pm.voigt_model(gf, nbins=2000)
+    a.set_data(ra, oa, [x])
+    b.set_data(rb, ob, [x])
+    b.set_graphs(False)
+    for k in range(4):
+        th = th0 * (1.0 + 0.01 * k)
+        fa, ga = a.nll_grad(th)
+        rep, why = a.last_eval_graph()
+        assert rep and why == ""
+        fb, gb = b.nll_grad(th)
+        assert b.last_eval_graph()[0] is False
+        assert fa == fb and np.array_equal(ga, gb)
+        assert a.nll(th) == b.nll(th)
