@@ -1,11 +1,13 @@
 // df64.cuh -- double-float ("df64") arithmetic on the FP32 pipe for FP64-accurate results.
 //
-// GB300 issues FP32 operations at 61 times its FP64 rate (measured 72.4 vs 1.19 TFLOP/s),
-// so the FP64-mode event kernels carry their long polynomial and transcendental chains as
-// unevaluated pairs hi + lo of floats (48-bit significands, relative rounding ~2^-46) and
-// keep FP64 for range reductions, the inputs and the results.  Error-free transformations:
-// Knuth's TwoSum, Dekker's FastTwoSum, and the FMA product error (exact for binary32).
-// __fadd_rn / __fmul_rn / __fmaf_rn keep the compiler from contracting or reordering them.
+// GB300 issues FP32 operations at 64 times its FP64 rate (measured 72.4 vs 1.19 TFLOP/s),
+// so the FP64-mode event kernels carry their arithmetic as unevaluated pairs hi + lo of
+// floats (48-bit significands, relative rounding ~2^-47): data enter by an exact-to-2^-48
+// bit split, range reductions of exp and log work on pairs with split constants, and
+// FP64 is left for the exact differences of data and constants, the cold paths and the
+// cross-thread sums.  Error-free transformations: Knuth's TwoSum, Dekker's FastTwoSum,
+// and the FMA product error (exact for binary32).  __fadd_rn / __fmul_rn / __fmaf_rn keep
+// the compiler from contracting or reordering them.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -135,54 +137,69 @@ static __constant__ DFC kExpSeries[15] = {1.0,
                                           1.0 / 6227020800.0,
                                           1.0 / 87178291200.0};  // 1/j!
 
-// ---- natural logarithm of a pair ------------------------------------------------------
-// a = m 2^e with m in [1/sqrt2, sqrt2) from hi's exponent bits (both parts scaled
-// exactly); log m = 2 atanh(s), s = (m - 1)/(m + 1), |s| <= 0.1716, odd series to s^21;
-// e ln2 with ln2 split so that e times its leading part is exact.  a <= 0, non-finite or
-// outside [2^-100, 2^125) goes to the float logf (-inf, NaN, inf or a low-accuracy value).
-__device__ __forceinline__ F2 df_log2(F2 a) {
+// ---- table-driven exponential and logarithm of a pair ---------------------------------
+// Tables of 64 pairs each (filled on the host in FP64, kept in shared memory by the
+// kernels that use them): E[j] = 2^(j/64), G[j] = log(1 + (j + 1/2)/64).
+constexpr int kTab = 64;
+
+// u = (64 e + j) ln2/64 + r with k = 64 e + j = rint(64 u / ln2), r = u - k C1 - k C23
+// (C1 = ln2/64 to 10 bits, so k C1 is exact for |k| < 2^14), |r| <= ln2/128; e^r by its
+// Taylor series to r^6/6! (truncation < 1e-19); times E[j] and 2^e (two exact steps).
+// Relative error ~1e-15 down to e^u ~ 2^-100, absolute < 2^-149 below; u above 88.5
+// gives inf (NaN stays NaN), below -104 gives 0.
+__device__ __forceinline__ F2 df_exp_tab(F2 u, const F2* __restrict__ E) {
+  if (!(u.hi < 88.5f)) return {u.hi != u.hi ? u.hi : INFINITY, 0.f};
+  if (!(u.hi > -104.0f)) return {0.f, 0.f};
+  const float k = rintf(__fmul_rn(u.hi, 92.3324826168936563f));  // 64 / ln2
+  const float C1 = 0.010833740234375f;                            // 10 significant bits
+  constexpr DFC C23(0.0108304246962491474 - 0.010833740234375);
+  const F2 r = df_sub(df_add_f(u, -__fmul_rn(k, C1)), df_mul_f(F2(C23), k));
+  constexpr DFC c6(1.0 / 720), c5(1.0 / 120), c4(1.0 / 24), c3(1.0 / 6);
+  F2 p = df_add(df_mul(F2(c6), r), F2(c5));
+  p = df_add(df_mul(p, r), F2(c4));
+  p = df_add(df_mul(p, r), F2(c3));
+  p = df_add_f(df_mul(p, r), 0.5f);
+  p = df_add_f(df_mul(p, r), 1.f);
+  p = df_add_f(df_mul(p, r), 1.f);
+  const int ki = (int)k;
+  const int j = ki & (kTab - 1);
+  const int e = (ki - j) / kTab;  // floor(k / 64)
+  p = df_mul(p, E[j]);
+  const int e1 = e / 2, e2 = e - e1;
+  const float s1 = __uint_as_float((unsigned)(e1 + 127) << 23);
+  const float s2 = __uint_as_float((unsigned)(e2 + 127) << 23);
+  return {__fmul_rn(__fmul_rn(p.hi, s1), s2), __fmul_rn(__fmul_rn(p.lo, s1), s2)};
+}
+
+// a = m 2^e, m in [1, 2) from hi's exponent bits (both parts scaled exactly); c = 1 +
+// (j + 1/2)/64 from m's top six fraction bits; log m = log c + 2 atanh(s), s = (m - c)/(m + c),
+// |s| < 1/256, odd series to s^7 (truncation < 1e-22).  For m >= 3/2 (j >= 32) the pair
+// (m/2, c/2) is used instead -- same s -- and e goes up by one, so that log a near 1 has
+// no cancellation: G[j] holds log c for j < 32 and log(c/2) for j >= 32.  e ln2 with ln2
+// split so that e times its leading part is exact.  Absolute error ~2e-16 plus
+// ~1e-15 |log a|.  a outside [2^-100, 2^125) (and a <= 0, NaN) goes to the float logf.
+__device__ __forceinline__ F2 df_log_tab(F2 a, const F2* __restrict__ G) {
   if (!(a.hi >= 7.888609052210118e-31f && a.hi < 4.2535295865117308e37f))
     return {logf(a.hi), 0.f};
-  unsigned hb = __float_as_uint(a.hi);
-  int e = (int)((hb >> 23) & 0xff) - 127;
-  if ((hb & 0x7fffffu) > 0x3504f3u) e += 1;  // mantissa above sqrt 2: use the next power
+  const unsigned hb = __float_as_uint(a.hi);
+  const int j = (int)((hb >> 17) & 0x3f);
+  const int e = (int)((hb >> 23) & 0xff) - 127 + (j >> 5);
   const float sc = __uint_as_float((unsigned)(127 - e) << 23);  // 2^-e, exact
   const F2 m = {__fmul_rn(a.hi, sc), __fmul_rn(a.lo, sc)};
-  const F2 s = df_div(df_add_f(m, -1.f), df_add_f(m, 1.f));
+  // c (or c/2), exact in float
+  const float c = (1.f + ((float)j + 0.5f) * 0.015625f) * ((j >> 5) ? 0.5f : 1.f);
+  const F2 s = df_div(df_add_f(m, -c), df_add_f(m, c));
   const F2 s2 = df_mul(s, s);
-  F2 p = kLogSeries[10];
-#pragma unroll 1
-  for (int k = 9; k >= 0; --k) p = df_add(df_mul(p, s2), kLogSeries[k]);
-  const F2 lm = df_mul(df_mul_f(s, 2.f), p);
-  // ln2 = L1 + L2 + L3: L1 with 12 significant bits, so e L1 is exact for |e| < 2^12
+  constexpr DFC i7(1.0 / 7), i5(1.0 / 5), i3(1.0 / 3);
+  F2 p = df_add(df_mul(F2(i7), s2), F2(i5));
+  p = df_add(df_mul(p, s2), F2(i3));
+  p = df_add_f(df_mul(p, s2), 1.f);
+  const F2 lm = df_add(df_mul(df_mul_f(s, 2.f), p), G[j]);
+  if (e == 0) return lm;
   const float L1 = 0.693115234375f;
   constexpr DFC L23(0.69314718055994530942 - 0.693115234375);
   const F2 el = df_add_f(df_mul_f(F2(L23), (float)e), __fmul_rn((float)e, L1));
   return df_add(el, lm);
-}
-
-// ---- exponential of a pair --------------------------------------------------------------
-// u = k ln2 + r, k = rint(u / ln2) (-150 <= k <= 128), r = u - k L1 - k (L2 + L3) in pairs
-// with the split ln2 of df_log2, |r| <= 0.347; e^r by its Taylor series to r^14/14!; 2^k
-// applied in two exact steps.  Relative error ~1e-15 down to e^u ~ 2^-100; below that
-// the low part, then the high part, go subnormal, so the absolute error stays below
-// 2^-149.  u above 88.5 gives inf, below -104 gives 0.
-__device__ __forceinline__ F2 df_exp2(F2 u) {
-  if (!(u.hi < 88.5f)) return {u.hi != u.hi ? u.hi : INFINITY, 0.f};
-  if (!(u.hi > -104.0f)) return {0.f, 0.f};
-  const float k = rintf(__fmul_rn(u.hi, 1.44269504088896341f));
-  const float L1 = 0.693115234375f;
-  constexpr DFC L23(0.69314718055994530942 - 0.693115234375);
-  const F2 r = df_sub(df_add_f(u, -__fmul_rn(k, L1)), df_mul_f(F2(L23), k));
-  F2 p = kExpSeries[14];
-#pragma unroll 1
-  for (int j = 13; j >= 0; --j) p = df_add(df_mul(p, r), kExpSeries[j]);
-  // 2^k in two steps so that k = 128 or -150 stays representable
-  const int ki = (int)k;
-  const int k1 = ki / 2, k2 = ki - k1;
-  const float s1 = __uint_as_float((unsigned)(k1 + 127) << 23);
-  const float s2 = __uint_as_float((unsigned)(k2 + 127) << 23);
-  return {__fmul_rn(__fmul_rn(p.hi, s1), s2), __fmul_rn(__fmul_rn(p.lo, s1), s2)};
 }
 
 // ---- natural logarithm -----------------------------------------------------------------

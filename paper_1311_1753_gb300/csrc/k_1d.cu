@@ -8,12 +8,25 @@
 //               postfix program evaluated per event (forward-mode gradient optional),
 //               -log P summed per thread, per block (warp shuffles), and across blocks
 //               by the last block in a fixed order.
+#include <cmath>
 #include <cstdio>
 #include "devutil.cuh"
 #include "gf_internal.h"
 #include "launch.h"
 
 namespace gfi {
+
+// exp / log tables of df_exp_tab and df_log_tab: filled on the host once per device
+// (prepare_kernels_1d), copied into shared memory by each block of the event kernels.
+__device__ F2 g_exp_tab[kTab], g_log_tab[kTab];
+__shared__ F2 s_exp_tab[kTab], s_log_tab[kTab];
+
+__device__ __forceinline__ void load_tables() {
+  for (int k = threadIdx.x; k < kTab; k += blockDim.x) {
+    s_exp_tab[k] = g_exp_tab[k];
+    s_log_tab[k] = g_log_tab[k];
+  }
+}
 
 // ---- shape functions (unnormalised r(x) and d r / d local parameter) ------------------
 // Voigtian: r = Re w(z)/(sigma sqrt(2 pi)), z = (x - mu)/(sigma sqrt 2) + i Gamma/(2 sigma sqrt 2).
@@ -272,8 +285,8 @@ struct ArF2 {
   static __device__ __forceinline__ T neg(T a) { return df_neg(a); }
   static __device__ __forceinline__ T rcp(T a) { return df_rcp(a); }
   static __device__ __forceinline__ T sqrt_(T a) { return df_sqrt(a); }
-  static __device__ __forceinline__ T exp_(T a) { return df_exp2(a); }
-  static __device__ __forceinline__ T log_(T a) { return df_log2(a); }
+  static __device__ __forceinline__ T exp_(T a) { return df_exp_tab(a, s_exp_tab); }
+  static __device__ __forceinline__ T log_(T a) { return df_log_tab(a, s_log_tab); }
   static __device__ __forceinline__ bool pos(T a) { return a.hi > 0.f; }
   static __device__ __forceinline__ T two_inv_sqrt_pi() { return DFC(kTwoInvSqrtPi); }
   static __device__ __forceinline__ void faddeeva(T x, T y, const WeidCoef& W, T& wr, T& wi) {
@@ -527,7 +540,7 @@ __device__ __forceinline__ void events_1d_block(
       const bool ok = P.root_log ? (fabsf(s.hi) < 3.0e38f)
                                  : (s.hi >= 8.271806125530277e-25f && s.hi < 4.2535295865117308e37f);
       if (ok) {
-        const F2 lp = P.root_log ? s : df_log2(s);
+        const F2 lp = P.root_log ? s : df_log_tab(s, s_log_tab);
         if (MODE == 1) {
           out_logp[i] = df_to(lp);
         } else {
@@ -582,6 +595,7 @@ __global__ void __launch_bounds__(kThreads1D) k_events_1d(
   __shared__ F2 rf[kMaxLeaf * kLeafRec + kMaxCoef];
   __shared__ double red[32];
   __shared__ int last;
+  load_tables();
   load_program(Pg, P);
   events_1d_block<G, MODE>(P, W, cols, n, theta, derived_g, partials, counter, result, out_logp,
                            analytic_only, blockIdx.x, gridDim.x, dyn, rec, rf, red, &last);
@@ -634,6 +648,7 @@ __global__ void __launch_bounds__(kThreads1D) k_tick_events_1d(const TickItem* _
   __shared__ F2 rf[kMaxLeaf * kLeafRec + kMaxCoef];
   __shared__ double red[32];
   __shared__ int last;
+  load_tables();  // visible after tick_item's first barrier
   int cur = -1;
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const TickItem& ti = tick_item(items, nfits, it, cur, Ps);
@@ -721,6 +736,18 @@ cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCo
 // Opt the gradient kernels in to > 48 KB of dynamic shared memory on the current device.
 // Called once per device when a context is created: never inside a stream capture.
 void prepare_kernels_1d() {
+  F2 e[kTab], g[kTab];
+  for (int j = 0; j < kTab; ++j) {
+    const double ev = std::exp2(j / (double)kTab);
+    const double c = 1.0 + (j + 0.5) / kTab;
+    const double gv = std::log(j >= kTab / 2 ? 0.5 * c : c);
+    e[j].hi = (float)ev;
+    e[j].lo = (float)(ev - (double)e[j].hi);
+    g[j].hi = (float)gv;
+    g[j].lo = (float)(gv - (double)g[j].hi);
+  }
+  cudaMemcpyToSymbol(g_exp_tab, e, sizeof(e));
+  cudaMemcpyToSymbol(g_log_tab, g, sizeof(g));
   cudaFuncSetAttribute(k_events_1d<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
   cudaFuncSetAttribute(k_tick_events_1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
