@@ -243,6 +243,16 @@ int gf_last_eval_times(gf_ctx* ctx, double* total_ms, double* stream_ms);
  * reason, at most n bytes with the terminating NUL; the context then launches directly
  * from there on, with the same results). */
 int gf_last_eval_graph(gf_ctx* ctx, int* replayed, char* why_not, size_t n);
+/* Allow (enable != 0, the default) or forbid the context to keep its own copy of a 1D
+ * data set sorted ascending by the observable of the first Voigtian leaf.  Sorted, each
+ * GPU thread takes a contiguous run of events and evaluates the Faddeeva function w(z)
+ * once per run of 24, expanding it around that point for the others; the NLL is the same
+ * sum (order-independent up to rounding) and gf_logpdf still returns log P_i in the
+ * caller's event order.  The sort happens in gf_set_data (columns copied by the library
+ * only, never gf_set_data_device), and again on the second evaluation after
+ * gf_update_data; it costs one radix sort and 4 bytes per event for the permutation.
+ * Takes effect at the next gf_set_data.  The fit server turns it off for its requests. */
+int gf_set_event_sort(gf_ctx* ctx, int enable);
 /* Turn the replay of captured evaluation graphs on (enable != 0, the default) or off (every
  * evaluation launches its kernels one by one; the results are the same bits). */
 int gf_set_graphs(gf_ctx* ctx, int enable);

@@ -136,6 +136,7 @@ static void free_dev(gf_ctx* ctx) {
   cudaFree(d.flag);
   cudaFree(d.tick_desc);
   cudaFree(d.prog);
+  cudaFree(d.perm);
   for (auto& g : d.graph)
     if (g) cudaGraphExecDestroy(g);
   d = DevState();
@@ -680,10 +681,22 @@ int ensure_compiled(gf_ctx* ctx) {
       }
     }
     P.ngrid_blocks = blk;
-    // the kernels read the program from device memory (it is too large for parameters)
+    // the first Voigtian leaf is the one expanded per chunk on sorted data
+    P.tay_slot = -1;
+    P.tay_obs = 0;
+    for (int pc = 0; pc < P.n; ++pc)
+      if (P.ins[pc].op == OP_LEAF && P.ins[pc].kind == L_VOIGT) {
+        P.tay_slot = P.ins[pc].slot;
+        P.tay_obs = P.ins[pc].obs;
+        break;
+      }
+    P.sorted = (d.sorted && P.tay_slot >= 0 && d.sort_obs == P.tay_obs) ? 1 : 0;
+    // the kernels read the program from device memory (it is too large for parameters);
+    // stream-ordered copy, then wait: the next launch may go to another stream
     DevState& dv = ctx->dev;
     if (!dv.prog) CK(cudaMalloc(&dv.prog, sizeof(Program)));
-    CK(cudaMemcpy(dv.prog, &P, sizeof(Program), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(dv.prog, &P, sizeof(Program), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
   }
   ctx->compiled = true;
   return GF_OK;
@@ -861,6 +874,88 @@ static int finish_set_data(gf_ctx* ctx) {
   return GF_OK;
 }
 
+// ---- sorted layout of owned 1D columns (k_sort.cu) ------------------------------------
+// Worth it when the chunked event loop will run: a Voigtian leaf, columns the context
+// owns (the caller's device columns are never reordered) and at least kChunk/2 events
+// per thread of the event launch.
+static bool sort_eligible(const gf_ctx* ctx) {
+  const DevState& d = ctx->dev;
+  return ctx->event_sort && ctx->compiled && !ctx->is_dalitz && d.owns_cols &&
+         ctx->prog.tay_slot >= 0 && d.n < INT32_MAX &&
+         d.n >= (int64_t)(kChunk / 2) * d.nblocks * kThreads1D;
+}
+
+// Reorder the columns ascending by the Voigtian's observable and keep the permutation.
+// A pure optimisation: if scratch memory is short the data stay as they are.
+static int sort_events(gf_ctx* ctx) {
+  DevState& d = ctx->dev;
+  const int64_t n = d.n;
+  const int ov = ctx->prog.tay_obs;
+  cudaStream_t st = ctx->stream;
+  const size_t bytes = round_up((size_t)std::max<int64_t>(n + 2, 2) * 8, 256);
+  size_t tb = 0;
+  CK(sort_by_key_f64(d.cols[ov], nullptr, nullptr, nullptr, n, nullptr, &tb, st));
+  std::vector<double*> fresh(d.nobs, nullptr);
+  int32_t* ptmp = nullptr;
+  int32_t* pout = d.perm;
+  void* temp = nullptr;
+  bool ok = cudaMalloc(&ptmp, sizeof(int32_t) * n) == cudaSuccess &&
+            (pout || cudaMalloc(&pout, sizeof(int32_t) * n) == cudaSuccess) &&
+            cudaMalloc(&temp, std::max<size_t>(tb, 16)) == cudaSuccess;
+  for (int k = 0; ok && k < d.nobs; ++k)
+    ok = cudaMalloc(&fresh[k], bytes) == cudaSuccess &&
+         cudaMemsetAsync(fresh[k], 0, bytes, st) == cudaSuccess;
+  if (ok) ok = sort_by_key_f64(d.cols[ov], fresh[ov], ptmp, pout, n, temp, &tb, st) == cudaSuccess;
+  for (int k = 0; ok && k < d.nobs; ++k)
+    if (k != ov) ok = launch_gather(d.cols[k], pout, fresh[k], n, st) == cudaSuccess;
+  if (ok) ok = cudaStreamSynchronize(st) == cudaSuccess;
+  cudaFree(ptmp);
+  cudaFree(temp);
+  if (!ok) {
+    cudaGetLastError();
+    for (double* p : fresh) cudaFree(p);
+    if (pout != d.perm) cudaFree(pout);
+    return GF_OK;
+  }
+  for (int k = 0; k < d.nobs; ++k) {
+    cudaFree(d.cols[k]);
+    d.cols[k] = fresh[k];
+  }
+  d.perm = pout;
+  d.sorted = true;
+  d.sort_obs = ov;
+  // kernels read the sorted flag from the program; captured graphs and the serving
+  // descriptor hold the old column pointers
+  ctx->prog.sorted = 1;
+  CK(cudaMemcpyAsync(d.prog, &ctx->prog, sizeof(Program), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  for (auto& g : d.graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  cudaFree(d.tick_desc);
+  d.tick_desc = nullptr;
+  d.tick_kind = 0;
+  return GF_OK;
+}
+
+// The columns were overwritten in the caller's order: back to the strided event loop.
+static int mark_unsorted(gf_ctx* ctx) {
+  DevState& d = ctx->dev;
+  d.evals_since_load = 0;
+  if (!d.sorted) return GF_OK;
+  d.sorted = false;
+  d.sort_obs = -1;
+  if (ctx->compiled && !ctx->is_dalitz) {
+    ctx->prog.sorted = 0;
+    CK(cudaMemcpyAsync(d.prog, &ctx->prog, sizeof(Program), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return GF_OK;
+}
+
 extern "C" int gf_set_data(gf_ctx* ctx, int root, const gf_dataset* ds) {
   if (!ctx || !ds || ds->ctx != ctx || !valid_node(ctx, root)) return GF_EINVAL;
   CK(cudaSetDevice(ctx->device));
@@ -899,7 +994,9 @@ extern "C" int gf_set_data(gf_ctx* ctx, int root, const gf_dataset* ds) {
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->root = root;
   ctx->compiled = false;
-  return finish_set_data(ctx);
+  int rc = finish_set_data(ctx);
+  if (rc == GF_OK && sort_eligible(ctx)) rc = sort_events(ctx);
+  return rc;
 }
 
 extern "C" int gf_set_data_device(gf_ctx* ctx, int root, int nobs, const int* obs, int64_t n,
@@ -1118,7 +1215,7 @@ static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool capt
     for (int k = 0; k < d.nobs; ++k) cols.c[k] = d.cols[k];
     CK(cudaEventRecordWithFlags(d.evm, ctx->stream, evf));
     CK(launch_events_1d(ctx->prog, d.prog, W, cols, d.n, d.theta, d.derived, d.partials, d.counters,
-                        d.result, nullptr, grad, false, ctx->has_grid ? 0 : 1, d.nblocks,
+                        d.result, nullptr, nullptr, grad, false, ctx->has_grid ? 0 : 1, d.nblocks,
                         ctx->stream));
     (*launches)++;
   }
@@ -1261,7 +1358,8 @@ int tick_prepare(gf_ctx* ctx) {
     F.counter_norm = d.counters + 1;
     F.analytic_only = ctx->has_grid ? 0 : 1;
     CK(cudaMalloc(&d.tick_desc, sizeof(F)));
-    CK(cudaMemcpy(d.tick_desc, &F, sizeof(F), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(d.tick_desc, &F, sizeof(F), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     d.tick_kind = 1;
     return 1;
   }
@@ -1285,7 +1383,8 @@ int tick_prepare(gf_ctx* ctx) {
   F.counter = d.counters;
   F.cache_wide = mixed ? 0 : 1;
   CK(cudaMalloc(&d.tick_desc, sizeof(F)));
-  CK(cudaMemcpy(d.tick_desc, &F, sizeof(F), cudaMemcpyHostToDevice));
+  CK(cudaMemcpyAsync(d.tick_desc, &F, sizeof(F), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   d.tick_kind = 2;
   return 2;
 }
@@ -1306,6 +1405,13 @@ int tick_finish(gf_ctx* ctx, const double* res, double* nll, double* grad) {
 }
 
 int evaluate(gf_ctx* ctx, const double* theta, double* nll, double* grad, bool fp64) {
+  // a data set evaluated repeatedly (a fit) after gf_update_data gets sorted again
+  DevState& d = ctx->dev;
+  if (!d.sorted && d.owns_cols && ++d.evals_since_load >= 2 && sort_eligible(ctx)) {
+    CK(cudaSetDevice(ctx->device));
+    const int rs = sort_events(ctx);
+    if (rs) return rs;
+  }
   int rc = evaluate_async(ctx, theta, grad != nullptr, fp64);
   if (rc) return rc;
   return evaluate_finish(ctx, nll, grad, grad != nullptr);
@@ -1373,7 +1479,8 @@ static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host)
     for (int k = 0; k < d.nobs; ++k) cols.c[k] = d.cols[k];
     if (rc == GF_OK) {
       cudaError_t e = launch_events_1d(ctx->prog, d.prog, W, cols, d.n, d.theta, d.derived, d.partials,
-                                       d.counters, d.result, dst, false, true,
+                                       d.counters, d.result, dst, d.sorted ? d.perm : nullptr,
+                                       false, true,
                                        ctx->has_grid ? 0 : 1, d.nblocks, ctx->stream);
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "launch_events_1d");
     }
@@ -1447,6 +1554,8 @@ int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
   int rc = ensure_compiled(ctx);
   if (rc) return rc;
   CK(cudaSetDevice(ctx->device));
+  rc = mark_unsorted(ctx);  // the new events arrive in the caller's order
+  if (rc) return rc;
   for (int k = 0; k < d.nobs; ++k) {
     if (!cols[k]) return GF_EINVAL;
     if (n > 0)
@@ -1469,6 +1578,12 @@ int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
     }
     CK(launch_check_range(c, d.nobs, n, lo, hi, d.flag, ctx->stream));
   }
+  return GF_OK;
+}
+
+int gf_set_event_sort(gf_ctx* ctx, int enable) {
+  if (!ctx) return GF_EINVAL;
+  ctx->event_sort = enable != 0;
   return GF_OK;
 }
 

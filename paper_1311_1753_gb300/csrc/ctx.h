@@ -75,6 +75,11 @@ struct DevState {
   int tick_kind = 0;                  // 0: none, 1: 1D, 2: Dalitz (Gram normalisation)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;  // eval start, stream kernel, end
   int* flag = nullptr;                // device-side data check (0 = ok)
+  // sorted layout of owned 1D columns (ascending by the first Voigtian's observable)
+  bool sorted = false;
+  int sort_obs = -1;                  // the column the events are sorted by
+  int32_t* perm = nullptr;            // sorted position -> original event index
+  int evals_since_load = 0;           // evaluations since the columns were (re)loaded
 };
 
 }  // namespace gfi
@@ -111,6 +116,7 @@ struct gf_ctx {
   int last_launches = 0;
   bool last_graph = false;  // the last evaluation replayed a captured graph
   bool graphs = true;       // replay captured graphs of steady evaluations
+  bool event_sort = true;   // keep owned 1D columns sorted for the chunked event loop
 };
 
 namespace gfi {

@@ -1,7 +1,7 @@
 // gf_internal.h -- plans shared by the host-side PDF-tree compiler (capi.cpp) and the
-// sm_103a kernels (k_1d.cu, k_dalitz.cu).  Plain structs passed to kernels by value
-// (they land in the constant bank, so every warp reads the same instruction stream
-// with broadcast loads).
+// sm_103a kernels (k_1d.cu, k_dalitz.cu).  Plain structs: the Dalitz plan and the
+// Faddeeva table go to kernels by value (constant bank), the 1D program lives in device
+// memory and each block copies it to shared memory.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -17,11 +17,12 @@ constexpr int kLeafRec = 20;    // doubles per leaf record: invN, logN, dlogN[8]
 constexpr int kMaxFree1D = 24;  // free parameters of a 1D model with gradient
 constexpr int kMaxStack = 4;    // evaluation stack depth (Sethi-Ullman ordered)
 constexpr int kMaxRes = 12;     // resonances of a Dalitz model
-constexpr int kWeidN = 40;      // terms of the FP64 Faddeeva series
-constexpr int kWeidNf = 16;     // terms of the FP32 Faddeeva series
+constexpr int kWeidN = 40;      // terms of the Faddeeva series
 constexpr int kThreads = 256;   // threads per block of the Dalitz and normalisation kernels
 constexpr int kThreads1D = 128; // threads per block of the 1D event kernel (its gradient
                                 // stack: 5 x nfree x 128 doubles of shared memory <= 123 KB)
+constexpr int kChunk = 24;      // sorted 1D data: events per expansion of w (k_1d.cu); the
+                                // chunked loop runs when there are >= kChunk/2 events per thread
 
 // Leaf kinds (shape functions; Sec. 2-3 of the paper and gf.h).
 enum Leaf : int32_t { L_EXP = 1, L_GAUSS = 2, L_VOIGT = 3, L_THRESH = 4, L_POLY = 5 };
@@ -61,7 +62,10 @@ struct CoefDesc {
 };
 
 struct Program {
-  int32_t n, nleaf, ncoef, nfree, nobs, root_log, ngrid_blocks, pad;
+  int32_t n, nleaf, ncoef, nfree, nobs, root_log, ngrid_blocks;
+  int32_t tay_slot;  // leaf record of the first Voigtian leaf (expanded per chunk), -1: none
+  int32_t tay_obs;   // its observable column
+  int32_t sorted;    // events sorted ascending by column tay_obs (chunked event loop)
   Instr ins[kMaxIns];
   LeafDesc leaf[kMaxLeaf];
   CoefDesc coef[kMaxCoef];

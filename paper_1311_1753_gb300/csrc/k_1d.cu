@@ -10,6 +10,7 @@
 //               by the last block in a fixed order.
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 #include "devutil.cuh"
 #include "gf_internal.h"
 #include "launch.h"
@@ -314,6 +315,69 @@ struct ArD {
   }
 };
 
+// ---- per-chunk expansion of w(z) on sorted data ------------------------------------------
+// With the events sorted by the Voigtian's observable, a thread's chunk of kChunk
+// consecutive events spans a short interval of z = (x - mu)/(sigma sqrt2) + i y.  The
+// thread evaluates w exactly at the chunk's middle event z0 (faddeeva_f2) and builds the
+// Taylor coefficients t_k = w^(k)(z0)/k! from the differential equation w' = -2 z w +
+// 2i/sqrt(pi):  t_1 = -2 z0 t_0 + 2i/sqrt(pi),  t_{k+1} = -2 (z0 t_k + t_{k-1})/(k + 1).
+// Each event then takes w(z0 + d) = sum_k t_k d^k, d = Re z - Re z0 real, to degree
+// kTayDeg.  Used only when the chunk's largest |d| is at most kTayLim: |t_k| <= 3 on the
+// unit circle around any z0 with Im z0 >= 0 (Cauchy), so the truncation is below
+// 3 kTayLim^6 ~ 2e-21, and the coefficient rounding (amplified ~2|z0|^2 by the
+// recurrence at large |z0|) adds < 2e-13 relative to Re w at |z0| = 37, below the
+// series' own error there.  Wider chunks evaluate w directly per event.
+constexpr int kTayDeg = 5;
+constexpr float kTayLim = 3e-4f;
+
+struct Tay {
+  int slot;   // leaf record of the expanded Voigtian leaf, -1: none
+  bool ok;    // the current chunk uses the expansion
+  F2 z0;      // Re z0 (Im z0 is the leaf constant c[2])
+  F2* t;      // shared memory: t_k as (re, im) pairs, [kTayDeg + 1][2][stride], this thread
+  int stride;
+};
+
+__device__ __forceinline__ void cmul2(F2 ar, F2 ai, F2 br, F2 bi, F2& cr, F2& ci) {
+  cr = df_sub(df_mul(ar, br), df_mul(ai, bi));
+  ci = df_add(df_mul(ar, bi), df_mul(ai, br));
+}
+
+// Expansion of w at z0 = zr + i y into tay.t (caller checked the chunk width).
+__device__ __forceinline__ void tay_build(Tay& tay, F2 zr, F2 y, const WeidCoef& W) {
+  F2 tr[kTayDeg + 1], ti[kTayDeg + 1];
+  faddeeva_f2(zr, y, W, tr[0], ti[0]);
+  F2 ar, ai;
+  cmul2(zr, y, tr[0], ti[0], ar, ai);  // z0 t0
+  tr[1] = df_mul_f(ar, -2.f);
+  ti[1] = df_add(df_mul_f(ai, -2.f), DFC(kTwoInvSqrtPi));
+  constexpr DFC sc[kTayDeg] = {0.0, 1.0, 2.0 / 3, 0.5, 2.0 / 5};  // 2/(k + 1), k >= 1
+#pragma unroll
+  for (int k = 1; k < kTayDeg; ++k) {
+    cmul2(zr, y, tr[k], ti[k], ar, ai);
+    const F2 s = F2(sc[k]);
+    tr[k + 1] = df_neg(df_mul(df_add(ar, tr[k - 1]), s));
+    ti[k + 1] = df_neg(df_mul(df_add(ai, ti[k - 1]), s));
+  }
+#pragma unroll
+  for (int k = 0; k <= kTayDeg; ++k) {
+    tay.t[(2 * k) * tay.stride] = tr[k];
+    tay.t[(2 * k + 1) * tay.stride] = ti[k];
+  }
+  tay.z0 = zr;
+}
+
+__device__ __forceinline__ void tay_eval(const Tay& tay, F2 zr, F2& wr, F2& wi) {
+  const F2 d = df_sub(zr, tay.z0);
+  wr = tay.t[(2 * kTayDeg) * tay.stride];
+  wi = tay.t[(2 * kTayDeg + 1) * tay.stride];
+#pragma unroll
+  for (int k = kTayDeg - 1; k >= 0; --k) {
+    wr = df_add(df_mul(wr, d), tay.t[(2 * k) * tay.stride]);
+    wi = df_add(df_mul(wi, d), tay.t[(2 * k + 1) * tay.stride]);
+  }
+}
+
 // ---- event-side leaf evaluation ------------------------------------------------------------
 // Returns the normalised leaf value (log domain for EXP and GAUSS).  With G, adds the
 // partials with respect to the leaf's free parameters into the gradient slot g (stride bd).
@@ -323,7 +387,7 @@ template <class A, bool G>
 __device__ __forceinline__ typename A::T eval_leaf(const Instr& I, const double* rec,
                                                    const typename A::T* r, double x,
                                                    const WeidCoef& W, typename A::T* g,
-                                                   int bd) {
+                                                   int bd, const Tay* tay) {
   using T = typename A::T;
   const T* c = r + 10;
   switch (I.kind) {
@@ -345,7 +409,12 @@ __device__ __forceinline__ typename A::T eval_leaf(const Instr& I, const double*
     case L_VOIGT: {
       const T zr = A::mul(A::diff(x, rec[10]), c[1]);
       T wr, wi;
-      A::faddeeva(zr, c[2], W, wr, wi);
+      if constexpr (std::is_same<A, ArF2>::value) {
+        if (tay && tay->ok && I.slot == tay->slot) tay_eval(*tay, zr, wr, wi);
+        else A::faddeeva(zr, c[2], W, wr, wi);
+      } else {
+        A::faddeeva(zr, c[2], W, wr, wi);
+      }
       const T l = A::mul(c[3], wr);
       if (G) {
         // w' = -2 z w + 2i/sqrt(pi)
@@ -411,7 +480,8 @@ template <class A, bool G>
 __device__ __forceinline__ typename A::T run_program(const Program& P, const double* rec,
                                                      const typename A::T* rc, const double* x,
                                                      const WeidCoef& W, typename A::T* dyn,
-                                                     int nf, int bd, int tid) {
+                                                     int nf, int bd, int tid,
+                                                     const Tay* tay = nullptr) {
   using T = typename A::T;
   const T* coef = rc + kMaxLeaf * kLeafRec;
   T s0 = A::zero(), s1 = A::zero(), s2 = A::zero(), s3 = A::zero();
@@ -425,7 +495,7 @@ __device__ __forceinline__ typename A::T run_program(const Program& P, const dou
         if (G)
           for (int k = 0; k < nf; ++k) gn[k * bd] = A::zero();
         const T v = eval_leaf<A, G>(I, rec + I.slot * kLeafRec, rc + I.slot * kLeafRec, x[I.obs],
-                                    W, gn, bd);
+                                    W, gn, bd, tay);
         s3 = s2; s2 = s1; s1 = s0; s0 = v;
         ++dep;
         break;
@@ -491,8 +561,9 @@ __device__ __forceinline__ void events_1d_block(
     const Program& P, const WeidCoef& W, const Cols& cols, const int64_t n,
     const double* __restrict__ theta, const double* __restrict__ derived_g,
     double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
-    double* __restrict__ out_logp, const int analytic_only, const int vb, const int vgrid,
-    double* dyn, double* rec, F2* rf, double* red, int* last) {
+    double* __restrict__ out_logp, const int32_t* __restrict__ perm, const int analytic_only,
+    const int vb, const int vgrid, double* dyn, double* rec, F2* rf, double* red, int* last,
+    F2* tay_smem) {
   const int bd = blockDim.x, tid = threadIdx.x;
   const int nf = P.nfree;
   constexpr int kRec = kMaxLeaf * kLeafRec + kMaxCoef;
@@ -512,60 +583,97 @@ __device__ __forceinline__ void events_1d_block(
     for (int k = 0; k < nf; ++k) gacc[k * bd] = F2{0.f, 0.f};
   F2 acc = {0.f, 0.f};
 
-  const int64_t npairs = (n + 1) >> 1;
-  const int64_t stride = (int64_t)vgrid * bd;
-  for (int64_t pr = (int64_t)vb * bd + tid; pr < npairs; pr += stride) {
-    double2 xv[kMaxObs];
-    const bool full = 2 * pr + 1 < n;  // the last pair of an odd n holds one event
-#pragma unroll
-    for (int o = 0; o < kMaxObs; ++o)
-      if (o < P.nobs) {
-        if (full) {
-          xv[o] = __ldcs(reinterpret_cast<const double2*>(cols.c[o]) + pr);
-        } else {
-          xv[o].x = __ldcs(cols.c[o] + 2 * pr);
-          xv[o].y = 0.0;
+  // one event: log P_i into the sums (MODE 0) or out_logp (MODE 1, through perm if sorted)
+  auto one_event = [&](int64_t i, const double* x, const Tay* tay) {
+    const F2 s = run_program<ArF2, G>(P, rec, rf, x, W, dynf, nf, bd, tid, tay);
+    // P in [2^-80, 2^125): every term that underflowed on the way (absolute error below
+    // 2^-149 times a leaf constant) is negligible against P
+    const bool ok = P.root_log ? (fabsf(s.hi) < 3.0e38f)
+                               : (s.hi >= 8.271806125530277e-25f && s.hi < 4.2535295865117308e37f);
+    if (ok) {
+      const F2 lp = P.root_log ? s : df_log_tab(s, s_log_tab);
+      if (MODE == 1) {
+        out_logp[perm ? perm[i] : i] = df_to(lp);
+      } else {
+        acc = df_sub(acc, lp);
+        if (G) {
+          const F2 sc = P.root_log ? F2{-1.f, 0.f} : df_neg(df_rcp(s));
+          const F2* g0 = dynf + tid;
+          for (int k = 0; k < nf; ++k) gacc[k * bd] = df_add(gacc[k * bd], df_mul(g0[k * bd], sc));
         }
       }
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int64_t i = 2 * pr + e;
-      if (i >= n) break;
-      double x[kMaxObs];
-#pragma unroll
-      for (int o = 0; o < kMaxObs; ++o) x[o] = e ? xv[o].y : xv[o].x;
-      const F2 s = run_program<ArF2, G>(P, rec, rf, x, W, dynf, nf, bd, tid);
-      // P in [2^-80, 2^125): every term that underflowed on the way (absolute error below
-      // 2^-149 times a leaf constant) is negligible against P
-      const bool ok = P.root_log ? (fabsf(s.hi) < 3.0e38f)
-                                 : (s.hi >= 8.271806125530277e-25f && s.hi < 4.2535295865117308e37f);
-      if (ok) {
-        const F2 lp = P.root_log ? s : df_log_tab(s, s_log_tab);
-        if (MODE == 1) {
-          out_logp[i] = df_to(lp);
-        } else {
-          acc = df_sub(acc, lp);
-          if (G) {
-            const F2 sc = P.root_log ? F2{-1.f, 0.f} : df_neg(df_rcp(s));
-            const F2* g0 = dynf + tid;
-            for (int k = 0; k < nf; ++k) gacc[k * bd] = df_add(gacc[k * bd], df_mul(g0[k * bd], sc));
-          }
-        }
+    } else {
+      // outside the float exponent range: this event again in FP64
+      const double sd = run_program_fp64<G>(P, rec, x, W, dyn, nf, bd, tid);
+      const double lp = P.root_log ? sd : df_log(sd);
+      if (MODE == 1) {
+        out_logp[perm ? perm[i] : i] = lp;
       } else {
-        // outside the float exponent range: this event again in FP64
-        const double sd = run_program_fp64<G>(P, rec, x, W, dyn, nf, bd, tid);
-        const double lp = P.root_log ? sd : df_log(sd);
-        if (MODE == 1) {
-          out_logp[i] = lp;
-        } else {
-          acc = df_sub(acc, df_from(lp));
-          if (G) {
-            const double sc = P.root_log ? -1.0 : -1.0 / sd;
-            const double* g0 = dyn + tid;
-            for (int k = 0; k < nf; ++k)
-              gacc[k * bd] = df_add(gacc[k * bd], df_from(g0[k * bd] * sc));
+        acc = df_sub(acc, df_from(lp));
+        if (G) {
+          const double sc = P.root_log ? -1.0 : -1.0 / sd;
+          const double* g0 = dyn + tid;
+          for (int k = 0; k < nf; ++k)
+            gacc[k * bd] = df_add(gacc[k * bd], df_from(g0[k * bd] * sc));
+        }
+      }
+    }
+  };
+
+  const int64_t nthreads = (int64_t)vgrid * bd;
+  const bool chunked = tay_smem && P.sorted && P.tay_slot >= 0 &&
+                       n >= (int64_t)kChunk / 2 * nthreads;
+  if (chunked) {
+    // sorted events: thread g takes the contiguous share [n g / T, n (g + 1) / T), in
+    // chunks of kChunk with one expansion of w per chunk
+    Tay tay;
+    tay.slot = P.tay_slot;
+    tay.t = tay_smem + tid;
+    tay.stride = bd;
+    const int64_t g = (int64_t)vb * bd + tid;
+    const int64_t lo = n * g / nthreads, hi = n * (g + 1) / nthreads;
+    const double* xc = cols.c[P.tay_obs];
+    const double* rv = rec + P.tay_slot * kLeafRec;
+    const F2* fv = rf + P.tay_slot * kLeafRec;
+    for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
+      const int cnt = (int)(hi - c0 < kChunk ? hi - c0 : kChunk);
+      const double xm = __ldg(xc + c0 + (cnt - 1) / 2);
+      const float da = fabsf(__fmul_rn((float)(__ldg(xc + c0) - xm), fv[11].hi));
+      const float db = fabsf(__fmul_rn((float)(__ldg(xc + c0 + cnt - 1) - xm), fv[11].hi));
+      tay.ok = fmaxf(da, db) <= kTayLim;
+      if (tay.ok) tay_build(tay, df_mul(df_split(xm - rv[10]), fv[11]), fv[12], W);
+      for (int k = 0; k < cnt; ++k) {
+        const int64_t i = c0 + k;
+        double x[kMaxObs];
+#pragma unroll
+        for (int o = 0; o < kMaxObs; ++o)
+          if (o < P.nobs) x[o] = __ldg(cols.c[o] + i);
+        one_event(i, x, &tay);
+      }
+    }
+  } else {
+    const int64_t npairs = (n + 1) >> 1;
+    for (int64_t pr = (int64_t)vb * bd + tid; pr < npairs; pr += nthreads) {
+      double2 xv[kMaxObs];
+      const bool full = 2 * pr + 1 < n;  // the last pair of an odd n holds one event
+#pragma unroll
+      for (int o = 0; o < kMaxObs; ++o)
+        if (o < P.nobs) {
+          if (full) {
+            xv[o] = __ldcs(reinterpret_cast<const double2*>(cols.c[o]) + pr);
+          } else {
+            xv[o].x = __ldcs(cols.c[o] + 2 * pr);
+            xv[o].y = 0.0;
           }
         }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int64_t i = 2 * pr + e;
+        if (i >= n) break;
+        double x[kMaxObs];
+#pragma unroll
+        for (int o = 0; o < kMaxObs; ++o) x[o] = e ? xv[o].y : xv[o].x;
+        one_event(i, x, nullptr);
       }
     }
   }
@@ -585,20 +693,22 @@ __device__ __forceinline__ void events_1d_block(
 
 template <bool G, int MODE>
 __global__ void __launch_bounds__(kThreads1D) k_events_1d(
-    const Program* __restrict__ Pg, const __grid_constant__ WeidCoef W, const Cols cols, const int64_t n,
-    const double* __restrict__ theta, const double* __restrict__ derived_g,
+    const Program* __restrict__ Pg, const __grid_constant__ WeidCoef W, const Cols cols,
+    const int64_t n, const double* __restrict__ theta, const double* __restrict__ derived_g,
     double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
-    double* __restrict__ out_logp, const int analytic_only) {
+    double* __restrict__ out_logp, const int32_t* __restrict__ perm, const int analytic_only) {
   extern __shared__ double dyn[];  // G: (kMaxStack + 1) * nfree * blockDim entries
   __shared__ Program P;
   __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
   __shared__ F2 rf[kMaxLeaf * kLeafRec + kMaxCoef];
   __shared__ double red[32];
   __shared__ int last;
+  __shared__ F2 tay_t[(kTayDeg + 1) * 2 * kThreads1D];
   load_tables();
   load_program(Pg, P);
   events_1d_block<G, MODE>(P, W, cols, n, theta, derived_g, partials, counter, result, out_logp,
-                           analytic_only, blockIdx.x, gridDim.x, dyn, rec, rf, red, &last);
+                           perm, analytic_only, blockIdx.x, gridDim.x, dyn, rec, rf, red, &last,
+                           tay_t);
 }
 
 // ---- batched tick: every waiting 1D fit in one persistent launch -----------------------
@@ -654,8 +764,8 @@ __global__ void __launch_bounds__(kThreads1D) k_tick_events_1d(const TickItem* _
     const TickItem& ti = tick_item(items, nfits, it, cur, Ps);
     const Fit1D* F = static_cast<const Fit1D*>(ti.fit);
     events_1d_block<true, 0>(Ps, W, F->cols, F->n, ti.theta, F->derived, F->partials,
-                             F->counter_ev, ti.result, nullptr, F->analytic_only, it - ti.item0,
-                             ti.nitems, dyn, rec, rf, red, &last);
+                             F->counter_ev, ti.result, nullptr, nullptr, F->analytic_only,
+                             it - ti.item0, ti.nitems, dyn, rec, rf, red, &last, nullptr);
     __syncthreads();
   }
 }
@@ -716,19 +826,23 @@ size_t events_1d_smem(const Program& P, bool grad, int threads) {
 cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCoef& W,
                              const Cols& cols, int64_t n,
                              const double* theta, const double* derived, double* partials,
-                             unsigned* counter, double* result, double* out_logp, bool grad,
-                             bool store, int analytic_only, int nblocks, cudaStream_t st) {
+                             unsigned* counter, double* result, double* out_logp,
+                             const int32_t* perm, bool grad, bool store, int analytic_only,
+                             int nblocks, cudaStream_t st) {
   const int threads = kThreads1D;
   const size_t smem = events_1d_smem(P, grad, threads);
   if (store) {
     k_events_1d<false, 1><<<nblocks, threads, 0, st>>>(prog, W, cols, n, theta, derived, partials,
-                                                       counter, result, out_logp, analytic_only);
+                                                       counter, result, out_logp, perm,
+                                                       analytic_only);
   } else if (grad) {
     k_events_1d<true, 0><<<nblocks, threads, smem, st>>>(prog, W, cols, n, theta, derived, partials,
-                                                         counter, result, out_logp, analytic_only);
+                                                         counter, result, out_logp, nullptr,
+                                                         analytic_only);
   } else {
     k_events_1d<false, 0><<<nblocks, threads, 0, st>>>(prog, W, cols, n, theta, derived, partials,
-                                                       counter, result, out_logp, analytic_only);
+                                                       counter, result, out_logp, nullptr,
+                                                       analytic_only);
   }
   return cudaGetLastError();
 }

@@ -250,6 +250,8 @@ extern "C" int gf_nll_noalloc(gf_ctx* ctx, int root, int nobs, const int* obs, i
   Program P{};
   P.nobs = nobs;
   P.nfree = nf;
+  P.tay_slot = -1;  // the caller's columns are used as they are: strided event loop
+  P.sorted = 0;
   NACompiler C{ctx, P, col_of_obs, free_pos};
   uint64_t used = 0;
   const int dom = C.walk(root, &used);
@@ -314,7 +316,8 @@ extern "C" int gf_nll_noalloc(gf_ctx* ctx, int root, int nobs, const int* obs, i
   Cols cols{};
   for (int k = 0; k < nobs; ++k) cols.c[k] = dev_cols[k];
   if (e == cudaSuccess)
-    e = launch_events_1d(P, d_prog, W, cols, n, d_theta, d_derived, d_pev, d_cnt_ev, nll_dev, nullptr,
+    e = launch_events_1d(P, d_prog, W, cols, n, d_theta, d_derived, d_pev, d_cnt_ev, nll_dev,
+                         nullptr, nullptr,
                          false, false, has_grid ? 0 : 1, (int)nb, st);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -14,13 +14,25 @@ cudaError_t launch_norm_1d(const Program& P, const Program* prog, const WeidCoef
                            const double* theta, double* partials, unsigned* counter,
                            double* derived, cudaStream_t st);
 size_t events_1d_smem(const Program& P, bool grad, int threads);
+// store: out_logp[perm ? perm[i] : i] = log P_i (perm: the sort permutation of the
+// data set, or nullptr); otherwise the NLL (and gradient) into result.
 cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCoef& W,
                              const Cols& cols, int64_t n,
                              const double* theta, const double* derived, double* partials,
-                             unsigned* counter, double* result, double* out_logp, bool grad,
-                             bool store, int analytic_only, int nblocks, cudaStream_t st);
+                             unsigned* counter, double* result, double* out_logp,
+                             const int32_t* perm, bool grad, bool store, int analytic_only,
+                             int nblocks, cudaStream_t st);
 int events_1d_blocks_per_sm(bool grad, size_t smem);  // also opts in to large shared memory
 void prepare_kernels_1d();
+// Sort (key, index) pairs ascending by the FP64 key (k_sort.cu): perm_tmp receives
+// 0 .. n-1, perm_out the permutation, key_out the sorted keys.  temp == nullptr: only
+// sets *temp_bytes to the scratch size the sort needs.
+cudaError_t sort_by_key_f64(const double* key_in, double* key_out, int32_t* perm_tmp,
+                            int32_t* perm_out, int64_t n, void* temp, size_t* temp_bytes,
+                            cudaStream_t st);
+// out[i] = in[perm[i]]
+cudaError_t launch_gather(const double* in, const int32_t* perm, double* out, int64_t n,
+                          cudaStream_t st);
 void prepare_kernels_dalitz();
 // batched fit-server tick (persistent launches over a work list of TickItems)
 cudaError_t launch_tick_1d(bool norm, const TickItem* items, int nfits, int total,

@@ -259,6 +259,8 @@ static void scheduler(gf_server* S) {
       if (S->used_bytes + R->bytes > S->opts.mem_budget && !S->active.empty()) break;
       S->pending.pop_front();
       lk.unlock();
+      // batched ticks walk the events strided: a sorted copy would not pay for itself
+      R->ctx->event_sort = false;
       int rc = gf_set_data(R->ctx, R->root, R->ds);
       lk.lock();
       if (rc != GF_OK) {
