@@ -36,12 +36,21 @@ from paper_1311_1753_gb300 import synth  # noqa: E402
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# Algorithmic FP64 flops per event of the config-2 event pass with the fused gradient,
-# counted from the source (FMA = 2, add/mul = 1; each exp, log, sqrt or division = 1):
-# Faddeeva series N = 40 (Horner 39 x 7 + 32 setup) = 305; Voigt value and 3 partials
-# 31; threshold value and partial 9; two fraction scalings with 5-wide gradients 14;
-# sum and gradient sum 6; log P, 1/P and the 5 gradient accumulations 12.
-FLOPS_PER_EVENT = {"voigt_grad": 377, "voigt": 318}
+# The config-2 event pass computes FP64-accurate results in double-float arithmetic (pairs
+# of floats) on the FP32 pipe, so its roofline is the FP32 pipe.  Algorithmic work per
+# event = the FP32 flops of that double-float algorithm (FADD + FMUL + 2 FFMA executed per
+# event, predicated-on, counted by ncu on the 10^7-event launch of this configuration:
+# 857.9 + 89.5 + 2 x 237.6; profiles/k_events_1d_voigt_1e7.md).  DRAM traffic of one
+# launch from the same capture (80.87 MB read + 5.52 MB written).
+FP32_FLOPS_PER_EVENT = {"voigt_grad": 1422.6}
+TRAFFIC_PER_LAUNCH = {"voigt_grad": 86.38e6}
+# Context: the same pass in FP64 operations of the method (FMA = 2, add/mul = 1, each
+# exp, log, sqrt or division = 1), counted from the source: w(z) by one Weideman series
+# (N = 40: 305) and its degree-5 expansion per chunk of 24 events (recurrence ~40 per
+# chunk, evaluation 20, argument 3) = 37 per event; Voigt value and 3 partials 31;
+# threshold value and partial 9; two fraction scalings with 5-wide gradients 14; sum and
+# gradient sum 6; log P, 1/P and the 5 gradient accumulations 12.
+FP64_FLOPS_PER_EVENT = {"voigt_grad": 109}
 
 
 def _peaks():
@@ -306,15 +315,19 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     seed = synth.SEED_VOIGT + 1000 * rank
 
+    # arithmetic of the timed event pass: double-float pairs of f32 (FP64-accurate, f64 in
+    # and out) for the 1D paths, f64 for the Dalitz FP64 path, f32 amplitudes for the
+    # mixed Dalitz path
+    dtype = {"dalitz": "f64", "dalitz-mixed": "f32"}.get(args.workload, "df64")
     if args.workload == "voigt":
         n = 10_000_000
         ctx, root, obs, cols, th0 = voigt_workload(gf, n, seed, gf.GF_FP64)
-        flops_ev = FLOPS_PER_EVENT["voigt_grad"]
+        flops_ev = FP32_FLOPS_PER_EVENT["voigt_grad"]
         wl = "1D composite: Voigtian (mu,sigma,Gamma) + threshold (c) with fraction f, 10^7 FP64 events, 2 x 10,000-bin grid normalisation"
     elif args.workload == "exp":
         n = 100_000
         ctx, root, obs, cols, th0 = exp_workload(gf, n, synth.SEED_EXP + rank, gf.GF_FP64)
-        flops_ev = 4
+        flops_ev = None  # launch-latency bound at 10^5 events
         wl = "truncated exponential, 10^5 FP64 events, analytic normalisation"
         metric = "NLL+gradient evaluations: events x evals/s (exponential, FP64)"
     else:
@@ -350,13 +363,22 @@ def main():
     roofline = None
     if flops_ev is not None:
         ach = flops_ev * n / kern_s / 1e12
-        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                    "kernel": "k_events_1d<grad> (FP64 pipe)",
-                    "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (unit counts and max clock)",
+        ach64 = FP64_FLOPS_PER_EVENT["voigt_grad"] * n / kern_s / 1e12
+        roofline = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP32_PEAK_TFLOPS,
+                    "traffic": TRAFFIC_PER_LAUNCH["voigt_grad"],
+                    "kernel": "k_events_1d<grad> (double-float on the FP32 pipe)",
+                    "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz "
+                                   "(unit counts and max clock)",
                     "kernel_ms": kern_s * 1e3,
                     "algorithmic_flops_per_event": flops_ev,
-                    "hbm_frac_of_measured": (8 * n / kern_s / 1e9) / hbm_peak}
+                    "fp64_equivalent": {"flops_per_event": FP64_FLOPS_PER_EVENT["voigt_grad"],
+                                        "achieved_tflops": ach64,
+                                        "fp64_pipe_peak_tflops": FP64_PEAK_TFLOPS,
+                                        "frac": ach64 / FP64_PEAK_TFLOPS},
+                    "hbm": {"algorithmic_bytes_per_event": 8,
+                            "achieved_gbs": 8 * n / kern_s / 1e9,
+                            "frac_of_measured": (8 * n / kern_s / 1e9) / hbm_peak}}
 
     # end-to-end through the C ABI with host buffers
     e2e = None
@@ -388,7 +410,7 @@ def main():
         out = {"metric": metric, "value": value, "unit": unit, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                "config": {"workload": wl, "events": n, "free_params": len(th0),
                           "l2": "flushed between steps (256 MB write)",
                           "parallelism": f"replicas x{world} (independent data sets)"},

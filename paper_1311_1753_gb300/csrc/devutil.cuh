@@ -24,6 +24,12 @@ struct Acc<double> {
   __device__ __forceinline__ double get() const { return s; }
 };
 template <>
+struct Acc<DF> {
+  DF s = DF(0.f);
+  __device__ __forceinline__ void add(DF v) { s += v; }
+  __device__ __forceinline__ double get() const { return s.to_double(); }
+};
+template <>
 struct Acc<float> {
   float s = 0.f, c = 0.f;
   __device__ __forceinline__ void add(float v) {

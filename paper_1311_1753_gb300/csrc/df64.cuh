@@ -11,6 +11,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 
 namespace gfi {
@@ -108,6 +109,21 @@ __device__ __forceinline__ F2 df_sqrt(F2 a) {
   return fast_two_sum(s, __fmul_rn(e, __fdiv_rn(0.5f, s)));
 }
 
+// 1/sqrt(a), a > 0: float estimate y0 (MUFU, ~2^-22), then two Newton-Raphson steps
+// y <- y + y (1 - a y^2)/2, the second on the pair (error ~2^-47).
+__device__ __forceinline__ F2 df_rsqrt(F2 a) {
+  const float y0 = rsqrtf(a.hi);
+  // first step in float with the residual formed exactly: e = 1 - a.hi y0^2 - a.lo y0^2
+  const float p = __fmul_rn(y0, y0);
+  float e = __fmaf_rn(-a.hi, p, 1.f);
+  e = __fmaf_rn(-a.hi, __fmaf_rn(y0, y0, -p), e);
+  e = __fmaf_rn(-a.lo, p, e);
+  const F2 y1 = fast_two_sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), e));
+  // second step on pairs
+  const F2 r = df_sub(F2{1.f, 0.f}, df_mul(a, df_mul(y1, y1)));
+  return df_add(y1, df_mul_f(df_mul(y1, r), 0.5f));
+}
+
 // Constant c as a df64 pair, formed at compile time.
 struct DFC {
   float hi, lo;
@@ -202,6 +218,34 @@ __device__ __forceinline__ F2 df_log_tab(F2 a, const F2* __restrict__ G) {
   return df_add(el, lm);
 }
 
+// The tables, one copy per translation unit: filled on the host once per device
+// (upload_df_tables, from each unit's kernel preparation), copied into shared memory by
+// each block of the kernels that use them (load_df_tables, visible after a barrier).
+static __device__ F2 g_exp_tab[kTab], g_log_tab[kTab];
+static __shared__ F2 s_exp_tab[kTab], s_log_tab[kTab];
+
+__device__ __forceinline__ void load_df_tables() {
+  for (int k = threadIdx.x; k < kTab; k += blockDim.x) {
+    s_exp_tab[k] = g_exp_tab[k];
+    s_log_tab[k] = g_log_tab[k];
+  }
+}
+
+static inline void upload_df_tables() {
+  F2 e[kTab], g[kTab];
+  for (int j = 0; j < kTab; ++j) {
+    const double ev = std::exp2(j / (double)kTab);
+    const double c = 1.0 + (j + 0.5) / kTab;
+    const double gv = std::log(j >= kTab / 2 ? 0.5 * c : c);
+    e[j].hi = (float)ev;
+    e[j].lo = (float)(ev - (double)e[j].hi);
+    g[j].hi = (float)gv;
+    g[j].lo = (float)(gv - (double)g[j].hi);
+  }
+  cudaMemcpyToSymbol(g_exp_tab, e, sizeof(e));
+  cudaMemcpyToSymbol(g_log_tab, g, sizeof(g));
+}
+
 // ---- natural logarithm -----------------------------------------------------------------
 // x = m 2^e with m in [1/sqrt2, sqrt2) (exponent bits, integer pipe); log m = 2 atanh(s),
 // s = (m - 1)/(m + 1), |s| <= 0.1716, by its odd series to s^21 in df64; e ln2 in FP64.
@@ -238,6 +282,29 @@ __device__ __forceinline__ double df_exp(double u) {
   for (int j = 13; j >= 0; --j) p = df_add(df_mul(p, r), kExpSeries[j]);
   const double v = df_to(p);
   return __longlong_as_double(__double_as_longlong(v) + ((long long)k << 52));
+}
+
+// ---- value type with operators (template code written for float or double) ----------
+// Arithmetic on DF is the pair arithmetic above; values enter from FP64 through from(),
+// the bit split (no FP64 conversion instructions), and leave through to_double().
+struct DF {
+  float hi, lo;
+  DF() = default;
+  __device__ __forceinline__ constexpr DF(float v) : hi(v), lo(0.f) {}
+  __device__ __forceinline__ constexpr DF(F2 v) : hi(v.hi), lo(v.lo) {}
+  __device__ __forceinline__ constexpr DF(DFC v) : hi(v.hi), lo(v.lo) {}
+  __device__ __forceinline__ operator F2() const { return {hi, lo}; }
+  static __device__ __forceinline__ DF from(double v) { return DF(df_split(v)); }
+  __device__ __forceinline__ double to_double() const { return df_to(F2{hi, lo}); }
+};
+__device__ __forceinline__ DF operator+(DF a, DF b) { return df_add(a, b); }
+__device__ __forceinline__ DF operator-(DF a, DF b) { return df_sub(a, b); }
+__device__ __forceinline__ DF operator-(DF a) { return df_neg(a); }
+__device__ __forceinline__ DF operator*(DF a, DF b) { return df_mul(a, b); }
+__device__ __forceinline__ DF operator/(DF a, DF b) { return df_div(a, b); }
+__device__ __forceinline__ DF& operator+=(DF& a, DF b) { return a = a + b; }
+__device__ __forceinline__ bool operator>(DF a, DF b) {
+  return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
 }
 
 }  // namespace gfi

@@ -17,18 +17,6 @@
 
 namespace gfi {
 
-// exp / log tables of df_exp_tab and df_log_tab: filled on the host once per device
-// (prepare_kernels_1d), copied into shared memory by each block of the event kernels.
-__device__ F2 g_exp_tab[kTab], g_log_tab[kTab];
-__shared__ F2 s_exp_tab[kTab], s_log_tab[kTab];
-
-__device__ __forceinline__ void load_tables() {
-  for (int k = threadIdx.x; k < kTab; k += blockDim.x) {
-    s_exp_tab[k] = g_exp_tab[k];
-    s_log_tab[k] = g_log_tab[k];
-  }
-}
-
 // ---- shape functions (unnormalised r(x) and d r / d local parameter) ------------------
 // Voigtian: r = Re w(z)/(sigma sqrt(2 pi)), z = (x - mu)/(sigma sqrt 2) + i Gamma/(2 sigma sqrt 2).
 __device__ __forceinline__ double voigt_r(double x, double mu, double s, double G,
@@ -704,7 +692,7 @@ __global__ void __launch_bounds__(kThreads1D) k_events_1d(
   __shared__ double red[32];
   __shared__ int last;
   __shared__ F2 tay_t[(kTayDeg + 1) * 2 * kThreads1D];
-  load_tables();
+  load_df_tables();
   load_program(Pg, P);
   events_1d_block<G, MODE>(P, W, cols, n, theta, derived_g, partials, counter, result, out_logp,
                            perm, analytic_only, blockIdx.x, gridDim.x, dyn, rec, rf, red, &last,
@@ -758,7 +746,7 @@ __global__ void __launch_bounds__(kThreads1D) k_tick_events_1d(const TickItem* _
   __shared__ F2 rf[kMaxLeaf * kLeafRec + kMaxCoef];
   __shared__ double red[32];
   __shared__ int last;
-  load_tables();  // visible after tick_item's first barrier
+  load_df_tables();  // visible after tick_item's first barrier
   int cur = -1;
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const TickItem& ti = tick_item(items, nfits, it, cur, Ps);
@@ -850,18 +838,7 @@ cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCo
 // Opt the gradient kernels in to > 48 KB of dynamic shared memory on the current device.
 // Called once per device when a context is created: never inside a stream capture.
 void prepare_kernels_1d() {
-  F2 e[kTab], g[kTab];
-  for (int j = 0; j < kTab; ++j) {
-    const double ev = std::exp2(j / (double)kTab);
-    const double c = 1.0 + (j + 0.5) / kTab;
-    const double gv = std::log(j >= kTab / 2 ? 0.5 * c : c);
-    e[j].hi = (float)ev;
-    e[j].lo = (float)(ev - (double)e[j].hi);
-    g[j].hi = (float)gv;
-    g[j].lo = (float)(gv - (double)g[j].hi);
-  }
-  cudaMemcpyToSymbol(g_exp_tab, e, sizeof(e));
-  cudaMemcpyToSymbol(g_log_tab, g, sizeof(g));
+  upload_df_tables();
   cudaFuncSetAttribute(k_events_1d<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
   cudaFuncSetAttribute(k_tick_events_1d, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -13,6 +13,8 @@
 //   k_dalitz_stream    the event pass (METRIC_NLL / METRIC_STORE) or the direct norm
 //                      pass over grid cells (METRIC_NORM) when some shape is free;
 //                      FP64 or FP32 amplitudes (T), optional fused gradient (G)
+#include <type_traits>
+
 #include "devutil.cuh"
 #include "gf_internal.h"
 #include "launch.h"
@@ -32,18 +34,46 @@ template <>
 __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
 template <>
 __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ DF rsq<DF>(DF x) { return df_rsqrt(x); }
 template <typename T>
 __device__ __forceinline__ T rcp(T x);
 template <>
 __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
 template <>
 __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
+template <>
+__device__ __forceinline__ DF rcp<DF>(DF x) { return df_rcp(x); }
 template <typename T>
 __device__ __forceinline__ T lg(T x);
 template <>
 __device__ __forceinline__ double lg<double>(double x) { return log(x); }
 template <>
 __device__ __forceinline__ float lg<float>(float x) { return logf(x); }
+template <>
+__device__ __forceinline__ DF lg<DF>(DF x) { return df_log_tab(x, s_log_tab); }
+// an FP64 value in the arithmetic T (per block: conversion cost does not matter)
+template <typename T>
+__device__ __forceinline__ T conv(double v);
+template <>
+__device__ __forceinline__ double conv<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float conv<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ DF conv<DF>(double v) { return DF(df_from(v)); }
+// an event coordinate (FP64 data) in T, per event: the pair split has no FP64 conversion
+template <typename T>
+__device__ __forceinline__ T ev_in(double v) { return conv<T>(v); }
+template <>
+__device__ __forceinline__ DF ev_in<DF>(double v) { return DF::from(v); }
+template <typename T>
+__device__ __forceinline__ double to_d(T v) { return (double)v; }
+template <>
+__device__ __forceinline__ double to_d<DF>(DF v) { return v.to_double(); }
+template <typename T>
+__device__ __forceinline__ T third() { return (T)(1.0 / 3.0); }
+template <>
+__device__ __forceinline__ DF third<DF>() { return DF(DFC(1.0 / 3.0)); }
 
 // Per-call constants of one resonance, from theta (FP64 arithmetic, once per block).
 struct ResK {
@@ -126,6 +156,97 @@ __device__ __forceinline__ void chan_kin(const DalitzPlan& D, int ch, T s12, T s
   k.S2 = k.S1 * k.S1 - a2 * (T)4 * q2 * (T)(1.0 / 3.0);
 }
 
+// Per-block constants of the event pass in its arithmetic T (float or DF): channel
+// constants of the plan and per-resonance constants from theta, converted once per block
+// so that no event converts an FP64 value.
+template <typename T>
+struct DzC {
+  T thrA[3], thrB[3], k1[3], a2c[3], a2k[3];
+  T R2;
+  T m0[kMaxRes], m0sq[kMaxRes], K[kMaxRes], sB[kMaxRes], cr[kMaxRes], ci[kMaxRes];
+  T hF[kMaxRes], dDfac[kMaxRes], twom0[kMaxRes], invg0[kMaxRes];
+};
+
+// Threads 0..2 fill the channel constants, threads 0..nres-1 the resonance constants
+// (rk already holds the FP64 per-call constants); a barrier must follow.
+template <typename T>
+__device__ __forceinline__ void fill_dzc(const DalitzPlan& D, const ResK* rk, DzC<T>& C) {
+  const int t = threadIdx.x;
+  if (t < 3) {
+    const DalitzChannel& c = D.ch[t];
+    C.thrA[t] = conv<T>(c.thrA);
+    C.thrB[t] = conv<T>(c.thrB);
+    C.k1[t] = conv<T>(c.k1);
+    C.a2c[t] = conv<T>(c.a2c);
+    C.a2k[t] = conv<T>(c.a2k);
+  }
+  if (t == 0) C.R2 = conv<T>(D.R2);
+  if (t < D.nres) {
+    const ResK& k = rk[t];
+    C.m0[t] = conv<T>(k.m0);
+    C.m0sq[t] = conv<T>(k.m0sq);
+    C.K[t] = conv<T>(k.K);
+    C.sB[t] = conv<T>(k.sqrtB0);
+    C.cr[t] = conv<T>(k.cr);
+    C.ci[t] = conv<T>(k.ci);
+    C.hF[t] = conv<T>(k.hF);
+    C.dDfac[t] = conv<T>(1.0 + k.m0 * k.dlogK);
+    C.twom0[t] = conv<T>(2.0 * k.m0);
+    C.invg0[t] = conv<T>(k.invg0);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void chan_kin_c(const DzC<T>& C, int ch, T s12, T s13, T s23,
+                                           ChanK<T>& k) {
+  T sab, sbc, sac;
+  if (ch == 0) { sab = s12; sbc = s23; sac = s13; }
+  else if (ch == 1) { sab = s13; sbc = s23; sac = s12; }
+  else { sab = s23; sbc = s13; sac = s12; }
+  const T zero = T(0.f);
+  const T rs = rsq<T>(sab);
+  const T inv_s = rs * rs;
+  k.sab = sab;
+  k.minv = rs;
+  T q2 = (sab - C.thrA[ch]) * (sab - C.thrB[ch]) * inv_s * T(0.25f);
+  q2 = q2 > zero ? q2 : zero;
+  const T rq = q2 > zero ? rsq<T>(q2) : zero;
+  k.q = q2 * rq;
+  k.qp1 = k.q * q2;
+  k.qp2 = k.qp1 * q2;
+  const T z = q2 * C.R2;
+  const T B1 = T(1.f) + z;
+  const T B2 = z * (z + T(3.f)) + T(9.f);
+  k.rB1 = rsq<T>(B1);
+  k.iB1 = k.rB1 * k.rB1;
+  k.rB2 = rsq<T>(B2);
+  k.iB2 = k.rB2 * k.rB2;
+  k.S1 = sbc - sac + C.k1[ch] * inv_s;
+  const T a2 = sab - C.a2c[ch] + C.a2k[ch] * inv_s;
+  k.S2 = k.S1 * k.S1 - a2 * T(4.f) * q2 * third<T>();
+}
+
+// Breit-Wigner pieces of resonance r (event pass, arithmetic T = DF).
+template <typename T>
+__device__ __forceinline__ void res_amp_c(const DalitzRes& R, const DzC<T>& C, int r,
+                                          const ChanK<T>& c, C2<T>& A, T& FS, C2<T>& BW,
+                                          T& Gm) {
+  const int L = R.spin;
+  T qpow, iB, F, S;
+  if (L == 0) { qpow = c.q; iB = T(1.f); F = T(1.f); S = T(1.f); }
+  else if (L == 1) { qpow = c.qp1; iB = c.iB1; F = C.sB[r] * c.rB1; S = c.S1; }
+  else { qpow = c.qp2; iB = c.iB2; F = C.sB[r] * c.rB2; S = c.S2; }
+  Gm = C.K[r] * qpow * c.minv * iB;
+  const T Dr = C.m0sq[r] - c.sab;
+  const T mG = C.m0[r] * Gm;
+  const T inv = rcp<T>(Dr * Dr + mG * mG);
+  BW.r = Dr * inv;
+  BW.i = mG * inv;
+  FS = F * S;
+  A.r = FS * BW.r;
+  A.i = FS * BW.i;
+}
+
 // Breit-Wigner pieces of resonance r at an event: returns A_r, and (for the gradient)
 // FS = F_L S_L, BW, Gamma(m).
 template <typename T>
@@ -148,8 +269,9 @@ __device__ __forceinline__ void res_amp(const DalitzRes& R, const ResK& k, const
   A.i = FS * BW.i;
 }
 
-// Cached columns are double2 (FP64 plans, and the grid columns of every plan) or float2
-// (per-event columns of an FP32 plan); wide = 1 selects double2.
+// Cached columns: float2 per-event amplitudes of FP32 plans (wide = 0), double2 grid
+// columns of every plan (wide = 1), per-event amplitudes of FP64 plans as two float
+// pairs (re hi, re lo, im hi, im lo) in a float4 (wide = 2).
 // FP32 plans: the theta-dependent constants enter as hi + lo float pairs.  A constant
 // rounded once per call carries the same relative error into every event, so the FP32
 // likelihood would jump by ~n x 6e-8 whenever the rounding of m0, K, c_r ... flips as
@@ -193,12 +315,21 @@ __device__ __forceinline__ void res_amp_f(const DalitzRes& R, const ResKf& k, co
 template <typename T>
 __device__ __forceinline__ C2<T> load_cached(const void* base, int64_t stride, int slot,
                                              int64_t i, int wide) {
-  if (wide) {
+  if constexpr (std::is_same<T, DF>::value) {
+    if (wide == 2) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(base) + (size_t)slot * stride + i);
+      return {DF(F2{v.x, v.y}), DF(F2{v.z, v.w})};
+    }
     const double2 v = __ldg(reinterpret_cast<const double2*>(base) + (size_t)slot * stride + i);
+    return {DF::from(v.x), DF::from(v.y)};
+  } else {
+    if (wide) {
+      const double2 v = __ldg(reinterpret_cast<const double2*>(base) + (size_t)slot * stride + i);
+      return {(T)v.x, (T)v.y};
+    }
+    const float2 v = __ldg(reinterpret_cast<const float2*>(base) + (size_t)slot * stride + i);
     return {(T)v.x, (T)v.y};
   }
-  const float2 v = __ldg(reinterpret_cast<const float2*>(base) + (size_t)slot * stride + i);
-  return {(T)v.x, (T)v.y};
 }
 
 // ---- set-up kernels --------------------------------------------------------------------------
@@ -246,7 +377,8 @@ __global__ void k_dalitz_fcols(const DalitzPlan D, const double* __restrict__ s1
   }
 }
 
-// Per-event amplitudes of the event-cached resonances, FP64 (double2) or FP32 (float2).
+// Per-event amplitudes of the event-cached resonances: FP64 values stored as float pairs
+// (T = double, for the pair-arithmetic event pass) or FP32 (float2).
 template <typename T>
 __global__ void k_dalitz_ev_cache(const DalitzPlan D, const double* __restrict__ theta,
                                   const double* __restrict__ s12, const double* __restrict__ s13,
@@ -266,9 +398,11 @@ __global__ void k_dalitz_ev_cache(const DalitzPlan D, const double* __restrict__
       C2<double> A, BW;
       double FS, Gm;
       res_amp<double>(R, rk[r], ck[R.channel], A, FS, BW, Gm);
-      if (sizeof(T) == 8)
-        reinterpret_cast<double2*>(cache)[(size_t)R.ev_cached * n + i] = make_double2(A.r, A.i);
-      else
+      if (sizeof(T) == 8) {
+        const float rh = (float)A.r, ih = (float)A.i;
+        reinterpret_cast<float4*>(cache)[(size_t)R.ev_cached * n + i] =
+            make_float4(rh, (float)(A.r - (double)rh), ih, (float)(A.i - (double)ih));
+      } else
         reinterpret_cast<float2*>(cache)[(size_t)R.ev_cached * n + i] =
             make_float2((float)A.r, (float)A.i);
     }
@@ -393,16 +527,21 @@ __global__ void __launch_bounds__(kThreads) k_dalitz_gram(const DalitzPlan D,
 // -log P (events) or P dA (cells); with G the partials d/dtheta as well.
 // Shared memory: gacc[nfree][blockDim] per-thread gradient sums.
 // Shared scratch of one block (static part).
+template <typename T>
 struct DzShared {
   ResK rk[kMaxRes];
   ResKf rkf[kMaxRes];
+  DzC<T> C;
   double red[32];
   double tot[1 + 4 * kMaxRes];
   double logN;
   int last;
+  int need_ch[3];  // a channel's kinematics are needed by some resonance not cached
 };
 
-// Body of one (virtual) block vb of the vgrid blocks of a stream launch.
+// Body of one (virtual) block vb of the vgrid blocks of a stream launch.  T = float (FP32
+// plans: amplitudes in float with the hi/lo constants of ResKf) or DF (FP64 plans: every
+// step in double-float pairs; only the event coordinates' differences enter in FP64).
 template <typename T, bool G, int METRIC>
 __device__ __forceinline__ void dalitz_stream_block(
     const DalitzPlan& D, const double* __restrict__ theta, const double* __restrict__ s12d,
@@ -411,9 +550,12 @@ __device__ __forceinline__ void dalitz_stream_block(
     const uint8_t* __restrict__ inside,
     double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
     double* __restrict__ out_logp, const double* __restrict__ norm_in, int norm_mode,
-    const double* __restrict__ gram, const int vb, const int vgrid, double* dyn, DzShared& sh) {
+    const double* __restrict__ gram, const int vb, const int vgrid, double* dyn,
+    DzShared<T>& sh) {
+  constexpr bool kF = std::is_same<T, float>::value;
   ResK* rk = sh.rk;
   ResKf* rkf = sh.rkf;
+  const DzC<T>& C = sh.C;
   double* red = sh.red;
   const int tid = threadIdx.x, bd = blockDim.x;
   const int nf = D.nfree;
@@ -422,10 +564,16 @@ __device__ __forceinline__ void dalitz_stream_block(
     res_constants(D, D.res[tid], theta, rk[tid]);
     make_resf(rk[tid], rkf[tid]);
   }
+  if (tid < 3) {
+    int need = 0;
+    for (int r = 0; r < nres; ++r) need |= (D.res[r].ev_cached < 0 && D.res[r].channel == tid);
+    sh.need_ch[tid] = need;
+  }
   Acc<T>* gacc = reinterpret_cast<Acc<T>*>(dyn) + tid;
   if (G)
     for (int k = 0; k < nf; ++k) gacc[k * bd] = Acc<T>();
   __syncthreads();
+  fill_dzc<T>(D, rk, sh.C);
   if (METRIC == METRIC_STORE && tid == 0) {
     // normalised log P: log |A|^2 - log N, N = c^H G c (Gram mode) or the direct pass
     double N;
@@ -447,6 +595,7 @@ __device__ __forceinline__ void dalitz_stream_block(
     sh.logN = log(N);
   }
   __syncthreads();
+  const bool need0 = sh.need_ch[0] != 0, need1 = sh.need_ch[1] != 0, need2 = sh.need_ch[2] != 0;
   Acc<T> acc;
   const int64_t nitems = (METRIC == METRIC_NORM) ? (int64_t)D.nbx * D.nby : n;
 
@@ -456,59 +605,57 @@ __device__ __forceinline__ void dalitz_stream_block(
       if (!inside[i]) continue;
       const int ix = (int)(i / D.nby), iy = (int)(i % D.nby);
       const double da = D.x0 + (ix + 0.5) * D.hx, db = D.y0 + (iy + 0.5) * D.hy;
-      a = (T)da;
-      b = (T)db;
-      c = (T)(D.sum_m2 - da - db);
-    } else if (sizeof(T) == 8) {
+      a = ev_in<T>(da);
+      b = ev_in<T>(db);
+      c = ev_in<T>(D.sum_m2 - da - db);
+    } else if constexpr (!kF) {
       const double da = __ldcs(s12d + i), db = __ldcs(s13d + i);
-      a = (T)da;
-      b = (T)db;
-      c = (T)(D.sum_m2 - da - db);
+      a = ev_in<T>(da);
+      b = ev_in<T>(db);
+      c = ev_in<T>(D.sum_m2 - da - db);
     } else {
-      a = (T)__ldcs(sf + i);
-      b = (T)__ldcs(sf + n + i);
-      c = (T)__ldcs(sf + 2 * n + i);
+      a = __ldcs(sf + i);
+      b = __ldcs(sf + n + i);
+      c = __ldcs(sf + 2 * n + i);
     }
     ChanK<T> ck[3];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch) chan_kin<T>(D, ch, a, b, c, ck[ch]);
+    if (need0) chan_kin_c<T>(C, 0, a, b, c, ck[0]);
+    if (need1) chan_kin_c<T>(C, 1, a, b, c, ck[1]);
+    if (need2) chan_kin_c<T>(C, 2, a, b, c, ck[2]);
     C2<T> Ar[kMaxRes], BW[kMaxRes];
     T FS[kMaxRes], Gm[kMaxRes];
-    C2<T> At = {(T)1, (T)0};  // a_NR
+    C2<T> At = {T(1.f), T(0.f)};  // a_NR
 #pragma unroll
     for (int r = 0; r < kMaxRes; ++r) {
       if (r >= nres) break;
       const DalitzRes& R = D.res[r];
       if (R.ev_cached >= 0) {
         Ar[r] = load_cached<T>(cache, cache_stride, R.ev_cached, i, cache_wide);
-      } else if constexpr (sizeof(T) == 4) {
-        res_amp_f(R, rkf[r], reinterpret_cast<const ChanK<float>&>(ck[R.channel]),
-                  reinterpret_cast<C2<float>&>(Ar[r]), reinterpret_cast<float&>(FS[r]),
-                  reinterpret_cast<C2<float>&>(BW[r]), reinterpret_cast<float&>(Gm[r]));
+      } else if constexpr (kF) {
+        res_amp_f(R, rkf[r], ck[R.channel], Ar[r], FS[r], BW[r], Gm[r]);
       } else {
-        res_amp<T>(R, rk[r], ck[R.channel], Ar[r], FS[r], BW[r], Gm[r]);
+        res_amp_c<T>(R, C, r, ck[R.channel], Ar[r], FS[r], BW[r], Gm[r]);
       }
-      if constexpr (sizeof(T) == 4) {
+      if constexpr (kF) {
         const ResKf& f = rkf[r];
-        const T ar = Ar[r].r, ai = Ar[r].i;
+        const float ar = Ar[r].r, ai = Ar[r].i;
         At.r += fmaf(f.crh, ar, -f.cih * ai) + fmaf(f.crl, ar, -f.cil * ai);
         At.i += fmaf(f.crh, ai, f.cih * ar) + fmaf(f.crl, ai, f.cil * ar);
       } else {
-        const T cr = (T)rk[r].cr, ci = (T)rk[r].ci;
-        At.r += cr * Ar[r].r - ci * Ar[r].i;
-        At.i += cr * Ar[r].i + ci * Ar[r].r;
+        At.r += C.cr[r] * Ar[r].r - C.ci[r] * Ar[r].i;
+        At.i += C.cr[r] * Ar[r].i + C.ci[r] * Ar[r].r;
       }
     }
     const T P = At.r * At.r + At.i * At.i;
     if (METRIC == METRIC_STORE) {
-      out_logp[i] = (double)lg<T>(P) - sh.logN;
+      out_logp[i] = to_d<T>(lg<T>(P)) - sh.logN;
       continue;
     }
     if (METRIC == METRIC_NLL) acc.add(-lg<T>(P));
     else acc.add(P);
     if (G) {
       // d P / d theta; events use d(-log P) = -(dP)/P, cells use dP
-      const T sc = (METRIC == METRIC_NLL) ? (T)(-2) / P : (T)2;
+      const T sc = (METRIC == METRIC_NLL) ? T(-2.f) * rcp<T>(P) : T(2.f);
 #pragma unroll
       for (int r = 0; r < kMaxRes; ++r) {
         if (r >= nres) break;
@@ -517,28 +664,28 @@ __device__ __forceinline__ void dalitz_stream_block(
         const T xr = At.r * Ar[r].r + At.i * Ar[r].i;
         const T xi = At.r * Ar[r].i - At.i * Ar[r].r;
         if (R.g_re >= 0) gacc[R.g_re * bd].add(sc * xr);
-        if (R.g_im >= 0) gacc[R.g_im * bd].add(-sc * xi);
+        if (R.g_im >= 0) gacc[R.g_im * bd].add(-(sc * xi));
         if (R.ev_cached < 0 && (R.g_m0 >= 0 || R.g_g0 >= 0)) {
-          const T cr = (T)rk[r].cr, ci = (T)rk[r].ci;
+          const T cr = C.cr[r], ci = C.ci[r];
           // BW^2
           const T b2r = BW[r].r * BW[r].r - BW[r].i * BW[r].i;
-          const T b2i = (T)2 * BW[r].r * BW[r].i;
+          const T b2i = T(2.f) * BW[r].r * BW[r].i;
           // conj(A) c_r
           const T yr = At.r * cr + At.i * ci;
           const T yi = At.r * ci - At.i * cr;
           if (R.g_m0 >= 0) {
             // dA_r/dm0 = FS (hF BW - BW^2 dD),  dD = 2 m0 - i Gamma (1 + m0 dlogK)
-            const T dDr = (T)(2.0 * rk[r].m0);
-            const T dDi = -Gm[r] * (T)(1.0 + rk[r].m0 * rk[r].dlogK);
-            const T hF = (T)rk[r].hF;
+            const T dDr = C.twom0[r];
+            const T dDi = -(Gm[r] * C.dDfac[r]);
+            const T hF = C.hF[r];
             const T dr = FS[r] * (hF * BW[r].r - (b2r * dDr - b2i * dDi));
             const T di = FS[r] * (hF * BW[r].i - (b2r * dDi + b2i * dDr));
             gacc[R.g_m0 * bd].add(sc * (yr * dr - yi * di));
           }
           if (R.g_g0 >= 0) {
             // dA_r/dGamma0 = FS i m0 (Gamma/Gamma0) BW^2
-            const T f = FS[r] * (T)rk[r].m0 * Gm[r] * (T)rk[r].invg0;
-            const T dr = -f * b2i, di = f * b2r;
+            const T f = FS[r] * C.m0[r] * Gm[r] * C.invg0[r];
+            const T dr = -(f * b2i), di = f * b2r;
             gacc[R.g_g0 * bd].add(sc * (yr * dr - yi * di));
           }
         }
@@ -612,7 +759,8 @@ __global__ void __launch_bounds__(kThreads) k_dalitz_stream(
     double* __restrict__ out_logp, const double* __restrict__ norm_in, int norm_mode,
     const double* __restrict__ gram) {
   extern __shared__ double dyn[];
-  __shared__ DzShared sh;
+  __shared__ DzShared<T> sh;
+  load_df_tables();
   dalitz_stream_block<T, G, METRIC>(D, theta, s12d, s13d, sf, n, cache, cache_stride, cache_wide,
                                     inside, partials, counter, result, out_logp, norm_in,
                                     norm_mode, gram, blockIdx.x, gridDim.x, dyn, sh);
@@ -624,7 +772,8 @@ __global__ void __launch_bounds__(kThreads) k_tick_dalitz(const TickItem* __rest
                                                           int nfits, int total) {
   extern __shared__ double dyn[];
   __shared__ DalitzPlan Ds;
-  __shared__ DzShared sh;
+  __shared__ DzShared<T> sh;
+  load_df_tables();
   int cur = -1;
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     int f = 0;
@@ -744,10 +893,10 @@ cudaError_t launch_dalitz_norm_direct(const DalitzPlan& D, bool mixed, bool grad
                                                         nblocks, st);
   }
   if (grad)
-    return launch_stream_t<double, true, METRIC_NORM>(E, theta, B, B.grid_cols, ncell, 1,
+    return launch_stream_t<DF, true, METRIC_NORM>(E, theta, B, B.grid_cols, ncell, 1,
                                                         B.partials2, B.counter2, B.norm_out, 0,
                                                         nblocks, st);
-  return launch_stream_t<double, false, METRIC_NORM>(E, theta, B, B.grid_cols, ncell, 1,
+  return launch_stream_t<DF, false, METRIC_NORM>(E, theta, B, B.grid_cols, ncell, 1,
                                                        B.partials2, B.counter2, B.norm_out, 0,
                                                        nblocks, st);
 }
@@ -758,27 +907,27 @@ cudaError_t launch_dalitz_events(const DalitzPlan& D, bool mixed, bool grad, boo
   const int64_t cs = B.n;
   if (store) {
     if (mixed)
-      return launch_stream_t<float, false, METRIC_STORE>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 1, B.partials,
+      return launch_stream_t<float, false, METRIC_STORE>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 2, B.partials,
                                                            B.counter, B.result, norm_mode,
                                                            nblocks, st);
-    return launch_stream_t<double, false, METRIC_STORE>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 1, B.partials,
+    return launch_stream_t<DF, false, METRIC_STORE>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 2, B.partials,
                                                           B.counter, B.result, norm_mode, nblocks,
                                                           st);
   }
   if (mixed) {
     if (grad)
-      return launch_stream_t<float, true, METRIC_NLL>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 1, B.partials,
+      return launch_stream_t<float, true, METRIC_NLL>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 2, B.partials,
                                                         B.counter, B.result, norm_mode, nblocks,
                                                         st);
-    return launch_stream_t<float, false, METRIC_NLL>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 1, B.partials,
+    return launch_stream_t<float, false, METRIC_NLL>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 2, B.partials,
                                                        B.counter, B.result, norm_mode, nblocks,
                                                        st);
   }
   if (grad)
-    return launch_stream_t<double, true, METRIC_NLL>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 1, B.partials,
+    return launch_stream_t<DF, true, METRIC_NLL>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 2, B.partials,
                                                        B.counter, B.result, norm_mode, nblocks,
                                                        st);
-  return launch_stream_t<double, false, METRIC_NLL>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 1, B.partials,
+  return launch_stream_t<DF, false, METRIC_NLL>(D, theta, B, B.ev_cache, cs, mixed ? 0 : 2, B.partials,
                                                       B.counter, B.result, norm_mode, nblocks, st);
 }
 
@@ -786,24 +935,25 @@ cudaError_t launch_tick_dalitz(bool mixed, const TickItem* items, int nfits, int
                                size_t smem, int grid, cudaStream_t st) {
   if (total <= 0) return cudaSuccess;
   if (mixed) k_tick_dalitz<float><<<grid, kThreads, smem, st>>>(items, nfits, total);
-  else k_tick_dalitz<double><<<grid, kThreads, smem, st>>>(items, nfits, total);
+  else k_tick_dalitz<DF><<<grid, kThreads, smem, st>>>(items, nfits, total);
   return cudaGetLastError();
 }
 
 // Opt the gradient kernels in to > 48 KB of dynamic shared memory on the current device.
 // Called once per device when a context is created: never inside a stream capture.
 void prepare_kernels_dalitz() {
+  upload_df_tables();
   const int lim = 160 * 1024;
   cudaFuncSetAttribute(k_dalitz_stream<float, true, METRIC_NLL>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_dalitz_stream<float, true, METRIC_NORM>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_dalitz_stream<double, true, METRIC_NLL>,
+  cudaFuncSetAttribute(k_dalitz_stream<DF, true, METRIC_NLL>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_dalitz_stream<double, true, METRIC_NORM>,
+  cudaFuncSetAttribute(k_dalitz_stream<DF, true, METRIC_NORM>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_tick_dalitz<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_tick_dalitz<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_tick_dalitz<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 int dalitz_blocks_per_sm(bool mixed, bool grad) {
@@ -819,11 +969,11 @@ int dalitz_blocks_per_sm(bool mixed, bool grad) {
                                                     kThreads, 0);
   } else {
     if (grad)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dalitz_stream<double, true, METRIC_NLL>,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dalitz_stream<DF, true, METRIC_NLL>,
                                                     kThreads, smem);
     else
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &nb, k_dalitz_stream<double, false, METRIC_NLL>, kThreads, 0);
+          &nb, k_dalitz_stream<DF, false, METRIC_NLL>, kThreads, 0);
   }
   return nb > 0 ? nb : 1;
 }
