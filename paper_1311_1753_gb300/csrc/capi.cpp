@@ -823,7 +823,9 @@ static int finish_set_data(gf_ctx* ctx) {
   // event-stream grid: a multiple of the SM count, capped by the work
   int per_sm;
   if (ctx->is_dalitz) {
-    per_sm = dalitz_blocks_per_sm(ctx->precision == GF_MIXED, true);
+    bool co = ctx->dplan.nres > 0;
+    for (int r = 0; r < ctx->dplan.nres; ++r) co = co && ctx->dplan.res[r].ev_cached >= 0;
+    per_sm = dalitz_blocks_per_sm(ctx->precision == GF_MIXED, true, co, ctx->dplan.nfree);
   } else {
     per_sm = events_1d_blocks_per_sm(true, events_1d_smem(ctx->prog, true, kThreads1D));
   }
@@ -1194,7 +1196,7 @@ static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool capt
     if (mode == DN_DIRECT) {
       const int ncell_blocks = (int)std::min<int64_t>(
           ((int64_t)ctx->dplan.nbx * ctx->dplan.nby + kThreads - 1) / kThreads,
-          (int64_t)ctx->sm_count * 4);
+          (int64_t)ctx->sm_count);  // a few cells per thread: amortise the block set-up
       // the normalisation integral and its gradient in FP64 in every mode
       CK(launch_dalitz_norm_direct(ctx->dplan, false, grad, d.theta, B, ncell_blocks,
                                    ctx->stream));
@@ -1459,7 +1461,7 @@ static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host)
       if (mode == DN_DIRECT) {
         const int ncell_blocks = (int)std::min<int64_t>(
             ((int64_t)ctx->dplan.nbx * ctx->dplan.nby + kThreads - 1) / kThreads,
-            (int64_t)ctx->sm_count * 4);
+            (int64_t)ctx->sm_count);  // a few cells per thread: amortise the block set-up
         e = launch_dalitz_norm_direct(ctx->dplan, false, false, d.theta, B, ncell_blocks,
                                       ctx->stream);
       }

@@ -156,6 +156,16 @@ __device__ __forceinline__ void chan_kin(const DalitzPlan& D, int ch, T s12, T s
   k.S2 = k.S1 * k.S1 - a2 * (T)4 * q2 * (T)(1.0 / 3.0);
 }
 
+// a b + c d and |z|^2 with every rounding explicit (float: one fma and one product)
+template <typename T>
+__device__ __forceinline__ T dot2(T a, T b, T c, T d) { return a * b + c * d; }
+template <>
+__device__ __forceinline__ float dot2<float>(float a, float b, float c, float d) {
+  return __fmaf_rn(a, b, __fmul_rn(c, d));
+}
+template <typename T>
+__device__ __forceinline__ T cabs2(const C2<T>& z) { return dot2<T>(z.r, z.r, z.i, z.i); }
+
 // Per-block constants of the event pass in its arithmetic T (float or DF): channel
 // constants of the plan and per-resonance constants from theta, converted once per block
 // so that no event converts an FP64 value.
@@ -542,7 +552,9 @@ struct DzShared {
 // Body of one (virtual) block vb of the vgrid blocks of a stream launch.  T = float (FP32
 // plans: amplitudes in float with the hi/lo constants of ResKf) or DF (FP64 plans: every
 // step in double-float pairs; only the event coordinates' differences enter in FP64).
-template <typename T, bool G, int METRIC>
+// CO: every resonance comes from the event cache (fixed shapes): no kinematics, and the
+// gradient pass reloads the amplitudes (L1 hits) instead of keeping them in registers.
+template <typename T, bool G, int METRIC, bool CO = false>
 __device__ __forceinline__ void dalitz_stream_block(
     const DalitzPlan& D, const double* __restrict__ theta, const double* __restrict__ s12d,
     const double* __restrict__ s13d, const float* __restrict__ sf, int64_t n,
@@ -600,6 +612,45 @@ __device__ __forceinline__ void dalitz_stream_block(
   const int64_t nitems = (METRIC == METRIC_NORM) ? (int64_t)D.nbx * D.nby : n;
 
   for (int64_t i = (int64_t)vb * bd + tid; i < nitems; i += (int64_t)vgrid * bd) {
+    if constexpr (CO) {
+      C2<T> At = {T(1.f), T(0.f)};  // a_NR
+#pragma unroll
+      for (int r = 0; r < kMaxRes; ++r) {
+        if (r >= nres) break;
+        const C2<T> Ar = load_cached<T>(cache, cache_stride, D.res[r].ev_cached, i, cache_wide);
+        if constexpr (kF) {
+          const ResKf& f = rkf[r];
+          At.r = __fadd_rn(At.r, __fadd_rn(__fmaf_rn(f.crh, Ar.r, -__fmul_rn(f.cih, Ar.i)),
+                                           __fmaf_rn(f.crl, Ar.r, -__fmul_rn(f.cil, Ar.i))));
+          At.i = __fadd_rn(At.i, __fadd_rn(__fmaf_rn(f.crh, Ar.i, __fmul_rn(f.cih, Ar.r)),
+                                           __fmaf_rn(f.crl, Ar.i, __fmul_rn(f.cil, Ar.r))));
+        } else {
+          At.r += C.cr[r] * Ar.r - C.ci[r] * Ar.i;
+          At.i += C.cr[r] * Ar.i + C.ci[r] * Ar.r;
+        }
+      }
+      // the serving tick runs this path in another kernel: float roundings are spelled
+      // out (no contraction left to the compiler) so both give the same bits
+      const T P = cabs2<T>(At);
+      if (METRIC == METRIC_STORE) {
+        out_logp[i] = to_d<T>(lg<T>(P)) - sh.logN;
+        continue;
+      }
+      acc.add(-lg<T>(P));
+      if (G) {
+        const T sc = T(-2.f) * rcp<T>(P);
+        const C2<T> As = {sc * At.r, sc * At.i};
+#pragma unroll 1
+        for (int r = 0; r < nres; ++r) {
+          const DalitzRes& R = D.res[r];
+          const C2<T> Ar = load_cached<T>(cache, cache_stride, R.ev_cached, i, cache_wide);
+          // sc conj(A) A_r
+          if (R.g_re >= 0) gacc[R.g_re * bd].add(dot2<T>(As.r, Ar.r, As.i, Ar.i));
+          if (R.g_im >= 0) gacc[R.g_im * bd].add(dot2<T>(As.i, Ar.r, -As.r, Ar.i));
+        }
+      }
+      continue;
+    }
     T a, b, c;
     if (METRIC == METRIC_NORM) {
       if (!inside[i]) continue;
@@ -749,7 +800,7 @@ __device__ __forceinline__ void dalitz_stream_block(
   if (tid == 0) *counter = 0u;
 }
 
-template <typename T, bool G, int METRIC>
+template <typename T, bool G, int METRIC, bool CO>
 __global__ void __launch_bounds__(kThreads) k_dalitz_stream(
     const DalitzPlan D, const double* __restrict__ theta, const double* __restrict__ s12d,
     const double* __restrict__ s13d, const float* __restrict__ sf, int64_t n,
@@ -761,9 +812,9 @@ __global__ void __launch_bounds__(kThreads) k_dalitz_stream(
   extern __shared__ double dyn[];
   __shared__ DzShared<T> sh;
   load_df_tables();
-  dalitz_stream_block<T, G, METRIC>(D, theta, s12d, s13d, sf, n, cache, cache_stride, cache_wide,
-                                    inside, partials, counter, result, out_logp, norm_in,
-                                    norm_mode, gram, blockIdx.x, gridDim.x, dyn, sh);
+  dalitz_stream_block<T, G, METRIC, CO>(D, theta, s12d, s13d, sf, n, cache, cache_stride,
+                                        cache_wide, inside, partials, counter, result, out_logp,
+                                        norm_in, norm_mode, gram, blockIdx.x, gridDim.x, dyn, sh);
 }
 
 // ---- batched tick: every waiting Dalitz fit (Gram normalisation) in one persistent launch
@@ -788,7 +839,7 @@ __global__ void __launch_bounds__(kThreads) k_tick_dalitz(const TickItem* __rest
       __syncthreads();
       cur = f;
     }
-    dalitz_stream_block<T, true, METRIC_NLL>(Ds, ti.theta, F->s12, F->s13, F->sf, F->n,
+    dalitz_stream_block<T, true, METRIC_NLL, true>(Ds, ti.theta, F->s12, F->s13, F->sf, F->n,
                                              F->ev_cache, F->n, F->cache_wide, nullptr,
                                              F->partials, F->counter, ti.result, nullptr, nullptr,
                                              DN_GRAM, F->gram, it - ti.item0, ti.nitems, dyn, sh);
@@ -869,9 +920,16 @@ static cudaError_t launch_stream_t(const DalitzPlan& D, const double* theta, con
       (M == METRIC_STORE && !B.out_logp) || (B.n > 0 && (!B.s12 || !B.s13)))
     return cudaErrorInvalidValue;
   const size_t smem = G ? (size_t)D.nfree * kThreads * sizeof(Acc<T>) : 0;
-  k_dalitz_stream<T, G, M><<<nblocks, kThreads, smem, st>>>(
-      D, theta, B.s12, B.s13, B.sf, B.n, cache, cstride, cwide, B.inside, partials, counter, result,
-      B.out_logp, B.norm_out, norm_mode, B.gram);
+  bool co = M != METRIC_NORM && D.nres > 0;
+  for (int r = 0; r < D.nres; ++r) co = co && D.res[r].ev_cached >= 0;
+  if (co && M != METRIC_NORM)
+    k_dalitz_stream<T, G, M, true><<<nblocks, kThreads, smem, st>>>(
+        D, theta, B.s12, B.s13, B.sf, B.n, cache, cstride, cwide, B.inside, partials, counter,
+        result, B.out_logp, B.norm_out, norm_mode, B.gram);
+  else
+    k_dalitz_stream<T, G, M, false><<<nblocks, kThreads, smem, st>>>(
+        D, theta, B.s12, B.s13, B.sf, B.n, cache, cstride, cwide, B.inside, partials, counter,
+        result, B.out_logp, B.norm_out, norm_mode, B.gram);
   return cudaGetLastError();
 }
 
@@ -944,37 +1002,46 @@ cudaError_t launch_tick_dalitz(bool mixed, const TickItem* items, int nfits, int
 void prepare_kernels_dalitz() {
   upload_df_tables();
   const int lim = 160 * 1024;
-  cudaFuncSetAttribute(k_dalitz_stream<float, true, METRIC_NLL>,
+  cudaFuncSetAttribute(k_dalitz_stream<float, true, METRIC_NLL, false>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_dalitz_stream<float, true, METRIC_NORM>,
+  cudaFuncSetAttribute(k_dalitz_stream<float, true, METRIC_NORM, false>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_dalitz_stream<DF, true, METRIC_NLL>,
+  cudaFuncSetAttribute(k_dalitz_stream<DF, true, METRIC_NLL, false>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_dalitz_stream<DF, true, METRIC_NORM>,
+  cudaFuncSetAttribute(k_dalitz_stream<DF, true, METRIC_NORM, false>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_dalitz_stream<float, true, METRIC_NLL, true>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_dalitz_stream<DF, true, METRIC_NLL, true>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_tick_dalitz<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_tick_dalitz<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
-int dalitz_blocks_per_sm(bool mixed, bool grad) {
+int dalitz_blocks_per_sm(bool mixed, bool grad, bool cached_only, int nfree) {
   int nb = 0;
-  // smem depends on nfree; size for the largest plan (4 kMaxRes free parameters)
-  const size_t smem = grad ? (size_t)4 * kMaxRes * kThreads * (mixed ? 8 : 8) : 0;
+  const size_t smem = grad ? (size_t)(nfree > 0 ? nfree : 1) * kThreads * 8 : 0;
+  auto q = [&](const void* f, size_t sm) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, sm);
+  };
   if (mixed) {
-    if (grad)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dalitz_stream<float, true, METRIC_NLL>,
-                                                    kThreads, smem);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dalitz_stream<float, false, METRIC_NLL>,
-                                                    kThreads, 0);
+    if (cached_only) {
+      if (grad) q((const void*)k_dalitz_stream<float, true, METRIC_NLL, true>, smem);
+      else q((const void*)k_dalitz_stream<float, false, METRIC_NLL, true>, 0);
+    } else {
+      if (grad) q((const void*)k_dalitz_stream<float, true, METRIC_NLL, false>, smem);
+      else q((const void*)k_dalitz_stream<float, false, METRIC_NLL, false>, 0);
+    }
   } else {
-    if (grad)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dalitz_stream<DF, true, METRIC_NLL>,
-                                                    kThreads, smem);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &nb, k_dalitz_stream<DF, false, METRIC_NLL>, kThreads, 0);
+    if (cached_only) {
+      if (grad) q((const void*)k_dalitz_stream<DF, true, METRIC_NLL, true>, smem);
+      else q((const void*)k_dalitz_stream<DF, false, METRIC_NLL, true>, 0);
+    } else {
+      if (grad) q((const void*)k_dalitz_stream<DF, true, METRIC_NLL, false>, smem);
+      else q((const void*)k_dalitz_stream<DF, false, METRIC_NLL, false>, 0);
+    }
   }
+  cudaGetLastError();
   return nb > 0 ? nb : 1;
 }
 

@@ -81,7 +81,7 @@ cudaError_t launch_dalitz_norm_direct(const DalitzPlan& D, bool mixed, bool grad
 cudaError_t launch_dalitz_events(const DalitzPlan& D, bool mixed, bool grad, bool store,
                                  int norm_mode, const double* theta, const DalitzBufs& B,
                                  int nblocks, cudaStream_t st);
-int dalitz_blocks_per_sm(bool mixed, bool grad);
+int dalitz_blocks_per_sm(bool mixed, bool grad, bool cached_only, int nfree);
 cudaError_t launch_tick_dalitz(bool mixed, const TickItem* items, int nfits, int total,
                                size_t smem, int grid, cudaStream_t st);
 constexpr int kGramEntries = (kMaxRes + 1) * (kMaxRes + 2) / 2;
