@@ -1037,15 +1037,20 @@ static int fill_theta_host(gf_ctx* ctx, const double* theta) {
   return GF_OK;
 }
 
-static int upload_theta(gf_ctx* ctx, const double* theta) {
-  int rc = fill_theta_host(ctx, theta);
-  if (rc) return rc;
+// Queue the upload of theta on the context's stream.
+static int enqueue_uploads(gf_ctx* ctx) {
   DevState& d = ctx->dev;
   const int np = (int)ctx->pars.size();
   if (np > 0)
     CK(cudaMemcpyAsync(d.theta, d.h_theta, sizeof(double) * np, cudaMemcpyHostToDevice,
                        ctx->stream));
   return GF_OK;
+}
+
+static int upload_theta(gf_ctx* ctx, const double* theta) {
+  int rc = fill_theta_host(ctx, theta);
+  if (rc) return rc;
+  return enqueue_uploads(ctx);
 }
 
 // Dalitz: true when no cache needs (re)building for this evaluation (mask, per-event and
@@ -1185,10 +1190,10 @@ static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool capt
   const unsigned evf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   const bool with_upload = capturing;
   const int nf = (int)ctx->free_ids.size();
-  const int np = (int)ctx->pars.size();
-  if (with_upload && np > 0)
-    CK(cudaMemcpyAsync(d.theta, d.h_theta, sizeof(double) * np, cudaMemcpyHostToDevice,
-                       ctx->stream));
+  if (with_upload) {
+    const int rc = enqueue_uploads(ctx);
+    if (rc) return rc;
+  }
   CK(cudaEventRecordWithFlags(d.ev0, ctx->stream, evf));
   if (ctx->is_dalitz) {
     const bool mixed = ctx->precision == GF_MIXED && !fp64;
@@ -1288,10 +1293,8 @@ int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64) {
   }
   ctx->last_graph = false;
   // cache maintenance first (Dalitz), then the evaluation
-  const int np = (int)ctx->pars.size();
-  if (np > 0)
-    CK(cudaMemcpyAsync(d.theta, d.h_theta, sizeof(double) * np, cudaMemcpyHostToDevice,
-                       ctx->stream));
+  rc = enqueue_uploads(ctx);
+  if (rc) return rc;
   int launches = 0, mode = DN_GRAM;
   if (ctx->is_dalitz) {
     rc = dalitz_prepare(ctx, &mode, &launches, mixed);

@@ -28,6 +28,7 @@ struct Acc<DF> {
   DF s = DF(0.f);
   __device__ __forceinline__ void add(DF v) { s += v; }
   __device__ __forceinline__ double get() const { return s.to_double(); }
+  __device__ __forceinline__ F2 pair() const { return s; }
 };
 template <>
 struct Acc<float> {
@@ -39,6 +40,7 @@ struct Acc<float> {
     s = t;
   }
   __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+  __device__ __forceinline__ F2 pair() const { return two_sum(s, -c); }
 };
 
 // ---- warp / block reductions in a fixed order (bitwise reproducible) -------------------
@@ -85,6 +87,32 @@ __device__ inline void reduce_partials(const double* partials, int nblk, int str
     double r = block_sum(v, red);
     if (threadIdx.x == 0) out[k] = r;
     __syncthreads();
+  }
+}
+
+// Sum m per-thread values (pairs, from val(k)) over the block in a fixed order and write
+// the block's sums to out[0 .. m-1] (global memory): each warp folds its 32 lanes with
+// pair shuffles (lane order fixed), lane 0 stores the warp's m sums as doubles in
+// red[warp * m + k], one barrier, then thread k adds the warps' k-th sums in FP64.
+// red: (blockDim / 32) * m doubles.  Replaces m separate FP64 block sums (2 barriers and
+// 5 FP64 shuffle-adds per value and thread).
+template <class Val>
+__device__ __forceinline__ void block_sum_pairs(Val val, int m, double* red, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = 0; k < m; ++k) {
+    F2 v = val(k);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const F2 u = {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+      v = df_add(v, u);
+    }
+    if (lane == 0) red[warp * m + k] = df_to(v);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    double r = 0.0;
+    for (int w = 0; w < nw; ++w) r += red[w * m + k];
+    out[k] = r;
   }
 }
 

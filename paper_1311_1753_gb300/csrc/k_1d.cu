@@ -17,42 +17,61 @@
 
 namespace gfi {
 
-// ---- shape functions (unnormalised r(x) and d r / d local parameter) ------------------
+// ---- shape functions of the normalisation grid (unnormalised r(x), d r / d local par) ----
+// Per-block constants of the leaf's shape, from theta once per block (FP64, then pairs);
+// each bin is then evaluated in pairs on the FP32 pipe.
+struct ShapeK {
+  double x0;        // mu (Voigtian) or x0 (threshold)
+  F2 a, b, c, d, e;
+};
+
 // Voigtian: r = Re w(z)/(sigma sqrt(2 pi)), z = (x - mu)/(sigma sqrt 2) + i Gamma/(2 sigma sqrt 2).
-__device__ __forceinline__ double voigt_r(double x, double mu, double s, double G,
-                                          const WeidCoef& W, double* dr) {
+// a = 1/(sigma sqrt2), b = Im z, c = 1/(sigma sqrt(2 pi)), d = 1/sigma, e = a/2.
+__device__ __forceinline__ void voigt_consts(double mu, double s, double G, ShapeK& K) {
   const double c1 = 1.0 / (s * kSqrt2);
-  const double zr = (x - mu) * c1, zi = 0.5 * G * c1;
-  double wr, wi;
-  faddeeva_df(zr, zi, W, wr, wi);
-  const double pref = 1.0 / (s * kSqrt2Pi);
-  const double r = wr * pref;
-  if (dr) {
-    // w' = -2 z w + 2i/sqrt(pi)
-    const double dre = -2.0 * (zr * wr - zi * wi);
-    const double dim = -2.0 * (zr * wi + zi * wr) + kTwoInvSqrtPi;
-    dr[0] = -pref * c1 * dre;                               // d/dmu
-    dr[1] = -pref / s * (dre * zr - dim * zi) - r / s;      // d/dsigma
-    dr[2] = -pref * 0.5 * c1 * dim;                         // d/dGamma
-  }
-  return r;
+  K.x0 = mu;
+  K.a = df_from(c1);
+  K.b = df_from(0.5 * G * c1);
+  K.c = df_from(1.0 / (s * kSqrt2Pi));
+  K.d = df_from(1.0 / s);
+  K.e = df_from(0.5 * c1);
+}
+__device__ __forceinline__ double voigt_r(double x, const ShapeK& K, const WeidCoef& W,
+                                          double* dr) {
+  const F2 zr = df_mul(df_split(x - K.x0), K.a);
+  F2 wr, wi;
+  faddeeva_f2(zr, K.b, W, wr, wi);
+  const F2 r = df_mul(wr, K.c);
+  // w' = -2 z w + 2i/sqrt(pi)
+  const F2 dre = df_mul_f(df_sub(df_mul(zr, wr), df_mul(K.b, wi)), -2.f);
+  const F2 dim = df_add(df_mul_f(df_add(df_mul(zr, wi), df_mul(K.b, wr)), -2.f),
+                        F2(DFC(kTwoInvSqrtPi)));
+  dr[0] = -df_to(df_mul(df_mul(K.c, K.a), dre));                                 // d/dmu
+  dr[1] = -df_to(df_add(df_mul(df_mul(K.c, K.d), df_sub(df_mul(dre, zr), df_mul(dim, K.b))),
+                        df_mul(r, K.d)));                                           // d/dsigma
+  dr[2] = -df_to(df_mul(df_mul(K.c, K.e), dim));                                 // d/dGamma
+  return df_to(r);
 }
 
-// Threshold: r = (x - x0)^p e^{-c (x - x0)} for x > x0.
-__device__ __forceinline__ double thresh_r(double x, double x0, double p, double c, double* dr) {
-  const double t = x - x0;
+// Threshold: r = (x - x0)^p e^{-c (x - x0)} for x > x0.  a = p, b = c.
+__device__ __forceinline__ void thresh_consts(double x0, double p, double c, ShapeK& K) {
+  K.x0 = x0;
+  K.a = df_from(p);
+  K.b = df_from(c);
+}
+__device__ __forceinline__ double thresh_r(double x, const ShapeK& K, double* dr) {
+  const double t = x - K.x0;
   if (!(t > 0.0)) {
-    if (dr) dr[0] = dr[1] = dr[2] = 0.0;
+    dr[0] = dr[1] = dr[2] = 0.0;
     return 0.0;
   }
-  const double lt = log(t);
-  const double r = exp(fma(p, lt, -c * t));
-  if (dr) {
-    dr[0] = r * (c - p / t);
-    dr[1] = r * lt;
-    dr[2] = -t * r;
-  }
-  return r;
+  const F2 T = df_split(t);
+  const F2 lt = df_log_tab(T, s_log_tab);
+  const F2 r = df_exp_tab(df_sub(df_mul(K.a, lt), df_mul(K.b, T)), s_exp_tab);
+  dr[0] = df_to(df_mul(r, df_sub(K.b, df_mul(K.a, df_rcp(T)))));
+  dr[1] = df_to(df_mul(r, lt));
+  dr[2] = -df_to(df_mul(T, r));
+  return df_to(r);
 }
 
 // ---- leaf records ------------------------------------------------------------------------
@@ -178,7 +197,8 @@ __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& 
                                               double* __restrict__ partials,
                                               unsigned* __restrict__ counter,
                                               double* __restrict__ derived, int vb, int vgrid,
-                                              double* red, int* last, double (*sums)[4]) {
+                                              double* red, int* last, double (*sums)[4],
+                                              ShapeK* shk) {
   // locate this block's leaf
   int li = -1;
   for (int l = 0; l < P.nleaf; ++l) {
@@ -186,6 +206,12 @@ __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& 
     if (L.nbins > 0 && vb >= L.grid_first_block && vb < L.grid_first_block + L.grid_nblocks)
       li = l;
   }
+  if (li >= 0 && threadIdx.x == 0) {
+    const LeafDesc& L = P.leaf[li];
+    if (L.kind == L_VOIGT) voigt_consts(theta[L.par[0]], theta[L.par[1]], theta[L.par[2]], *shk);
+    else thresh_consts(theta[L.par[0]], theta[L.par[1]], theta[L.par[2]], *shk);
+  }
+  __syncthreads();
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   if (li >= 0) {
     const LeafDesc& L = P.leaf[li];
@@ -194,10 +220,8 @@ __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& 
       const double h = (L.hi - L.lo) / L.nbins;
       const double x = L.lo + (b + 0.5) * h;
       double dr[3];
-      if (L.kind == L_VOIGT)
-        v[0] = voigt_r(x, theta[L.par[0]], theta[L.par[1]], theta[L.par[2]], W, dr);
-      else
-        v[0] = thresh_r(x, theta[L.par[0]], theta[L.par[1]], theta[L.par[2]], dr);
+      if (L.kind == L_VOIGT) v[0] = voigt_r(x, *shk, W, dr);
+      else v[0] = thresh_r(x, *shk, dr);
       v[1] = dr[0];
       v[2] = dr[1];
       v[3] = dr[2];
@@ -250,8 +274,11 @@ __global__ void __launch_bounds__(kThreads) k_norm_1d(const Program* __restrict_
   __shared__ double red[32];
   __shared__ int last;
   __shared__ double sums[kMaxLeaf][4];
+  __shared__ ShapeK shk;
+  load_df_tables();
   load_program(Pg, P);
-  norm_1d_block(P, W, theta, partials, counter, derived, blockIdx.x, gridDim.x, red, &last, sums);
+  norm_1d_block(P, W, theta, partials, counter, derived, blockIdx.x, gridDim.x, red, &last, sums,
+                &shk);
 }
 
 // ---- event-side arithmetic ----------------------------------------------------------------
@@ -543,7 +570,7 @@ __device__ __noinline__ double run_program_fp64(const Program& P, const double* 
 // MODE 0: reduce -log P (and gradient) to result[0 .. nfree]; MODE 1: store log P_i.
 // Body of one (virtual) block vb of the vgrid blocks of an event launch.  Shared
 // scratch: dyn (G: (kMaxStack + 1) nfree blockDim pairs/doubles), rec (leaf records in
-// FP64), rf (the same as pairs), red[32], *last.
+// FP64), rf (the same as pairs), red[(blockDim / 32) (1 + kMaxFree1D)], *last.
 template <bool G, int MODE>
 __device__ __forceinline__ void events_1d_block(
     const Program& P, const WeidCoef& W, const Cols& cols, const int64_t n,
@@ -669,11 +696,8 @@ __device__ __forceinline__ void events_1d_block(
 
   const int m = 1 + (G ? nf : 0);
   const int stride_p = 1 + kMaxFree1D;
-  for (int k = 0; k < m; ++k) {
-    const double v = (k == 0) ? df_to(acc) : df_to(gacc[(k - 1) * bd]);
-    const double r = block_sum(v, red);
-    if (tid == 0) partials[(size_t)vb * stride_p + k] = r;
-  }
+  block_sum_pairs([&](int k) -> F2 { return k == 0 ? acc : gacc[(k - 1) * bd]; }, m, red,
+                  partials + (size_t)vb * stride_p);
   if (!arrive_last_of(counter, (unsigned)vgrid, last)) return;
   reduce_partials(partials, vgrid, stride_p, m, result, red);
   if (tid == 0) *counter = 0u;
@@ -689,7 +713,7 @@ __global__ void __launch_bounds__(kThreads1D) k_events_1d(
   __shared__ Program P;
   __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
   __shared__ F2 rf[kMaxLeaf * kLeafRec + kMaxCoef];
-  __shared__ double red[32];
+  __shared__ double red[(kThreads1D / 32) * (1 + kMaxFree1D)];  // >= 32
   __shared__ int last;
   __shared__ F2 tay_t[(kTayDeg + 1) * 2 * kThreads1D];
   load_df_tables();
@@ -726,12 +750,14 @@ __global__ void __launch_bounds__(kThreads) k_tick_norm_1d(const TickItem* __res
   __shared__ double red[32];
   __shared__ int last;
   __shared__ double sums[kMaxLeaf][4];
+  __shared__ ShapeK shk;
+  load_df_tables();  // visible after tick_item's first barrier
   int cur = -1;
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const TickItem& ti = tick_item(items, nfits, it, cur, Ps);
     const Fit1D* F = static_cast<const Fit1D*>(ti.fit);
     norm_1d_block(Ps, W, ti.theta, F->partials_norm, F->counter_norm, F->derived,
-                  it - ti.item0, ti.nitems, red, &last, sums);
+                  it - ti.item0, ti.nitems, red, &last, sums, &shk);
     __syncthreads();
   }
 }
@@ -744,7 +770,7 @@ __global__ void __launch_bounds__(kThreads1D) k_tick_events_1d(const TickItem* _
   __shared__ Program Ps;
   __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
   __shared__ F2 rf[kMaxLeaf * kLeafRec + kMaxCoef];
-  __shared__ double red[32];
+  __shared__ double red[(kThreads1D / 32) * (1 + kMaxFree1D)];  // >= 32
   __shared__ int last;
   load_df_tables();  // visible after tick_item's first barrier
   int cur = -1;

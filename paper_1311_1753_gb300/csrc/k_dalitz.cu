@@ -542,7 +542,7 @@ struct DzShared {
   ResK rk[kMaxRes];
   ResKf rkf[kMaxRes];
   DzC<T> C;
-  double red[32];
+  double red[(kThreads / 32) * (1 + 4 * kMaxRes)];  // >= 32: also reduce_partials' scratch
   double tot[1 + 4 * kMaxRes];
   double logN;
   int last;
@@ -747,11 +747,8 @@ __device__ __forceinline__ void dalitz_stream_block(
 
   const int m = 1 + (G ? nf : 0);
   const int stride_p = 1 + 2 * kMaxRes * 2;
-  for (int k = 0; k < m; ++k) {
-    const double v = (k == 0) ? acc.get() : gacc[(k - 1) * bd].get();
-    const double r = block_sum(v, red);
-    if (tid == 0) partials[(size_t)vb * stride_p + k] = r;
-  }
+  block_sum_pairs([&](int k) { return k == 0 ? acc.pair() : gacc[(k - 1) * bd].pair(); }, m, red,
+                  partials + (size_t)vb * stride_p);
   if (!arrive_last_of(counter, (unsigned)vgrid, &sh.last)) return;
   double* tot = sh.tot;
   reduce_partials(partials, vgrid, stride_p, m, tot, red);
