@@ -77,18 +77,6 @@ struct Neu {
 
 // Block-wide fixed-order sum of partials[b * stride + k] over b < nblk, for each
 // k < m; writes out[k].  Called by every thread of one block.
-__device__ inline void reduce_partials(const double* partials, int nblk, int stride, int m,
-                                       double* out, double* red) {
-  for (int k = 0; k < m; ++k) {
-    Neu a;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) a.add(__ldcg(partials + (size_t)b * stride + k));
-    // fixed tree over threads: compensated values folded in by warp then by warp index
-    double v = a.get();
-    double r = block_sum(v, red);
-    if (threadIdx.x == 0) out[k] = r;
-    __syncthreads();
-  }
-}
 
 // Sum m per-thread values (pairs, from val(k)) over the block in a fixed order and write
 // the block's sums to out[0 .. m-1] (global memory): each warp folds its 32 lanes with
@@ -114,6 +102,22 @@ __device__ __forceinline__ void block_sum_pairs(Val val, int m, double* red, dou
     for (int w = 0; w < nw; ++w) r += red[w * m + k];
     out[k] = r;
   }
+}
+
+// Cross-block sum by the last block: out[k] = sum over b < nblk of partials[b stride + k],
+// k < m, in a fixed order.  Each thread accumulates its strided share as pairs (partials
+// enter by the bit split: no FP64 conversions), then block_sum_pairs.  red: as there.
+__device__ inline void reduce_partials(const double* partials, int nblk, int stride, int m,
+                                       double* out, double* red) {
+  block_sum_pairs(
+      [&](int k) {
+        F2 a = {0.f, 0.f};
+        for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+          a = df_add(a, df_split(__ldcg(partials + (size_t)b * stride + k)));
+        return a;
+      },
+      m, red, out);
+  __syncthreads();
 }
 
 // Last-block pattern: every block publishes its partial, then bumps a counter; the

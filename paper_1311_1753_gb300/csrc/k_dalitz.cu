@@ -545,9 +545,33 @@ struct DzShared {
   double red[(kThreads / 32) * (1 + 4 * kMaxRes)];  // >= 32: also reduce_partials' scratch
   double tot[1 + 4 * kMaxRes];
   double logN;
+  double gv[2 * (kMaxRes + 1)];  // v_k = sum_s G_ks c_s (Gram normalisation), re/im
   int last;
   int need_ch[3];  // a channel's kinematics are needed by some resonance not cached
 };
+
+// c_k of the Gram form: c_0 = a_NR = 1, c_{r+1} = the resonance coefficients.
+__device__ __forceinline__ void gram_coef(const ResK* rk, int k, double& cr, double& ci) {
+  cr = k == 0 ? 1.0 : rk[k - 1].cr;
+  ci = k == 0 ? 0.0 : rk[k - 1].ci;
+}
+// Threads k < K form v_k = sum_s G_ks c_s into gv (K = nres + 1); a barrier must follow.
+__device__ __forceinline__ void gram_apply(const double* __restrict__ gram, const ResK* rk, int K,
+                                           double* gv) {
+  const int k = threadIdx.x;
+  if (k < K) {
+    double vr = 0.0, vi = 0.0;
+    for (int s = 0; s < K; ++s) {
+      double cr, ci;
+      gram_coef(rk, s, cr, ci);
+      const double gr = gram[2 * (k * K + s)], gi = gram[2 * (k * K + s) + 1];
+      vr += gr * cr - gi * ci;
+      vi += gr * ci + gi * cr;
+    }
+    gv[2 * k] = vr;
+    gv[2 * k + 1] = vi;
+  }
+}
 
 // Body of one (virtual) block vb of the vgrid blocks of a stream launch.  T = float (FP32
 // plans: amplitudes in float with the hi/lo constants of ResKf) or DF (FP64 plans: every
@@ -586,21 +610,17 @@ __device__ __forceinline__ void dalitz_stream_block(
     for (int k = 0; k < nf; ++k) gacc[k * bd] = Acc<T>();
   __syncthreads();
   fill_dzc<T>(D, rk, sh.C);
+  if (METRIC == METRIC_STORE && norm_mode == DN_GRAM) gram_apply(gram, rk, nres + 1, sh.gv);
+  __syncthreads();
   if (METRIC == METRIC_STORE && tid == 0) {
     // normalised log P: log |A|^2 - log N, N = c^H G c (Gram mode) or the direct pass
-    double N;
+    double N = 0.0;
     if (norm_mode == DN_GRAM) {
-      const int K = nres + 1;
-      double cr[kMaxRes + 1], ci[kMaxRes + 1];
-      cr[0] = 1.0;
-      ci[0] = 0.0;
-      for (int r = 0; r < nres; ++r) { cr[r + 1] = rk[r].cr; ci[r + 1] = rk[r].ci; }
-      N = 0.0;
-      for (int k = 0; k < K; ++k)
-        for (int s = 0; s < K; ++s) {
-          const double gr = gram[2 * (k * K + s)], gi = gram[2 * (k * K + s) + 1];
-          N += cr[k] * (gr * cr[s] - gi * ci[s]) + ci[k] * (gr * ci[s] + gi * cr[s]);
-        }
+      for (int k = 0; k <= nres; ++k) {
+        double cr, ci;
+        gram_coef(rk, k, cr, ci);
+        N += cr * sh.gv[2 * k] + ci * sh.gv[2 * k + 1];
+      }
     } else {
       N = norm_in[0];
     }
@@ -756,7 +776,11 @@ __device__ __forceinline__ void dalitz_stream_block(
   if (METRIC == METRIC_NORM) {
     const double dA = D.hx * D.hy;
     if (tid < m) result[tid] = tot[tid] * dA;
-  } else if (tid == 0) {
+  } else {
+    if (norm_mode == DN_GRAM) gram_apply(gram, rk, nres + 1, sh.gv);
+    __syncthreads();
+  }
+  if (METRIC != METRIC_NORM && tid == 0) {
     // combine with the normalisation: + n log N, + n dN/N
     double N;
     double dN[4 * kMaxRes];
@@ -764,20 +788,12 @@ __device__ __forceinline__ void dalitz_stream_block(
     if (norm_mode == DN_GRAM) {
       // N = c^H G c, c_0 = a_NR = 1;  v_k = sum_s G_ks c_s;  dN/dRe c_k = 2 Re v_k,
       // dN/dIm c_k = 2 Im v_k
-      const int K = nres + 1;
-      double cr[kMaxRes + 1], ci[kMaxRes + 1];
-      cr[0] = 1.0;
-      ci[0] = 0.0;
-      for (int r = 0; r < nres; ++r) { cr[r + 1] = rk[r].cr; ci[r + 1] = rk[r].ci; }
       N = 0.0;
-      for (int k = 0; k < K; ++k) {
-        double vr = 0.0, vi = 0.0;
-        for (int s = 0; s < K; ++s) {
-          const double gr = gram[2 * (k * K + s)], gi = gram[2 * (k * K + s) + 1];
-          vr += gr * cr[s] - gi * ci[s];
-          vi += gr * ci[s] + gi * cr[s];
-        }
-        N += cr[k] * vr + ci[k] * vi;  // Re(conj(c_k) v_k)
+      for (int k = 0; k <= nres; ++k) {
+        double cr, ci;
+        gram_coef(rk, k, cr, ci);
+        const double vr = sh.gv[2 * k], vi = sh.gv[2 * k + 1];
+        N += cr * vr + ci * vi;  // Re(conj(c_k) v_k)
         if (k > 0 && G) {
           const DalitzRes& R = D.res[k - 1];
           if (R.g_re >= 0) dN[R.g_re] += 2.0 * vr;
