@@ -253,6 +253,12 @@ int gf_last_eval_graph(gf_ctx* ctx, int* replayed, char* why_not, size_t n);
  * gf_update_data; it costs one radix sort and 4 bytes per event for the permutation.
  * Takes effect at the next gf_set_data.  The fit server turns it off for its requests. */
 int gf_set_event_sort(gf_ctx* ctx, int enable);
+/* Evaluate a 1D tree that is an AddPdf of leaves (up to 4 components, each leaf with at
+ * most 3 parameters) directly as P = sum_k c_k L_k with its gradient (enable != 0, the
+ * default), or on the general postfix stack machine (0).  Both compute the same
+ * quantities (Sec. 3's AddPdf); the direct form avoids the stack's per-operation
+ * gradient vectors.  Takes effect at the next evaluation. */
+int gf_set_mixture_path(gf_ctx* ctx, int enable);
 /* Turn the replay of captured evaluation graphs on (enable != 0, the default) or off (every
  * evaluation launches its kernels one by one; the results are the same bits). */
 int gf_set_graphs(gf_ctx* ctx, int enable);

@@ -590,6 +590,40 @@ struct Compiler {
   }
 };
 
+// An AddPdf whose children are leaves compiles to K x [LEAF, (TOLIN), SCALE, (ADD)]; the
+// event kernel then evaluates P = sum_k c_k L_k directly (each leaf with at most
+// kMixLocal parameters, K <= kMixMax), otherwise the program runs on the stack machine.
+static void detect_mixture(Program& P) {
+  P.mix = 0;
+  if (P.root_log) return;
+  int pc = 0, K = 0;
+  int lf[kMixMax], lg[kMixMax], sc[kMixMax];
+  while (pc < P.n) {
+    if (K >= kMixMax) return;
+    if (P.ins[pc].op != OP_LEAF || P.ins[pc].npar > kMixLocal) return;
+    lf[K] = pc++;
+    lg[K] = 0;
+    if (pc < P.n && P.ins[pc].op == OP_TOLIN) {
+      lg[K] = 1;
+      ++pc;
+    }
+    if (pc >= P.n || P.ins[pc].op != OP_SCALE) return;
+    sc[K] = pc++;
+    if (K > 0) {
+      if (pc >= P.n || P.ins[pc].op != OP_ADD) return;
+      ++pc;
+    }
+    ++K;
+  }
+  if (K < 2) return;
+  P.mix = K;
+  for (int k = 0; k < K; ++k) {
+    P.mix_leaf[k] = lf[k];
+    P.mix_log[k] = lg[k];
+    P.mix_scale[k] = sc[k];
+  }
+}
+
 bool has_cycle(gf_ctx* ctx, int id, std::vector<int>& state) {
   if (state[id] == 1) return true;
   if (state[id] == 2) return false;
@@ -691,6 +725,8 @@ int ensure_compiled(gf_ctx* ctx) {
         break;
       }
     P.sorted = (d.sorted && P.tay_slot >= 0 && d.sort_obs == P.tay_obs) ? 1 : 0;
+    if (ctx->mixture_path) detect_mixture(P);
+    else P.mix = 0;
     // the kernels read the program from device memory (it is too large for parameters);
     // stream-ordered copy, then wait: the next launch may go to another stream
     DevState& dv = ctx->dev;
@@ -1582,6 +1618,15 @@ int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
       hi[k] = ctx->obs[d.obs_ids[k]].hi;
     }
     CK(launch_check_range(c, d.nobs, n, lo, hi, d.flag, ctx->stream));
+  }
+  return GF_OK;
+}
+
+int gf_set_mixture_path(gf_ctx* ctx, int enable) {
+  if (!ctx) return GF_EINVAL;
+  if (ctx->mixture_path != (enable != 0)) {
+    ctx->mixture_path = enable != 0;
+    ctx->compiled = false;  // recompiled (and graphs re-captured) at the next call
   }
   return GF_OK;
 }

@@ -117,6 +117,7 @@ struct gf_ctx {
   bool last_graph = false;  // the last evaluation replayed a captured graph
   bool graphs = true;       // replay captured graphs of steady evaluations
   bool event_sort = true;   // keep owned 1D columns sorted for the chunked event loop
+  bool mixture_path = true; // evaluate AddPdf-of-leaves programs without the stack machine
 };
 
 namespace gfi {

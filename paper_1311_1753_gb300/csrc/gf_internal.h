@@ -21,6 +21,8 @@ constexpr int kWeidN = 40;      // terms of the Faddeeva series
 constexpr int kThreads = 256;   // threads per block of the Dalitz and normalisation kernels
 constexpr int kThreads1D = 128; // threads per block of the 1D event kernel (its gradient
                                 // stack: 5 x nfree x 128 doubles of shared memory <= 123 KB)
+constexpr int kMixMax = 4;      // components of an AddPdf evaluated without the stack machine
+constexpr int kMixLocal = 3;    // ... each leaf with at most 3 local parameters
 constexpr int kChunk = 24;      // sorted 1D data: events per expansion of w (k_1d.cu); the
                                 // chunked loop runs when there are >= kChunk/2 events per thread
 
@@ -66,6 +68,11 @@ struct Program {
   int32_t tay_slot;  // leaf record of the first Voigtian leaf (expanded per chunk), -1: none
   int32_t tay_obs;   // its observable column
   int32_t sorted;    // events sorted ascending by column tay_obs (chunked event loop)
+  // AddPdf of leaves (the program is K x [LEAF, (TOLIN), SCALE, (ADD)]): evaluated as
+  // P = sum_k c_k L_k without the stack machine.  mix = K (2..kMixMax), 0: not a mixture.
+  int32_t mix;
+  int32_t mix_leaf[4], mix_log[4], mix_scale[4];  // instruction indices; TOLIN present
+  int32_t pad0;
   Instr ins[kMaxIns];
   LeafDesc leaf[kMaxLeaf];
   CoefDesc coef[kMaxCoef];

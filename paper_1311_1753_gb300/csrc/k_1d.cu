@@ -8,6 +8,7 @@
 //               postfix program evaluated per event (forward-mode gradient optional),
 //               -log P summed per thread, per block (warp shuffles), and across blocks
 //               by the last block in a fixed order.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <type_traits>
@@ -398,26 +399,26 @@ __device__ __forceinline__ void tay_eval(const Tay& tay, F2 zr, F2& wr, F2& wi) 
 // partials with respect to the leaf's free parameters into the gradient slot g (stride bd).
 // rec: the leaf record in FP64 (its constant c0 = rec[10] enters the exact difference
 // x - c0); r: the same record in the arithmetic A.
-template <class A, bool G>
-__device__ __forceinline__ typename A::T eval_leaf(const Instr& I, const double* rec,
-                                                   const typename A::T* r, double x,
-                                                   const WeidCoef& W, typename A::T* g,
-                                                   int bd, const Tay* tay) {
+template <class A, bool G, class Sink>
+__device__ __forceinline__ typename A::T eval_leaf_s(const Instr& I, const double* rec,
+                                                     const typename A::T* r, double x,
+                                                     const WeidCoef& W, Sink sink,
+                                                     const Tay* tay) {
   using T = typename A::T;
   const T* c = r + 10;
   switch (I.kind) {
     case L_EXP: {
       const T X = A::of(x);
-      if (G && I.gidx[0] >= 0) g[I.gidx[0] * bd] = A::add(g[I.gidx[0] * bd], A::sub(X, r[2]));
+      if (G && I.gidx[0] >= 0) sink(0, A::sub(X, r[2]));
       return A::add(A::mul(c[0], X), c[1]);
     }
     case L_GAUSS: {
       const T u = A::mul(A::diff(x, rec[10]), c[1]);
       if (G) {
         const T uc = A::mul(u, c[1]);
-        if (I.gidx[0] >= 0) g[I.gidx[0] * bd] = A::add(g[I.gidx[0] * bd], A::sub(uc, r[2]));
+        if (I.gidx[0] >= 0) sink(0, A::sub(uc, r[2]));
         if (I.gidx[1] >= 0)
-          g[I.gidx[1] * bd] = A::add(g[I.gidx[1] * bd], A::sub(A::mul(u, uc), r[3]));
+          sink(1, A::sub(A::mul(u, uc), r[3]));
       }
       return A::add(A::mulf(A::mul(u, u), -0.5f), c[2]);
     }
@@ -437,16 +438,13 @@ __device__ __forceinline__ typename A::T eval_leaf(const Instr& I, const double*
         const T dim = A::add(A::mulf(A::add(A::mul(zr, wi), A::mul(c[2], wr)), -2.f),
                              A::two_inv_sqrt_pi());
         if (I.gidx[0] >= 0)
-          g[I.gidx[0] * bd] =
-              A::sub(g[I.gidx[0] * bd], A::add(A::mul(c[5], dre), A::mul(l, r[2])));
+          sink(0, A::neg(A::add(A::mul(c[5], dre), A::mul(l, r[2]))));
         if (I.gidx[1] >= 0) {
           const T q = A::sub(A::mul(dre, zr), A::mul(dim, c[2]));
-          g[I.gidx[1] * bd] =
-              A::sub(g[I.gidx[1] * bd], A::add(A::mul(c[6], q), A::mul(l, c[8])));
+          sink(1, A::neg(A::add(A::mul(c[6], q), A::mul(l, c[8]))));
         }
         if (I.gidx[2] >= 0)
-          g[I.gidx[2] * bd] =
-              A::sub(g[I.gidx[2] * bd], A::add(A::mul(c[7], dim), A::mul(l, r[4])));
+          sink(2, A::neg(A::add(A::mul(c[7], dim), A::mul(l, r[4]))));
       }
       return l;
     }
@@ -462,12 +460,11 @@ __device__ __forceinline__ typename A::T eval_leaf(const Instr& I, const double*
       }
       if (G) {
         if (I.gidx[0] >= 0)
-          g[I.gidx[0] * bd] = A::add(
-              g[I.gidx[0] * bd], A::mul(l, A::sub(A::sub(c[2], A::mul(c[1], A::rcp(t))), r[2])));
+          sink(0, A::mul(l, A::sub(A::sub(c[2], A::mul(c[1], A::rcp(t))), r[2])));
         if (I.gidx[1] >= 0)
-          g[I.gidx[1] * bd] = A::add(g[I.gidx[1] * bd], A::mul(l, A::sub(lt, r[3])));
+          sink(1, A::mul(l, A::sub(lt, r[3])));
         if (I.gidx[2] >= 0)
-          g[I.gidx[2] * bd] = A::sub(g[I.gidx[2] * bd], A::mul(l, A::add(t, r[4])));
+          sink(2, A::neg(A::mul(l, A::add(t, r[4]))));
       }
       return l;
     }
@@ -479,7 +476,7 @@ __device__ __forceinline__ typename A::T eval_leaf(const Instr& I, const double*
         T xk = r[0];
         for (int k = 0; k < I.npar; ++k) {
           if (I.gidx[k] >= 0)
-            g[I.gidx[k] * bd] = A::add(g[I.gidx[k] * bd], A::sub(xk, A::mul(l, r[2 + k])));
+            sink(k, A::sub(xk, A::mul(l, r[2 + k])));
           xk = A::mul(xk, X);
         }
       }
@@ -487,6 +484,17 @@ __device__ __forceinline__ typename A::T eval_leaf(const Instr& I, const double*
     }
   }
   return A::zero();
+}
+
+template <class A, bool G>
+__device__ __forceinline__ typename A::T eval_leaf(const Instr& I, const double* rec,
+                                                   const typename A::T* r, double x,
+                                                   const WeidCoef& W, typename A::T* g,
+                                                   int bd, const Tay* tay) {
+  using T = typename A::T;
+  return eval_leaf_s<A, G>(I, rec, r, x, W,
+                           [&](int j, T term) { g[I.gidx[j] * bd] = A::add(g[I.gidx[j] * bd], term); },
+                           tay);
 }
 
 // The compiled postfix program for one event: returns the root's value (log domain if
@@ -566,6 +574,70 @@ __device__ __noinline__ double run_program_fp64(const Program& P, const double* 
   return run_program<ArD, G>(P, rec, rec, x, W, dyn, nf, bd, tid);
 }
 
+// AddPdf of leaves (P.mix = K components) for one event: P = sum_k c_k L_k, each leaf by
+// the same code as the interpreter's.  With G, the thread's slots comp[(4k + e) bd] get
+// L_k (e = 0) and dL_k/d(local parameter e - 1) (e = 1..3, linear domain); the caller adds
+// c_k dL_k/P and +-L_k/P into the gradient sums once P is known.
+template <bool G>
+__device__ __forceinline__ F2 run_mixture(const Program& P, const double* rec, const F2* rf,
+                                          const double* x, const WeidCoef& W, F2* comp, int bd,
+                                          const Tay* tay) {
+  const F2* coef = rf + kMaxLeaf * kLeafRec;
+  F2 s = {0.f, 0.f};
+  for (int k = 0; k < P.mix; ++k) {
+    const Instr& I = P.ins[P.mix_leaf[k]];
+    F2 d0 = {0.f, 0.f}, d1 = {0.f, 0.f}, d2 = {0.f, 0.f};
+    F2 v = eval_leaf_s<ArF2, G>(
+        I, rec + I.slot * kLeafRec, rf + I.slot * kLeafRec, x[I.obs], W,
+        [&](int j, F2 t) {
+          if (j == 0) d0 = t;
+          else if (j == 1) d1 = t;
+          else d2 = t;
+        },
+        tay);
+    if (P.mix_log[k]) {  // log-domain leaf: L = e^v, dL = L dv
+      v = df_exp_tab(v, s_exp_tab);
+      if (G) {
+        d0 = df_mul(d0, v);
+        d1 = df_mul(d1, v);
+        d2 = df_mul(d2, v);
+      }
+    }
+    if (G) {
+      comp[(4 * k) * bd] = v;
+      comp[(4 * k + 1) * bd] = d0;
+      comp[(4 * k + 2) * bd] = d1;
+      comp[(4 * k + 3) * bd] = d2;
+    }
+    const F2 t = df_mul(v, coef[P.ins[P.mix_scale[k]].slot]);
+    s = k == 0 ? t : df_add(s, t);
+  }
+  return s;
+}
+
+// Gradient sums of one mixture event: sc = -1/P.
+__device__ __forceinline__ void mixture_grad(const Program& P, const F2* rf, const F2* comp,
+                                             F2 sc, F2* gacc, int bd) {
+  const F2* coef = rf + kMaxLeaf * kLeafRec;
+  for (int k = 0; k < P.mix; ++k) {
+    const Instr& I = P.ins[P.mix_leaf[k]];
+    const Instr& S = P.ins[P.mix_scale[k]];
+    const F2 cs = df_mul(coef[S.slot], sc);
+#pragma unroll
+    for (int j = 0; j < kMixLocal; ++j)
+      if (j < I.npar && I.gidx[j] >= 0) {
+        F2& g = gacc[I.gidx[j] * bd];
+        g = df_add(g, df_mul(comp[(4 * k + 1 + j) * bd], cs));
+      }
+    const F2 vs = df_mul(comp[(4 * k) * bd], sc);
+    for (int q = 0; q < S.npar; ++q)
+      if (S.gidx[q] >= 0) {
+        F2& g = gacc[S.gidx[q] * bd];
+        g = df_add(g, S.kind > 0 ? vs : df_neg(vs));
+      }
+  }
+}
+
 // ---- event stream ------------------------------------------------------------------------
 // MODE 0: reduce -log P (and gradient) to result[0 .. nfree]; MODE 1: store log P_i.
 // Body of one (virtual) block vb of the vgrid blocks of an event launch.  Shared
@@ -593,14 +665,19 @@ __device__ __forceinline__ void events_1d_block(
   for (int k = tid; k < kRec; k += bd) rf[k] = df_from(rec[k]);
   __syncthreads();
   F2* dynf = reinterpret_cast<F2*>(dyn);
-  F2* gacc = dynf + (size_t)kMaxStack * nf * bd + tid;  // per-thread gradient sums
+  // per-thread gradient sums: after the interpreter's stack (kMaxStack levels of nf), or
+  // for a mixture after its 4 x kMixMax component slots and the FP64 fallback's stack
+  const int gbase = P.mix > 0 ? max(4 * kMixMax, kMaxStack * nf) : kMaxStack * nf;
+  F2* gacc = dynf + (size_t)gbase * bd + tid;
   if (G)
     for (int k = 0; k < nf; ++k) gacc[k * bd] = F2{0.f, 0.f};
   F2 acc = {0.f, 0.f};
 
   // one event: log P_i into the sums (MODE 0) or out_logp (MODE 1, through perm if sorted)
+  const bool mix = P.mix > 0;
   auto one_event = [&](int64_t i, const double* x, const Tay* tay) {
-    const F2 s = run_program<ArF2, G>(P, rec, rf, x, W, dynf, nf, bd, tid, tay);
+    const F2 s = mix ? run_mixture<G>(P, rec, rf, x, W, dynf + tid, bd, tay)
+                     : run_program<ArF2, G>(P, rec, rf, x, W, dynf, nf, bd, tid, tay);
     // P in [2^-80, 2^125): every term that underflowed on the way (absolute error below
     // 2^-149 times a leaf constant) is negligible against P
     const bool ok = P.root_log ? (fabsf(s.hi) < 3.0e38f)
@@ -613,8 +690,13 @@ __device__ __forceinline__ void events_1d_block(
         acc = df_sub(acc, lp);
         if (G) {
           const F2 sc = P.root_log ? F2{-1.f, 0.f} : df_neg(df_rcp(s));
-          const F2* g0 = dynf + tid;
-          for (int k = 0; k < nf; ++k) gacc[k * bd] = df_add(gacc[k * bd], df_mul(g0[k * bd], sc));
+          if (mix) {
+            mixture_grad(P, rf, dynf + tid, sc, gacc, bd);
+          } else {
+            const F2* g0 = dynf + tid;
+            for (int k = 0; k < nf; ++k)
+              gacc[k * bd] = df_add(gacc[k * bd], df_mul(g0[k * bd], sc));
+          }
         }
       }
     } else {
@@ -834,7 +916,10 @@ cudaError_t launch_norm_1d(const Program& P, const Program* prog, const WeidCoef
 }
 
 size_t events_1d_smem(const Program& P, bool grad, int threads) {
-  return grad ? (size_t)(kMaxStack + 1) * P.nfree * threads * sizeof(double) : 0;
+  if (!grad) return 0;
+  const int per = P.mix > 0 ? std::max(4 * kMixMax, kMaxStack * P.nfree) + P.nfree
+                            : (kMaxStack + 1) * P.nfree;
+  return (size_t)per * threads * sizeof(double);
 }
 
 cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCoef& W,

@@ -169,7 +169,8 @@ static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
   TickItem* d_items = static_cast<TickItem*>(T.d_block);
   double* d_theta = reinterpret_cast<double*>(static_cast<char*>(T.d_block) + T.bytes_items());
   int n_norm = 0, n_ev1 = 0, n_dz = 0, tot_norm = 0, tot_ev1 = 0, tot_dz = 0;
-  int nf1 = 0, nfd = 0;
+  int nfd = 0;
+  size_t smem1 = 0;  // the largest per-block scratch of the batched 1D programs
   for (int j = 0; j < nfit; ++j) {
     gf_ctx* c = fits[j]->ctx;
     fill_theta_all(c, fits[j]->theta.data(), T.h_theta + (size_t)j * T.cap_par);
@@ -182,7 +183,7 @@ static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
       }
       it_ev1[n_ev1++] = TickItem{c->dev.tick_desc, th, res, tot_ev1, c->dev.nblocks};
       tot_ev1 += c->dev.nblocks;
-      nf1 = std::max(nf1, (int)c->free_ids.size());
+      smem1 = std::max(smem1, events_1d_smem(c->prog, true, kThreads1D));
     } else {
       it_dz[n_dz++] = TickItem{c->dev.tick_desc, th, res, tot_dz, c->dev.nblocks};
       tot_dz += c->dev.nblocks;
@@ -202,8 +203,7 @@ static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
     ++nl;
   }
   if (e == cudaSuccess && n_ev1) {
-    const size_t smem = (size_t)(kMaxStack + 1) * nf1 * kThreads1D * sizeof(double);
-    e = launch_tick_1d(false, d_items + T.cap_fits, n_ev1, tot_ev1, W, smem, grid, st);
+    e = launch_tick_1d(false, d_items + T.cap_fits, n_ev1, tot_ev1, W, smem1, grid, st);
     ++nl;
   }
   if (e == cudaSuccess && n_dz) {

@@ -103,6 +103,7 @@ def _load():
         "gf_last_eval_graph": ([vp, _I, C.c_char_p, C.c_size_t], C.c_int),
         "gf_set_graphs": ([vp, C.c_int], C.c_int),
         "gf_set_event_sort": ([vp, C.c_int], C.c_int),
+        "gf_set_mixture_path": ([vp, C.c_int], C.c_int),
         "gf_update_data": ([vp, C.c_int64, C.POINTER(_D)], C.c_int),
         "gf_nll_noalloc": ([vp, C.c_int, C.c_int, _I, C.c_int64, C.POINTER(vp), _D, vp], C.c_int),
     }
@@ -342,6 +343,9 @@ class Context:
         t, s = C.c_double(), C.c_double()
         lib.gf_last_eval_times(self.h, C.byref(t), C.byref(s))
         return t.value, s.value
+
+    def set_mixture_path(self, enable):
+        self._ck(lib.gf_set_mixture_path(self.h, 1 if enable else 0), "gf_set_mixture_path")
 
     def set_event_sort(self, enable):
         self._ck(lib.gf_set_event_sort(self.h, 1 if enable else 0), "gf_set_event_sort")

@@ -153,6 +153,59 @@ def test_sorted_layout_matches_strided_loop(gf):
     assert np.max(np.abs(la - lb)) <= 1e-12 * np.abs(lb).max()
 
 
+def _mix3_models(gf):
+    """AddPdf of three leaves, two of them in the log domain: f1 Gauss + f2 Exp + rest Poly."""
+    ctx = gf.Context()
+    m = oracle.Model1D([(-1.0, 2.0)])
+    x = ctx.observable("x", -1.0, 2.0)
+    vals = [0.4, 0.3, -0.7, 1.0, 0.3, 0.5, 0.2]
+    names = ["mu", "s", "ax", "a0", "a1", "f1", "f2"]
+    P = [ctx.parameter(nm, v, 0.01) for nm, v in zip(names, vals)]
+    O = [m.param(v) for v in vals]
+    g = ctx.gauss(x, P[0], P[1]); og = m.gauss(0, O[0], O[1])
+    ex = ctx.exp(x, P[2]); oex = m.exp(0, O[2])
+    po = ctx.poly(x, [P[3], P[4]]); opo = m.poly(0, [O[3], O[4]])
+    root = ctx.add([g, ex, po], [P[5], P[6]]); m.add([og, oex, opo], [O[5], O[6]])
+    return ctx, root, [x], m
+
+
+@pytest.mark.parametrize("which", ["voigt", "mix3"])
+def test_mixture_path_matches_stack_machine(gf, which):
+    """An AddPdf of leaves is evaluated directly (P = sum c_k L_k) by default; the general
+    stack machine gives the same NLL, gradient and per-event log P, and both match the
+    oracle."""
+    rng = np.random.default_rng(21)
+    if which == "voigt":
+        x = _voigt_data(300_007)
+        a, ra, oa = pm.voigt_model(gf, nbins=2000)
+        b, rb, ob = pm.voigt_model(gf, nbins=2000)
+        m, free = om.voigt_model(nbins=2000)
+        th = m.p[free] * np.array([1.0, 1.03, 0.95, 1.02, 1.05])
+        p = m.p.copy(); p[free] = th
+        cols = [x]
+    else:
+        a, ra, oa, m = _mix3_models(gf)
+        b, rb, ob, _ = _mix3_models(gf)
+        cols = [rng.uniform(-1.0, 2.0, 50_001)]
+        th = m.p.copy()
+        p = th
+        free = np.arange(len(th))
+    b.set_mixture_path(False)
+    a.set_data(ra, oa, cols)
+    b.set_data(rb, ob, cols)
+    fa, ga = a.nll_grad(th)
+    fb, gb = b.nll_grad(th)
+    assert abs(fa - fb) <= 1e-12 * abs(fb)
+    _grad_close(ga, gb, len(cols[0]), rel=1e-10)
+    la, lb = a.logpdf(th), b.logpdf(th)
+    assert np.max(np.abs(la - lb)) <= 1e-12 * np.abs(lb).max()
+    fo, go = m.nll(cols, p, grad=True)
+    assert abs(fa - fo) <= 1e-9 * abs(fo)
+    _grad_close(ga, go[free], len(cols[0]))
+    lo_ = m.logpdf(cols, p)
+    assert np.max(np.abs(la - lo_)) <= 1e-12 * np.abs(lo_).max()
+
+
 # ---- generic trees (Sec. 3: sums, products, nesting) ----------------------------------------------------
 def _tree_models(gf):
     """Depth-3 tree over two observables: PROD(ADD(gauss, poly, exp), ADD(exp, gauss))."""
