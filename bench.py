@@ -40,17 +40,17 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # of floats) on the FP32 pipe, so its roofline is the FP32 pipe.  Algorithmic work per
 # event = the FP32 flops of that double-float algorithm (FADD + FMUL + 2 FFMA executed per
 # event, predicated-on, counted by ncu on the 10^7-event launch of this configuration:
-# 865.1 + 90.0 + 2 x 238.9; profiles/k_events_1d_voigt_1e7.md).  DRAM traffic of one
-# launch from the same capture (80.88 MB read + 5.58 MB written).
-FP32_FLOPS_PER_EVENT = {"voigt_grad": 1432.9}
-TRAFFIC_PER_LAUNCH = {"voigt_grad": 86.46e6}
+# 726.8 + 80.0 + 2 x 211.3; profiles/k_events_1d_voigt_1e7.md).  DRAM traffic of one
+# launch from the same capture (81.01 MB read + 4.89 MB written).
+FP32_FLOPS_PER_EVENT = {"voigt_grad": 1229.4}
+TRAFFIC_PER_LAUNCH = {"voigt_grad": 85.90e6}
 # Context: the same pass in FP64 operations of the method (FMA = 2, add/mul = 1, each
 # exp, log, sqrt or division = 1), counted from the source: w(z) by one Weideman series
 # (N = 40: 305) and its degree-5 expansion per chunk of 24 events (recurrence ~40 per
 # chunk, evaluation 20, argument 3) = 37 per event; Voigt value and 3 partials 31;
-# threshold value and partial 9; two fraction scalings with 5-wide gradients 14; sum and
-# gradient sum 6; log P, 1/P and the 5 gradient accumulations 12.
-FP64_FLOPS_PER_EVENT = {"voigt_grad": 109}
+# threshold value and partial 9; the mixture (2 products, 1 sum) and its gradient terms
+# (6 products, 6 sums) 15; log P and 1/P 2.
+FP64_FLOPS_PER_EVENT = {"voigt_grad": 94}
 
 
 def _peaks():
