@@ -813,8 +813,15 @@ __device__ __forceinline__ void dalitz_stream_block(
   if (tid == 0) *counter = 0u;
 }
 
+// Registers per variant (measured): pair (DF) event passes are held to 85 (3 blocks of
+// 256 per SM) -- their dependent pair chains need the warps more than the registers --,
+// FP32 ones to 128 (2 blocks); the pair cell pass keeps its registers (1 block).
+template <typename T, bool G, int METRIC>
+constexpr int dz_min_blocks() {
+  return std::is_same<T, DF>::value ? (METRIC == METRIC_NORM ? 1 : 3) : 2;
+}
 template <typename T, bool G, int METRIC, bool CO>
-__global__ void __launch_bounds__(kThreads) k_dalitz_stream(
+__global__ void __launch_bounds__(kThreads, dz_min_blocks<T, G, METRIC>()) k_dalitz_stream(
     const DalitzPlan D, const double* __restrict__ theta, const double* __restrict__ s12d,
     const double* __restrict__ s13d, const float* __restrict__ sf, int64_t n,
     const void* __restrict__ cache, int64_t cache_stride, int cache_wide,
