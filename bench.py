@@ -557,6 +557,34 @@ def voigt_model_nodata(gf):
     return ctx, root, [xo], None, None
 
 
+def run_exp_sweep(torch, gf, sizes=(10**6, 10**7, 10**8, 10**9), steps=20):
+    """Truncated exponential at growing event counts: the event pass reads 8 B per event
+    and does little arithmetic, so at large n it is bound by HBM.  The data are 10^7 draws
+    at alpha = -1 tiled on the device (device columns, gf_set_data_device); NLL and
+    gradient per step, L2 flushed between steps."""
+    base = torch.from_numpy(synth.exp_events(10**7, -1.0, seed=synth.SEED_EXP)).cuda()
+    hbm = _peaks().get("hbm_gbs", 6800.0)
+    rows = []
+    for n in sizes:
+        reps = (n + len(base) - 1) // len(base)
+        x = base.repeat(reps)[:n].contiguous() if reps > 1 else base[:n].contiguous()
+        ctx = gf.Context(0, gf.GF_FP64)
+        xo = ctx.observable("x", 0.0, 10.0)
+        a = ctx.parameter("alpha", -1.0, 0.1, -10.0, 10.0)
+        root = ctx.exp(xo, a)
+        ctx.set_data_device(root, [xo], n, [x.data_ptr()], keep=x)
+        r = time_steps(torch, ctx, [np.array([-1.0 - 1e-3 * k]) for k in range(4)], steps, 3)
+        k_s = float(np.mean(r["kernel_ms"])) / 1e3
+        rows.append({"events": n, "ms_per_eval": float(np.mean(r["step_ms"])),
+                     "kernel_ms": k_s * 1e3, "kernel_gbs": 8 * n / k_s / 1e9,
+                     "kernel_frac_of_measured_hbm": 8 * n / k_s / 1e9 / hbm,
+                     "events_x_evals_per_s": n * steps / (sum(r["step_ms"]) / 1e3)})
+        ctx.close()
+        del x
+    torch.cuda.empty_cache()
+    return rows
+
+
 def run_extra(torch, gf, args):
     """Secondary measurements: configs 1, 3, 4 evaluation rates (and, on request, fit
     times and the serving study)."""
@@ -569,6 +597,7 @@ def run_extra(torch, gf, args):
                               "us_per_eval": 1e3 * float(np.mean(r["step_ms"])),
                               "kernel_us": 1e3 * float(np.mean(r["kernel_ms"]))}
     ctx.close()
+    out["config1_exp_hbm_sweep"] = run_exp_sweep(torch, gf)
     # config 3 (FP64, 1e6 events, cached per-event amplitudes, Gram normalisation)
     spec = dalitz_spec()
     data = dalitz_events_gpu(gf, spec, 1_000_000, synth.SEED_DALITZ_EVENTS)

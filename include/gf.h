@@ -254,10 +254,12 @@ int gf_last_eval_graph(gf_ctx* ctx, int* replayed, char* why_not, size_t n);
  * Takes effect at the next gf_set_data.  The fit server turns it off for its requests. */
 int gf_set_event_sort(gf_ctx* ctx, int enable);
 /* Evaluate a 1D tree that is an AddPdf of leaves (up to 4 components, each leaf with at
- * most 3 parameters) directly as P = sum_k c_k L_k with its gradient (enable != 0, the
- * default), or on the general postfix stack machine (0).  Both compute the same
- * quantities (Sec. 3's AddPdf); the direct form avoids the stack's per-operation
- * gradient vectors.  Takes effect at the next evaluation. */
+ * most 3 parameters) directly as P = sum_k c_k L_k with its gradient, and a single
+ * exponential or Gaussian leaf, or a ProdPdf of up to 4 of them over at most two
+ * observables (Listing 1, Listing 2), directly as log P = sum_k log L_k (enable != 0,
+ * the default); or run both on the general postfix stack machine (0).  Both compute the
+ * same quantities (Sec. 3's AddPdf and ProdPdf); the direct forms avoid the stack's
+ * per-operation gradient vectors.  Takes effect at the next evaluation. */
 int gf_set_mixture_path(gf_ctx* ctx, int enable);
 /* Turn the replay of captured evaluation graphs on (enable != 0, the default) or off (every
  * evaluation launches its kernels one by one; the results are the same bits). */

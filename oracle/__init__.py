@@ -79,6 +79,9 @@ def lib():
             so.orc_logpdf.restype = C.c_int
             so.orc_nll.argtypes = [C.POINTER(OrcModel), _D, C.c_int, C.c_int64, C.POINTER(_D), _D, _D]
             so.orc_nll.restype = C.c_int
+            so.orc_binned.argtypes = [C.POINTER(OrcModel), _D, C.c_int, C.c_int64, C.POINTER(_D),
+                                      _D, _D, C.c_double, C.c_int, _D, _D]
+            so.orc_binned.restype = C.c_int
             so.orc_leaf_shape_many.argtypes = [C.POINTER(OrcNode), _D, C.c_int64, _D, _D]
             so.orc_dalitz_inside.argtypes = [C.POINTER(OrcDkin), C.c_double, C.c_double]
             so.orc_dalitz_inside_many.argtypes = [C.POINTER(OrcDkin), C.c_int64, _D, _D,
@@ -186,6 +189,9 @@ class Model1D:
 
     def _cols(self, cols):
         cols = [_f64(c) for c in cols]
+        if len(cols) != len(self.lo) or any(len(c) != len(cols[0]) for c in cols):
+            raise ValueError(f"the model has {len(self.lo)} observables: one column each, "
+                             "all of the same length")
         ptrs = (_D * len(cols))(*[_dp(c) for c in cols])
         return cols, ptrs
 
@@ -215,6 +221,24 @@ class Model1D:
         g = np.zeros(len(p)) if grad else None
         rc = lib().orc_nll(C.byref(m), _dp(p), len(p), len(cols[0]), ptrs, _dp(out),
                            _dp(g) if grad else None)
+        assert rc == 0
+        return (out[0], g) if grad else out[0]
+
+    def binned(self, centres, counts, K, metric, s2=None, p=None, grad: bool = False):
+        """Binned metric over bins with the given centres (one column per observable) and
+        contents: 0 multinomial -sum n log P, 1 Poisson sum nu - n log nu, 2 chi-squared
+        sum (n - nu)^2/s2, with nu = K P(centre)."""
+        p = self.p if p is None else _f64(p)
+        m, keep = self._model()
+        cols, ptrs = self._cols(centres)
+        n = _f64(counts)
+        assert len(n) == len(cols[0])
+        v = _f64(s2) if s2 is not None else None
+        out = np.zeros(1)
+        g = np.zeros(len(p)) if grad else None
+        rc = lib().orc_binned(C.byref(m), _dp(p), len(p), len(n), ptrs, _dp(n),
+                              _dp(v) if v is not None else None, float(K), int(metric),
+                              _dp(out), _dp(g) if grad else None)
         assert rc == 0
         return (out[0], g) if grad else out[0]
 

@@ -624,6 +624,28 @@ static void detect_mixture(Program& P) {
   }
 }
 
+// A log-domain product of exponential and Gaussian leaves (LEAF, then (LEAF, LMUL) x
+// (K - 1), K <= kLogLeaf, over at most two observables) runs on the direct log-sum kernel.
+static void detect_logsum(Program& P) {
+  P.logsum = 0;
+  if (!P.root_log || P.nobs > 2 || P.nleaf < 1 || P.nleaf > kLogLeaf || P.n != 2 * P.nleaf - 1)
+    return;
+  for (int pc = 0; pc < P.n; ++pc) {
+    const Instr& I = P.ins[pc];
+    const bool leaf_slot = pc == 0 || (pc % 2) == 1;
+    if (leaf_slot) {
+      if (I.op != OP_LEAF || (I.kind != L_EXP && I.kind != L_GAUSS) ||
+          I.slot != (pc == 0 ? 0 : (pc + 1) / 2) || I.obs > 1)
+        return;
+    } else if (I.op != OP_LMUL) {
+      return;
+    }
+  }
+  for (int l = 0; l < P.nleaf; ++l)
+    if (P.leaf[l].nbins > 0) return;
+  P.logsum = 1;
+}
+
 bool has_cycle(gf_ctx* ctx, int id, std::vector<int>& state) {
   if (state[id] == 1) return true;
   if (state[id] == 2) return false;
@@ -727,6 +749,7 @@ int ensure_compiled(gf_ctx* ctx) {
     P.sorted = (d.sorted && P.tay_slot >= 0 && d.sort_obs == P.tay_obs) ? 1 : 0;
     if (ctx->mixture_path) detect_mixture(P);
     else P.mix = 0;
+    if (ctx->mixture_path) detect_logsum(P);
     // the kernels read the program from device memory (it is too large for parameters);
     // stream-ordered copy, then wait: the next launch may go to another stream
     DevState& dv = ctx->dev;
@@ -862,6 +885,8 @@ static int finish_set_data(gf_ctx* ctx) {
     bool co = ctx->dplan.nres > 0;
     for (int r = 0; r < ctx->dplan.nres; ++r) co = co && ctx->dplan.res[r].ev_cached >= 0;
     per_sm = dalitz_blocks_per_sm(ctx->precision == GF_MIXED, true, co, ctx->dplan.nfree);
+  } else if (ctx->prog.logsum) {
+    per_sm = events_logsum_blocks_per_sm(ctx->prog);
   } else {
     per_sm = events_1d_blocks_per_sm(true, events_1d_smem(ctx->prog, true, kThreads1D));
   }

@@ -23,6 +23,7 @@ constexpr int kThreads1D = 128; // threads per block of the 1D event kernel (its
                                 // stack: 5 x nfree x 128 doubles of shared memory <= 123 KB)
 constexpr int kMixMax = 4;      // components of an AddPdf evaluated without the stack machine
 constexpr int kMixLocal = 3;    // ... each leaf with at most 3 local parameters
+constexpr int kLogLeaf = 4;    // leaves of a log-domain product evaluated directly
 constexpr int kChunk = 24;      // sorted 1D data: events per expansion of w (k_1d.cu); the
                                 // chunked loop runs when there are >= kChunk/2 events per thread
 
@@ -72,7 +73,10 @@ struct Program {
   // P = sum_k c_k L_k without the stack machine.  mix = K (2..kMixMax), 0: not a mixture.
   int32_t mix;
   int32_t mix_leaf[4], mix_log[4], mix_scale[4];  // instruction indices; TOLIN present
-  int32_t pad0;
+  // log-domain product of exponential and Gaussian leaves (the program is LEAF, then
+  // K - 1 x [LEAF, LMUL], K <= kLogLeaf, at most 2 observables): log P = sum_k l_k is
+  // evaluated directly, without the stack machine.  1: this form, 0: not.
+  int32_t logsum;
   Instr ins[kMaxIns];
   LeafDesc leaf[kMaxLeaf];
   CoefDesc coef[kMaxCoef];

@@ -805,6 +805,228 @@ __global__ void __launch_bounds__(kThreads1D) k_events_1d(
                            tay_t);
 }
 
+// ---- log-domain products of exponential and Gaussian leaves ----------------------------
+// A program of the form LEAF, (LEAF, LMUL) x (K - 1) with exponential and Gaussian leaves
+// (Listing 1's ExpPdf, Listing 2's ProdPdf of two of them) has
+//   log P_i = sum_k l_k(x_i),  l = a x - log N (EXP),  l = -u^2/2 - log N,
+//   u = (x - mu)/sigma (GAUSS),
+// so each event needs a few pair operations and no stack.  Per event the kernel adds the
+// data-dependent part of every l_k (a x, -u^2/2) and of its gradient (x; u/sigma,
+// u^2/sigma) into register accumulators; the constants -log N and d log N/d theta of each
+// leaf enter once per thread, times its event count.  Data enter through df_split_trunc.
+
+// x as a pair on the integer and FP32 pipes only: hi = x truncated to 24 significant bits,
+// lo = the 29-bit remainder m, formed as m_hi 2^23 + m_lo from two exact floats (the
+// 2^23 + k bit trick; no conversion instruction) with one rounding (|hi + lo - x| <=
+// 2^-47 |x|; |lo| < ulp(hi)).  |x| outside [2^-74, 2^127), zero included, takes the
+// conversion path.
+__device__ __forceinline__ F2 df_split_trunc(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+  if (e - 949u > 201u) return df_from(d);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  // exponent field e - 896 (8 bits) and the top 23 mantissa bits, by one funnel shift
+  const unsigned hb = ((unsigned)(b >> 29) - (896u << 23)) | sign;
+  const unsigned scale = ((hb & 0x7f800000u) - (52u << 23)) | sign;  // +-2^(e - 1075)
+  const unsigned m = (unsigned)b & 0x1fffffffu;
+  const float ml = __fsub_rn(__uint_as_float(0x4b000000u | (m & 0x7fffffu)), 8388608.f);
+  const float mh = __fsub_rn(__uint_as_float(0x4b000000u | (m >> 23)), 8388608.f);
+  const float lo = __fmul_rn(__fmaf_rn(mh, 8388608.f, ml), __uint_as_float(scale));
+  return {__uint_as_float(hb), lo};
+}
+
+// Running sum of pairs: the high parts by TwoSum, the low parts and rounding errors in a
+// float, renormalised after every few terms (renorm) so that |lo| stays within a few
+// ulp(hi): each term then adds at most ~2^-47 |sum| of rounding, n terms n 2^-47.
+struct LazyAcc {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float e) {
+    const F2 s = two_sum(hi, a);
+    hi = s.hi;
+    lo = __fadd_rn(lo, __fadd_rn(s.lo, e));
+  }
+  __device__ __forceinline__ void renorm() {
+    const F2 s = two_sum(hi, lo);
+    hi = s.hi;
+    lo = s.lo;
+  }
+  __device__ __forceinline__ F2 get() const { return two_sum(hi, lo); }
+};
+
+// a * b as p + e (p = fl(a.hi b.hi), e = its error and the cross terms)
+__device__ __forceinline__ void prod_pe(F2 a, F2 b, float& p, float& e) {
+  p = __fmul_rn(a.hi, b.hi);
+  e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+}
+
+constexpr int kLogUnroll = 4;  // double2 loads in flight per thread and observable
+
+// KM: leaves handled (1: a single leaf over one observable; kLogLeaf: the general form);
+// KIND: the leaf kind when KM == 1 (L_EXP or L_GAUSS), 0: read from the program.
+template <bool G, int KM, int KIND>
+__global__ void __launch_bounds__(kThreads1D) k_events_logsum(
+    const Program* __restrict__ Pg, const Cols cols, const int64_t n,
+    const double* __restrict__ theta, double* __restrict__ partials,
+    unsigned* __restrict__ counter, double* __restrict__ result) {
+  __shared__ Program P;
+  __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
+  __shared__ F2 rf[kMaxLeaf * kLeafRec];
+  __shared__ double red[(kThreads1D / 32) * (1 + kMaxFree1D)];
+  __shared__ int last;
+  extern __shared__ F2 gsh[];  // G: nfree x blockDim pairs (the per-thread gradient sums)
+  const int tid = threadIdx.x, bd = blockDim.x;
+  load_program(Pg, P);
+  if (tid < P.nleaf) make_leaf_record(P.leaf[tid], theta, 1.0, nullptr, rec + tid * kLeafRec);
+  __syncthreads();
+  for (int k = tid; k < kMaxLeaf * kLeafRec; k += bd) rf[k] = df_from(rec[k]);
+  __syncthreads();
+
+  const int K = KM == 1 ? 1 : P.nleaf;
+  int kind[KM], ob[KM];
+  F2 c0[KM], c1[KM];  // EXP: a; GAUSS: 1/sigma (c1 unused for EXP)
+  double mu[KM];
+#pragma unroll
+  for (int k = 0; k < KM; ++k) {
+    const int s = k < K ? k : 0;  // leaf k: record slot k, instruction 2k - 1 (k > 0)
+    kind[k] = KIND ? KIND : (k < K ? P.leaf[s].kind : 0);
+    ob[k] = k < K ? P.leaf[s].obs : 0;
+    c0[k] = rf[s * kLeafRec + 10];
+    c1[k] = rf[s * kLeafRec + 11];
+    mu[k] = rec[s * kLeafRec + 10];
+  }
+  LazyAcc v;
+  LazyAcc g[KM][2];
+
+  // one event: the data-dependent parts of log P and of its gradient
+  auto event = [&](double x0, double x1) {
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      if (KM > 1 && k >= K) break;
+      const double x = (KM > 1 && ob[k]) ? x1 : x0;
+      float p, q;
+      if (kind[k] == L_EXP) {
+        const F2 X = df_split_trunc(x);
+        prod_pe(c0[k], X, p, q);  // a x
+        v.add(p, q);
+        if (G) g[k][0].add(X.hi, X.lo);
+      } else {  // L_GAUSS: u = (x - mu)/sigma from the exact difference
+        const F2 U = df_mul(df_split(x - mu[k]), c1[k]);
+        const F2 U2 = df_mul(U, U);
+        v.add(-0.5f * U2.hi, -0.5f * U2.lo);  // -u^2/2
+        if (G) {
+          prod_pe(U, c1[k], p, q);  // u / sigma
+          g[k][0].add(p, q);
+          prod_pe(U2, c1[k], p, q);  // u^2 / sigma
+          g[k][1].add(p, q);
+        }
+      }
+    }
+  };
+  auto renorm = [&]() {
+    v.renorm();
+    if (G)
+#pragma unroll
+      for (int k = 0; k < KM; ++k) {
+        g[k][0].renorm();
+        g[k][1].renorm();
+      }
+  };
+
+  const int64_t nfull = n >> 1;  // pairs holding two events
+  const int64_t npairs = (n + 1) >> 1;
+  const int64_t nthreads = (int64_t)gridDim.x * bd;
+  const bool two = KM > 1 && P.nobs > 1;
+  const double2* pa = reinterpret_cast<const double2*>(cols.c[0]);
+  const double2* pb = reinterpret_cast<const double2*>(two ? cols.c[1] : cols.c[0]);
+  int64_t p0 = (int64_t)blockIdx.x * bd + tid;
+  // main loop: kLogUnroll full pairs per thread and iteration, loads first, no guards;
+  // pointers advance by increments (no 64-bit multiplies in the loop)
+  const int64_t step = kLogUnroll * nthreads;
+  const int64_t span = p0 + (kLogUnroll - 1) * nthreads;
+  const int iters = span < nfull ? (int)((nfull - 1 - span) / step + 1) : 0;
+  int cnt = 2 * kLogUnroll * iters;
+  {
+    const double2* qa = pa + p0;
+    const double2* qb = pb + p0;
+    for (int it = 0; it < iters; ++it) {
+      double2 xa[kLogUnroll], xb[kLogUnroll];
+#pragma unroll
+      for (int u = 0; u < kLogUnroll; ++u) {
+        xa[u] = __ldcs(qa + u * nthreads);
+        if (two) xb[u] = __ldcs(qb + u * nthreads);
+        else xb[u] = xa[u];
+      }
+      qa += step;
+      qb += step;
+#pragma unroll
+      for (int u = 0; u < kLogUnroll; ++u) {
+        event(xa[u].x, xb[u].x);
+        event(xa[u].y, xb[u].y);
+      }
+      renorm();
+    }
+  }
+  p0 += (int64_t)iters * step;
+  // the thread's remaining pairs (fewer than kLogUnroll), the last one possibly single
+  for (int64_t pr = p0; pr < npairs; pr += nthreads) {
+    if (pr < nfull) {
+      const double2 a = __ldcs(pa + pr);
+      const double2 b = two ? __ldcs(pb + pr) : a;
+      event(a.x, b.x);
+      event(a.y, b.y);
+      cnt += 2;
+    } else {
+      const double a = __ldcs(cols.c[0] + 2 * pr);
+      const double b = two ? __ldcs(cols.c[1] + 2 * pr) : a;
+      event(a, b);
+      cnt += 1;
+    }
+  }
+  renorm();
+
+  // constants once per thread: value + cnt sum_k (-log N_k); gradient - cnt dlogN/dtheta
+  // (cnt < 2^24 per thread: exact as a float)
+  const F2 fc = F2{(float)cnt, 0.f};
+  F2 val = v.get();
+#pragma unroll
+  for (int k = 0; k < KM; ++k)
+    if (k < K) val = df_sub(val, df_mul(fc, rf[k * kLeafRec + 1]));
+  val = df_neg(val);  // -sum log P
+  const int nf = P.nfree;
+  if (G) {
+    for (int j = 0; j < nf; ++j) gsh[j * bd + tid] = F2{0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      if (k >= K) break;
+      const Instr& I = P.ins[k == 0 ? 0 : 2 * k - 1];
+      const int np = kind[k] == L_EXP ? 1 : 2;
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        if (j < np && I.gidx[j] >= 0) {
+          F2& t = gsh[I.gidx[j] * bd + tid];
+          t = df_sub(t, df_sub(g[k][j].get(), df_mul(fc, rf[k * kLeafRec + 2 + j])));
+        }
+    }
+  }
+  const int m = 1 + (G ? nf : 0);
+  const int stride_p = 1 + kMaxFree1D;
+  block_sum_pairs([&](int k) -> F2 { return k == 0 ? val : gsh[(k - 1) * bd + tid]; }, m, red,
+                  partials + (size_t)blockIdx.x * stride_p);
+  if (!arrive_last_of(counter, gridDim.x, &last)) return;
+  reduce_partials(partials, gridDim.x, stride_p, m, result, red);
+  if (tid == 0) *counter = 0u;
+}
+
+// the instantiation for a program (single exponential or Gaussian leaf, or the general form)
+template <bool G>
+static auto logsum_kernel(const Program& P) {
+  if (P.nleaf == 1 && P.leaf[0].kind == L_EXP) return k_events_logsum<G, 1, L_EXP>;
+  if (P.nleaf == 1 && P.leaf[0].kind == L_GAUSS) return k_events_logsum<G, 1, L_GAUSS>;
+  return k_events_logsum<G, kLogLeaf, 0>;
+}
+
 // ---- batched tick: every waiting 1D fit in one persistent launch -----------------------
 // Shared by the two tick kernels: find the item's fit and bring its program into shared
 // memory when it changes (blocks walk the items in increasing order).
@@ -930,7 +1152,11 @@ cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCo
                              int nblocks, cudaStream_t st) {
   const int threads = kThreads1D;
   const size_t smem = events_1d_smem(P, grad, threads);
-  if (store) {
+  if (P.logsum && !store) {
+    const size_t gs = grad ? sizeof(F2) * P.nfree * threads : 0;
+    auto k = grad ? logsum_kernel<true>(P) : logsum_kernel<false>(P);
+    k<<<nblocks, threads, gs, st>>>(prog, cols, n, theta, partials, counter, result);
+  } else if (store) {
     k_events_1d<false, 1><<<nblocks, threads, 0, st>>>(prog, W, cols, n, theta, derived, partials,
                                                        counter, result, out_logp, perm,
                                                        analytic_only);
@@ -954,6 +1180,14 @@ void prepare_kernels_1d() {
                        200 * 1024);
   cudaFuncSetAttribute(k_tick_events_1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
+}
+
+int events_logsum_blocks_per_sm(const Program& P) {
+  int nb = 0;
+  const size_t gs = sizeof(F2) * P.nfree * kThreads1D;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, logsum_kernel<true>(P), kThreads1D, gs);
+  cudaGetLastError();
+  return nb > 0 ? nb : 1;
 }
 
 int events_1d_blocks_per_sm(bool grad, size_t smem) {

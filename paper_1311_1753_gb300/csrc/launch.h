@@ -23,6 +23,7 @@ cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCo
                              const int32_t* perm, bool grad, bool store, int analytic_only,
                              int nblocks, cudaStream_t st);
 int events_1d_blocks_per_sm(bool grad, size_t smem);  // also opts in to large shared memory
+int events_logsum_blocks_per_sm(const Program& P);  // the direct log-sum kernel
 void prepare_kernels_1d();
 // Sort (key, index) pairs ascending by the FP64 key (k_sort.cu): perm_tmp receives
 // 0 .. n-1, perm_out the permutation, key_out the sorted keys.  temp == nullptr: only

@@ -206,6 +206,68 @@ def test_mixture_path_matches_stack_machine(gf, which):
     assert np.max(np.abs(la - lo_)) <= 1e-12 * np.abs(lo_).max()
 
 
+# ---- direct log-sum path (exponential / Gaussian leaves and their products) ------------------------
+def _logsum_models(gf, which):
+    """Returns (ctx_direct, ctx_stack, root_a, root_b, obs_a, obs_b, oracle model, columns)."""
+    rng = np.random.default_rng(31)
+    out = []
+    for _ in range(2):
+        ctx = gf.Context()
+        m = oracle.Model1D([(0.0, 10.0)] if which == "exp" else [(0.0, 10.0), (-2.0, 3.0)])
+        x = ctx.observable("x", 0.0, 10.0)
+        y = ctx.observable("y", -2.0, 3.0)
+        if which == "exp":
+            a = ctx.parameter("a", -1.3, 0.1, -10, 10)
+            root, obs = ctx.exp(x, a), [x]
+            m.exp(0, m.param(-1.3))
+        elif which == "gauss":
+            mu = ctx.parameter("mu", 0.4, 0.1)
+            s = ctx.parameter("s", 0.9, 0.1, 0.01, 5)
+            root, obs = ctx.gauss(y, mu, s), [y]
+            m = oracle.Model1D([(-2.0, 3.0)])
+            m.gauss(0, m.param(0.4), m.param(0.9))
+        else:  # exp(x) * gauss(y) * exp(y)-free: three leaves over two observables
+            a = ctx.parameter("a", -0.7, 0.1, -10, 10)
+            mu = ctx.parameter("mu", 0.4, 0.1)
+            s = ctx.parameter("s", 0.9, 0.1, 0.01, 5)
+            b = ctx.parameter("b", 0.2, 0.1, -10, 10, fixed=True)
+            root = ctx.prod([ctx.exp(x, a), ctx.gauss(y, mu, s)])
+            obs = [x, y]
+            m.prod([m.exp(0, m.param(-0.7)), m.gauss(1, m.param(0.4), m.param(0.9))])
+            m.param(0.2)
+        out.append((ctx, root, obs, m))
+    n = {"exp": 200_003, "gauss": 50_001, "prod": 100_001}[which]
+    xs = synth.exp_events(n, -1.0, seed=4)
+    xs[:5] = [0.0, 1e-30, 10.0, 5e-23, 2.0 ** -74]  # conversion path of the bit split
+    ys = np.clip(rng.normal(0.4, 0.9, n), -2.0, 3.0)
+    cols = {"exp": [xs], "gauss": [ys], "prod": [xs, ys]}[which]
+    return out, cols
+
+
+@pytest.mark.parametrize("which", ["exp", "gauss", "prod"])
+def test_logsum_path_matches_stack_machine(gf, which):
+    """A single exponential or Gaussian leaf, or a ProdPdf of them, runs on the direct
+    log-sum kernel by default; the stack machine gives the same NLL and gradient, and both
+    match the oracle."""
+    ((a, ra, oa, m), (b, rb, ob, _)), cols = _logsum_models(gf, which)
+    b.set_mixture_path(False)
+    for n in (1, 2, 3, 257, len(cols[0])):
+        cc = [c[:n] for c in cols]
+        a.set_data(ra, oa, cc)
+        b.set_data(rb, ob, cc)
+        for scale in (1.0, 1.1):
+            th = m.p[: len(a.free_params())] * scale
+            fa, ga = a.nll_grad(th)
+            fb, gb = b.nll_grad(th)
+            assert abs(a.nll(th) - fa) <= 1e-12 * max(1.0, abs(fa))
+            assert abs(fa - fb) <= 1e-11 * max(1.0, abs(fb)), (n, fa, fb)
+            _grad_close(ga, gb, n, rel=1e-10)
+            p = m.p.copy(); p[: len(th)] = th
+            fo, go = m.nll(cc, p, grad=True)
+            assert abs(fa - fo) <= 1e-9 * max(1.0, abs(fo))
+            _grad_close(ga, go[: len(th)], n)
+
+
 # ---- generic trees (Sec. 3: sums, products, nesting) ----------------------------------------------------
 def _tree_models(gf):
     """Depth-3 tree over two observables: PROD(ADD(gauss, poly, exp), ADD(exp, gauss))."""

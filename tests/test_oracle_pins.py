@@ -566,3 +566,104 @@ def test_config1_fit_matches_mle_root_and_error():
     assert abs(r.x[0] - root) < 1e-3 * sig
     assert abs(r.err[0] / sig - 1) < 1e-3
     assert abs(sig - 0.003169) < 2e-5
+
+
+# --------------------------------------------------------------------------------
+# Binned metrics (Sec. 2: the metric is separate from the PDF's evaluation; Sec. 4:
+# the binned D*+ line-width fit)
+# --------------------------------------------------------------------------------
+def _exp_hist(alpha_true=-1.0, nb=40, lo=0.0, hi=10.0, n=20_000, seed=7):
+    x = synth.exp_events(n, alpha_true, lo, hi, seed=seed)
+    counts, edges = np.histogram(x, bins=nb, range=(lo, hi))
+    return 0.5 * (edges[1:] + edges[:-1]), counts.astype(float), (hi - lo) / nb
+
+
+def test_binned_multinomial_equals_unbinned_on_repeated_centres():
+    """-sum n_b log P(x_b) is the unbinned NLL of a data set holding each centre n_b
+    times (integer contents), value and gradient."""
+    m, free = om.exp_model(-0.8)
+    c, n, h = _exp_hist()
+    rep = np.repeat(c, n.astype(int))
+    fb, gb = m.binned([c], n, n.sum() * h, 0, grad=True)
+    fu, gu = m.nll([rep], grad=True)
+    assert abs(fb - fu) <= 1e-12 * abs(fu)
+    assert abs(gb[0] - gu[0]) <= 1e-11 * abs(gu[0])
+
+
+def test_binned_poisson_vs_scipy_logpmf():
+    """Poisson metric = -sum log Poisson(n_b; nu_b) - sum log n_b! with nu_b from the
+    closed-form truncated exponential density (scipy's pmf, no oracle density)."""
+    alpha = -0.8
+    m, free = om.exp_model(alpha)
+    c, n, h = _exp_hist()
+    K = n.sum() * h
+    nu = K * alpha * np.exp(alpha * c) / np.expm1(alpha * 10.0)
+    ref = -(stats.poisson.logpmf(n, nu) + special.gammaln(n + 1)).sum()
+    assert abs(m.binned([c], n, K, 1) - ref) <= 1e-11 * abs(ref)
+
+
+def test_binned_chisq_minimum_matches_curve_fit():
+    """The chi-squared fit of a truncated Gaussian histogram (oracle metric + oracle BFGS)
+    lands where scipy's least-squares curve_fit puts it, with its covariance."""
+    lo, hi, nb = -3.0, 4.0, 70
+    rng = np.random.Generator(np.random.PCG64(99))
+    x = rng.normal(0.3, 0.8, 60_000)
+    x = x[(x >= lo) & (x <= hi)]
+    counts, edges = np.histogram(x, nb, (lo, hi))
+    c = 0.5 * (edges[1:] + edges[:-1])
+    h = (hi - lo) / nb
+    n = counts.astype(float)
+    s2 = np.maximum(n, 1.0)
+    K = n.sum() * h
+
+    def shape(xc, mu, s):
+        return K * stats.truncnorm.pdf(xc, (lo - mu) / s, (hi - mu) / s, loc=mu, scale=s)
+
+    popt, pcov = optimize.curve_fit(shape, c, n, p0=[0.2, 0.9], sigma=np.sqrt(s2),
+                                    absolute_sigma=True)
+    m = oracle.Model1D([(lo, hi)])
+    m.gauss(0, m.param(0.2), m.param(0.9))
+    r = minimise.fit(lambda q: m.binned([c], n, K, 2, s2=s2, p=q, grad=True),
+                     np.array([0.2, 0.9]), step=np.array([0.05, 0.05]), up=1.0, tol=1e-12)
+    assert r.converged
+    err = np.sqrt(np.diag(pcov))
+    assert np.all(np.abs(r.x - popt) <= 1e-4 * err), (r.x, popt)
+    # curve_fit's covariance is the Gauss-Newton (J^T W J)^-1: equal to 2 H^-1 up to the
+    # residual terms of the chi-squared Hessian (a few per cent here)
+    assert np.all(np.abs(np.sqrt(np.diag(r.cov)) / err - 1) < 0.05)
+
+
+@pytest.mark.parametrize("metric", [0, 1, 2])
+def test_binned_metrics_gradient_fd(metric):
+    m, free = om.voigt_model(nbins=2000)
+    lo, hi = synth.VOIGT_RANGE
+    x = synth.voigt_threshold_events(50_000, **synth.VOIGT_TRUTH, lo=lo, hi=hi)
+    counts, edges = np.histogram(x, 500, (lo, hi))
+    c = 0.5 * (edges[1:] + edges[:-1])
+    n = counts.astype(float)
+    K = n.sum() * (hi - lo) / 500
+    p = m.p
+    p[free] *= np.array([1.00001, 1.02, 0.97, 1.05, 0.9])
+    _fd_check(lambda q: m.binned([c], n, K, metric, s2=np.maximum(n, 1.0), p=q, grad=True),
+              p, free, rel=2e-6)
+
+
+def test_binned_asimov_contents_are_stationary():
+    """Contents equal to their expectation (n_b = nu_b(theta0)) make the Poisson and
+    chi-squared metrics stationary at theta0, with chi-squared = 0 there."""
+    m, free = om.voigt_model(nbins=400)
+    lo, hi = synth.VOIGT_RANGE
+    h = (hi - lo) / 400
+    c = lo + (np.arange(400) + 0.5) * h
+    K = 1e6 * h
+    n = K * np.exp(m.logpdf([c]))
+    q = m.p.copy()
+    q[free] *= 1.001
+    for metric in (1, 2):
+        s2 = np.maximum(n, 1.0)
+        f, g = m.binned([c], n, K, metric, s2=s2, grad=True)
+        # scale: the same gradient 0.1 % away from theta0, parameter by parameter
+        g1 = m.binned([c], n, K, metric, s2=s2, p=q, grad=True)[1]
+        assert np.all(np.abs(g[free]) <= 1e-9 * np.abs(g1[free])), (metric, g[free], g1[free])
+        if metric == 2:
+            assert f <= 1e-18 * K
