@@ -64,6 +64,11 @@ __device__ __forceinline__ F2 df_from(double v) {
 }
 __device__ __forceinline__ double df_to(F2 a) { return (double)a.hi + (double)a.lo; }
 
+// df_from out of line, for the rare inputs of the bit splits below: inline, the compiler
+// may predicate its two conversions and FP64 subtraction into every call, and predicated-
+// off FP64 instructions still occupy GB300's narrow FP64 pipe.
+static __device__ __noinline__ F2 df_from_cold(double v) { return df_from(v); }
+
 // d as a pair without FP64 conversions (integer pipe and a few FP32 operations): hi is d
 // rounded to 24 significant bits (round half up on the magnitude), lo the remainder
 // (at most 28 bits and a sign) rounded to 24, so hi + lo equals d to 2^-48 relative.
@@ -71,7 +76,7 @@ __device__ __forceinline__ double df_to(F2 a) { return (double)a.hi + (double)a.
 __device__ __forceinline__ F2 df_split(double d) {
   const long long b = __double_as_longlong(d);
   const int e = (int)((b >> 52) & 0x7ff);
-  if (e < 949 || e > 1149) return df_from(d);
+  if (e < 949 || e > 1149) return df_from_cold(d);
   const unsigned sign = (unsigned)((unsigned long long)b >> 32) & 0x80000000u;
   const unsigned up = (unsigned)(b >> 28) & 1u;  // top bit of the remainder: round up
   const float hi = __uint_as_float((sign | ((unsigned)(e - 896) << 23) |

@@ -823,7 +823,7 @@ __global__ void __launch_bounds__(kThreads1D) k_events_1d(
 __device__ __forceinline__ F2 df_split_trunc(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
-  if (e - 949u > 201u) return df_from(d);
+  if (e - 949u > 201u) return df_from_cold(d);
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
   // exponent field e - 896 (8 bits) and the top 23 mantissa bits, by one funnel shift
   const unsigned hb = ((unsigned)(b >> 29) - (896u << 23)) | sign;
