@@ -141,6 +141,32 @@ int gf_dataset_create(gf_ctx* ctx, int nobs, const int* obs, gf_dataset** ds);
 int gf_dataset_add_events(gf_dataset* ds, int64_t n, const double* const* cols);
 int64_t gf_dataset_size(const gf_dataset* ds);
 int gf_dataset_destroy(gf_dataset* ds);
+/* Binned data set (Sec. 4: the D*+ line-width fit is a binned fit; Sec. 2: the fit's
+ * metric is separate from the PDF's evaluation).  Each observable obs[k]'s range is
+ * divided into nbins[k] equal bins; counts[b] >= 0 is the content of bin b, row-major
+ * over the observables (the last one fastest), prod(nbins) entries; errors is NULL or
+ * the uncertainty sigma_b > 0 of each bin (used by GF_METRIC_CHISQ; NULL: sigma_b^2 =
+ * max(counts[b], 1)).  The bin centres become the data set's events; bin b's expected
+ * content is nu_b = N V P(x_b) with N = sum_b counts[b] and V the bin volume.  Arrays are
+ * copied.  Errors: GF_EINVAL for a bad id, nbins < 1, more than 2^31 bins, a negative or
+ * non-finite count, or a non-positive error; gf_dataset_add_events on it fails. */
+int gf_dataset_create_binned(gf_ctx* ctx, int nobs, const int* obs, const int* nbins,
+                             const double* counts, const double* errors, gf_dataset** ds);
+
+/* The fit's metric (Sec. 2: FitManager's metric, summed over events or bins):
+ *  GF_METRIC_NLL         -sum_i w_i log P(x_i); w_i = 1 for unbinned data, the bin
+ *                        content for binned data (multinomial likelihood).  Default.
+ *  GF_METRIC_BINNED_NLL  sum_b (nu_b - n_b log nu_b): Poisson likelihood of the bin
+ *                        contents (the constant sum log n_b! is left out).  Binned only.
+ *  GF_METRIC_CHISQ       sum_b (n_b - nu_b)^2 / sigma_b^2.  Binned only.
+ * gf_nll, gf_nll_grad and gf_fit then return / minimise this quantity; the error
+ * definition of gf_fit defaults to 1 for GF_METRIC_CHISQ and 0.5 otherwise.  Takes effect
+ * at the next evaluation; a binned metric without binned data gives GF_EINVAL there. */
+#define GF_METRIC_NLL 0
+#define GF_METRIC_BINNED_NLL 1
+#define GF_METRIC_CHISQ 2
+int gf_set_metric(gf_ctx* ctx, int metric);
+
 /* Compile the tree rooted at `root`, copy the dataset's columns to device memory
  * (structure of arrays, 256-byte aligned, padded), and invalidate the normalisation
  * caches.  The dataset stays owned by the caller. */
@@ -157,11 +183,13 @@ int gf_set_data_device(gf_ctx* ctx, int root, int nobs, const int* obs, int64_t 
  * observable ranges (Dalitz: the kinematic region) and the next evaluation returns
  * GF_EINVAL if any is outside.  The per-event caches are rebuilt at that evaluation. */
 int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols);
+/* (Binned data sets are replaced with gf_set_data; gf_update_data rejects them.) */
 
 /* ---- evaluation (Sec. 2: evaluate and metric, summed over events) ------------------ */
-/* NLL(theta) = -sum_i log P(x_i; theta) with P normalised, at theta = the free
- * parameters in gf_free_params order (external units).  Blocking: returns when the
- * value is on the host.  Non-finite result: *nll = +inf, GF_ENONFINITE. */
+/* NLL(theta) = -sum_i log P(x_i; theta) with P normalised (or the context's binned
+ * metric, gf_set_metric), at theta = the free parameters in gf_free_params order
+ * (external units).  Blocking: returns when the value is on the host.  Non-finite
+ * result: *nll = +inf, GF_ENONFINITE. */
 int gf_nll(gf_ctx* ctx, const double* theta, double* nll);
 /* NLL and its gradient over theta from the same event pass. */
 int gf_nll_grad(gf_ctx* ctx, const double* theta, double* nll, double* grad);
@@ -179,7 +207,7 @@ typedef struct {
   double tol;      /* EDM tolerance (default 1e-6 when <= 0) */
   int max_calls;   /* evaluation budget (default 5000 when <= 0) */
   int use_grad;    /* 1: fused analytic gradient; 0: central differences of gf_nll */
-  double up;       /* error definition (0.5 for a negative log-likelihood; <= 0 -> 0.5) */
+  double up;       /* error definition; <= 0: 1 for GF_METRIC_CHISQ, else 0.5 */
   int hesse;       /* 1: covariance from the Hessian by differences of the gradient */
   int refine;      /* GF_MIXED contexts: 1 (default when opts is NULL) runs BFGS on the FP32
                       likelihood to EDM < max(tol, 1) (or until its rounding noise stops

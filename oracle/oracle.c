@@ -452,8 +452,11 @@ int orc_nll(const orc_model* m, const double* p, int np, int64_t n, const double
 /*                                                     the constant log n_b!)       */
 /*   metric 2:   sum_b (n_b - nu_b)^2 / s2_b          (chi-squared, s2_b the        */
 /*                                                     variance of bin b)           */
-/* Gradient: d/dtheta = sum_b c_b dlogP_b/dtheta with c_b = -n_b, nu_b - n_b and    */
-/* -2 (n_b - nu_b) nu_b / s2_b respectively.                                        */
+/* Gradient: d/dtheta = sum_b (d term_b / d P_b) dP_b/dtheta with d term/d P =      */
+/* -n_b/P_b, K - n_b/P_b and -2 (n_b - nu_b) K / s2_b respectively (a bin with       */
+/* n_b = 0 contributes nothing to metric 0 and K dP_b/dtheta to metric 1; at P_b = 0 */
+/* the chi-squared term still moves with nu_b, so the chain goes through P, not      */
+/* log P).                                                                          */
 /* ------------------------------------------------------------------------------ */
 int orc_binned(const orc_model* m, const double* p, int np, int64_t nb, const double* const* cols,
                const double* cnt, const double* s2, double K, int metric, double* val,
@@ -468,24 +471,25 @@ int orc_binned(const orc_model* m, const double* p, int np, int64_t nb, const do
   double x[16];
   for (int64_t b = 0; b < nb; ++b) {
     for (int o = 0; o < m->nobs; ++o) x[o] = cols[o][b];
-    double lp = node_logvalue(m, m->root, p, np, N, dN, x, grad ? g : NULL);
+    double v = node_value(m, m->root, p, np, N, dN, x, grad ? g : NULL); /* P_b, dP_b */
+    double lp = log(v);
     double n = cnt[b], term, c;
     if (metric == 0) {
       term = n == 0 ? 0.0 : -n * lp;
-      c = -n;
+      c = n == 0 ? 0.0 : -n / v;
     } else {
-      double nu = K * exp(lp);
+      double nu = K * v;
       if (metric == 1) {
         term = n == 0 ? nu : nu - n * (lp + log(K));
-        c = nu - n;
+        c = n == 0 ? K : K - n / v;
       } else {
         double r = n - nu;
         term = r * r / s2[b];
-        c = -2.0 * r * nu / s2[b];
+        c = -2.0 * r * K / s2[b];
       }
     }
     acc_add(&s, term);
-    if (grad) for (int k = 0; k < np; ++k) acc_add(&gs[k], c * g[k]);
+    if (grad && c != 0.0) for (int k = 0; k < np; ++k) acc_add(&gs[k], c * g[k]);
   }
   *val = acc_get(&s);
   if (grad) for (int k = 0; k < np; ++k) grad[k] = acc_get(&gs[k]);

@@ -137,6 +137,8 @@ static void free_dev(gf_ctx* ctx) {
   cudaFree(d.tick_desc);
   cudaFree(d.prog);
   cudaFree(d.perm);
+  cudaFree(d.bw);
+  cudaFree(d.bs2);
   for (auto& g : d.graph)
     if (g) cudaGraphExecDestroy(g);
   d = DevState();
@@ -667,6 +669,10 @@ int ensure_compiled(gf_ctx* ctx) {
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
+  // the serving descriptor holds a copy of the program
+  cudaFree(ctx->dev.tick_desc);
+  ctx->dev.tick_desc = nullptr;
+  ctx->dev.tick_kind = 0;
   if (ctx->root < 0 || !valid_node(ctx, ctx->root))
     return set_error(ctx, GF_ESTATE, "no data set: call gf_set_data first");
   ctx->free_ids.clear();
@@ -684,6 +690,8 @@ int ensure_compiled(gf_ctx* ctx) {
   std::vector<int> col_of_obs(ctx->obs.size(), -1);
   for (int k = 0; k < (int)d.obs_ids.size(); ++k) col_of_obs[d.obs_ids[k]] = k;
   if (root.type == N_DALITZ) {
+    if (d.binned || ctx->metric != GF_METRIC_NLL)
+      return set_error(ctx, GF_EINVAL, "binned data and binned metrics are for 1D trees");
     ctx->is_dalitz = true;
     DalitzPlan& D = ctx->dplan;
     D = DalitzPlan{};
@@ -749,7 +757,15 @@ int ensure_compiled(gf_ctx* ctx) {
     P.sorted = (d.sorted && P.tay_slot >= 0 && d.sort_obs == P.tay_obs) ? 1 : 0;
     if (ctx->mixture_path) detect_mixture(P);
     else P.mix = 0;
-    if (ctx->mixture_path) detect_logsum(P);
+    if (ctx->metric != GF_METRIC_NLL && !d.binned)
+      return set_error(ctx, GF_EINVAL, "a binned metric needs a binned data set");
+    P.binned = d.binned ? 1 : 0;
+    P.metric = ctx->metric;
+    P.kbin = d.kbin;
+    P.logk = d.kbin > 0 ? std::log(d.kbin) : 0.0;
+    P.bw = d.bw;
+    P.bs2 = d.bs2;
+    if (ctx->mixture_path && !d.binned) detect_logsum(P);
     // the kernels read the program from device memory (it is too large for parameters);
     // stream-ordered copy, then wait: the next launch may go to another stream
     DevState& dv = ctx->dev;
@@ -783,9 +799,65 @@ int gf_dataset_create(gf_ctx* ctx, int nobs, const int* obs, gf_dataset** ds) {
   return GF_OK;
 }
 
+int gf_dataset_create_binned(gf_ctx* ctx, int nobs, const int* obs, const int* nbins,
+                             const double* counts, const double* errors, gf_dataset** ds) {
+  if (!ctx || !ds || !nbins || !counts) return GF_EINVAL;
+  *ds = nullptr;
+  if (nobs > kMaxObs) return set_error(ctx, GF_EINVAL, "too many observables");
+  int64_t nb = 1;
+  for (int k = 0; k < nobs; ++k) {
+    if (nbins[k] < 1) return set_error(ctx, GF_EINVAL, "nbins must be >= 1");
+    nb *= nbins[k];
+    if (nb > INT32_MAX) return set_error(ctx, GF_EINVAL, "more than 2^31 bins");
+  }
+  gf_dataset* d = nullptr;
+  int rc = gf_dataset_create(ctx, nobs, obs, &d);
+  if (rc) return rc;
+  double total = 0.0, vol = 1.0;
+  for (int64_t b = 0; b < nb; ++b) {
+    if (!(counts[b] >= 0.0) || !std::isfinite(counts[b])) {
+      delete d;
+      return set_error(ctx, GF_EINVAL, "bin " + std::to_string(b) + ": negative or non-finite count");
+    }
+    if (errors && !(errors[b] > 0.0 && std::isfinite(errors[b]))) {
+      delete d;
+      return set_error(ctx, GF_EINVAL, "bin " + std::to_string(b) + ": error must be > 0");
+    }
+    total += counts[b];
+  }
+  try {
+    for (int k = 0; k < nobs; ++k) {
+      const ObsDef& o = ctx->obs[obs[k]];
+      vol *= (o.hi - o.lo) / nbins[k];
+      d->cols[k].resize(nb);
+    }
+    d->w.assign(counts, counts + nb);
+    d->s2.resize(nb);
+    for (int64_t b = 0; b < nb; ++b) {
+      d->s2[b] = errors ? errors[b] * errors[b] : std::max(counts[b], 1.0);
+      int64_t r = b;
+      for (int k = nobs - 1; k >= 0; --k) {  // last observable fastest
+        const ObsDef& o = ctx->obs[obs[k]];
+        const int64_t i = r % nbins[k];
+        r /= nbins[k];
+        d->cols[k][b] = o.lo + (o.hi - o.lo) * ((double)i + 0.5) / nbins[k];
+      }
+    }
+  } catch (...) {
+    delete d;
+    return set_error(ctx, GF_ENOMEM, "host allocation failed");
+  }
+  d->n = nb;
+  d->binned = true;
+  d->kbin = total * vol;
+  *ds = d;
+  return GF_OK;
+}
+
 int gf_dataset_add_events(gf_dataset* ds, int64_t n, const double* const* cols) {
   if (!ds || n < 0 || (n > 0 && !cols)) return GF_EINVAL;
   gf_ctx* ctx = ds->ctx;
+  if (ds->binned) return set_error(ctx, GF_EINVAL, "a binned data set takes no events");
   for (size_t k = 0; k < ds->obs.size(); ++k) {
     if (n > 0 && !cols[k]) return set_error(ctx, GF_EINVAL, "NULL column");
     const ObsDef& o = ctx->obs[ds->obs[k]];
@@ -833,7 +905,7 @@ size_t device_bytes_for(const gf_ctx* ctx, int root, int64_t n) {
     b += (size_t)ncached * n * (ctx->precision == GF_MIXED ? 8 : 16);
     if (ctx->precision == GF_MIXED) b += 3 * (size_t)n * 4;
   } else {
-    b += col * 2;  // observables (typically 1-2)
+    b += col * 4;  // observables (typically 1-2), or centres + contents + variances
   }
   return b + (4u << 20);  // work buffers
 }
@@ -943,7 +1015,7 @@ static int finish_set_data(gf_ctx* ctx) {
 // per thread of the event launch.
 static bool sort_eligible(const gf_ctx* ctx) {
   const DevState& d = ctx->dev;
-  return ctx->event_sort && ctx->compiled && !ctx->is_dalitz && d.owns_cols &&
+  return ctx->event_sort && ctx->compiled && !ctx->is_dalitz && d.owns_cols && !d.binned &&
          ctx->prog.tay_slot >= 0 && d.n < INT32_MAX &&
          d.n >= (int64_t)(kChunk / 2) * d.nblocks * kThreads1D;
 }
@@ -1053,6 +1125,22 @@ extern "C" int gf_set_data(gf_ctx* ctx, int root, const gf_dataset* ds) {
     CK(cudaMemsetAsync(p, 0, bytes, ctx->stream));
     if (ds->n > 0)
       CK(cudaMemcpyAsync(p, ds->cols[k].data(), 8 * ds->n, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  if (ds->binned) {
+    d.binned = true;
+    d.kbin = ds->kbin;
+    for (double** dst : {&d.bw, &d.bs2}) {
+      if (cudaMalloc(dst, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        free_dev(ctx);
+        return set_error(ctx, GF_ENOMEM, "device allocation of the bin contents failed");
+      }
+      CK(cudaMemsetAsync(*dst, 0, bytes, ctx->stream));
+    }
+    if (ds->n > 0) {
+      CK(cudaMemcpyAsync(d.bw, ds->w.data(), 8 * ds->n, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(d.bs2, ds->s2.data(), 8 * ds->n, cudaMemcpyHostToDevice, ctx->stream));
+    }
   }
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->root = root;
@@ -1617,6 +1705,7 @@ int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
   DevState& d = ctx->dev;
   if (!d.owns_cols || !d.theta) return set_error(ctx, GF_ESTATE, "no data set owned by the context");
   if (n != d.n) return set_error(ctx, GF_EINVAL, "gf_update_data: n must equal the loaded size");
+  if (d.binned) return set_error(ctx, GF_EINVAL, "gf_update_data: binned data go through gf_set_data");
   int rc = ensure_compiled(ctx);
   if (rc) return rc;
   CK(cudaSetDevice(ctx->device));
@@ -1643,6 +1732,17 @@ int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
       hi[k] = ctx->obs[d.obs_ids[k]].hi;
     }
     CK(launch_check_range(c, d.nobs, n, lo, hi, d.flag, ctx->stream));
+  }
+  return GF_OK;
+}
+
+int gf_set_metric(gf_ctx* ctx, int metric) {
+  if (!ctx) return GF_EINVAL;
+  if (metric != GF_METRIC_NLL && metric != GF_METRIC_BINNED_NLL && metric != GF_METRIC_CHISQ)
+    return set_error(ctx, GF_EINVAL, "unknown metric");
+  if (ctx->metric != metric) {
+    ctx->metric = metric;
+    ctx->compiled = false;  // recompiled (and graphs re-captured) at the next call
   }
   return GF_OK;
 }

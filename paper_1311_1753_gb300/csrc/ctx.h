@@ -80,6 +80,11 @@ struct DevState {
   int sort_obs = -1;                  // the column the events are sorted by
   int32_t* perm = nullptr;            // sorted position -> original event index
   int evals_since_load = 0;           // evaluations since the columns were (re)loaded
+  // binned data: bin contents and chi-squared variances (device), N x bin volume
+  bool binned = false;
+  double* bw = nullptr;
+  double* bs2 = nullptr;
+  double kbin = 0.0;
 };
 
 }  // namespace gfi
@@ -89,6 +94,11 @@ struct gf_dataset {
   std::vector<int> obs;
   std::vector<std::vector<double>> cols;
   int64_t n = 0;
+  // binned data set: cols hold the bin centres, w the contents, s2 the variances of the
+  // chi-squared metric, kbin = (sum of contents) x (bin volume)
+  bool binned = false;
+  std::vector<double> w, s2;
+  double kbin = 0.0;
 };
 
 struct gf_ctx {
@@ -118,6 +128,7 @@ struct gf_ctx {
   bool graphs = true;       // replay captured graphs of steady evaluations
   bool event_sort = true;   // keep owned 1D columns sorted for the chunked event loop
   bool mixture_path = true; // evaluate AddPdf-of-leaves programs without the stack machine
+  int metric = GF_METRIC_NLL; // the fit's metric over events or bins (gf_set_metric)
 };
 
 namespace gfi {

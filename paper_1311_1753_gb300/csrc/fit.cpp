@@ -372,6 +372,7 @@ extern "C" int gf_fit(gf_ctx* ctx, const gf_fit_opts* opts, gf_fit_result* res) 
   int rc = ensure_compiled(ctx);
   if (rc) return rc;
   MinOpts mo;
+  mo.up = ctx->metric == GF_METRIC_CHISQ ? 1.0 : 0.5;  // chi-squared: Delta chi2 = 1
   bool use_grad = true;
   if (opts) {
     if (opts->tol > 0) mo.tol = opts->tol;

@@ -77,6 +77,12 @@ struct Program {
   // K - 1 x [LEAF, LMUL], K <= kLogLeaf, at most 2 observables): log P = sum_k l_k is
   // evaluated directly, without the stack machine.  1: this form, 0: not.
   int32_t logsum;
+  // binned data (the events are bin centres): the metric over bins and its inputs.
+  // binned = 0: unbinned events, metric -sum log P.
+  int32_t binned, metric;  // metric: GF_METRIC_NLL / _BINNED_NLL / _CHISQ (gf.h)
+  double kbin, logk;       // N x bin volume and its log: nu_b = kbin P(x_b)
+  const double* bw;        // bin contents (device)
+  const double* bs2;       // chi-squared variances (device)
   Instr ins[kMaxIns];
   LeafDesc leaf[kMaxLeaf];
   CoefDesc coef[kMaxCoef];

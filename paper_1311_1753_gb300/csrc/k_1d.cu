@@ -638,8 +638,59 @@ __device__ __forceinline__ void mixture_grad(const Program& P, const F2* rf, con
   }
 }
 
+// ---- binned metrics ------------------------------------------------------------------------
+// One bin (Sec. 2: the metric applied to the PDF's value at the bin centre): contents n,
+// expected nu = K P.  term: the bin's share of the metric; dP: the factor of the
+// gradient's dP/dtheta (linear root) or, for a log-domain root, of dlogP/dtheta (dlog).
+//   NLL (multinomial)  -n log P             dP = -n / P          dlog = -n
+//   BINNED_NLL         nu - n log nu        dP = K - n / P       dlog = nu - n
+//   CHISQ              (n - nu)^2 / s2      dP = -2 (n - nu) K/s2  dlog = -2 (n - nu) nu/s2
+// In pairs, for P in the float range (P > 0).
+__device__ __forceinline__ void bin_metric_f2(const Program& P, int64_t i, F2 lp, F2 pv, F2 kb,
+                                              F2 lk, F2& term, F2& fac) {
+  const double nd = P.bw[i];
+  const F2 n = df_split(nd);
+  const bool lin = !P.root_log;
+  if (P.metric == 0) {
+    term = nd == 0.0 ? F2{0.f, 0.f} : df_neg(df_mul(n, lp));
+    fac = lin ? (nd == 0.0 ? F2{0.f, 0.f} : df_neg(df_mul(n, df_rcp(pv)))) : df_neg(n);
+    return;
+  }
+  const F2 nu = df_mul(kb, pv);
+  if (P.metric == 1) {
+    term = nd == 0.0 ? nu : df_sub(nu, df_mul(n, df_add(lp, lk)));
+    fac = lin ? (nd == 0.0 ? kb : df_sub(kb, df_mul(n, df_rcp(pv)))) : df_sub(nu, n);
+    return;
+  }
+  const F2 is2 = df_rcp(df_split(P.bs2[i]));
+  const F2 r = df_sub(n, nu);
+  term = df_mul(df_mul(r, r), is2);
+  fac = df_mul_f(df_mul(df_mul(r, lin ? kb : nu), is2), -2.f);
+}
+// The same in FP64 for the re-evaluated bins (P may be 0 or outside the float range).
+__device__ __forceinline__ void bin_metric_d(const Program& P, int64_t i, double lp, double pv,
+                                             double& term, double& fac) {
+  const double n = P.bw[i], K = P.kbin;
+  const bool lin = !P.root_log;
+  if (P.metric == 0) {
+    term = n == 0.0 ? 0.0 : -n * lp;
+    fac = n == 0.0 ? 0.0 : (lin ? -n / pv : -n);
+    return;
+  }
+  const double nu = K * pv;
+  if (P.metric == 1) {
+    term = n == 0.0 ? nu : nu - n * (lp + P.logk);
+    fac = lin ? (n == 0.0 ? K : K - n / pv) : nu - n;
+    return;
+  }
+  const double r = n - nu;
+  term = r * r / P.bs2[i];
+  fac = -2.0 * r * (lin ? K : nu) / P.bs2[i];
+}
+
 // ---- event stream ------------------------------------------------------------------------
-// MODE 0: reduce -log P (and gradient) to result[0 .. nfree]; MODE 1: store log P_i.
+// MODE 0: reduce -log P (and gradient) to result[0 .. nfree]; MODE 1: store log P_i;
+// MODE 2: reduce the binned metric (the events are bin centres; Program.binned).
 // Body of one (virtual) block vb of the vgrid blocks of an event launch.  Shared
 // scratch: dyn (G: (kMaxStack + 1) nfree blockDim pairs/doubles), rec (leaf records in
 // FP64), rf (the same as pairs), red[(blockDim / 32) (1 + kMaxFree1D)], *last.
@@ -673,8 +724,11 @@ __device__ __forceinline__ void events_1d_block(
     for (int k = 0; k < nf; ++k) gacc[k * bd] = F2{0.f, 0.f};
   F2 acc = {0.f, 0.f};
 
-  // one event: log P_i into the sums (MODE 0) or out_logp (MODE 1, through perm if sorted)
+  // one event: log P_i into the sums (MODE 0, 2) or out_logp (MODE 1, through perm if
+  // sorted)
   const bool mix = P.mix > 0;
+  const F2 kb = MODE == 2 ? df_split(P.kbin) : F2{0.f, 0.f};
+  const F2 lk = MODE == 2 ? df_split(P.logk) : F2{0.f, 0.f};
   auto one_event = [&](int64_t i, const double* x, const Tay* tay) {
     const F2 s = mix ? run_mixture<G>(P, rec, rf, x, W, dynf + tid, bd, tay)
                      : run_program<ArF2, G>(P, rec, rf, x, W, dynf, nf, bd, tid, tay);
@@ -687,9 +741,17 @@ __device__ __forceinline__ void events_1d_block(
       if (MODE == 1) {
         out_logp[perm ? perm[i] : i] = df_to(lp);
       } else {
-        acc = df_sub(acc, lp);
+        F2 fac = {0.f, 0.f};
+        if (MODE == 2) {
+          F2 term;
+          const F2 pv = P.root_log ? df_exp_tab(lp, s_exp_tab) : s;
+          bin_metric_f2(P, i, lp, pv, kb, lk, term, fac);
+          acc = df_add(acc, term);
+        } else {
+          acc = df_sub(acc, lp);
+        }
         if (G) {
-          const F2 sc = P.root_log ? F2{-1.f, 0.f} : df_neg(df_rcp(s));
+          const F2 sc = MODE == 2 ? fac : P.root_log ? F2{-1.f, 0.f} : df_neg(df_rcp(s));
           if (mix) {
             mixture_grad(P, rf, dynf + tid, sc, gacc, bd);
           } else {
@@ -706,9 +768,16 @@ __device__ __forceinline__ void events_1d_block(
       if (MODE == 1) {
         out_logp[perm ? perm[i] : i] = lp;
       } else {
-        acc = df_sub(acc, df_from(lp));
-        if (G) {
-          const double sc = P.root_log ? -1.0 : -1.0 / sd;
+        double fac = 0.0;
+        if (MODE == 2) {
+          double term;
+          bin_metric_d(P, i, lp, P.root_log ? df_exp(sd) : sd, term, fac);
+          acc = df_add(acc, df_from(term));
+        } else {
+          acc = df_sub(acc, df_from(lp));
+        }
+        if (G && (MODE != 2 || fac != 0.0)) {
+          const double sc = MODE == 2 ? fac : P.root_log ? -1.0 : -1.0 / sd;
           const double* g0 = dyn + tid;
           for (int k = 0; k < nf; ++k)
             gacc[k * bd] = df_add(gacc[k * bd], df_from(g0[k * bd] * sc));
@@ -1081,9 +1150,14 @@ __global__ void __launch_bounds__(kThreads1D) k_tick_events_1d(const TickItem* _
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const TickItem& ti = tick_item(items, nfits, it, cur, Ps);
     const Fit1D* F = static_cast<const Fit1D*>(ti.fit);
-    events_1d_block<true, 0>(Ps, W, F->cols, F->n, ti.theta, F->derived, F->partials,
-                             F->counter_ev, ti.result, nullptr, nullptr, F->analytic_only,
-                             it - ti.item0, ti.nitems, dyn, rec, rf, red, &last, nullptr);
+    if (Ps.binned)
+      events_1d_block<true, 2>(Ps, W, F->cols, F->n, ti.theta, F->derived, F->partials,
+                               F->counter_ev, ti.result, nullptr, nullptr, F->analytic_only,
+                               it - ti.item0, ti.nitems, dyn, rec, rf, red, &last, nullptr);
+    else
+      events_1d_block<true, 0>(Ps, W, F->cols, F->n, ti.theta, F->derived, F->partials,
+                               F->counter_ev, ti.result, nullptr, nullptr, F->analytic_only,
+                               it - ti.item0, ti.nitems, dyn, rec, rf, red, &last, nullptr);
     __syncthreads();
   }
 }
@@ -1152,7 +1226,17 @@ cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCo
                              int nblocks, cudaStream_t st) {
   const int threads = kThreads1D;
   const size_t smem = events_1d_smem(P, grad, threads);
-  if (P.logsum && !store) {
+  if (P.binned && !store) {
+    if (grad) {
+      k_events_1d<true, 2><<<nblocks, threads, smem, st>>>(prog, W, cols, n, theta, derived,
+                                                           partials, counter, result, out_logp,
+                                                           nullptr, analytic_only);
+    } else {
+      k_events_1d<false, 2><<<nblocks, threads, 0, st>>>(prog, W, cols, n, theta, derived,
+                                                         partials, counter, result, out_logp,
+                                                         nullptr, analytic_only);
+    }
+  } else if (P.logsum && !store) {
     const size_t gs = grad ? sizeof(F2) * P.nfree * threads : 0;
     auto k = grad ? logsum_kernel<true>(P) : logsum_kernel<false>(P);
     k<<<nblocks, threads, gs, st>>>(prog, cols, n, theta, partials, counter, result);
@@ -1177,6 +1261,8 @@ cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCo
 void prepare_kernels_1d() {
   upload_df_tables();
   cudaFuncSetAttribute(k_events_1d<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       200 * 1024);
+  cudaFuncSetAttribute(k_events_1d<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
   cudaFuncSetAttribute(k_tick_events_1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);

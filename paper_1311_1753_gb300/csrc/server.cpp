@@ -97,6 +97,7 @@ static void fit_thread(gf_server* S, std::shared_ptr<Req> R) {
     hi[k] = p.hi;
   }
   MinOpts mo;
+  mo.up = R->ctx->metric == GF_METRIC_CHISQ ? 1.0 : 0.5;  // chi-squared: Delta chi2 = 1
   if (R->has_opts) {
     if (R->opts.tol > 0) mo.tol = R->opts.tol;
     if (R->opts.max_calls > 0) mo.max_calls = R->opts.max_calls;

@@ -17,6 +17,7 @@ from . import _build
 GF_OK, GF_EINVAL, GF_ENOMEM, GF_ECUDA, GF_ENONFINITE, GF_ENOCONV, GF_ETIMEOUT, GF_ESTATE = (
     0, -1, -2, -3, -4, -5, -6, -7)
 GF_FP64, GF_MIXED = 0, 1
+GF_METRIC_NLL, GF_METRIC_BINNED_NLL, GF_METRIC_CHISQ = 0, 1, 2
 
 _D = C.POINTER(C.c_double)
 _I = C.POINTER(C.c_int)
@@ -80,6 +81,8 @@ def _load():
         "gf_dalitz_inside": ([vp, C.c_int, C.c_int64, _D, _D, C.POINTER(C.c_int8)], C.c_int),
         "gf_dataset_create": ([vp, C.c_int, _I, C.POINTER(vp)], C.c_int),
         "gf_dataset_add_events": ([vp, C.c_int64, C.POINTER(_D)], C.c_int),
+        "gf_dataset_create_binned": ([vp, C.c_int, _I, _I, _D, _D, C.POINTER(vp)], C.c_int),
+        "gf_set_metric": ([vp, C.c_int], C.c_int),
         "gf_dataset_size": ([vp], C.c_int64),
         "gf_dataset_destroy": ([vp], C.c_int),
         "gf_set_data": ([vp, C.c_int, vp], C.c_int),
@@ -270,6 +273,31 @@ class Context:
             self._ck(rc, "gf_dataset_add_events")
         return ds
 
+    def make_binned_dataset(self, obs, nbins, counts, errors=None):
+        """A host binned gf_dataset: equal bins over each observable's range, contents
+        row-major (last observable fastest), optional per-bin errors."""
+        ds = C.c_void_p()
+        ids = (C.c_int * len(obs))(*obs)
+        nb = (C.c_int * len(obs))(*[int(b) for b in nbins])
+        cnt = _f64(np.ravel(counts))
+        err = _f64(np.ravel(errors)) if errors is not None else None
+        self._ck(lib.gf_dataset_create_binned(self.h, len(obs), ids, nb, _dp(cnt),
+                                              _dp(err) if err is not None else None,
+                                              C.byref(ds)), "gf_dataset_create_binned")
+        return ds
+
+    def set_binned_data(self, root, obs, nbins, counts, errors=None):
+        """Load a binned data set (bin centres as events, contents as weights)."""
+        ds = self.make_binned_dataset(obs, nbins, counts, errors)
+        try:
+            self._ck(lib.gf_set_data(self.h, root, ds), "gf_set_data")
+        finally:
+            lib.gf_dataset_destroy(ds)
+        self.n = int(np.prod(nbins))
+
+    def set_metric(self, metric):
+        self._ck(lib.gf_set_metric(self.h, int(metric)), "gf_set_metric")
+
     def set_data_device(self, root, obs, n, dev_ptrs, keep=None):
         """Use device columns in place (e.g. torch tensors' data_ptr()); ``keep`` holds
         the owning objects alive for the lifetime of this context."""
@@ -367,7 +395,8 @@ class Context:
         lib.gf_last_eval_stats(self.h, C.byref(ms), C.byref(nl))
         return ms.value, nl.value
 
-    def fit(self, tol=1e-6, max_calls=5000, use_grad=True, up=0.5, hesse=True, refine=True):
+    def fit(self, tol=1e-6, max_calls=5000, use_grad=True, up=0.0, hesse=True, refine=True):
+        """up <= 0: the library's default for the metric (1 for chi-squared, else 0.5)."""
         nf = len(self.free_params())
         th = np.zeros(max(1, nf))
         err = np.zeros(max(1, nf))
@@ -396,7 +425,7 @@ class Server:
 
     def submit(self, ctx: Context, ds, root, tol=1e-6, max_calls=5000, hesse=True, refine=True):
         t = C.c_uint64()
-        o = FitOpts(tol, max_calls, 1, 0.5, 1 if hesse else 0, 1 if refine else 0)
+        o = FitOpts(tol, max_calls, 1, 0.0, 1 if hesse else 0, 1 if refine else 0)
         rc = lib.gf_server_submit(self.h, ctx.h, ds, root, C.byref(o), C.byref(t))
         if rc:
             raise GFError(rc, "gf_server_submit")
