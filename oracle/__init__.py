@@ -27,7 +27,7 @@ _lock = threading.Lock()
 _lib = None
 
 # Leaf and combinator codes, as in oracle.c.
-EXP, GAUSS, VOIGT, THRESH, POLY, ADD, PROD = 1, 2, 3, 4, 5, 10, 11
+EXP, GAUSS, VOIGT, THRESH, POLY, RELBW, ADD, PROD, CONV = 1, 2, 3, 4, 5, 6, 10, 11, 12
 MAXPAR, MAXCHILD = 16, 8
 
 
@@ -44,13 +44,14 @@ def build(force: bool = False) -> str:
 
 class OrcNode(C.Structure):
     _fields_ = [("type", C.c_int32), ("obs", C.c_int32), ("npar", C.c_int32),
-                ("par", C.c_int32 * MAXPAR), ("nchild", C.c_int32), ("child", C.c_int32 * MAXCHILD)]
+                ("par", C.c_int32 * MAXPAR), ("nchild", C.c_int32), ("child", C.c_int32 * MAXCHILD),
+                ("aux", C.c_int32)]
 
 
 class OrcModel(C.Structure):
     _fields_ = [("nnodes", C.c_int32), ("root", C.c_int32), ("nodes", C.POINTER(OrcNode)),
                 ("nobs", C.c_int32), ("lo", C.POINTER(C.c_double)), ("hi", C.POINTER(C.c_double)),
-                ("nbins", C.c_int32)]
+                ("nbins", C.c_int32), ("ndata", C.c_int32)]
 
 
 class OrcDkin(C.Structure):
@@ -132,6 +133,7 @@ class Model1D:
         self.lo = _f64([r[0] for r in obs_ranges])
         self.hi = _f64([r[1] for r in obs_ranges])
         self.nbins = int(nbins)
+        self._ndata = len(self.lo)
         self.values: list[float] = []
         self.nodes: list[OrcNode] = []
         self.root = -1
@@ -146,9 +148,9 @@ class Model1D:
         return _f64(self.values)
 
     # nodes ---------------------------------------------------------------------
-    def _node(self, typ, obs=0, pars=(), children=()) -> int:
+    def _node(self, typ, obs=0, pars=(), children=(), aux=0) -> int:
         nd = OrcNode()
-        nd.type, nd.obs, nd.npar, nd.nchild = typ, obs, len(pars), len(children)
+        nd.type, nd.obs, nd.npar, nd.nchild, nd.aux = typ, obs, len(pars), len(children), aux
         assert len(pars) <= MAXPAR and len(children) <= MAXCHILD
         for i, q in enumerate(pars):
             nd.par[i] = q
@@ -173,6 +175,17 @@ class Model1D:
     def poly(self, obs, coefs):
         return self._node(POLY, obs, list(coefs))
 
+    def relbw(self, obs, dm0, gamma0, shift, ma, mb, radius, spin=1):
+        """Relativistic Breit-Wigner line shape in x = m - shift (Sec. 4's D*+ fit: a
+        P-wave resonance in the D*+ - D0 mass difference)."""
+        return self._node(RELBW, obs, [dm0, gamma0, shift, ma, mb, radius], aux=int(spin))
+
+    def conv(self, obs, model, resolution, lattice):
+        """ConvolutionPdf (Sec. 3): model (a node over obs) convolved with resolution (a
+        node over its own residual observable, declared after the data observables) on a
+        lattice of `lattice` bins of obs's range."""
+        return self._node(CONV, obs, [], [model, resolution], aux=int(lattice))
+
     def add(self, children, fracs):
         assert len(fracs) == len(children) - 1
         return self._node(ADD, 0, list(fracs), list(children))
@@ -184,14 +197,16 @@ class Model1D:
     def _model(self):
         arr = (OrcNode * len(self.nodes))(*self.nodes)
         m = OrcModel(len(self.nodes), self.root, arr, len(self.lo), _dp(self.lo), _dp(self.hi),
-                     self.nbins)
+                     self.nbins, self._ndata)
         return m, arr
 
     def _cols(self, cols):
         cols = [_f64(c) for c in cols]
-        if len(cols) != len(self.lo) or any(len(c) != len(cols[0]) for c in cols):
-            raise ValueError(f"the model has {len(self.lo)} observables: one column each, "
-                             "all of the same length")
+        nres = sum(1 for nd in self.nodes if nd.type == CONV)  # one residual observable each
+        if len(cols) != len(self.lo) - nres or any(len(c) != len(cols[0]) for c in cols):
+            raise ValueError(f"the model has {len(self.lo) - nres} data observables: one "
+                             "column each, all of the same length")
+        self._ndata = len(cols)
         ptrs = (_D * len(cols))(*[_dp(c) for c in cols])
         return cols, ptrs
 
@@ -206,8 +221,8 @@ class Model1D:
 
     def logpdf(self, cols, p=None) -> np.ndarray:
         p = self.p if p is None else _f64(p)
-        m, keep = self._model()
         cols, ptrs = self._cols(cols)
+        m, keep = self._model()
         out = np.empty(len(cols[0]))
         rc = lib().orc_logpdf(C.byref(m), _dp(p), len(p), len(out), ptrs, _dp(out))
         assert rc == 0
@@ -215,8 +230,8 @@ class Model1D:
 
     def nll(self, cols, p=None, grad: bool = False):
         p = self.p if p is None else _f64(p)
-        m, keep = self._model()
         cols, ptrs = self._cols(cols)
+        m, keep = self._model()
         out = np.zeros(1)
         g = np.zeros(len(p)) if grad else None
         rc = lib().orc_nll(C.byref(m), _dp(p), len(p), len(cols[0]), ptrs, _dp(out),
@@ -229,8 +244,8 @@ class Model1D:
         contents: 0 multinomial -sum n log P, 1 Poisson sum nu - n log nu, 2 chi-squared
         sum (n - nu)^2/s2, with nu = K P(centre)."""
         p = self.p if p is None else _f64(p)
-        m, keep = self._model()
         cols, ptrs = self._cols(centres)
+        m, keep = self._model()
         n = _f64(counts)
         assert len(n) == len(cols[0])
         v = _f64(s2) if s2 is not None else None

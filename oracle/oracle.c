@@ -125,8 +125,17 @@ enum {
   ORC_VOIGT = 3,  /* Re w(z)/(sigma sqrt(2 pi))          par: mu, sigma, Gamma           */
   ORC_THRESH = 4, /* (x-x0)^p e^{-c (x-x0)}, x > x0      par: x0, p, c                   */
   ORC_POLY = 5,   /* sum_k a_k x^k                       par: a_0 .. a_deg               */
+  ORC_RELBW = 6,  /* relativistic Breit-Wigner line shape (Sec. 4, the D*+ width fit):
+                   * m Gamma(m) / ((m0^2 - m^2)^2 + m0^2 Gamma(m)^2), m = x + shift,
+                   * m0 = dm0 + shift, Gamma(m) = Gamma0 (q/q0)^{2L+1} (m0/m) F_L^2,
+                   * zero at or below threshold m <= ma + mb;
+                   *                                     par: dm0, Gamma0, shift, ma, mb, R;
+                   *                                     aux: L (orbital angular momentum) */
   ORC_ADD = 10,   /* sum_k f_k P_k + (1 - sum f) P_last  par: f_0 .. f_{n-2}  (AddPdf)   */
-  ORC_PROD = 11   /* prod_k P_k (distinct observables)                        (ProdPdf)  */
+  ORC_PROD = 11,  /* prod_k P_k (distinct observables)                        (ProdPdf)  */
+  ORC_CONV = 12   /* ConvolutionPdf (Sec. 3): model (child 0, observable obs) convolved
+                   * with a resolution (child 1, over its own residual observable), on a
+                   * lattice of aux bins of obs's range; see conv_table              */
 };
 
 #define ORC_MAXPAR 16
@@ -138,6 +147,7 @@ typedef struct {
   int32_t par[ORC_MAXPAR];
   int32_t nchild;
   int32_t child[ORC_MAXCHILD];
+  int32_t aux; /* RELBW: L; CONV: lattice bins */
 } orc_node;
 
 typedef struct {
@@ -148,12 +158,68 @@ typedef struct {
   const double* lo;
   const double* hi;
   int32_t nbins; /* midpoint-rule bins for grid-normalised leaves */
+  int32_t ndata; /* data columns: observables 0 .. ndata-1 (the rest are residual
+                    observables of resolution functions) */
 } orc_model;
 
+/* Per-evaluation state: normalisation of every node and its gradient, and the lattice
+ * table of every convolution node ((1 + np) x (L + 1): C_i, then dC_i/dp_k). */
+typedef struct {
+  double* N;
+  double* dN;
+  double** tab;
+} orc_state;
+
+/* Relativistic Breit-Wigner line shape (ORC_RELBW).  With s = m^2 and the squared
+ * break-up momentum of a, b at s, q^2(s) = (s - (ma+mb)^2)(s - (ma-mb)^2)/(4 s),
+ * Blatt-Weisskopf B_L(z) = 1, 1 + z, 9 + 3z + z^2 (z = q^2 R^2), F_L^2 = B_L(z0)/B_L(z),
+ *   Gamma(m) = Gamma0 (q/q0)^{2L+1} (m0/m) F_L^2,   f = m Gamma / D,
+ *   D = (m0^2 - m^2)^2 + m0^2 Gamma^2.
+ * Derivatives (m0 enters through q0, z0, m0/m and D):
+ *   dGamma/dGamma0 = Gamma/Gamma0,
+ *   dln Gamma/dm0 = -(2L+1) dln q0/dm0 + 1/m0 + B_L'(z0)/B_L(z0) dz0/dm0,
+ *   dq0^2/dm0 = 2 m0 (s0^2 - A B)/(4 s0^2), A = (ma+mb)^2, B = (ma-mb)^2, s0 = m0^2,
+ *   df = m dGamma/D - f dD/D,  dD = 4 m0 (m0^2 - m^2) dm0 + 2 m0 Gamma^2 dm0
+ *                                   + 2 m0^2 Gamma dGamma. */
+static double rb_poly(int L, double z) { return L == 0 ? 1.0 : L == 1 ? 1.0 + z : 9.0 + 3.0 * z + z * z; }
+static double rb_poly_dz(int L, double z) { return L == 0 ? 0.0 : L == 1 ? 1.0 : 3.0 + 2.0 * z; }
+static double relbw_shape(const orc_node* nd, const double* p, double x, double* dr) {
+  double dm0 = p[nd->par[0]], g0 = p[nd->par[1]], shift = p[nd->par[2]];
+  double ma = p[nd->par[3]], mb = p[nd->par[4]], R = p[nd->par[5]];
+  int L = nd->aux;
+  double m = x + shift, m0 = dm0 + shift;
+  if (dr) for (int k = 0; k < 6; ++k) dr[k] = 0.0;
+  if (!(m > ma + mb)) return 0.0;
+  double A = (ma + mb) * (ma + mb), B = (ma - mb) * (ma - mb);
+  double s = m * m, s0 = m0 * m0;
+  double q2 = (s - A) * (s - B) / (4 * s), q02 = (s0 - A) * (s0 - B) / (4 * s0);
+  double z = q2 * R * R, z0 = q02 * R * R;
+  double F2 = rb_poly(L, z0) / rb_poly(L, z);
+  double G = g0 * pow(q2 / q02, L + 0.5) * (m0 / m) * F2;
+  double D = (s0 - s) * (s0 - s) + s0 * G * G;
+  double f = m * G / D;
+  if (dr) {
+    /* Gamma0 */
+    double dG = G / g0;
+    double dD = 2 * s0 * G * dG;
+    dr[1] = m * dG / D - f * dD / D;
+    /* dm0 */
+    double dq02 = 2 * m0 * (s0 * s0 - A * B) / (4 * s0 * s0);
+    double dlnG = -(L + 0.5) * dq02 / q02 + 1.0 / m0 + rb_poly_dz(L, z0) * R * R * dq02 / rb_poly(L, z0);
+    dG = G * dlnG;
+    dD = 4 * m0 * (s0 - s) + 2 * m0 * G * G + 2 * s0 * G * dG;
+    dr[0] = m * dG / D - f * dD / D;
+  }
+  return f;
+}
+
 /* Unnormalised leaf shape r(x) and its partial derivatives with respect to the
- * leaf's own parameters (dr[k] for par[k]). */
+ * leaf's own parameters (dr[k] for par[k]).  RELBW: derivatives for dm0 and Gamma0
+ * only (its other parameters are constants of the decay). */
 static double leaf_shape(const orc_node* nd, const double* p, double x, double* dr) {
   switch (nd->type) {
+    case ORC_RELBW:
+      return relbw_shape(nd, p, x, dr);
     case ORC_EXP: {
       double a = p[nd->par[0]];
       double v = exp(a * x);
@@ -216,8 +282,10 @@ static double leaf_shape(const orc_node* nd, const double* p, double x, double* 
   return NAN;
 }
 
-static int is_leaf(int type) { return type >= ORC_EXP && type <= ORC_POLY; }
-static int grid_normalised(int type) { return type == ORC_VOIGT || type == ORC_THRESH; }
+static int is_leaf(int type) { return type >= ORC_EXP && type <= ORC_RELBW; }
+static int grid_normalised(int type) {
+  return type == ORC_VOIGT || type == ORC_THRESH || type == ORC_RELBW;
+}
 
 /* Integral of e^{a x} on [lo, hi] and its a-derivative (Int x e^{a x}). */
 static void exp_integral(double a, double lo, double hi, double* N, double* dN) {
@@ -305,9 +373,11 @@ int orc_norms(const orc_model* m, const double* p, int np, double* N, double* dN
 }
 
 /* Normalised value of a node at one event, optionally with its gradient g[np]. */
-static double node_value(const orc_model* m, int i, const double* p, int np, const double* N,
-                         const double* dN, const double* x, double* g) {
+static double node_value(const orc_model* m, int i, const double* p, int np,
+                         const orc_state* st, const double* x, double* g) {
   const orc_node* nd = &m->nodes[i];
+  const double* N = st->N;
+  const double* dN = st->dN;
   if (is_leaf(nd->type)) {
     double dr[ORC_MAXPAR];
     double r = leaf_shape(nd, p, x[nd->obs], g ? dr : NULL);
@@ -319,18 +389,37 @@ static double node_value(const orc_model* m, int i, const double* p, int np, con
     }
     return v;
   }
+  if (nd->type == ORC_CONV) {
+    /* linear interpolation of the lattice table, divided by the node's normalisation */
+    const double* T = st->tab[i];
+    int L = nd->aux;
+    double lo = m->lo[nd->obs], hi = m->hi[nd->obs], h = (hi - lo) / L;
+    double sx = (x[nd->obs] - lo) / h;
+    int k = (int)floor(sx);
+    if (k < 0) k = 0;
+    if (k > L - 1) k = L - 1;
+    double u = sx - k;
+    double c = (1 - u) * T[k] + u * T[k + 1];
+    double v = c / N[i];
+    if (g)
+      for (int q = 0; q < np; ++q) {
+        const double* Tq = T + (size_t)(1 + q) * (L + 1);
+        g[q] = ((1 - u) * Tq[k] + u * Tq[k + 1]) / N[i] - v * dN[(size_t)i * np + q] / N[i];
+      }
+    return v;
+  }
   if (nd->type == ORC_ADD) {
     int nc = nd->nchild;
     double fsum = 0, v = 0, vlast;
     double* gc = g ? (double*)malloc(sizeof(double) * np) : NULL;
     if (g) memset(g, 0, sizeof(double) * np);
-    vlast = node_value(m, nd->child[nc - 1], p, np, N, dN, x, gc);
+    vlast = node_value(m, nd->child[nc - 1], p, np, st, x, gc);
     for (int k = 0; k < nc - 1; ++k) fsum += p[nd->par[k]];
     v = (1.0 - fsum) * vlast;
     if (g) for (int j = 0; j < np; ++j) g[j] += (1.0 - fsum) * gc[j];
     for (int k = 0; k < nc - 1; ++k) {
       double f = p[nd->par[k]];
-      double vk = node_value(m, nd->child[k], p, np, N, dN, x, gc);
+      double vk = node_value(m, nd->child[k], p, np, st, x, gc);
       v += f * vk;
       if (g) {
         for (int j = 0; j < np; ++j) g[j] += f * gc[j];
@@ -346,7 +435,7 @@ static double node_value(const orc_model* m, int i, const double* p, int np, con
     double* gcs = g ? (double*)malloc(sizeof(double) * np * nc) : NULL;
     double v = 1;
     for (int k = 0; k < nc; ++k) {
-      vals[k] = node_value(m, nd->child[k], p, np, N, dN, x, g ? gcs + (size_t)k * np : NULL);
+      vals[k] = node_value(m, nd->child[k], p, np, st, x, g ? gcs + (size_t)k * np : NULL);
       v *= vals[k];
     }
     if (g) {
@@ -366,9 +455,11 @@ static double node_value(const orc_model* m, int i, const double* p, int np, con
 /* log of the normalised value.  Exponential and Gaussian leaves and products are
  * taken in the log domain (log e^{a x}/N = a x - log N), which is the same quantity
  * without the round trip through exp. */
-static double node_logvalue(const orc_model* m, int i, const double* p, int np, const double* N,
-                            const double* dN, const double* x, double* g) {
+static double node_logvalue(const orc_model* m, int i, const double* p, int np,
+                            const orc_state* st, const double* x, double* g) {
   const orc_node* nd = &m->nodes[i];
+  const double* N = st->N;
+  const double* dN = st->dN;
   if (nd->type == ORC_EXP) {
     double a = p[nd->par[0]], xv = x[nd->obs];
     if (g) {
@@ -391,52 +482,143 @@ static double node_logvalue(const orc_model* m, int i, const double* p, int np, 
     double* gc = g ? (double*)malloc(sizeof(double) * np) : NULL;
     if (g) memset(g, 0, sizeof(double) * np);
     for (int k = 0; k < nd->nchild; ++k) {
-      v += node_logvalue(m, nd->child[k], p, np, N, dN, x, gc);
+      v += node_logvalue(m, nd->child[k], p, np, st, x, gc);
       if (g) for (int j = 0; j < np; ++j) g[j] += gc[j];
     }
     free(gc);
     return v;
   }
-  double v = node_value(m, i, p, np, N, dN, x, g);
+  double v = node_value(m, i, p, np, st, x, g);
   if (g) for (int j = 0; j < np; ++j) g[j] /= v;
   return log(v);
+}
+
+/* ------------------------------------------------------------------------------ */
+/* ConvolutionPdf (Sec. 3; Sec. 4: a Breit-Wigner convolved with a resolution of    */
+/* several Gaussians).  The paper names the class, not its numerics; the reading    */
+/* used here:                                                                      */
+/*  - lattice x_i = lo + i h, i = 0..L, h = (hi - lo)/L on the observable's range;  */
+/*  - resolution R (normalised on its residual observable's range [rlo, rhi]) at    */
+/*    the offsets u_k = k h inside that range, k = kmin..kmax;                     */
+/*  - model M (normalised on [lo, hi], evaluated wherever needed) at t = x_i - u_k;  */
+/*  - C_i = h sum_k R(u_k) M(x_i - u_k)   (Riemann sum of Int M(t) R(x - t) dt);     */
+/*  - C(x) linear between lattice points, P(x) = C(x)/N with N = Int_lo^hi C, the    */
+/*    trapezoid sum h (C_0/2 + C_1 + ... + C_{L-1} + C_L/2), exact for the           */
+/*    interpolant;                                                                 */
+/*  - gradients by differentiating every step.                                     */
+/* ------------------------------------------------------------------------------ */
+static int subtree_obs(const orc_model* m, int i) {
+  const orc_node* nd = &m->nodes[i];
+  if (is_leaf(nd->type)) return nd->obs;
+  return nd->nchild > 0 ? subtree_obs(m, nd->child[0]) : -1;
+}
+
+static int conv_table(const orc_model* m, int i, const double* p, int np, orc_state* st) {
+  const orc_node* nd = &m->nodes[i];
+  int L = nd->aux, M = nd->child[0], R = nd->child[1];
+  int ro = subtree_obs(m, R);
+  if (L < 1 || ro < 0 || ro == nd->obs) return -1;
+  double lo = m->lo[nd->obs], hi = m->hi[nd->obs], h = (hi - lo) / L;
+  int kmin = (int)ceil(m->lo[ro] / h - 1e-9), kmax = (int)floor(m->hi[ro] / h + 1e-9);
+  if (kmax < kmin) return -1;
+  int J = L + kmax - kmin + 1, K = kmax - kmin + 1;
+  double* mt = (double*)calloc((size_t)(1 + np) * J, sizeof(double));
+  double* rt = (double*)calloc((size_t)(1 + np) * K, sizeof(double));
+  double* T = (double*)calloc((size_t)(1 + np) * (L + 1), sizeof(double));
+  double* g = (double*)malloc(sizeof(double) * np);
+  double x[16] = {0};
+  for (int j = 0; j < J; ++j) {
+    x[nd->obs] = lo + (j - kmax) * h;
+    mt[j] = node_value(m, M, p, np, st, x, g);
+    for (int q = 0; q < np; ++q) mt[(size_t)(1 + q) * J + j] = g[q];
+  }
+  for (int k = 0; k < K; ++k) {
+    x[ro] = (kmin + k) * h;
+    rt[k] = node_value(m, R, p, np, st, x, g);
+    for (int q = 0; q < np; ++q) rt[(size_t)(1 + q) * K + k] = g[q];
+  }
+  orc_acc nsum = {0, 0};
+  orc_acc* dsum = (orc_acc*)calloc(np, sizeof(orc_acc));
+  for (int ii = 0; ii <= L; ++ii) {
+    double wt = (ii == 0 || ii == L) ? 0.5 : 1.0;
+    /* u_k = (kmin + k) h pairs with t = x_ii - u_k, model index j = ii - kmin - k + kmax */
+    orc_acc c = {0, 0};
+    for (int k = 0; k < K; ++k) acc_add(&c, rt[k] * mt[ii - kmin - k + kmax]);
+    T[ii] = h * acc_get(&c);
+    acc_add(&nsum, wt * T[ii]);
+    for (int q = 0; q < np; ++q) {
+      orc_acc d = {0, 0};
+      const double* mq = mt + (size_t)(1 + q) * J;
+      const double* rq = rt + (size_t)(1 + q) * K;
+      for (int k = 0; k < K; ++k) {
+        int j = ii - kmin - k + kmax;
+        acc_add(&d, rq[k] * mt[j]);
+        acc_add(&d, rt[k] * mq[j]);
+      }
+      T[(size_t)(1 + q) * (L + 1) + ii] = h * acc_get(&d);
+      acc_add(&dsum[q], wt * T[(size_t)(1 + q) * (L + 1) + ii]);
+    }
+  }
+  st->N[i] = h * acc_get(&nsum);
+  for (int q = 0; q < np; ++q) st->dN[(size_t)i * np + q] = h * acc_get(&dsum[q]);
+  st->tab[i] = T;
+  free(mt); free(rt); free(g); free(dsum);
+  return 0;
+}
+
+static void state_free(const orc_model* m, orc_state* st) {
+  if (st->tab)
+    for (int i = 0; i < m->nnodes; ++i) free(st->tab[i]);
+  free(st->tab);
+  free(st->N);
+  free(st->dN);
+}
+
+/* Normalisations of every leaf, then the lattice table and normalisation of every
+ * convolution node (their subtrees hold no convolution). */
+static int state_init(const orc_model* m, const double* p, int np, orc_state* st) {
+  st->N = (double*)malloc(sizeof(double) * m->nnodes);
+  st->dN = (double*)malloc(sizeof(double) * m->nnodes * (size_t)(np > 0 ? np : 1));
+  st->tab = (double**)calloc(m->nnodes, sizeof(double*));
+  if (orc_norms(m, p, np, st->N, st->dN)) { state_free(m, st); return -1; }
+  for (int i = 0; i < m->nnodes; ++i)
+    if (m->nodes[i].type == ORC_CONV && conv_table(m, i, p, np, st)) { state_free(m, st); return -1; }
+  return 0;
 }
 
 /* Per-event log P (normalised).  cols[o] is the column of observable o. */
 int orc_logpdf(const orc_model* m, const double* p, int np, int64_t n, const double* const* cols,
                double* out) {
-  double* N = (double*)malloc(sizeof(double) * m->nnodes);
-  double* dN = (double*)malloc(sizeof(double) * m->nnodes * np);
-  if (orc_norms(m, p, np, N, dN)) { free(N); free(dN); return -1; }
-  double x[16];
+  orc_state S, *st = &S;
+  if (state_init(m, p, np, st)) return -1;
+  double x[16] = {0};
   for (int64_t i = 0; i < n; ++i) {
-    for (int o = 0; o < m->nobs; ++o) x[o] = cols[o][i];
-    out[i] = node_logvalue(m, m->root, p, np, N, dN, x, NULL);
+    for (int o = 0; o < m->ndata; ++o) x[o] = cols[o][i];
+    out[i] = node_logvalue(m, m->root, p, np, st, x, NULL);
   }
-  free(N);
-  free(dN);
+  state_free(m, st);
   return 0;
 }
 
 /* NLL = -sum_i log P_i and, if grad != NULL, its gradient over all np parameters. */
 int orc_nll(const orc_model* m, const double* p, int np, int64_t n, const double* const* cols,
             double* nll, double* grad) {
-  double* N = (double*)malloc(sizeof(double) * m->nnodes);
-  double* dN = (double*)malloc(sizeof(double) * m->nnodes * np);
-  if (orc_norms(m, p, np, N, dN)) { free(N); free(dN); return -1; }
+  orc_state S, *st = &S;
+  if (state_init(m, p, np, st)) return -1;
   orc_acc s = {0, 0};
   orc_acc* gs = (orc_acc*)calloc(np, sizeof(orc_acc));
   double* g = (double*)malloc(sizeof(double) * np);
-  double x[16];
+  double x[16] = {0};
   for (int64_t i = 0; i < n; ++i) {
-    for (int o = 0; o < m->nobs; ++o) x[o] = cols[o][i];
-    double lp = node_logvalue(m, m->root, p, np, N, dN, x, grad ? g : NULL);
+    for (int o = 0; o < m->ndata; ++o) x[o] = cols[o][i];
+    double lp = node_logvalue(m, m->root, p, np, st, x, grad ? g : NULL);
     acc_add(&s, -lp);
     if (grad) for (int k = 0; k < np; ++k) acc_add(&gs[k], -g[k]);
   }
   *nll = acc_get(&s);
   if (grad) for (int k = 0; k < np; ++k) grad[k] = acc_get(&gs[k]);
-  free(N); free(dN); free(gs); free(g);
+  state_free(m, st);
+  free(gs); free(g);
   return 0;
 }
 
@@ -462,16 +644,15 @@ int orc_binned(const orc_model* m, const double* p, int np, int64_t nb, const do
                const double* cnt, const double* s2, double K, int metric, double* val,
                double* grad) {
   if (metric < 0 || metric > 2 || (metric == 2 && !s2)) return -1;
-  double* N = (double*)malloc(sizeof(double) * m->nnodes);
-  double* dN = (double*)malloc(sizeof(double) * m->nnodes * np);
-  if (orc_norms(m, p, np, N, dN)) { free(N); free(dN); return -1; }
+  orc_state S, *st = &S;
+  if (state_init(m, p, np, st)) return -1;
   orc_acc s = {0, 0};
   orc_acc* gs = (orc_acc*)calloc(np, sizeof(orc_acc));
   double* g = (double*)malloc(sizeof(double) * np);
-  double x[16];
+  double x[16] = {0};
   for (int64_t b = 0; b < nb; ++b) {
-    for (int o = 0; o < m->nobs; ++o) x[o] = cols[o][b];
-    double v = node_value(m, m->root, p, np, N, dN, x, grad ? g : NULL); /* P_b, dP_b */
+    for (int o = 0; o < m->ndata; ++o) x[o] = cols[o][b];
+    double v = node_value(m, m->root, p, np, st, x, grad ? g : NULL); /* P_b, dP_b */
     double lp = log(v);
     double n = cnt[b], term, c;
     if (metric == 0) {
@@ -493,7 +674,8 @@ int orc_binned(const orc_model* m, const double* p, int np, int64_t nb, const do
   }
   *val = acc_get(&s);
   if (grad) for (int k = 0; k < np; ++k) grad[k] = acc_get(&gs[k]);
-  free(N); free(dN); free(gs); free(g);
+  state_free(m, st);
+  free(gs); free(g);
   return 0;
 }
 

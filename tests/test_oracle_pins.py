@@ -667,3 +667,165 @@ def test_binned_asimov_contents_are_stationary():
         assert np.all(np.abs(g[free]) <= 1e-9 * np.abs(g1[free])), (metric, g[free], g1[free])
         if metric == 2:
             assert f <= 1e-18 * K
+
+
+# --------------------------------------------------------------------------------
+# ConvolutionPdf (Sec. 3) and the relativistic Breit-Wigner (Sec. 4, the D*+ fit)
+# --------------------------------------------------------------------------------
+D0_MASS, PI_MASS = 1.86484, 0.13957
+
+
+def _lattice(lo, hi, L):
+    return lo + np.arange(L + 1) * (hi - lo) / L
+
+
+def test_conv_gauss_gauss_is_gauss_on_the_lattice():
+    """Gaussian (mu, s1) convolved with a Gaussian resolution (0, s2) is a Gaussian of
+    sigma sqrt(s1^2 + s2^2) (closed form); the lattice values of the normalised
+    convolution match the truncated normal up to the interpolant's normalisation."""
+    lo, hi, L = -4.0, 6.0, 2000
+    s1, s2, mu = 0.7, 0.25, 0.9
+    # a 10 sigma resolution window: at 8 sigma its cut tails already shift lattice values
+    # 8 sigma_tot from mu by ~5e-10
+    m = oracle.Model1D([(lo, hi), (-10 * s2, 10 * s2)])
+    g1 = m.gauss(0, m.param(mu), m.param(s1))
+    r = m.gauss(1, m.param(0.0), m.param(s2))
+    m.conv(0, g1, r, L)
+    xs = _lattice(lo, hi, L)
+    P = np.exp(m.logpdf([xs]))
+    st = math.hypot(s1, s2)
+    ref = stats.truncnorm.pdf(xs, (lo - mu) / st, (hi - mu) / st, loc=mu, scale=st)
+    # the trapezoid normalisation of the lattice values differs from the exact integral
+    # by O(h^2 f''): compare shapes through the ratio, and the ratio to 1 within h^2
+    ratio = P / ref
+    assert np.max(np.abs(ratio / ratio.mean() - 1)) < 1e-10
+    assert abs(ratio.mean() - 1) < ((hi - lo) / L) ** 2
+
+
+def test_conv_interpolation_error_within_bound():
+    """Between lattice points the value is the linear interpolant: its error against the
+    closed form stays below h^2/8 max|f''|."""
+    lo, hi, L = -4.0, 6.0, 400
+    s1, s2, mu = 0.7, 0.25, 0.9
+    m = oracle.Model1D([(lo, hi), (-8 * s2, 8 * s2)])
+    m.conv(0, m.gauss(0, m.param(mu), m.param(s1)), m.gauss(1, m.param(0.0), m.param(s2)), L)
+    h = (hi - lo) / L
+    xs = lo + (np.arange(L) + 0.37) * h
+    st = math.hypot(s1, s2)
+    f = stats.truncnorm.pdf(xs, (lo - mu) / st, (hi - mu) / st, loc=mu, scale=st)
+    fpp = np.max(np.abs(stats.norm.pdf(0) / st ** 3)) * 1.0  # max |f''| of the Gaussian
+    err = np.abs(np.exp(m.logpdf([xs])) - f)
+    assert np.max(err) <= h * h / 8 * fpp * 1.2 + 3 * h * h * np.max(f)
+
+
+def test_conv_one_sided_exponential_is_exponnorm():
+    """A one-sided exponential (threshold shape with power 0) convolved with a Gaussian
+    is scipy's exponentially modified normal; the step of the model sits midway between
+    model lattice points, so the Riemann sum errs by O(h^2)."""
+    lo, hi, L = -1.0, 5.0, 3000
+    h = (hi - lo) / L
+    x0 = lo + 250.5 * h
+    c, s = 1.3, 0.2
+    m = oracle.Model1D([(lo, hi), (-9 * s, 9 * s)])
+    th = m.threshold(0, m.param(x0), m.param(0.0), m.param(c))
+    m.conv(0, th, m.gauss(1, m.param(0.0), m.param(s)), L)
+    xs = _lattice(lo, hi, L)
+    P = np.exp(m.logpdf([xs]))
+    ref = stats.exponnorm.pdf(xs - x0, 1.0 / (c * s), scale=s)
+    ref /= integrate.trapezoid(ref, xs)
+    assert np.max(np.abs(P - ref)) < 2e-5 * np.max(ref)
+
+
+def test_conv_voigt_gauss_is_voigt_profile():
+    """Voigtian (sigma1, Gamma) convolved with a Gaussian (sigma2) is scipy's Voigt profile
+    with sigma = sqrt(sigma1^2 + sigma2^2) (shapes compared on the lattice)."""
+    lo, hi, L = 0.1395, 0.1610, 2150
+    mu, s1, G, s2 = 0.1455, 2e-4, 8e-5, 2.5e-4
+    m = oracle.Model1D([(lo, hi), (-10 * s2, 10 * s2)], nbins=20000)
+    v = m.voigt(0, m.param(mu), m.param(s1), m.param(G))
+    m.conv(0, v, m.gauss(1, m.param(0.0), m.param(s2)), L)
+    xs = _lattice(lo, hi, L)
+    P = np.exp(m.logpdf([xs]))
+    ref = special.voigt_profile(xs - mu, math.hypot(s1, s2), G / 2)
+    k = np.argmax(ref)
+    # the Voigtian model is normalised on [lo, hi] (its Lorentzian tails reach outside):
+    # compare shapes
+    assert np.max(np.abs(P / P[k] - ref / ref[k])) < 2e-6
+
+
+def test_conv_gradient_fd():
+    lo, hi = 0.1395, 0.1610
+    m = oracle.Model1D([(lo, hi), (-0.002, 0.002)], nbins=4000)
+    v = m.voigt(0, m.param(0.1455), m.param(2e-4), m.param(8e-5))
+    r1 = m.gauss(1, m.param(0.0), m.param(3e-4))
+    r2 = m.gauss(1, m.param(1e-4), m.param(8e-4))
+    res = m.add([r1, r2], [m.param(0.7)])
+    m.conv(0, v, res, 860)
+    x = synth.voigt_threshold_events(3000, **synth.VOIGT_TRUTH, lo=lo, hi=hi)
+    p = m.p
+    _fd_check(lambda q: m.nll([x], q, grad=True), p, list(range(8)), rel=2e-6)
+
+
+def _relbw_model(lo, hi, dm0, g0, L=1, nbins=20000):
+    m = oracle.Model1D([(lo, hi)], nbins=nbins)
+    m.relbw(0, m.param(dm0), m.param(g0), m.param(D0_MASS), m.param(D0_MASS), m.param(PI_MASS),
+            m.param(1.5), L)
+    return m
+
+
+def test_relbw_value_at_the_pole_and_threshold():
+    """At m = m0 the running width equals Gamma0 and the shape is 1/(m0 Gamma0); at the
+    D0 pi+ threshold it vanishes."""
+    dm0, g0 = 0.14543, 8.3e-5
+    m = _relbw_model(0.139, 0.16, dm0, g0)
+    v = m.leaf_shape(0, np.array([dm0, PI_MASS + 1e-12, PI_MASS - 1e-6]))
+    assert abs(v[0] * (dm0 + D0_MASS) * g0 - 1) < 1e-13
+    assert v[1] < 1e-6 * v[0] and v[2] == 0.0
+
+
+def test_relbw_running_width_vs_two_body_momentum():
+    """Gamma(m)/Gamma0 from the shape (f D/m) against (q/q0)^3 (m0/m) F_1^2 with q the
+    pion momentum computed from explicit two-body energies."""
+    dm0, g0 = 0.14543, 8.3e-5
+    m = _relbw_model(0.139, 0.16, dm0, g0)
+    xs = np.array([0.1420, 0.1450, 0.1500, 0.1580])
+    f = m.leaf_shape(0, xs)
+    M, M0 = xs + D0_MASS, dm0 + D0_MASS
+
+    def q(mm):
+        e = (mm * mm + PI_MASS ** 2 - D0_MASS ** 2) / (2 * mm)
+        return np.sqrt(e * e - PI_MASS ** 2)
+    z, z0 = (q(M) * 1.5) ** 2, (q(M0) * 1.5) ** 2
+    G = g0 * (q(M) / q(M0)) ** 3 * (M0 / M) * (1 + z0) / (1 + z)
+    D = (M0 ** 2 - M ** 2) ** 2 + M0 ** 2 * G ** 2
+    assert np.max(np.abs(f * D / (M * G) - 1)) < 1e-12
+
+
+def test_relbw_narrow_limit_is_cauchy():
+    """For Gamma0 -> 0 the normalised line shape near the pole approaches a Cauchy
+    density of half-width Gamma0/2 in m; at an offset d from the pole the P-wave factor
+    (q/q0)^3 ~ (1 + d/(dm0 - threshold))^(3/2) tilts it by ~ 1.5 d/(dm0 - threshold)."""
+    dm0, g0 = 0.1455, 2e-6
+    lo, hi = dm0 - 2e-4, dm0 + 2e-4
+    m = _relbw_model(lo, hi, dm0, g0, nbins=100000)
+    xs = np.linspace(dm0 - 2e-5, dm0 + 2e-5, 41)
+    P = np.exp(m.logpdf([xs]))
+    ref = stats.cauchy.pdf(xs, dm0, g0 / 2)
+    ref /= stats.cauchy.cdf(hi, dm0, g0 / 2) - stats.cauchy.cdf(lo, dm0, g0 / 2)
+    tilt = 1.5 * np.abs(xs - dm0) / (dm0 - PI_MASS)
+    assert np.all(np.abs(P / ref - 1) <= 1.2 * tilt + 2e-4)
+
+
+def test_relbw_gradient_fd():
+    lo, hi = 0.1395, 0.1610
+    m = _relbw_model(lo, hi, 0.14543, 8.3e-5, nbins=4000)
+    x = synth.voigt_threshold_events(3000, **synth.VOIGT_TRUTH, lo=lo, hi=hi)
+    p = m.p
+    f0, g = m.nll([x], p, grad=True)
+    # steps well below the width 8.3e-5 (the curvature scale of the line shape)
+    for k, h in ((0, 3e-9), (1, 1e-11)):
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (m.nll([x], pp) - m.nll([x], pm)) / (2 * h)
+        assert abs(fd / g[k] - 1) < 1e-7, (k, fd, g[k])
