@@ -98,6 +98,27 @@ int gf_pdf_voigt(gf_ctx* ctx, int obs, int mu, int sigma, int width, int* node);
 int gf_pdf_threshold(gf_ctx* ctx, int obs, int x0, int power, int c, int* node);
 /* Polynomial sum_k coef[k] x^k, ncoef <= 8. */
 int gf_pdf_poly(gf_ctx* ctx, int obs, int ncoef, const int* coefs, int* node);
+/* Relativistic Breit-Wigner line shape (Sec. 4: the P-wave D*+ line fitted in the D*+ - D0
+ * mass difference) in x = m - shift:
+ *   f = m Gamma(m) / ((m0^2 - m^2)^2 + m0^2 Gamma(m)^2),  m = x + shift, m0 = dm0 + shift,
+ *   Gamma(m) = gamma0 (q/q0)^{2 spin + 1} (m0/m) B(z0)/B(z),
+ * q the break-up momentum of masses ma, mb at m, z = (q radius)^2, Blatt-Weisskopf
+ * B = 1, 1 + z, 9 + 3z + z^2 for spin 0, 1, 2; zero at or below ma + mb.  Normalised on
+ * the node's grid.  shift, ma, mb and radius must be fixed parameters (GF_EINVAL at the
+ * first evaluation otherwise). */
+int gf_pdf_relbw(gf_ctx* ctx, int obs, int dm0, int gamma0, int shift, int ma, int mb,
+                 int radius, int spin, int* node);
+/* ConvolutionPdf (Sec. 3): the model node (over obs) convolved with the resolution node,
+ * whose leaves use one residual observable r (declared like any observable; its range
+ * [rlo, rhi] is the resolution's support and is not a data column).  Numerically, on a
+ * lattice of L bins of obs's range (gf_set_norm_grid(node, L), default 1000, at most
+ * 65536; h = (hi - lo)/L): C_i = h sum_k R(k h) M(x_i - k h) over the offsets k h in
+ * [rlo, rhi] (at most 8193), C linear between lattice points, P = C / N with N the
+ * trapezoid integral h (C_0/2 + C_1 + ... + C_L/2).  Model and resolution are normalised
+ * on their own ranges (the model is evaluated outside its range where the lattice needs
+ * it).  At most 2 convolutions per tree, none nested, at most 8 free parameters in the
+ * model and resolution together. */
+int gf_pdf_conv(gf_ctx* ctx, int obs, int model, int resolution, int* node);
 /* AddPdf (Sec. 3): sum_{k<n-1} f_k P_k + (1 - sum f) P_{n-1}; fracs has n-1 ids, n <= 8. */
 int gf_pdf_add(gf_ctx* ctx, int n, const int* nodes, const int* fracs, int* node);
 /* ProdPdf (Sec. 3, Listing 2): prod_k P_k; the factors must use distinct observables. */
@@ -123,8 +144,8 @@ typedef struct {
 } gf_resonance;
 int gf_pdf_dalitz(gf_ctx* ctx, int obs12, int obs13, const gf_dalitz_kin* kin, int nres,
                   const gf_resonance* res, int* node);
-/* Grid of the node's numerical normalisation: nbins_x bins for a 1D leaf, or
- * nbins_x x nbins_y cells for a Dalitz node. */
+/* Grid of the node's numerical normalisation: nbins_x bins for a 1D leaf, the lattice
+ * of a convolution, or nbins_x x nbins_y cells for a Dalitz node. */
 int gf_set_norm_grid(gf_ctx* ctx, int node, int nbins_x, int nbins_y);
 /* 1 if (s12, s13) lies inside the kinematic region of the Dalitz node, else 0, for n
  * points (host arrays). */

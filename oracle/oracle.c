@@ -188,15 +188,22 @@ static double relbw_shape(const orc_node* nd, const double* p, double x, double*
   double ma = p[nd->par[3]], mb = p[nd->par[4]], R = p[nd->par[5]];
   int L = nd->aux;
   double m = x + shift, m0 = dm0 + shift;
+  /* distances to threshold from the observable directly: s - A = (m - ma - mb)(m + ma + mb)
+   * with m - ma - mb = x - (ma + mb - shift), free of the cancellation of s - A near
+   * threshold */
+  double thr = ma + mb - shift;
   if (dr) for (int k = 0; k < 6; ++k) dr[k] = 0.0;
-  if (!(m > ma + mb)) return 0.0;
+  if (!(x - thr > 0)) return 0.0;
   double A = (ma + mb) * (ma + mb), B = (ma - mb) * (ma - mb);
   double s = m * m, s0 = m0 * m0;
-  double q2 = (s - A) * (s - B) / (4 * s), q02 = (s0 - A) * (s0 - B) / (4 * s0);
+  double q2 = (x - thr) * (m + ma + mb) * (s - B) / (4 * s);
+  double q02 = (dm0 - thr) * (m0 + ma + mb) * (s0 - B) / (4 * s0);
   double z = q2 * R * R, z0 = q02 * R * R;
   double F2 = rb_poly(L, z0) / rb_poly(L, z);
   double G = g0 * pow(q2 / q02, L + 0.5) * (m0 / m) * F2;
-  double D = (s0 - s) * (s0 - s) + s0 * G * G;
+  /* m0^2 - m^2 = (dm0 - x)(m0 + m): no cancellation near the pole */
+  double ds = (dm0 - x) * (m0 + m);
+  double D = ds * ds + s0 * G * G;
   double f = m * G / D;
   if (dr) {
     /* Gamma0 */
@@ -207,7 +214,7 @@ static double relbw_shape(const orc_node* nd, const double* p, double x, double*
     double dq02 = 2 * m0 * (s0 * s0 - A * B) / (4 * s0 * s0);
     double dlnG = -(L + 0.5) * dq02 / q02 + 1.0 / m0 + rb_poly_dz(L, z0) * R * R * dq02 / rb_poly(L, z0);
     dG = G * dlnG;
-    dD = 4 * m0 * (s0 - s) + 2 * m0 * G * G + 2 * s0 * G * dG;
+    dD = 4 * m0 * ds + 2 * m0 * G * G + 2 * s0 * G * dG;
     dr[0] = m * dG / D - f * dD / D;
   }
   return f;

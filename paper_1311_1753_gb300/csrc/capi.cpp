@@ -139,6 +139,7 @@ static void free_dev(gf_ctx* ctx) {
   cudaFree(d.perm);
   cudaFree(d.bw);
   cudaFree(d.bs2);
+  for (void* p : d.conv_bufs) cudaFree(p);
   for (auto& g : d.graph)
     if (g) cudaGraphExecDestroy(g);
   d = DevState();
@@ -306,6 +307,33 @@ int gf_pdf_poly(gf_ctx* ctx, int obs, int ncoef, const int* coefs, int* node) {
   return leaf(ctx, N_POLY, obs, std::vector<int>(coefs, coefs + ncoef), node);
 }
 
+int gf_pdf_relbw(gf_ctx* ctx, int obs, int dm0, int gamma0, int shift, int ma, int mb,
+                 int radius, int spin, int* node) {
+  if (!ctx) return GF_EINVAL;
+  if (spin < 0 || spin > 2) return set_error(ctx, GF_EINVAL, "relbw: spin 0, 1 or 2");
+  const int rc = leaf(ctx, N_RELBW, obs, {dm0, gamma0, shift, ma, mb, radius}, node);
+  if (rc == GF_OK) ctx->nodes[*node].aux = spin;
+  return rc;
+}
+
+int gf_pdf_conv(gf_ctx* ctx, int obs, int model, int resolution, int* node) {
+  if (!ctx) return GF_EINVAL;
+  if (!valid_obs(ctx, obs) || !valid_node(ctx, model) || !valid_node(ctx, resolution) ||
+      model == resolution)
+    return set_error(ctx, GF_EINVAL, "ConvolutionPdf: bad observable or nodes");
+  for (int c : {model, resolution}) {
+    const int t = ctx->nodes[c].type;
+    if (t == N_DALITZ || t == N_CONV)
+      return set_error(ctx, GF_EINVAL, "ConvolutionPdf: model and resolution are 1D, unconvolved");
+  }
+  NodeDef nd;
+  nd.type = N_CONV;
+  nd.obs = obs;
+  nd.nbx = 1000;
+  nd.children = {model, resolution};
+  return add_node(ctx, std::move(nd), node);
+}
+
 int gf_pdf_add(gf_ctx* ctx, int n, const int* nodes, const int* fracs, int* node) {
   if (!ctx) return GF_EINVAL;
   if (n < 2 || n > kMaxLocal || !nodes || !fracs)
@@ -372,8 +400,11 @@ int gf_set_norm_grid(gf_ctx* ctx, int node, int nbins_x, int nbins_y) {
     if (nbins_x < 1 || nbins_y < 1 || (int64_t)nbins_x * nbins_y > (1 << 26))
       return set_error(ctx, GF_EINVAL, "Dalitz grid: 1 <= nbx*nby <= 2^26");
     nd.nby = nbins_y;
-  } else if (nd.type == N_VOIGT || nd.type == N_THRESH) {
+  } else if (nd.type == N_VOIGT || nd.type == N_THRESH || nd.type == N_RELBW) {
     if (nbins_x < 1 || nbins_x > (1 << 24)) return set_error(ctx, GF_EINVAL, "grid: 1..2^24 bins");
+  } else if (nd.type == N_CONV) {
+    if (nbins_x < 1 || nbins_x > kConvMaxLattice)
+      return set_error(ctx, GF_EINVAL, "convolution lattice: 1..65536 bins");
   } else {
     return set_error(ctx, GF_EINVAL, "node has an analytic normalisation");
   }
@@ -444,12 +475,33 @@ extern "C" int gf_dalitz_inside(gf_ctx* ctx, int node, int64_t n, const double* 
 // ---- the PDF-tree compiler (1D trees) ------------------------------------------------------------
 namespace {
 
+// A ConvolutionPdf found by the compiler: its model and resolution subtrees as programs of
+// their own (sharing the main program's leaf and coefficient tables).
+struct ConvInfo {
+  int node = -1, mcol = -1, ro = -1, slot = -1;
+  std::vector<int> loc;  // local parameters (free parameters of both subtrees)
+  Program pm{}, pr{};
+};
+
+int first_leaf_obs(const gf_ctx* ctx, int id) {
+  const NodeDef& nd = ctx->nodes[id];
+  if (nd.type >= N_EXP && nd.type <= N_RELBW) return nd.obs;
+  return nd.children.empty() ? -1 : first_leaf_obs(ctx, nd.children[0]);
+}
+
 struct Compiler {
   gf_ctx* ctx;
   Program& P;
   const std::vector<int>& col_of_obs;  // observable id -> dataset column, -1 if absent
   std::string err;
   int depth = 0, maxdepth = 0;
+  // convolutions: instructions of a subtree go to tgt (the main program when null); inside
+  // a resolution its residual observable resid_obs maps to column kResidCol; conv_pars
+  // collects the parameters of the subtree's leaves and fractions
+  Program* tgt = nullptr;
+  int resid_obs = -1, conv_mobs = -1;
+  std::vector<int>* conv_pars = nullptr;
+  std::vector<ConvInfo> convs;
 
   int need(int id) {
     const NodeDef& nd = ctx->nodes[id];
@@ -469,8 +521,9 @@ struct Compiler {
     return idx;
   }
   bool emit(const Instr& I) {
-    if (P.n >= kMaxIns) { err = "PDF tree too large (more than 32 instructions)"; return false; }
-    P.ins[P.n++] = I;
+    Program& T = tgt ? *tgt : P;
+    if (T.n >= kMaxIns) { err = "PDF tree too large (more than 32 instructions)"; return false; }
+    T.ins[T.n++] = I;
     if (I.op == OP_LEAF) depth++;
     if (I.op == OP_MUL || I.op == OP_LMUL || I.op == OP_ADD) depth--;
     maxdepth = std::max(maxdepth, depth);
@@ -481,18 +534,34 @@ struct Compiler {
   // returns 1 for log domain, 0 linear, -1 error
   int walk(int id, std::vector<int>& obs_used) {
     const NodeDef& nd = ctx->nodes[id];
-    if (nd.type >= N_EXP && nd.type <= N_POLY) {
+    if (nd.type >= N_EXP && nd.type <= N_RELBW) {
       if (P.nleaf >= kMaxLeaf) { err = "more than 16 leaves"; return -1; }
-      const int col = col_of_obs[nd.obs];
+      if (resid_obs >= 0 && nd.obs != resid_obs) {
+        err = "a resolution's leaves must share one residual observable";
+        return -1;
+      }
+      if (conv_mobs >= 0 && nd.obs != conv_mobs) {
+        err = "a convolution's model must use the convolution's observable";
+        return -1;
+      }
+      const int col = resid_obs >= 0 ? kResidCol : col_of_obs[nd.obs];
       if (col < 0) { err = "the dataset lacks an observable used by the PDF"; return -1; }
+      if (nd.type == N_RELBW)
+        for (int k = 2; k < 6; ++k)
+          if (gidx(nd.pars[k]) >= 0) {
+            err = "relbw: shift, daughter masses and radius must be fixed parameters";
+            return -1;
+          }
       obs_used.push_back(nd.obs);
+      if (conv_pars) conv_pars->insert(conv_pars->end(), nd.pars.begin(), nd.pars.end());
       LeafDesc& L = P.leaf[P.nleaf];
       L = LeafDesc{};
-      L.kind = nd.type;  // N_EXP..N_POLY coincide with L_EXP..L_POLY
+      L.kind = nd.type;  // N_EXP..N_RELBW coincide with L_EXP..L_RELBW
       L.obs = col;
       L.npar = (int)nd.pars.size();
+      L.aux = nd.aux;
       for (int k = 0; k < L.npar; ++k) L.par[k] = nd.pars[k];
-      L.nbins = (nd.type == N_VOIGT || nd.type == N_THRESH) ? nd.nbx : 0;
+      L.nbins = (nd.type == N_VOIGT || nd.type == N_THRESH || nd.type == N_RELBW) ? nd.nbx : 0;
       L.lo = ctx->obs[nd.obs].lo;
       L.hi = ctx->obs[nd.obs].hi;
       Instr I{};
@@ -505,6 +574,68 @@ struct Compiler {
       P.nleaf++;
       if (!emit(I)) return -1;
       return (nd.type == N_EXP || nd.type == N_GAUSS) ? 1 : 0;
+    }
+    if (nd.type == N_CONV) {
+      if (tgt) { err = "ConvolutionPdf nodes cannot be nested"; return -1; }
+      if ((int)convs.size() >= kMaxConv) { err = "more than 2 ConvolutionPdf nodes"; return -1; }
+      if (P.nleaf >= kMaxLeaf) { err = "more than 16 leaves"; return -1; }
+      ConvInfo ci;
+      ci.node = id;
+      ci.mcol = col_of_obs[nd.obs];
+      ci.ro = first_leaf_obs(ctx, nd.children[1]);
+      if (ci.mcol < 0) { err = "the dataset lacks the convolution's observable"; return -1; }
+      if (ci.ro < 0 || ci.ro == nd.obs) {
+        err = "the resolution needs its own residual observable";
+        return -1;
+      }
+      std::vector<int> pars, u;
+      conv_pars = &pars;
+      const int saved = depth;
+      tgt = &ci.pm;
+      depth = 0;
+      conv_mobs = nd.obs;
+      const int dm = walk(nd.children[0], u);
+      conv_mobs = -1;
+      if (dm < 0) return -1;
+      ci.pm.root_log = dm;
+      tgt = &ci.pr;
+      depth = 0;
+      resid_obs = ci.ro;
+      const int dr = walk(nd.children[1], u);
+      resid_obs = -1;
+      tgt = nullptr;
+      depth = saved;
+      conv_pars = nullptr;
+      if (dr < 0) return -1;
+      ci.pr.root_log = dr;
+      for (int q : pars)
+        if (gidx(q) >= 0 && std::find(ci.loc.begin(), ci.loc.end(), q) == ci.loc.end())
+          ci.loc.push_back(q);
+      if ((int)ci.loc.size() > kMaxLocal) {
+        err = "a convolution's model and resolution have more than 8 free parameters";
+        return -1;
+      }
+      LeafDesc& L = P.leaf[P.nleaf];
+      L = LeafDesc{};
+      L.kind = L_CONV;
+      L.obs = ci.mcol;
+      L.npar = (int)ci.loc.size();
+      for (int k = 0; k < L.npar; ++k) L.par[k] = ci.loc[k];
+      L.lo = ctx->obs[nd.obs].lo;
+      L.hi = ctx->obs[nd.obs].hi;
+      L.aux = (int)convs.size();
+      Instr I{};
+      I.op = OP_LEAF;
+      I.kind = L_CONV;
+      I.obs = ci.mcol;
+      I.slot = P.nleaf;
+      I.npar = L.npar;
+      for (int k = 0; k < kMaxLocal; ++k) I.gidx[k] = k < L.npar ? gidx(L.par[k]) : -1;
+      ci.slot = P.nleaf++;
+      if (!emit(I)) return -1;
+      obs_used.push_back(nd.obs);
+      convs.push_back(std::move(ci));
+      return 0;
     }
     if (nd.type == N_PROD) {
       // factors must use distinct observables (ProdPdf of Listing 2)
@@ -564,6 +695,7 @@ struct Compiler {
           C.n = nc - 1;
           for (int q = 0; q < nc - 1; ++q) C.par[q] = nd.pars[q];
         }
+        if (conv_pars) conv_pars->insert(conv_pars->end(), C.par, C.par + C.n);
         S.kind = C.sign;
         S.npar = C.n;
         for (int q = 0; q < kMaxLocal; ++q) S.gidx[q] = q < C.n ? gidx(C.par[q]) : -1;
@@ -646,6 +778,92 @@ static void detect_logsum(Program& P) {
   for (int l = 0; l < P.nleaf; ++l)
     if (P.leaf[l].nbins > 0) return;
   P.logsum = 1;
+}
+
+// Device tables of every convolution (freed and rebuilt at each compilation).
+static void free_convs(DevState& d) {
+  for (void* p : d.conv_bufs) cudaFree(p);
+  d.conv_bufs.clear();
+  d.nconv = 0;
+  for (auto& c : d.conv_desc) c = nullptr;
+}
+
+static int setup_convs(gf_ctx* ctx, std::vector<ConvInfo>& convs) {
+  DevState& d = ctx->dev;
+  free_convs(d);
+  const Program& P = ctx->prog;
+  for (size_t c = 0; c < convs.size(); ++c) {
+    ConvInfo& ci = convs[c];
+    const NodeDef& nd = ctx->nodes[ci.node];
+    for (Program* sp : {&ci.pm, &ci.pr}) {  // the subtrees share the main tables
+      sp->nleaf = P.nleaf;
+      sp->ncoef = P.ncoef;
+      sp->nfree = P.nfree;
+      sp->nobs = P.nobs;
+      std::copy(P.leaf, P.leaf + kMaxLeaf, sp->leaf);
+      std::copy(P.coef, P.coef + kMaxCoef, sp->coef);
+    }
+    ConvDesc h{};
+    h.L = nd.nbx;
+    h.lo = ctx->obs[nd.obs].lo;
+    h.h = (ctx->obs[nd.obs].hi - h.lo) / h.L;
+    h.kmin = (int)std::ceil(ctx->obs[ci.ro].lo / h.h - 1e-9);
+    h.kmax = (int)std::floor(ctx->obs[ci.ro].hi / h.h + 1e-9);
+    h.K = h.kmax - h.kmin + 1;
+    if (h.K < 1 || h.K > kConvMaxOffsets)
+      return set_error(ctx, GF_EINVAL,
+                       "convolution: 1..8193 lattice steps must fit the residual range");
+    h.J = h.L + h.K;
+    h.nloc = (int)ci.loc.size();
+    h.slot = ci.slot;
+    h.mcol = ci.mcol;
+    for (int l = 0; l < h.nloc; ++l) h.loc2free[l] = ctx->free_pos[ci.loc[l]];
+    const int nq = 1 + h.nloc;
+    const int nsum = (h.L + 1 + kThreads1D - 1) / kThreads1D;
+    auto alloc = [&](size_t bytes) -> void* {
+      void* p = nullptr;
+      if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      d.conv_bufs.push_back(p);
+      return p;
+    };
+    Program* pm = static_cast<Program*>(alloc(sizeof(Program)));
+    Program* pr = static_cast<Program*>(alloc(sizeof(Program)));
+    h.mt = static_cast<float2*>(alloc(sizeof(float2) * nq * (size_t)h.J));
+    h.rt = static_cast<float2*>(alloc(sizeof(float2) * nq * (size_t)h.K));
+    h.ct = static_cast<double*>(alloc(sizeof(double) * nq * (size_t)(h.L + 1)));
+    h.partials = static_cast<double*>(alloc(sizeof(double) * (1 + kMaxLocal) * (size_t)nsum));
+    h.counter = static_cast<unsigned*>(alloc(sizeof(unsigned)));
+    ConvDesc* dd = static_cast<ConvDesc*>(alloc(sizeof(ConvDesc)));
+    if (!pm || !pr || !h.mt || !h.rt || !h.ct || !h.partials || !h.counter || !dd) {
+      free_convs(d);
+      return set_error(ctx, GF_ENOMEM, "device allocation of the convolution tables failed");
+    }
+    h.pm = pm;
+    h.pr = pr;
+    CK(cudaMemcpyAsync(pm, &ci.pm, sizeof(Program), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(pr, &ci.pr, sizeof(Program), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(h.counter, 0, sizeof(unsigned), ctx->stream));
+    CK(cudaMemcpyAsync(dd, &h, sizeof(ConvDesc), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    d.conv_host[c] = h;
+    d.conv_desc[c] = dd;
+    d.nconv = (int)c + 1;
+  }
+  return GF_OK;
+}
+
+// Convolution tables after the normalisation launch (every evaluation of a tree with them).
+static int enqueue_convs(gf_ctx* ctx, int* launches) {
+  DevState& d = ctx->dev;
+  for (int c = 0; c < d.nconv; ++c) {
+    CK(launch_conv(d.conv_host[c], d.conv_desc[c], weideman(), ctx->prog.nfree, d.derived,
+                   ctx->stream));
+    if (launches) *launches += 2;
+  }
+  return GF_OK;
 }
 
 bool has_cycle(gf_ctx* ctx, int id, std::vector<int>& state) {
@@ -745,6 +963,9 @@ int ensure_compiled(gf_ctx* ctx) {
       }
     }
     P.ngrid_blocks = blk;
+    const int rcc = setup_convs(ctx, C.convs);
+    if (rcc) return rcc;
+    if (!C.convs.empty()) ctx->has_grid = true;  // records come from the device
     // the first Voigtian leaf is the one expanded per chunk on sorted data
     P.tay_slot = -1;
     P.tay_obs = 0;
@@ -1366,6 +1587,8 @@ static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool capt
       CK(launch_norm_1d(ctx->prog, d.prog, W, d.theta, d.partials2, d.counters + 1, d.derived,
                         ctx->stream));
       (*launches)++;
+      const int rc = enqueue_convs(ctx, launches);
+      if (rc) return rc;
     }
     Cols cols{};
     for (int k = 0; k < d.nobs; ++k) cols.c[k] = d.cols[k];
@@ -1499,6 +1722,7 @@ int tick_prepare(gf_ctx* ctx) {
   DevState& d = ctx->dev;
   if (d.tick_desc) return d.tick_kind;
   if (!ctx->compiled || !d.theta || d.n <= 0) return 0;
+  if (d.nconv > 0) return 0;  // convolution tables: per-fit evaluations
   CK(cudaSetDevice(ctx->device));
   if (!ctx->is_dalitz) {
     Fit1D F{};
@@ -1628,6 +1852,7 @@ static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host)
       cudaError_t e = launch_norm_1d(ctx->prog, d.prog, W, d.theta, d.partials2, d.counters + 1,
                                      d.derived, ctx->stream);
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "launch_norm_1d");
+      if (rc == GF_OK) rc = enqueue_convs(ctx, nullptr);
     }
     Cols cols{};
     for (int k = 0; k < d.nobs; ++k) cols.c[k] = d.cols[k];

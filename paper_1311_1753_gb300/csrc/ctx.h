@@ -12,7 +12,8 @@
 
 namespace gfi {
 
-enum NodeType { N_EXP = 1, N_GAUSS, N_VOIGT, N_THRESH, N_POLY, N_ADD = 10, N_PROD, N_DALITZ };
+enum NodeType { N_EXP = 1, N_GAUSS, N_VOIGT, N_THRESH, N_POLY, N_RELBW, N_ADD = 10, N_PROD,
+                N_DALITZ, N_CONV };
 
 struct ObsDef {
   std::string name;
@@ -28,7 +29,8 @@ struct NodeDef {
   int obs = -1, obs2 = -1;
   std::vector<int> pars;      // leaf parameters / ADD fractions
   std::vector<int> children;  // ADD / PROD
-  int nbx = 10000, nby = 0;   // normalisation grid
+  int nbx = 10000, nby = 0;   // normalisation grid (N_CONV: lattice bins, default 1000)
+  int aux = 0;                // N_RELBW: orbital angular momentum
   gf_dalitz_kin kin{};
   std::vector<gf_resonance> res;
 };
@@ -80,6 +82,11 @@ struct DevState {
   int sort_obs = -1;                  // the column the events are sorted by
   int32_t* perm = nullptr;            // sorted position -> original event index
   int evals_since_load = 0;           // evaluations since the columns were (re)loaded
+  // convolution nodes: device descriptors and their tables (allocated at compile)
+  std::vector<void*> conv_bufs;        // every allocation of the conv tables
+  ConvDesc* conv_desc[kMaxConv] = {};  // device copies
+  ConvDesc conv_host[kMaxConv] = {};
+  int nconv = 0;
   // binned data: bin contents and chi-squared variances (device), N x bin volume
   bool binned = false;
   double* bw = nullptr;

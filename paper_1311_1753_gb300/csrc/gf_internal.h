@@ -28,7 +28,15 @@ constexpr int kChunk = 24;      // sorted 1D data: events per expansion of w (k_
                                 // chunked loop runs when there are >= kChunk/2 events per thread
 
 // Leaf kinds (shape functions; Sec. 2-3 of the paper and gf.h).
-enum Leaf : int32_t { L_EXP = 1, L_GAUSS = 2, L_VOIGT = 3, L_THRESH = 4, L_POLY = 5 };
+enum Leaf : int32_t {
+  L_EXP = 1, L_GAUSS = 2, L_VOIGT = 3, L_THRESH = 4, L_POLY = 5,
+  L_RELBW = 6,  // relativistic Breit-Wigner line shape (grid-normalised)
+  L_CONV = 7    // a ConvolutionPdf read from its lattice table (k_conv.cu builds it)
+};
+constexpr int kResidCol = 7;     // observable column of a resolution's residual variable
+constexpr int kMaxConv = 2;      // convolution nodes of one tree
+constexpr int kConvMaxLattice = 65536;  // lattice bins of one convolution
+constexpr int kConvMaxOffsets = 8193;   // resolution offsets of one convolution
 
 // Opcodes of the postfix (stack) program of a 1D PDF tree.  "log" values live in the
 // log domain, "lin" values in the linear domain; the compiler inserts TOLIN where a
@@ -57,6 +65,8 @@ struct LeafDesc {
   double lo, hi;                   // observable range
   int32_t grid_first_block;        // first block of this leaf in the norm grid launch
   int32_t grid_nblocks;
+  int32_t aux;                     // L_RELBW: orbital angular momentum; L_CONV: conv index
+  int32_t pad;
 };
 
 struct CoefDesc {
@@ -90,6 +100,25 @@ struct Program {
 
 struct Cols {
   const double* c[kMaxObs];
+};
+
+// One ConvolutionPdf node (k_conv.cu).  Lattice x_i = lo + i h (i = 0..L); resolution
+// offsets u_k = (kmin + k) h (k < K); model points t_j = lo + (j - kmax) h (j < J =
+// L + K); C_i = h sum_k R(u_k) M(x_i - u_k).  Tables hold a value row, then one row per
+// local parameter (the free parameters of the model and resolution subtrees).
+struct ConvDesc {
+  const Program* pm;  // model subtree as a program (device), its leaves in the main table
+  const Program* pr;  // resolution subtree (its observable in column kResidCol)
+  float2* mt;         // [1 + nloc][J] pairs (hi, lo)
+  float2* rt;         // [1 + nloc][K]
+  double* ct;         // [1 + nloc][L + 1]: C_i and dC_i/dtheta_l
+  double* partials;   // [blocks][1 + nloc]: trapezoid sums
+  unsigned* counter;
+  int32_t L, kmin, kmax, J, K, nloc;
+  int32_t slot;        // leaf record of the conv leaf in the main program
+  int32_t mcol;        // the model's observable column
+  int32_t loc2free[kMaxLocal];
+  double lo, h;
 };
 
 // Faddeeva coefficients (Weideman 1994 rational series) as double-float pairs, filled on

@@ -18,13 +18,140 @@
 
 namespace gfi {
 
+// ---- event-side arithmetic ----------------------------------------------------------------
+// The per-event program runs in one of two arithmetics with the same code:
+//  ArF2  double-float pairs on the FP32 pipe (the normal path: FP64-accurate, no FP64
+//        instruction per event except the exact differences x - c of the data and a
+//        leaf constant);
+//  ArD   plain FP64, for the rare event whose density leaves the float exponent range
+//        (P < 2^-80 or > 2^125, or an intermediate that overflows), re-evaluated so that
+//        the result is the FP64 one.
+struct ArF2 {
+  using T = F2;
+  static __device__ __forceinline__ T zero() { return {0.f, 0.f}; }
+  static __device__ __forceinline__ T of(double x) { return df_split(x); }
+  static __device__ __forceinline__ T diff(double x, double c) { return df_split(x - c); }
+  static __device__ __forceinline__ T add(T a, T b) { return df_add(a, b); }
+  static __device__ __forceinline__ T sub(T a, T b) { return df_sub(a, b); }
+  static __device__ __forceinline__ T mul(T a, T b) { return df_mul(a, b); }
+  static __device__ __forceinline__ T mulf(T a, float b) { return df_mul_f(a, b); }
+  static __device__ __forceinline__ T neg(T a) { return df_neg(a); }
+  static __device__ __forceinline__ T rcp(T a) { return df_rcp(a); }
+  static __device__ __forceinline__ T sqrt_(T a) { return df_sqrt(a); }
+  static __device__ __forceinline__ T exp_(T a) { return df_exp_tab(a, s_exp_tab); }
+  static __device__ __forceinline__ T log_(T a) { return df_log_tab(a, s_log_tab); }
+  static __device__ __forceinline__ bool pos(T a) { return a.hi > 0.f; }
+  static __device__ __forceinline__ T two_inv_sqrt_pi() { return DFC(kTwoInvSqrtPi); }
+  static __device__ __forceinline__ void faddeeva(T x, T y, const WeidCoef& W, T& wr, T& wi) {
+    faddeeva_f2(x, y, W, wr, wi);
+  }
+};
+struct ArD {
+  using T = double;
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ T of(double x) { return x; }
+  static __device__ __forceinline__ T diff(double x, double c) { return x - c; }
+  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+  static __device__ __forceinline__ T mulf(T a, float b) { return a * (double)b; }
+  static __device__ __forceinline__ T neg(T a) { return -a; }
+  static __device__ __forceinline__ T rcp(T a) { return 1.0 / a; }
+  static __device__ __forceinline__ T sqrt_(T a) { return sqrt(a); }
+  static __device__ __forceinline__ T exp_(T a) { return df_exp(a); }
+  static __device__ __forceinline__ T log_(T a) { return df_log(a); }
+  static __device__ __forceinline__ bool pos(T a) { return a > 0.0; }
+  static __device__ __forceinline__ T two_inv_sqrt_pi() { return kTwoInvSqrtPi; }
+  static __device__ __forceinline__ void faddeeva(T x, T y, const WeidCoef& W, T& wr, T& wi) {
+    faddeeva_df(x, y, W, wr, wi);
+  }
+};
+
 // ---- shape functions of the normalisation grid (unnormalised r(x), d r / d local par) ----
 // Per-block constants of the leaf's shape, from theta once per block (FP64, then pairs);
 // each bin is then evaluated in pairs on the FP32 pipe.
 struct ShapeK {
   double x0;        // mu (Voigtian) or x0 (threshold)
   F2 a, b, c, d, e;
+  double rb[10];    // relativistic Breit-Wigner constants (relbw_consts)
+  double rb_dm0;    // and its dm0
 };
+
+// ---- relativistic Breit-Wigner line shape (Sec. 4: the P-wave D*+ line in the D*+ - D0
+// mass difference) ------------------------------------------------------------------------
+// f(x) = m Gamma(m) / ((m0^2 - m^2)^2 + m0^2 Gamma(m)^2), m = x + shift, m0 = dm0 + shift,
+// Gamma(m) = Gamma0 (q/q0)^{2L+1} (m0/m) B_L(z0)/B_L(z), q^2 = (s - A)(s - B)/(4 s),
+// A = (ma + mb)^2, B = (ma - mb)^2, z = q^2 R^2, B_L = 1, 1 + z, 9 + 3 z + z^2; zero at or
+// below threshold.  Parameters: dm0, Gamma0, shift, ma, mb, R (the last four fixed).
+// s - A is formed as (x - thr)(m + ma + mb), thr = ma + mb - shift, from the exact
+// difference x - thr: no cancellation near threshold.
+// Constants (the record's c[0..9]): -shift, m0, m0^2, thr, B, R^2,
+// k = Gamma0 B_L(z0) m0 / q0^{2L+1} (so Gamma = k q^{2L+1}/(m B_L(z))), 1/Gamma0,
+// dln Gamma/dm0 (independent of m), ma + mb.
+__device__ inline double rb_poly(int L, double z) {
+  return L == 0 ? 1.0 : L == 1 ? 1.0 + z : 9.0 + z * (3.0 + z);
+}
+__device__ inline void relbw_consts(const LeafDesc& Lf, const double* th, double* c) {
+  const double dm0 = th[Lf.par[0]], g0 = th[Lf.par[1]], shift = th[Lf.par[2]];
+  const double ma = th[Lf.par[3]], mb = th[Lf.par[4]], R = th[Lf.par[5]];
+  const int L = Lf.aux;
+  const double m0 = dm0 + shift, s0 = m0 * m0;
+  const double A = (ma + mb) * (ma + mb), B = (ma - mb) * (ma - mb);
+  const double thr = ma + mb - shift;
+  const double q02 = (dm0 - thr) * (m0 + ma + mb) * (s0 - B) / (4.0 * s0), z0 = q02 * R * R;
+  const double bl0 = rb_poly(L, z0);
+  const double dq02 = 2.0 * m0 * (s0 * s0 - A * B) / (4.0 * s0 * s0);  // d q0^2 / d m0
+  const double dbl0 = L == 0 ? 0.0 : L == 1 ? 1.0 : 3.0 + 2.0 * z0;
+  c[0] = -shift;
+  c[1] = m0;
+  c[2] = s0;
+  c[3] = thr;
+  c[4] = B;
+  c[5] = R * R;
+  c[6] = g0 * bl0 * m0 / pow(q02, L + 0.5);
+  c[7] = 1.0 / g0;
+  c[8] = -(L + 0.5) * dq02 / q02 + 1.0 / m0 + dbl0 * R * R * dq02 / bl0;
+  c[9] = ma + mb;
+}
+// f and, with G, df/dm0 and df/dGamma0 (unnormalised), in the arithmetic A.  cd: the
+// constants in FP64 (x + shift and x - thr enter as exact differences), c: the same in A.
+template <class A, bool G>
+__device__ __forceinline__ typename A::T relbw_f(double x, const double* cd,
+                                                 const typename A::T* c, int L, double pdm0,
+                                                 typename A::T& dm0, typename A::T& dg0) {
+  using T = typename A::T;
+  const T dx = A::diff(x, cd[3]);  // m - ma - mb
+  if (!A::pos(dx)) {
+    dm0 = dg0 = A::zero();
+    return A::zero();
+  }
+  const T m = A::diff(x, cd[0]);
+  const T s = A::mul(m, m);
+  const T sa = A::mul(dx, A::add(m, c[9]));  // s - (ma + mb)^2
+  const T q2 = A::mul(A::mul(sa, A::sub(s, c[4])), A::rcp(A::mulf(s, 4.f)));
+  const T z = A::mul(q2, c[5]);
+  const T one = A::of(1.0);
+  const T bl = L == 0 ? one
+             : L == 1 ? A::add(one, z)
+                      : A::add(A::mul(z, A::add(z, A::of(3.0))), A::of(9.0));
+  const T sq = A::sqrt_(q2);
+  const T qp = L == 0 ? sq : L == 1 ? A::mul(q2, sq) : A::mul(A::mul(q2, q2), sq);
+  const T g = A::mul(A::mul(c[6], qp), A::rcp(A::mul(m, bl)));
+  const T ds = A::mul(A::neg(A::diff(x, pdm0)), A::add(c[1], m));  // m0^2 - m^2, no cancellation
+  const T g2 = A::mul(g, g);
+  const T iD = A::rcp(A::add(A::mul(ds, ds), A::mul(c[2], g2)));
+  const T f = A::mul(A::mul(m, g), iD);
+  if (G) {
+    // df/dGamma0 = f/Gamma0 (1 - 2 m0^2 Gamma^2/D)
+    dg0 = A::mul(A::mul(f, c[7]), A::sub(one, A::mulf(A::mul(c[2], A::mul(g2, iD)), 2.f)));
+    // dGamma = Gamma dlnGamma/dm0;  dD = m0 (4 (m0^2 - m^2) + 2 Gamma^2) + 2 m0^2 Gamma dGamma
+    const T dg = A::mul(g, c[8]);
+    const T dD = A::add(A::mul(c[1], A::add(A::mulf(ds, 4.f), A::mulf(g2, 2.f))),
+                        A::mulf(A::mul(c[2], A::mul(g, dg)), 2.f));
+    dm0 = A::mul(A::sub(A::mul(m, dg), A::mul(f, dD)), iD);
+  }
+  return f;
+}
 
 // Voigtian: r = Re w(z)/(sigma sqrt(2 pi)), z = (x - mu)/(sigma sqrt 2) + i Gamma/(2 sigma sqrt 2).
 // a = 1/(sigma sqrt2), b = Im z, c = 1/(sigma sqrt(2 pi)), d = 1/sigma, e = a/2.
@@ -154,6 +281,18 @@ __device__ void make_leaf_record(const LeafDesc& L, const double* th, double N, 
       c[3] = 1.0 / N;
       break;
     }
+    case L_RELBW: {
+      rec[0] = 1.0 / N;
+      rec[1] = log(N);
+      rec[2] = dN[0] / N;
+      rec[3] = dN[1] / N;
+      rec[4] = L.aux;          // orbital angular momentum and dm0 (the other dlogN slots
+      rec[5] = th[L.par[0]];   // are unused)
+      relbw_consts(L, th, c);
+      break;
+    }
+    case L_CONV:
+      break;  // written by the convolution kernel (k_conv_sum) after this one
     case L_POLY: {
       // N = Q(hi) - Q(lo), Q(x) = sum_k a_k x^{k+1}/(k+1)
       double n = 0.0, phk = hi, plk = lo;
@@ -210,6 +349,10 @@ __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& 
   if (li >= 0 && threadIdx.x == 0) {
     const LeafDesc& L = P.leaf[li];
     if (L.kind == L_VOIGT) voigt_consts(theta[L.par[0]], theta[L.par[1]], theta[L.par[2]], *shk);
+    else if (L.kind == L_RELBW) {
+      relbw_consts(L, theta, shk->rb);
+      shk->rb_dm0 = theta[L.par[0]];
+    }
     else thresh_consts(theta[L.par[0]], theta[L.par[1]], theta[L.par[2]], *shk);
   }
   __syncthreads();
@@ -221,8 +364,14 @@ __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& 
       const double h = (L.hi - L.lo) / L.nbins;
       const double x = L.lo + (b + 0.5) * h;
       double dr[3];
-      if (L.kind == L_VOIGT) v[0] = voigt_r(x, *shk, W, dr);
-      else v[0] = thresh_r(x, *shk, dr);
+      if (L.kind == L_VOIGT) {
+        v[0] = voigt_r(x, *shk, W, dr);
+      } else if (L.kind == L_RELBW) {
+        v[0] = relbw_f<ArD, true>(x, shk->rb, shk->rb, L.aux, shk->rb_dm0, dr[0], dr[1]);
+        dr[2] = 0.0;
+      } else {
+        v[0] = thresh_r(x, *shk, dr);
+      }
       v[1] = dr[0];
       v[2] = dr[1];
       v[3] = dr[2];
@@ -281,55 +430,6 @@ __global__ void __launch_bounds__(kThreads) k_norm_1d(const Program* __restrict_
   norm_1d_block(P, W, theta, partials, counter, derived, blockIdx.x, gridDim.x, red, &last, sums,
                 &shk);
 }
-
-// ---- event-side arithmetic ----------------------------------------------------------------
-// The per-event program runs in one of two arithmetics with the same code:
-//  ArF2  double-float pairs on the FP32 pipe (the normal path: FP64-accurate, no FP64
-//        instruction per event except the exact differences x - c of the data and a
-//        leaf constant);
-//  ArD   plain FP64, for the rare event whose density leaves the float exponent range
-//        (P < 2^-80 or > 2^125, or an intermediate that overflows), re-evaluated so that
-//        the result is the FP64 one.
-struct ArF2 {
-  using T = F2;
-  static __device__ __forceinline__ T zero() { return {0.f, 0.f}; }
-  static __device__ __forceinline__ T of(double x) { return df_split(x); }
-  static __device__ __forceinline__ T diff(double x, double c) { return df_split(x - c); }
-  static __device__ __forceinline__ T add(T a, T b) { return df_add(a, b); }
-  static __device__ __forceinline__ T sub(T a, T b) { return df_sub(a, b); }
-  static __device__ __forceinline__ T mul(T a, T b) { return df_mul(a, b); }
-  static __device__ __forceinline__ T mulf(T a, float b) { return df_mul_f(a, b); }
-  static __device__ __forceinline__ T neg(T a) { return df_neg(a); }
-  static __device__ __forceinline__ T rcp(T a) { return df_rcp(a); }
-  static __device__ __forceinline__ T sqrt_(T a) { return df_sqrt(a); }
-  static __device__ __forceinline__ T exp_(T a) { return df_exp_tab(a, s_exp_tab); }
-  static __device__ __forceinline__ T log_(T a) { return df_log_tab(a, s_log_tab); }
-  static __device__ __forceinline__ bool pos(T a) { return a.hi > 0.f; }
-  static __device__ __forceinline__ T two_inv_sqrt_pi() { return DFC(kTwoInvSqrtPi); }
-  static __device__ __forceinline__ void faddeeva(T x, T y, const WeidCoef& W, T& wr, T& wi) {
-    faddeeva_f2(x, y, W, wr, wi);
-  }
-};
-struct ArD {
-  using T = double;
-  static __device__ __forceinline__ T zero() { return 0.0; }
-  static __device__ __forceinline__ T of(double x) { return x; }
-  static __device__ __forceinline__ T diff(double x, double c) { return x - c; }
-  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
-  static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
-  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
-  static __device__ __forceinline__ T mulf(T a, float b) { return a * (double)b; }
-  static __device__ __forceinline__ T neg(T a) { return -a; }
-  static __device__ __forceinline__ T rcp(T a) { return 1.0 / a; }
-  static __device__ __forceinline__ T sqrt_(T a) { return sqrt(a); }
-  static __device__ __forceinline__ T exp_(T a) { return df_exp(a); }
-  static __device__ __forceinline__ T log_(T a) { return df_log(a); }
-  static __device__ __forceinline__ bool pos(T a) { return a > 0.0; }
-  static __device__ __forceinline__ T two_inv_sqrt_pi() { return kTwoInvSqrtPi; }
-  static __device__ __forceinline__ void faddeeva(T x, T y, const WeidCoef& W, T& wr, T& wi) {
-    faddeeva_df(x, y, W, wr, wi);
-  }
-};
 
 // ---- per-chunk expansion of w(z) on sorted data ------------------------------------------
 // With the events sorted by the Voigtian's observable, a thread's chunk of kChunk
@@ -466,6 +566,35 @@ __device__ __forceinline__ typename A::T eval_leaf_s(const Instr& I, const doubl
         if (I.gidx[2] >= 0)
           sink(2, A::neg(A::mul(l, A::add(t, r[4]))));
       }
+      return l;
+    }
+    case L_RELBW: {
+      T dm, dg;
+      const T f = relbw_f<A, G>(x, rec + 10, c, (int)rec[4], rec[5], dm, dg);
+      const T l = A::mul(f, r[0]);
+      if (G) {
+        if (I.gidx[0] >= 0) sink(0, A::sub(A::mul(dm, r[0]), A::mul(l, r[2])));
+        if (I.gidx[1] >= 0) sink(1, A::sub(A::mul(dg, r[0]), A::mul(l, r[3])));
+      }
+      return l;
+    }
+    case L_CONV: {
+      // lattice table (k_conv_sum): C_i then dC_i/dtheta_l, rows of L + 1; linear in
+      // between (FP64 index arithmetic: convolutions serve binned or modest data)
+      const double* T_ = reinterpret_cast<const double*>(__double_as_longlong(rec[13]));
+      const int Lt = (int)rec[12];
+      const double sd = (x - rec[10]) * rec[11];
+      int k = (int)floor(sd);
+      k = k < 0 ? 0 : (k > Lt - 1 ? Lt - 1 : k);
+      const double u = sd - k;
+      const T l = A::mul(A::of(fma(u, T_[k + 1] - T_[k], T_[k])), r[0]);
+      if (G)
+        for (int j = 0; j < I.npar; ++j)
+          if (I.gidx[j] >= 0) {
+            const double* Tj = T_ + (size_t)(1 + j) * (Lt + 1);
+            sink(j, A::sub(A::mul(A::of(fma(u, Tj[k + 1] - Tj[k], Tj[k])), r[0]),
+                           A::mul(l, r[2 + j])));
+          }
       return l;
     }
     case L_POLY: {
@@ -1096,6 +1225,135 @@ static auto logsum_kernel(const Program& P) {
   return k_events_logsum<G, kLogLeaf, 0>;
 }
 
+// ---- ConvolutionPdf (Sec. 3): lattice tables ------------------------------------------
+// k_conv_points: the model subtree at the J model points and the resolution subtree at the
+// K offsets, in FP64 through the same interpreter (records from k_norm_1d), value and
+// gradient over the conv's local parameters, stored as float pairs.  One thread per point;
+// the first ceil(J / blockDim) blocks take model points, the rest resolution offsets.
+__global__ void __launch_bounds__(kThreads1D) k_conv_points(const ConvDesc* __restrict__ cdp,
+                                                            const __grid_constant__ WeidCoef W,
+                                                            const double* __restrict__ derived_g) {
+  extern __shared__ double dyn[];  // (kMaxStack + 1) nfree blockDim doubles
+  __shared__ Program P;
+  __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
+  const ConvDesc& cd = *cdp;
+  const int bd = blockDim.x, tid = threadIdx.x;
+  const int nbm = (cd.J + bd - 1) / bd;
+  const bool model = (int)blockIdx.x < nbm;
+  load_program(model ? cd.pm : cd.pr, P);
+  for (int k = tid; k < kMaxLeaf * kLeafRec + kMaxCoef; k += bd) rec[k] = derived_g[k];
+  __syncthreads();
+  const int t = (model ? (int)blockIdx.x : (int)blockIdx.x - nbm) * bd + tid;
+  const int npts = model ? cd.J : cd.K;
+  if (t >= npts) return;
+  double x[kMaxObs];
+#pragma unroll
+  for (int o = 0; o < kMaxObs; ++o) x[o] = 0.0;
+  if (model) x[cd.mcol] = cd.lo + (t - cd.kmax) * cd.h;
+  else x[kResidCol] = (cd.kmin + t) * cd.h;
+  const int nf = P.nfree;
+  double v = run_program<ArD, true>(P, rec, rec, x, W, dyn, nf, bd, tid);
+  double sc = 1.0;
+  if (P.root_log) {  // the subtree's value in the linear domain: e^s, gradient e^s ds
+    v = df_exp(v);
+    sc = v;
+  }
+  float2* out = model ? cd.mt : cd.rt;
+  const float vh = __double2float_rn(v);
+  out[t] = make_float2(vh, __double2float_rn(v - (double)vh));
+  for (int l = 0; l < cd.nloc; ++l) {
+    const double g = dyn[(size_t)cd.loc2free[l] * bd + tid] * sc;
+    const float gh = __double2float_rn(g);
+    out[(size_t)(1 + l) * npts + t] = make_float2(gh, __double2float_rn(g - (double)gh));
+  }
+}
+
+// k_conv_sum: C_i = h sum_k r_k m_{i - kmin - k + kmax} and its gradient rows (pairs,
+// resolution rows staged in shared memory), the table in FP64, then the trapezoid
+// normalisation N = h (C_0/2 + C_1 + ... + C_L/2) and dN across blocks (fixed order, last
+// block), which writes the conv leaf's record: 1/N, log N, dlogN/dtheta_l, and the
+// constants lo, 1/h, L and the table's address.
+__global__ void __launch_bounds__(kThreads1D) k_conv_sum(const ConvDesc* __restrict__ cdp,
+                                                         double* __restrict__ derived) {
+  extern __shared__ float2 rs[];  // two resolution rows of K pairs
+  __shared__ double red[(kThreads1D / 32) * (1 + kMaxLocal)];
+  __shared__ int last;
+  const ConvDesc& cd = *cdp;
+  const int bd = blockDim.x, tid = threadIdx.x;
+  const int i = blockIdx.x * bd + tid;
+  const int K = cd.K, J = cd.J, L = cd.L, nq = 1 + cd.nloc;
+  const bool on = i <= L;
+  const int j0 = i - cd.kmin + cd.kmax;  // model index for k = 0 (then j0 - k)
+  F2 tr[1 + kMaxLocal];
+  for (int q = 0; q < nq; ++q) {
+    // rows: q = 0: r with m; q = l + 1: dr_l with m, then r with dm_l
+    __syncthreads();
+    for (int k = tid; k < K; k += bd) {
+      rs[k] = cd.rt[(size_t)q * K + k];
+      rs[K + k] = cd.rt[k];
+    }
+    __syncthreads();
+    LazyAcc acc;
+    if (on) {
+      const float2* m0 = cd.mt + j0;
+      for (int k = 0; k < K; ++k) {
+        float p, e;
+        const float2 a = rs[k], b = m0[-k];
+        prod_pe(F2{a.x, a.y}, F2{b.x, b.y}, p, e);
+        acc.add(p, e);
+        if ((k & 7) == 7) acc.renorm();
+      }
+      if (q > 0) {
+        const float2* mq = cd.mt + (size_t)q * J + j0;
+        for (int k = 0; k < K; ++k) {
+          float p, e;
+          const float2 a = rs[K + k], b = mq[-k];
+          prod_pe(F2{a.x, a.y}, F2{b.x, b.y}, p, e);
+          acc.add(p, e);
+          if ((k & 7) == 7) acc.renorm();
+        }
+      }
+    }
+    const double c = on ? df_to(acc.get()) * cd.h : 0.0;
+    if (on) cd.ct[(size_t)q * (L + 1) + i] = c;
+    const double w = (i == 0 || i == L) ? 0.5 : 1.0;
+    tr[q] = df_split(w * c);
+  }
+  const int stride = 1 + kMaxLocal;
+  block_sum_pairs([&](int q) -> F2 { return tr[q]; }, nq, red,
+                  cd.partials + (size_t)blockIdx.x * stride);
+  if (!arrive_last_of(cd.counter, gridDim.x, &last)) return;
+  __shared__ double sums[1 + kMaxLocal];
+  reduce_partials(cd.partials, gridDim.x, stride, nq, sums, red);
+  __syncthreads();
+  if (tid == 0) {
+    double* r = derived + (size_t)cd.slot * kLeafRec;
+    for (int k = 0; k < kLeafRec; ++k) r[k] = 0.0;
+    const double N = sums[0] * cd.h;
+    r[0] = 1.0 / N;
+    r[1] = log(N);
+    for (int l = 0; l < cd.nloc; ++l) r[2 + l] = sums[1 + l] * cd.h / N;
+    r[10] = cd.lo;
+    r[11] = 1.0 / cd.h;
+    r[12] = L;
+    r[13] = __longlong_as_double(reinterpret_cast<long long>(cd.ct));
+    *cd.counter = 0u;
+  }
+}
+
+cudaError_t launch_conv(const ConvDesc& host, const ConvDesc* dev, const WeidCoef& W, int nfree,
+                        double* derived, cudaStream_t st) {
+  const int bd = kThreads1D;
+  const int nb = (host.J + bd - 1) / bd + (host.K + bd - 1) / bd;
+  const size_t dyn = (size_t)(kMaxStack + 1) * std::max(nfree, 1) * bd * sizeof(double);
+  k_conv_points<<<nb, bd, dyn, st>>>(dev, W, derived);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_conv_sum<<<(host.L + 1 + bd - 1) / bd, bd, 2 * (size_t)host.K * sizeof(float2), st>>>(dev,
+                                                                                         derived);
+  return cudaGetLastError();
+}
+
 // ---- batched tick: every waiting 1D fit in one persistent launch -----------------------
 // Shared by the two tick kernels: find the item's fit and bring its program into shared
 // memory when it changes (blocks walk the items in increasing order).
@@ -1260,6 +1518,9 @@ cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCo
 // Called once per device when a context is created: never inside a stream capture.
 void prepare_kernels_1d() {
   upload_df_tables();
+  cudaFuncSetAttribute(k_conv_points, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_conv_sum, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       2 * kConvMaxOffsets * (int)sizeof(float2));
   cudaFuncSetAttribute(k_events_1d<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
   cudaFuncSetAttribute(k_events_1d<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,

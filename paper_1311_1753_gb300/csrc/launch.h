@@ -25,6 +25,10 @@ cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCo
 int events_1d_blocks_per_sm(bool grad, size_t smem);  // also opts in to large shared memory
 int events_logsum_blocks_per_sm(const Program& P);  // the direct log-sum kernel
 void prepare_kernels_1d();
+// ConvolutionPdf tables of one node (after launch_norm_1d; before the event pass):
+// host: the descriptor's sizes, dev: its device copy
+cudaError_t launch_conv(const ConvDesc& host, const ConvDesc* dev, const WeidCoef& W, int nfree,
+                        double* derived, cudaStream_t st);
 // Sort (key, index) pairs ascending by the FP64 key (k_sort.cu): perm_tmp receives
 // 0 .. n-1, perm_out the permutation, key_out the sorted keys.  temp == nullptr: only
 // sets *temp_bytes to the scratch size the sort needs.

@@ -74,6 +74,9 @@ def _load():
         "gf_pdf_threshold": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, _I], C.c_int),
         "gf_pdf_poly": ([vp, C.c_int, C.c_int, _I, _I], C.c_int),
         "gf_pdf_add": ([vp, C.c_int, _I, _I, _I], C.c_int),
+        "gf_pdf_relbw": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                          C.c_int, _I], C.c_int),
+        "gf_pdf_conv": ([vp, C.c_int, C.c_int, C.c_int, _I], C.c_int),
         "gf_pdf_prod": ([vp, C.c_int, _I, _I], C.c_int),
         "gf_pdf_dalitz": ([vp, C.c_int, C.c_int, C.POINTER(DalitzKin), C.c_int,
                            C.POINTER(Resonance), _I], C.c_int),
@@ -218,6 +221,19 @@ class Context:
     def poly(self, obs, coefs):
         arr = (C.c_int * len(coefs))(*coefs)
         return self._id(lib.gf_pdf_poly, obs, len(coefs), arr)
+
+    def relbw(self, obs, dm0, gamma0, shift, ma, mb, radius, spin=1):
+        """Relativistic Breit-Wigner line shape in x = m - shift (parameter ids; shift,
+        ma, mb and radius fixed)."""
+        return self._id(lib.gf_pdf_relbw, obs, dm0, gamma0, shift, ma, mb, radius, int(spin))
+
+    def conv(self, obs, model, resolution, lattice=None):
+        """ConvolutionPdf: model (over obs) convolved with resolution (over its own
+        residual observable) on a lattice of `lattice` bins (default 1000)."""
+        node = self._id(lib.gf_pdf_conv, obs, model, resolution)
+        if lattice is not None:
+            self.set_norm_grid(node, int(lattice))
+        return node
 
     def add(self, nodes, fracs):
         a = (C.c_int * len(nodes))(*nodes)
