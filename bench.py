@@ -616,6 +616,67 @@ def run_binned(torch, gf, nb=4000, steps=50):
     return out
 
 
+def zach_model(gf, lattice=860, nbins=4000):
+    """The paper's binned D*+ width fit (Sec. 4): a P-wave relativistic Breit-Wigner in the
+    D*+ - D0 mass difference convolved with a resolution of three Gaussians, plus a
+    threshold background; free: dm0, Gamma0, the three widths and two fractions of the
+    resolution, the background slope and the signal fraction."""
+    lo, hi = synth.VOIGT_RANGE
+    ctx = gf.Context(0, gf.GF_FP64)
+    x = ctx.observable("dm", lo, hi)
+    r = ctx.observable("res", -0.002, 0.002)
+    d0, pic = 1.86484, 0.13957
+    dm0 = ctx.parameter("dm0", 0.14543, 1e-5, 0.143, 0.148)
+    g0 = ctx.parameter("gamma0", 8.3e-5, 1e-5, 1e-6, 1e-3)
+    cst = [ctx.parameter(nm, v, 1e-3, fixed=True)
+           for nm, v in (("shift", d0), ("mD0", d0), ("mpi", pic), ("R", 1.5))]
+    sig = ctx.relbw(x, dm0, g0, *cst, spin=1)
+    ctx.set_norm_grid(sig, nbins)
+    zero = ctx.parameter("zero", 0.0, 1e-5, fixed=True)
+    s = [ctx.parameter(f"s{k}", v, 1e-5, 1e-6, 2e-3) for k, v in enumerate((2e-4, 4.5e-4, 9e-4))]
+    f = [ctx.parameter("f0", 0.6, 0.01, 0.0, 1.0), ctx.parameter("f1", 0.3, 0.01, 0.0, 1.0)]
+    res = ctx.add([ctx.gauss(r, zero, sk) for sk in s], f)
+    conv = ctx.conv(x, sig, res, lattice)
+    x0 = ctx.parameter("x0", lo, 1e-4, fixed=True)
+    pw = ctx.parameter("power", 0.5, 0.01, fixed=True)
+    c = ctx.parameter("c", 20.0, 0.5, 0.0, 200.0)
+    fs = ctx.parameter("fsig", 0.3, 0.01, 0.0, 1.0)
+    th = ctx.threshold(x, x0, pw, c)
+    ctx.set_norm_grid(th, nbins)
+    root = ctx.add([conv, th], [fs])
+    return ctx, root, [x]
+
+
+def run_zach(torch, gf, nb=4000, steps=50):
+    """Binned chi-squared fit of the line shape x resolution + background on the 10^7
+    events of the headline workload in 4000 bins: evaluation time (norm grids, the two
+    convolution launches, the bin pass) and a fit from a displaced start."""
+    lo, hi = synth.VOIGT_RANGE
+    x = synth.voigt_threshold_events(10_000_000, **synth.VOIGT_TRUTH, lo=lo, hi=hi,
+                                     seed=synth.SEED_VOIGT)
+    counts = np.histogram(x, nb, (lo, hi))[0].astype(float)
+    ctx, root, obs = zach_model(gf)
+    ctx.set_binned_data(root, obs, [nb], counts)
+    ctx.set_metric(gf.GF_METRIC_CHISQ)
+    th0 = np.array([ctx.value(p) for p in ctx.free_params()])
+    r = time_steps(torch, ctx, [th0 * (1 + 1e-4 * k) for k in range(4)], steps, 3, flush=False)
+    start = th0 * np.array([1.0001, 1.2, 1.1, 0.9, 1.05, 0.95, 1.02, 1.1, 0.9])
+    for k, pid in enumerate(ctx.free_params()):
+        ctx.set_value(pid, start[k])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f = ctx.fit(tol=1e-6)
+    sec = time.perf_counter() - t0
+    out = {"bins": nb, "lattice": 860, "resolution_offsets": 161, "free_params": len(th0),
+           "us_per_eval": 1e3 * float(np.mean(r["step_ms"])),
+           "event_kernel_us": 1e3 * float(np.mean(r["kernel_ms"])),
+           "launches_per_eval": r["launches"] / steps,
+           "fit_seconds": sec, "fit_calls": f["n_calls"], "fit_status": f["status"],
+           "chi2_per_bin": f["nll"] / nb}
+    ctx.close()
+    return out
+
+
 def run_extra(torch, gf, args):
     """Secondary measurements: configs 1, 3, 4 evaluation rates (and, on request, fit
     times and the serving study)."""
@@ -630,6 +691,7 @@ def run_extra(torch, gf, args):
     ctx.close()
     out["config1_exp_hbm_sweep"] = run_exp_sweep(torch, gf)
     out["binned_voigt_4000"] = run_binned(torch, gf)
+    out["binned_relbw_conv_4000"] = run_zach(torch, gf)
     # config 3 (FP64, 1e6 events, cached per-event amplitudes, Gram normalisation)
     spec = dalitz_spec()
     data = dalitz_events_gpu(gf, spec, 1_000_000, synth.SEED_DALITZ_EVENTS)

@@ -27,7 +27,8 @@ _lock = threading.Lock()
 _lib = None
 
 # Leaf and combinator codes, as in oracle.c.
-EXP, GAUSS, VOIGT, THRESH, POLY, RELBW, ADD, PROD, CONV = 1, 2, 3, 4, 5, 6, 10, 11, 12
+EXP, GAUSS, VOIGT, THRESH, POLY, RELBW, ADD, PROD, CONV, MAPPED, COMPOSITE = (
+    1, 2, 3, 4, 5, 6, 10, 11, 12, 13, 14)
 MAXPAR, MAXCHILD = 16, 8
 
 
@@ -186,6 +187,17 @@ class Model1D:
         lattice of `lattice` bins of obs's range."""
         return self._node(CONV, obs, [], [model, resolution], aux=int(lattice))
 
+    def mapped(self, obs, children, bounds):
+        """MappedPdf (Sec. 3): child k on [b_{k-1}, b_k) of obs's range; bounds are the
+        n-1 interior boundaries (parameter indices, normally fixed)."""
+        assert len(bounds) == len(children) - 1
+        return self._node(MAPPED, obs, list(bounds), list(children))
+
+    def composite(self, obs, core, shell):
+        """CompositePdf (Sec. 3): shell(core(x)), both unnormalised leaf shapes, the
+        result normalised on obs's range (midpoint rule, nbins)."""
+        return self._node(COMPOSITE, obs, [], [core, shell])
+
     def add(self, children, fracs):
         assert len(fracs) == len(children) - 1
         return self._node(ADD, 0, list(fracs), list(children))
@@ -202,7 +214,9 @@ class Model1D:
 
     def _cols(self, cols):
         cols = [_f64(c) for c in cols]
-        nres = sum(1 for nd in self.nodes if nd.type == CONV)  # one residual observable each
+        # one auxiliary observable per convolution (its residual variable) and per
+        # composite (its shell's argument), declared after the data observables
+        nres = sum(1 for nd in self.nodes if nd.type in (CONV, COMPOSITE))
         if len(cols) != len(self.lo) - nres or any(len(c) != len(cols[0]) for c in cols):
             raise ValueError(f"the model has {len(self.lo) - nres} data observables: one "
                              "column each, all of the same length")

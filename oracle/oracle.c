@@ -133,9 +133,17 @@ enum {
                    *                                     aux: L (orbital angular momentum) */
   ORC_ADD = 10,   /* sum_k f_k P_k + (1 - sum f) P_last  par: f_0 .. f_{n-2}  (AddPdf)   */
   ORC_PROD = 11,  /* prod_k P_k (distinct observables)                        (ProdPdf)  */
-  ORC_CONV = 12   /* ConvolutionPdf (Sec. 3): model (child 0, observable obs) convolved
+  ORC_CONV = 12,  /* ConvolutionPdf (Sec. 3): model (child 0, observable obs) convolved
                    * with a resolution (child 1, over its own residual observable), on a
                    * lattice of aux bins of obs's range; see conv_table              */
+  ORC_MAPPED = 13,   /* MappedPdf (Sec. 3): child k on [b_{k-1}, b_k) of obs's range
+                      * (b_{-1} = lo, b_{n-1} = hi; par: the n-1 interior boundaries),
+                      * each child normalised on the whole range, the result normalised
+                      * by the midpoint rule on nbins bins                              */
+  ORC_COMPOSITE = 14 /* CompositePdf (Sec. 3): f(g(x)) with g the core leaf (child 0, its
+                      * unnormalised shape over obs) and f the shell leaf (child 1:
+                      * exponential, Gaussian or polynomial, unnormalised shape of the
+                      * core's value), normalised by the midpoint rule on nbins bins     */
 };
 
 #define ORC_MAXPAR 16
@@ -289,6 +297,21 @@ static double leaf_shape(const orc_node* nd, const double* p, double x, double* 
   return NAN;
 }
 
+/* d f/d u of an analytic shell shape f(u) (exponential, Gaussian, polynomial). */
+static double shell_du(const orc_node* nd, const double* p, double u) {
+  if (nd->type == ORC_EXP) return p[nd->par[0]] * exp(p[nd->par[0]] * u);
+  if (nd->type == ORC_GAUSS) {
+    double mu = p[nd->par[0]], s = p[nd->par[1]], t = (u - mu) / s;
+    return -t / s * exp(-0.5 * t * t);
+  }
+  double d = 0, uk = 1; /* polynomial: sum_k k a_k u^{k-1} */
+  for (int k = 1; k < nd->npar; ++k) {
+    d += k * p[nd->par[k]] * uk;
+    uk *= u;
+  }
+  return d;
+}
+
 static int is_leaf(int type) { return type >= ORC_EXP && type <= ORC_RELBW; }
 static int grid_normalised(int type) {
   return type == ORC_VOIGT || type == ORC_THRESH || type == ORC_RELBW;
@@ -379,6 +402,36 @@ int orc_norms(const orc_model* m, const double* p, int np, double* N, double* dN
   return 0;
 }
 
+static double node_value(const orc_model* m, int i, const double* p, int np,
+                         const orc_state* st, const double* x, double* g);
+
+/* MappedPdf / CompositePdf before their normalisation, with the gradient g[np]:
+ *  mapped:    P_k(x) for the interval k holding x (the last interval is closed);
+ *  composite: f(u), u = g(x) (both unnormalised leaf shapes), d/dtheta = df/dtheta_f +
+ *             f'(u) du/dtheta_g. */
+static double mapped_raw(const orc_model* m, int i, const double* p, int np,
+                         const orc_state* st, const double* x, double* g) {
+  const orc_node* nd = &m->nodes[i];
+  double xv = x[nd->obs];
+  if (nd->type == ORC_MAPPED) {
+    int k = 0;
+    while (k < nd->nchild - 1 && xv >= p[nd->par[k]]) ++k;
+    return node_value(m, nd->child[k], p, np, st, x, g);
+  }
+  const orc_node* core = &m->nodes[nd->child[0]];
+  const orc_node* shell = &m->nodes[nd->child[1]];
+  double dc[ORC_MAXPAR], ds[ORC_MAXPAR];
+  double u = leaf_shape(core, p, xv, g ? dc : NULL);
+  double f = leaf_shape(shell, p, u, g ? ds : NULL);
+  if (g) {
+    memset(g, 0, sizeof(double) * np);
+    double fu = shell_du(shell, p, u);
+    for (int k = 0; k < core->npar; ++k) g[core->par[k]] += fu * dc[k];
+    for (int k = 0; k < shell->npar; ++k) g[shell->par[k]] += ds[k];
+  }
+  return f;
+}
+
 /* Normalised value of a node at one event, optionally with its gradient g[np]. */
 static double node_value(const orc_model* m, int i, const double* p, int np,
                          const orc_state* st, const double* x, double* g) {
@@ -394,6 +447,13 @@ static double node_value(const orc_model* m, int i, const double* p, int np,
       for (int k = 0; k < np; ++k) g[k] = -v * dN[(size_t)i * np + k] / N[i];
       for (int k = 0; k < nd->npar; ++k) g[nd->par[k]] += dr[k] / N[i];
     }
+    return v;
+  }
+  if (nd->type == ORC_MAPPED || nd->type == ORC_COMPOSITE) {
+    /* unnormalised value (mapped_raw), divided by the grid normalisation */
+    double v = mapped_raw(m, i, p, np, st, x, g) / N[i];
+    if (g)
+      for (int q = 0; q < np; ++q) g[q] = g[q] / N[i] - v * dN[(size_t)i * np + q] / N[i];
     return v;
   }
   if (nd->type == ORC_CONV) {
@@ -590,6 +650,25 @@ static int state_init(const orc_model* m, const double* p, int np, orc_state* st
   if (orc_norms(m, p, np, st->N, st->dN)) { state_free(m, st); return -1; }
   for (int i = 0; i < m->nnodes; ++i)
     if (m->nodes[i].type == ORC_CONV && conv_table(m, i, p, np, st)) { state_free(m, st); return -1; }
+  /* MappedPdf / CompositePdf: midpoint rule over their observable's range */
+  for (int i = 0; i < m->nnodes; ++i) {
+    const orc_node* nd = &m->nodes[i];
+    if (nd->type != ORC_MAPPED && nd->type != ORC_COMPOSITE) continue;
+    double lo = m->lo[nd->obs], hi = m->hi[nd->obs], h = (hi - lo) / m->nbins;
+    double x[16] = {0};
+    double* g = (double*)malloc(sizeof(double) * (np > 0 ? np : 1));
+    orc_acc s = {0, 0};
+    orc_acc* ds = (orc_acc*)calloc(np > 0 ? np : 1, sizeof(orc_acc));
+    for (int b = 0; b < m->nbins; ++b) {
+      x[nd->obs] = lo + (b + 0.5) * h;
+      acc_add(&s, mapped_raw(m, i, p, np, st, x, g));
+      for (int q = 0; q < np; ++q) acc_add(&ds[q], g[q]);
+    }
+    st->N[i] = h * acc_get(&s);
+    for (int q = 0; q < np; ++q) st->dN[(size_t)i * np + q] = h * acc_get(&ds[q]);
+    free(g);
+    free(ds);
+  }
   return 0;
 }
 

@@ -829,3 +829,88 @@ def test_relbw_gradient_fd():
         pm[k] -= h
         fd = (m.nll([x], pp) - m.nll([x], pm)) / (2 * h)
         assert abs(fd / g[k] - 1) < 1e-7, (k, fd, g[k])
+
+
+# --------------------------------------------------------------------------------
+# MappedPdf and CompositePdf (Sec. 3)
+# --------------------------------------------------------------------------------
+def test_mapped_two_gaussians_piecewise_closed_form():
+    """Child k on its interval, each child normalised on the whole range: against the
+    truncated normal densities of scipy, normalised by the exact piecewise integral (the
+    boundary on a grid edge: the midpoint rule then errs by O(h^2) only)."""
+    lo, hi, nb = -2.0, 4.0, 6000
+    b = lo + 2500 * (hi - lo) / nb
+    m = oracle.Model1D([(lo, hi)], nbins=nb)
+    g1 = m.gauss(0, m.param(0.3), m.param(0.5))
+    g2 = m.gauss(0, m.param(1.8), m.param(1.1))
+    m.mapped(0, [g1, g2], [m.param(b)])
+    xs = np.linspace(lo, hi, 997)
+    P = np.exp(m.logpdf([xs]))
+    t1 = stats.truncnorm((lo - 0.3) / 0.5, (hi - 0.3) / 0.5, loc=0.3, scale=0.5)
+    t2 = stats.truncnorm((lo - 1.8) / 1.1, (hi - 1.8) / 1.1, loc=1.8, scale=1.1)
+    Z = (t1.cdf(b) - t1.cdf(lo)) + (t2.cdf(hi) - t2.cdf(b))
+    ref = np.where(xs < b, t1.pdf(xs), t2.pdf(xs)) / Z
+    h = (hi - lo) / nb
+    assert np.max(np.abs(P / ref - 1)) < 4 * h * h
+
+
+def test_mapped_identical_children_is_the_child():
+    lo, hi = 0.0, 10.0
+    m = oracle.Model1D([(lo, hi)], nbins=20000)
+    a = m.param(-0.4)
+    e1, e2, e3 = m.exp(0, a), m.exp(0, a), m.exp(0, a)
+    m.mapped(0, [e1, e2, e3], [m.param(3.0), m.param(7.5)])
+    xs = np.linspace(lo, hi, 301)
+    ref = -0.4 * np.exp(-0.4 * xs) / np.expm1(-0.4 * 10.0)
+    assert np.max(np.abs(np.exp(m.logpdf([xs])) / ref - 1)) < ((hi - lo) / 20000) ** 2
+
+
+def test_composite_exp_of_linear_is_exponential():
+    """exp(a g(x)) with the linear core g = c0 + c1 x is the exponential of rate a c1."""
+    lo, hi, nb = 0.0, 5.0, 10000
+    m = oracle.Model1D([(lo, hi), (-50.0, 50.0)], nbins=nb)
+    core = m.poly(0, [m.param(0.7), m.param(1.3)])
+    shell = m.exp(1, m.param(-0.45))
+    m.composite(0, core, shell)
+    xs = np.linspace(lo, hi, 211)
+    rate = -0.45 * 1.3
+    ref = rate * np.exp(rate * xs) / np.expm1(rate * hi)
+    # the second observable only carries the shell's range: one data column
+    P = np.exp(oracle_logpdf_1col(m, xs))
+    assert np.max(np.abs(P / ref - 1)) < 2 * ((hi - lo) / nb) ** 2
+
+
+def test_composite_gauss_of_linear_is_gauss():
+    """A Gaussian shell (mu, s) of the core c0 + c1 x is a Gaussian in x of mean
+    (mu - c0)/c1 and width s/|c1| (scipy's truncated normal)."""
+    lo, hi, nb = -3.0, 3.0, 12000
+    c0, c1, mu, s = 0.4, -1.7, 0.9, 1.2
+    m = oracle.Model1D([(lo, hi), (-50.0, 50.0)], nbins=nb)
+    m.composite(0, m.poly(0, [m.param(c0), m.param(c1)]), m.gauss(1, m.param(mu), m.param(s)))
+    xs = np.linspace(lo, hi, 301)
+    mx, sx = (mu - c0) / c1, s / abs(c1)
+    ref = stats.truncnorm.pdf(xs, (lo - mx) / sx, (hi - mx) / sx, loc=mx, scale=sx)
+    P = np.exp(oracle_logpdf_1col(m, xs))
+    assert np.max(np.abs(P / ref - 1)) < 2 * ((hi - lo) / nb) ** 2 * 4
+
+
+def oracle_logpdf_1col(m, xs):
+    return m.logpdf([xs])
+
+
+@pytest.mark.parametrize("which", ["mapped", "composite"])
+def test_mapped_composite_gradient_fd(which):
+    x = synth.exp_events(2000, -0.5, 0.0, 5.0, seed=9)
+    if which == "mapped":
+        m = oracle.Model1D([(0.0, 5.0)], nbins=4000)
+        g = m.gauss(0, m.param(1.0), m.param(0.8))
+        e = m.exp(0, m.param(-0.6))
+        po = m.poly(0, [m.param(1.0), m.param(0.3)])
+        m.mapped(0, [g, e, po], [m.param(1.7), m.param(3.2)])
+        idx = [0, 1, 2, 4]
+    else:
+        m = oracle.Model1D([(0.0, 5.0), (-50.0, 50.0)], nbins=4000)
+        m.composite(0, m.poly(0, [m.param(0.2), m.param(0.9), m.param(-0.05)]),
+                    m.gauss(1, m.param(1.0), m.param(1.5)))
+        idx = [0, 1, 2, 3, 4]
+    _fd_check(lambda q: m.nll([x], q, grad=True), m.p, idx, rel=2e-6)
