@@ -119,6 +119,18 @@ int gf_pdf_relbw(gf_ctx* ctx, int obs, int dm0, int gamma0, int shift, int ma, i
  * it).  At most 2 convolutions per tree, none nested, at most 8 free parameters in the
  * model and resolution together. */
 int gf_pdf_conv(gf_ctx* ctx, int obs, int model, int resolution, int* node);
+/* MappedPdf (Sec. 3): nodes[k] on [b_{k-1}, b_k) of obs's range (b_{-1} = lo; the last
+ * interval is closed at hi), bounds the n - 1 interior boundaries as parameter ids (fixed;
+ * increasing), 2 <= n <= 4.  Each component is normalised on its own range as usual; the
+ * piecewise result is normalised by the midpoint rule on the node's grid
+ * (gf_set_norm_grid, default 10,000 bins). */
+int gf_pdf_mapped(gf_ctx* ctx, int obs, int n, const int* nodes, const int* bounds, int* node);
+/* CompositePdf (Sec. 3): f(g(x)) with g the core leaf (over obs) and f the shell leaf (an
+ * exponential, Gaussian or polynomial node over any observable, whose range is ignored),
+ * both as unnormalised shapes; the result is normalised by the midpoint rule on the node's
+ * grid (default 10,000 bins).  A tree holds at most 2 MappedPdf/CompositePdf nodes, not
+ * nested in one another or in a convolution, with at most 8 free parameters each. */
+int gf_pdf_composite(gf_ctx* ctx, int obs, int core, int shell, int* node);
 /* AddPdf (Sec. 3): sum_{k<n-1} f_k P_k + (1 - sum f) P_{n-1}; fracs has n-1 ids, n <= 8. */
 int gf_pdf_add(gf_ctx* ctx, int n, const int* nodes, const int* fracs, int* node);
 /* ProdPdf (Sec. 3, Listing 2): prod_k P_k; the factors must use distinct observables. */

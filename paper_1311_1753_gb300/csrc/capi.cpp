@@ -140,6 +140,7 @@ static void free_dev(gf_ctx* ctx) {
   cudaFree(d.bw);
   cudaFree(d.bs2);
   for (void* p : d.conv_bufs) cudaFree(p);
+  for (void* p : d.gn_bufs) cudaFree(p);
   for (auto& g : d.graph)
     if (g) cudaGraphExecDestroy(g);
   d = DevState();
@@ -334,6 +335,41 @@ int gf_pdf_conv(gf_ctx* ctx, int obs, int model, int resolution, int* node) {
   return add_node(ctx, std::move(nd), node);
 }
 
+int gf_pdf_mapped(gf_ctx* ctx, int obs, int n, const int* nodes, const int* bounds, int* node) {
+  if (!ctx) return GF_EINVAL;
+  if (!valid_obs(ctx, obs) || n < 2 || n > 4 || !nodes || !bounds)
+    return set_error(ctx, GF_EINVAL, "MappedPdf: 2..4 components over one observable");
+  NodeDef nd;
+  nd.type = N_MAPPED;
+  nd.obs = obs;
+  for (int k = 0; k < n; ++k) {
+    if (!valid_node(ctx, nodes[k]) || ctx->nodes[nodes[k]].type == N_DALITZ)
+      return set_error(ctx, GF_EINVAL, "MappedPdf: unknown or non-1D component");
+    nd.children.push_back(nodes[k]);
+  }
+  for (int k = 0; k < n - 1; ++k) {
+    if (!valid_par(ctx, bounds[k])) return set_error(ctx, GF_EINVAL, "MappedPdf: unknown boundary id");
+    nd.pars.push_back(bounds[k]);
+  }
+  return add_node(ctx, std::move(nd), node);
+}
+
+int gf_pdf_composite(gf_ctx* ctx, int obs, int core, int shell, int* node) {
+  if (!ctx) return GF_EINVAL;
+  if (!valid_obs(ctx, obs) || !valid_node(ctx, core) || !valid_node(ctx, shell) || core == shell)
+    return set_error(ctx, GF_EINVAL, "CompositePdf: bad observable or nodes");
+  const int ct = ctx->nodes[core].type, st = ctx->nodes[shell].type;
+  if (!(ct >= N_EXP && ct <= N_RELBW) || ctx->nodes[core].obs != obs)
+    return set_error(ctx, GF_EINVAL, "CompositePdf: the core is a leaf over the observable");
+  if (st != N_EXP && st != N_GAUSS && st != N_POLY)
+    return set_error(ctx, GF_EINVAL, "CompositePdf: the shell is an exponential, Gaussian or polynomial");
+  NodeDef nd;
+  nd.type = N_COMPOSITE;
+  nd.obs = obs;
+  nd.children = {core, shell};
+  return add_node(ctx, std::move(nd), node);
+}
+
 int gf_pdf_add(gf_ctx* ctx, int n, const int* nodes, const int* fracs, int* node) {
   if (!ctx) return GF_EINVAL;
   if (n < 2 || n > kMaxLocal || !nodes || !fracs)
@@ -405,6 +441,8 @@ int gf_set_norm_grid(gf_ctx* ctx, int node, int nbins_x, int nbins_y) {
   } else if (nd.type == N_CONV) {
     if (nbins_x < 1 || nbins_x > kConvMaxLattice)
       return set_error(ctx, GF_EINVAL, "convolution lattice: 1..65536 bins");
+  } else if (nd.type == N_MAPPED || nd.type == N_COMPOSITE) {
+    if (nbins_x < 1 || nbins_x > (1 << 24)) return set_error(ctx, GF_EINVAL, "grid: 1..2^24 bins");
   } else {
     return set_error(ctx, GF_EINVAL, "node has an analytic normalisation");
   }
@@ -483,6 +521,14 @@ struct ConvInfo {
   Program pm{}, pr{};
 };
 
+// A MappedPdf or CompositePdf found by the compiler: its body as a program of its own
+// (the grid normalisation evaluates it at midpoints), also copied into the main program.
+struct GNInfo {
+  int node = -1, mcol = -1, slot = -1;
+  std::vector<int> loc;
+  Program body{};
+};
+
 int first_leaf_obs(const gf_ctx* ctx, int id) {
   const NodeDef& nd = ctx->nodes[id];
   if (nd.type >= N_EXP && nd.type <= N_RELBW) return nd.obs;
@@ -502,9 +548,12 @@ struct Compiler {
   int resid_obs = -1, conv_mobs = -1;
   std::vector<int>* conv_pars = nullptr;
   std::vector<ConvInfo> convs;
+  std::vector<GNInfo> gns;
+  bool raw_next = false;  // the next leaf keeps its unnormalised shape (CompositePdf core)
 
   int need(int id) {
     const NodeDef& nd = ctx->nodes[id];
+    if (nd.type == N_MAPPED) return 3;  // component, indicator, running sum
     if (nd.type != N_ADD && nd.type != N_PROD) return 1;
     std::vector<int> nn;
     for (int c : nd.children) nn.push_back(need(c));
@@ -559,9 +608,10 @@ struct Compiler {
       L.kind = nd.type;  // N_EXP..N_RELBW coincide with L_EXP..L_RELBW
       L.obs = col;
       L.npar = (int)nd.pars.size();
-      L.aux = nd.aux;
+      L.aux = nd.aux | (raw_next ? kRawLeaf : 0);
       for (int k = 0; k < L.npar; ++k) L.par[k] = nd.pars[k];
-      L.nbins = (nd.type == N_VOIGT || nd.type == N_THRESH || nd.type == N_RELBW) ? nd.nbx : 0;
+      L.nbins = (!raw_next && (nd.type == N_VOIGT || nd.type == N_THRESH || nd.type == N_RELBW))
+                    ? nd.nbx : 0;
       L.lo = ctx->obs[nd.obs].lo;
       L.hi = ctx->obs[nd.obs].hi;
       Instr I{};
@@ -635,6 +685,122 @@ struct Compiler {
       if (!emit(I)) return -1;
       obs_used.push_back(nd.obs);
       convs.push_back(std::move(ci));
+      return 0;
+    }
+    if (nd.type == N_MAPPED || nd.type == N_COMPOSITE) {
+      if (tgt) { err = "MappedPdf/CompositePdf nodes cannot be nested"; return -1; }
+      if ((int)gns.size() >= kMaxGNorm) { err = "more than 2 MappedPdf/CompositePdf nodes"; return -1; }
+      GNInfo gi;
+      gi.node = id;
+      gi.mcol = col_of_obs[nd.obs];
+      if (gi.mcol < 0) { err = "the dataset lacks the node's observable"; return -1; }
+      std::vector<int> pars, u;
+      conv_pars = &pars;
+      const int saved = depth;
+      tgt = &gi.body;
+      depth = 0;
+      auto leaf_slot = [&]() -> int {
+        if (P.nleaf >= kMaxLeaf) { err = "more than 16 leaves"; return -1; }
+        P.leaf[P.nleaf] = LeafDesc{};
+        return P.nleaf++;
+      };
+      if (nd.type == N_MAPPED) {
+        const int nc = (int)nd.children.size();
+        for (int k = 0; k < nc; ++k) {
+          const int dk = walk(nd.children[k], u);
+          if (dk < 0) return -1;
+          if (dk == 1) {
+            Instr T{};
+            T.op = OP_TOLIN;
+            if (!emit(T)) return -1;
+          }
+          const int sl = leaf_slot();
+          if (sl < 0) return -1;
+          LeafDesc& L = P.leaf[sl];
+          L.kind = L_IND;
+          L.obs = gi.mcol;
+          L.lo = ctx->obs[nd.obs].lo;
+          L.hi = ctx->obs[nd.obs].hi;
+          if (k > 0) L.par[L.npar++] = nd.pars[k - 1];
+          if (k < nc - 1) L.par[L.npar++] = nd.pars[k];
+          L.aux = (k > 0 ? 1 : 0) | (k < nc - 1 ? 2 : 0);
+          for (int q = 0; q < L.npar; ++q)
+            if (gidx(L.par[q]) >= 0) { err = "MappedPdf boundaries must be fixed"; return -1; }
+          Instr I{};
+          I.op = OP_LEAF;
+          I.kind = L_IND;
+          I.obs = gi.mcol;
+          I.slot = sl;
+          for (int q = 0; q < kMaxLocal; ++q) I.gidx[q] = -1;
+          Instr M{};
+          M.op = OP_MUL;
+          if (!emit(I) || !emit(M)) return -1;
+          if (k > 0) {
+            Instr A{};
+            A.op = OP_ADD;
+            if (!emit(A)) return -1;
+          }
+        }
+      } else {
+        raw_next = true;
+        const int dc = walk(nd.children[0], u);
+        raw_next = false;
+        if (dc < 0) return -1;
+        if (dc == 1) {
+          Instr T{};
+          T.op = OP_TOLIN;
+          if (!emit(T)) return -1;
+        }
+        const NodeDef& sh = ctx->nodes[nd.children[1]];
+        const int sl = leaf_slot();
+        if (sl < 0) return -1;
+        LeafDesc& L = P.leaf[sl];
+        L.kind = sh.type;
+        L.obs = gi.mcol;  // unused: the shell reads the core's value
+        L.npar = (int)sh.pars.size();
+        for (int k = 0; k < L.npar; ++k) L.par[k] = sh.pars[k];
+        L.lo = ctx->obs[sh.obs].lo;
+        L.hi = ctx->obs[sh.obs].hi;
+        L.aux = kRawLeaf;
+        pars.insert(pars.end(), sh.pars.begin(), sh.pars.end());
+        Instr C{};
+        C.op = OP_COMPOSE;
+        C.kind = sh.type;
+        C.slot = sl;
+        C.npar = L.npar;
+        for (int k = 0; k < kMaxLocal; ++k) C.gidx[k] = k < L.npar ? gidx(L.par[k]) : -1;
+        if (!emit(C)) return -1;
+      }
+      tgt = nullptr;
+      depth = saved;
+      conv_pars = nullptr;
+      for (int q : pars)
+        if (gidx(q) >= 0 && std::find(gi.loc.begin(), gi.loc.end(), q) == gi.loc.end())
+          gi.loc.push_back(q);
+      if ((int)gi.loc.size() > kMaxLocal) {
+        err = "a MappedPdf/CompositePdf has more than 8 free parameters";
+        return -1;
+      }
+      const int gs = leaf_slot();
+      if (gs < 0) return -1;
+      LeafDesc& G = P.leaf[gs];
+      G.kind = L_GNORM;
+      G.obs = gi.mcol;
+      G.npar = (int)gi.loc.size();
+      for (int k = 0; k < G.npar; ++k) G.par[k] = gi.loc[k];
+      G.lo = ctx->obs[nd.obs].lo;
+      G.hi = ctx->obs[nd.obs].hi;
+      gi.slot = gs;
+      for (int pc = 0; pc < gi.body.n; ++pc)
+        if (!emit(gi.body.ins[pc])) return -1;
+      Instr Nm{};
+      Nm.op = OP_GNORM;
+      Nm.slot = gs;
+      Nm.npar = G.npar;
+      for (int k = 0; k < kMaxLocal; ++k) Nm.gidx[k] = k < G.npar ? gidx(G.par[k]) : -1;
+      if (!emit(Nm)) return -1;
+      obs_used.push_back(nd.obs);
+      gns.push_back(std::move(gi));
       return 0;
     }
     if (nd.type == N_PROD) {
@@ -819,7 +985,6 @@ static int setup_convs(gf_ctx* ctx, std::vector<ConvInfo>& convs) {
     h.mcol = ci.mcol;
     for (int l = 0; l < h.nloc; ++l) h.loc2free[l] = ctx->free_pos[ci.loc[l]];
     const int nq = 1 + h.nloc;
-    const int nsum = (h.L + 1 + kThreads1D - 1) / kThreads1D;
     auto alloc = [&](size_t bytes) -> void* {
       void* p = nullptr;
       if (cudaMalloc(&p, bytes) != cudaSuccess) {
@@ -834,7 +999,7 @@ static int setup_convs(gf_ctx* ctx, std::vector<ConvInfo>& convs) {
     h.mt = static_cast<float2*>(alloc(sizeof(float2) * nq * (size_t)h.J));
     h.rt = static_cast<float2*>(alloc(sizeof(float2) * nq * (size_t)h.K));
     h.ct = static_cast<double*>(alloc(sizeof(double) * nq * (size_t)(h.L + 1)));
-    h.partials = static_cast<double*>(alloc(sizeof(double) * (1 + kMaxLocal) * (size_t)nsum));
+    h.partials = static_cast<double*>(alloc(sizeof(double) * nq * (size_t)(h.L + 1)));
     h.counter = static_cast<unsigned*>(alloc(sizeof(unsigned)));
     ConvDesc* dd = static_cast<ConvDesc*>(alloc(sizeof(ConvDesc)));
     if (!pm || !pr || !h.mt || !h.rt || !h.ct || !h.partials || !h.counter || !dd) {
@@ -855,13 +1020,78 @@ static int setup_convs(gf_ctx* ctx, std::vector<ConvInfo>& convs) {
   return GF_OK;
 }
 
-// Convolution tables after the normalisation launch (every evaluation of a tree with them).
+static void free_gnorms(DevState& d) {
+  for (void* p : d.gn_bufs) cudaFree(p);
+  d.gn_bufs.clear();
+  d.ngn = 0;
+  for (auto& g : d.gn_desc) g = nullptr;
+}
+
+static int setup_gnorms(gf_ctx* ctx, std::vector<GNInfo>& gns) {
+  DevState& d = ctx->dev;
+  free_gnorms(d);
+  const Program& P = ctx->prog;
+  for (size_t g = 0; g < gns.size(); ++g) {
+    GNInfo& gi = gns[g];
+    const NodeDef& nd = ctx->nodes[gi.node];
+    Program& B = gi.body;
+    B.nleaf = P.nleaf;
+    B.ncoef = P.ncoef;
+    B.nfree = P.nfree;
+    B.nobs = P.nobs;
+    std::copy(P.leaf, P.leaf + kMaxLeaf, B.leaf);
+    std::copy(P.coef, P.coef + kMaxCoef, B.coef);
+    GNormDesc h{};
+    h.nbins = nd.nbx;
+    h.lo = ctx->obs[nd.obs].lo;
+    h.h = (ctx->obs[nd.obs].hi - h.lo) / h.nbins;
+    h.slot = gi.slot;
+    h.mcol = gi.mcol;
+    h.nloc = (int)gi.loc.size();
+    for (int l = 0; l < h.nloc; ++l) h.loc2free[l] = ctx->free_pos[gi.loc[l]];
+    const int nb = (h.nbins + kThreads1D - 1) / kThreads1D;
+    auto alloc = [&](size_t bytes) -> void* {
+      void* p = nullptr;
+      if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+      }
+      d.gn_bufs.push_back(p);
+      return p;
+    };
+    Program* sub = static_cast<Program*>(alloc(sizeof(Program)));
+    h.partials = static_cast<double*>(alloc(sizeof(double) * (1 + kMaxLocal) * (size_t)nb));
+    h.counter = static_cast<unsigned*>(alloc(sizeof(unsigned)));
+    GNormDesc* dd = static_cast<GNormDesc*>(alloc(sizeof(GNormDesc)));
+    if (!sub || !h.partials || !h.counter || !dd) {
+      free_gnorms(d);
+      return set_error(ctx, GF_ENOMEM, "device allocation of a grid normalisation failed");
+    }
+    h.sub = sub;
+    CK(cudaMemcpyAsync(sub, &B, sizeof(Program), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(h.counter, 0, sizeof(unsigned), ctx->stream));
+    CK(cudaMemcpyAsync(dd, &h, sizeof(GNormDesc), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    d.gn_host[g] = h;
+    d.gn_desc[g] = dd;
+    d.ngn = (int)g + 1;
+  }
+  return GF_OK;
+}
+
+// Convolution tables and grid normalisations after the normalisation launch (every
+// evaluation of a tree with them).
 static int enqueue_convs(gf_ctx* ctx, int* launches) {
   DevState& d = ctx->dev;
   for (int c = 0; c < d.nconv; ++c) {
     CK(launch_conv(d.conv_host[c], d.conv_desc[c], weideman(), ctx->prog.nfree, d.derived,
                    ctx->stream));
     if (launches) *launches += 2;
+  }
+  for (int g = 0; g < d.ngn; ++g) {
+    CK(launch_gnorm(d.gn_host[g], d.gn_desc[g], weideman(), ctx->prog.nfree, d.derived,
+                    ctx->stream));
+    if (launches) *launches += 1;
   }
   return GF_OK;
 }
@@ -963,9 +1193,10 @@ int ensure_compiled(gf_ctx* ctx) {
       }
     }
     P.ngrid_blocks = blk;
-    const int rcc = setup_convs(ctx, C.convs);
+    int rcc = setup_convs(ctx, C.convs);
+    if (rcc == GF_OK) rcc = setup_gnorms(ctx, C.gns);
     if (rcc) return rcc;
-    if (!C.convs.empty()) ctx->has_grid = true;  // records come from the device
+    if (!C.convs.empty() || !C.gns.empty()) ctx->has_grid = true;  // records from the device
     // the first Voigtian leaf is the one expanded per chunk on sorted data
     P.tay_slot = -1;
     P.tay_obs = 0;
@@ -1654,7 +1885,8 @@ int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64) {
         d.graph[key] = ge;
       }
     } else {
-      launches = (ctx->is_dalitz ? (direct ? 2 : 1) : (ctx->has_grid ? 2 : 1));
+      launches = (ctx->is_dalitz ? (direct ? 2 : 1)
+                                 : (ctx->has_grid ? 2 + 2 * d.nconv + d.ngn : 1));
     }
     if (!d.graph_off) {
       CK(cudaGraphLaunch(d.graph[key], ctx->stream));
@@ -1722,7 +1954,7 @@ int tick_prepare(gf_ctx* ctx) {
   DevState& d = ctx->dev;
   if (d.tick_desc) return d.tick_kind;
   if (!ctx->compiled || !d.theta || d.n <= 0) return 0;
-  if (d.nconv > 0) return 0;  // convolution tables: per-fit evaluations
+  if (d.nconv > 0 || d.ngn > 0) return 0;  // tables / grid normalisations: per-fit evaluations
   CK(cudaSetDevice(ctx->device));
   if (!ctx->is_dalitz) {
     Fit1D F{};

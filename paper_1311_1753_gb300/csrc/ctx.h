@@ -13,7 +13,7 @@
 namespace gfi {
 
 enum NodeType { N_EXP = 1, N_GAUSS, N_VOIGT, N_THRESH, N_POLY, N_RELBW, N_ADD = 10, N_PROD,
-                N_DALITZ, N_CONV };
+                N_DALITZ, N_CONV, N_MAPPED, N_COMPOSITE };
 
 struct ObsDef {
   std::string name;
@@ -87,6 +87,11 @@ struct DevState {
   ConvDesc* conv_desc[kMaxConv] = {};  // device copies
   ConvDesc conv_host[kMaxConv] = {};
   int nconv = 0;
+  // grid-normalised nodes (MappedPdf, CompositePdf)
+  std::vector<void*> gn_bufs;
+  GNormDesc* gn_desc[kMaxGNorm] = {};
+  GNormDesc gn_host[kMaxGNorm] = {};
+  int ngn = 0;
   // binned data: bin contents and chi-squared variances (device), N x bin volume
   bool binned = false;
   double* bw = nullptr;

@@ -31,8 +31,12 @@ constexpr int kChunk = 24;      // sorted 1D data: events per expansion of w (k_
 enum Leaf : int32_t {
   L_EXP = 1, L_GAUSS = 2, L_VOIGT = 3, L_THRESH = 4, L_POLY = 5,
   L_RELBW = 6,  // relativistic Breit-Wigner line shape (grid-normalised)
-  L_CONV = 7    // a ConvolutionPdf read from its lattice table (k_conv.cu builds it)
+  L_CONV = 7,   // a ConvolutionPdf read from its lattice table (k_conv_sum builds it)
+  L_IND = 8,    // indicator of an interval of the observable (MappedPdf)
+  L_GNORM = 9   // record of a grid-normalised node (MappedPdf, CompositePdf; k_gnorm)
 };
+constexpr int kRawLeaf = 0x100;  // LeafDesc.aux flag: the unnormalised shape (N = 1)
+constexpr int kMaxGNorm = 2;     // grid-normalised nodes of one tree
 constexpr int kResidCol = 7;     // observable column of a resolution's residual variable
 constexpr int kMaxConv = 2;      // convolution nodes of one tree
 constexpr int kConvMaxLattice = 65536;  // lattice bins of one convolution
@@ -48,6 +52,8 @@ enum Op : int32_t {
   OP_LMUL = 4,    // s0 = s1 + s0        (ProdPdf, log domain)
   OP_SCALE = 5,   // s0 = coef[slot] * s0 (AddPdf fraction, or 1 - sum of fractions)
   OP_ADD = 6,     // s0 = s1 + s0        (AddPdf)
+  OP_COMPOSE = 7, // s0 = shell(s0): the shell leaf (slot, kind) of a CompositePdf
+  OP_GNORM = 8,   // s0 = s0 / N of a grid-normalised node (record slot)
 };
 
 struct Instr {
@@ -102,7 +108,19 @@ struct Cols {
   const double* c[kMaxObs];
 };
 
-// One ConvolutionPdf node (k_conv.cu).  Lattice x_i = lo + i h (i = 0..L); resolution
+// One grid-normalised node (MappedPdf, CompositePdf): N = h sum_b F(lo + (b + 1/2) h) over
+// nbins midpoints of the observable, F the node's body (sub-program), with dN over the
+// node's local parameters; k_gnorm writes the record at slot.
+struct GNormDesc {
+  const Program* sub;
+  double* partials;  // [blocks][1 + kMaxLocal]
+  unsigned* counter;
+  int32_t nbins, slot, mcol, nloc;
+  int32_t loc2free[kMaxLocal];
+  double lo, h;
+};
+
+// One ConvolutionPdf node (k_1d.cu: k_conv_points, k_conv_sum).  Lattice x_i = lo + i h (i = 0..L); resolution
 // offsets u_k = (kmin + k) h (k < K); model points t_j = lo + (j - kmax) h (j < J =
 // L + K); C_i = h sum_k R(u_k) M(x_i - u_k).  Tables hold a value row, then one row per
 // local parameter (the free parameters of the model and resolution subtrees).
@@ -112,7 +130,7 @@ struct ConvDesc {
   float2* mt;         // [1 + nloc][J] pairs (hi, lo)
   float2* rt;         // [1 + nloc][K]
   double* ct;         // [1 + nloc][L + 1]: C_i and dC_i/dtheta_l
-  double* partials;   // [blocks][1 + nloc]: trapezoid sums
+  double* partials;   // [L + 1][1 + nloc]: trapezoid terms
   unsigned* counter;
   int32_t L, kmin, kmax, J, K, nloc;
   int32_t slot;        // leaf record of the conv leaf in the main program

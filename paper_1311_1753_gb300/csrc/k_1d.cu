@@ -94,7 +94,7 @@ __device__ inline double rb_poly(int L, double z) {
 __device__ inline void relbw_consts(const LeafDesc& Lf, const double* th, double* c) {
   const double dm0 = th[Lf.par[0]], g0 = th[Lf.par[1]], shift = th[Lf.par[2]];
   const double ma = th[Lf.par[3]], mb = th[Lf.par[4]], R = th[Lf.par[5]];
-  const int L = Lf.aux;
+  const int L = Lf.aux & 0xff;
   const double m0 = dm0 + shift, s0 = m0 * m0;
   const double A = (ma + mb) * (ma + mb), B = (ma - mb) * (ma - mb);
   const double thr = ma + mb - shift;
@@ -204,11 +204,19 @@ __device__ __forceinline__ double thresh_r(double x, const ShapeK& K, double* dr
 
 // ---- leaf records ------------------------------------------------------------------------
 // rec[0] = 1/N, rec[1] = log N, rec[2 + k] = d log N / d par_k, rec[10 + j] = constants.
+// A leaf flagged kRawLeaf (the core and shell of a CompositePdf) keeps its unnormalised
+// shape: N = 1 and dN = 0.
 __device__ void make_leaf_record(const LeafDesc& L, const double* th, double N, const double* dN,
                                  double* rec) {
   for (int k = 0; k < kLeafRec; ++k) rec[k] = 0.0;
   const double lo = L.lo, hi = L.hi, D = hi - lo;
   double* c = rec + 10;
+  const bool raw = (L.aux & kRawLeaf) != 0;
+  const double zero3[3] = {0.0, 0.0, 0.0};
+  if (raw) {
+    N = 1.0;
+    dN = zero3;
+  }
   switch (L.kind) {
     case L_EXP: {
       // N = e^{a lo} expm1(a D)/a;  d log N/da = lo + D phi(aD),
@@ -229,9 +237,10 @@ __device__ void make_leaf_record(const LeafDesc& L, const double* th, double N, 
           phi = -1.0 / expm1(-u) - 1.0 / u;
         }
       }
+      if (raw) logN = 0.0;
       rec[0] = exp(-logN);
       rec[1] = logN;
-      rec[2] = lo + D * phi;
+      rec[2] = raw ? 0.0 : lo + D * phi;
       c[0] = a;
       c[1] = -logN;
       break;
@@ -243,12 +252,12 @@ __device__ void make_leaf_record(const LeafDesc& L, const double* th, double N, 
       if (a > 0.0) diff = 0.5 * (erfc(a / kSqrt2) - erfc(b / kSqrt2));
       else if (b < 0.0) diff = 0.5 * (erfc(-b / kSqrt2) - erfc(-a / kSqrt2));
       else diff = 0.5 * (erf(b / kSqrt2) - erf(a / kSqrt2));
-      const double n = s * kSqrt2Pi * diff;
+      const double n = raw ? 1.0 : s * kSqrt2Pi * diff;
       const double ea = exp(-0.5 * a * a), eb = exp(-0.5 * b * b);
       rec[0] = 1.0 / n;
       rec[1] = log(n);
-      rec[2] = (ea - eb) / n;
-      rec[3] = (a * ea - b * eb) / n + 1.0 / s;
+      rec[2] = raw ? 0.0 : (ea - eb) / n;
+      rec[3] = raw ? 0.0 : (a * ea - b * eb) / n + 1.0 / s;
       c[0] = mu;
       c[1] = 1.0 / s;
       c[2] = -rec[1];
@@ -286,23 +295,33 @@ __device__ void make_leaf_record(const LeafDesc& L, const double* th, double N, 
       rec[1] = log(N);
       rec[2] = dN[0] / N;
       rec[3] = dN[1] / N;
-      rec[4] = L.aux;          // orbital angular momentum and dm0 (the other dlogN slots
+      rec[4] = L.aux & 0xff;   // orbital angular momentum and dm0 (the other dlogN slots
       rec[5] = th[L.par[0]];   // are unused)
       relbw_consts(L, th, c);
       break;
     }
     case L_CONV:
-      break;  // written by the convolution kernel (k_conv_sum) after this one
+    case L_GNORM:
+      break;  // written after this kernel (k_conv_sum, k_gnorm)
+    case L_IND: {
+      // [c0, c1) with c0, c1 the boundary parameters (aux bit 1: lower, bit 2: upper) or
+      // the range ends; the interval reaching hi is closed (c1 = +inf)
+      rec[0] = 1.0;
+      c[0] = (L.aux & 1) ? th[L.par[0]] : -INFINITY;
+      c[1] = (L.aux & 2) ? th[L.par[(L.aux & 1) ? 1 : 0]] : INFINITY;
+      break;
+    }
     case L_POLY: {
       // N = Q(hi) - Q(lo), Q(x) = sum_k a_k x^{k+1}/(k+1)
       double n = 0.0, phk = hi, plk = lo;
       double ik[kMaxLocal];
       for (int k = 0; k < L.npar; ++k) {
-        ik[k] = (phk - plk) / (k + 1);
+        ik[k] = raw ? 0.0 : (phk - plk) / (k + 1);
         n = fma(th[L.par[k]], ik[k], n);
         phk *= hi;
         plk *= lo;
       }
+      if (raw) n = 1.0;
       rec[0] = 1.0 / n;
       rec[1] = log(n);
       for (int k = 0; k < L.npar; ++k) {
@@ -367,7 +386,7 @@ __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& 
       if (L.kind == L_VOIGT) {
         v[0] = voigt_r(x, *shk, W, dr);
       } else if (L.kind == L_RELBW) {
-        v[0] = relbw_f<ArD, true>(x, shk->rb, shk->rb, L.aux, shk->rb_dm0, dr[0], dr[1]);
+        v[0] = relbw_f<ArD, true>(x, shk->rb, shk->rb, L.aux & 0xff, shk->rb_dm0, dr[0], dr[1]);
         dr[2] = 0.0;
       } else {
         v[0] = thresh_r(x, *shk, dr);
@@ -578,6 +597,8 @@ __device__ __forceinline__ typename A::T eval_leaf_s(const Instr& I, const doubl
       }
       return l;
     }
+    case L_IND:
+      return (x >= rec[10] && x < rec[11]) ? A::of(1.0) : A::zero();
     case L_CONV: {
       // lattice table (k_conv_sum): C_i then dC_i/dtheta_l, rows of L + 1; linear in
       // between (FP64 index arithmetic: convolutions serve binned or modest data)
@@ -624,6 +645,44 @@ __device__ __forceinline__ typename A::T eval_leaf(const Instr& I, const double*
   return eval_leaf_s<A, G>(I, rec, r, x, W,
                            [&](int j, T term) { g[I.gidx[j] * bd] = A::add(g[I.gidx[j] * bd], term); },
                            tay);
+}
+
+// Shell of a CompositePdf (Sec. 3) at u: its unnormalised shape f(u), f'(u) and, with G,
+// df/d(local parameter j) into dp[j].  Constants c: EXP a; GAUSS mu, 1/sigma; POLY a_k
+// (the leaf's record with kRawLeaf: N = 1).
+template <class A, bool G>
+__device__ __forceinline__ void shell_f(int kind, int npar, const typename A::T* c,
+                                        typename A::T u, typename A::T& f, typename A::T& fu,
+                                        typename A::T* dp) {
+  using T = typename A::T;
+  if (kind == L_EXP) {
+    f = A::exp_(A::mul(c[0], u));
+    fu = A::mul(c[0], f);
+    if (G) dp[0] = A::mul(u, f);
+  } else if (kind == L_GAUSS) {
+    const T t = A::mul(A::sub(u, c[0]), c[1]);
+    f = A::exp_(A::mulf(A::mul(t, t), -0.5f));
+    const T tf = A::mul(A::mul(t, f), c[1]);  // t f / sigma
+    fu = A::neg(tf);
+    if (G) {
+      dp[0] = tf;
+      dp[1] = A::mul(t, tf);
+    }
+  } else {  // L_POLY: Horner for f and f'
+    f = c[npar - 1];
+    fu = A::zero();
+    for (int k = npar - 2; k >= 0; --k) {
+      fu = A::add(A::mul(fu, u), f);
+      f = A::add(A::mul(f, u), c[k]);
+    }
+    if (G) {
+      T uk = A::of(1.0);
+      for (int k = 0; k < npar; ++k) {
+        dp[k] = uk;
+        uk = A::mul(uk, u);
+      }
+    }
+  }
 }
 
 // The compiled postfix program for one event: returns the root's value (log domain if
@@ -676,6 +735,31 @@ __device__ __forceinline__ typename A::T run_program(const Program& P, const dou
         }
         s0 = A::add(s1, s0); s1 = s2; s2 = s3;
         --dep;
+        break;
+      }
+      case OP_COMPOSE: {
+        // shell(u), u = s0 (the core's value): d/dtheta = f'(u) du/dtheta + df/dtheta_shell
+        const T* c = rc + I.slot * kLeafRec + 10;
+        T f, fu, dp[kMaxLocal];
+        shell_f<A, G>(I.kind, I.npar, c, s0, f, fu, dp);
+        if (G) {
+          for (int k = 0; k < nf; ++k) gt[k * bd] = A::mul(gt[k * bd], fu);
+          for (int j = 0; j < I.npar; ++j)
+            if (I.gidx[j] >= 0) gt[I.gidx[j] * bd] = A::add(gt[I.gidx[j] * bd], dp[j]);
+        }
+        s0 = f;
+        break;
+      }
+      case OP_GNORM: {
+        // s0 / N: d/dtheta = ds0/N - (s0/N) dlogN/dtheta (the node's local parameters)
+        const T* r = rc + I.slot * kLeafRec;
+        s0 = A::mul(s0, r[0]);
+        if (G) {
+          for (int k = 0; k < nf; ++k) gt[k * bd] = A::mul(gt[k * bd], r[0]);
+          for (int j = 0; j < I.npar; ++j)
+            if (I.gidx[j] >= 0)
+              gt[I.gidx[j] * bd] = A::sub(gt[I.gidx[j] * bd], A::mul(s0, r[2 + j]));
+        }
         break;
       }
       case OP_SCALE: {
@@ -1268,63 +1352,56 @@ __global__ void __launch_bounds__(kThreads1D) k_conv_points(const ConvDesc* __re
   }
 }
 
-// k_conv_sum: C_i = h sum_k r_k m_{i - kmin - k + kmax} and its gradient rows (pairs,
-// resolution rows staged in shared memory), the table in FP64, then the trapezoid
-// normalisation N = h (C_0/2 + C_1 + ... + C_L/2) and dN across blocks (fixed order, last
-// block), which writes the conv leaf's record: 1/N, log N, dlogN/dtheta_l, and the
-// constants lo, 1/h, L and the table's address.
+// k_conv_sum: C_i = h sum_k r_k m_{i - kmin - k + kmax} and its gradient rows in float
+// pairs, one warp per (lattice point, row) with the lanes splitting the offsets, the table
+// in FP64; then the trapezoid normalisation N = h (C_0/2 + C_1 + ... + C_L/2) and dN by
+// the last block in a fixed order, which writes the conv leaf's record: 1/N, log N,
+// dlogN/dtheta_l, and the constants lo, 1/h, L and the table's address.
 __global__ void __launch_bounds__(kThreads1D) k_conv_sum(const ConvDesc* __restrict__ cdp,
                                                          double* __restrict__ derived) {
-  extern __shared__ float2 rs[];  // two resolution rows of K pairs
   __shared__ double red[(kThreads1D / 32) * (1 + kMaxLocal)];
+  __shared__ double sums[1 + kMaxLocal];
   __shared__ int last;
   const ConvDesc& cd = *cdp;
-  const int bd = blockDim.x, tid = threadIdx.x;
-  const int i = blockIdx.x * bd + tid;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int K = cd.K, J = cd.J, L = cd.L, nq = 1 + cd.nloc;
-  const bool on = i <= L;
-  const int j0 = i - cd.kmin + cd.kmax;  // model index for k = 0 (then j0 - k)
-  F2 tr[1 + kMaxLocal];
-  for (int q = 0; q < nq; ++q) {
-    // rows: q = 0: r with m; q = l + 1: dr_l with m, then r with dm_l
-    __syncthreads();
-    for (int k = tid; k < K; k += bd) {
-      rs[k] = cd.rt[(size_t)q * K + k];
-      rs[K + k] = cd.rt[k];
-    }
-    __syncthreads();
+  const int w = (int)((blockIdx.x * (unsigned)blockDim.x + tid) >> 5);
+  if (w < (L + 1) * nq) {
+    const int i = w / nq, q = w - i * nq;
+    const int j0 = i - cd.kmin + cd.kmax;  // model index for offset k = 0 (then j0 - k)
     LazyAcc acc;
-    if (on) {
-      const float2* m0 = cd.mt + j0;
-      for (int k = 0; k < K; ++k) {
+    // row q = 0: r with m; row q = l + 1: dr_l with m, then r with dm_l
+    const float2* ra = cd.rt + (size_t)q * K;
+    const float2* ma = cd.mt + j0;
+    for (int k = lane; k < K; k += 32) {
+      float p, e;
+      const float2 x = ra[k], y = ma[-k];
+      prod_pe(F2{x.x, x.y}, F2{y.x, y.y}, p, e);
+      acc.add(p, e);
+    }
+    if (q > 0) {
+      const float2* mb = cd.mt + (size_t)q * J + j0;
+      for (int k = lane; k < K; k += 32) {
         float p, e;
-        const float2 a = rs[k], b = m0[-k];
-        prod_pe(F2{a.x, a.y}, F2{b.x, b.y}, p, e);
+        const float2 x = cd.rt[k], y = mb[-k];
+        prod_pe(F2{x.x, x.y}, F2{y.x, y.y}, p, e);
         acc.add(p, e);
-        if ((k & 7) == 7) acc.renorm();
-      }
-      if (q > 0) {
-        const float2* mq = cd.mt + (size_t)q * J + j0;
-        for (int k = 0; k < K; ++k) {
-          float p, e;
-          const float2 a = rs[K + k], b = mq[-k];
-          prod_pe(F2{a.x, a.y}, F2{b.x, b.y}, p, e);
-          acc.add(p, e);
-          if ((k & 7) == 7) acc.renorm();
-        }
       }
     }
-    const double c = on ? df_to(acc.get()) * cd.h : 0.0;
-    if (on) cd.ct[(size_t)q * (L + 1) + i] = c;
-    const double w = (i == 0 || i == L) ? 0.5 : 1.0;
-    tr[q] = df_split(w * c);
+    F2 v = acc.get();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const F2 u = {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+      v = df_add(v, u);
+    }
+    if (lane == 0) {
+      const double c = df_to(v) * cd.h;
+      cd.ct[(size_t)q * (L + 1) + i] = c;
+      cd.partials[w] = (i == 0 || i == L) ? 0.5 * c : c;  // [i][q]: trapezoid terms
+    }
   }
-  const int stride = 1 + kMaxLocal;
-  block_sum_pairs([&](int q) -> F2 { return tr[q]; }, nq, red,
-                  cd.partials + (size_t)blockIdx.x * stride);
   if (!arrive_last_of(cd.counter, gridDim.x, &last)) return;
-  __shared__ double sums[1 + kMaxLocal];
-  reduce_partials(cd.partials, gridDim.x, stride, nq, sums, red);
+  reduce_partials(cd.partials, L + 1, nq, nq, sums, red);
   __syncthreads();
   if (tid == 0) {
     double* r = derived + (size_t)cd.slot * kLeafRec;
@@ -1343,14 +1420,78 @@ __global__ void __launch_bounds__(kThreads1D) k_conv_sum(const ConvDesc* __restr
 
 cudaError_t launch_conv(const ConvDesc& host, const ConvDesc* dev, const WeidCoef& W, int nfree,
                         double* derived, cudaStream_t st) {
-  const int bd = kThreads1D;
-  const int nb = (host.J + bd - 1) / bd + (host.K + bd - 1) / bd;
-  const size_t dyn = (size_t)(kMaxStack + 1) * std::max(nfree, 1) * bd * sizeof(double);
-  k_conv_points<<<nb, bd, dyn, st>>>(dev, W, derived);
+  // points: 32 threads per block, so that the FP64 work of the subtrees spreads over
+  // many SMs (each SM issues 2 FP64 operations per clock)
+  const int bp = 32;
+  const int nb = (host.J + bp - 1) / bp + (host.K + bp - 1) / bp;
+  const size_t dyn = (size_t)(kMaxStack + 1) * std::max(nfree, 1) * bp * sizeof(double);
+  k_conv_points<<<nb, bp, dyn, st>>>(dev, W, derived);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_conv_sum<<<(host.L + 1 + bd - 1) / bd, bd, 2 * (size_t)host.K * sizeof(float2), st>>>(dev,
-                                                                                         derived);
+  const int64_t warps = (int64_t)(host.L + 1) * (1 + host.nloc);
+  const int bd = kThreads1D;
+  k_conv_sum<<<(int)((warps * 32 + bd - 1) / bd), bd, 0, st>>>(dev, derived);
+  return cudaGetLastError();
+}
+
+// ---- grid-normalised nodes (MappedPdf, CompositePdf; Sec. 3) -------------------------
+// k_gnorm: the node's body (sub-program) at the nbins midpoints of its observable in FP64
+// with the gradient over the node's local parameters; per-block pair sums, the last block
+// forms N = h sum and dN, and writes the node's record: 1/N, log N, dlogN/dtheta_l.
+__global__ void __launch_bounds__(kThreads1D) k_gnorm(const GNormDesc* __restrict__ gdp,
+                                                      const __grid_constant__ WeidCoef W,
+                                                      double* __restrict__ derived) {
+  extern __shared__ double dyn[];  // (kMaxStack + 1) nfree blockDim doubles
+  __shared__ Program P;
+  __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
+  __shared__ double red[(kThreads1D / 32) * (1 + kMaxLocal)];
+  __shared__ double sums[1 + kMaxLocal];
+  __shared__ int last;
+  const GNormDesc& gd = *gdp;
+  const int bd = blockDim.x, tid = threadIdx.x;
+  load_program(gd.sub, P);
+  for (int k = tid; k < kMaxLeaf * kLeafRec + kMaxCoef; k += bd) rec[k] = derived[k];
+  __syncthreads();
+  const int nf = P.nfree, nq = 1 + gd.nloc;
+  const int b = blockIdx.x * bd + tid;
+  F2 tr[1 + kMaxLocal];
+  for (int q = 0; q < nq; ++q) tr[q] = F2{0.f, 0.f};
+  if (b < gd.nbins) {
+    double x[kMaxObs];
+#pragma unroll
+    for (int o = 0; o < kMaxObs; ++o) x[o] = 0.0;
+    x[gd.mcol] = gd.lo + (b + 0.5) * gd.h;
+    double v = run_program<ArD, true>(P, rec, rec, x, W, dyn, nf, bd, tid);
+    double sc = 1.0;
+    if (P.root_log) {
+      v = df_exp(v);
+      sc = v;
+    }
+    tr[0] = df_split(v);
+    for (int l = 0; l < gd.nloc; ++l) tr[1 + l] = df_split(dyn[(size_t)gd.loc2free[l] * bd + tid] * sc);
+  }
+  const int stride = 1 + kMaxLocal;
+  block_sum_pairs([&](int q) -> F2 { return tr[q]; }, nq, red,
+                  gd.partials + (size_t)blockIdx.x * stride);
+  if (!arrive_last_of(gd.counter, gridDim.x, &last)) return;
+  reduce_partials(gd.partials, gridDim.x, stride, nq, sums, red);
+  __syncthreads();
+  if (tid == 0) {
+    double* r = derived + (size_t)gd.slot * kLeafRec;
+    for (int k = 0; k < kLeafRec; ++k) r[k] = 0.0;
+    const double N = sums[0] * gd.h;
+    r[0] = 1.0 / N;
+    r[1] = log(N);
+    for (int l = 0; l < gd.nloc; ++l) r[2 + l] = sums[1 + l] * gd.h / N;
+    *gd.counter = 0u;
+  }
+}
+
+cudaError_t launch_gnorm(const GNormDesc& host, const GNormDesc* dev, const WeidCoef& W,
+                         int nfree, double* derived, cudaStream_t st) {
+  const int bd = kThreads1D;
+  const size_t dyn = (size_t)(kMaxStack + 1) * std::max(nfree, 1) * bd * sizeof(double);
+  k_gnorm<<<(host.nbins + bd - 1) / bd, bd, dyn, st>>>(dev, W, derived);
   return cudaGetLastError();
 }
 
@@ -1519,8 +1660,8 @@ cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCo
 void prepare_kernels_1d() {
   upload_df_tables();
   cudaFuncSetAttribute(k_conv_points, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_conv_sum, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       2 * kConvMaxOffsets * (int)sizeof(float2));
+  cudaFuncSetAttribute(k_gnorm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+
   cudaFuncSetAttribute(k_events_1d<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
   cudaFuncSetAttribute(k_events_1d<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -29,6 +29,9 @@ void prepare_kernels_1d();
 // host: the descriptor's sizes, dev: its device copy
 cudaError_t launch_conv(const ConvDesc& host, const ConvDesc* dev, const WeidCoef& W, int nfree,
                         double* derived, cudaStream_t st);
+// normalisation record of one grid-normalised node (after the convolutions)
+cudaError_t launch_gnorm(const GNormDesc& host, const GNormDesc* dev, const WeidCoef& W,
+                         int nfree, double* derived, cudaStream_t st);
 // Sort (key, index) pairs ascending by the FP64 key (k_sort.cu): perm_tmp receives
 // 0 .. n-1, perm_out the permutation, key_out the sorted keys.  temp == nullptr: only
 // sets *temp_bytes to the scratch size the sort needs.

@@ -77,6 +77,8 @@ def _load():
         "gf_pdf_relbw": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                           C.c_int, _I], C.c_int),
         "gf_pdf_conv": ([vp, C.c_int, C.c_int, C.c_int, _I], C.c_int),
+        "gf_pdf_mapped": ([vp, C.c_int, C.c_int, _I, _I, _I], C.c_int),
+        "gf_pdf_composite": ([vp, C.c_int, C.c_int, C.c_int, _I], C.c_int),
         "gf_pdf_prod": ([vp, C.c_int, _I, _I], C.c_int),
         "gf_pdf_dalitz": ([vp, C.c_int, C.c_int, C.POINTER(DalitzKin), C.c_int,
                            C.POINTER(Resonance), _I], C.c_int),
@@ -234,6 +236,16 @@ class Context:
         if lattice is not None:
             self.set_norm_grid(node, int(lattice))
         return node
+
+    def mapped(self, obs, nodes, bounds):
+        """MappedPdf: nodes[k] on [b_{k-1}, b_k); bounds = n - 1 fixed parameter ids."""
+        n = (C.c_int * len(nodes))(*nodes)
+        b = (C.c_int * max(1, len(bounds)))(*bounds)
+        return self._id(lib.gf_pdf_mapped, obs, len(nodes), n, b)
+
+    def composite(self, obs, core, shell):
+        """CompositePdf: shell(core(x)), unnormalised shapes, normalised on obs's range."""
+        return self._id(lib.gf_pdf_composite, obs, core, shell)
 
     def add(self, nodes, fracs):
         a = (C.c_int * len(nodes))(*nodes)
