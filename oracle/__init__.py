@@ -364,3 +364,71 @@ class Dalitz:
                              anr.real, anr.imag, self.nbx, self.nby, len(s12), _dp(s12), _dp(s13),
                              _dp(out), _dp(g) if grad else None)
         return (out[0], g) if grad else out[0]
+
+
+class OrcTpar(C.Structure):
+    _fields_ = [("p_tau", C.c_int32), ("p_x", C.c_int32), ("p_y", C.c_int32), ("p_s", C.c_int32)]
+
+
+def _tddp_lib():
+    so = lib()
+    if not getattr(so, "_tddp_ready", False):
+        so.orc_smeared_exp_many.argtypes = [C.c_int64, C.c_double, C.c_double, _D, C.c_double,
+                                            _D, _D]
+        args = [C.POINTER(OrcDkin), C.c_int, C.POINTER(OrcRes), C.POINTER(OrcTpar), _D, C.c_int]
+        so.orc_tddp_intensity.argtypes = args + [C.c_int64, _D, _D, _D, _D, _D]
+        so.orc_tddp_norm.argtypes = args + [C.c_int, C.c_int, _D]
+        so.orc_tddp_norm.restype = C.c_double
+        so.orc_tddp_nll.argtypes = args + [C.c_int, C.c_int, C.c_int64, _D, _D, _D, _D, _D, _D]
+        so._tddp_ready = True
+    return so
+
+
+def smeared_exp(lam: complex, t, sigma: float) -> np.ndarray:
+    """Int_0^inf e^{-lam u} Gauss(t - u; sigma) du (complex lam, Re lam > 0)."""
+    t = _f64(t)
+    re, im = np.empty_like(t), np.empty_like(t)
+    _tddp_lib().orc_smeared_exp_many(len(t), lam.real, lam.imag, _dp(t), float(sigma), _dp(re),
+                                      _dp(im))
+    return re + 1j * im
+
+
+class Tddp(Dalitz):
+    """Time-dependent Dalitz model (Sec. 4: the D0 mixing fit): the Dalitz amplitude model
+    for D0 (A) and D0bar (B, at the point with particles 1 and 2 exchanged), decay time
+    with mixing (tau, x, y) convolved with a Gaussian of width scale * sigma_t."""
+
+    def __init__(self, M, m1, m2, m3, R=1.5, nbx=512, nby=512):
+        super().__init__(M, m1, m2, m3, R, nbx, nby)
+        self.tp = None
+
+    def time_params(self, tau, x, y, scale):
+        self.tp = OrcTpar(tau, x, y, scale)
+
+    def _args(self, p):
+        p = self.p if p is None else _f64(p)
+        return (C.byref(self.kin), len(self.res), self._resarr(), C.byref(self.tp), _dp(p),
+                len(p)), p
+
+    def intensity_t(self, s12, s13, t, sigt, p=None):
+        a, p = self._args(p)
+        s12, s13, t, sigt = (_f64(v) for v in (s12, s13, t, sigt))
+        out = np.empty_like(s12)
+        _tddp_lib().orc_tddp_intensity(*a, len(s12), _dp(s12), _dp(s13), _dp(t), _dp(sigt),
+                                       _dp(out))
+        return out
+
+    def norm_t(self, p=None, grad=False):
+        a, p = self._args(p)
+        dN = np.zeros(len(p)) if grad else None
+        N = _tddp_lib().orc_tddp_norm(*a, self.nbx, self.nby, _dp(dN) if grad else None)
+        return (N, dN) if grad else N
+
+    def nll_t(self, s12, s13, t, sigt, p=None, grad=False):
+        a, p = self._args(p)
+        s12, s13, t, sigt = (_f64(v) for v in (s12, s13, t, sigt))
+        out = np.zeros(1)
+        g = np.zeros(len(p)) if grad else None
+        _tddp_lib().orc_tddp_nll(*a, self.nbx, self.nby, len(s12), _dp(s12), _dp(s13), _dp(t),
+                                 _dp(sigt), _dp(out), _dp(g) if grad else None)
+        return (out[0], g) if grad else out[0]

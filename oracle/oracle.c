@@ -1040,3 +1040,248 @@ double orc_zemach_at(const orc_dkin* k, int ch, int L, double s12, double s13) {
   channel_invariants(k, ch, s12, s13, &sab, &sbc, &sac, &ma, &mb, &mc);
   return zemach(L, k, sab, sbc, sac, ma, mb, mc);
 }
+
+/* ------------------------------------------------------------------------------ */
+/* Time-dependent Dalitz model (Sec. 4: the D0 -> pi+ pi- pi0 mixing fit, with      */
+/* "hyperbolic and trigonometric functions convolved with Gaussian resolution        */
+/* functions" and a per-event decay-time uncertainty).  The paper gives no formula;  */
+/* the reading used here is the standard one for D0 mixing in a self-conjugate       */
+/* multi-body final state, with q/p = 1:                                           */
+/*   I(s12, s13, t) = 1/2 (|A|^2 + |B|^2) Tch + 1/2 (|A|^2 - |B|^2) Tc               */
+/*                    + Re(A* B) Tsh - Im(A* B) Ts,                                  */
+/* A = a_NR + sum_r c_r A_r(s12, s13) the D0 amplitude, B the D0bar amplitude, the   */
+/* same sum at the CP-conjugate point (1 <-> 2 exchanged: s13 <-> s23), and the time  */
+/* factors e^{-Gt} {cosh yGt, cos xGt, sinh yGt, sin xGt} each convolved with a      */
+/* Gaussian of width sigma = s sigma_t (sigma_t per event, s a scale parameter):     */
+/*   Tch = (T(l1) + T(l2))/2, Tsh = (T(l1) - T(l2))/2, Tc + i Ts = T(l3),            */
+/*   l1 = G(1 - y), l2 = G(1 + y), l3 = G(1 - i x), G = 1/tau,                       */
+/*   T(l) = Int_0^inf e^{-l u} Gauss(t - u; sigma) du.                               */
+/* Normalised over the Dalitz region (cell centres of the nbx x nby grid) and all t: */
+/*   N = dA sum_cells [1/2 (|A|^2 + |B|^2) Ich + 1/2 (|A|^2 - |B|^2) Ic             */
+/*                     + Re(A* B) Ish - Im(A* B) Is],                                */
+/* Ich = (1/l1 + 1/l2)/2, Ish = (1/l1 - 1/l2)/2, Ic + i Is = 1/l3 (the time          */
+/* integrals over the real line; independent of sigma).  P = I/N; conditional on    */
+/* sigma_t (no sigma_t density).                                                     */
+/* ------------------------------------------------------------------------------ */
+#include <complex.h>
+
+typedef struct {
+  int32_t p_tau, p_x, p_y, p_s;
+} orc_tpar;
+
+/* w(z) for any z: the Im z > 0 routine, w(z) = 2 e^{-z^2} - w(-z) below the axis. */
+static double complex faddeeva_any(double complex z) {
+  double re, im;
+  if (cimag(z) > 0) {
+    orc_faddeeva(creal(z), cimag(z), &re, &im);
+    return re + I * im;
+  }
+  orc_faddeeva(-creal(z), -cimag(z), &re, &im);
+  return 2.0 * cexp(-z * z) - (re + I * im);
+}
+
+/* T(l; t, sigma) = 1/2 e^{l^2 sigma^2/2 - l t} erfc((l sigma^2 - t)/(sigma sqrt2))
+ *               = 1/2 e^{-t^2/(2 sigma^2)} w(i u),  u = (l sigma^2 - t)/(sigma sqrt2),
+ * using w(i u) = e^{u^2} erfc(u); for Re u < 0 the reflection gives
+ * T = e^{l^2 sigma^2/2 - l t} - 1/2 e^{-t^2/(2 sigma^2)} w(-i u).
+ * dT/dl = (l sigma^2 - t) T - sigma/sqrt(2 pi) e^{-t^2/(2 sigma^2)},
+ * dT/dsigma = l^2 sigma T - e^{-t^2/(2 sigma^2)} (l sigma^2 + t)/(sqrt(2 pi) sigma^2). */
+static double complex smeared_exp(double complex l, double t, double sig, double complex* dl,
+                                  double complex* ds) {
+  double complex u = (l * sig * sig - t) / (sig * ORC_SQRT2);
+  double g = exp(-t * t / (2 * sig * sig));
+  double complex T;
+  if (creal(u) >= 0) T = 0.5 * g * faddeeva_any(I * u);
+  else T = cexp(l * l * sig * sig / 2 - l * t) - 0.5 * g * faddeeva_any(-I * u);
+  if (dl) *dl = (l * sig * sig - t) * T - sig / sqrt(2 * ORC_PI) * g;
+  if (ds) *ds = l * l * sig * T - g * (l * sig * sig + t) / (sqrt(2 * ORC_PI) * sig * sig);
+  return T;
+}
+
+void orc_smeared_exp_many(int64_t n, double lr, double li, const double* t, double sig,
+                          double* Tr, double* Ti) {
+  for (int64_t i = 0; i < n; ++i) {
+    double complex T = smeared_exp(lr + I * li, t[i], sig, NULL, NULL);
+    Tr[i] = creal(T);
+    Ti[i] = cimag(T);
+  }
+}
+
+/* Amplitudes A (at (s12, s13)) and B (at (s12, s23)) with their coefficient derivatives:
+ * a[r], b[r] the per-resonance amplitudes (A = 1 + sum c_r a_r). */
+static void tddp_amps(const orc_dkin* k, int nres, const orc_res* res, const double* p,
+                      double s12, double s13, double complex* A, double complex* B,
+                      double complex* a, double complex* b) {
+  double s23 = k->M * k->M + k->m1 * k->m1 + k->m2 * k->m2 + k->m3 * k->m3 - s12 - s13;
+  *A = 1.0;
+  *B = 1.0;
+  for (int r = 0; r < nres; ++r) {
+    double re, im;
+    orc_dalitz_amp(k, res[r].channel, res[r].spin, p[res[r].p_m0], p[res[r].p_g0], s12, s13,
+                   &re, &im, NULL);
+    a[r] = re + I * im;
+    orc_dalitz_amp(k, res[r].channel, res[r].spin, p[res[r].p_m0], p[res[r].p_g0], s12, s23,
+                   &re, &im, NULL);
+    b[r] = re + I * im;
+    double complex c = p[res[r].p_re] + I * p[res[r].p_im];
+    *A += c * a[r];
+    *B += c * b[r];
+  }
+}
+
+/* The four time coefficients and the combination h(A, B) = 1/2 (|A|^2 + |B|^2) k0 +
+ * 1/2 (|A|^2 - |B|^2) k1 + Re(A* B) k2 - Im(A* B) k3, with its derivatives in the
+ * coefficients c_r (added to g scaled by w) and in the k's (returned in dk[4]). */
+static double tddp_comb(int nres, const orc_res* res, double complex A, double complex B,
+                        const double complex* a, const double complex* b, const double* kk,
+                        double w, double* g, double* dk) {
+  double aa = creal(A) * creal(A) + cimag(A) * cimag(A);
+  double bb = creal(B) * creal(B) + cimag(B) * cimag(B);
+  double complex x = conj(A) * B;
+  if (dk) {
+    dk[0] = 0.5 * (aa + bb);
+    dk[1] = 0.5 * (aa - bb);
+    dk[2] = creal(x);
+    dk[3] = -cimag(x);
+  }
+  if (g)
+    for (int r = 0; r < nres; ++r)
+      for (int part = 0; part < 2; ++part) {
+        double complex dA = part ? I * a[r] : a[r], dB = part ? I * b[r] : b[r];
+        double daa = 2 * creal(conj(A) * dA), dbb = 2 * creal(conj(B) * dB);
+        double complex dx = conj(dA) * B + conj(A) * dB;
+        double d = 0.5 * (daa + dbb) * kk[0] + 0.5 * (daa - dbb) * kk[1] + creal(dx) * kk[2] -
+                   cimag(dx) * kk[3];
+        g[part ? res[r].p_im : res[r].p_re] += w * d;
+      }
+  return 0.5 * (aa + bb) * kk[0] + 0.5 * (aa - bb) * kk[1] + creal(x) * kk[2] - cimag(x) * kk[3];
+}
+
+/* Time coefficients of an event (T's) or of the normalisation (integrals), and their
+ * derivatives d k_j / d(tau, x, y, s) in dkk[j][0..3]. */
+static void tddp_time(const double* p, const orc_tpar* tp, double t, double sigt, int integral,
+                      double* kk, double dkk[4][4]) {
+  double tau = p[tp->p_tau], x = p[tp->p_x], y = p[tp->p_y], s = p[tp->p_s];
+  double G = 1.0 / tau;
+  double complex l[3] = {G * (1 - y), G * (1 + y), G * (1 - I * x)};
+  /* dl/dtau, dl/dx, dl/dy */
+  double complex dlt[3] = {-(1 - y) * G * G, -(1 + y) * G * G, -(1 - I * x) * G * G};
+  double complex dlx[3] = {0, 0, -I * G};
+  double complex dly[3] = {-G, G, 0};
+  double complex T[3], Tl[3], Ts[3];
+  double sig = s * sigt;
+  for (int j = 0; j < 3; ++j) {
+    if (integral) {
+      T[j] = 1.0 / l[j];
+      Tl[j] = -1.0 / (l[j] * l[j]);
+      Ts[j] = 0;
+    } else {
+      T[j] = smeared_exp(l[j], t, sig, &Tl[j], &Ts[j]);
+      Ts[j] *= sigt; /* d/ds */
+    }
+  }
+  kk[0] = 0.5 * creal(T[0] + T[1]);
+  kk[2] = 0.5 * creal(T[0] - T[1]);
+  kk[1] = creal(T[2]);
+  kk[3] = cimag(T[2]);
+  for (int q = 0; q < 4; ++q) {
+    double complex d[3];
+    for (int j = 0; j < 3; ++j)
+      d[j] = q == 0 ? Tl[j] * dlt[j] : q == 1 ? Tl[j] * dlx[j] : q == 2 ? Tl[j] * dly[j] : Ts[j];
+    dkk[0][q] = 0.5 * creal(d[0] + d[1]);
+    dkk[2][q] = 0.5 * creal(d[0] - d[1]);
+    dkk[1][q] = creal(d[2]);
+    dkk[3][q] = cimag(d[2]);
+  }
+}
+
+/* Normalisation N and its gradient (cell centres inside the region, dA per cell). */
+static double tddp_norm(const orc_dkin* k, int nres, const orc_res* res, const orc_tpar* tp,
+                        const double* p, int np, int nbx, int nby, double* dN) {
+  double x0, x1, y0, y1;
+  dalitz_box(k, &x0, &x1, &y0, &y1);
+  double hx = (x1 - x0) / nbx, hy = (y1 - y0) / nby, dA = hx * hy;
+  double kk[4], dkk[4][4];
+  tddp_time(p, tp, 0, 1, 1, kk, dkk);
+  orc_acc s = {0, 0};
+  orc_acc* gs = (orc_acc*)calloc(np, sizeof(orc_acc));
+  orc_acc sk[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  double* g = (double*)malloc(sizeof(double) * np);
+  double complex a[64], b[64], A, B;
+  for (int i = 0; i < nbx; ++i)
+    for (int j = 0; j < nby; ++j) {
+      double s12 = x0 + (i + 0.5) * hx, s13 = y0 + (j + 0.5) * hy;
+      if (!orc_dalitz_inside(k, s12, s13)) continue;
+      tddp_amps(k, nres, res, p, s12, s13, &A, &B, a, b);
+      double dk[4];
+      memset(g, 0, sizeof(double) * np);
+      acc_add(&s, tddp_comb(nres, res, A, B, a, b, kk, 1.0, dN ? g : NULL, dk));
+      if (dN) {
+        for (int q = 0; q < np; ++q) acc_add(&gs[q], g[q]);
+        for (int j = 0; j < 4; ++j) acc_add(&sk[j], dk[j]);
+      }
+    }
+  if (dN) {
+    for (int q = 0; q < np; ++q) dN[q] = dA * acc_get(&gs[q]);
+    int ip[4] = {tp->p_tau, tp->p_x, tp->p_y, tp->p_s};
+    for (int q = 0; q < 4; ++q)
+      for (int j = 0; j < 4; ++j) dN[ip[q]] += dA * acc_get(&sk[j]) * dkk[j][q];
+  }
+  free(gs);
+  free(g);
+  return dA * acc_get(&s);
+}
+
+/* Per-event intensity I (unnormalised) with gradient g (optional). */
+static double tddp_event(const orc_dkin* k, int nres, const orc_res* res, const orc_tpar* tp,
+                         const double* p, int np, double s12, double s13, double t, double sigt,
+                         double* g) {
+  double kk[4], dkk[4][4], dk[4];
+  tddp_time(p, tp, t, sigt, 0, kk, dkk);
+  double complex a[64], b[64], A, B;
+  tddp_amps(k, nres, res, p, s12, s13, &A, &B, a, b);
+  if (g) memset(g, 0, sizeof(double) * np);
+  double v = tddp_comb(nres, res, A, B, a, b, kk, 1.0, g, dk);
+  if (g) {
+    int ip[4] = {tp->p_tau, tp->p_x, tp->p_y, tp->p_s};
+    for (int q = 0; q < 4; ++q)
+      for (int j = 0; j < 4; ++j) g[ip[q]] += dk[j] * dkk[j][q];
+  }
+  return v;
+}
+
+int orc_tddp_intensity(const orc_dkin* k, int nres, const orc_res* res, const orc_tpar* tp,
+                       const double* p, int np, int64_t n, const double* s12, const double* s13,
+                       const double* t, const double* sigt, double* out) {
+  for (int64_t i = 0; i < n; ++i)
+    out[i] = tddp_event(k, nres, res, tp, p, np, s12[i], s13[i], t[i], sigt[i], NULL);
+  return 0;
+}
+
+double orc_tddp_norm(const orc_dkin* k, int nres, const orc_res* res, const orc_tpar* tp,
+                     const double* p, int np, int nbx, int nby, double* dN) {
+  return tddp_norm(k, nres, res, tp, p, np, nbx, nby, dN);
+}
+
+/* NLL = -sum_i log(I_i / N) and its gradient. */
+int orc_tddp_nll(const orc_dkin* k, int nres, const orc_res* res, const orc_tpar* tp,
+                 const double* p, int np, int nbx, int nby, int64_t n, const double* s12,
+                 const double* s13, const double* t, const double* sigt, double* nll,
+                 double* grad) {
+  double* dN = grad ? (double*)calloc(np, sizeof(double)) : NULL;
+  double N = tddp_norm(k, nres, res, tp, p, np, nbx, nby, dN);
+  orc_acc s = {0, 0};
+  orc_acc* gs = (orc_acc*)calloc(np, sizeof(orc_acc));
+  double* g = (double*)malloc(sizeof(double) * np);
+  for (int64_t i = 0; i < n; ++i) {
+    double v = tddp_event(k, nres, res, tp, p, np, s12[i], s13[i], t[i], sigt[i], grad ? g : NULL);
+    acc_add(&s, -log(v));
+    if (grad) for (int q = 0; q < np; ++q) acc_add(&gs[q], -g[q] / v);
+  }
+  *nll = acc_get(&s) + (double)n * log(N);
+  if (grad) for (int q = 0; q < np; ++q) grad[q] = acc_get(&gs[q]) + (double)n * dN[q] / N;
+  free(gs);
+  free(g);
+  free(dN);
+  return 0;
+}

@@ -914,3 +914,94 @@ def test_mapped_composite_gradient_fd(which):
                     m.gauss(1, m.param(1.0), m.param(1.5)))
         idx = [0, 1, 2, 3, 4]
     _fd_check(lambda q: m.nll([x], q, grad=True), m.p, idx, rel=2e-6)
+
+
+# --------------------------------------------------------------------------------
+# Time-dependent Dalitz model (Sec. 4: the D0 -> pi+ pi- pi0 mixing fit)
+# --------------------------------------------------------------------------------
+@pytest.mark.parametrize("lam", [2.4, 2.4 * (1 - 0.3j), 2.4 * (1 + 0.05j)])
+@pytest.mark.parametrize("sig", [0.05, 0.3])
+def test_smeared_exponential_vs_quadrature(lam, sig):
+    """Int_0^inf e^{-lam u} Gauss(t - u; sigma) du by adaptive quadrature."""
+    ts = np.array([-0.8, -0.1, 0.0, 0.2, 1.0, 3.5])
+    T = oracle.smeared_exp(complex(lam), ts, sig)
+    for t, v in zip(ts, T):
+        f = lambda u, part: (np.exp(-complex(lam) * u) * stats.norm.pdf(t - u, scale=sig)).__getattribute__(part)
+        ref = (integrate.quad(f, 0, np.inf, args=("real",), epsabs=0, epsrel=1e-13, limit=200)[0]
+               + 1j * integrate.quad(f, 0, np.inf, args=("imag",), epsabs=0, epsrel=1e-13, limit=200)[0])
+        assert abs(v - ref) <= 1e-11 * max(abs(ref), 1e-3), (t, v, ref)
+
+
+def test_smeared_exponential_real_rate_is_exponnorm():
+    lam, sig = 2.4, 0.12
+    ts = np.linspace(-1.0, 6.0, 57)
+    T = oracle.smeared_exp(lam, ts, sig).real
+    ref = stats.exponnorm.pdf(ts, 1.0 / (lam * sig), scale=sig) / lam
+    assert np.max(np.abs(T / ref - 1)) < 1e-12
+
+
+def _tddp_model(nbx=48, nby=48, tau=0.41, x=0.01, y=0.007, scale=1.1):
+    spec = om.load_dalitz_spec()
+    k = spec["kin"]
+    d = oracle.Tddp(k["M"], k["m1"], k["m2"], k["m3"], k["R"], nbx, nby)
+    for r in spec["resonances"]:
+        idx = [d.param(r[f]) for f in ("m0", "g0", "re", "im")]
+        d.resonance(r["channel"], r["spin"], *idx)
+    d.time_params(d.param(tau), d.param(x), d.param(y), d.param(scale))
+    return d, spec
+
+
+def _tddp_events(d, spec, n, seed=3):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    s12, s13 = synth.dalitz_events(n, om.dalitz_accept(d, spec["envelope"]), seed=seed)
+    sigt = rng.uniform(0.05, 0.15, n)
+    t = rng.exponential(0.41, n) + sigt * rng.standard_normal(n)
+    return s12, s13, t, sigt
+
+
+def test_tddp_without_mixing_is_dalitz_times_exponnorm():
+    """x = y = 0: the intensity factorises into |A|^2 and the smeared exponential, so
+    the NLL is the (separately pinned) Dalitz NLL plus -sum log of scipy's exponentially
+    modified normal density."""
+    d, spec = _tddp_model(x=0.0, y=0.0)
+    s12, s13, t, sigt = _tddp_events(d, spec, 300)
+    f = d.nll_t(s12, s13, t, sigt)
+    dz = om.dalitz_from_spec(spec, nbx=48, nby=48)
+    fd = dz.nll(s12, s13)
+    tau, sc = 0.41, 1.1
+    ft = -np.sum(np.log(stats.exponnorm.pdf(t, tau / (sc * sigt), scale=sc * sigt)))
+    assert abs(f - (fd + ft)) <= 1e-11 * abs(f)
+
+
+def test_tddp_time_integral_of_the_intensity():
+    """Integrating the smeared intensity over t reproduces the time integral of the
+    unsmeared mixing formula (quadrature of e^{-Gt} cosh/cos/sinh/sin)."""
+    d, spec = _tddp_model()
+    tau, x, y = 0.41, 0.01, 0.007
+    G = 1 / tau
+    for s12, s13 in ((0.9, 1.1), (1.6, 0.7), (0.4, 2.1)):
+        assert d.inside([s12], [s13])[0]
+        A = 1 + sum((r["re"] + 1j * r["im"]) * d.amp(i, [s12], [s13])[0]
+                    for i, r in enumerate(spec["resonances"]))
+        s23 = sum(v ** 2 for v in (spec["kin"]["M"], spec["kin"]["m1"], spec["kin"]["m2"],
+                                   spec["kin"]["m3"])) - s12 - s13
+        B = 1 + sum((r["re"] + 1j * r["im"]) * d.amp(i, [s12], [s23])[0]
+                    for i, r in enumerate(spec["resonances"]))
+        aa, bb, xab = abs(A) ** 2, abs(B) ** 2, np.conj(A) * B
+
+        def unsmeared(u):
+            e = math.exp(-G * u)
+            return e * (0.5 * (aa + bb) * math.cosh(y * G * u) + 0.5 * (aa - bb) * math.cos(x * G * u)
+                        + xab.real * math.sinh(y * G * u) - xab.imag * math.sin(x * G * u))
+        ref = integrate.quad(unsmeared, 0, np.inf, epsabs=0, epsrel=1e-12, limit=200)[0]
+        got = integrate.quad(lambda u: d.intensity_t([s12], [s13], [u], [0.1])[0], -2.0, 12.0,
+                             points=[0.0], epsabs=0, epsrel=1e-12, limit=400)[0]
+        assert abs(got / ref - 1) < 1e-9
+
+
+def test_tddp_gradient_fd():
+    d, spec = _tddp_model(nbx=24, nby=24)
+    s12, s13, t, sigt = _tddp_events(d, spec, 200)
+    p = d.p
+    free = [i for i in range(len(p)) if i % 4 >= 2 and i < 32] + [32, 33, 34, 35]
+    _fd_check(lambda q: d.nll_t(s12, s13, t, sigt, p=q, grad=True), p, free, rel=2e-6)
