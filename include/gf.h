@@ -156,6 +156,20 @@ typedef struct {
 } gf_resonance;
 int gf_pdf_dalitz(gf_ctx* ctx, int obs12, int obs13, const gf_dalitz_kin* kin, int nres,
                   const gf_resonance* res, int* node);
+/* Time-dependent Dalitz model (Sec. 4: the D0 -> pi+ pi- pi0 mixing fit): the amplitude
+ * model of gf_pdf_dalitz (resonance shapes fixed; particles 1 and 2 CP conjugates, m1 =
+ * m2) for D0 (A at (s12, s13)) and D0bar (B, the same sum at (s12, s23)), with the decay
+ * time t and its per-event uncertainty sigma_t:
+ *   I = 1/2 (|A|^2 + |B|^2) Tch + 1/2 (|A|^2 - |B|^2) Tc + Re(A* B) Tsh - Im(A* B) Ts,
+ * the time factors e^{-t/tau} {cosh(y t/tau), cos(x t/tau), sinh(y t/tau),
+ * sin(x t/tau)} (t >= 0) each convolved with a Gaussian of width scale * sigma_t.
+ * Normalised over the Dalitz grid (gf_set_norm_grid; default 256 x 256 cells) and all t;
+ * conditional on sigma_t.  tau, x, y, scale are parameter ids.  The data set holds the
+ * columns s12, s13, t, sigma_t in this order (sigma_t > 0).  Evaluated in FP64 in both
+ * precision modes. */
+int gf_pdf_tddp(gf_ctx* ctx, int obs12, int obs13, int obs_t, int obs_sigt,
+                const gf_dalitz_kin* kin, int nres, const gf_resonance* res, int tau, int x,
+                int y, int scale, int* node);
 /* Grid of the node's numerical normalisation: nbins_x bins for a 1D leaf, the lattice
  * of a convolution, or nbins_x x nbins_y cells for a Dalitz node. */
 int gf_set_norm_grid(gf_ctx* ctx, int node, int nbins_x, int nbins_y);

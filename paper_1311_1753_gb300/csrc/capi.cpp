@@ -139,6 +139,9 @@ static void free_dev(gf_ctx* ctx) {
   cudaFree(d.perm);
   cudaFree(d.bw);
   cudaFree(d.bs2);
+  cudaFree(d.tddp_cache);
+  cudaFree(d.tddp_gcols);
+  cudaFree(d.tddp_gram);
   for (void* p : d.conv_bufs) cudaFree(p);
   for (void* p : d.gn_bufs) cudaFree(p);
   for (auto& g : d.graph)
@@ -429,10 +432,34 @@ int gf_pdf_dalitz(gf_ctx* ctx, int obs12, int obs13, const gf_dalitz_kin* kin, i
   return add_node(ctx, std::move(nd), node);
 }
 
+int gf_pdf_tddp(gf_ctx* ctx, int obs12, int obs13, int obs_t, int obs_sigt,
+                const gf_dalitz_kin* kin, int nres, const gf_resonance* res, int tau, int x,
+                int y, int scale, int* node) {
+  if (!ctx) return GF_EINVAL;
+  int id = -1;
+  int rc = gf_pdf_dalitz(ctx, obs12, obs13, kin, nres, res, &id);
+  if (rc) return rc;
+  NodeDef& nd = ctx->nodes[id];
+  if (!valid_obs(ctx, obs_t) || !valid_obs(ctx, obs_sigt) || obs_t == obs_sigt ||
+      obs_t == obs12 || obs_t == obs13 || obs_sigt == obs12 || obs_sigt == obs13)
+    return set_error(ctx, GF_EINVAL, "time-dependent Dalitz: bad time observables");
+  if (!(std::fabs(kin->m1 - kin->m2) <= 1e-12 * kin->m1))
+    return set_error(ctx, GF_EINVAL, "time-dependent Dalitz: particles 1 and 2 are CP conjugates (m1 = m2)");
+  for (int p : {tau, x, y, scale})
+    if (!valid_par(ctx, p)) return set_error(ctx, GF_EINVAL, "time-dependent Dalitz: unknown parameter id");
+  nd.type = N_TDDP;
+  nd.obs3 = obs_t;
+  nd.obs4 = obs_sigt;
+  nd.pars = {tau, x, y, scale};
+  nd.nbx = nd.nby = 256;
+  *node = id;
+  return GF_OK;
+}
+
 int gf_set_norm_grid(gf_ctx* ctx, int node, int nbins_x, int nbins_y) {
   if (!ctx || !valid_node(ctx, node)) return GF_EINVAL;
   NodeDef& nd = ctx->nodes[node];
-  if (nd.type == N_DALITZ) {
+  if (nd.type == N_DALITZ || nd.type == N_TDDP) {
     if (nbins_x < 1 || nbins_y < 1 || (int64_t)nbins_x * nbins_y > (1 << 26))
       return set_error(ctx, GF_EINVAL, "Dalitz grid: 1 <= nbx*nby <= 2^26");
     nd.nby = nbins_y;
@@ -501,7 +528,8 @@ static bool dalitz_inside_host(const DalitzPlan& D, double s12, double s13) {
 
 extern "C" int gf_dalitz_inside(gf_ctx* ctx, int node, int64_t n, const double* s12,
                                 const double* s13, int8_t* out) {
-  if (!ctx || !valid_node(ctx, node) || ctx->nodes[node].type != N_DALITZ || n < 0 ||
+  if (!ctx || !valid_node(ctx, node) ||
+      (ctx->nodes[node].type != N_DALITZ && ctx->nodes[node].type != N_TDDP) || n < 0 ||
       (n > 0 && (!s12 || !s13 || !out)))
     return GF_EINVAL;
   DalitzPlan D{};
@@ -1137,6 +1165,53 @@ int ensure_compiled(gf_ctx* ctx) {
   DevState& d = ctx->dev;
   std::vector<int> col_of_obs(ctx->obs.size(), -1);
   for (int k = 0; k < (int)d.obs_ids.size(); ++k) col_of_obs[d.obs_ids[k]] = k;
+  ctx->is_tddp = false;
+  if (root.type == N_TDDP) {
+    if (d.binned || ctx->metric != GF_METRIC_NLL)
+      return set_error(ctx, GF_EINVAL, "binned data and binned metrics are for 1D trees");
+    if (col_of_obs[root.obs] != 0 || col_of_obs[root.obs2] != 1 || col_of_obs[root.obs3] != 2 ||
+        col_of_obs[root.obs4] != 3)
+      return set_error(ctx, GF_EINVAL,
+                       "time-dependent Dalitz data: columns s12, s13, t, sigma_t in this order");
+    if ((int)ctx->pars.size() > 4 * kMaxRes + 8)
+      return set_error(ctx, GF_EINVAL, "time-dependent Dalitz: at most 56 parameters in the context");
+    ctx->is_tddp = true;
+    ctx->is_dalitz = false;
+    ctx->has_grid = false;
+    TddpPlan& T = ctx->tplan;
+    T = TddpPlan{};
+    dalitz_geometry(root, T.D);
+    T.D.nres = (int)root.res.size();
+    T.D.nfree = nf;
+    T.nfree = nf;
+    for (int r = 0; r < T.D.nres; ++r) {
+      const gf_resonance& R = root.res[r];
+      if (ctx->free_pos[R.mass] >= 0 || ctx->free_pos[R.width] >= 0)
+        return set_error(ctx, GF_EINVAL, "time-dependent Dalitz: resonance shapes must be fixed");
+      DalitzRes& X = T.D.res[r];
+      X.channel = R.channel;
+      X.spin = R.spin;
+      X.p_m0 = R.mass;
+      X.p_g0 = R.width;
+      X.p_re = R.re;
+      X.p_im = R.im;
+      X.g_m0 = X.g_g0 = -1;
+      X.g_re = ctx->free_pos[R.re];
+      X.g_im = ctx->free_pos[R.im];
+      X.ev_cached = r;
+      X.grid_col = r + 1;
+    }
+    T.p_tau = root.pars[0];
+    T.p_x = root.pars[1];
+    T.p_y = root.pars[2];
+    T.p_s = root.pars[3];
+    T.g_tau = ctx->free_pos[T.p_tau];
+    T.g_x = ctx->free_pos[T.p_x];
+    T.g_y = ctx->free_pos[T.p_y];
+    T.g_s = ctx->free_pos[T.p_s];
+    ctx->compiled = true;
+    return GF_OK;
+  }
   if (root.type == N_DALITZ) {
     if (d.binned || ctx->metric != GF_METRIC_NLL)
       return set_error(ctx, GF_EINVAL, "binned data and binned metrics are for 1D trees");
@@ -1403,6 +1478,26 @@ static int finish_set_data(gf_ctx* ctx) {
   if (rc) return rc;
   rc = ensure_compiled(ctx);
   if (rc) return rc;
+  if (ctx->is_tddp) {
+    const TddpPlan& T = ctx->tplan;
+    const int64_t want = (d.n + kThreads - 1) / kThreads;
+    d.nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->sm_count * 4));
+    rc = grow(ctx, &d.partials, &d.partials_cap, (size_t)std::max(d.nblocks, 2048) * 64);
+    if (rc) return rc;
+    const size_t ncell = (size_t)T.D.nbx * T.D.nby;
+    cudaFree(d.inside);
+    cudaFree(d.tddp_cache);
+    cudaFree(d.tddp_gcols);
+    cudaFree(d.tddp_gram);
+    d.inside = nullptr;
+    d.tddp_cache = d.tddp_gcols = d.tddp_gram = nullptr;
+    CK(cudaMalloc(&d.inside, ncell));
+    CK(cudaMalloc(&d.tddp_cache, sizeof(double2) * 2 * std::max(T.D.nres, 1) * (size_t)std::max<int64_t>(d.n, 1)));
+    CK(cudaMalloc(&d.tddp_gcols, sizeof(double2) * 2 * std::max(T.D.nres, 1) * ncell));
+    CK(cudaMalloc(&d.tddp_gram, sizeof(double2) * 3 * (kMaxRes + 1) * (kMaxRes + 1)));
+    d.tddp_ready = false;
+    return GF_OK;
+  }
   // event-stream grid: a multiple of the SM count, capped by the work
   int per_sm;
   if (ctx->is_dalitz) {
@@ -1547,10 +1642,18 @@ extern "C" int gf_set_data(gf_ctx* ctx, int root, const gf_dataset* ds) {
   if (!ctx || !ds || ds->ctx != ctx || !valid_node(ctx, root)) return GF_EINVAL;
   CK(cudaSetDevice(ctx->device));
   const NodeDef& nd = ctx->nodes[root];
-  if (nd.type == N_DALITZ) {
+  if (nd.type == N_DALITZ || nd.type == N_TDDP) {
     // both observables as columns 0, 1 and every event inside the kinematic region
     if (ds->obs.size() < 2 || ds->obs[0] != nd.obs || ds->obs[1] != nd.obs2)
       return set_error(ctx, GF_EINVAL, "Dalitz data set must hold (s12, s13) as columns 0, 1");
+    if (nd.type == N_TDDP) {
+      if (ds->obs.size() != 4 || ds->obs[2] != nd.obs3 || ds->obs[3] != nd.obs4)
+        return set_error(ctx, GF_EINVAL,
+                         "time-dependent Dalitz data: columns s12, s13, t, sigma_t in this order");
+      for (int64_t i = 0; i < ds->n; ++i)
+        if (!(ds->cols[3][i] > 0.0))
+          return set_error(ctx, GF_EINVAL, "event " + std::to_string(i) + ": sigma_t must be > 0");
+    }
     DalitzPlan D{};
     dalitz_geometry(nd, D);
     for (int64_t i = 0; i < ds->n; ++i)
@@ -1838,6 +1941,38 @@ static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool capt
   return GF_OK;
 }
 
+// Time-dependent Dalitz model: theta upload, the caches on the first evaluation after a
+// data load (cell mask, per-event amplitudes, grid sums; the resonance shapes are fixed),
+// then the event pass (every block forms N from the grid sums), storing per-event log P
+// when out_logp is given; launched directly (no graph).
+static int tddp_enqueue(gf_ctx* ctx, bool grad, double* out_logp, int* launches) {
+  DevState& d = ctx->dev;
+  const TddpPlan& T = ctx->tplan;
+  int rc = enqueue_uploads(ctx);
+  if (rc) return rc;
+  CK(cudaEventRecord(d.ev0, ctx->stream));
+  if (!d.tddp_ready) {
+    CK(launch_dalitz_mask(T.D, d.inside, ctx->stream));
+    CK(launch_tddp_cache(T, d.theta, d.cols[0], d.cols[1], d.n, d.tddp_cache, ctx->stream));
+    CK(launch_tddp_gram(T, d.theta, d.inside, d.tddp_gcols, d.tddp_gram, ctx->stream));
+    *launches += 4;
+    d.tddp_ready = true;
+  }
+  CK(cudaEventRecord(d.evm, ctx->stream));
+  const double* cols[4] = {d.cols[0], d.cols[1], d.cols[2], d.cols[3]};
+  CK(launch_tddp_events(T, grad, d.theta, cols, d.n, d.tddp_cache, d.tddp_gram, d.partials,
+                        d.counters, d.result, out_logp, d.nblocks, weideman(), ctx->stream));
+  (*launches)++;
+  CK(cudaEventRecord(d.ev1, ctx->stream));
+  if (!out_logp) {
+    CK(cudaMemcpyAsync(d.h_result, d.result, sizeof(double) * (1 + (grad ? T.nfree : 0)),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(reinterpret_cast<int*>(d.h_result + 63), d.flag, sizeof(int),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  return GF_OK;
+}
+
 int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64) {
   int rc = ensure_compiled(ctx);
   if (rc) return rc;
@@ -1846,6 +1981,13 @@ int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64) {
   CK(cudaSetDevice(ctx->device));
   rc = fill_theta_host(ctx, theta);
   if (rc) return rc;
+  if (ctx->is_tddp) {
+    int launches = 0;
+    rc = tddp_enqueue(ctx, grad, nullptr, &launches);
+    ctx->last_launches = launches;
+    ctx->last_graph = false;
+    return rc;
+  }
   // steady state: replay the evaluation graph of this (grad, fp64, normalisation mode)
   bool direct = false;
   const bool mixed = ctx->precision == GF_MIXED && !fp64;
@@ -1955,6 +2097,7 @@ int tick_prepare(gf_ctx* ctx) {
   if (d.tick_desc) return d.tick_kind;
   if (!ctx->compiled || !d.theta || d.n <= 0) return 0;
   if (d.nconv > 0 || d.ngn > 0) return 0;  // tables / grid normalisations: per-fit evaluations
+  if (ctx->is_tddp) return 0;
   CK(cudaSetDevice(ctx->device));
   if (!ctx->is_dalitz) {
     Fit1D F{};
@@ -2059,7 +2202,9 @@ static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host)
   double* dst = out;
   if (host) CK(cudaMalloc(&dst, sizeof(double) * std::max<int64_t>(d.n, 1)));
   int launches = 0;
-  if (ctx->is_dalitz) {
+  if (ctx->is_tddp) {
+    rc = tddp_enqueue(ctx, false, dst, &launches);
+  } else if (ctx->is_dalitz) {
     int mode = 0;
     rc = dalitz_prepare(ctx, &mode, &launches, ctx->precision == GF_MIXED);
     if (rc == GF_OK) {
@@ -2163,6 +2308,7 @@ int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
   if (!d.owns_cols || !d.theta) return set_error(ctx, GF_ESTATE, "no data set owned by the context");
   if (n != d.n) return set_error(ctx, GF_EINVAL, "gf_update_data: n must equal the loaded size");
   if (d.binned) return set_error(ctx, GF_EINVAL, "gf_update_data: binned data go through gf_set_data");
+  d.tddp_ready = false;  // per-event amplitudes of the new events
   int rc = ensure_compiled(ctx);
   if (rc) return rc;
   CK(cudaSetDevice(ctx->device));

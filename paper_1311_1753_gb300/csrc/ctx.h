@@ -13,7 +13,7 @@
 namespace gfi {
 
 enum NodeType { N_EXP = 1, N_GAUSS, N_VOIGT, N_THRESH, N_POLY, N_RELBW, N_ADD = 10, N_PROD,
-                N_DALITZ, N_CONV, N_MAPPED, N_COMPOSITE };
+                N_DALITZ, N_CONV, N_MAPPED, N_COMPOSITE, N_TDDP };
 
 struct ObsDef {
   std::string name;
@@ -26,7 +26,7 @@ struct ParDef {
 };
 struct NodeDef {
   int type;
-  int obs = -1, obs2 = -1;
+  int obs = -1, obs2 = -1, obs3 = -1, obs4 = -1;  // N_TDDP: s12, s13, t, sigma_t
   std::vector<int> pars;      // leaf parameters / ADD fractions
   std::vector<int> children;  // ADD / PROD
   int nbx = 10000, nby = 0;   // normalisation grid (N_CONV: lattice bins, default 1000)
@@ -92,6 +92,11 @@ struct DevState {
   GNormDesc* gn_desc[kMaxGNorm] = {};
   GNormDesc gn_host[kMaxGNorm] = {};
   int ngn = 0;
+  // time-dependent Dalitz model: per-event amplitudes, grid columns, the three grid sums
+  double2* tddp_cache = nullptr;
+  double2* tddp_gcols = nullptr;
+  double2* tddp_gram = nullptr;
+  bool tddp_ready = false;             // caches built for the loaded events
   // binned data: bin contents and chi-squared variances (device), N x bin volume
   bool binned = false;
   double* bw = nullptr;
@@ -126,6 +131,8 @@ struct gf_ctx {
   int root = -1;
   bool compiled = false;
   bool is_dalitz = false;
+  bool is_tddp = false;      // time-dependent Dalitz model (Sec. 4's mixing fit)
+  gfi::TddpPlan tplan{};
   bool has_grid = false;
   gfi::Program prog{};
   gfi::DalitzPlan dplan{};

@@ -11,6 +11,7 @@ constexpr double kInvSqrtPi = 0.56418958354775628695;  // 1/sqrt(pi)
 constexpr double kTwoInvSqrtPi = 1.12837916709551257390;
 constexpr double kSqrt2 = 1.41421356237309504880;
 constexpr double kSqrt2Pi = 2.50662827463100050242;
+constexpr double kInvSqrt2Pi = 0.39894228040143267794;  // 1/sqrt(2 pi)
 
 // ---- compensated accumulation ------------------------------------------------------
 // FP64: plain sum (a thread adds O(100) terms).  FP32: Kahan pair, converted to FP64

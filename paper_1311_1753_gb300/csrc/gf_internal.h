@@ -172,6 +172,17 @@ struct DalitzPlan {
   DalitzRes res[kMaxRes];
 };
 
+// ---- time-dependent Dalitz model (Sec. 4: the mixing fit) -------------------------------
+// The Dalitz plan (fixed resonance shapes) plus the time parameters: tau, mixing x, y and
+// the resolution scale s (sigma = s sigma_t per event); theta_all indices and free
+// indices (-1: fixed).  Data columns: s12, s13, t, sigma_t.
+struct TddpPlan {
+  DalitzPlan D;
+  int32_t p_tau, p_x, p_y, p_s;
+  int32_t g_tau, g_x, g_y, g_s;
+  int32_t nfree, pad;
+};
+
 // ---- batched evaluation of many fits (one fit-server tick) ----------------------------
 // Per-fit descriptors live in device memory; a tick's work list holds one TickItem per fit
 // per launch: items item0 .. item0 + nitems - 1 of the launch are that fit's virtual

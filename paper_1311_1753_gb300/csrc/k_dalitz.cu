@@ -1065,4 +1065,367 @@ int dalitz_blocks_per_sm(bool mixed, bool grad, bool cached_only, int nfree) {
   return nb > 0 ? nb : 1;
 }
 
+// ---- time-dependent Dalitz model (Sec. 4: the D0 -> pi+ pi- pi0 mixing fit) -------------
+// Intensity I = 1/2 (|A|^2 + |B|^2) Tch + 1/2 (|A|^2 - |B|^2) Tc + Re(A* B) Tsh - Im(A* B) Ts,
+// A = 1 + sum_r c_r a_r at (s12, s13), B the same sum at (s12, s23) (pi+ and pi- exchanged),
+// Tch = (T(l1) + T(l2))/2, Tsh = (T(l1) - T(l2))/2, Tc + i Ts = T(l3), l1 = G(1 - y),
+// l2 = G(1 + y), l3 = G(1 - i x), G = 1/tau, T(l) = e^{-l t} (t >= 0) convolved with a
+// Gaussian of width s sigma_t; normalised over the Dalitz grid and all t, where the time
+// integrals are 1/l.  FP64 throughout (the amplitudes come from a per-event cache, the
+// resonance shapes being fixed).
+
+// Per-event amplitudes a_r, b_r: the resonance code of the Dalitz event pass in FP64.
+__global__ void __launch_bounds__(kThreads) k_tddp_cache(const __grid_constant__ TddpPlan T,
+                                                        const double* __restrict__ theta,
+                                                        const double* __restrict__ s12,
+                                                        const double* __restrict__ s13, int64_t n,
+                                                        double2* __restrict__ cache) {
+  const DalitzPlan& D = T.D;
+  __shared__ ResK rk[kMaxRes];
+  __shared__ DzC<double> C;
+  if (threadIdx.x < D.nres) res_constants(D, D.res[threadIdx.x], theta, rk[threadIdx.x]);
+  __syncthreads();
+  fill_dzc<double>(D, rk, C);
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = s12[i], y = s13[i], z = D.sum_m2 - x - y;
+    for (int r = 0; r < D.nres; ++r) {
+      const DalitzRes& R = D.res[r];
+      ChanK<double> k;
+      C2<double> A, BW;
+      double FS, Gm;
+      chan_kin_c<double>(C, R.channel, x, y, z, k);
+      res_amp_c<double>(R, C, r, k, A, FS, BW, Gm);
+      cache[(size_t)r * n + i] = make_double2(A.r, A.i);
+      chan_kin_c<double>(C, R.channel, x, z, y, k);  // (s12, s23): the CP-conjugate point
+      res_amp_c<double>(R, C, r, k, A, FS, BW, Gm);
+      cache[(size_t)(D.nres + r) * n + i] = make_double2(A.r, A.i);
+    }
+  }
+}
+
+// Grid columns a_r, b_r at the cell centres inside the region (zero outside).
+__global__ void __launch_bounds__(kThreads) k_tddp_gcols(const __grid_constant__ TddpPlan T,
+                                                        const double* __restrict__ theta,
+                                                        const uint8_t* __restrict__ inside,
+                                                        double2* __restrict__ gcols) {
+  const DalitzPlan& D = T.D;
+  __shared__ ResK rk[kMaxRes];
+  __shared__ DzC<double> C;
+  if (threadIdx.x < D.nres) res_constants(D, D.res[threadIdx.x], theta, rk[threadIdx.x]);
+  __syncthreads();
+  fill_dzc<double>(D, rk, C);
+  __syncthreads();
+  const int64_t ncell = (int64_t)D.nbx * D.nby;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncell;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int ix = (int)(i / D.nby), iy = (int)(i % D.nby);
+    const double x = D.x0 + (ix + 0.5) * D.hx, y = D.y0 + (iy + 0.5) * D.hy;
+    const double z = D.sum_m2 - x - y;
+    for (int r = 0; r < D.nres; ++r) {
+      double2 a = make_double2(0.0, 0.0), b = a;
+      if (inside[i]) {
+        const DalitzRes& R = D.res[r];
+        ChanK<double> k;
+        C2<double> A, BW;
+        double FS, Gm;
+        chan_kin_c<double>(C, R.channel, x, y, z, k);
+        res_amp_c<double>(R, C, r, k, A, FS, BW, Gm);
+        a = make_double2(A.r, A.i);
+        chan_kin_c<double>(C, R.channel, x, z, y, k);
+        res_amp_c<double>(R, C, r, k, A, FS, BW, Gm);
+        b = make_double2(A.r, A.i);
+      }
+      gcols[(size_t)r * ncell + i] = a;
+      gcols[(size_t)(D.nres + r) * ncell + i] = b;
+    }
+  }
+}
+
+// One block per entry (m, r, s) of the three matrices: dA sum_cells conj(u_r) v_s with
+// (u, v) = (a, a), (b, b), (a, b) and index 0 the constant 1 (inside cells only), in a
+// fixed order (per-thread FP64 sums, block_sum).
+__global__ void __launch_bounds__(kThreads) k_tddp_gram(const __grid_constant__ TddpPlan T,
+                                                       const uint8_t* __restrict__ inside,
+                                                       const double2* __restrict__ gcols,
+                                                       double2* __restrict__ gram) {
+  const DalitzPlan& D = T.D;
+  const int K1 = D.nres + 1;
+  const int e = blockIdx.x, m = e / (K1 * K1), r = (e / K1) % K1, q = e % K1;
+  const int64_t ncell = (int64_t)D.nbx * D.nby;
+  const int ur = m == 1 ? 1 : 0, vs = m == 0 ? 0 : 1;  // 0: a columns, 1: b columns
+  const double2* U = r > 0 ? gcols + (size_t)(ur * D.nres + r - 1) * ncell : nullptr;
+  const double2* V = q > 0 ? gcols + (size_t)(vs * D.nres + q - 1) * ncell : nullptr;
+  double sr = 0.0, si = 0.0;
+  for (int64_t i = threadIdx.x; i < ncell; i += blockDim.x) {
+    if (!inside[i]) continue;
+    const double2 u = U ? U[i] : make_double2(1.0, 0.0);
+    const double2 v = V ? V[i] : make_double2(1.0, 0.0);
+    sr += u.x * v.x + u.y * v.y;  // conj(u) v
+    si += u.x * v.y - u.y * v.x;
+  }
+  __shared__ double red[32];
+  const double tr = block_sum(sr, red);
+  __syncthreads();
+  const double ti = block_sum(si, red);
+  if (threadIdx.x == 0) gram[e] = make_double2(tr * D.hx * D.hy, ti * D.hx * D.hy);
+}
+
+// T(l; t, sigma) and dT/dl, dT/dsigma for complex l = (lr, li) (FP64; Faddeeva by
+// Weideman's series for the complex rate, erfcx for real ones):
+//   T = 1/2 e^{-t^2/(2 sigma^2)} w(i u), u = (l sigma^2 - t)/(sigma sqrt2), Re u >= 0,
+//   T = e^{l^2 sigma^2/2 - l t} - 1/2 e^{-t^2/(2 sigma^2)} w(-i u), Re u < 0 (reflection);
+//   dT/dl = (l sigma^2 - t) T - sigma/sqrt(2 pi) e^{-t^2/(2 sigma^2)},
+//   dT/dsigma = l^2 sigma T - e^{-t^2/(2 sigma^2)} (l sigma^2 + t)/(sqrt(2 pi) sigma^2).
+struct Cx {
+  double r, i;
+};
+__device__ __forceinline__ Cx cmul(Cx a, Cx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ __forceinline__ Cx cinv(Cx a) {
+  const double d = 1.0 / (a.r * a.r + a.i * a.i);
+  return {a.r * d, -a.i * d};
+}
+__device__ void smeared_exp(Cx l, double t, double sig, const WeidCoef& W, Cx& T, Cx& dl, Cx& ds) {
+  const double k = 1.0 / (sig * kSqrt2);
+  const Cx u = {(l.r * sig * sig - t) * k, l.i * sig * sig * k};
+  const double g = exp(-0.5 * t * t / (sig * sig));
+  Cx w;
+  if (u.r >= 0.0) {
+    if (l.i == 0.0) w = {erfcx(u.r), 0.0};
+    else faddeeva_df(-u.i, u.r, W, w.r, w.i);  // w(i u), i u = -ui + i ur
+    T = {0.5 * g * w.r, 0.5 * g * w.i};
+  } else {
+    if (l.i == 0.0) w = {erfcx(-u.r), 0.0};
+    else faddeeva_df(u.i, -u.r, W, w.r, w.i);  // w(-i u)
+    // e^{l^2 sigma^2/2 - l t}
+    const double er = 0.5 * (l.r * l.r - l.i * l.i) * sig * sig - l.r * t;
+    const double ei = l.r * l.i * sig * sig - l.i * t;
+    const double m = exp(er);
+    double sn, cs;
+    sincos(ei, &sn, &cs);
+    T = {m * cs - 0.5 * g * w.r, m * sn - 0.5 * g * w.i};
+  }
+  const double c = sig * kInvSqrt2Pi;  // sigma / sqrt(2 pi)
+  const Cx a = {l.r * sig * sig - t, l.i * sig * sig};
+  const Cx aT = cmul(a, T);
+  dl = {aT.r - c * g, aT.i};
+  const Cx l2 = cmul(l, l);
+  const Cx l2T = cmul(l2, T);
+  const double f = g * kInvSqrt2Pi / (sig * sig);
+  ds = {l2T.r * sig - f * (l.r * sig * sig + t), l2T.i * sig - f * (l.i * sig * sig)};
+}
+
+// Rates and their derivatives in (tau, x, y): l_j and dl_j/d(tau, x, y).
+__device__ __forceinline__ void tddp_rates(double tau, double x, double y, Cx* l, Cx (*dl)[3]) {
+  const double G = 1.0 / tau, G2 = G * G;
+  l[0] = {G * (1 - y), 0.0};
+  l[1] = {G * (1 + y), 0.0};
+  l[2] = {G, -G * x};
+  dl[0][0] = {-(1 - y) * G2, 0.0};
+  dl[0][1] = {0.0, 0.0};
+  dl[0][2] = {-G, 0.0};
+  dl[1][0] = {-(1 + y) * G2, 0.0};
+  dl[1][1] = {0.0, 0.0};
+  dl[1][2] = {G, 0.0};
+  dl[2][0] = {-G2, x * G2};
+  dl[2][1] = {0.0, -G};
+  dl[2][2] = {0.0, 0.0};
+}
+
+// The normalisation N(theta) and dN/dtheta_free (thread-local; O(K^2)).
+__device__ void tddp_norm(const TddpPlan& T, const double* th, const double2* gram, double* N,
+                          double* dN) {
+  const DalitzPlan& D = T.D;
+  const int K1 = D.nres + 1;
+  Cx c[kMaxRes + 1];
+  c[0] = {1.0, 0.0};
+  for (int r = 0; r < D.nres; ++r) c[r + 1] = {th[D.res[r].p_re], th[D.res[r].p_im]};
+  // v_k = sum_s M_ks c_s for the three matrices; w_k = sum_r conj(c_r) X_rk
+  double GA = 0.0, GB = 0.0;
+  Cx X = {0.0, 0.0};
+  Cx vA[kMaxRes + 1], vB[kMaxRes + 1], uX[kMaxRes + 1], wX[kMaxRes + 1];
+  for (int a = 0; a < K1; ++a) {
+    vA[a] = vB[a] = uX[a] = wX[a] = {0.0, 0.0};
+    for (int b = 0; b < K1; ++b) {
+      const double2 ga = gram[a * K1 + b], gb = gram[K1 * K1 + a * K1 + b];
+      const double2 gx = gram[2 * K1 * K1 + a * K1 + b];
+      const Cx pa = cmul({ga.x, ga.y}, c[b]), pb = cmul({gb.x, gb.y}, c[b]);
+      const Cx px = cmul({gx.x, gx.y}, c[b]);
+      vA[a] = {vA[a].r + pa.r, vA[a].i + pa.i};
+      vB[a] = {vB[a].r + pb.r, vB[a].i + pb.i};
+      uX[a] = {uX[a].r + px.r, uX[a].i + px.i};
+      const double2 gxt = gram[2 * K1 * K1 + b * K1 + a];  // X_ba: conj(c_b) X_ba
+      const Cx q = cmul({c[b].r, -c[b].i}, {gxt.x, gxt.y});
+      wX[a] = {wX[a].r + q.r, wX[a].i + q.i};
+    }
+    const Cx cc = {c[a].r, -c[a].i};
+    GA += cmul(cc, vA[a]).r;
+    GB += cmul(cc, vB[a]).r;
+    const Cx t = cmul(cc, uX[a]);
+    X = {X.r + t.r, X.i + t.i};
+  }
+  Cx l[3], dl[3][3];
+  tddp_rates(th[T.p_tau], th[T.p_x], th[T.p_y], l, dl);
+  const Cx i1 = cinv(l[0]), i2 = cinv(l[1]), i3 = cinv(l[2]);
+  const double kk[4] = {0.5 * (i1.r + i2.r), i3.r, 0.5 * (i1.r - i2.r), i3.i};
+  const double dI[4] = {0.5 * (GA + GB), 0.5 * (GA - GB), X.r, -X.i};
+  *N = dI[0] * kk[0] + dI[1] * kk[1] + dI[2] * kk[2] + dI[3] * kk[3];
+  if (!dN) return;
+  for (int k = 0; k < T.nfree; ++k) dN[k] = 0.0;
+  for (int r = 0; r < D.nres; ++r)
+    for (int part = 0; part < 2; ++part) {
+      const int g = part ? D.res[r].g_im : D.res[r].g_re;
+      if (g < 0) continue;
+      const int a = r + 1;
+      // d/dRe c: 2 Re v, u + w; d/dIm c: 2 Im v, -i u + i w
+      const double dGA = 2.0 * (part ? vA[a].i : vA[a].r);
+      const double dGB = 2.0 * (part ? vB[a].i : vB[a].r);
+      const Cx dX = part ? Cx{uX[a].i - wX[a].i, -uX[a].r + wX[a].r}
+                         : Cx{uX[a].r + wX[a].r, uX[a].i + wX[a].i};
+      dN[g] += 0.5 * (dGA + dGB) * kk[0] + 0.5 * (dGA - dGB) * kk[1] + dX.r * kk[2] - dX.i * kk[3];
+    }
+  const int gp[3] = {T.g_tau, T.g_x, T.g_y};
+  for (int q = 0; q < 3; ++q) {
+    if (gp[q] < 0) continue;
+    // d(1/l)/dq = -(1/l^2) dl/dq
+    const Cx d1 = cmul(cmul(i1, i1), dl[0][q]), d2 = cmul(cmul(i2, i2), dl[1][q]);
+    const Cx d3 = cmul(cmul(i3, i3), dl[2][q]);
+    const double dk[4] = {-0.5 * (d1.r + d2.r), -d3.r, -0.5 * (d1.r - d2.r), -d3.i};
+    dN[gp[q]] += dI[0] * dk[0] + dI[1] * dk[1] + dI[2] * dk[2] + dI[3] * dk[3];
+  }
+}
+
+// The event pass: -log(I/N) summed (or stored per event) with the gradient; per-thread
+// gradient sums in shared memory (nfree x blockDim doubles).
+template <bool G, bool STORE>
+__global__ void __launch_bounds__(kThreads) k_tddp_events(
+    const __grid_constant__ TddpPlan T, const __grid_constant__ WeidCoef W,
+    const double* __restrict__ theta, const double* __restrict__ ct,
+    const double* __restrict__ csig, int64_t n, const double2* __restrict__ cache,
+    const double2* __restrict__ gram, double* __restrict__ partials,
+    unsigned* __restrict__ counter, double* __restrict__ result, double* __restrict__ out_logp) {
+  const DalitzPlan& D = T.D;
+  extern __shared__ double gsh[];  // G: nfree x blockDim
+  __shared__ double th[4 * kMaxRes + 8];
+  __shared__ double Nsh[1 + 4 * kMaxRes + 8];
+  __shared__ double red[(kThreads / 32) * (1 + 4 * kMaxRes + 4)];
+  __shared__ int last;
+  const int tid = threadIdx.x, bd = blockDim.x, nf = T.nfree;
+  // theta_all holds at most 4 kMaxRes + 4 parameters for this model
+  for (int k = tid; k < 4 * kMaxRes + 8; k += bd) th[k] = theta[k];
+  __syncthreads();
+  if (tid == 0) tddp_norm(T, th, gram, &Nsh[0], G ? Nsh + 1 : nullptr);
+  if (G)
+    for (int k = 0; k < nf; ++k) gsh[k * bd + tid] = 0.0;
+  __syncthreads();
+  const double tau = th[T.p_tau], mx = th[T.p_x], my = th[T.p_y], sc = th[T.p_s];
+  Cx l[3], dl[3][3];
+  tddp_rates(tau, mx, my, l, dl);
+  const double logN = log(Nsh[0]);
+  Neu acc;
+  for (int64_t i = (int64_t)blockIdx.x * bd + tid; i < n; i += (int64_t)gridDim.x * bd) {
+    Cx A = {1.0, 0.0}, B = {1.0, 0.0};
+    for (int r = 0; r < D.nres; ++r) {
+      const double2 a = cache[(size_t)r * n + i], b = cache[(size_t)(D.nres + r) * n + i];
+      const Cx c = {th[D.res[r].p_re], th[D.res[r].p_im]};
+      const Cx ca = cmul(c, {a.x, a.y}), cb = cmul(c, {b.x, b.y});
+      A = {A.r + ca.r, A.i + ca.i};
+      B = {B.r + cb.r, B.i + cb.i};
+    }
+    const double t = ct[i], sigt = csig[i], sig = sc * sigt;
+    Cx Tv[3], Tl[3], Ts[3];
+    for (int j = 0; j < 3; ++j) smeared_exp(l[j], t, sig, W, Tv[j], Tl[j], Ts[j]);
+    const double kk[4] = {0.5 * (Tv[0].r + Tv[1].r), Tv[2].r, 0.5 * (Tv[0].r - Tv[1].r), Tv[2].i};
+    const double aa = A.r * A.r + A.i * A.i, bb = B.r * B.r + B.i * B.i;
+    const Cx X = cmul({A.r, -A.i}, B);
+    const double dI[4] = {0.5 * (aa + bb), 0.5 * (aa - bb), X.r, -X.i};
+    const double I = dI[0] * kk[0] + dI[1] * kk[1] + dI[2] * kk[2] + dI[3] * kk[3];
+    if (STORE) {
+      out_logp[i] = log(I) - logN;
+      continue;
+    }
+    acc.add(-log(I));
+    if (G) {
+      const double iI = -1.0 / I;
+      for (int r = 0; r < D.nres; ++r) {
+        const double2 a2 = cache[(size_t)r * n + i], b2 = cache[(size_t)(D.nres + r) * n + i];
+        for (int part = 0; part < 2; ++part) {
+          const int g = part ? D.res[r].g_im : D.res[r].g_re;
+          if (g < 0) continue;
+          const Cx dA = part ? Cx{-a2.y, a2.x} : Cx{a2.x, a2.y};
+          const Cx dB = part ? Cx{-b2.y, b2.x} : Cx{b2.x, b2.y};
+          const double daa = 2.0 * (A.r * dA.r + A.i * dA.i), dbb = 2.0 * (B.r * dB.r + B.i * dB.i);
+          const Cx x1 = cmul({dA.r, -dA.i}, B), x2 = cmul({A.r, -A.i}, dB);
+          const double dXr = x1.r + x2.r, dXi = x1.i + x2.i;
+          const double d = 0.5 * (daa + dbb) * kk[0] + 0.5 * (daa - dbb) * kk[1] + dXr * kk[2] -
+                           dXi * kk[3];
+          gsh[g * bd + tid] += d * iI;
+        }
+      }
+      const int gp[4] = {T.g_tau, T.g_x, T.g_y, T.g_s};
+      for (int q = 0; q < 4; ++q) {
+        if (gp[q] < 0) continue;
+        Cx d[3];
+        for (int j = 0; j < 3; ++j) d[j] = q < 3 ? cmul(Tl[j], dl[j][q]) : Cx{Ts[j].r * sigt, Ts[j].i * sigt};
+        const double dk[4] = {0.5 * (d[0].r + d[1].r), d[2].r, 0.5 * (d[0].r - d[1].r), d[2].i};
+        gsh[gp[q] * bd + tid] += (dI[0] * dk[0] + dI[1] * dk[1] + dI[2] * dk[2] + dI[3] * dk[3]) * iI;
+      }
+    }
+  }
+  if (STORE) return;
+  const int m = 1 + (G ? nf : 0);
+  const int stride = 1 + 4 * kMaxRes + 4;
+  block_sum_pairs([&](int k) -> F2 { return df_split(k == 0 ? acc.get() : gsh[(k - 1) * bd + tid]); },
+                  m, red, partials + (size_t)blockIdx.x * stride);
+  if (!arrive_last_of(counter, gridDim.x, &last)) return;
+  reduce_partials(partials, gridDim.x, stride, m, result, red);
+  if (tid == 0) {
+    result[0] += (double)n * logN;
+    if (G)
+      for (int k = 0; k < nf; ++k) result[1 + k] += (double)n * Nsh[1 + k] / Nsh[0];
+    *counter = 0u;
+  }
+}
+
+cudaError_t launch_tddp_cache(const TddpPlan& T, const double* theta, const double* s12,
+                              const double* s13, int64_t n, double2* cache, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_tddp_cache<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(T, theta, s12, s13, n, cache);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tddp_gram(const TddpPlan& T, const double* theta, const uint8_t* inside,
+                             double2* gcols, double2* gram, cudaStream_t st) {
+  const int64_t ncell = (int64_t)T.D.nbx * T.D.nby;
+  k_tddp_gcols<<<grid_for(ncell, kThreads, 152 * 8), kThreads, 0, st>>>(T, theta, inside, gcols);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int K1 = T.D.nres + 1;
+  k_tddp_gram<<<3 * K1 * K1, kThreads, 0, st>>>(T, inside, gcols, gram);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tddp_events(const TddpPlan& T, bool grad, const double* theta,
+                               const double* const* cols, int64_t n, const double2* cache,
+                               const double2* gram, double* partials, unsigned* counter,
+                               double* result, double* out_logp, int nblocks,
+                               const WeidCoef& W, cudaStream_t st) {
+  const size_t smem = grad ? sizeof(double) * T.nfree * kThreads : 0;
+  if (out_logp) {
+    k_tddp_events<false, true><<<nblocks, kThreads, 0, st>>>(T, W, theta, cols[2], cols[3], n,
+                                                            cache, gram, partials, counter,
+                                                            result, out_logp);
+  } else if (grad) {
+    k_tddp_events<true, false><<<nblocks, kThreads, smem, st>>>(T, W, theta, cols[2], cols[3], n,
+                                                               cache, gram, partials, counter,
+                                                               result, nullptr);
+  } else {
+    k_tddp_events<false, false><<<nblocks, kThreads, 0, st>>>(T, W, theta, cols[2], cols[3], n,
+                                                             cache, gram, partials, counter,
+                                                             result, nullptr);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace gfi

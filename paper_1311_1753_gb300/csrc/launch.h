@@ -94,4 +94,20 @@ cudaError_t launch_tick_dalitz(bool mixed, const TickItem* items, int nfits, int
                                size_t smem, int grid, cudaStream_t st);
 constexpr int kGramEntries = (kMaxRes + 1) * (kMaxRes + 2) / 2;
 
+// time-dependent Dalitz model (k_dalitz.cu)
+// per-event amplitudes a_r (at s12, s13) and b_r (at s12, s23): cache [2][nres][n] double2
+cudaError_t launch_tddp_cache(const TddpPlan& T, const double* theta, const double* s12,
+                              const double* s13, int64_t n, double2* cache, cudaStream_t st);
+// the three (nres+1)^2 complex grid sums G_A, G_B, X (dA sum conj(a_r) a_s, conj(b_r) b_s,
+// conj(a_r) b_s; index 0 the non-resonant 1) into gram [3][(nres+1)^2]; gcols: scratch
+// [2][nres][nbx nby] double2; inside: the cell mask
+cudaError_t launch_tddp_gram(const TddpPlan& T, const double* theta, const uint8_t* inside,
+                             double2* gcols, double2* gram, cudaStream_t st);
+// NLL (+ gradient) into result[0 .. nfree], or (out_logp) per-event log P
+cudaError_t launch_tddp_events(const TddpPlan& T, bool grad, const double* theta,
+                               const double* const* cols, int64_t n, const double2* cache,
+                               const double2* gram, double* partials, unsigned* counter,
+                               double* result, double* out_logp, int nblocks,
+                               const WeidCoef& W, cudaStream_t st);
+
 }  // namespace gfi

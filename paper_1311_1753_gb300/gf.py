@@ -83,6 +83,8 @@ def _load():
         "gf_pdf_dalitz": ([vp, C.c_int, C.c_int, C.POINTER(DalitzKin), C.c_int,
                            C.POINTER(Resonance), _I], C.c_int),
         "gf_set_norm_grid": ([vp, C.c_int, C.c_int, C.c_int], C.c_int),
+        "gf_pdf_tddp": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(DalitzKin), C.c_int,
+                         C.POINTER(Resonance), C.c_int, C.c_int, C.c_int, C.c_int, _I], C.c_int),
         "gf_dalitz_inside": ([vp, C.c_int, C.c_int64, _D, _D, C.POINTER(C.c_int8)], C.c_int),
         "gf_dataset_create": ([vp, C.c_int, _I, C.POINTER(vp)], C.c_int),
         "gf_dataset_add_events": ([vp, C.c_int64, C.POINTER(_D)], C.c_int),
@@ -262,6 +264,17 @@ class Context:
             *[Resonance(r["channel"], r["spin"], r["mass"], r["width"], r["re"], r["im"])
               for r in resonances])
         return self._id(lib.gf_pdf_dalitz, obs12, obs13, C.byref(k), len(resonances), rs)
+
+    def tddp(self, obs12, obs13, obs_t, obs_sigt, kin: dict, resonances: list, tau, x, y,
+             scale):
+        """Time-dependent Dalitz model (fixed resonance shapes); data columns s12, s13, t,
+        sigma_t."""
+        k = DalitzKin(kin["M"], kin["m1"], kin["m2"], kin["m3"], kin.get("R", 1.5))
+        rs = (Resonance * max(1, len(resonances)))(
+            *[Resonance(r["channel"], r["spin"], r["mass"], r["width"], r["re"], r["im"])
+              for r in resonances])
+        return self._id(lib.gf_pdf_tddp, obs12, obs13, obs_t, obs_sigt, C.byref(k),
+                        len(resonances), rs, tau, x, y, scale)
 
     def set_norm_grid(self, node, nbx, nby=0):
         self._ck(lib.gf_set_norm_grid(self.h, node, nbx, nby), "gf_set_norm_grid")

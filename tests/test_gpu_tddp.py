@@ -1,0 +1,121 @@
+"""The time-dependent Dalitz model (Sec. 4: the D0 -> pi+ pi- pi0 mixing fit) on the
+sm_103a path against the FP64 oracle.
+
+Tolerances: per event |log P_gpu - log P_orc| <= 1e-12 x kappa_i (the interference
+condition number of both amplitudes, (|a_NR| + sum |c_r a_r|)^2 / |A|^2 and the same for
+B, the larger), 1e-9 relative on the NLL, gradients 1e-9 of their scale."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1311_1753_gb300 import synth
+from tests import oracle_models as om
+
+pytestmark = pytest.mark.gpu
+SPEC = om.load_dalitz_spec()
+TIME = dict(tau=0.41, x=0.01, y=0.007, scale=1.1)
+
+
+@pytest.fixture(scope="module")
+def gf():
+    from paper_1311_1753_gb300 import gf as _gf
+    return _gf
+
+
+def _models(gf, nb=64):
+    k = SPEC["kin"]
+    d = oracle.Tddp(k["M"], k["m1"], k["m2"], k["m3"], k["R"], nb, nb)
+    ctx = gf.Context()
+    o12 = ctx.observable("s12", 0.0, 4.0)
+    o13 = ctx.observable("s13", 0.0, 4.0)
+    ot = ctx.observable("t", -2.0, 20.0)
+    osg = ctx.observable("sigt", 0.0, 1.0)
+    res = []
+    for i, r in enumerate(SPEC["resonances"]):
+        m0 = ctx.parameter(f"m0_{i}", r["m0"], 0.005, fixed=True)
+        g0 = ctx.parameter(f"g0_{i}", r["g0"], 0.005, fixed=True)
+        re = ctx.parameter(f"re_{i}", r["re"], 0.01)
+        im = ctx.parameter(f"im_{i}", r["im"], 0.01)
+        res.append(dict(channel=r["channel"], spin=r["spin"], mass=m0, width=g0, re=re, im=im))
+        idx = [d.param(r[f]) for f in ("m0", "g0", "re", "im")]
+        d.resonance(r["channel"], r["spin"], *idx)
+    tp = [ctx.parameter(nm, v, 1e-3, 1e-3 if nm in ("tau", "scale") else -1.0,
+                        5.0 if nm in ("tau", "scale") else 1.0) for nm, v in TIME.items()]
+    d.time_params(*[d.param(v) for v in TIME.values()])
+    root = ctx.tddp(o12, o13, ot, osg, k, res, *tp)
+    ctx.set_norm_grid(root, nb, nb)
+    return ctx, root, [o12, o13, ot, osg], d, np.array(ctx.free_params())
+
+
+def _events(d, n, seed=3):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    s12, s13 = synth.dalitz_events(n, om.dalitz_accept(om.dalitz_from_spec(SPEC), SPEC["envelope"]),
+                                   seed=seed)
+    sigt = rng.uniform(0.05, 0.15, n)
+    t = np.clip(rng.exponential(0.41, n) + sigt * rng.standard_normal(n), -1.9, 19.0)
+    return [s12, s13, t, sigt]
+
+
+def _kappa(d, cols, p):
+    s12, s13 = cols[0], cols[1]
+    k = SPEC["kin"]
+    s23 = k["M"] ** 2 + k["m1"] ** 2 + k["m2"] ** 2 + k["m3"] ** 2 - s12 - s13
+    out = []
+    for a, b in ((s12, s13), (s12, s23)):
+        A = np.ones(len(a), complex)
+        S = np.ones(len(a))
+        for i, r in enumerate(SPEC["resonances"]):
+            c = p[4 * i + 2] + 1j * p[4 * i + 3]
+            v = c * d.amp(i, a, b, p=p)
+            A += v
+            S += np.abs(v)
+        out.append(S ** 2 / np.abs(A) ** 2)
+    return np.maximum(*out)
+
+
+@pytest.mark.parametrize("n", [1, 257, 20_001])
+def test_tddp_parity(gf, n):
+    ctx, root, obs, d, free = _models(gf)
+    cols = _events(d, n)
+    ctx.set_data(root, obs, cols)
+    rng = np.random.default_rng(1)
+    for k in range(2):
+        th = d.p[free] * (1 + (0.02 * rng.standard_normal(len(free)) if k else 0.0))
+        p = d.p.copy(); p[free] = th
+        lg = ctx.logpdf(th)
+        lo_ = np.log(d.intensity_t(*cols, p=p)) - np.log(d.norm_t(p=p))
+        kap = _kappa(d, cols, p)
+        assert np.all(np.abs(lg - lo_) <= 1e-12 * kap * np.maximum(1.0, np.abs(lo_))), \
+            np.max(np.abs(lg - lo_) / kap)
+        f, g = ctx.nll_grad(th)
+        fo, go = d.nll_t(*cols, p=p, grad=True)
+        assert abs(f - fo) <= 1e-9 * abs(fo)
+        scale = np.abs(go[free]).max()
+        assert np.all(np.abs(g - go[free]) <= 1e-9 * np.maximum(np.abs(go[free]), 1e-3 * scale)), (g, go[free])
+
+
+def test_tddp_fit_matches_oracle_fit(gf):
+    """A fit of the 16 coefficients, tau, x, y and the resolution scale (20 free) lands
+    within 0.01 sigma of the oracle's fit from the same start."""
+    from oracle import minimise
+    ctx, root, obs, d, free = _models(gf, nb=48)
+    cols = _events(d, 5000, seed=9)
+    ctx.set_data(root, obs, cols)
+    start = d.p[free] * (1 + 0.01 * np.random.default_rng(2).standard_normal(len(free)))
+    for k, pid in enumerate(ctx.free_params()):
+        ctx.set_value(pid, start[k])
+    r = ctx.fit(tol=1e-9)
+    assert r["status"] == gf.GF_OK
+
+    def fg(q):
+        p = d.p.copy(); p[free] = q
+        f, g = d.nll_t(*cols, p=p, grad=True)
+        return f, g[free]
+    lo = np.array([-np.inf] * 16 + [1e-3, -1.0, -1.0, 1e-3])
+    hi = np.array([np.inf] * 16 + [5.0, 1.0, 1.0, 5.0])
+    lo[:16], hi[:16] = 0.0, 0.0  # unbounded
+    ro = minimise.fit(fg, start, np.full(len(free), 1e-3), lo, hi, up=0.5, tol=1e-9)
+    assert ro.converged
+    assert np.all(np.abs(r["theta"] - ro.x) <= 0.01 * ro.err), np.max(np.abs(r["theta"] - ro.x) / ro.err)
