@@ -40,10 +40,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # of floats) on the FP32 pipe, so its roofline is the FP32 pipe.  Algorithmic work per
 # event = the FP32 flops of that double-float algorithm (FADD + FMUL + 2 FFMA executed per
 # event, predicated-on, counted by ncu on the 10^7-event launch of this configuration:
-# 726.8 + 80.0 + 2 x 211.3; profiles/k_events_1d_voigt_1e7.md).  DRAM traffic of one
-# launch from the same capture (81.01 MB read + 4.89 MB written).
-FP32_FLOPS_PER_EVENT = {"voigt_grad": 1229.4}
-TRAFFIC_PER_LAUNCH = {"voigt_grad": 85.90e6}
+# 728.7 + 80.2 + 2 x 211.9; profiles/k_events_1d_voigt_1e7.md).  DRAM traffic of one
+# launch from the same capture (80.41 MB read + 5.65 MB written).
+FP32_FLOPS_PER_EVENT = {"voigt_grad": 1232.7}
+TRAFFIC_PER_LAUNCH = {"voigt_grad": 86.06e6}
 # Context: the same pass in FP64 operations of the method (FMA = 2, add/mul = 1, each
 # exp, log, sqrt or division = 1), counted from the source: w(z) by one Weideman series
 # (N = 40: 305) and its degree-5 expansion per chunk of 24 events (recurrence ~40 per
@@ -263,7 +263,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="voigt",
-                    choices=["voigt", "exp", "dalitz", "dalitz-mixed"])
+                    choices=["voigt", "exp", "dalitz", "dalitz-mixed", "exp-sweep", "binned",
+                             "conv", "tddp"])
+    ap.add_argument("--sweep-sizes", default="1000000,10000000,100000000,1000000000",
+                    help="event counts of --workload exp-sweep")
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--fits", action="store_true")
     ap.add_argument("--serve", action="store_true")
@@ -303,6 +306,21 @@ def main():
         return 0
 
     import torch
+    if args.workload in ("exp-sweep", "binned", "conv", "tddp"):
+        # secondary workloads alone (one JSON object: their measurements), for profiling
+        torch.cuda.set_device(local)
+        from paper_1311_1753_gb300 import gf
+        if args.workload == "exp-sweep":
+            sizes = [int(v) for v in args.sweep_sizes.split(",")]
+            res = run_exp_sweep(torch, gf, sizes=sizes, steps=args.steps)
+        elif args.workload == "binned":
+            res = run_binned(torch, gf, steps=args.steps)
+        elif args.workload == "conv":
+            res = run_zach(torch, gf, steps=args.steps)
+        else:
+            res = run_tddp(torch, gf, steps=args.steps)
+        print(json.dumps({"workload": args.workload, "result": res}))
+        return 0
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -677,6 +695,56 @@ def run_zach(torch, gf, nb=4000, steps=50):
     return out
 
 
+def run_tddp(torch, gf, n=100_000, steps=30):
+    """The paper's driver, the time-dependent Dalitz (mixing) fit of D0 -> pi+ pi- pi0
+    (Sec. 4: ~10^5 events): the 8-resonance model for D0 and D0bar, decay time with tau,
+    x, y and a per-event resolution sigma_t (uniform in [0.05, 0.15] ps) scaled by s;
+    20 free parameters (16 coefficients, tau, x, y, s), 256 x 256 normalisation grid.
+    Events: (s12, s13) drawn with the library's Dalitz density, t = exponential(tau) +
+    Gaussian(sigma_t).  Evaluation time (NLL + gradient) and a fit from a displaced start."""
+    spec = dalitz_spec()
+    s12, s13 = dalitz_events_gpu(gf, spec, n, synth.SEED_DALITZ_EVENTS + 7)
+    rng = np.random.Generator(np.random.PCG64(synth.SEED_DALITZ_EVENTS + 8))
+    sigt = rng.uniform(0.05, 0.15, n)
+    t = np.clip(rng.exponential(0.41, n) + sigt * rng.standard_normal(n), -1.9, 19.0)
+    ctx = gf.Context(0, gf.GF_FP64)
+    o12 = ctx.observable("s12", 0.0, 4.0)
+    o13 = ctx.observable("s13", 0.0, 4.0)
+    ot = ctx.observable("t", -2.0, 20.0)
+    osg = ctx.observable("sigt", 0.0, 1.0)
+    res = []
+    for i, r in enumerate(spec["resonances"]):
+        m0 = ctx.parameter(f"m0_{i}", r["m0"], 0.005, fixed=True)
+        g0 = ctx.parameter(f"g0_{i}", r["g0"], 0.005, fixed=True)
+        re = ctx.parameter(f"re_{i}", r["re"], 0.01)
+        im = ctx.parameter(f"im_{i}", r["im"], 0.01)
+        res.append(dict(channel=r["channel"], spin=r["spin"], mass=m0, width=g0, re=re, im=im))
+    tau = ctx.parameter("tau", 0.41, 0.01, 0.05, 5.0)
+    mx = ctx.parameter("x", 0.0, 0.01, -1.0, 1.0)
+    my = ctx.parameter("y", 0.0, 0.01, -1.0, 1.0)
+    sc = ctx.parameter("scale", 1.0, 0.01, 0.1, 5.0)
+    root = ctx.tddp(o12, o13, ot, osg, spec["kin"], res, tau, mx, my, sc)
+    ctx.set_data(root, [o12, o13, ot, osg], [s12, s13, t, sigt])
+    th0 = np.array([ctx.value(p) for p in ctx.free_params()])
+    r = time_steps(torch, ctx, [th0 + 1e-4 * k for k in range(4)], steps, 3)
+    start = th0 + 0.02 * np.random.default_rng(3).standard_normal(len(th0))
+    for k, pid in enumerate(ctx.free_params()):
+        ctx.set_value(pid, start[k])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f = ctx.fit(tol=1e-6)
+    sec = time.perf_counter() - t0
+    fp = ctx.free_params()
+    out = {"events": n, "free_params": len(th0), "grid": "256 x 256",
+           "ms_per_eval": float(np.mean(r["step_ms"])),
+           "event_kernel_ms": float(np.mean(r["kernel_ms"])),
+           "events_x_evals_per_s": n * steps / (sum(r["step_ms"]) / 1e3),
+           "fit_seconds": sec, "fit_calls": f["n_calls"], "fit_status": f["status"],
+           "tau_x_y_scale": f["theta"][-4:].tolist(), "errors": f["err"][-4:].tolist()}
+    ctx.close()
+    return out
+
+
 def run_extra(torch, gf, args):
     """Secondary measurements: configs 1, 3, 4 evaluation rates (and, on request, fit
     times and the serving study)."""
@@ -692,6 +760,7 @@ def run_extra(torch, gf, args):
     out["config1_exp_hbm_sweep"] = run_exp_sweep(torch, gf)
     out["binned_voigt_4000"] = run_binned(torch, gf)
     out["binned_relbw_conv_4000"] = run_zach(torch, gf)
+    out["tddp_mixing_1e5"] = run_tddp(torch, gf)
     # config 3 (FP64, 1e6 events, cached per-event amplitudes, Gram normalisation)
     spec = dalitz_spec()
     data = dalitz_events_gpu(gf, spec, 1_000_000, synth.SEED_DALITZ_EVENTS)

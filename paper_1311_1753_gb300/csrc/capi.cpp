@@ -928,7 +928,8 @@ static void detect_mixture(Program& P) {
   int lf[kMixMax], lg[kMixMax], sc[kMixMax];
   while (pc < P.n) {
     if (K >= kMixMax) return;
-    if (P.ins[pc].op != OP_LEAF || P.ins[pc].npar > kMixLocal) return;
+    // the basic leaves only (the mixture kernel holds no code for the others)
+    if (P.ins[pc].op != OP_LEAF || P.ins[pc].npar > kMixLocal || P.ins[pc].kind > L_POLY) return;
     lf[K] = pc++;
     lg[K] = 0;
     if (pc < P.n && P.ins[pc].op == OP_TOLIN) {
@@ -1507,7 +1508,8 @@ static int finish_set_data(gf_ctx* ctx) {
   } else if (ctx->prog.logsum) {
     per_sm = events_logsum_blocks_per_sm(ctx->prog);
   } else {
-    per_sm = events_1d_blocks_per_sm(true, events_1d_smem(ctx->prog, true, kThreads1D));
+    per_sm = events_1d_blocks_per_sm(true, events_1d_smem(ctx->prog, true, kThreads1D),
+                                     ctx->prog.mix > 0);
   }
   per_sm = std::max(1, std::min(per_sm, 8));
   const int64_t items = ctx->is_dalitz ? d.n : (d.n + 1) / 2;

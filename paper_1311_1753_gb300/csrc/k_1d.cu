@@ -518,7 +518,9 @@ __device__ __forceinline__ void tay_eval(const Tay& tay, F2 zr, F2& wr, F2& wi) 
 // partials with respect to the leaf's free parameters into the gradient slot g (stride bd).
 // rec: the leaf record in FP64 (its constant c0 = rec[10] enters the exact difference
 // x - c0); r: the same record in the arithmetic A.
-template <class A, bool G, class Sink>
+// EXT: also the line shape, convolution and indicator leaves (false in the AddPdf-of-leaves
+// path, which the compiler gives the basic leaves only).
+template <class A, bool G, bool EXT = true, class Sink>
 __device__ __forceinline__ typename A::T eval_leaf_s(const Instr& I, const double* rec,
                                                      const typename A::T* r, double x,
                                                      const WeidCoef& W, Sink sink,
@@ -588,6 +590,7 @@ __device__ __forceinline__ typename A::T eval_leaf_s(const Instr& I, const doubl
       return l;
     }
     case L_RELBW: {
+      if constexpr (!EXT) return A::zero();
       T dm, dg;
       const T f = relbw_f<A, G>(x, rec + 10, c, (int)rec[4], rec[5], dm, dg);
       const T l = A::mul(f, r[0]);
@@ -598,8 +601,10 @@ __device__ __forceinline__ typename A::T eval_leaf_s(const Instr& I, const doubl
       return l;
     }
     case L_IND:
+      if constexpr (!EXT) return A::zero();
       return (x >= rec[10] && x < rec[11]) ? A::of(1.0) : A::zero();
     case L_CONV: {
+      if constexpr (!EXT) return A::zero();
       // lattice table (k_conv_sum): C_i then dC_i/dtheta_l, rows of L + 1; linear in
       // between (FP64 index arithmetic: convolutions serve binned or modest data)
       const double* T_ = reinterpret_cast<const double*>(__double_as_longlong(rec[13]));
@@ -800,7 +805,7 @@ __device__ __forceinline__ F2 run_mixture(const Program& P, const double* rec, c
   for (int k = 0; k < P.mix; ++k) {
     const Instr& I = P.ins[P.mix_leaf[k]];
     F2 d0 = {0.f, 0.f}, d1 = {0.f, 0.f}, d2 = {0.f, 0.f};
-    F2 v = eval_leaf_s<ArF2, G>(
+    F2 v = eval_leaf_s<ArF2, G, false>(
         I, rec + I.slot * kLeafRec, rf + I.slot * kLeafRec, x[I.obs], W,
         [&](int j, F2 t) {
           if (j == 0) d0 = t;
@@ -907,7 +912,9 @@ __device__ __forceinline__ void bin_metric_d(const Program& P, int64_t i, double
 // Body of one (virtual) block vb of the vgrid blocks of an event launch.  Shared
 // scratch: dyn (G: (kMaxStack + 1) nfree blockDim pairs/doubles), rec (leaf records in
 // FP64), rf (the same as pairs), red[(blockDim / 32) (1 + kMaxFree1D)], *last.
-template <bool G, int MODE>
+// MX: 1 the program is an AddPdf of leaves (run_mixture only), 0 it is not (the stack
+// machine only), -1 decided per launch from the program (the kernel holds both).
+template <bool G, int MODE, int MX = -1>
 __device__ __forceinline__ void events_1d_block(
     const Program& P, const WeidCoef& W, const Cols& cols, const int64_t n,
     const double* __restrict__ theta, const double* __restrict__ derived_g,
@@ -939,7 +946,7 @@ __device__ __forceinline__ void events_1d_block(
 
   // one event: log P_i into the sums (MODE 0, 2) or out_logp (MODE 1, through perm if
   // sorted)
-  const bool mix = P.mix > 0;
+  const bool mix = MX < 0 ? P.mix > 0 : MX == 1;
   const F2 kb = MODE == 2 ? df_split(P.kbin) : F2{0.f, 0.f};
   const F2 lk = MODE == 2 ? df_split(P.logk) : F2{0.f, 0.f};
   auto one_event = [&](int64_t i, const double* x, const Tay* tay) {
@@ -1067,7 +1074,7 @@ __device__ __forceinline__ void events_1d_block(
   if (tid == 0) *counter = 0u;
 }
 
-template <bool G, int MODE>
+template <bool G, int MODE, int MX = -1>
 __global__ void __launch_bounds__(kThreads1D) k_events_1d(
     const Program* __restrict__ Pg, const __grid_constant__ WeidCoef W, const Cols cols,
     const int64_t n, const double* __restrict__ theta, const double* __restrict__ derived_g,
@@ -1082,9 +1089,9 @@ __global__ void __launch_bounds__(kThreads1D) k_events_1d(
   __shared__ F2 tay_t[(kTayDeg + 1) * 2 * kThreads1D];
   load_df_tables();
   load_program(Pg, P);
-  events_1d_block<G, MODE>(P, W, cols, n, theta, derived_g, partials, counter, result, out_logp,
-                           perm, analytic_only, blockIdx.x, gridDim.x, dyn, rec, rf, red, &last,
-                           tay_t);
+  events_1d_block<G, MODE, MX>(P, W, cols, n, theta, derived_g, partials, counter, result,
+                               out_logp, perm, analytic_only, blockIdx.x, gridDim.x, dyn, rec, rf,
+                               red, &last, tay_t);
 }
 
 // ---- log-domain products of exponential and Gaussian leaves ----------------------------
@@ -1643,14 +1650,14 @@ cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCo
     k_events_1d<false, 1><<<nblocks, threads, 0, st>>>(prog, W, cols, n, theta, derived, partials,
                                                        counter, result, out_logp, perm,
                                                        analytic_only);
-  } else if (grad) {
-    k_events_1d<true, 0><<<nblocks, threads, smem, st>>>(prog, W, cols, n, theta, derived, partials,
-                                                         counter, result, out_logp, nullptr,
-                                                         analytic_only);
   } else {
-    k_events_1d<false, 0><<<nblocks, threads, 0, st>>>(prog, W, cols, n, theta, derived, partials,
-                                                       counter, result, out_logp, nullptr,
-                                                       analytic_only);
+    // AddPdf-of-leaves programs and the others in kernels of their own: each holds only its
+    // path (fewer registers for the mixture, the headline workload)
+    auto k = grad ? (P.mix ? k_events_1d<true, 0, 1> : k_events_1d<true, 0, 0>)
+                  : (P.mix ? k_events_1d<false, 0, 1> : k_events_1d<false, 0, 0>);
+    k<<<nblocks, threads, grad ? smem : 0, st>>>(prog, W, cols, n, theta, derived, partials,
+                                                 counter, result, out_logp, nullptr,
+                                                 analytic_only);
   }
   return cudaGetLastError();
 }
@@ -1662,7 +1669,9 @@ void prepare_kernels_1d() {
   cudaFuncSetAttribute(k_conv_points, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_gnorm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 
-  cudaFuncSetAttribute(k_events_1d<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_events_1d<true, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       200 * 1024);
+  cudaFuncSetAttribute(k_events_1d<true, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
   cudaFuncSetAttribute(k_events_1d<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        200 * 1024);
@@ -1678,12 +1687,14 @@ int events_logsum_blocks_per_sm(const Program& P) {
   return nb > 0 ? nb : 1;
 }
 
-int events_1d_blocks_per_sm(bool grad, size_t smem) {
+int events_1d_blocks_per_sm(bool grad, size_t smem, bool mix) {
   int nb = 0;
   if (grad) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_events_1d<true, 0>, kThreads1D, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &nb, mix ? k_events_1d<true, 0, 1> : k_events_1d<true, 0, 0>, kThreads1D, smem);
   } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_events_1d<false, 0>, kThreads1D, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &nb, mix ? k_events_1d<false, 0, 1> : k_events_1d<false, 0, 0>, kThreads1D, 0);
   }
   cudaGetLastError();
   return nb > 0 ? nb : 1;

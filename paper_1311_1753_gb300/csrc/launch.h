@@ -22,7 +22,8 @@ cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCo
                              unsigned* counter, double* result, double* out_logp,
                              const int32_t* perm, bool grad, bool store, int analytic_only,
                              int nblocks, cudaStream_t st);
-int events_1d_blocks_per_sm(bool grad, size_t smem);  // also opts in to large shared memory
+// blocks per SM of the event kernel (mix: the AddPdf-of-leaves variant)
+int events_1d_blocks_per_sm(bool grad, size_t smem, bool mix = false);
 int events_logsum_blocks_per_sm(const Program& P);  // the direct log-sum kernel
 void prepare_kernels_1d();
 // ConvolutionPdf tables of one node (after launch_norm_1d; before the event pass):
