@@ -230,7 +230,9 @@ int gf_set_data_device(gf_ctx* ctx, int root, int nobs, const int* obs, int64_t 
  * observable ranges (Dalitz: the kinematic region) and the next evaluation returns
  * GF_EINVAL if any is outside.  The per-event caches are rebuilt at that evaluation. */
 int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols);
-/* (Binned data sets are replaced with gf_set_data; gf_update_data rejects them.) */
+/* (Binned data sets are replaced with gf_set_data; gf_update_data rejects them.  For the
+ * time-dependent Dalitz model the kinematic region and sigma_t > 0 are checked on the
+ * host, as gf_set_data does, and GF_EINVAL is returned with no event replaced.) */
 
 /* ---- evaluation (Sec. 2: evaluate and metric, summed over events) ------------------ */
 /* NLL(theta) = -sum_i log P(x_i; theta) with P normalised (or the context's binned

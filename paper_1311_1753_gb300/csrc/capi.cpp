@@ -1482,7 +1482,8 @@ static int finish_set_data(gf_ctx* ctx) {
   if (ctx->is_tddp) {
     const TddpPlan& T = ctx->tplan;
     const int64_t want = (d.n + kThreads - 1) / kThreads;
-    d.nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->sm_count * 4));
+    d.nblocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>(want, (int64_t)ctx->sm_count * kTddpBlocksPerSm));
     rc = grow(ctx, &d.partials, &d.partials_cap, (size_t)std::max(d.nblocks, 2048) * 64);
     if (rc) return rc;
     const size_t ncell = (size_t)T.D.nbx * T.D.nby;
@@ -1564,7 +1565,8 @@ static int finish_set_data(gf_ctx* ctx) {
 // per thread of the event launch.
 static bool sort_eligible(const gf_ctx* ctx) {
   const DevState& d = ctx->dev;
-  return ctx->event_sort && ctx->compiled && !ctx->is_dalitz && d.owns_cols && !d.binned &&
+  return ctx->event_sort && ctx->compiled && !ctx->is_dalitz && !ctx->is_tddp && d.owns_cols &&
+         !d.binned &&
          ctx->prog.tay_slot >= 0 && d.n < INT32_MAX &&
          d.n >= (int64_t)(kChunk / 2) * d.nblocks * kThreads1D;
 }
@@ -1631,7 +1633,7 @@ static int mark_unsorted(gf_ctx* ctx) {
   if (!d.sorted) return GF_OK;
   d.sorted = false;
   d.sort_obs = -1;
-  if (ctx->compiled && !ctx->is_dalitz) {
+  if (ctx->compiled && !ctx->is_dalitz && !ctx->is_tddp) {
     ctx->prog.sorted = 0;
     CK(cudaMemcpyAsync(d.prog, &ctx->prog, sizeof(Program), cudaMemcpyHostToDevice,
                        ctx->stream));
@@ -2316,8 +2318,19 @@ int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
   CK(cudaSetDevice(ctx->device));
   rc = mark_unsorted(ctx);  // the new events arrive in the caller's order
   if (rc) return rc;
-  for (int k = 0; k < d.nobs; ++k) {
+  for (int k = 0; k < d.nobs; ++k)
     if (!cols[k]) return GF_EINVAL;
+  if (ctx->is_tddp) {
+    // the checks gf_set_data makes, on the host copies, before any event is replaced
+    for (int64_t i = 0; i < n; ++i) {
+      if (!(cols[3][i] > 0.0))
+        return set_error(ctx, GF_EINVAL, "event " + std::to_string(i) + ": sigma_t must be > 0");
+      if (!dalitz_inside_host(ctx->tplan.D, cols[0][i], cols[1][i]))
+        return set_error(ctx, GF_EINVAL,
+                         "event " + std::to_string(i) + " outside the Dalitz kinematic region");
+    }
+  }
+  for (int k = 0; k < d.nobs; ++k) {
     if (n > 0)
       CK(cudaMemcpyAsync(d.cols[k], cols[k], sizeof(double) * n, cudaMemcpyHostToDevice,
                          ctx->stream));

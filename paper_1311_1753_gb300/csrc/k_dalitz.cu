@@ -1186,10 +1186,12 @@ __device__ __forceinline__ Cx cinv(Cx a) {
   const double d = 1.0 / (a.r * a.r + a.i * a.i);
   return {a.r * d, -a.i * d};
 }
-__device__ void smeared_exp(Cx l, double t, double sig, const WeidCoef& W, Cx& T, Cx& dl, Cx& ds) {
+// g = e^{-t^2/(2 sigma^2)} is the same for the three rates of an event and comes in.
+// Inlined into the event loop, where l.i == 0 is known for the two real rates.
+__device__ __forceinline__ void smeared_exp(Cx l, double t, double sig, double g,
+                                            const WeidCoef& W, Cx& T, Cx& dl, Cx& ds) {
   const double k = 1.0 / (sig * kSqrt2);
   const Cx u = {(l.r * sig * sig - t) * k, l.i * sig * sig * k};
-  const double g = exp(-0.5 * t * t / (sig * sig));
   Cx w;
   if (u.r >= 0.0) {
     if (l.i == 0.0) w = {erfcx(u.r), 0.0};
@@ -1299,7 +1301,7 @@ __device__ void tddp_norm(const TddpPlan& T, const double* th, const double2* gr
 // The event pass: -log(I/N) summed (or stored per event) with the gradient; per-thread
 // gradient sums in shared memory (nfree x blockDim doubles).
 template <bool G, bool STORE>
-__global__ void __launch_bounds__(kThreads) k_tddp_events(
+__global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
     const __grid_constant__ TddpPlan T, const __grid_constant__ WeidCoef W,
     const double* __restrict__ theta, const double* __restrict__ ct,
     const double* __restrict__ csig, int64_t n, const double2* __restrict__ cache,
@@ -1334,8 +1336,10 @@ __global__ void __launch_bounds__(kThreads) k_tddp_events(
       B = {B.r + cb.r, B.i + cb.i};
     }
     const double t = ct[i], sigt = csig[i], sig = sc * sigt;
+    const double g = exp(-0.5 * t * t / (sig * sig));
     Cx Tv[3], Tl[3], Ts[3];
-    for (int j = 0; j < 3; ++j) smeared_exp(l[j], t, sig, W, Tv[j], Tl[j], Ts[j]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) smeared_exp(l[j], t, sig, g, W, Tv[j], Tl[j], Ts[j]);
     const double kk[4] = {0.5 * (Tv[0].r + Tv[1].r), Tv[2].r, 0.5 * (Tv[0].r - Tv[1].r), Tv[2].i};
     const double aa = A.r * A.r + A.i * A.i, bb = B.r * B.r + B.i * B.i;
     const Cx X = cmul({A.r, -A.i}, B);
@@ -1348,25 +1352,27 @@ __global__ void __launch_bounds__(kThreads) k_tddp_events(
     acc.add(-log(I));
     if (G) {
       const double iI = -1.0 / I;
+      // I = p |A|^2 + q |B|^2 + Re(z conj(A) B), p, q = (kk0 +- kk1)/2, z = kk2 + i kk3, so
+      // dI/dconj(c_r) = conj(a_r) E + conj(b_r) F with E = p A + z B/2, F = q B + conj(z) A/2,
+      // and dI/dRe c_r + i dI/dIm c_r = 2 dI/dconj(c_r).
+      const double p = 0.5 * (kk[0] + kk[1]), q = 0.5 * (kk[0] - kk[1]);
+      const Cx zB = cmul({kk[2], kk[3]}, B), zA = cmul({kk[2], -kk[3]}, A);
+      const double f2 = 2.0 * iI;
+      const Cx E = {f2 * (p * A.r + 0.5 * zB.r), f2 * (p * A.i + 0.5 * zB.i)};
+      const Cx F = {f2 * (q * B.r + 0.5 * zA.r), f2 * (q * B.i + 0.5 * zA.i)};
       for (int r = 0; r < D.nres; ++r) {
         const double2 a2 = cache[(size_t)r * n + i], b2 = cache[(size_t)(D.nres + r) * n + i];
-        for (int part = 0; part < 2; ++part) {
-          const int g = part ? D.res[r].g_im : D.res[r].g_re;
-          if (g < 0) continue;
-          const Cx dA = part ? Cx{-a2.y, a2.x} : Cx{a2.x, a2.y};
-          const Cx dB = part ? Cx{-b2.y, b2.x} : Cx{b2.x, b2.y};
-          const double daa = 2.0 * (A.r * dA.r + A.i * dA.i), dbb = 2.0 * (B.r * dB.r + B.i * dB.i);
-          const Cx x1 = cmul({dA.r, -dA.i}, B), x2 = cmul({A.r, -A.i}, dB);
-          const double dXr = x1.r + x2.r, dXi = x1.i + x2.i;
-          const double d = 0.5 * (daa + dbb) * kk[0] + 0.5 * (daa - dbb) * kk[1] + dXr * kk[2] -
-                           dXi * kk[3];
-          gsh[g * bd + tid] += d * iI;
-        }
+        // conj(a) E + conj(b) F
+        const double dr = a2.x * E.r + a2.y * E.i + b2.x * F.r + b2.y * F.i;
+        const double di = a2.x * E.i - a2.y * E.r + b2.x * F.i - b2.y * F.r;
+        if (D.res[r].g_re >= 0) gsh[D.res[r].g_re * bd + tid] += dr;
+        if (D.res[r].g_im >= 0) gsh[D.res[r].g_im * bd + tid] += di;
       }
       const int gp[4] = {T.g_tau, T.g_x, T.g_y, T.g_s};
       for (int q = 0; q < 4; ++q) {
         if (gp[q] < 0) continue;
         Cx d[3];
+#pragma unroll
         for (int j = 0; j < 3; ++j) d[j] = q < 3 ? cmul(Tl[j], dl[j][q]) : Cx{Ts[j].r * sigt, Ts[j].i * sigt};
         const double dk[4] = {0.5 * (d[0].r + d[1].r), d[2].r, 0.5 * (d[0].r - d[1].r), d[2].i};
         gsh[gp[q] * bd + tid] += (dI[0] * dk[0] + dI[1] * dk[1] + dI[2] * dk[2] + dI[3] * dk[3]) * iI;

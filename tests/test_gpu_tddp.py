@@ -119,3 +119,37 @@ def test_tddp_fit_matches_oracle_fit(gf):
     ro = minimise.fit(fg, start, np.full(len(free), 1e-3), lo, hi, up=0.5, tol=1e-9)
     assert ro.converged
     assert np.all(np.abs(r["theta"] - ro.x) <= 0.01 * ro.err), np.max(np.abs(r["theta"] - ro.x) / ro.err)
+
+
+def test_tddp_large_and_update(gf):
+    """10^6 events (a size at which a 1D context would reorder its columns; the mixing
+    context keeps the caller's order): sampled per-event log P against the oracle and the
+    NLL equal to the sum of the stored log P.  gf_update_data then replaces the events,
+    and rejects, with nothing replaced, events outside the kinematic region or with
+    sigma_t <= 0."""
+    ctx, root, obs, d, free = _models(gf)
+    n = 1_000_000
+    cols = _events(d, n, seed=11)
+    ctx.set_data(root, obs, cols)
+    th = d.p[free]
+    lg = ctx.logpdf(th)
+    idx = np.random.default_rng(5).choice(n, 300, replace=False)
+    sub = [c[idx] for c in cols]
+    lo_ = np.log(d.intensity_t(*sub, p=d.p)) - np.log(d.norm_t(p=d.p))
+    kap = _kappa(d, sub, d.p)
+    assert np.all(np.abs(lg[idx] - lo_) <= 1e-12 * kap * np.maximum(1.0, np.abs(lo_)))
+    f = ctx.nll(th)
+    assert abs(f + np.sum(lg)) <= 1e-9 * abs(f)
+
+    new = _events(d, n, seed=12)
+    ctx.update_data(new)
+    lg2 = ctx.logpdf(th)
+    sub = [c[idx] for c in new]
+    lo2 = np.log(d.intensity_t(*sub, p=d.p)) - np.log(d.norm_t(p=d.p))
+    assert np.all(np.abs(lg2[idx] - lo2) <= 1e-12 * _kappa(d, sub, d.p) * np.maximum(1.0, np.abs(lo2)))
+    for k, v in ((3, 0.0), (0, 10.0)):
+        bad = [c.copy() for c in cols]
+        bad[k][n // 2] = v
+        with pytest.raises(gf.GFError):
+            ctx.update_data(bad)
+        assert np.array_equal(ctx.logpdf(th), lg2)
