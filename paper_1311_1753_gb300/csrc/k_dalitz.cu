@@ -1192,21 +1192,25 @@ __device__ __forceinline__ void smeared_exp(Cx l, double t, double sig, double g
                                             const WeidCoef& W, Cx& T, Cx& dl, Cx& ds) {
   const double k = 1.0 / (sig * kSqrt2);
   const Cx u = {(l.r * sig * sig - t) * k, l.i * sig * sig * k};
+  // One Faddeeva (or erfcx) evaluation at a selected argument, w(i u) or under reflection
+  // w(-i u), i (sg u) = -sg Im u + i sg Re u: a warp holding events of both signs of Re u
+  // (the usual case: Re u < 0 for t above l sigma^2) evaluates it once, not twice.
+  const bool refl = u.r < 0.0;
+  const double sg = refl ? -1.0 : 1.0;
   Cx w;
-  if (u.r >= 0.0) {
-    if (l.i == 0.0) w = {erfcx(u.r), 0.0};
-    else faddeeva_df(-u.i, u.r, W, w.r, w.i);  // w(i u), i u = -ui + i ur
-    T = {0.5 * g * w.r, 0.5 * g * w.i};
-  } else {
-    if (l.i == 0.0) w = {erfcx(-u.r), 0.0};
-    else faddeeva_df(u.i, -u.r, W, w.r, w.i);  // w(-i u)
-    // e^{l^2 sigma^2/2 - l t}
-    const double er = 0.5 * (l.r * l.r - l.i * l.i) * sig * sig - l.r * t;
-    const double ei = l.r * l.i * sig * sig - l.i * t;
-    const double m = exp(er);
-    double sn, cs;
-    sincos(ei, &sn, &cs);
-    T = {m * cs - 0.5 * g * w.r, m * sn - 0.5 * g * w.i};
+  if (l.i == 0.0) w = {erfcx(sg * u.r), 0.0};
+  else faddeeva_df(-sg * u.i, sg * u.r, W, w.r, w.i);
+  const double h = 0.5 * g * sg;
+  T = {h * w.r, h * w.i};
+  if (refl) {  // + e^{l^2 sigma^2/2 - l t}
+    const double m = exp(0.5 * (l.r * l.r - l.i * l.i) * sig * sig - l.r * t);
+    if (l.i == 0.0) {
+      T.r += m;
+    } else {
+      double sn, cs;
+      sincos(l.i * (l.r * sig * sig - t), &sn, &cs);
+      T = {T.r + m * cs, T.i + m * sn};
+    }
   }
   const double c = sig * kInvSqrt2Pi;  // sigma / sqrt(2 pi)
   const Cx a = {l.r * sig * sig - t, l.i * sig * sig};
@@ -1235,71 +1239,88 @@ __device__ __forceinline__ void tddp_rates(double tau, double x, double y, Cx* l
   dl[2][2] = {0.0, 0.0};
 }
 
-// The normalisation N(theta) and dN/dtheta_free (thread-local; O(K^2)).
-__device__ void tddp_norm(const TddpPlan& T, const double* th, const double2* gram, double* N,
-                          double* dN) {
+// The normalisation N(theta) and dN/dtheta_free, by the block: thread a < K + 1 forms row
+// a of v = M c for M = G_A, G_B, X and of w = X^T conj(c) into vec[4 (K + 1)]; thread 0
+// then combines them.  Nsh[0] = N, Nsh[1 + k] = dN/dtheta_k.  Called by every thread of
+// the block; ends with a barrier.
+__device__ void tddp_norm_block(const TddpPlan& T, const double* th, const double2* gram,
+                                double* Nsh, Cx* vec, bool grad) {
   const DalitzPlan& D = T.D;
   const int K1 = D.nres + 1;
-  Cx c[kMaxRes + 1];
-  c[0] = {1.0, 0.0};
-  for (int r = 0; r < D.nres; ++r) c[r + 1] = {th[D.res[r].p_re], th[D.res[r].p_im]};
-  // v_k = sum_s M_ks c_s for the three matrices; w_k = sum_r conj(c_r) X_rk
-  double GA = 0.0, GB = 0.0;
-  Cx X = {0.0, 0.0};
-  Cx vA[kMaxRes + 1], vB[kMaxRes + 1], uX[kMaxRes + 1], wX[kMaxRes + 1];
-  for (int a = 0; a < K1; ++a) {
-    vA[a] = vB[a] = uX[a] = wX[a] = {0.0, 0.0};
+  auto coef = [&](int a) -> Cx {
+    return a == 0 ? Cx{1.0, 0.0} : Cx{th[D.res[a - 1].p_re], th[D.res[a - 1].p_im]};
+  };
+  const int a = threadIdx.x;
+  if (a < K1) {
+    Cx vA = {0.0, 0.0}, vB = vA, uX = vA, wX = vA;
     for (int b = 0; b < K1; ++b) {
+      const Cx cb = coef(b);
       const double2 ga = gram[a * K1 + b], gb = gram[K1 * K1 + a * K1 + b];
       const double2 gx = gram[2 * K1 * K1 + a * K1 + b];
-      const Cx pa = cmul({ga.x, ga.y}, c[b]), pb = cmul({gb.x, gb.y}, c[b]);
-      const Cx px = cmul({gx.x, gx.y}, c[b]);
-      vA[a] = {vA[a].r + pa.r, vA[a].i + pa.i};
-      vB[a] = {vB[a].r + pb.r, vB[a].i + pb.i};
-      uX[a] = {uX[a].r + px.r, uX[a].i + px.i};
       const double2 gxt = gram[2 * K1 * K1 + b * K1 + a];  // X_ba: conj(c_b) X_ba
-      const Cx q = cmul({c[b].r, -c[b].i}, {gxt.x, gxt.y});
-      wX[a] = {wX[a].r + q.r, wX[a].i + q.i};
+      const Cx pa = cmul({ga.x, ga.y}, cb), pb = cmul({gb.x, gb.y}, cb);
+      const Cx px = cmul({gx.x, gx.y}, cb), pw = cmul({cb.r, -cb.i}, {gxt.x, gxt.y});
+      vA = {vA.r + pa.r, vA.i + pa.i};
+      vB = {vB.r + pb.r, vB.i + pb.i};
+      uX = {uX.r + px.r, uX.i + px.i};
+      wX = {wX.r + pw.r, wX.i + pw.i};
     }
-    const Cx cc = {c[a].r, -c[a].i};
-    GA += cmul(cc, vA[a]).r;
-    GB += cmul(cc, vB[a]).r;
-    const Cx t = cmul(cc, uX[a]);
-    X = {X.r + t.r, X.i + t.i};
+    vec[a] = vA;
+    vec[K1 + a] = vB;
+    vec[2 * K1 + a] = uX;
+    vec[3 * K1 + a] = wX;
   }
-  Cx l[3], dl[3][3];
-  tddp_rates(th[T.p_tau], th[T.p_x], th[T.p_y], l, dl);
-  const Cx i1 = cinv(l[0]), i2 = cinv(l[1]), i3 = cinv(l[2]);
-  const double kk[4] = {0.5 * (i1.r + i2.r), i3.r, 0.5 * (i1.r - i2.r), i3.i};
-  const double dI[4] = {0.5 * (GA + GB), 0.5 * (GA - GB), X.r, -X.i};
-  *N = dI[0] * kk[0] + dI[1] * kk[1] + dI[2] * kk[2] + dI[3] * kk[3];
-  if (!dN) return;
-  for (int k = 0; k < T.nfree; ++k) dN[k] = 0.0;
-  for (int r = 0; r < D.nres; ++r)
-    for (int part = 0; part < 2; ++part) {
-      const int g = part ? D.res[r].g_im : D.res[r].g_re;
-      if (g < 0) continue;
-      const int a = r + 1;
-      // d/dRe c: 2 Re v, u + w; d/dIm c: 2 Im v, -i u + i w
-      const double dGA = 2.0 * (part ? vA[a].i : vA[a].r);
-      const double dGB = 2.0 * (part ? vB[a].i : vB[a].r);
-      const Cx dX = part ? Cx{uX[a].i - wX[a].i, -uX[a].r + wX[a].r}
-                         : Cx{uX[a].r + wX[a].r, uX[a].i + wX[a].i};
-      dN[g] += 0.5 * (dGA + dGB) * kk[0] + 0.5 * (dGA - dGB) * kk[1] + dX.r * kk[2] - dX.i * kk[3];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double GA = 0.0, GB = 0.0;
+    Cx X = {0.0, 0.0};
+    for (int k = 0; k < K1; ++k) {
+      const Cx c = coef(k), cc = {c.r, -c.i};
+      GA += cmul(cc, vec[k]).r;
+      GB += cmul(cc, vec[K1 + k]).r;
+      const Cx t = cmul(cc, vec[2 * K1 + k]);
+      X = {X.r + t.r, X.i + t.i};
     }
-  const int gp[3] = {T.g_tau, T.g_x, T.g_y};
-  for (int q = 0; q < 3; ++q) {
-    if (gp[q] < 0) continue;
-    // d(1/l)/dq = -(1/l^2) dl/dq
-    const Cx d1 = cmul(cmul(i1, i1), dl[0][q]), d2 = cmul(cmul(i2, i2), dl[1][q]);
-    const Cx d3 = cmul(cmul(i3, i3), dl[2][q]);
-    const double dk[4] = {-0.5 * (d1.r + d2.r), -d3.r, -0.5 * (d1.r - d2.r), -d3.i};
-    dN[gp[q]] += dI[0] * dk[0] + dI[1] * dk[1] + dI[2] * dk[2] + dI[3] * dk[3];
+    Cx l[3], dl[3][3];
+    tddp_rates(th[T.p_tau], th[T.p_x], th[T.p_y], l, dl);
+    const Cx i1 = cinv(l[0]), i2 = cinv(l[1]), i3 = cinv(l[2]);
+    const double kk[4] = {0.5 * (i1.r + i2.r), i3.r, 0.5 * (i1.r - i2.r), i3.i};
+    const double dI[4] = {0.5 * (GA + GB), 0.5 * (GA - GB), X.r, -X.i};
+    Nsh[0] = dI[0] * kk[0] + dI[1] * kk[1] + dI[2] * kk[2] + dI[3] * kk[3];
+    if (grad) {
+      double* dN = Nsh + 1;
+      for (int k = 0; k < T.nfree; ++k) dN[k] = 0.0;
+      for (int r = 0; r < D.nres; ++r)
+        for (int part = 0; part < 2; ++part) {
+          const int g = part ? D.res[r].g_im : D.res[r].g_re;
+          if (g < 0) continue;
+          const int q = r + 1;
+          // d/dRe c: 2 Re v, u + w; d/dIm c: 2 Im v, -i u + i w
+          const Cx va = vec[q], vb = vec[K1 + q], ux = vec[2 * K1 + q], wx = vec[3 * K1 + q];
+          const double dGA = 2.0 * (part ? va.i : va.r);
+          const double dGB = 2.0 * (part ? vb.i : vb.r);
+          const Cx dX = part ? Cx{ux.i - wx.i, -ux.r + wx.r} : Cx{ux.r + wx.r, ux.i + wx.i};
+          dN[g] += 0.5 * (dGA + dGB) * kk[0] + 0.5 * (dGA - dGB) * kk[1] + dX.r * kk[2] -
+                   dX.i * kk[3];
+        }
+      const int gp[3] = {T.g_tau, T.g_x, T.g_y};
+      for (int q = 0; q < 3; ++q) {
+        if (gp[q] < 0) continue;
+        // d(1/l)/dq = -(1/l^2) dl/dq
+        const Cx d1 = cmul(cmul(i1, i1), dl[0][q]), d2 = cmul(cmul(i2, i2), dl[1][q]);
+        const Cx d3 = cmul(cmul(i3, i3), dl[2][q]);
+        const double dk[4] = {-0.5 * (d1.r + d2.r), -d3.r, -0.5 * (d1.r - d2.r), -d3.i};
+        dN[gp[q]] += dI[0] * dk[0] + dI[1] * dk[1] + dI[2] * dk[2] + dI[3] * dk[3];
+      }
+    }
   }
+  __syncthreads();
 }
 
 // The event pass: -log(I/N) summed (or stored per event) with the gradient; per-thread
-// gradient sums in shared memory (nfree x blockDim doubles).
+// gradient sums in shared memory (nfree x blockDim doubles).  N enters the sums only
+// through n log N and n dN/N, so the last block forms it after the events; a block that
+// stores log P per event forms it first.
 template <bool G, bool STORE>
 __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
     const __grid_constant__ TddpPlan T, const __grid_constant__ WeidCoef W,
@@ -1312,19 +1333,22 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   __shared__ double th[4 * kMaxRes + 8];
   __shared__ double Nsh[1 + 4 * kMaxRes + 8];
   __shared__ double red[(kThreads / 32) * (1 + 4 * kMaxRes + 4)];
+  __shared__ Cx vec[4 * (kMaxRes + 1)];
   __shared__ int last;
   const int tid = threadIdx.x, bd = blockDim.x, nf = T.nfree;
-  // theta_all holds at most 4 kMaxRes + 4 parameters for this model
+  // theta_all holds at most 4 kMaxRes + 8 parameters for this model (checked at compile)
   for (int k = tid; k < 4 * kMaxRes + 8; k += bd) th[k] = theta[k];
-  __syncthreads();
-  if (tid == 0) tddp_norm(T, th, gram, &Nsh[0], G ? Nsh + 1 : nullptr);
   if (G)
     for (int k = 0; k < nf; ++k) gsh[k * bd + tid] = 0.0;
   __syncthreads();
+  double logN = 0.0;
+  if (STORE) {
+    tddp_norm_block(T, th, gram, Nsh, vec, false);
+    logN = log(Nsh[0]);
+  }
   const double tau = th[T.p_tau], mx = th[T.p_x], my = th[T.p_y], sc = th[T.p_s];
   Cx l[3], dl[3][3];
   tddp_rates(tau, mx, my, l, dl);
-  const double logN = log(Nsh[0]);
   Neu acc;
   for (int64_t i = (int64_t)blockIdx.x * bd + tid; i < n; i += (int64_t)gridDim.x * bd) {
     Cx A = {1.0, 0.0}, B = {1.0, 0.0};
@@ -1386,8 +1410,9 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
                   m, red, partials + (size_t)blockIdx.x * stride);
   if (!arrive_last_of(counter, gridDim.x, &last)) return;
   reduce_partials(partials, gridDim.x, stride, m, result, red);
+  tddp_norm_block(T, th, gram, Nsh, vec, G);
   if (tid == 0) {
-    result[0] += (double)n * logN;
+    result[0] += (double)n * log(Nsh[0]);
     if (G)
       for (int k = 0; k < nf; ++k) result[1 + k] += (double)n * Nsh[1 + k] / Nsh[0];
     *counter = 0u;
