@@ -10,6 +10,7 @@ namespace gfi {
 constexpr double kInvSqrtPi = 0.56418958354775628695;  // 1/sqrt(pi)
 constexpr double kTwoInvSqrtPi = 1.12837916709551257390;
 constexpr double kSqrt2 = 1.41421356237309504880;
+constexpr double kInvSqrt2 = 0.70710678118654752440;
 constexpr double kSqrt2Pi = 2.50662827463100050242;
 constexpr double kInvSqrt2Pi = 0.39894228040143267794;  // 1/sqrt(2 pi)
 
@@ -192,6 +193,23 @@ __device__ __forceinline__ void faddeeva_f2(F2 X, F2 Y, const WeidCoef& W, F2& W
   constexpr DFC c(kInvSqrtPi);
   WR = df_add(df_mul(c, ir), df_mul_f(df_sub(df_mul(pr, qr), df_mul(pi, qi)), 2.f));
   WI = df_add(df_mul(c, ii), df_mul_f(df_add(df_mul(pr, qi), df_mul(pi, qr)), 2.f));
+}
+// erfcx(y) = w(i y) for real y >= 0 by the same series: with z = i y, L - iz = L + y and
+// Z = (L - y)/(L + y) are real, so erfcx(y) = (1/sqrt(pi) + 2 P(Z)/(L + y))/(L + y) with
+// P(Z) = sum_n a_n Z^{n-1}; real pair arithmetic, the high-order terms in float as above.
+// FP64 in and out.
+__device__ __forceinline__ double erfcx_df(double y, const WeidCoef& W) {
+  const F2 L = {W.Lhi, W.Llo}, Y = df_from(y);
+  const F2 ir = df_rcp(df_add(L, Y));                                // 1/(L + y)
+  const F2 z = df_mul(df_sub(L, Y), ir);
+  float f = W.ahi[kWeidN];
+#pragma unroll
+  for (int n = kWeidN - 1; n >= kWeidSplit; --n) f = __fmaf_rn(f, z.hi, W.ahi[n]);
+  F2 p = {f, 0.f};
+#pragma unroll 1
+  for (int n = kWeidSplit - 1; n >= 1; --n) p = df_add(df_mul(p, z), F2{W.ahi[n], W.alo[n]});
+  constexpr DFC c(kInvSqrtPi);
+  return df_to(df_mul(df_add(c, df_mul_f(df_mul(p, ir), 2.f)), ir));
 }
 // FP64 in and out (the normalisation grid)
 __device__ __forceinline__ void faddeeva_df(double x, double y, const WeidCoef& W, double& wr,

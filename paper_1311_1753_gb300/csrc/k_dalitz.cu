@@ -1186,11 +1186,11 @@ __device__ __forceinline__ Cx cinv(Cx a) {
   const double d = 1.0 / (a.r * a.r + a.i * a.i);
   return {a.r * d, -a.i * d};
 }
-// g = e^{-t^2/(2 sigma^2)} is the same for the three rates of an event and comes in.
-// Inlined into the event loop, where l.i == 0 is known for the two real rates.
-__device__ __forceinline__ void smeared_exp(Cx l, double t, double sig, double g,
+// g = e^{-t^2/(2 sigma^2)} and is = 1/sigma are the same for the three rates of an event
+// and come in.
+__device__ __forceinline__ void smeared_exp(Cx l, double t, double sig, double is, double g,
                                             const WeidCoef& W, Cx& T, Cx& dl, Cx& ds) {
-  const double k = 1.0 / (sig * kSqrt2);
+  const double k = is * kInvSqrt2;
   const Cx u = {(l.r * sig * sig - t) * k, l.i * sig * sig * k};
   // One Faddeeva (or erfcx) evaluation at a selected argument, w(i u) or under reflection
   // w(-i u), i (sg u) = -sg Im u + i sg Re u: a warp holding events of both signs of Re u
@@ -1198,12 +1198,12 @@ __device__ __forceinline__ void smeared_exp(Cx l, double t, double sig, double g
   const bool refl = u.r < 0.0;
   const double sg = refl ? -1.0 : 1.0;
   Cx w;
-  if (l.i == 0.0) w = {erfcx(sg * u.r), 0.0};
+  if (l.i == 0.0) w = {erfcx_df(sg * u.r, W), 0.0};
   else faddeeva_df(-sg * u.i, sg * u.r, W, w.r, w.i);
   const double h = 0.5 * g * sg;
   T = {h * w.r, h * w.i};
   if (refl) {  // + e^{l^2 sigma^2/2 - l t}
-    const double m = exp(0.5 * (l.r * l.r - l.i * l.i) * sig * sig - l.r * t);
+    const double m = df_exp(0.5 * (l.r * l.r - l.i * l.i) * sig * sig - l.r * t);
     if (l.i == 0.0) {
       T.r += m;
     } else {
@@ -1218,8 +1218,21 @@ __device__ __forceinline__ void smeared_exp(Cx l, double t, double sig, double g
   dl = {aT.r - c * g, aT.i};
   const Cx l2 = cmul(l, l);
   const Cx l2T = cmul(l2, T);
-  const double f = g * kInvSqrt2Pi / (sig * sig);
+  const double f = g * kInvSqrt2Pi * is * is;
   ds = {l2T.r * sig - f * (l.r * sig * sig + t), l2T.i * sig - f * (l.i * sig * sig)};
+}
+
+// The same for a real rate l, written out in real arithmetic.
+__device__ __forceinline__ void smeared_exp_re(double l, double t, double sig, double is,
+                                               double g, const WeidCoef& W, double& T,
+                                               double& dl, double& ds) {
+  const double a = l * sig * sig - t;
+  const double u = a * is * kInvSqrt2;
+  const bool refl = u < 0.0;
+  T = (refl ? -0.5 : 0.5) * g * erfcx_df(fabs(u), W);
+  if (refl) T += df_exp(0.5 * l * l * sig * sig - l * t);
+  dl = a * T - sig * kInvSqrt2Pi * g;
+  ds = l * l * sig * T - g * kInvSqrt2Pi * is * is * (l * sig * sig + t);
 }
 
 // Rates and their derivatives in (tau, x, y): l_j and dl_j/d(tau, x, y).
@@ -1349,6 +1362,7 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   const double tau = th[T.p_tau], mx = th[T.p_x], my = th[T.p_y], sc = th[T.p_s];
   Cx l[3], dl[3][3];
   tddp_rates(tau, mx, my, l, dl);
+  const double gam = 1.0 / tau;
   Neu acc;
   for (int64_t i = (int64_t)blockIdx.x * bd + tid; i < n; i += (int64_t)gridDim.x * bd) {
     Cx A = {1.0, 0.0}, B = {1.0, 0.0};
@@ -1359,21 +1373,24 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
       A = {A.r + ca.r, A.i + ca.i};
       B = {B.r + cb.r, B.i + cb.i};
     }
-    const double t = ct[i], sigt = csig[i], sig = sc * sigt;
-    const double g = exp(-0.5 * t * t / (sig * sig));
-    Cx Tv[3], Tl[3], Ts[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) smeared_exp(l[j], t, sig, g, W, Tv[j], Tl[j], Ts[j]);
-    const double kk[4] = {0.5 * (Tv[0].r + Tv[1].r), Tv[2].r, 0.5 * (Tv[0].r - Tv[1].r), Tv[2].i};
+    const double t = ct[i], sigt = csig[i], sig = sc * sigt, is = 1.0 / sig;
+    const double g = df_exp(-0.5 * t * t * is * is);
+    // T_j, dT_j/dl_j, dT_j/dsigma for l_0,1 = G (1 -+ y) (real) and l_2 = G (1 - i x)
+    double T0, T1, L0, L1, S0, S1;
+    smeared_exp_re(l[0].r, t, sig, is, g, W, T0, L0, S0);
+    smeared_exp_re(l[1].r, t, sig, is, g, W, T1, L1, S1);
+    Cx T2, L2, S2;
+    smeared_exp(l[2], t, sig, is, g, W, T2, L2, S2);
+    const double kk[4] = {0.5 * (T0 + T1), T2.r, 0.5 * (T0 - T1), T2.i};
     const double aa = A.r * A.r + A.i * A.i, bb = B.r * B.r + B.i * B.i;
     const Cx X = cmul({A.r, -A.i}, B);
     const double dI[4] = {0.5 * (aa + bb), 0.5 * (aa - bb), X.r, -X.i};
     const double I = dI[0] * kk[0] + dI[1] * kk[1] + dI[2] * kk[2] + dI[3] * kk[3];
     if (STORE) {
-      out_logp[i] = log(I) - logN;
+      out_logp[i] = df_log(I) - logN;
       continue;
     }
-    acc.add(-log(I));
+    acc.add(-df_log(I));
     if (G) {
       const double iI = -1.0 / I;
       // I = p |A|^2 + q |B|^2 + Re(z conj(A) B), p, q = (kk0 +- kk1)/2, z = kk2 + i kk3, so
@@ -1392,15 +1409,18 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
         if (D.res[r].g_re >= 0) gsh[D.res[r].g_re * bd + tid] += dr;
         if (D.res[r].g_im >= 0) gsh[D.res[r].g_im * bd + tid] += di;
       }
-      const int gp[4] = {T.g_tau, T.g_x, T.g_y, T.g_s};
-      for (int q = 0; q < 4; ++q) {
-        if (gp[q] < 0) continue;
-        Cx d[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) d[j] = q < 3 ? cmul(Tl[j], dl[j][q]) : Cx{Ts[j].r * sigt, Ts[j].i * sigt};
-        const double dk[4] = {0.5 * (d[0].r + d[1].r), d[2].r, 0.5 * (d[0].r - d[1].r), d[2].i};
-        gsh[gp[q] * bd + tid] += (dI[0] * dk[0] + dI[1] * dk[1] + dI[2] * dk[2] + dI[3] * dk[3]) * iI;
-      }
+      // time parameters: dI = sum_k dI_k dkk_k with dkk from dT_j = dT_j/dl_j dl_j:
+      // dl_j/dtau = -G l_j, dl_2/dx = -i G, dl_0,1/dy = -+ G; dT_j/ds = dT_j/dsigma sigma_t
+      auto add_time = [&](int gi, double d0, double d1, Cx d2) {
+        if (gi >= 0)
+          gsh[gi * bd + tid] += (dI[0] * 0.5 * (d0 + d1) + dI[1] * d2.r +
+                                 dI[2] * 0.5 * (d0 - d1) + dI[3] * d2.i) * iI;
+      };
+      const Cx lL2 = cmul(L2, l[2]);
+      add_time(T.g_tau, -gam * l[0].r * L0, -gam * l[1].r * L1, {-gam * lL2.r, -gam * lL2.i});
+      add_time(T.g_x, 0.0, 0.0, {gam * L2.i, -gam * L2.r});
+      add_time(T.g_y, -gam * L0, gam * L1, {0.0, 0.0});
+      add_time(T.g_s, S0 * sigt, S1 * sigt, {S2.r * sigt, S2.i * sigt});
     }
   }
   if (STORE) return;
