@@ -1481,7 +1481,8 @@ static int finish_set_data(gf_ctx* ctx) {
   if (rc) return rc;
   if (ctx->is_tddp) {
     const TddpPlan& T = ctx->tplan;
-    const int64_t want = (d.n + kThreads - 1) / kThreads;
+    // every block resident, events split evenly over them (>= 64 per block)
+    const int64_t want = (d.n + 63) / 64;
     d.nblocks = (int)std::max<int64_t>(
         1, std::min<int64_t>(want, (int64_t)ctx->sm_count * kTddpBlocksPerSm));
     rc = grow(ctx, &d.partials, &d.partials_cap, (size_t)std::max(d.nblocks, 2048) * 64);

@@ -1364,7 +1364,11 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   tddp_rates(tau, mx, my, l, dl);
   const double gam = 1.0 / tau;
   Neu acc;
-  for (int64_t i = (int64_t)blockIdx.x * bd + tid; i < n; i += (int64_t)gridDim.x * bd) {
+  // a contiguous share of ceil(n / gridDim) events per block: with every block resident
+  // (kTddpBlocksPerSm per SM) each SM gets the same number of events
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t i_end = min(n, (int64_t)blockIdx.x * per + per);
+  for (int64_t i = (int64_t)blockIdx.x * per + tid; i < i_end; i += bd) {
     Cx A = {1.0, 0.0}, B = {1.0, 0.0};
     for (int r = 0; r < D.nres; ++r) {
       const double2 a = cache[(size_t)r * n + i], b = cache[(size_t)(D.nres + r) * n + i];

@@ -105,7 +105,7 @@ cudaError_t launch_tddp_cache(const TddpPlan& T, const double* theta, const doub
 cudaError_t launch_tddp_gram(const TddpPlan& T, const double* theta, const uint8_t* inside,
                              double2* gcols, double2* gram, cudaStream_t st);
 // NLL (+ gradient) into result[0 .. nfree], or (out_logp) per-event log P; nblocks at most
-// kTddpBlocksPerSm x the SM count (all blocks resident, the events strided over them)
+// kTddpBlocksPerSm x the SM count (all blocks resident, each a contiguous equal share of events)
 constexpr int kTddpBlocksPerSm = 3;
 cudaError_t launch_tddp_events(const TddpPlan& T, bool grad, const double* theta,
                                const double* const* cols, int64_t n, const double2* cache,
