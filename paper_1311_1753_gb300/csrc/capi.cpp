@@ -1493,9 +1493,10 @@ static int finish_set_data(gf_ctx* ctx) {
     cudaFree(d.tddp_gcols);
     cudaFree(d.tddp_gram);
     d.inside = nullptr;
-    d.tddp_cache = d.tddp_gcols = d.tddp_gram = nullptr;
+    d.tddp_cache = nullptr;
+    d.tddp_gcols = d.tddp_gram = nullptr;
     CK(cudaMalloc(&d.inside, ncell));
-    CK(cudaMalloc(&d.tddp_cache, sizeof(double2) * 2 * std::max(T.D.nres, 1) * (size_t)std::max<int64_t>(d.n, 1)));
+    CK(cudaMalloc(&d.tddp_cache, sizeof(float4) * 2 * std::max(T.D.nres, 1) * (size_t)std::max<int64_t>(d.n, 1)));
     CK(cudaMalloc(&d.tddp_gcols, sizeof(double2) * 2 * std::max(T.D.nres, 1) * ncell));
     CK(cudaMalloc(&d.tddp_gram, sizeof(double2) * 3 * (kMaxRes + 1) * (kMaxRes + 1)));
     d.tddp_ready = false;

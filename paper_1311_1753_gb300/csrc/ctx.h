@@ -93,7 +93,7 @@ struct DevState {
   GNormDesc gn_host[kMaxGNorm] = {};
   int ngn = 0;
   // time-dependent Dalitz model: per-event amplitudes, grid columns, the three grid sums
-  double2* tddp_cache = nullptr;
+  float4* tddp_cache = nullptr;  // per-event amplitudes as float pairs
   double2* tddp_gcols = nullptr;
   double2* tddp_gram = nullptr;
   bool tddp_ready = false;             // caches built for the loaded events

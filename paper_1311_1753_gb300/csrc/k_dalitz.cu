@@ -1074,12 +1074,19 @@ int dalitz_blocks_per_sm(bool mixed, bool grad, bool cached_only, int nfree) {
 // integrals are 1/l.  FP64 throughout (the amplitudes come from a per-event cache, the
 // resonance shapes being fixed).
 
-// Per-event amplitudes a_r, b_r: the resonance code of the Dalitz event pass in FP64.
+// A complex FP64 value as two float pairs (re hi, re lo, im hi, im lo).
+__device__ __forceinline__ float4 pair4(double re, double im) {
+  const float a = __double2float_rn(re), c = __double2float_rn(im);
+  return make_float4(a, __double2float_rn(re - (double)a), c, __double2float_rn(im - (double)c));
+}
+
+// Per-event amplitudes a_r, b_r: the resonance code of the Dalitz event pass in FP64,
+// stored as float pairs (the event pass multiplies them in pair arithmetic).
 __global__ void __launch_bounds__(kThreads) k_tddp_cache(const __grid_constant__ TddpPlan T,
                                                         const double* __restrict__ theta,
                                                         const double* __restrict__ s12,
                                                         const double* __restrict__ s13, int64_t n,
-                                                        double2* __restrict__ cache) {
+                                                        float4* __restrict__ cache) {
   const DalitzPlan& D = T.D;
   __shared__ ResK rk[kMaxRes];
   __shared__ DzC<double> C;
@@ -1097,10 +1104,10 @@ __global__ void __launch_bounds__(kThreads) k_tddp_cache(const __grid_constant__
       double FS, Gm;
       chan_kin_c<double>(C, R.channel, x, y, z, k);
       res_amp_c<double>(R, C, r, k, A, FS, BW, Gm);
-      cache[(size_t)r * n + i] = make_double2(A.r, A.i);
+      cache[(size_t)r * n + i] = pair4(A.r, A.i);
       chan_kin_c<double>(C, R.channel, x, z, y, k);  // (s12, s23): the CP-conjugate point
       res_amp_c<double>(R, C, r, k, A, FS, BW, Gm);
-      cache[(size_t)(D.nres + r) * n + i] = make_double2(A.r, A.i);
+      cache[(size_t)(D.nres + r) * n + i] = pair4(A.r, A.i);
     }
   }
 }
@@ -1331,28 +1338,33 @@ __device__ void tddp_norm_block(const TddpPlan& T, const double* th, const doubl
 }
 
 // The event pass: -log(I/N) summed (or stored per event) with the gradient; per-thread
-// gradient sums in shared memory (nfree x blockDim doubles).  N enters the sums only
+// gradient sums in shared memory (nfree x blockDim pairs).  The amplitude sums A, B and
+// the coefficient gradient (multiply-adds of cached amplitudes) run in double-float pairs
+// on the FP32 pipe, the time dependence in FP64.  N enters the sums only
 // through n log N and n dN/N, so the last block forms it after the events; a block that
 // stores log P per event forms it first.
 template <bool G, bool STORE>
 __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
     const __grid_constant__ TddpPlan T, const __grid_constant__ WeidCoef W,
     const double* __restrict__ theta, const double* __restrict__ ct,
-    const double* __restrict__ csig, int64_t n, const double2* __restrict__ cache,
+    const double* __restrict__ csig, int64_t n, const float4* __restrict__ cache,
     const double2* __restrict__ gram, double* __restrict__ partials,
     unsigned* __restrict__ counter, double* __restrict__ result, double* __restrict__ out_logp) {
   const DalitzPlan& D = T.D;
-  extern __shared__ double gsh[];  // G: nfree x blockDim
+  extern __shared__ F2 gsh[];  // G: nfree x blockDim
   __shared__ double th[4 * kMaxRes + 8];
   __shared__ double Nsh[1 + 4 * kMaxRes + 8];
   __shared__ double red[(kThreads / 32) * (1 + 4 * kMaxRes + 4)];
   __shared__ Cx vec[4 * (kMaxRes + 1)];
+  __shared__ F2 cp[2 * kMaxRes];  // c_r as pairs (re, im)
   __shared__ int last;
   const int tid = threadIdx.x, bd = blockDim.x, nf = T.nfree;
   // theta_all holds at most 4 kMaxRes + 8 parameters for this model (checked at compile)
   for (int k = tid; k < 4 * kMaxRes + 8; k += bd) th[k] = theta[k];
   if (G)
-    for (int k = 0; k < nf; ++k) gsh[k * bd + tid] = 0.0;
+    for (int k = 0; k < nf; ++k) gsh[k * bd + tid] = F2{0.f, 0.f};
+  if (tid < 2 * D.nres)
+    cp[tid] = df_split(theta[(tid & 1) ? D.res[tid >> 1].p_im : D.res[tid >> 1].p_re]);
   __syncthreads();
   double logN = 0.0;
   if (STORE) {
@@ -1369,14 +1381,18 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t i_end = min(n, (int64_t)blockIdx.x * per + per);
   for (int64_t i = (int64_t)blockIdx.x * per + tid; i < i_end; i += bd) {
-    Cx A = {1.0, 0.0}, B = {1.0, 0.0};
+    // A = 1 + sum_r c_r a_r, B = 1 + sum_r c_r b_r in pairs
+    F2 Ar = {1.f, 0.f}, Ai = {0.f, 0.f}, Br = Ar, Bi = Ai;
     for (int r = 0; r < D.nres; ++r) {
-      const double2 a = cache[(size_t)r * n + i], b = cache[(size_t)(D.nres + r) * n + i];
-      const Cx c = {th[D.res[r].p_re], th[D.res[r].p_im]};
-      const Cx ca = cmul(c, {a.x, a.y}), cb = cmul(c, {b.x, b.y});
-      A = {A.r + ca.r, A.i + ca.i};
-      B = {B.r + cb.r, B.i + cb.i};
+      const float4 a = cache[(size_t)r * n + i], b = cache[(size_t)(D.nres + r) * n + i];
+      const F2 cr = cp[2 * r], ci = cp[2 * r + 1];
+      const F2 are = {a.x, a.y}, aim = {a.z, a.w}, bre = {b.x, b.y}, bim = {b.z, b.w};
+      Ar = df_add(Ar, df_sub(df_mul(cr, are), df_mul(ci, aim)));
+      Ai = df_add(Ai, df_add(df_mul(cr, aim), df_mul(ci, are)));
+      Br = df_add(Br, df_sub(df_mul(cr, bre), df_mul(ci, bim)));
+      Bi = df_add(Bi, df_add(df_mul(cr, bim), df_mul(ci, bre)));
     }
+    const Cx A = {df_to(Ar), df_to(Ai)}, B = {df_to(Br), df_to(Bi)};
     const double t = ct[i], sigt = csig[i], sig = sc * sigt, is = 1.0 / sig;
     const double g = df_exp(-0.5 * t * t * is * is);
     // T_j, dT_j/dl_j, dT_j/dsigma for l_0,1 = G (1 -+ y) (real) and l_2 = G (1 - i x)
@@ -1403,22 +1419,31 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
       const double p = 0.5 * (kk[0] + kk[1]), q = 0.5 * (kk[0] - kk[1]);
       const Cx zB = cmul({kk[2], kk[3]}, B), zA = cmul({kk[2], -kk[3]}, A);
       const double f2 = 2.0 * iI;
-      const Cx E = {f2 * (p * A.r + 0.5 * zB.r), f2 * (p * A.i + 0.5 * zB.i)};
-      const Cx F = {f2 * (q * B.r + 0.5 * zA.r), f2 * (q * B.i + 0.5 * zA.i)};
+      const F2 Er = df_split(f2 * (p * A.r + 0.5 * zB.r)), Ei = df_split(f2 * (p * A.i + 0.5 * zB.i));
+      const F2 Fr = df_split(f2 * (q * B.r + 0.5 * zA.r)), Fi = df_split(f2 * (q * B.i + 0.5 * zA.i));
       for (int r = 0; r < D.nres; ++r) {
-        const double2 a2 = cache[(size_t)r * n + i], b2 = cache[(size_t)(D.nres + r) * n + i];
+        const float4 a = cache[(size_t)r * n + i], b = cache[(size_t)(D.nres + r) * n + i];
+        const F2 are = {a.x, a.y}, aim = {a.z, a.w}, bre = {b.x, b.y}, bim = {b.z, b.w};
         // conj(a) E + conj(b) F
-        const double dr = a2.x * E.r + a2.y * E.i + b2.x * F.r + b2.y * F.i;
-        const double di = a2.x * E.i - a2.y * E.r + b2.x * F.i - b2.y * F.r;
-        if (D.res[r].g_re >= 0) gsh[D.res[r].g_re * bd + tid] += dr;
-        if (D.res[r].g_im >= 0) gsh[D.res[r].g_im * bd + tid] += di;
+        if (D.res[r].g_re >= 0) {
+          F2& s = gsh[D.res[r].g_re * bd + tid];
+          s = df_add(s, df_add(df_add(df_mul(are, Er), df_mul(aim, Ei)),
+                               df_add(df_mul(bre, Fr), df_mul(bim, Fi))));
+        }
+        if (D.res[r].g_im >= 0) {
+          F2& s = gsh[D.res[r].g_im * bd + tid];
+          s = df_add(s, df_add(df_sub(df_mul(are, Ei), df_mul(aim, Er)),
+                               df_sub(df_mul(bre, Fi), df_mul(bim, Fr))));
+        }
       }
       // time parameters: dI = sum_k dI_k dkk_k with dkk from dT_j = dT_j/dl_j dl_j:
       // dl_j/dtau = -G l_j, dl_2/dx = -i G, dl_0,1/dy = -+ G; dT_j/ds = dT_j/dsigma sigma_t
       auto add_time = [&](int gi, double d0, double d1, Cx d2) {
-        if (gi >= 0)
-          gsh[gi * bd + tid] += (dI[0] * 0.5 * (d0 + d1) + dI[1] * d2.r +
-                                 dI[2] * 0.5 * (d0 - d1) + dI[3] * d2.i) * iI;
+        if (gi >= 0) {
+          F2& s = gsh[gi * bd + tid];
+          s = df_add(s, df_split((dI[0] * 0.5 * (d0 + d1) + dI[1] * d2.r +
+                                  dI[2] * 0.5 * (d0 - d1) + dI[3] * d2.i) * iI));
+        }
       };
       const Cx lL2 = cmul(L2, l[2]);
       add_time(T.g_tau, -gam * l[0].r * L0, -gam * l[1].r * L1, {-gam * lL2.r, -gam * lL2.i});
@@ -1430,7 +1455,7 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   if (STORE) return;
   const int m = 1 + (G ? nf : 0);
   const int stride = 1 + 4 * kMaxRes + 4;
-  block_sum_pairs([&](int k) -> F2 { return df_split(k == 0 ? acc.get() : gsh[(k - 1) * bd + tid]); },
+  block_sum_pairs([&](int k) -> F2 { return k == 0 ? df_split(acc.get()) : gsh[(k - 1) * bd + tid]; },
                   m, red, partials + (size_t)blockIdx.x * stride);
   if (!arrive_last_of(counter, gridDim.x, &last)) return;
   reduce_partials(partials, gridDim.x, stride, m, result, red);
@@ -1444,7 +1469,7 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
 }
 
 cudaError_t launch_tddp_cache(const TddpPlan& T, const double* theta, const double* s12,
-                              const double* s13, int64_t n, double2* cache, cudaStream_t st) {
+                              const double* s13, int64_t n, float4* cache, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_tddp_cache<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(T, theta, s12, s13, n, cache);
   return cudaGetLastError();
@@ -1462,11 +1487,11 @@ cudaError_t launch_tddp_gram(const TddpPlan& T, const double* theta, const uint8
 }
 
 cudaError_t launch_tddp_events(const TddpPlan& T, bool grad, const double* theta,
-                               const double* const* cols, int64_t n, const double2* cache,
+                               const double* const* cols, int64_t n, const float4* cache,
                                const double2* gram, double* partials, unsigned* counter,
                                double* result, double* out_logp, int nblocks,
                                const WeidCoef& W, cudaStream_t st) {
-  const size_t smem = grad ? sizeof(double) * T.nfree * kThreads : 0;
+  const size_t smem = grad ? sizeof(F2) * T.nfree * kThreads : 0;
   if (out_logp) {
     k_tddp_events<false, true><<<nblocks, kThreads, 0, st>>>(T, W, theta, cols[2], cols[3], n,
                                                             cache, gram, partials, counter,

@@ -96,9 +96,10 @@ cudaError_t launch_tick_dalitz(bool mixed, const TickItem* items, int nfits, int
 constexpr int kGramEntries = (kMaxRes + 1) * (kMaxRes + 2) / 2;
 
 // time-dependent Dalitz model (k_dalitz.cu)
-// per-event amplitudes a_r (at s12, s13) and b_r (at s12, s23): cache [2][nres][n] double2
+// per-event amplitudes a_r (at s12, s13) and b_r (at s12, s23): cache [2][nres][n], each
+// complex value as two float pairs (re hi, re lo, im hi, im lo)
 cudaError_t launch_tddp_cache(const TddpPlan& T, const double* theta, const double* s12,
-                              const double* s13, int64_t n, double2* cache, cudaStream_t st);
+                              const double* s13, int64_t n, float4* cache, cudaStream_t st);
 // the three (nres+1)^2 complex grid sums G_A, G_B, X (dA sum conj(a_r) a_s, conj(b_r) b_s,
 // conj(a_r) b_s; index 0 the non-resonant 1) into gram [3][(nres+1)^2]; gcols: scratch
 // [2][nres][nbx nby] double2; inside: the cell mask
@@ -108,7 +109,7 @@ cudaError_t launch_tddp_gram(const TddpPlan& T, const double* theta, const uint8
 // kTddpBlocksPerSm x the SM count (all blocks resident, each a contiguous equal share of events)
 constexpr int kTddpBlocksPerSm = 3;
 cudaError_t launch_tddp_events(const TddpPlan& T, bool grad, const double* theta,
-                               const double* const* cols, int64_t n, const double2* cache,
+                               const double* const* cols, int64_t n, const float4* cache,
                                const double2* gram, double* partials, unsigned* counter,
                                double* result, double* out_logp, int nblocks,
                                const WeidCoef& W, cudaStream_t st);
