@@ -1259,39 +1259,43 @@ __device__ __forceinline__ void tddp_rates(double tau, double x, double y, Cx* l
   dl[2][2] = {0.0, 0.0};
 }
 
-// The normalisation N(theta) and dN/dtheta_free, by the block: thread a < K + 1 forms row
-// a of v = M c for M = G_A, G_B, X and of w = X^T conj(c) into vec[4 (K + 1)]; thread 0
-// then combines them.  Nsh[0] = N, Nsh[1 + k] = dN/dtheta_k.  Called by every thread of
-// the block; ends with a barrier.
+// The normalisation N(theta) and dN/dtheta_free, by the block, in three phases (each a
+// short FP64 chain per thread; a serial chain on one thread costs the narrow FP64 pipe's
+// full latency per operation):
+//  1. thread (j, a), j < 4, a < K + 1: row a of v = M c for M = G_A, G_B, X (j = 0, 1, 2)
+//     or of w = X^T conj(c) (j = 3) into vec[j (K + 1) + a];
+//  2. thread 0: G_A = c^H G_A c, G_B, X = c^H X c, the time integrals 1/l_j and N;
+//  3. thread e < 2 nres: the coefficient term e (Re, Im of c_{e/2}); threads 2 nres + q:
+//     tau, x, y; into part[]; then thread k sums the terms of free parameter k in order
+//     (a parameter may serve several coefficients).
+// Nsh[0] = N, Nsh[1 + k] = dN/dtheta_k; scratch: vec[4 (kMaxRes + 1)], part[2 kMaxRes + 3],
+// kd[8].  Called by every thread of the block; ends with a barrier.
 __device__ void tddp_norm_block(const TddpPlan& T, const double* th, const double2* gram,
-                                double* Nsh, Cx* vec, bool grad) {
+                                double* Nsh, Cx* vec, double* part, double* kd, bool grad) {
   const DalitzPlan& D = T.D;
-  const int K1 = D.nres + 1;
+  const int K1 = D.nres + 1, tid = threadIdx.x;
   auto coef = [&](int a) -> Cx {
     return a == 0 ? Cx{1.0, 0.0} : Cx{th[D.res[a - 1].p_re], th[D.res[a - 1].p_im]};
   };
-  const int a = threadIdx.x;
-  if (a < K1) {
-    Cx vA = {0.0, 0.0}, vB = vA, uX = vA, wX = vA;
+  if (tid < 4 * K1) {
+    const int j = tid / K1, a = tid % K1;
+    Cx v = {0.0, 0.0};
     for (int b = 0; b < K1; ++b) {
       const Cx cb = coef(b);
-      const double2 ga = gram[a * K1 + b], gb = gram[K1 * K1 + a * K1 + b];
-      const double2 gx = gram[2 * K1 * K1 + a * K1 + b];
-      const double2 gxt = gram[2 * K1 * K1 + b * K1 + a];  // X_ba: conj(c_b) X_ba
-      const Cx pa = cmul({ga.x, ga.y}, cb), pb = cmul({gb.x, gb.y}, cb);
-      const Cx px = cmul({gx.x, gx.y}, cb), pw = cmul({cb.r, -cb.i}, {gxt.x, gxt.y});
-      vA = {vA.r + pa.r, vA.i + pa.i};
-      vB = {vB.r + pb.r, vB.i + pb.i};
-      uX = {uX.r + px.r, uX.i + px.i};
-      wX = {wX.r + pw.r, wX.i + pw.i};
+      Cx pr;
+      if (j < 3) {
+        const double2 g = gram[j * K1 * K1 + a * K1 + b];
+        pr = cmul({g.x, g.y}, cb);
+      } else {
+        const double2 g = gram[2 * K1 * K1 + b * K1 + a];  // X_ba: conj(c_b) X_ba
+        pr = cmul({cb.r, -cb.i}, {g.x, g.y});
+      }
+      v = {v.r + pr.r, v.i + pr.i};
     }
-    vec[a] = vA;
-    vec[K1 + a] = vB;
-    vec[2 * K1 + a] = uX;
-    vec[3 * K1 + a] = wX;
+    vec[tid] = v;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double GA = 0.0, GB = 0.0;
     Cx X = {0.0, 0.0};
     for (int k = 0; k < K1; ++k) {
@@ -1307,32 +1311,66 @@ __device__ void tddp_norm_block(const TddpPlan& T, const double* th, const doubl
     const double kk[4] = {0.5 * (i1.r + i2.r), i3.r, 0.5 * (i1.r - i2.r), i3.i};
     const double dI[4] = {0.5 * (GA + GB), 0.5 * (GA - GB), X.r, -X.i};
     Nsh[0] = dI[0] * kk[0] + dI[1] * kk[1] + dI[2] * kk[2] + dI[3] * kk[3];
-    if (grad) {
-      double* dN = Nsh + 1;
-      for (int k = 0; k < T.nfree; ++k) dN[k] = 0.0;
-      for (int r = 0; r < D.nres; ++r)
-        for (int part = 0; part < 2; ++part) {
-          const int g = part ? D.res[r].g_im : D.res[r].g_re;
-          if (g < 0) continue;
-          const int q = r + 1;
-          // d/dRe c: 2 Re v, u + w; d/dIm c: 2 Im v, -i u + i w
-          const Cx va = vec[q], vb = vec[K1 + q], ux = vec[2 * K1 + q], wx = vec[3 * K1 + q];
-          const double dGA = 2.0 * (part ? va.i : va.r);
-          const double dGB = 2.0 * (part ? vb.i : vb.r);
-          const Cx dX = part ? Cx{ux.i - wx.i, -ux.r + wx.r} : Cx{ux.r + wx.r, ux.i + wx.i};
-          dN[g] += 0.5 * (dGA + dGB) * kk[0] + 0.5 * (dGA - dGB) * kk[1] + dX.r * kk[2] -
-                   dX.i * kk[3];
-        }
-      const int gp[3] = {T.g_tau, T.g_x, T.g_y};
-      for (int q = 0; q < 3; ++q) {
-        if (gp[q] < 0) continue;
-        // d(1/l)/dq = -(1/l^2) dl/dq
-        const Cx d1 = cmul(cmul(i1, i1), dl[0][q]), d2 = cmul(cmul(i2, i2), dl[1][q]);
-        const Cx d3 = cmul(cmul(i3, i3), dl[2][q]);
-        const double dk[4] = {-0.5 * (d1.r + d2.r), -d3.r, -0.5 * (d1.r - d2.r), -d3.i};
-        dN[gp[q]] += dI[0] * dk[0] + dI[1] * dk[1] + dI[2] * dk[2] + dI[3] * dk[3];
-      }
+    for (int k = 0; k < 4; ++k) {
+      kd[k] = kk[k];
+      kd[4 + k] = dI[k];
     }
+  }
+  __syncthreads();
+  if (!grad) return;
+  const int ne = 2 * D.nres;
+  if (tid < ne) {
+    // d/dRe c: 2 Re v, u + w; d/dIm c: 2 Im v, -i u + i w
+    const int q = tid / 2 + 1, im = tid & 1;
+    const Cx va = vec[q], vb = vec[K1 + q], ux = vec[2 * K1 + q], wx = vec[3 * K1 + q];
+    const double dGA = 2.0 * (im ? va.i : va.r), dGB = 2.0 * (im ? vb.i : vb.r);
+    const Cx dX = im ? Cx{ux.i - wx.i, -ux.r + wx.r} : Cx{ux.r + wx.r, ux.i + wx.i};
+    part[tid] = 0.5 * (dGA + dGB) * kd[0] + 0.5 * (dGA - dGB) * kd[1] + dX.r * kd[2] -
+                dX.i * kd[3];
+  } else if (tid < ne + 3) {
+    // d(1/l)/dq = -(1/l^2) dl/dq
+    const int q = tid - ne;
+    Cx l[3], dl[3][3];
+    tddp_rates(th[T.p_tau], th[T.p_x], th[T.p_y], l, dl);
+    Cx d[3];
+    for (int j = 0; j < 3; ++j) {
+      const Cx ij = cinv(l[j]);
+      d[j] = cmul(cmul(ij, ij), dl[j][q]);
+    }
+    const double dk[4] = {-0.5 * (d[0].r + d[1].r), -d[2].r, -0.5 * (d[0].r - d[1].r), -d[2].i};
+    part[tid] = kd[4] * dk[0] + kd[5] * dk[1] + kd[6] * dk[2] + kd[7] * dk[3];
+  }
+  __syncthreads();
+  for (int k = tid; k < T.nfree; k += blockDim.x) {
+    double v = 0.0;
+    for (int e = 0; e < ne; ++e)
+      if ((e & 1 ? D.res[e / 2].g_im : D.res[e / 2].g_re) == k) v += part[e];
+    const int gp[3] = {T.g_tau, T.g_x, T.g_y};
+    for (int q = 0; q < 3; ++q)
+      if (gp[q] == k) v += part[ne + q];
+    Nsh[1 + k] = v;
+  }
+  __syncthreads();
+}
+
+// Cross-block sums by the last block: out[k] = sum over b < nblk of partials[b stride + k],
+// k < m.  Warp w takes k = w, w + nwarps, ...; its lanes stride over the blocks with
+// several loads in flight, pair sums, then a fixed shuffle tree: a fixed order, and a
+// short chain per value (the generic pass walks the values one after another).
+__device__ inline void reduce_partials_warps(const double* partials, int nblk, int stride, int m,
+                                             double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = warp; k < m; k += nw) {
+    F2 a = {0.f, 0.f};
+#pragma unroll 8
+    for (int b = lane; b < nblk; b += 32)
+      a = df_add(a, df_split(__ldcg(partials + (size_t)b * stride + k)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const F2 u = {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+      a = df_add(a, u);
+    }
+    if (lane == 0) out[k] = df_to(a);
   }
   __syncthreads();
 }
@@ -1356,6 +1394,7 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   __shared__ double Nsh[1 + 4 * kMaxRes + 8];
   __shared__ double red[(kThreads / 32) * (1 + 4 * kMaxRes + 4)];
   __shared__ Cx vec[4 * (kMaxRes + 1)];
+  __shared__ double part[2 * kMaxRes + 3], kd[8];
   __shared__ F2 cp[2 * kMaxRes];  // c_r as pairs (re, im)
   __shared__ int last;
   const int tid = threadIdx.x, bd = blockDim.x, nf = T.nfree;
@@ -1368,7 +1407,7 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   __syncthreads();
   double logN = 0.0;
   if (STORE) {
-    tddp_norm_block(T, th, gram, Nsh, vec, false);
+    tddp_norm_block(T, th, gram, Nsh, vec, part, kd, false);
     logN = log(Nsh[0]);
   }
   const double tau = th[T.p_tau], mx = th[T.p_x], my = th[T.p_y], sc = th[T.p_s];
@@ -1458,14 +1497,14 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   block_sum_pairs([&](int k) -> F2 { return k == 0 ? df_split(acc.get()) : gsh[(k - 1) * bd + tid]; },
                   m, red, partials + (size_t)blockIdx.x * stride);
   if (!arrive_last_of(counter, gridDim.x, &last)) return;
-  reduce_partials(partials, gridDim.x, stride, m, result, red);
-  tddp_norm_block(T, th, gram, Nsh, vec, G);
+  reduce_partials_warps(partials, gridDim.x, stride, m, result);
+  tddp_norm_block(T, th, gram, Nsh, vec, part, kd, G);
   if (tid == 0) {
     result[0] += (double)n * log(Nsh[0]);
-    if (G)
-      for (int k = 0; k < nf; ++k) result[1 + k] += (double)n * Nsh[1 + k] / Nsh[0];
     *counter = 0u;
   }
+  if (G)
+    for (int k = tid; k < nf; k += bd) result[1 + k] += (double)n * Nsh[1 + k] / Nsh[0];
 }
 
 cudaError_t launch_tddp_cache(const TddpPlan& T, const double* theta, const double* s12,
