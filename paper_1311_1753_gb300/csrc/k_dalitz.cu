@@ -1279,17 +1279,18 @@ __device__ void tddp_norm_block(const TddpPlan& T, const double* th, const doubl
   };
   if (tid < 4 * K1) {
     const int j = tid / K1, a = tid % K1;
+    // the row's entries first, all loads in flight (X_ba for w: conj(c_b) X_ba)
+    double2 g[kMaxRes + 1];
+#pragma unroll
+    for (int b = 0; b < kMaxRes + 1; ++b)
+      g[b] = b < K1 ? gram[j < 3 ? j * K1 * K1 + a * K1 + b : 2 * K1 * K1 + b * K1 + a]
+                    : make_double2(0.0, 0.0);
     Cx v = {0.0, 0.0};
-    for (int b = 0; b < K1; ++b) {
+#pragma unroll
+    for (int b = 0; b < kMaxRes + 1; ++b) {
+      if (b >= K1) break;
       const Cx cb = coef(b);
-      Cx pr;
-      if (j < 3) {
-        const double2 g = gram[j * K1 * K1 + a * K1 + b];
-        pr = cmul({g.x, g.y}, cb);
-      } else {
-        const double2 g = gram[2 * K1 * K1 + b * K1 + a];  // X_ba: conj(c_b) X_ba
-        pr = cmul({cb.r, -cb.i}, {g.x, g.y});
-      }
+      const Cx pr = j < 3 ? cmul({g[b].x, g[b].y}, cb) : cmul({cb.r, -cb.i}, {g[b].x, g[b].y});
       v = {v.r + pr.r, v.i + pr.i};
     }
     vec[tid] = v;
@@ -1354,17 +1355,25 @@ __device__ void tddp_norm_block(const TddpPlan& T, const double* th, const doubl
 }
 
 // Cross-block sums by the last block: out[k] = sum over b < nblk of partials[b stride + k],
-// k < m.  Warp w takes k = w, w + nwarps, ...; its lanes stride over the blocks with
-// several loads in flight, pair sums, then a fixed shuffle tree: a fixed order, and a
-// short chain per value (the generic pass walks the values one after another).
+// k < m.  Warp w takes k = w, w + nwarps, ...; its lanes stride over the blocks with all
+// their loads in flight (a load that waits for the previous one costs a full L2 round
+// trip), pair sums (the padding zeros add exactly), then a fixed shuffle tree.
 __device__ inline void reduce_partials_warps(const double* partials, int nblk, int stride, int m,
                                              double* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int kPer = 16;  // loads per lane in flight (456 blocks: one pass)
   for (int k = warp; k < m; k += nw) {
     F2 a = {0.f, 0.f};
-#pragma unroll 8
-    for (int b = lane; b < nblk; b += 32)
-      a = df_add(a, df_split(__ldcg(partials + (size_t)b * stride + k)));
+    for (int b0 = 0; b0 < nblk; b0 += 32 * kPer) {
+      double v[kPer];
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int b = b0 + lane + 32 * j;
+        v[j] = b < nblk ? __ldcg(partials + (size_t)b * stride + k) : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) a = df_add(a, df_split(v[j]));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const F2 u = {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
