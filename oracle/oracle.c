@@ -1042,9 +1042,9 @@ double orc_zemach_at(const orc_dkin* k, int ch, int L, double s12, double s13) {
 }
 
 /* ------------------------------------------------------------------------------ */
-/* Time-dependent Dalitz model (Sec. 4: the D0 -> pi+ pi- pi0 mixing fit, with      */
-/* "hyperbolic and trigonometric functions convolved with Gaussian resolution        */
-/* functions" and a per-event decay-time uncertainty).  The paper gives no formula;  */
+/* Time-dependent Dalitz model (Sec. 4: the D0 -> pi+ pi- pi0 mixing fit, whose time */
+/* dependence is cosh/sinh and cos/sin terms, each smeared by a Gaussian resolution, */
+/* with a per-event decay-time uncertainty).  The paper gives no formula;           */
 /* the reading used here is the standard one for D0 mixing in a self-conjugate       */
 /* multi-body final state, with q/p = 1:                                           */
 /*   I(s12, s13, t) = 1/2 (|A|^2 + |B|^2) Tch + 1/2 (|A|^2 - |B|^2) Tc               */
