@@ -106,19 +106,34 @@ __device__ __forceinline__ void block_sum_pairs(Val val, int m, double* red, dou
   }
 }
 
-// Cross-block sum by the last block: out[k] = sum over b < nblk of partials[b stride + k],
-// k < m, in a fixed order.  Each thread accumulates its strided share as pairs (partials
-// enter by the bit split: no FP64 conversions), then block_sum_pairs.  red: as there.
+// Cross-block sums by the last block: out[k] = sum over b < nblk of partials[b stride + k],
+// k < m, in a fixed order.  Warp w takes k = w, w + nwarps, ...; its lanes stride over the
+// blocks with all their loads in flight (16 per lane and pass), summing as pairs (partials
+// enter by the bit split: no FP64 conversions; the padding zeros add exactly), then a
+// fixed shuffle tree.  Called by every thread of one block; ends with a barrier.
 __device__ inline void reduce_partials(const double* partials, int nblk, int stride, int m,
-                                       double* out, double* red) {
-  block_sum_pairs(
-      [&](int k) {
-        F2 a = {0.f, 0.f};
-        for (int b = threadIdx.x; b < nblk; b += blockDim.x)
-          a = df_add(a, df_split(__ldcg(partials + (size_t)b * stride + k)));
-        return a;
-      },
-      m, red, out);
+                                       double* out) {
+  constexpr int kPer = 16;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = warp; k < m; k += nw) {
+    F2 a = {0.f, 0.f};
+    for (int b0 = 0; b0 < nblk; b0 += 32 * kPer) {
+      double v[kPer];
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int b = b0 + lane + 32 * j;
+        v[j] = b < nblk ? __ldcg(partials + (size_t)b * stride + k) : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) a = df_add(a, df_split(v[j]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const F2 u = {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+      a = df_add(a, u);
+    }
+    if (lane == 0) out[k] = df_to(a);
+  }
   __syncthreads();
 }
 

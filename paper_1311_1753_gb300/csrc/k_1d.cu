@@ -1070,7 +1070,7 @@ __device__ __forceinline__ void events_1d_block(
   block_sum_pairs([&](int k) -> F2 { return k == 0 ? acc : gacc[(k - 1) * bd]; }, m, red,
                   partials + (size_t)vb * stride_p);
   if (!arrive_last_of(counter, (unsigned)vgrid, last)) return;
-  reduce_partials(partials, vgrid, stride_p, m, result, red);
+  reduce_partials(partials, vgrid, stride_p, m, result);
   if (tid == 0) *counter = 0u;
 }
 
@@ -1084,7 +1084,7 @@ __global__ void __launch_bounds__(kThreads1D) k_events_1d(
   __shared__ Program P;
   __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
   __shared__ F2 rf[kMaxLeaf * kLeafRec + kMaxCoef];
-  __shared__ double red[(kThreads1D / 32) * (1 + kMaxFree1D)];  // >= 32
+  __shared__ double red[(kThreads1D / 32) * (1 + kMaxFree1D)];
   __shared__ int last;
   __shared__ F2 tay_t[(kTayDeg + 1) * 2 * kThreads1D];
   load_df_tables();
@@ -1304,7 +1304,7 @@ __global__ void __launch_bounds__(kThreads1D) k_events_logsum(
   block_sum_pairs([&](int k) -> F2 { return k == 0 ? val : gsh[(k - 1) * bd + tid]; }, m, red,
                   partials + (size_t)blockIdx.x * stride_p);
   if (!arrive_last_of(counter, gridDim.x, &last)) return;
-  reduce_partials(partials, gridDim.x, stride_p, m, result, red);
+  reduce_partials(partials, gridDim.x, stride_p, m, result);
   if (tid == 0) *counter = 0u;
 }
 
@@ -1408,7 +1408,7 @@ __global__ void __launch_bounds__(kThreads1D) k_conv_sum(const ConvDesc* __restr
     }
   }
   if (!arrive_last_of(cd.counter, gridDim.x, &last)) return;
-  reduce_partials(cd.partials, L + 1, nq, nq, sums, red);
+  reduce_partials(cd.partials, L + 1, nq, nq, sums);
   __syncthreads();
   if (tid == 0) {
     double* r = derived + (size_t)cd.slot * kLeafRec;
@@ -1481,7 +1481,7 @@ __global__ void __launch_bounds__(kThreads1D) k_gnorm(const GNormDesc* __restric
   block_sum_pairs([&](int q) -> F2 { return tr[q]; }, nq, red,
                   gd.partials + (size_t)blockIdx.x * stride);
   if (!arrive_last_of(gd.counter, gridDim.x, &last)) return;
-  reduce_partials(gd.partials, gridDim.x, stride, nq, sums, red);
+  reduce_partials(gd.partials, gridDim.x, stride, nq, sums);
   __syncthreads();
   if (tid == 0) {
     double* r = derived + (size_t)gd.slot * kLeafRec;
@@ -1549,7 +1549,7 @@ __global__ void __launch_bounds__(kThreads1D) k_tick_events_1d(const TickItem* _
   __shared__ Program Ps;
   __shared__ double rec[kMaxLeaf * kLeafRec + kMaxCoef];
   __shared__ F2 rf[kMaxLeaf * kLeafRec + kMaxCoef];
-  __shared__ double red[(kThreads1D / 32) * (1 + kMaxFree1D)];  // >= 32
+  __shared__ double red[(kThreads1D / 32) * (1 + kMaxFree1D)];
   __shared__ int last;
   load_df_tables();  // visible after tick_item's first barrier
   int cur = -1;

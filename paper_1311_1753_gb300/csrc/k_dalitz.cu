@@ -542,7 +542,7 @@ struct DzShared {
   ResK rk[kMaxRes];
   ResKf rkf[kMaxRes];
   DzC<T> C;
-  double red[(kThreads / 32) * (1 + 4 * kMaxRes)];  // >= 32: also reduce_partials' scratch
+  double red[(kThreads / 32) * (1 + 4 * kMaxRes)];  // block_sum_pairs scratch
   double tot[1 + 4 * kMaxRes];
   double logN;
   double gv[2 * (kMaxRes + 1)];  // v_k = sum_s G_ks c_s (Gram normalisation), re/im
@@ -771,7 +771,7 @@ __device__ __forceinline__ void dalitz_stream_block(
                   partials + (size_t)vb * stride_p);
   if (!arrive_last_of(counter, (unsigned)vgrid, &sh.last)) return;
   double* tot = sh.tot;
-  reduce_partials(partials, vgrid, stride_p, m, tot, red);
+  reduce_partials(partials, vgrid, stride_p, m, tot);
   __syncthreads();
   if (METRIC == METRIC_NORM) {
     const double dA = D.hx * D.hy;
@@ -1354,36 +1354,6 @@ __device__ void tddp_norm_block(const TddpPlan& T, const double* th, const doubl
   __syncthreads();
 }
 
-// Cross-block sums by the last block: out[k] = sum over b < nblk of partials[b stride + k],
-// k < m.  Warp w takes k = w, w + nwarps, ...; its lanes stride over the blocks with all
-// their loads in flight (a load that waits for the previous one costs a full L2 round
-// trip), pair sums (the padding zeros add exactly), then a fixed shuffle tree.
-__device__ inline void reduce_partials_warps(const double* partials, int nblk, int stride, int m,
-                                             double* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  constexpr int kPer = 16;  // loads per lane in flight (456 blocks: one pass)
-  for (int k = warp; k < m; k += nw) {
-    F2 a = {0.f, 0.f};
-    for (int b0 = 0; b0 < nblk; b0 += 32 * kPer) {
-      double v[kPer];
-#pragma unroll
-      for (int j = 0; j < kPer; ++j) {
-        const int b = b0 + lane + 32 * j;
-        v[j] = b < nblk ? __ldcg(partials + (size_t)b * stride + k) : 0.0;
-      }
-#pragma unroll
-      for (int j = 0; j < kPer; ++j) a = df_add(a, df_split(v[j]));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const F2 u = {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
-      a = df_add(a, u);
-    }
-    if (lane == 0) out[k] = df_to(a);
-  }
-  __syncthreads();
-}
-
 // The event pass: -log(I/N) summed (or stored per event) with the gradient; per-thread
 // gradient sums in shared memory (nfree x blockDim pairs).  The amplitude sums A, B and
 // the coefficient gradient (multiply-adds of cached amplitudes) run in double-float pairs
@@ -1506,7 +1476,7 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   block_sum_pairs([&](int k) -> F2 { return k == 0 ? df_split(acc.get()) : gsh[(k - 1) * bd + tid]; },
                   m, red, partials + (size_t)blockIdx.x * stride);
   if (!arrive_last_of(counter, gridDim.x, &last)) return;
-  reduce_partials_warps(partials, gridDim.x, stride, m, result);
+  reduce_partials(partials, gridDim.x, stride, m, result);
   tddp_norm_block(T, th, gram, Nsh, vec, part, kd, G);
   if (tid == 0) {
     result[0] += (double)n * log(Nsh[0]);
