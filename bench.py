@@ -43,7 +43,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # 728.7 + 80.2 + 2 x 211.9; profiles/k_events_1d_voigt_1e7.md).  DRAM traffic of one
 # launch from the same capture (80.41 MB read + 5.65 MB written).
 FP32_FLOPS_PER_EVENT = {"voigt_grad": 1232.7}
-TRAFFIC_PER_LAUNCH = {"voigt_grad": 86.06e6}
+TRAFFIC_PER_LAUNCH = {"voigt_grad": 85.99e6}
 # Context: the same pass in FP64 operations of the method (FMA = 2, add/mul = 1, each
 # exp, log, sqrt or division = 1), counted from the source: w(z) by one Weideman series
 # (N = 40: 305) and its degree-5 expansion per chunk of 24 events (recurrence ~40 per
