@@ -1005,3 +1005,41 @@ def test_tddp_gradient_fd():
     p = d.p
     free = [i for i in range(len(p)) if i % 4 >= 2 and i < 32] + [32, 33, 34, 35]
     _fd_check(lambda q: d.nll_t(s12, s13, t, sigt, p=q, grad=True), p, free, rel=2e-6)
+
+
+def test_tddp_norm_is_grid_sum_of_time_integrals():
+    """N(theta) = sum over the inside cell centres of dA x the integral over all t of the
+    intensity: per cell the integral of the unsmeared mixing formula over t >= 0 by
+    quadrature (Gaussian smearing keeps the integral), with large x and y so that every
+    mixing term (cosh, cos, sinh, sin with A and the CP-conjugate B) weighs in."""
+    tau, x, y = 0.41, 0.2, 0.15
+    d, spec = _tddp_model(nbx=10, nby=10, tau=tau, x=x, y=y)
+    N = d.norm_t()
+    x0, x1, y0, y1 = d.box()
+    hx, hy = (x1 - x0) / 10, (y1 - y0) / 10
+    k = spec["kin"]
+    msum = k["M"] ** 2 + k["m1"] ** 2 + k["m2"] ** 2 + k["m3"] ** 2
+    G = 1 / tau
+    ref, ncell = 0.0, 0
+    for i in range(10):
+        for j in range(10):
+            s12, s13 = x0 + (i + 0.5) * hx, y0 + (j + 0.5) * hy
+            if not d.inside([s12], [s13])[0]:
+                continue
+            ncell += 1
+            s23 = msum - s12 - s13
+            A = 1 + sum((r["re"] + 1j * r["im"]) * d.amp(q, [s12], [s13])[0]
+                        for q, r in enumerate(spec["resonances"]))
+            B = 1 + sum((r["re"] + 1j * r["im"]) * d.amp(q, [s12], [s23])[0]
+                        for q, r in enumerate(spec["resonances"]))
+            aa, bb, xab = abs(A) ** 2, abs(B) ** 2, np.conj(A) * B
+
+            def unsmeared(u):
+                # e^{-Gu} cosh(yGu), e^{-Gu} sinh(yGu) as sums of decaying exponentials
+                e1, e2, e = math.exp(-G * (1 - y) * u), math.exp(-G * (1 + y) * u), math.exp(-G * u)
+                return (0.5 * (aa + bb) * 0.5 * (e1 + e2) + 0.5 * (aa - bb) * e * math.cos(x * G * u)
+                        + xab.real * 0.5 * (e1 - e2) - xab.imag * e * math.sin(x * G * u))
+            ref += hx * hy * integrate.quad(unsmeared, 0, np.inf, epsabs=0, epsrel=1e-13,
+                                            limit=200)[0]
+    assert ncell > 30
+    assert abs(N / ref - 1) < 1e-10, (N, ref)
