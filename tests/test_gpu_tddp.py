@@ -24,7 +24,7 @@ def gf():
     return _gf
 
 
-def _models(gf, nb=64):
+def _models(gf, nb=64, time=TIME):
     k = SPEC["kin"]
     d = oracle.Tddp(k["M"], k["m1"], k["m2"], k["m3"], k["R"], nb, nb)
     ctx = gf.Context()
@@ -42,8 +42,8 @@ def _models(gf, nb=64):
         idx = [d.param(r[f]) for f in ("m0", "g0", "re", "im")]
         d.resonance(r["channel"], r["spin"], *idx)
     tp = [ctx.parameter(nm, v, 1e-3, 1e-3 if nm in ("tau", "scale") else -1.0,
-                        5.0 if nm in ("tau", "scale") else 1.0) for nm, v in TIME.items()]
-    d.time_params(*[d.param(v) for v in TIME.values()])
+                        5.0 if nm in ("tau", "scale") else 1.0) for nm, v in time.items()]
+    d.time_params(*[d.param(v) for v in time.values()])
     root = ctx.tddp(o12, o13, ot, osg, k, res, *tp)
     ctx.set_norm_grid(root, nb, nb)
     return ctx, root, [o12, o13, ot, osg], d, np.array(ctx.free_params())
@@ -153,3 +153,23 @@ def test_tddp_large_and_update(gf):
         with pytest.raises(gf.GFError):
             ctx.update_data(bad)
         assert np.array_equal(ctx.logpdf(th), lg2)
+
+
+def test_tddp_parity_strong_mixing(gf):
+    """x = 0.2, y = 0.15, sigma scale 0.6: every mixing term (cosh, cos, sinh, sin) and the
+    reflection of the smeared exponentials weighs in; per-event log P, NLL and gradient
+    against the oracle."""
+    ctx, root, obs, d, free = _models(gf, time=dict(tau=0.41, x=0.2, y=0.15, scale=0.6))
+    cols = _events(d, 4099, seed=21)
+    ctx.set_data(root, obs, cols)
+    p = d.p
+    lg = ctx.logpdf(p[free])
+    lo_ = np.log(d.intensity_t(*cols, p=p)) - np.log(d.norm_t(p=p))
+    kap = _kappa(d, cols, p)
+    assert np.all(np.abs(lg - lo_) <= 1e-12 * kap * np.maximum(1.0, np.abs(lo_))), \
+        np.max(np.abs(lg - lo_) / kap)
+    f, g = ctx.nll_grad(p[free])
+    fo, go = d.nll_t(*cols, p=p, grad=True)
+    assert abs(f - fo) <= 1e-9 * abs(fo)
+    scale = np.abs(go[free]).max()
+    assert np.all(np.abs(g - go[free]) <= 1e-9 * np.maximum(np.abs(go[free]), 1e-3 * scale)), (g, go[free])
