@@ -44,6 +44,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # launch from the same capture (80.41 MB read + 5.65 MB written).
 FP32_FLOPS_PER_EVENT = {"voigt_grad": 1232.7}
 TRAFFIC_PER_LAUNCH = {"voigt_grad": 85.99e6}
+# the headline workload's name, shared by both arms' JSON lines
+VOIGT_WORKLOAD = ("1D composite: Voigtian (mu,sigma,Gamma) + threshold (c) with fraction f, "
+                  "10^7 FP64 events, 2 x 10,000-bin grid normalisation")
 # Context: the same pass in FP64 operations of the method (FMA = 2, add/mul = 1, each
 # exp, log, sqrt or division = 1), counted from the source: w(z) by one Weideman series
 # (N = 40: 305) and its degree-5 expansion per chunk of 24 events (recurrence ~40 per
@@ -292,12 +295,13 @@ def main():
                 rate_reps.append(el)
         tot = sum(rate_reps)
         value = S * args.steps / tot
-        out = {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": 0,
+        out = {"impl": "reference", "metric": metric, "value": value, "unit": unit,
+               "n_gpus": args.gpus,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                "data": "synthetic",
-               "config": {"workload": "1D composite Voigtian + threshold, FP64, NLL+grad",
-                          "events_per_step": S, "full_workload_events": 10_000_000},
+               "config": {"workload": VOIGT_WORKLOAD, "events": 10_000_000, "free_params": 5,
+                          "sample_events_per_step": S, "parallelism": "host cores (oracle)"},
                "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
                                 "sample": f"{S} events of the 10^7-event workload per step"},
                "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
@@ -341,7 +345,7 @@ def main():
         n = 10_000_000
         ctx, root, obs, cols, th0 = voigt_workload(gf, n, seed, gf.GF_FP64)
         flops_ev = FP32_FLOPS_PER_EVENT["voigt_grad"]
-        wl = "1D composite: Voigtian (mu,sigma,Gamma) + threshold (c) with fraction f, 10^7 FP64 events, 2 x 10,000-bin grid normalisation"
+        wl = VOIGT_WORKLOAD
     elif args.workload == "exp":
         n = 100_000
         ctx, root, obs, cols, th0 = exp_workload(gf, n, synth.SEED_EXP + rank, gf.GF_FP64)
