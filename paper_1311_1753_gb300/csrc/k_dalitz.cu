@@ -1357,9 +1357,9 @@ __device__ void tddp_norm_block(const TddpPlan& T, const double* th, const doubl
 // The event pass: -log(I/N) summed (or stored per event) with the gradient; per-thread
 // gradient sums in shared memory (nfree x blockDim pairs).  The amplitude sums A, B and
 // the coefficient gradient (multiply-adds of cached amplitudes) run in double-float pairs
-// on the FP32 pipe, the time dependence in FP64.  N enters the sums only
-// through n log N and n dN/N, so the last block forms it after the events; a block that
-// stores log P per event forms it first.
+// on the FP32 pipe, the time dependence in FP64.  N enters the sums only through n log N
+// and n dN/N, so the last block forms it after the events; a block that stores log P per
+// event forms it first.
 template <bool G, bool STORE>
 __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
     const __grid_constant__ TddpPlan T, const __grid_constant__ WeidCoef W,
