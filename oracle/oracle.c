@@ -30,6 +30,16 @@
  *    barrier factors at the resonance vertex and Zemach spin factors; P = |A|^2,
  *    normalised on a cell-centre grid over the kinematic region.
  *
+ *  - Later parts, each in its own section below with its reading: binned metrics,
+ *    the lattice ConvolutionPdf and the relativistic Breit-Wigner line shape, MappedPdf
+ *    and CompositePdf, the time-dependent (mixing) Dalitz model.
+ *
+ * Pins (tests/test_oracle_pins.py): closed forms, library routines, four-vector
+ * kinematics, quadrature and finite differences for every function.  Parity unpinned:
+ * the physics conventions of the Dalitz and mixing readings (barrier radius, Zemach
+ * factors, the CP-conjugate amplitude, q/p = 1) -- the paper prints no worked number
+ * that fixes them, so the oracle and the CUDA path share the reading.
+ *
  * Faddeeva function: trapezoidal rule on the integral representation
  *   w(z) = (i/pi) Int e^{-t^2}/(z - t) dt   (Im z > 0)
  * with the residue correction for the pole of the integrand (the method of Matta &
