@@ -165,8 +165,10 @@ int gf_pdf_dalitz(gf_ctx* ctx, int obs12, int obs13, const gf_dalitz_kin* kin, i
  * sin(x t/tau)} (t >= 0) each convolved with a Gaussian of width scale * sigma_t.
  * Normalised over the Dalitz grid (gf_set_norm_grid; default 256 x 256 cells) and all t;
  * conditional on sigma_t.  tau, x, y, scale are parameter ids.  The data set holds the
- * columns s12, s13, t, sigma_t in this order (sigma_t > 0).  Evaluated in FP64 in both
- * precision modes. */
+ * columns s12, s13, t, sigma_t in this order (sigma_t > 0; every event inside the
+ * kinematic region, else GF_EINVAL from gf_set_data / gf_update_data).  FP64-accurate in
+ * both precision modes: the time dependence in FP64, the amplitude algebra in
+ * double-float pairs. */
 int gf_pdf_tddp(gf_ctx* ctx, int obs12, int obs13, int obs_t, int obs_sigt,
                 const gf_dalitz_kin* kin, int nres, const gf_resonance* res, int tau, int x,
                 int y, int scale, int* node);
