@@ -65,19 +65,37 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling during the timed region: every 100 ms, started before the region
+    (its first line marks that the sampler runs); lines written before the region are
+    left out of the summary when the region has lines of its own."""
 
     def __init__(self, index=0):
         self.path = tempfile.mktemp(suffix=".csv")
+        self.n0 = 0
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader",
-                                       "-i", str(index), "-lms", "200"],
+                                       "-i", str(index), "-lms", "100"],
                                       stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+            return
+        t_end = time.perf_counter() + 3.0
+        while time.perf_counter() < t_end and self.p.poll() is None:
+            n = self._lines()
+            if n > 0:
+                self.n0 = n
+                break
+            time.sleep(0.02)
+
+    def _lines(self):
+        try:
+            with open(self.path) as fh:
+                return sum(1 for line in fh if line.count(",") >= 8)
+        except OSError:
+            return 0
 
     def stop(self):
         if self.p is None:
@@ -92,6 +110,8 @@ class Clocks:
             f = [x.strip() for x in line.split(",")]
             if len(f) >= 9:
                 rows.append(f)
+        if len(rows) > self.n0:
+            rows = rows[self.n0:]
         if not rows:
             return None
         sm = [float(r[1].split()[0]) for r in rows if r[1].split()[0].replace(".", "").isdigit()]
