@@ -435,6 +435,68 @@ def test_breit_wigner_at_pole():
         assert abs(a / S - target) < 1e-12 * abs(target)
 
 
+def _barrier_hankel(L, x):
+    """Blatt-Weisskopf barrier polynomial from the outgoing spherical wave:
+    B_L = x^{2L} |x h_L(x)|^2 with h_L = j_L + i y_L (scipy's spherical Bessel
+    functions), x = qR.  It is 1, 1 + x^2, 9 + 3x^2 + x^4 for L = 0, 1, 2 (von Hippel &
+    Quigg 1972), here obtained without writing the polynomials."""
+    h = special.spherical_jn(L, x) + 1j * special.spherical_yn(L, x)
+    return x ** (2 * L) * np.abs(x * h) ** 2
+
+
+def _two_body_q(m, ma, mb):
+    """Momentum of a in the rest frame of mass m decaying to a, b (explicit energies)."""
+    e = (m * m + ma * ma - mb * mb) / (2 * m)
+    return math.sqrt(e * e - ma * ma)
+
+
+@pytest.mark.parametrize("ch", [0, 1, 2])
+@pytest.mark.parametrize("L", [0, 1, 2])
+def test_breit_wigner_off_the_pole_vs_four_vectors(ch, L):
+    """A_r = F_L S_L BW off the pole, for every channel and spin, against an independent
+    construction: the pair's mass, the break-up momentum q and the bachelor momentum k
+    from explicit four-vectors boosted into the pair's rest frame; q0 from the two-body
+    energies at m0; the barrier factors from spherical Hankel functions; the running
+    width Gamma(m) = Gamma0 (q/q0)^{2L+1} (m0/m) B_L(z0)/B_L(z); S_L from k and q.  A
+    dropped power of q/q0 or a changed barrier polynomial moves A by far more than the
+    tolerance at these points (|m - m0| up to ~1 GeV)."""
+    k = SPEC["kin"]
+    R = k["R"]
+    names = [(1, 2, 3), (1, 3, 2), (2, 3, 1)]
+    ia, ib, ic = names[ch]
+    masses = {1: k["m1"], 2: k["m2"], 3: k["m3"]}
+    ma, mb = masses[ia], masses[ib]
+    rng = np.random.Generator(np.random.PCG64(900 + 10 * ch + L))
+    for m0, g0 in ((0.77, 0.15), (1.27, 0.185), (0.98, 0.05)):
+        d = oracle.Dalitz(k["M"], k["m1"], k["m2"], k["m3"], R)
+        d.resonance(ch, L, d.param(m0), d.param(g0), d.param(1.0), d.param(0.0))
+        x0, x1, y0, y1 = d.box()
+        n = 0
+        while n < 60:
+            s12, s13 = rng.uniform(x0, x1), rng.uniform(y0, y1)
+            fv = _fourvectors(s12, s13)
+            if fv is None:
+                continue
+            n += 1
+            P = dict(zip((1, 2, 3), fv))
+            frame = P[ia] + P[ib]
+            m = math.sqrt(_mdot(frame, frame))
+            qa = _boost_to_rest(P[ia], frame)[1:]
+            kc = _boost_to_rest(P[ic], frame)[1:]
+            q = math.sqrt(qa @ qa)
+            q0 = _two_body_q(m0, ma, mb)
+            B, B0 = _barrier_hankel(L, q * R), _barrier_hankel(L, q0 * R)
+            gam = g0 * (q / q0) ** (2 * L + 1) * (m0 / m) * B0 / B
+            bw = 1.0 / (m0 * m0 - m * m - 1j * m0 * gam)
+            kq, kk, qq = kc @ qa, kc @ kc, qa @ qa
+            S = (1.0, 4 * kq, 16 * (kq * kq - kk * qq / 3))[L]
+            Smax = (1.0, 4 * math.sqrt(kk * qq), 16 * kk * qq)[L]
+            F = math.sqrt(B0 / B)
+            want = F * S * bw
+            got = d.amp(0, np.array([s12]), np.array([s13]))[0]
+            assert abs(got - want) <= 1e-10 * F * Smax * abs(bw), (m0, s12, s13, got, want)
+
+
 def test_dalitz_only_nonresonant_gives_log_area():
     d = om.dalitz_from_spec(SPEC)
     p = d.p.copy()
@@ -783,11 +845,13 @@ def test_relbw_value_at_the_pole_and_threshold():
     assert v[1] < 1e-6 * v[0] and v[2] == 0.0
 
 
-def test_relbw_running_width_vs_two_body_momentum():
-    """Gamma(m)/Gamma0 from the shape (f D/m) against (q/q0)^3 (m0/m) F_1^2 with q the
-    pion momentum computed from explicit two-body energies."""
+@pytest.mark.parametrize("L", [0, 1, 2])
+def test_relbw_running_width_vs_two_body_momentum(L):
+    """Gamma(m)/Gamma0 from the shape (f D/m) against (q/q0)^{2L+1} (m0/m) B_L(z0)/B_L(z)
+    with q the pion momentum computed from explicit two-body energies and the barrier
+    polynomials from spherical Hankel functions."""
     dm0, g0 = 0.14543, 8.3e-5
-    m = _relbw_model(0.139, 0.16, dm0, g0)
+    m = _relbw_model(0.139, 0.16, dm0, g0, L=L)
     xs = np.array([0.1420, 0.1450, 0.1500, 0.1580])
     f = m.leaf_shape(0, xs)
     M, M0 = xs + D0_MASS, dm0 + D0_MASS
@@ -795,8 +859,9 @@ def test_relbw_running_width_vs_two_body_momentum():
     def q(mm):
         e = (mm * mm + PI_MASS ** 2 - D0_MASS ** 2) / (2 * mm)
         return np.sqrt(e * e - PI_MASS ** 2)
-    z, z0 = (q(M) * 1.5) ** 2, (q(M0) * 1.5) ** 2
-    G = g0 * (q(M) / q(M0)) ** 3 * (M0 / M) * (1 + z0) / (1 + z)
+    B = _barrier_hankel(L, q(M) * 1.5)
+    B0 = _barrier_hankel(L, q(M0) * 1.5)
+    G = g0 * (q(M) / q(M0)) ** (2 * L + 1) * (M0 / M) * B0 / B
     D = (M0 ** 2 - M ** 2) ** 2 + M0 ** 2 * G ** 2
     assert np.max(np.abs(f * D / (M * G) - 1)) < 1e-12
 
