@@ -40,10 +40,16 @@ extern "C" {
 #define GF_ESTATE (-7)      /* call out of order (e.g. evaluate before gf_set_data)  */
 
 /* ---- precision modes -------------------------------------------------------------- */
-#define GF_FP64 0   /* every per-event and per-cell operation in FP64                   */
-#define GF_MIXED 1  /* per-event amplitude arithmetic in FP32; FP64 for the log-sum      */
-                    /* across threads and blocks and for the normalisation integrals   */
-                    /* (1D trees evaluate in FP64 in either mode)                      */
+/* GF_FP64: FP64-accurate results.  On GB300 the per-event and per-cell arithmetic runs
+ *   as double-float (pairs of FP32 values, 48-bit significands, on the FP32 pipe), with
+ *   exact FP64 differences of data and constants and an FP64 re-evaluation of events
+ *   outside the float exponent range; per event it meets 1e-12 relative to the FP64
+ *   definition, the NLL 1e-9 relative (the library's tests).
+ * GF_MIXED: per-event PDF and amplitude arithmetic in FP32; the log-sum across threads
+ *   and blocks, the normalisation integrals and (1D trees) the Faddeeva function of the
+ *   Voigtian stay FP64-accurate.  Results carry FP32 rounding (stated by the tests). */
+#define GF_FP64 0
+#define GF_MIXED 1
 
 typedef struct gf_ctx gf_ctx;
 typedef struct gf_dataset gf_dataset;
@@ -353,19 +359,25 @@ int gf_set_graphs(gf_ctx* ctx, int enable);
  * memory; no gf_set_data is needed), over caller-owned device columns, and allocates
  * nothing: its working buffers (theta, normalisation records, block partials, counters,
  * the compiled program) are one static device array of 440 KiB compiled into the library,
- * which every GPU that loads the library holds until the process exits.
+ * which every GPU that loads the library holds until the process exits.  The array is made
+ * resident when the first context is created on a device (gf_create looks up its address
+ * there), so the footprint does not grow at the first call.
  *   obs[k], dev_cols[k]: observable id and device column of n doubles (16-byte aligned);
  *   theta: host array of the free parameters (gf_free_params order);
  *   nll_dev: one double in device memory, written when the context's stream reaches it
  *            (the call returns after queueing; synchronise the stream before reading).
  * Limits: at most 256 parameters and 64 observables in the context, 24 free parameters,
- * 262,144 normalisation-grid bins in total; beyond them the call returns GF_EINVAL with a
- * message (gf_last_error).  Dalitz nodes are not accepted.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current: make that first call before any stream capture.  Every call
- * reuses the same array, which keeps the last call's contents (the call clears what must
- * start at zero): calls whose GPU work overlaps -- other streams, other host threads --
- * race on it and must be serialised by the caller. */
+ * 262,144 normalisation-grid bins in total, 32 instructions of the compiled tree; beyond
+ * them, or for a node other than the exponential, Gaussian, Voigtian, threshold and
+ * polynomial leaves, AddPdf and ProdPdf, the call returns GF_EINVAL with a message
+ * (gf_last_error).
+ * Each call looks up the array's device address (cudaGetSymbolAddress) with the context's
+ * device current and stages theta and the compiled program from its own stack frame
+ * (pageable host memory); it therefore returns GF_EINVAL, queueing nothing, while the
+ * context's stream is capturing a graph.  Every call reuses the same array, which keeps
+ * the last call's contents (the call clears what must start at zero): calls whose GPU
+ * work overlaps -- other streams, other host threads -- race on it and must be
+ * serialised by the caller. */
 int gf_nll_noalloc(gf_ctx* ctx, int root, int nobs, const int* obs, int64_t n,
                    const double* const* dev_cols, const double* theta, double* nll_dev);
 

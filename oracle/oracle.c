@@ -19,7 +19,7 @@
  * and products ("ProdPdf", Sec. 3, Listing 2) multiply normalised components of
  * distinct observables.  Sums are compensated (Neumaier) and in fixed event order.
  *
- * Readings where the paper is silent (each one is listed in the design doc):
+ * Readings where the paper is silent:
  *  - Voigtian = Gaussian (std sigma) convolved with a Breit-Wigner of FWHM Gamma,
  *    V(x) = Re w(z) / (sigma sqrt(2 pi)),  z = (x - mu + i Gamma/2) / (sigma sqrt 2).
  *  - Leaves without a closed-form integral on a finite range (Voigtian, threshold)

@@ -153,17 +153,25 @@ static void free_dev(gf_ctx* ctx) {
 extern "C" {
 
 namespace {
-// Kernel attributes are set once per device, with that device current, before any of the
-// context's work can be captured into a graph.
+// Tables and kernel attributes are set up once per device, with that device current,
+// before any of the context's work can be captured into a graph.  A failed upload or
+// attribute call fails the context's creation (the kernels would otherwise read zero
+// tables).
 std::mutex g_prep_mu;
 bool g_prepared[64] = {false};
-void prepare_device(int device) {
+cudaError_t prepare_device(int device) {
   std::lock_guard<std::mutex> lk(g_prep_mu);
-  if (device < 0 || device >= 64 || g_prepared[device]) return;
-  gfi::prepare_kernels_1d();
-  gfi::prepare_kernels_dalitz();
-  cudaGetLastError();
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  if (g_prepared[device]) return cudaSuccess;
+  cudaError_t e = gfi::prepare_kernels_1d();
+  if (e == cudaSuccess) e = gfi::prepare_kernels_dalitz();
+  if (e == cudaSuccess) e = gfi::noalloc_preload();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
   g_prepared[device] = true;
+  return cudaSuccess;
 }
 }  // namespace
 
@@ -189,7 +197,12 @@ int gf_create(gf_ctx** out, int device, int precision) {
   ctx->stream = ctx->own_stream;
   cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
   weideman();
-  prepare_device(device);
+  const cudaError_t pe = prepare_device(device);
+  if (pe != cudaSuccess) {
+    cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+    return GF_ECUDA;
+  }
   *out = ctx;
   return GF_OK;
 }

@@ -236,7 +236,7 @@ __device__ __forceinline__ void load_df_tables() {
   }
 }
 
-static inline void upload_df_tables() {
+static inline cudaError_t upload_df_tables() {
   F2 e[kTab], g[kTab];
   for (int j = 0; j < kTab; ++j) {
     const double ev = std::exp2(j / (double)kTab);
@@ -247,8 +247,9 @@ static inline void upload_df_tables() {
     g[j].hi = (float)gv;
     g[j].lo = (float)(gv - (double)g[j].hi);
   }
-  cudaMemcpyToSymbol(g_exp_tab, e, sizeof(e));
-  cudaMemcpyToSymbol(g_log_tab, g, sizeof(g));
+  cudaError_t err = cudaMemcpyToSymbol(g_exp_tab, e, sizeof(e));
+  if (err == cudaSuccess) err = cudaMemcpyToSymbol(g_log_tab, g, sizeof(g));
+  return err;
 }
 
 // ---- natural logarithm -----------------------------------------------------------------

@@ -1664,19 +1664,19 @@ cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCo
 
 // Opt the gradient kernels in to > 48 KB of dynamic shared memory on the current device.
 // Called once per device when a context is created: never inside a stream capture.
-void prepare_kernels_1d() {
-  upload_df_tables();
-  cudaFuncSetAttribute(k_conv_points, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_gnorm, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-
-  cudaFuncSetAttribute(k_events_1d<true, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       200 * 1024);
-  cudaFuncSetAttribute(k_events_1d<true, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       200 * 1024);
-  cudaFuncSetAttribute(k_events_1d<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       200 * 1024);
-  cudaFuncSetAttribute(k_tick_events_1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       200 * 1024);
+cudaError_t prepare_kernels_1d() {
+  cudaError_t e = upload_df_tables();
+  auto attr = [&](const void* f) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  };
+  attr((const void*)k_conv_points);
+  attr((const void*)k_gnorm);
+  attr((const void*)k_events_1d<true, 0, 0>);
+  attr((const void*)k_events_1d<true, 0, 1>);
+  attr((const void*)k_events_1d<true, 2>);
+  attr((const void*)k_tick_events_1d);
+  return e;
 }
 
 int events_logsum_blocks_per_sm(const Program& P) {

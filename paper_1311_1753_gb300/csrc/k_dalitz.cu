@@ -1019,23 +1019,21 @@ cudaError_t launch_tick_dalitz(bool mixed, const TickItem* items, int nfits, int
 
 // Opt the gradient kernels in to > 48 KB of dynamic shared memory on the current device.
 // Called once per device when a context is created: never inside a stream capture.
-void prepare_kernels_dalitz() {
-  upload_df_tables();
+cudaError_t prepare_kernels_dalitz() {
+  cudaError_t e = upload_df_tables();
   const int lim = 160 * 1024;
-  cudaFuncSetAttribute(k_dalitz_stream<float, true, METRIC_NLL, false>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_dalitz_stream<float, true, METRIC_NORM, false>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_dalitz_stream<DF, true, METRIC_NLL, false>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_dalitz_stream<DF, true, METRIC_NORM, false>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_dalitz_stream<float, true, METRIC_NLL, true>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_dalitz_stream<DF, true, METRIC_NLL, true>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_tick_dalitz<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_tick_dalitz<DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  auto attr = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  };
+  attr((const void*)k_dalitz_stream<float, true, METRIC_NLL, false>);
+  attr((const void*)k_dalitz_stream<float, true, METRIC_NORM, false>);
+  attr((const void*)k_dalitz_stream<DF, true, METRIC_NLL, false>);
+  attr((const void*)k_dalitz_stream<DF, true, METRIC_NORM, false>);
+  attr((const void*)k_dalitz_stream<float, true, METRIC_NLL, true>);
+  attr((const void*)k_dalitz_stream<DF, true, METRIC_NLL, true>);
+  attr((const void*)k_tick_dalitz<float>);
+  attr((const void*)k_tick_dalitz<DF>);
+  return e;
 }
 
 int dalitz_blocks_per_sm(bool mixed, bool grad, bool cached_only, int nfree) {

@@ -10,7 +10,6 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 
 #include "../../include/gf.h"
 #include "ctx.h"
@@ -42,20 +41,17 @@ static __device__ __align__(256) double g_noalloc_scratch[gfi::kNADoubles];
 namespace gfi {
 namespace {
 
-// Device address of the array, looked up once per device with that device current.
-std::mutex g_na_mu;
-double* g_na_ptr[64] = {nullptr};
-
-int scratch_address(int dev, double** out) {
-  if (dev < 0 || dev >= 64) return GF_EINVAL;
-  std::lock_guard<std::mutex> lk(g_na_mu);
-  if (!g_na_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return GF_ECUDA;
-    g_na_ptr[dev] = static_cast<double*>(p);
+// Device address of the array in the current device's context.  Looked up on every call
+// (cheap, allocation-free): a cached address would go stale after a device reset or
+// under another context.
+int scratch_address(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    return GF_ECUDA;
   }
-  *out = g_na_ptr[dev];
+  *out = static_cast<double*>(p);
   return GF_OK;
 }
 
@@ -140,7 +136,8 @@ struct NACompiler {
       return (nd.type == N_EXP || nd.type == N_GAUSS) ? 1 : 0;
     }
     if (nd.type != N_ADD && nd.type != N_PROD) {
-      err = "only 1D trees (no Dalitz node)";
+      err = "unsupported node (exponential, Gaussian, Voigtian, threshold and polynomial "
+            "leaves, AddPdf and ProdPdf only)";
       return -1;
     }
     const int nc = (int)nd.children.size();
@@ -200,6 +197,15 @@ bool acyclic(const gf_ctx* ctx, int id, int depth) {
 }
 
 }  // namespace
+
+// Called when a context is created on a device (that device current): the lookup loads
+// this unit's module, so the array is resident from then on rather than appearing at the
+// first gf_nll_noalloc call.
+cudaError_t noalloc_preload() {
+  void* p = nullptr;
+  return cudaGetSymbolAddress(&p, g_noalloc_scratch);
+}
+
 }  // namespace gfi
 
 using namespace gfi;
@@ -275,13 +281,25 @@ extern "C" int gf_nll_noalloc(gf_ctx* ctx, int root, int nobs, const int* obs, i
     return set_error(ctx, GF_EINVAL,
                      "gf_nll_noalloc: more than 262,144 normalisation-grid bins in total");
 
-  // scratch: the static array's device address on this device (looked up once)
+  // scratch: the static array's device address on this device
   if (cudaSetDevice(ctx->device) != cudaSuccess) {
     cudaGetLastError();
     return set_error(ctx, GF_ECUDA, "gf_nll_noalloc: cudaSetDevice failed");
   }
+  cudaStream_t st = ctx->stream;
+  // theta and the program are staged from this call's stack frame (pageable memory),
+  // which a captured graph could not replay: refuse a capturing stream
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(ctx, GF_ECUDA, "gf_nll_noalloc: cudaStreamIsCapturing failed");
+  }
+  if (cap != cudaStreamCaptureStatusNone)
+    return set_error(ctx, GF_EINVAL,
+                     "gf_nll_noalloc: the context's stream is capturing; this call copies "
+                     "theta and the program from host stack memory and cannot be captured");
   double* base = nullptr;
-  int rc = scratch_address(ctx->device, &base);
+  int rc = scratch_address(&base);
   if (rc) return set_error(ctx, rc, "gf_nll_noalloc: cudaGetSymbolAddress failed");
   double* d_theta = base + kNATheta;
   double* d_derived = base + kNADerived;
@@ -300,7 +318,6 @@ extern "C" int gf_nll_noalloc(gf_ctx* ctx, int root, int nobs, const int* obs, i
   if (nb < 1) nb = 1;
   if (nb > kNAMaxEvBlocks) nb = kNAMaxEvBlocks;
 
-  cudaStream_t st = ctx->stream;
   // theta from the caller's host array (staged by the runtime), counters cleared: the
   // array keeps the previous call's contents
   if (cudaMemcpyAsync(d_theta, theta_all, sizeof(double) * (npar > 0 ? npar : 1),

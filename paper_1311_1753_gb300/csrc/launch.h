@@ -25,7 +25,8 @@ cudaError_t launch_events_1d(const Program& P, const Program* prog, const WeidCo
 // blocks per SM of the event kernel (mix: the AddPdf-of-leaves variant)
 int events_1d_blocks_per_sm(bool grad, size_t smem, bool mix = false);
 int events_logsum_blocks_per_sm(const Program& P);  // the direct log-sum kernel
-void prepare_kernels_1d();
+// table uploads and kernel attributes, once per device (that device current)
+cudaError_t prepare_kernels_1d();
 // ConvolutionPdf tables of one node (after launch_norm_1d; before the event pass):
 // host: the descriptor's sizes, dev: its device copy
 cudaError_t launch_conv(const ConvDesc& host, const ConvDesc* dev, const WeidCoef& W, int nfree,
@@ -42,7 +43,9 @@ cudaError_t sort_by_key_f64(const double* key_in, double* key_out, int32_t* perm
 // out[i] = in[perm[i]]
 cudaError_t launch_gather(const double* in, const int32_t* perm, double* out, int64_t n,
                           cudaStream_t st);
-void prepare_kernels_dalitz();
+cudaError_t prepare_kernels_dalitz();
+// loads the allocation-free entry point's module (its static scratch array)
+cudaError_t noalloc_preload();
 // batched fit-server tick (persistent launches over a work list of TickItems)
 cudaError_t launch_tick_1d(bool norm, const TickItem* items, int nfits, int total,
                            const WeidCoef& W, size_t smem, int grid, cudaStream_t st);
