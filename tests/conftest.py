@@ -11,3 +11,12 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long CPU test")
+
+
+def pytest_terminal_summary(terminalreporter):
+    """The worst per-event parity errors seen in this session (tests/parity.py)."""
+    from tests.parity import WORST
+    if WORST:
+        terminalreporter.write_sep("-", "parity: worst |log P_gpu - log P_orc| and stated errors")
+        for k, v in WORST.items():
+            terminalreporter.write_line(f"{k}: {v:.3e}")

@@ -13,6 +13,8 @@ import oracle
 from oracle import minimise
 from paper_1311_1753_gb300 import synth
 
+from tests.parity import per_event
+
 pytestmark = pytest.mark.gpu
 LO, HI = synth.VOIGT_RANGE
 D0, PIC = 1.86484, 0.13957
@@ -114,7 +116,7 @@ def test_relbw_leaf_parity(gf, n):
         th = np.array([BW[0] * sc, BW[1] * (2 - sc)])
         p = m.p.copy(); p[:2] = th
         lg, lo_ = ctx.logpdf(th), m.logpdf([xs], p)
-        assert np.max(np.abs(lg - lo_)) <= 1e-12 * max(1.0, np.abs(lo_).max())
+        per_event("relbw leaf", lg, lo_)
         f, g = ctx.nll_grad(th)
         fo, go = m.nll([xs], p, grad=True)
         assert abs(f - fo) <= 1e-9 * abs(fo)
@@ -134,7 +136,7 @@ def test_conv_unbinned_parity(gf, model, n):
     for sc in (None, np.array([1.0001, 0.97, 1.02, 1.03, 0.98, 1.05, 0.97, 1.04, 1.01, 0.99])):
         th, p = _theta(ctx, m, free, sc)
         lg, lo_ = ctx.logpdf(th), m.logpdf([xs], p)
-        assert np.max(np.abs(lg - lo_)) <= 1e-12 * max(1.0, np.abs(lo_).max()), model
+        per_event(f"conv {model}", lg, lo_)
         f, g = ctx.nll_grad(th)
         fo, go = m.nll([xs], p, grad=True)
         assert abs(f - fo) <= 1e-9 * abs(fo)

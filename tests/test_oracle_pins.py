@@ -1108,3 +1108,25 @@ def test_tddp_norm_is_grid_sum_of_time_integrals():
                                             limit=200)[0]
     assert ncell > 30
     assert abs(N / ref - 1) < 1e-10, (N, ref)
+
+
+def test_oracle_pool_sums_match_the_single_process_oracle():
+    """The full-size parity tests split the oracle's Dalitz sums over spawned worker
+    processes: the slice sums equal the one-process sums (up to summation order) and the
+    pooled accept-reject draws the same events."""
+    from tests import oracle_pool as op
+    d = om.dalitz_from_spec(SPEC, 64, 64)
+    s12, s13 = _inside_points(d, 1001)
+    p = d.p.copy()
+    p[2::4] *= 1.02
+    f1, g1 = d.nll(s12, s13, p, grad=True)
+    f2, g2 = op.dalitz_nll(SPEC, p, s12, s13, 64, 64, grad=True)
+    assert abs(f2 - f1) <= 1e-12 * abs(f1)
+    assert np.allclose(g2, g1, rtol=1e-11, atol=1e-11 * np.abs(g1).max())
+    P1, k1 = d.intensity(s12, s13, p, kappa=True)
+    P2, k2 = op.dalitz_intensity(SPEC, p, s12, s13, kappa=True)
+    assert np.array_equal(P1, P2) and np.array_equal(k1, k2)
+    a = synth.dalitz_events(500, om.dalitz_accept(om.dalitz_from_spec(SPEC), SPEC["envelope"]), 5,
+                            batch=4096)
+    b = synth.dalitz_events(500, op.dalitz_accept(SPEC), 5, batch=4096)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
