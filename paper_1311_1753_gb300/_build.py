@@ -18,7 +18,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgoofit_gb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["capi.cpp", "fit.cpp", "server.cpp", "k_1d.cu", "k_dalitz.cu", "k_noalloc.cu",
-           "k_sort.cu"]
+           "k_sigbkg.cu", "k_sort.cu"]
 
 
 def _nvcc() -> str:

@@ -165,6 +165,7 @@ cudaError_t prepare_device(int device) {
   if (g_prepared[device]) return cudaSuccess;
   cudaError_t e = gfi::prepare_kernels_1d();
   if (e == cudaSuccess) e = gfi::prepare_kernels_dalitz();
+  if (e == cudaSuccess) e = gfi::prepare_kernels_sigbkg();
   if (e == cudaSuccess) e = gfi::noalloc_preload();
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -988,6 +989,41 @@ static void detect_logsum(Program& P) {
   P.logsum = 1;
 }
 
+// An AddPdf of one Voigtian and one threshold leaf over the same observable (the paper's
+// signal + background line shape, Sec. 4) runs on its own kernel (k_sigbkg.cu).
+static bool detect_sigbkg(const Program& P, SigBkgDesc& D) {
+  if (P.mix != 2 || P.binned) return false;
+  int kv = -1, kt = -1;
+  for (int k = 0; k < 2; ++k) {
+    const Instr& I = P.ins[P.mix_leaf[k]];
+    if (I.kind == L_VOIGT && kv < 0) kv = k;
+    else if (I.kind == L_THRESH && kt < 0) kt = k;
+  }
+  if (kv < 0 || kt < 0) return false;
+  const Instr& V = P.ins[P.mix_leaf[kv]];
+  const Instr& T = P.ins[P.mix_leaf[kt]];
+  const Instr& SV = P.ins[P.mix_scale[kv]];
+  const Instr& ST = P.ins[P.mix_scale[kt]];
+  if (V.obs != T.obs || P.mix_log[kv] || P.mix_log[kt] || V.npar != 3 || T.npar != 3 ||
+      SV.npar != 1 || ST.npar != 1 || P.leaf[V.slot].nbins <= 0 || P.leaf[T.slot].nbins <= 0)
+    return false;
+  D = SigBkgDesc{};
+  D.slot_v = V.slot;
+  D.slot_t = T.slot;
+  D.cslot_v = SV.slot;
+  D.cslot_t = ST.slot;
+  for (int j = 0; j < 3; ++j) {
+    D.gv[j] = V.gidx[j];
+    D.gt[j] = T.gidx[j];
+  }
+  D.fpos_v = SV.gidx[0];
+  D.fpos_t = ST.gidx[0];
+  D.fsgn_v = SV.kind;
+  D.fsgn_t = ST.kind;
+  D.nfree = P.nfree;
+  return true;
+}
+
 // Device tables of every convolution (freed and rebuilt at each compilation).
 static void free_convs(DevState& d) {
   for (void* p : d.conv_bufs) cudaFree(p);
@@ -1154,6 +1190,7 @@ namespace gfi {
 
 int ensure_compiled(gf_ctx* ctx) {
   if (ctx->compiled) return GF_OK;
+  ctx->use_sb = false;
   for (auto& g : ctx->dev.graph)
     if (g) {
       cudaGraphExecDestroy(g);
@@ -1307,6 +1344,8 @@ int ensure_compiled(gf_ctx* ctx) {
     P.bw = d.bw;
     P.bs2 = d.bs2;
     if (ctx->mixture_path && !d.binned) detect_logsum(P);
+    ctx->use_sb = ctx->mixture_path && !d.binned && P.ngrid_blocks > 0 && C.convs.empty() &&
+                  C.gns.empty() && detect_sigbkg(P, ctx->sb);
     // the kernels read the program from device memory (it is too large for parameters);
     // stream-ordered copy, then wait: the next launch may go to another stream
     DevState& dv = ctx->dev;
@@ -1523,6 +1562,8 @@ static int finish_set_data(gf_ctx* ctx) {
     per_sm = dalitz_blocks_per_sm(ctx->precision == GF_MIXED, true, co, ctx->dplan.nfree);
   } else if (ctx->prog.logsum) {
     per_sm = events_logsum_blocks_per_sm(ctx->prog);
+  } else if (ctx->use_sb) {
+    per_sm = std::min(sigbkg_blocks_per_sm(false), sigbkg_blocks_per_sm(true));
   } else {
     per_sm = events_1d_blocks_per_sm(true, events_1d_smem(ctx->prog, true, kThreads1D),
                                      ctx->prog.mix > 0);
@@ -1946,9 +1987,16 @@ static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool capt
     Cols cols{};
     for (int k = 0; k < d.nobs; ++k) cols.c[k] = d.cols[k];
     CK(cudaEventRecordWithFlags(d.evm, ctx->stream, evf));
-    CK(launch_events_1d(ctx->prog, d.prog, W, cols, d.n, d.theta, d.derived, d.partials, d.counters,
-                        d.result, nullptr, nullptr, grad, false, ctx->has_grid ? 0 : 1, d.nblocks,
-                        ctx->stream));
+    if (ctx->use_sb) {
+      const bool mixed = ctx->precision == GF_MIXED && !fp64;
+      CK(launch_sigbkg(ctx->sb, W, d.prog, d.cols[ctx->prog.ins[ctx->prog.mix_leaf[0]].obs], d.n,
+                       d.derived, d.partials, d.counters, d.result, nullptr, nullptr, grad, mixed,
+                       d.nblocks, ctx->stream));
+    } else {
+      CK(launch_events_1d(ctx->prog, d.prog, W, cols, d.n, d.theta, d.derived, d.partials,
+                          d.counters, d.result, nullptr, nullptr, grad, false,
+                          ctx->has_grid ? 0 : 1, d.nblocks, ctx->stream));
+    }
     (*launches)++;
   }
   CK(cudaEventRecordWithFlags(d.ev1, ctx->stream, evf));
@@ -2252,7 +2300,14 @@ static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host)
     }
     Cols cols{};
     for (int k = 0; k < d.nobs; ++k) cols.c[k] = d.cols[k];
-    if (rc == GF_OK) {
+    if (rc == GF_OK && ctx->use_sb) {
+      cudaError_t e = launch_sigbkg(ctx->sb, W, d.prog,
+                                    d.cols[ctx->prog.ins[ctx->prog.mix_leaf[0]].obs], d.n,
+                                    d.derived, d.partials, d.counters, d.result, dst,
+                                    d.sorted ? d.perm : nullptr, false,
+                                    ctx->precision == GF_MIXED, d.nblocks, ctx->stream);
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e, "launch_sigbkg");
+    } else if (rc == GF_OK) {
       cudaError_t e = launch_events_1d(ctx->prog, d.prog, W, cols, d.n, d.theta, d.derived, d.partials,
                                        d.counters, d.result, dst, d.sorted ? d.perm : nullptr,
                                        false, true,

@@ -135,6 +135,8 @@ struct gf_ctx {
   gfi::TddpPlan tplan{};
   bool has_grid = false;
   gfi::Program prog{};
+  bool use_sb = false;       // the program is a signal + background AddPdf (k_sigbkg.cu)
+  gfi::SigBkgDesc sb{};
   gfi::DalitzPlan dplan{};
   std::vector<int> free_ids;     // theta position -> parameter id
   std::vector<int> free_pos;     // parameter id -> theta position or -1

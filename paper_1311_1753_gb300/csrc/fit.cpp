@@ -413,9 +413,10 @@ extern "C" int gf_fit(gf_ctx* ctx, const gf_fit_opts* opts, gf_fit_result* res) 
     };
   };
   // mixed contexts: FP32 BFGS, then an FP64 polish from the FP32 inverse Hessian
-  // (1D programs evaluate in FP64 in every context: nothing to refine)
-  const bool refine =
-      ctx->precision == GF_MIXED && ctx->is_dalitz && (!opts || opts->refine != 0);
+  // (only Dalitz models and the signal + background form have an FP32 plan; other 1D
+  // programs evaluate FP64-accurate in every context: nothing to refine)
+  const bool refine = ctx->precision == GF_MIXED && (ctx->is_dalitz || ctx->use_sb) &&
+                      (!opts || opts->refine != 0);
   FGFun fg_fast = make_fg(false), fg_exact = make_fg(ctx->precision == GF_MIXED);
   MinResult m = refine ? minimise_refined(&fg_fast, fg_exact, x0, step, lo, hi, mo)
                        : minimise(fg_fast, x0, step, lo, hi, mo);

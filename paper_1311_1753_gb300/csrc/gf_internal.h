@@ -108,6 +108,19 @@ struct Cols {
   const double* c[kMaxObs];
 };
 
+// An AddPdf of one Voigtian and one threshold leaf over the same observable (either order;
+// Sec. 4's line-shape fit), evaluated by k_sigbkg.cu: leaf-record and coefficient slots,
+// the theta positions of the leaves' parameters (-1 when fixed) and of the fraction.
+struct SigBkgDesc {
+  int32_t slot_v, slot_t;    // leaf records (Voigtian, threshold)
+  int32_t cslot_v, cslot_t;  // coefficient slots
+  int32_t gv[3];             // mu, sigma, Gamma
+  int32_t gt[3];             // x0, power, c
+  int32_t fpos_v, fpos_t;    // the fraction in each coefficient
+  int32_t fsgn_v, fsgn_t;    // +1: coefficient = f; -1: 1 - f
+  int32_t nfree;
+};
+
 // One grid-normalised node (MappedPdf, CompositePdf): N = h sum_b F(lo + (b + 1/2) h) over
 // nbins midpoints of the observable, F the node's body (sub-program), with dN over the
 // node's local parameters; k_gnorm writes the record at slot.

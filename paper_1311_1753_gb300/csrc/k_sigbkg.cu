@@ -1,0 +1,586 @@
+// k_sigbkg.cu -- the event pass of a signal + background line-shape fit: an AddPdf of a
+// Voigtian signal and a threshold background over one observable (Sec. 4: the D*+ width
+// fit's line shape over the D*+ - D0 mass difference; Sec. 3: AddPdf), NLL and gradient.
+//
+// The general kernels (k_1d.cu) interpret the compiled program per event with the leaf
+// constants and the gradient slots in shared memory.  This form holds everything in
+// registers and takes the gradient from per-thread moments of the event sums:
+//   NLL = -sum_i log P_i,   P = c_v V + c_t B,   V = c3 Re w(z),  z = (x - mu) c1 + i y,
+//   dNLL/dtheta = -sum_i (dP_i/dtheta)/P_i,
+// and with s = 1/P every derivative of V is a fixed linear combination (coefficients
+// depending on theta only) of the sums
+//   Ms = sum s, Mr = sum s Re w, Mi = sum s Im w, Mzr = sum s x_r Re w, Mzi = sum s x_r Im w,
+//   Mzzr = sum s x_r^2 Re w   (x_r = Re z; w' = -2 z w + 2i/sqrt(pi)),
+// every derivative of B one of  MB = sum s B, MtB = sum s t B, MBi = sum s B/t,
+// MBl = sum s B log t  (t = x - x0), and the fraction's of Mr and MB.  The last block
+// forms the gradient from the reduced moments in FP64.  The log-sum is a running product
+// of the P_i with its binary exponent split off after every factor, whose logarithm is
+// taken once per chunk of events.
+//
+// Two arithmetics:
+//  FP64 plan   double-float pairs on the FP32 pipe (as k_1d.cu): exact FP64 differences
+//              x - mu, x - x0; w by the Weideman series, or (events sorted by x) once per
+//              chunk of 24 events and expanded to degree 5 around the chunk's middle event
+//              (the tail of the expansion, k >= 2, in float); events whose P leaves
+//              [2^-80, 2^125) are re-evaluated in FP64.
+//  mixed plan  per-event arithmetic in FP32 (GF_MIXED): data enter by a bit split and exact
+//              float differences; w expanded to degree 4 in float around the middle event
+//              of each chunk of 96 (the expansion's coefficients from the FP64-accurate
+//              series), or the Weideman series in float for unsorted data or wide chunks;
+//              the chunk's moment sums in float, folded into pairs at the chunk's end; the
+//              log-sum, the block and cross-block sums, the normalisation integrals
+//              (k_norm_1d) and the gradient's combination in FP64-accurate arithmetic.
+#include <cmath>
+#include <cstdio>
+
+#include "devutil.cuh"
+#include "gf_internal.h"
+#include "launch.h"
+
+namespace gfi {
+namespace {
+
+constexpr int kSBThreads = 128;
+constexpr int kSBChunk64 = 24;     // FP64 plan: events per expansion of w
+constexpr float kSBLim64 = 3e-4f;  // largest |Re z - Re z0| of an expanded chunk (FP64 plan)
+constexpr int kSBChunk32 = 96;     // mixed plan
+constexpr float kSBLim32 = 3e-3f;
+constexpr int kSBFlush = 32;       // unsorted loop: events per log of the running product
+constexpr int kSBMom = 11;         // reduced values: sum log P and ten moments
+
+enum { SB_LOGP = 0, SB_S, SB_R, SB_I, SB_ZR, SB_ZI, SB_ZZR, SB_B, SB_TB, SB_BI, SB_BL };
+
+// ---- running product of P with its exponent split off -------------------------------------
+struct ProdF2 {
+  F2 p = {1.f, 0.f};
+  int e = 0;
+  __device__ __forceinline__ void mul(F2 x) {
+    p = df_mul(p, x);
+    const int k = (int)((__float_as_uint(p.hi) >> 23) & 0xff) - 127;
+    const float sc = __uint_as_float((unsigned)(127 - k) << 23);  // 2^-k, exact
+    p.hi = __fmul_rn(p.hi, sc);
+    p.lo = __fmul_rn(p.lo, sc);
+    e += k;
+  }
+  // log of the product (the caller resets it)
+  __device__ __forceinline__ F2 log() const {
+    constexpr DFC ln2(0.69314718055994530942);
+    return df_add(df_log_tab(p, s_log_tab), df_mul_f(F2(ln2), (float)e));
+  }
+};
+struct ProdF {
+  float p = 1.f;
+  int e = 0;
+  __device__ __forceinline__ void mul(float x) {
+    p = __fmul_rn(p, x);
+    const int k = (int)((__float_as_uint(p) >> 23) & 0xff) - 127;
+    p = __fmul_rn(p, __uint_as_float((unsigned)(127 - k) << 23));
+    e += k;
+  }
+  __device__ __forceinline__ F2 log() const {
+    constexpr DFC ln2(0.69314718055994530942);
+    return df_add(df_log_tab(F2{p, 0.f}, s_log_tab), df_mul_f(F2(ln2), (float)e));
+  }
+};
+
+// Pair sum whose low part is renormalised only on demand (sums of a few dozen terms).
+struct Lazy {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(F2 v) {
+    const F2 s = two_sum(hi, v.hi);
+    hi = s.hi;
+    lo = __fadd_rn(lo, __fadd_rn(s.lo, v.lo));
+  }
+  __device__ __forceinline__ void add_f(float v) {
+    const F2 s = two_sum(hi, v);
+    hi = s.hi;
+    lo = __fadd_rn(lo, s.lo);
+  }
+  __device__ __forceinline__ void norm() {
+    const F2 s = fast_two_sum(hi, lo);
+    hi = s.hi;
+    lo = s.lo;
+  }
+  __device__ __forceinline__ F2 get() const { return fast_two_sum(hi, lo); }
+};
+
+// ---- expansion of w around a chunk's middle event ------------------------------------------
+// t_k = w^(k)(z0)/k! from w' = -2 z w + 2i/sqrt(pi): t_1 = -2 z0 t_0 + 2i/sqrt(pi),
+// t_{k+1} = -2 (z0 t_k + t_{k-1})/(k + 1), in pairs (the recurrence cancels at large |z0|).
+// For real d = Re z - Re z0 the real and imaginary parts of sum t_k d^k separate.
+template <int DEG>
+__device__ __forceinline__ void tay_coefs(F2 zr, F2 y, const WeidCoef& W, F2* tr, F2* ti) {
+  faddeeva_f2(zr, y, W, tr[0], ti[0]);
+  F2 ar = df_sub(df_mul(zr, tr[0]), df_mul(y, ti[0]));
+  F2 ai = df_add(df_mul(zr, ti[0]), df_mul(y, tr[0]));
+  tr[1] = df_mul_f(ar, -2.f);
+  ti[1] = df_add(df_mul_f(ai, -2.f), DFC(kTwoInvSqrtPi));
+#pragma unroll
+  for (int k = 1; k < DEG; ++k) {
+    ar = df_sub(df_mul(zr, tr[k]), df_mul(y, ti[k]));
+    ai = df_add(df_mul(zr, ti[k]), df_mul(y, tr[k]));
+    const float s = -2.f / (float)(k + 1);  // exact for k + 1 in {2, 4}; else one rounding
+    const F2 sc = (k + 1 == 3) ? F2(DFC(-2.0 / 3)) : (k + 1 == 5) ? F2(DFC(-2.0 / 5))
+                                                                  : F2{s, 0.f};
+    tr[k + 1] = df_mul(df_add(ar, tr[k - 1]), sc);
+    ti[k + 1] = df_mul(df_add(ai, ti[k - 1]), sc);
+  }
+}
+
+// FP64 plan: t_0, t_1 as pairs, t_2 .. t_5 in float (their terms are below 3 d^2 <= 3e-7
+// of w, so float rounding there adds < 2e-14 of |w|).
+struct TayP {
+  F2 z0, t0r, t0i, t1r, t1i;
+  float qr[4], qi[4];
+};
+__device__ __forceinline__ void tayp_build(TayP& T, F2 zr, F2 y, const WeidCoef& W) {
+  F2 tr[6], ti[6];
+  tay_coefs<5>(zr, y, W, tr, ti);
+  T.z0 = zr;
+  T.t0r = tr[0];
+  T.t0i = ti[0];
+  T.t1r = tr[1];
+  T.t1i = ti[1];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    T.qr[k] = __fadd_rn(tr[k + 2].hi, tr[k + 2].lo);
+    T.qi[k] = __fadd_rn(ti[k + 2].hi, ti[k + 2].lo);
+  }
+}
+__device__ __forceinline__ void tayp_eval(const TayP& T, F2 zr, F2& wr, F2& wi) {
+  const F2 dd = df_sub(zr, T.z0);
+  const float d = dd.hi;
+  const float qr = __fmaf_rn(__fmaf_rn(__fmaf_rn(T.qr[3], d, T.qr[2]), d, T.qr[1]), d, T.qr[0]);
+  const float qi = __fmaf_rn(__fmaf_rn(__fmaf_rn(T.qi[3], d, T.qi[2]), d, T.qi[1]), d, T.qi[0]);
+  wr = df_add(T.t0r, df_mul(dd, df_add_f(T.t1r, __fmul_rn(d, qr))));
+  wi = df_add(T.t0i, df_mul(dd, df_add_f(T.t1i, __fmul_rn(d, qi))));
+}
+
+// Weideman's series in float (the mixed plan's unsorted events and wide chunks): the same
+// coefficients and rational map as faddeeva_f2, every step in FP32.
+__device__ __forceinline__ void faddeeva_f32(float x, float y, const WeidCoef& W, float& wr,
+                                             float& wi) {
+  const float L = W.Lhi;
+  const float dr = L + y;                     // L - iz = dr - i x
+  const float inv = 1.f / __fmaf_rn(dr, dr, x * x);
+  const float zr = __fmaf_rn(L - y, dr, -x * x) * inv;
+  const float zi = 2.f * L * x * inv;
+  float pr = W.ahi[kWeidN], pi = 0.f;
+#pragma unroll 8
+  for (int n = kWeidN - 1; n >= 1; --n) {
+    const float t = __fmaf_rn(pr, zr, __fmaf_rn(-pi, zi, W.ahi[n]));
+    pi = __fmaf_rn(pr, zi, pi * zr);
+    pr = t;
+  }
+  const float ir = dr * inv, ii = x * inv;   // 1/(L - iz)
+  const float qr = __fmaf_rn(ir, ir, -ii * ii), qi = 2.f * ir * ii;
+  wr = __fmaf_rn(0.56418958354775628695f, ir, 2.f * __fmaf_rn(pr, qr, -pi * qi));
+  wi = __fmaf_rn(0.56418958354775628695f, ii, 2.f * __fmaf_rn(pr, qi, pi * qr));
+}
+
+// ---- constants of one evaluation -------------------------------------------------------------
+// From the leaf records (k_norm_1d): Voigtian c0 = mu, c1 = 1/(sigma sqrt2), c2 = y = Im z,
+// c3 = 1/(sigma sqrt(2 pi) N); threshold c0 = x0, c1 = p, c2 = c, c3 = 1/N.
+struct SBConst {
+  double mu, x0, c1, y, c3v, pw, cc, c3t, cv, ct;
+  int half;  // p == 1/2 and no gradient in p: sqrt(t) instead of exp(p log t)
+};
+__device__ __forceinline__ void sb_consts(const SigBkgDesc& D, const double* __restrict__ der,
+                                          bool grad, SBConst& K) {
+  const double* rv = der + D.slot_v * kLeafRec;
+  const double* rt = der + D.slot_t * kLeafRec;
+  K.mu = rv[10];
+  K.c1 = rv[11];
+  K.y = rv[12];
+  K.c3v = rv[13];
+  K.x0 = rt[10];
+  K.pw = rt[11];
+  K.cc = rt[12];
+  K.c3t = rt[13];
+  K.cv = der[kMaxLeaf * kLeafRec + D.cslot_v];
+  K.ct = der[kMaxLeaf * kLeafRec + D.cslot_t];
+  K.half = (K.pw == 0.5 && !(grad && D.gt[1] >= 0)) ? 1 : 0;
+}
+
+// One event in FP64 (P outside the float-safe range): log P and the moments' terms.
+__device__ __noinline__ void sb_event_fp64(double x, const SBConst* __restrict__ K,
+                                           const WeidCoef& W, double* o) {
+  const double zr = (x - K->mu) * K->c1;
+  double wr, wi;
+  faddeeva_df(zr, K->y, W, wr, wi);
+  const double V = K->c3v * wr;
+  const double t = x - K->x0;
+  double B = 0.0, lt = 0.0;
+  if (t > 0.0) {
+    lt = df_log(t);
+    B = df_exp(K->pw * lt - K->cc * t) * K->c3t;
+  }
+  const double P = K->cv * V + K->ct * B;
+  const double s = 1.0 / P;
+  o[SB_LOGP] = df_log(P);
+  o[SB_S] = s;
+  o[SB_R] = s * wr;
+  o[SB_I] = s * wi;
+  o[SB_ZR] = zr * s * wr;
+  o[SB_ZI] = zr * s * wi;
+  o[SB_ZZR] = zr * zr * s * wr;
+  o[SB_B] = s * B;
+  o[SB_TB] = t > 0.0 ? s * B * t : 0.0;
+  o[SB_BI] = t > 0.0 ? s * B / t : 0.0;
+  o[SB_BL] = t > 0.0 ? s * B * lt : 0.0;
+}
+
+// Last block: NLL and gradient from the reduced sums M (FP64) into result[0 .. nfree].
+__device__ void sb_finish(const SigBkgDesc& D, const double* __restrict__ der, const double* M,
+                          bool grad, double* __restrict__ result) {
+  result[0] = -M[SB_LOGP];
+  if (!grad) return;
+  double g[kMaxFree1D];
+  for (int k = 0; k < D.nfree; ++k) g[k] = 0.0;
+  const double* rv = der + D.slot_v * kLeafRec;
+  const double* rt = der + D.slot_t * kLeafRec;
+  const double cv = der[kMaxLeaf * kLeafRec + D.cslot_v];
+  const double ct = der[kMaxLeaf * kLeafRec + D.cslot_t];
+  const double y = rv[12], c3 = rv[13];
+  // sums of s dRe w/dx_r, s dIm w/dx_r and s (dRe w/dx_r x_r - dIm w/dx_r y)
+  const double s_dre = -2.0 * (M[SB_ZR] - y * M[SB_I]);
+  const double s_dim = -2.0 * (M[SB_ZI] + y * M[SB_R]) + kTwoInvSqrtPi * M[SB_S];
+  const double s_q = -2.0 * M[SB_ZZR] + 4.0 * y * M[SB_ZI] + 2.0 * y * y * M[SB_R] -
+                     kTwoInvSqrtPi * y * M[SB_S];
+  const double sv = c3 * M[SB_R];  // sum V/P
+  // Voigtian: dV/dmu = -(c5 dre + V r2), dV/dsigma = -(c6 q + V c8), dV/dGamma = -(c7 dim
+  // + V r4), c5..c8 = rec[15..18], r_k = dlogN/dpar = rec[2..4]
+  if (D.gv[0] >= 0) g[D.gv[0]] += cv * (rv[15] * s_dre + rv[2] * sv);
+  if (D.gv[1] >= 0) g[D.gv[1]] += cv * (rv[16] * s_q + rv[18] * sv);
+  if (D.gv[2] >= 0) g[D.gv[2]] += cv * (rv[17] * s_dim + rv[4] * sv);
+  // threshold: dB/dx0 = B (c - p/t - r2), dB/dp = B (log t - r3), dB/dc = -B (t + r4)
+  if (D.gt[0] >= 0) g[D.gt[0]] -= ct * ((rt[12] - rt[2]) * M[SB_B] - rt[11] * M[SB_BI]);
+  if (D.gt[1] >= 0) g[D.gt[1]] -= ct * (M[SB_BL] - rt[3] * M[SB_B]);
+  if (D.gt[2] >= 0) g[D.gt[2]] += ct * (M[SB_TB] + rt[4] * M[SB_B]);
+  // fractions: dP/df = +-V or +-B
+  if (D.fpos_v >= 0) g[D.fpos_v] -= D.fsgn_v * sv;
+  if (D.fpos_t >= 0) g[D.fpos_t] -= D.fsgn_t * M[SB_B];
+  for (int k = 0; k < D.nfree; ++k) result[1 + k] = g[k];
+}
+
+// ---- the kernel -------------------------------------------------------------------------------
+// STORE: log P_i into out_logp[perm ? perm[i] : i] instead of the sums.
+template <bool G, bool MIXED, bool STORE>
+__global__ void __launch_bounds__(kSBThreads) k_sigbkg(
+    const __grid_constant__ SigBkgDesc D, const __grid_constant__ WeidCoef W,
+    const Program* __restrict__ prog, const double* __restrict__ xcol, const int64_t n,
+    const double* __restrict__ der,
+    double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
+    double* __restrict__ out_logp, const int32_t* __restrict__ perm) {
+  __shared__ SBConst Ks;
+  __shared__ double red[(kSBThreads / 32) * kSBMom];
+  __shared__ double fin[kSBMom];
+  __shared__ int last;
+  const int tid = threadIdx.x;
+  load_df_tables();
+  if (tid == 0) sb_consts(D, der, G, Ks);
+  __syncthreads();
+  const SBConst& K = Ks;
+
+  Lazy acc;            // sum log P
+  Lazy m[kSBMom - 1];  // moments SB_S .. SB_BL
+  const bool need_bi = G && D.gt[0] >= 0;
+  const bool need_bl = G && D.gt[1] >= 0;
+  const bool half = K.half != 0;
+
+  // FP64 fallback for one event (P outside the float-safe range or not positive)
+  auto fallback = [&](int64_t i, double xi) {
+    double o[kSBMom];
+    sb_event_fp64(xi, &K, W, o);
+    if (STORE) {
+      out_logp[perm ? perm[i] : i] = o[SB_LOGP];
+      return;
+    }
+    acc.add(df_from(o[SB_LOGP]));
+    if (G)
+#pragma unroll
+      for (int k = 1; k < kSBMom; ++k) m[k - 1].add(df_from(o[k]));
+  };
+
+  const int64_t nthreads = (int64_t)gridDim.x * kSBThreads;
+  const int64_t g = (int64_t)blockIdx.x * kSBThreads + tid;
+  constexpr int kChunk = MIXED ? kSBChunk32 : kSBChunk64;
+  // sorted events and at least 8 per thread: one expansion of w per chunk pays
+  const bool chunked = prog->sorted && n >= 8 * nthreads;
+
+  if constexpr (!MIXED) {
+    // ---------------- FP64 plan: pairs ----------------
+    const F2 c1 = df_from(K.c1), y = df_from(K.y), c3v = df_from(K.c3v);
+    const F2 pw = df_from(K.pw), cc = df_from(K.cc), c3t = df_from(K.c3t);
+    const F2 cv = df_from(K.cv), ct = df_from(K.ct);
+    ProdF2 prod;
+    TayP T;
+    auto one = [&](int64_t i, double xi, bool tay) {
+      const F2 zr = df_mul(df_split(xi - K.mu), c1);
+      F2 wr, wi;
+      if (tay) tayp_eval(T, zr, wr, wi);
+      else faddeeva_f2(zr, y, W, wr, wi);
+      const double td = xi - K.x0;
+      F2 B = {0.f, 0.f}, t = {0.f, 0.f}, lt = {0.f, 0.f};
+      if (td > 0.0) {
+        t = df_split(td);
+        if (half) {
+          B = df_mul(df_mul(df_sqrt(t), df_exp_tab(df_neg(df_mul(cc, t)), s_exp_tab)), c3t);
+        } else {
+          lt = df_log_tab(t, s_log_tab);
+          B = df_mul(df_exp_tab(df_sub(df_mul(pw, lt), df_mul(cc, t)), s_exp_tab), c3t);
+        }
+      }
+      const F2 P = df_add(df_mul(cv, df_mul(c3v, wr)), df_mul(ct, B));
+      if (!(P.hi >= 8.271806125530277e-25f && P.hi < 4.2535295865117308e37f)) {
+        fallback(i, xi);
+        return;
+      }
+      if (STORE) {
+        out_logp[perm ? perm[i] : i] = df_to(df_log_tab(P, s_log_tab));
+        return;
+      }
+      prod.mul(P);
+      if (G) {
+        const F2 s = df_rcp(P);
+        const F2 a = df_mul(s, wr), b = df_mul(s, wi);
+        const F2 za = df_mul(zr, a);
+        m[SB_S - 1].add(s);
+        m[SB_R - 1].add(a);
+        m[SB_I - 1].add(b);
+        m[SB_ZR - 1].add(za);
+        m[SB_ZI - 1].add(df_mul(zr, b));
+        m[SB_ZZR - 1].add(df_mul(zr, za));
+        if (td > 0.0) {
+          const F2 sb = df_mul(s, B);
+          m[SB_B - 1].add(sb);
+          m[SB_TB - 1].add(df_mul(t, sb));
+          if (need_bi) m[SB_BI - 1].add(df_mul(sb, df_rcp(t)));
+          if (need_bl) m[SB_BL - 1].add(df_mul(sb, lt));
+        }
+      }
+    };
+    auto flush = [&]() {
+      if (STORE) return;
+      acc.add(prod.log());
+      prod = ProdF2();
+      acc.norm();
+      if (G)
+#pragma unroll
+        for (int k = 0; k < kSBMom - 1; ++k) m[k].norm();
+    };
+    if (chunked) {
+      // thread g: the contiguous share [n g / T, n (g + 1) / T) of the sorted events, in
+      // chunks of kChunk with one expansion of w per chunk
+      const int64_t lo = n * g / nthreads, hi = n * (g + 1) / nthreads;
+      for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
+        const int cnt = (int)(hi - c0 < kChunk ? hi - c0 : kChunk);
+        const double xm = __ldg(xcol + c0 + (cnt - 1) / 2);
+        const float da = fabsf(__fmul_rn((float)(__ldg(xcol + c0) - xm), c1.hi));
+        const float db = fabsf(__fmul_rn((float)(__ldg(xcol + c0 + cnt - 1) - xm), c1.hi));
+        const bool ok = fmaxf(da, db) <= kSBLim64;
+        if (ok) tayp_build(T, df_mul(df_split(xm - K.mu), c1), y, W);
+        for (int k = 0; k < cnt; ++k) one(c0 + k, __ldg(xcol + c0 + k), ok);
+        flush();
+      }
+    } else {
+      int since = 0;
+      for (int64_t i = g; i < n; i += nthreads) {
+        one(i, __ldcs(xcol + i), false);
+        if (++since == kSBFlush) {
+          flush();
+          since = 0;
+        }
+      }
+      flush();
+    }
+  } else {
+    // ---------------- mixed plan: FP32 per event ----------------
+    const F2 mu2 = df_split(K.mu), x02 = df_split(K.x0);
+    const float c1 = (float)K.c1, y = (float)K.y, c3v = (float)K.c3v;
+    const float pw = (float)K.pw, cc = (float)K.cc, c3t = (float)K.c3t;
+    const float cv = (float)K.cv, ct = (float)K.ct;
+    const F2 c1p = df_from(K.c1), yp = df_from(K.y);
+    ProdF prod;
+    float cm[kSBMom - 1];
+#pragma unroll
+    for (int k = 0; k < kSBMom - 1; ++k) cm[k] = 0.f;
+    // one event: x as a pair, zr = Re z, dz = Re z - Re z0 (tay: T holds the degree-4
+    // expansion's coefficients, re then im; otherwise the float series)
+    float T[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    auto one = [&](int64_t i, double xi, F2 xs, float zr, float dz, bool tay) {
+      float wr, wi;
+      if (tay) {
+        wr = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(T[4], dz, T[3]), dz, T[2]), dz, T[1]), dz, T[0]);
+        wi = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(T[9], dz, T[8]), dz, T[7]), dz, T[6]), dz, T[5]);
+      } else {
+        faddeeva_f32(zr, y, W, wr, wi);
+      }
+      const float t = __fadd_rn(__fsub_rn(xs.hi, x02.hi), __fsub_rn(xs.lo, x02.lo));
+      float B = 0.f, lt = 0.f;
+      if (t > 0.f) {
+        if (half) {
+          B = __fmul_rn(__fmul_rn(__fsqrt_rn(t), __expf(-cc * t)), c3t);
+        } else {
+          lt = __logf(t);
+          B = __fmul_rn(__expf(__fmaf_rn(pw, lt, -cc * t)), c3t);
+        }
+      }
+      const float P = __fmaf_rn(cv, __fmul_rn(c3v, wr), __fmul_rn(ct, B));
+      if (!(P >= 8.271806125530277e-25f && P < 4.2535295865117308e37f)) {
+        fallback(i, xi);
+        return;
+      }
+      if (STORE) {
+        out_logp[perm ? perm[i] : i] = (double)logf(P);
+        return;
+      }
+      prod.mul(P);
+      if (G) {
+        const float s = __frcp_rn(P);
+        const float a = s * wr, b = s * wi, za = zr * a;
+        cm[SB_S - 1] += s;
+        cm[SB_R - 1] += a;
+        cm[SB_I - 1] += b;
+        cm[SB_ZR - 1] += za;
+        cm[SB_ZI - 1] += zr * b;
+        cm[SB_ZZR - 1] += zr * za;
+        if (t > 0.f) {
+          const float sb = s * B;
+          cm[SB_B - 1] += sb;
+          cm[SB_TB - 1] += t * sb;
+          if (need_bi) cm[SB_BI - 1] += __fdividef(sb, t);
+          if (need_bl) cm[SB_BL - 1] += sb * lt;
+        }
+      }
+    };
+    auto flush = [&]() {
+      if (STORE) return;
+      acc.add(prod.log());
+      prod = ProdF();
+      acc.norm();
+      if (G)
+#pragma unroll
+        for (int k = 0; k < kSBMom - 1; ++k) {
+          m[k].add_f(cm[k]);
+          m[k].norm();
+          cm[k] = 0.f;
+        }
+    };
+    if (chunked) {
+      const int64_t lo = n * g / nthreads, hi = n * (g + 1) / nthreads;
+      for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
+        const int cnt = (int)(hi - c0 < kChunk ? hi - c0 : kChunk);
+        const double xm = __ldg(xcol + c0 + (cnt - 1) / 2);
+        const F2 xms = df_split(xm);
+        const F2 z0 = df_mul(df_split(xm - K.mu), c1p);
+        const float z0f = __fadd_rn(z0.hi, z0.lo);
+        auto dzof = [&](F2 xs) {
+          return __fmul_rn(__fadd_rn(__fsub_rn(xs.hi, xms.hi), __fsub_rn(xs.lo, xms.lo)), c1);
+        };
+        const float da = fabsf(dzof(df_split(__ldg(xcol + c0))));
+        const float db = fabsf(dzof(df_split(__ldg(xcol + c0 + cnt - 1))));
+        const bool ok = fmaxf(da, db) <= kSBLim32;
+        if (ok) {
+          F2 tr[5], ti[5];
+          tay_coefs<4>(z0, yp, W, tr, ti);
+#pragma unroll
+          for (int k = 0; k < 5; ++k) {
+            T[k] = __fadd_rn(tr[k].hi, tr[k].lo);
+            T[5 + k] = __fadd_rn(ti[k].hi, ti[k].lo);
+          }
+        }
+        for (int k = 0; k < cnt; ++k) {
+          const double xi = __ldg(xcol + c0 + k);
+          const F2 xs = df_split(xi);
+          const float dz = dzof(xs);
+          one(c0 + k, xi, xs, __fadd_rn(z0f, dz), dz, ok);
+        }
+        flush();
+      }
+    } else {
+      int since = 0;
+      for (int64_t i = g; i < n; i += nthreads) {
+        const double xi = __ldcs(xcol + i);
+        const F2 xs = df_split(xi);
+        const float zr = __fmul_rn(__fadd_rn(__fsub_rn(xs.hi, mu2.hi), __fsub_rn(xs.lo, mu2.lo)), c1);
+        one(i, xi, xs, zr, 0.f, false);
+        if (++since == kSBChunk32) {
+          flush();
+          since = 0;
+        }
+      }
+      flush();
+    }
+  }
+  if (STORE) return;
+
+  // block sums (fixed order), then the last block's cross-block sums and the gradient
+  const int mm = G ? kSBMom : 1;
+  constexpr int stride = 1 + kMaxFree1D;
+  F2 vals[kSBMom];  // the register sums, copied once for the indexed reduction
+  vals[0] = acc.get();
+#pragma unroll
+  for (int k = 1; k < kSBMom; ++k) vals[k] = m[k - 1].get();
+  block_sum_pairs([&](int k) -> F2 { return vals[k]; }, mm, red,
+                  partials + (size_t)blockIdx.x * stride);
+  if (!arrive_last_of(counter, gridDim.x, &last)) return;
+  reduce_partials(partials, gridDim.x, stride, mm, fin);
+  if (tid == 0) {
+    sb_finish(D, der, fin, G, result);
+    *counter = 0u;
+  }
+}
+
+template <bool G, bool MIXED, bool STORE>
+const void* sb_kernel() {
+  return (const void*)k_sigbkg<G, MIXED, STORE>;
+}
+
+}  // namespace
+
+int sigbkg_blocks_per_sm(bool mixed) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &nb, mixed ? k_sigbkg<true, true, false> : k_sigbkg<true, false, false>, kSBThreads, 0);
+  cudaGetLastError();
+  return nb > 0 ? nb : 1;
+}
+
+int sigbkg_threads() { return kSBThreads; }
+
+cudaError_t launch_sigbkg(const SigBkgDesc& D, const WeidCoef& W, const Program* prog,
+                          const double* x, int64_t n,
+                          const double* derived, double* partials, unsigned* counter,
+                          double* result, double* out_logp, const int32_t* perm, bool grad,
+                          bool mixed, int nblocks, cudaStream_t st) {
+  if (nblocks < 1) nblocks = 1;
+  if (out_logp) {
+    if (mixed)
+      k_sigbkg<false, true, true><<<nblocks, kSBThreads, 0, st>>>(D, W, prog, x, n, derived, partials,
+                                                                  counter, result, out_logp, perm);
+    else
+      k_sigbkg<false, false, true><<<nblocks, kSBThreads, 0, st>>>(D, W, prog, x, n, derived, partials,
+                                                                   counter, result, out_logp, perm);
+  } else if (mixed) {
+    if (grad)
+      k_sigbkg<true, true, false><<<nblocks, kSBThreads, 0, st>>>(D, W, prog, x, n, derived, partials,
+                                                                  counter, result, nullptr, nullptr);
+    else
+      k_sigbkg<false, true, false><<<nblocks, kSBThreads, 0, st>>>(D, W, prog, x, n, derived, partials,
+                                                                   counter, result, nullptr, nullptr);
+  } else {
+    if (grad)
+      k_sigbkg<true, false, false><<<nblocks, kSBThreads, 0, st>>>(D, W, prog, x, n, derived, partials,
+                                                                   counter, result, nullptr, nullptr);
+    else
+      k_sigbkg<false, false, false><<<nblocks, kSBThreads, 0, st>>>(D, W, prog, x, n, derived, partials,
+                                                                    counter, result, nullptr, nullptr);
+  }
+  return cudaGetLastError();
+}
+
+// This unit's copy of the exp/log tables, once per device (that device current).
+cudaError_t prepare_kernels_sigbkg() { return upload_df_tables(); }
+
+}  // namespace gfi

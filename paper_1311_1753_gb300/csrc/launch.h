@@ -44,6 +44,17 @@ cudaError_t sort_by_key_f64(const double* key_in, double* key_out, int32_t* perm
 cudaError_t launch_gather(const double* in, const int32_t* perm, double* out, int64_t n,
                           cudaStream_t st);
 cudaError_t prepare_kernels_dalitz();
+// signal + background form (k_sigbkg.cu): NLL (+ gradient) into result[0 .. nfree], or
+// with out_logp the per-event log P (through perm if sorted); mixed: the FP32 plan.  The
+// kernel reads the sorted flag from the device copy of the program.
+cudaError_t launch_sigbkg(const SigBkgDesc& D, const WeidCoef& W, const Program* prog,
+                          const double* x, int64_t n,
+                          const double* derived, double* partials, unsigned* counter,
+                          double* result, double* out_logp, const int32_t* perm, bool grad,
+                          bool mixed, int nblocks, cudaStream_t st);
+int sigbkg_blocks_per_sm(bool mixed);
+int sigbkg_threads();
+cudaError_t prepare_kernels_sigbkg();
 // loads the allocation-free entry point's module (its static scratch array)
 cudaError_t noalloc_preload();
 // batched fit-server tick (persistent launches over a work list of TickItems)

@@ -1,0 +1,146 @@
+"""The signal + background form (an AddPdf of a Voigtian and a threshold leaf over one
+observable: Sec. 4's line shape, config 2) on its own kernel, in both precision modes.
+
+FP64 mode: per event |log P_gpu - log P_orc| <= 1e-12, NLL 1e-9 relative, gradient 1e-9 of
+its scale (the general tests of config 2 run this kernel too).  Mixed mode (FP32 per-event
+arithmetic, FP64 sums and normalisation): its errors against the FP64 oracle are measured
+at the workload's size, stated (tests/parity.py summary) and bounded; a mixed fit
+(FP32 BFGS, then the FP64 refinement) lands within 0.01 sigma of the oracle's fit."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import minimise
+from paper_1311_1753_gb300 import synth
+from tests import oracle_models as om
+from tests import product_models as pm
+from tests.parity import WORST, per_event
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gf():
+    from paper_1311_1753_gb300 import gf as _gf
+    return _gf
+
+
+def _data(n, seed=synth.SEED_VOIGT):
+    lo, hi = synth.VOIGT_RANGE
+    return synth.voigt_threshold_events(n, **synth.VOIGT_TRUTH, lo=lo, hi=hi, seed=seed)
+
+
+def _grad_close(g, go, n, rel=1e-9):
+    scale = np.maximum(np.abs(go), 1e-6 * n)
+    assert np.all(np.abs(g - go) <= rel * scale + 1e-9 * np.abs(go).max()), (g, go)
+
+
+@pytest.mark.parametrize("order", ["sig-bkg", "bkg-sig"])
+@pytest.mark.parametrize("n", [1, 2, 129, 40_001])
+@pytest.mark.parametrize("sort", [True, False])
+def test_fp64_plan_parity(gf, order, n, sort):
+    """Both component orders (the fraction on the Voigtian or on the background), sorted
+    and caller-ordered events, ragged sizes; x0 and power free in one of the trials."""
+    x = _data(n)
+    t = synth.VOIGT_TRUTH
+    lo, hi = synth.VOIGT_RANGE
+    ctx = gf.Context()
+    o = ctx.observable("dm", lo, hi)
+    mu = ctx.parameter("mu", t["mu"], 1e-5)
+    s = ctx.parameter("sigma", t["sigma"], 1e-5)
+    w = ctx.parameter("width", t["width"], 1e-5)
+    x0 = ctx.parameter("x0", t["x0"] - 1e-4, 1e-4)
+    pw = ctx.parameter("power", 0.55, 0.01)
+    c = ctx.parameter("c", t["c"], 0.5)
+    f = ctx.parameter("frac", 0.3 if order == "sig-bkg" else 0.7, 0.01)
+    v = ctx.voigt(o, mu, s, w)
+    b = ctx.threshold(o, x0, pw, c)
+    for node in (v, b):
+        ctx.set_norm_grid(node, 3000)
+    root = ctx.add([v, b] if order == "sig-bkg" else [b, v], [f])
+    ctx.set_event_sort(sort)
+    ctx.set_data(root, [o], [x])
+    m = om.oracle.Model1D([(lo, hi)], nbins=3000)
+    P = [m.param(ctx.value(p)) for p in ctx.free_params()]
+    ov = m.voigt(0, P[0], P[1], P[2])
+    ob = m.threshold(0, P[3], P[4], P[5])
+    m.add([ov, ob] if order == "sig-bkg" else [ob, ov], [P[6]])
+    for trial, fix_shape in ((0, True), (1, False)):
+        th = m.p.copy() * (1 + 0.02 * trial * np.cos(np.arange(7)))
+        if fix_shape:  # x0 and power fixed: the sqrt path at power 1/2
+            th[3], th[4] = t["x0"], 0.5
+        ctx.set_fixed(x0, fix_shape)
+        ctx.set_fixed(pw, fix_shape)
+        if fix_shape:
+            ctx.set_value(x0, th[3])
+            ctx.set_value(pw, th[4])
+        free = [k for k in range(7) if not (fix_shape and k in (3, 4))]
+        per_event(f"sigbkg fp64 {order} n={n} sort={sort}", ctx.logpdf(th[free]),
+                  m.logpdf([x], th))
+        fg, gg = ctx.nll_grad(th[free])
+        fo, go = m.nll([x], th, grad=True)
+        assert abs(fg - fo) <= 1e-9 * max(1.0, abs(fo)), (fg, fo)
+        _grad_close(gg, go[free], n)
+        assert abs(ctx.nll(th[free]) - fg) <= 1e-12 * max(1.0, abs(fg))
+
+
+def test_mixed_plan_errors_full_size(gf):
+    """10^7 events (config 2) in GF_MIXED: per-event relative error percentiles, NLL and
+    gradient against the FP64 oracle, stated and bounded."""
+    x = _data(10_000_000)
+    m, free = om.voigt_model()
+    p = m.p.copy()
+    p[free] *= np.array([1.00001, 1.02, 0.97, 1.03, 0.98])
+    th = p[free]
+    lo_ = m.logpdf([x], p)
+    fo, go = m.nll([x], p, grad=True)
+    ctx, root, obs = pm.voigt_model(gf, precision=gf.GF_MIXED)
+    ctx.set_data(root, obs, [x])
+    rel = np.abs(np.expm1(ctx.logpdf(th) - lo_))
+    pct = {q: float(np.quantile(rel, q)) for q in (0.5, 0.9, 0.99, 0.999)}
+    pct[1.0] = float(rel.max())
+    for q, v in pct.items():
+        WORST[f"config2 mixed full 1e7: per-event |P/P_orc - 1| quantile {q}"] = v
+    f, g = ctx.nll_grad(th)
+    WORST["config2 mixed full 1e7: NLL relative error"] = abs(f / fo - 1)
+    WORST["config2 mixed full 1e7: max |dgrad_k / grad_k|"] = float(np.max(np.abs(g / go[free] - 1)))
+    assert pct[0.5] < 1e-6 and pct[0.99] < 1e-5 and pct[1.0] < 1e-3
+    assert abs(f / fo - 1) < 1e-8
+    assert np.all(np.abs(g - go[free]) <= 1e-4 * np.abs(go[free]) + 1e-6 * np.abs(go[free]).max())
+    # the FP64 plan of the same (mixed) context: the refinement stage's evaluations
+    ctx64, root64, obs64 = pm.voigt_model(gf)
+    ctx64.set_data(root64, obs64, [x])
+    f64, g64 = ctx64.nll_grad(th)
+    assert abs(f64 - fo) <= 1e-9 * abs(fo)
+    _grad_close(g64, go[free], len(x))
+
+
+def test_mixed_fit_within_a_hundredth_sigma(gf):
+    """Config 2's form at 10^6 events: the mixed fit (FP32 BFGS, then FP64 from the FP32
+    inverse Hessian) against the oracle's BFGS on the FP64 likelihood."""
+    x = _data(1_000_000, seed=123)
+    m, free = om.voigt_model(nbins=2000)
+    truth = m.p[free]
+    start = truth * np.array([1.0002, 1.1, 0.85, 1.1, 0.93])
+    ctx, root, obs = pm.voigt_model(gf, precision=gf.GF_MIXED, nbins=2000)
+    for k, pid in enumerate(ctx.free_params()):
+        ctx.set_value(pid, start[k])
+    ctx.set_data(root, obs, [x])
+    r = ctx.fit(tol=1e-9)
+    assert r["status"] == gf.GF_OK, r
+    assert 0 < r["n_calls_fast"] < r["n_calls"]
+
+    def fg(q):
+        p = m.p.copy()
+        p[free] = q
+        f, g = m.nll([x], p, grad=True)
+        return f, g[free]
+    o = minimise.fit(fg, start, np.array([1e-5, 1e-5, 1e-5, 0.5, 0.01]),
+                     np.array([0.143, 1e-5, 1e-6, 0.0, 0.0]),
+                     np.array([0.148, 2e-3, 1e-3, 200.0, 1.0]), tol=1e-10)
+    assert o.converged
+    dev = (r["theta"] - o.x) / o.err
+    WORST["config2 mixed fit 1e6: max |theta - theta_orc| / sigma"] = float(np.abs(dev).max())
+    assert np.all(np.abs(dev) <= 0.01), dev
+    assert np.all(np.abs(r["err"] / o.err - 1) < 0.02)
