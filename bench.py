@@ -259,15 +259,21 @@ def e2e_steps(torch, ctx, cols, thetas, steps, warmup):
 
 
 # ---- the oracle on the host cores ------------------------------------------------------------------
-def oracle_voigt_rate(n_sample, min_seconds=10.0, max_reps=50):
-    import oracle  # CPU baseline only
-    lo, hi = synth.VOIGT_RANGE
-    x = synth.voigt_threshold_events(n_sample, **synth.VOIGT_TRUTH, lo=lo, hi=hi)
+def _oracle_voigt_model():
+    import oracle  # CPU baseline and reference arm only
     t = synth.VOIGT_TRUTH
     m = oracle.Model1D([synth.VOIGT_RANGE])
     mu, s, w = m.param(t["mu"]), m.param(t["sigma"]), m.param(t["width"])
     x0, pw, c, f = m.param(t["x0"]), m.param(t["power"]), m.param(t["c"]), m.param(t["frac"])
     m.add([m.voigt(0, mu, s, w), m.threshold(0, x0, pw, c)], [f])
+    return m
+
+
+def oracle_voigt_rate(n_sample, min_seconds=10.0, max_reps=50):
+    """The oracle on one core: NLL + gradient over n_sample events of the workload."""
+    lo, hi = synth.VOIGT_RANGE
+    x = synth.voigt_threshold_events(n_sample, **synth.VOIGT_TRUTH, lo=lo, hi=hi)
+    m = _oracle_voigt_model()
     reps, t0 = 0, time.perf_counter()
     while reps < max_reps:
         m.nll([x], grad=True)
@@ -276,6 +282,72 @@ def oracle_voigt_rate(n_sample, min_seconds=10.0, max_reps=50):
             break
     el = time.perf_counter() - t0
     return n_sample * reps / el, reps, el
+
+
+def _oracle_worker(conn, x):
+    m = _oracle_voigt_model()
+    while True:
+        reps = conn.recv()
+        if reps is None:
+            break
+        t0 = time.perf_counter()
+        f = 0.0
+        for _ in range(reps):
+            f += m.nll([x], grad=True)[0]
+        conn.send((time.perf_counter() - t0, f))
+
+
+class OraclePool:
+    """The plain FP64 oracle over the host cores: one process per core (started with spawn,
+    safe after CUDA initialisation), each holding a contiguous slice of the events; one
+    step = every process evaluates NLL + gradient over its slice (the sum over slices is
+    the NLL of all events)."""
+
+    def __init__(self, x, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or max(1, len(os.sched_getaffinity(0)))
+        ctx = mp.get_context("spawn")
+        self.procs, self.conns = [], []
+        for sl in np.array_split(np.ascontiguousarray(x), self.cores):
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_oracle_worker, args=(b, sl), daemon=True)
+            pr.start()
+            self.procs.append(pr)
+            self.conns.append(a)
+
+    def step(self, reps=1):
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send(reps)
+        f = sum(c.recv()[1] for c in self.conns)
+        return time.perf_counter() - t0, f
+
+    def close(self):
+        for c in self.conns:
+            c.send(None)
+        for pr in self.procs:
+            pr.join(timeout=10)
+
+
+def cpu_baseline(unit, n_all=2_000_000, seconds=5.0):
+    """The oracle as it stands, on one core and on every core of the host, on samples of
+    the headline workload (events of the same distribution)."""
+    rate1, reps1, el1 = oracle_voigt_rate(200_000, min_seconds=seconds)
+    lo, hi = synth.VOIGT_RANGE
+    x = synth.voigt_threshold_events(n_all, **synth.VOIGT_TRUTH, lo=lo, hi=hi,
+                                     seed=synth.SEED_VOIGT + 77)
+    pool = OraclePool(x)
+    pool.step()  # workers ready
+    dt, _ = pool.step()
+    reps = max(1, int(seconds / max(dt, 1e-3)))
+    el, _ = pool.step(reps)
+    pool.close()
+    rate = n_all * reps / el
+    return {"value": rate, "unit": unit, "cores": pool.cores, "kind": "oracle",
+            "sample": f"{reps} NLL+gradient evaluations over {n_all:,} events of the workload "
+                      f"split over {pool.cores} processes ({el:.1f} s)",
+            "single_core": {"value": rate1, "unit": unit, "cores": 1,
+                            "sample": f"{reps1} evaluations over 200,000 events ({el1:.1f} s)"}}
 
 
 # ---- main -----------------------------------------------------------------------------------------

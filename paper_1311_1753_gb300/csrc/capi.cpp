@@ -2177,11 +2177,26 @@ int tick_prepare(gf_ctx* ctx) {
     F.counter_ev = d.counters;
     F.counter_norm = d.counters + 1;
     F.analytic_only = ctx->has_grid ? 0 : 1;
-    CK(cudaMalloc(&d.tick_desc, sizeof(F)));
+    // the signal + background form also gets its own event descriptor, after the Fit1D
+    // (whose program the normalisation tick uses)
+    const size_t off = round_up(sizeof(F), 256);
+    CK(cudaMalloc(&d.tick_desc, off + sizeof(FitSB)));
     CK(cudaMemcpyAsync(d.tick_desc, &F, sizeof(F), cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->use_sb) {
+      FitSB S{};
+      S.D = ctx->sb;
+      S.x = d.cols[ctx->prog.ins[ctx->prog.mix_leaf[0]].obs];
+      S.n = d.n;
+      S.derived = d.derived;
+      S.partials = d.partials;
+      S.counter = d.counters;
+      S.sorted = ctx->prog.sorted;
+      CK(cudaMemcpyAsync(static_cast<char*>(d.tick_desc) + off, &S, sizeof(S),
+                         cudaMemcpyHostToDevice, ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
-    d.tick_kind = 1;
-    return 1;
+    d.tick_kind = ctx->use_sb ? 3 : 1;
+    return d.tick_kind;
   }
   // Dalitz: only with every shape fixed (Gram normalisation) and the caches built
   const DalitzPlan& D = ctx->dplan;

@@ -74,7 +74,9 @@ struct DevState {
   bool graph_off = false;             // a capture failed: launch directly from then on
   std::string graph_why;              // why (for gf_last_eval_graph)
   void* tick_desc = nullptr;          // Fit1D / FitDz for batched ticks (device)
-  int tick_kind = 0;                  // 0: none, 1: 1D, 2: Dalitz (Gram normalisation)
+  int tick_kind = 0;                  // 0: none, 1: 1D, 2: Dalitz (Gram normalisation),
+                                      // 3: 1D signal + background (FitSB after the Fit1D,
+                                      // 256-byte aligned)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;  // eval start, stream kernel, end
   int* flag = nullptr;                // device-side data check (0 = ok)
   // sorted layout of owned 1D columns (ascending by the first Voigtian's observable)

@@ -228,6 +228,18 @@ struct FitDz {
   int pad;
 };
 
+// A signal + background fit in the batched tick (k_sigbkg.cu).
+struct FitSB {
+  SigBkgDesc D;
+  const double* x;
+  int64_t n;
+  double* derived;
+  double* partials;
+  unsigned* counter;
+  int32_t sorted;
+  int32_t pad;
+};
+
 struct TickItem {
   const void* fit;       // Fit1D* or FitDz* (device)
   const double* theta;   // this fit's theta_all for this tick (device)

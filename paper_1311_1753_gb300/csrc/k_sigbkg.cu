@@ -183,6 +183,11 @@ __device__ __forceinline__ void faddeeva_f32(float x, float y, const WeidCoef& W
 // c3 = 1/(sigma sqrt(2 pi) N); threshold c0 = x0, c1 = p, c2 = c, c3 = 1/N.
 struct SBConst {
   double mu, x0, c1, y, c3v, pw, cc, c3t, cv, ct;
+  // the mixed plan's split P = ref (ca Re w + cb t^p e^{-c t}), ref > 0 (0: P = 0), one of
+  // ca, cb exactly 1: every constant that scales all events stays in FP64 (ref and its log
+  // enter the sums once per chunk), so FP32 rounding leaves no theta-dependent bias common
+  // to all events
+  double ref, lref, ca, cb;
   int half;  // p == 1/2 and no gradient in p: sqrt(t) instead of exp(p log t)
 };
 __device__ __forceinline__ void sb_consts(const SigBkgDesc& D, const double* __restrict__ der,
@@ -200,6 +205,17 @@ __device__ __forceinline__ void sb_consts(const SigBkgDesc& D, const double* __r
   K.cv = der[kMaxLeaf * kLeafRec + D.cslot_v];
   K.ct = der[kMaxLeaf * kLeafRec + D.cslot_t];
   K.half = (K.pw == 0.5 && !(grad && D.gt[1] >= 0)) ? 1 : 0;
+  const double kv = K.cv * K.c3v, kt = K.ct * K.c3t;
+  double ref = fabs(kv) >= fabs(kt) ? kv : kt;
+  K.ca = ref != 0.0 ? kv / ref : 0.0;
+  K.cb = ref != 0.0 ? kt / ref : 0.0;
+  if (ref < 0.0) {
+    ref = -ref;
+    K.ca = -K.ca;
+    K.cb = -K.cb;
+  }
+  K.ref = ref;
+  K.lref = log(ref);
 }
 
 // One event in FP64 (P outside the float-safe range): log P and the moments' terms.
@@ -265,22 +281,26 @@ __device__ void sb_finish(const SigBkgDesc& D, const double* __restrict__ der, c
 
 // ---- the kernel -------------------------------------------------------------------------------
 // STORE: log P_i into out_logp[perm ? perm[i] : i] instead of the sums.
+// Shared scratch of one block.
+struct SBShared {
+  SBConst K;
+  double red[(kSBThreads / 32) * kSBMom];
+  double fin[kSBMom];
+  int last;
+};
+
+// Body of one (virtual) block vb of a launch of vgrid blocks over one data set; the last
+// block to arrive finishes the reduction.  sorted: the events are sorted ascending by x.
 template <bool G, bool MIXED, bool STORE>
-__global__ void __launch_bounds__(kSBThreads) k_sigbkg(
-    const __grid_constant__ SigBkgDesc D, const __grid_constant__ WeidCoef W,
-    const Program* __restrict__ prog, const double* __restrict__ xcol, const int64_t n,
-    const double* __restrict__ der,
-    double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
-    double* __restrict__ out_logp, const int32_t* __restrict__ perm) {
-  __shared__ SBConst Ks;
-  __shared__ double red[(kSBThreads / 32) * kSBMom];
-  __shared__ double fin[kSBMom];
-  __shared__ int last;
+__device__ __forceinline__ void sigbkg_block(
+    const SigBkgDesc& D, const WeidCoef& W, const int sorted, const double* __restrict__ xcol,
+    const int64_t n, const double* __restrict__ der, double* __restrict__ partials,
+    unsigned* __restrict__ counter, double* __restrict__ result, double* __restrict__ out_logp,
+    const int32_t* __restrict__ perm, const int vb, const int vgrid, SBShared& sh) {
   const int tid = threadIdx.x;
-  load_df_tables();
-  if (tid == 0) sb_consts(D, der, G, Ks);
+  if (tid == 0) sb_consts(D, der, G, sh.K);
   __syncthreads();
-  const SBConst& K = Ks;
+  const SBConst& K = sh.K;
 
   Lazy acc;            // sum log P
   Lazy m[kSBMom - 1];  // moments SB_S .. SB_BL
@@ -302,11 +322,11 @@ __global__ void __launch_bounds__(kSBThreads) k_sigbkg(
       for (int k = 1; k < kSBMom; ++k) m[k - 1].add(df_from(o[k]));
   };
 
-  const int64_t nthreads = (int64_t)gridDim.x * kSBThreads;
-  const int64_t g = (int64_t)blockIdx.x * kSBThreads + tid;
+  const int64_t nthreads = (int64_t)vgrid * kSBThreads;
+  const int64_t g = (int64_t)vb * kSBThreads + tid;
   constexpr int kChunk = MIXED ? kSBChunk32 : kSBChunk64;
   // sorted events and at least 8 per thread: one expansion of w per chunk pays
-  const bool chunked = prog->sorted && n >= 8 * nthreads;
+  const bool chunked = sorted && n >= 8 * nthreads;
 
   if constexpr (!MIXED) {
     // ---------------- FP64 plan: pairs ----------------
@@ -397,11 +417,15 @@ __global__ void __launch_bounds__(kSBThreads) k_sigbkg(
   } else {
     // ---------------- mixed plan: FP32 per event ----------------
     const F2 mu2 = df_split(K.mu), x02 = df_split(K.x0);
-    const float c1 = (float)K.c1, y = (float)K.y, c3v = (float)K.c3v;
-    const float pw = (float)K.pw, cc = (float)K.cc, c3t = (float)K.c3t;
-    const float cv = (float)K.cv, ct = (float)K.ct;
-    const F2 c1p = df_from(K.c1), yp = df_from(K.y);
+    const float y = (float)K.y;
+    // constants that multiply per-event values as pairs (one extra FMA each): the float
+    // result then carries per-event rounding only
+    const F2 c1p = df_from(K.c1), yp = df_from(K.y), ccp = df_from(K.cc), pwp = df_from(K.pw);
+    const F2 cap = df_from(K.ca), cbp = df_from(K.cb);
+    const F2 sv = df_from(1.0 / K.ref), st = df_from(K.c3t / K.ref), lref = df_from(K.lref);
+    auto kmul = [](float a, F2 c) { return __fmaf_rn(a, c.hi, __fmul_rn(a, c.lo)); };
     ProdF prod;
+    int pcount = 0;  // events in the running product
     float cm[kSBMom - 1];
 #pragma unroll
     for (int k = 0; k < kSBMom - 1; ++k) cm[k] = 0.f;
@@ -420,22 +444,23 @@ __global__ void __launch_bounds__(kSBThreads) k_sigbkg(
       float B = 0.f, lt = 0.f;
       if (t > 0.f) {
         if (half) {
-          B = __fmul_rn(__fmul_rn(__fsqrt_rn(t), __expf(-cc * t)), c3t);
+          B = __fmul_rn(__fsqrt_rn(t), __expf(-kmul(t, ccp)));
         } else {
           lt = __logf(t);
-          B = __fmul_rn(__expf(__fmaf_rn(pw, lt, -cc * t)), c3t);
+          B = __expf(kmul(lt, pwp) - kmul(t, ccp));
         }
       }
-      const float P = __fmaf_rn(cv, __fmul_rn(c3v, wr), __fmul_rn(ct, B));
+      const float P = __fadd_rn(kmul(wr, cap), kmul(B, cbp));  // P / ref
       if (!(P >= 8.271806125530277e-25f && P < 4.2535295865117308e37f)) {
         fallback(i, xi);
         return;
       }
       if (STORE) {
-        out_logp[perm ? perm[i] : i] = (double)logf(P);
+        out_logp[perm ? perm[i] : i] = (double)logf(P) + K.lref;
         return;
       }
       prod.mul(P);
+      ++pcount;
       if (G) {
         const float s = __frcp_rn(P);
         const float a = s * wr, b = s * wi, za = zr * a;
@@ -454,15 +479,19 @@ __global__ void __launch_bounds__(kSBThreads) k_sigbkg(
         }
       }
     };
+    // chunk end: log of the product plus its events' log(ref); the float sums of the chunk
+    // in units of 1/ref (Voigtian terms) and c3t/ref (background terms) folded into pairs
     auto flush = [&]() {
       if (STORE) return;
       acc.add(prod.log());
+      if (pcount) acc.add(df_mul_f(lref, (float)pcount));
       prod = ProdF();
+      pcount = 0;
       acc.norm();
       if (G)
 #pragma unroll
         for (int k = 0; k < kSBMom - 1; ++k) {
-          m[k].add_f(cm[k]);
+          m[k].add(df_mul_f(k + 1 < SB_B ? sv : st, cm[k]));
           m[k].norm();
           cm[k] = 0.f;
         }
@@ -476,7 +505,7 @@ __global__ void __launch_bounds__(kSBThreads) k_sigbkg(
         const F2 z0 = df_mul(df_split(xm - K.mu), c1p);
         const float z0f = __fadd_rn(z0.hi, z0.lo);
         auto dzof = [&](F2 xs) {
-          return __fmul_rn(__fadd_rn(__fsub_rn(xs.hi, xms.hi), __fsub_rn(xs.lo, xms.lo)), c1);
+          return kmul(__fadd_rn(__fsub_rn(xs.hi, xms.hi), __fsub_rn(xs.lo, xms.lo)), c1p);
         };
         const float da = fabsf(dzof(df_split(__ldg(xcol + c0))));
         const float db = fabsf(dzof(df_split(__ldg(xcol + c0 + cnt - 1))));
@@ -503,7 +532,7 @@ __global__ void __launch_bounds__(kSBThreads) k_sigbkg(
       for (int64_t i = g; i < n; i += nthreads) {
         const double xi = __ldcs(xcol + i);
         const F2 xs = df_split(xi);
-        const float zr = __fmul_rn(__fadd_rn(__fsub_rn(xs.hi, mu2.hi), __fsub_rn(xs.lo, mu2.lo)), c1);
+        const float zr = kmul(__fadd_rn(__fsub_rn(xs.hi, mu2.hi), __fsub_rn(xs.lo, mu2.lo)), c1p);
         one(i, xi, xs, zr, 0.f, false);
         if (++since == kSBChunk32) {
           flush();
@@ -522,19 +551,48 @@ __global__ void __launch_bounds__(kSBThreads) k_sigbkg(
   vals[0] = acc.get();
 #pragma unroll
   for (int k = 1; k < kSBMom; ++k) vals[k] = m[k - 1].get();
-  block_sum_pairs([&](int k) -> F2 { return vals[k]; }, mm, red,
-                  partials + (size_t)blockIdx.x * stride);
-  if (!arrive_last_of(counter, gridDim.x, &last)) return;
-  reduce_partials(partials, gridDim.x, stride, mm, fin);
+  block_sum_pairs([&](int k) -> F2 { return vals[k]; }, mm, sh.red,
+                  partials + (size_t)vb * stride);
+  if (!arrive_last_of(counter, (unsigned)vgrid, &sh.last)) return;
+  reduce_partials(partials, vgrid, stride, mm, sh.fin);
   if (tid == 0) {
-    sb_finish(D, der, fin, G, result);
+    sb_finish(D, der, sh.fin, G, result);
     *counter = 0u;
   }
 }
 
 template <bool G, bool MIXED, bool STORE>
-const void* sb_kernel() {
-  return (const void*)k_sigbkg<G, MIXED, STORE>;
+__global__ void __launch_bounds__(kSBThreads) k_sigbkg(
+    const __grid_constant__ SigBkgDesc D, const __grid_constant__ WeidCoef W,
+    const Program* __restrict__ prog, const double* __restrict__ xcol, const int64_t n,
+    const double* __restrict__ der, double* __restrict__ partials,
+    unsigned* __restrict__ counter, double* __restrict__ result, double* __restrict__ out_logp,
+    const int32_t* __restrict__ perm) {
+  __shared__ SBShared sh;
+  load_df_tables();  // visible after the block body's first barrier
+  sigbkg_block<G, MIXED, STORE>(D, W, prog->sorted, xcol, n, der, partials, counter, result,
+                                out_logp, perm, blockIdx.x, gridDim.x, sh);
+}
+
+// The fit server's batched tick: every waiting signal + background fit in one persistent
+// launch; item it of the work list is virtual block it - item0 of its fit, which processes
+// the events of the fit's standalone block of that index (the same bits alone or batched).
+template <bool MIXED>
+__global__ void __launch_bounds__(kSBThreads) k_tick_sigbkg(const TickItem* __restrict__ items,
+                                                            int nfits, int total,
+                                                            const __grid_constant__ WeidCoef W) {
+  __shared__ SBShared sh;
+  load_df_tables();
+  for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    int f = 0;
+    while (f + 1 < nfits && items[f + 1].item0 <= it) ++f;
+    const TickItem& ti = items[f];
+    const FitSB* F = static_cast<const FitSB*>(ti.fit);
+    sigbkg_block<true, MIXED, false>(F->D, W, F->sorted, F->x, F->n, F->derived, F->partials,
+                                     F->counter, ti.result, nullptr, nullptr, it - ti.item0,
+                                     ti.nitems, sh);
+    __syncthreads();
+  }
 }
 
 }  // namespace
@@ -548,6 +606,14 @@ int sigbkg_blocks_per_sm(bool mixed) {
 }
 
 int sigbkg_threads() { return kSBThreads; }
+
+cudaError_t launch_tick_sigbkg(bool mixed, const TickItem* items, int nfits, int total,
+                               const WeidCoef& W, int grid, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  if (mixed) k_tick_sigbkg<true><<<grid, kSBThreads, 0, st>>>(items, nfits, total, W);
+  else k_tick_sigbkg<false><<<grid, kSBThreads, 0, st>>>(items, nfits, total, W);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sigbkg(const SigBkgDesc& D, const WeidCoef& W, const Program* prog,
                           const double* x, int64_t n,

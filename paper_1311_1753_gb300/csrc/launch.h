@@ -53,6 +53,9 @@ cudaError_t launch_sigbkg(const SigBkgDesc& D, const WeidCoef& W, const Program*
                           double* result, double* out_logp, const int32_t* perm, bool grad,
                           bool mixed, int nblocks, cudaStream_t st);
 int sigbkg_blocks_per_sm(bool mixed);
+// batched tick of signal + background fits (TickItem.fit -> FitSB)
+cudaError_t launch_tick_sigbkg(bool mixed, const TickItem* items, int nfits, int total,
+                               const WeidCoef& W, int grid, cudaStream_t st);
 int sigbkg_threads();
 cudaError_t prepare_kernels_sigbkg();
 // loads the allocation-free entry point's module (its static scratch array)

@@ -54,17 +54,18 @@ struct Req {
 
 }  // namespace
 
-// Device and pinned buffers of the batched tick: the work lists of the three launches,
+// Device and pinned buffers of the batched tick: the work lists of the four launches,
 // every batched fit's theta_all, and their results.
 struct TickBufs {
   int cap_fits = 0, cap_par = 0;
-  TickItem* h_items = nullptr;  // [3][cap_fits]: 1D norm, 1D events, Dalitz events
+  TickItem* h_items = nullptr;  // [4][cap_fits]: 1D norm, 1D events, Dalitz events,
+                                //   signal + background events
   double* h_theta = nullptr;    // [cap_fits][cap_par]
   double* h_res = nullptr;      // [cap_fits][64]
   void* d_block = nullptr;      // device mirror of items + theta
   double* d_res = nullptr;
   cudaStream_t st = nullptr;
-  size_t bytes_items() const { return sizeof(TickItem) * 3 * cap_fits; }
+  size_t bytes_items() const { return sizeof(TickItem) * 4 * cap_fits; }
   size_t bytes_theta() const { return sizeof(double) * (size_t)cap_fits * cap_par; }
 };
 
@@ -122,7 +123,7 @@ static void fit_thread(gf_server* S, std::shared_ptr<Req> R) {
     return R->eval_rc;
     };
   };
-  const bool refine = R->ctx->precision == GF_MIXED && R->ctx->is_dalitz &&
+  const bool refine = R->ctx->precision == GF_MIXED && (R->ctx->is_dalitz || R->ctx->use_sb) &&
                       (!R->has_opts || R->opts.refine != 0);
   FGFun fg_fast = make_fg(false), fg_exact = make_fg(R->ctx->precision == GF_MIXED);
   MinResult m = refine ? minimise_refined(&fg_fast, fg_exact, x0, step, lo, hi, mo)
@@ -136,8 +137,8 @@ static void fit_thread(gf_server* S, std::shared_ptr<Req> R) {
 }
 
 // One batched tick for fits with a tick descriptor: one host-to-device copy of the work
-// lists and theta, the persistent launches (1D normalisation, 1D events, Dalitz events),
-// one device-to-host copy of the results.  Returns the number of kernel launches.
+// lists and theta, the persistent launches (1D normalisation, 1D events, signal +
+// background events, Dalitz events), one device-to-host copy of the results.  Returns the number of kernel launches.
 static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
   TickBufs& T = S->tb;
   int maxpar = 1;
@@ -167,9 +168,11 @@ static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
   TickItem* it_norm = T.h_items;
   TickItem* it_ev1 = T.h_items + T.cap_fits;
   TickItem* it_dz = T.h_items + 2 * T.cap_fits;
+  TickItem* it_sb = T.h_items + 3 * T.cap_fits;
   TickItem* d_items = static_cast<TickItem*>(T.d_block);
   double* d_theta = reinterpret_cast<double*>(static_cast<char*>(T.d_block) + T.bytes_items());
-  int n_norm = 0, n_ev1 = 0, n_dz = 0, tot_norm = 0, tot_ev1 = 0, tot_dz = 0;
+  int n_norm = 0, n_ev1 = 0, n_dz = 0, n_sb = 0, tot_norm = 0, tot_ev1 = 0, tot_dz = 0,
+      tot_sb = 0;
   int nfd = 0;
   size_t smem1 = 0;  // the largest per-block scratch of the batched 1D programs
   for (int j = 0; j < nfit; ++j) {
@@ -177,14 +180,21 @@ static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
     fill_theta_all(c, fits[j]->theta.data(), T.h_theta + (size_t)j * T.cap_par);
     const double* th = d_theta + (size_t)j * T.cap_par;
     double* res = T.d_res + 64 * j;
-    if (c->dev.tick_kind == 1) {
+    if (c->dev.tick_kind == 1 || c->dev.tick_kind == 3) {
       if (c->has_grid) {
         it_norm[n_norm++] = TickItem{c->dev.tick_desc, th, res, tot_norm, c->prog.ngrid_blocks};
         tot_norm += c->prog.ngrid_blocks;
       }
-      it_ev1[n_ev1++] = TickItem{c->dev.tick_desc, th, res, tot_ev1, c->dev.nblocks};
-      tot_ev1 += c->dev.nblocks;
-      smem1 = std::max(smem1, events_1d_smem(c->prog, true, kThreads1D));
+      if (c->dev.tick_kind == 3) {
+        const void* fsb = static_cast<const char*>(c->dev.tick_desc) +
+                          ((sizeof(Fit1D) + 255) / 256) * 256;
+        it_sb[n_sb++] = TickItem{fsb, th, res, tot_sb, c->dev.nblocks};
+        tot_sb += c->dev.nblocks;
+      } else {
+        it_ev1[n_ev1++] = TickItem{c->dev.tick_desc, th, res, tot_ev1, c->dev.nblocks};
+        tot_ev1 += c->dev.nblocks;
+        smem1 = std::max(smem1, events_1d_smem(c->prog, true, kThreads1D));
+      }
     } else {
       it_dz[n_dz++] = TickItem{c->dev.tick_desc, th, res, tot_dz, c->dev.nblocks};
       tot_dz += c->dev.nblocks;
@@ -205,6 +215,11 @@ static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
   }
   if (e == cudaSuccess && n_ev1) {
     e = launch_tick_1d(false, d_items + T.cap_fits, n_ev1, tot_ev1, W, smem1, grid, st);
+    ++nl;
+  }
+  if (e == cudaSuccess && n_sb) {
+    e = launch_tick_sigbkg(S->opts.precision == GF_MIXED, d_items + 3 * T.cap_fits, n_sb, tot_sb,
+                           W, grid, st);
     ++nl;
   }
   if (e == cudaSuccess && n_dz) {

@@ -75,9 +75,10 @@ def test_server_alone_equals_mix(gf, precision):
     srv.drain()
     st = srv.stats()
     assert 1 <= st["peak_slots"] <= 4 and st["ticks"] > 0
-    # after its first evaluation every fit joins the batched tick: at most three
-    # persistent launches (1D normalisation, 1D events, Dalitz events) per tick
-    assert st["launches"] <= 3 * st["ticks"] + 2 * len(reqs) * 4, st
+    # after its first evaluation every fit joins the batched tick: at most four
+    # persistent launches (1D normalisation, 1D events, signal + background events,
+    # Dalitz events) per tick
+    assert st["launches"] <= 4 * st["ticks"] + 2 * len(reqs) * 4, st
     for a, t in zip(alone, tickets):
         r = srv.poll(t)
         assert r is not None and r["status"] == gf.GF_OK
