@@ -42,9 +42,17 @@ namespace {
 
 constexpr int kSBThreads = 128;
 constexpr int kSBChunk64 = 24;     // FP64 plan: events per expansion of w
+constexpr int kSBSub64 = 6;        // ... and per sub-chunk of a chunk too wide for one
 constexpr float kSBLim64 = 3e-4f;  // largest |Re z - Re z0| of an expanded chunk (FP64 plan)
 constexpr int kSBChunk32 = 96;     // mixed plan
+constexpr int kSBSub32 = 24;
+// mixed plan: largest |Re z - Re z0| at |Re z0| < 0.6 (the Cauchy bound |t_k| <= 6 on the
+// unit circle around z0: degree-4 truncation below 6 d^5 ~ 1.5e-12), and a wider one,
+// 0.005 |Re z0|, for |z0| >= 2, where |w| <= 1.2/|z0| on the circle of radius |z0|/2
+// gives |t_k| <= (1.2/|z0|)(2/|z0|)^k and a truncation below 1.2/|z0| (0.01)^5, i.e.
+// 2e-9 |z0| relative to Re w >= 0.05 y/|z0|^2 (y = 0.094 here): FP32-level
 constexpr float kSBLim32 = 3e-3f;
+constexpr float kSBLim32Rel = 5e-3f;
 constexpr int kSBFlush = 32;       // unsorted loop: events per log of the running product
 constexpr int kSBMom = 11;         // reduced values: sum log P and ten moments
 
@@ -90,11 +98,6 @@ struct Lazy {
     const F2 s = two_sum(hi, v.hi);
     hi = s.hi;
     lo = __fadd_rn(lo, __fadd_rn(s.lo, v.lo));
-  }
-  __device__ __forceinline__ void add_f(float v) {
-    const F2 s = two_sum(hi, v);
-    hi = s.hi;
-    lo = __fadd_rn(lo, s.lo);
   }
   __device__ __forceinline__ void norm() {
     const F2 s = fast_two_sum(hi, lo);
@@ -176,6 +179,16 @@ __device__ __forceinline__ void faddeeva_f32(float x, float y, const WeidCoef& W
   const float qr = __fmaf_rn(ir, ir, -ii * ii), qi = 2.f * ir * ii;
   wr = __fmaf_rn(0.56418958354775628695f, ir, 2.f * __fmaf_rn(pr, qr, -pi * qi));
   wi = __fmaf_rn(0.56418958354775628695f, ii, 2.f * __fmaf_rn(pr, qi, pi * qr));
+}
+
+// Direct evaluations out of line: after the sub-chunking below they are the rare path, and
+// inline their code would be repeated in every unrolled copy of the event body.
+__device__ __noinline__ void w_direct_f2(F2 x, F2 y, const WeidCoef& W, F2& wr, F2& wi) {
+  faddeeva_f2(x, y, W, wr, wi);
+}
+__device__ __noinline__ void w_direct_f32(float x, float y, const WeidCoef& W, float& wr,
+                                          float& wi) {
+  faddeeva_f32(x, y, W, wr, wi);
 }
 
 // ---- constants of one evaluation -------------------------------------------------------------
@@ -339,7 +352,7 @@ __device__ __forceinline__ void sigbkg_block(
       const F2 zr = df_mul(df_split(xi - K.mu), c1);
       F2 wr, wi;
       if (tay) tayp_eval(T, zr, wr, wi);
-      else faddeeva_f2(zr, y, W, wr, wi);
+      else w_direct_f2(zr, y, W, wr, wi);
       const double td = xi - K.x0;
       F2 B = {0.f, 0.f}, t = {0.f, 0.f}, lt = {0.f, 0.f};
       if (td > 0.0) {
@@ -392,15 +405,38 @@ __device__ __forceinline__ void sigbkg_block(
     if (chunked) {
       // thread g: the contiguous share [n g / T, n (g + 1) / T) of the sorted events, in
       // chunks of kChunk with one expansion of w per chunk
+      // (a chunk too wide for one expansion is taken as sub-chunks of kSBSub64 with one
+      // each, and only a sub-chunk still too wide -- the sparsest edge of the data --
+      // evaluates w per event: the threads' shares then cost about the same)
       const int64_t lo = n * g / nthreads, hi = n * (g + 1) / nthreads;
-      for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
-        const int cnt = (int)(hi - c0 < kChunk ? hi - c0 : kChunk);
-        const double xm = __ldg(xcol + c0 + (cnt - 1) / 2);
-        const float da = fabsf(__fmul_rn((float)(__ldg(xcol + c0) - xm), c1.hi));
-        const float db = fabsf(__fmul_rn((float)(__ldg(xcol + c0 + cnt - 1) - xm), c1.hi));
+      auto expand = [&](int64_t a, int c) {  // expansion for events a .. a + c - 1, if narrow
+        const double xm = __ldg(xcol + a + (c - 1) / 2);
+        const float da = fabsf(__fmul_rn((float)(__ldg(xcol + a) - xm), c1.hi));
+        const float db = fabsf(__fmul_rn((float)(__ldg(xcol + a + c - 1) - xm), c1.hi));
         const bool ok = fmaxf(da, db) <= kSBLim64;
         if (ok) tayp_build(T, df_mul(df_split(xm - K.mu), c1), y, W);
-        for (int k = 0; k < cnt; ++k) one(c0 + k, __ldg(xcol + c0 + k), ok);
+        return ok;
+      };
+      auto run = [&](int64_t a, int c, bool tay) {  // the loads of 4 events in flight at once
+        for (int k = 0; k < c; k += 4) {
+          double xv[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) xv[j] = k + j < c ? __ldg(xcol + a + k + j) : 0.0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (k + j < c) one(a + k + j, xv[j], tay);
+        }
+      };
+      for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
+        const int cnt = (int)(hi - c0 < kChunk ? hi - c0 : kChunk);
+        if (expand(c0, cnt)) {
+          run(c0, cnt, true);
+        } else {
+          for (int s0 = 0; s0 < cnt; s0 += kSBSub64) {
+            const int sc = cnt - s0 < kSBSub64 ? cnt - s0 : kSBSub64;
+            run(c0 + s0, sc, expand(c0 + s0, sc));
+          }
+        }
         flush();
       }
     } else {
@@ -438,7 +474,7 @@ __device__ __forceinline__ void sigbkg_block(
         wr = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(T[4], dz, T[3]), dz, T[2]), dz, T[1]), dz, T[0]);
         wi = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(T[9], dz, T[8]), dz, T[7]), dz, T[6]), dz, T[5]);
       } else {
-        faddeeva_f32(zr, y, W, wr, wi);
+        w_direct_f32(zr, y, W, wr, wi);
       }
       const float t = __fadd_rn(__fsub_rn(xs.hi, x02.hi), __fsub_rn(xs.lo, x02.lo));
       float B = 0.f, lt = 0.f;
@@ -498,18 +534,22 @@ __device__ __forceinline__ void sigbkg_block(
     };
     if (chunked) {
       const int64_t lo = n * g / nthreads, hi = n * (g + 1) / nthreads;
-      for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
-        const int cnt = (int)(hi - c0 < kChunk ? hi - c0 : kChunk);
-        const double xm = __ldg(xcol + c0 + (cnt - 1) / 2);
-        const F2 xms = df_split(xm);
+      F2 xms = {0.f, 0.f};
+      float z0f = 0.f;
+      auto dzof = [&](F2 xs) {
+        return kmul(__fadd_rn(__fsub_rn(xs.hi, xms.hi), __fsub_rn(xs.lo, xms.lo)), c1p);
+      };
+      // expansion (degree 4, float coefficients from the pair series) for events a ..
+      // a + c - 1 when they lie close enough to the middle one
+      auto expand = [&](int64_t a, int c) {
+        const double xm = __ldg(xcol + a + (c - 1) / 2);
+        xms = df_split(xm);
         const F2 z0 = df_mul(df_split(xm - K.mu), c1p);
-        const float z0f = __fadd_rn(z0.hi, z0.lo);
-        auto dzof = [&](F2 xs) {
-          return kmul(__fadd_rn(__fsub_rn(xs.hi, xms.hi), __fsub_rn(xs.lo, xms.lo)), c1p);
-        };
-        const float da = fabsf(dzof(df_split(__ldg(xcol + c0))));
-        const float db = fabsf(dzof(df_split(__ldg(xcol + c0 + cnt - 1))));
-        const bool ok = fmaxf(da, db) <= kSBLim32;
+        z0f = __fadd_rn(z0.hi, z0.lo);
+        const float da = fabsf(dzof(df_split(__ldg(xcol + a))));
+        const float db = fabsf(dzof(df_split(__ldg(xcol + a + c - 1))));
+        const float az = fabsf(z0f);
+        const bool ok = fmaxf(da, db) <= (az >= 2.f ? fmaxf(kSBLim32, kSBLim32Rel * az) : kSBLim32);
         if (ok) {
           F2 tr[5], ti[5];
           tay_coefs<4>(z0, yp, W, tr, ti);
@@ -519,11 +559,37 @@ __device__ __forceinline__ void sigbkg_block(
             T[5 + k] = __fadd_rn(ti[k].hi, ti[k].lo);
           }
         }
-        for (int k = 0; k < cnt; ++k) {
-          const double xi = __ldg(xcol + c0 + k);
-          const F2 xs = df_split(xi);
-          const float dz = dzof(xs);
-          one(c0 + k, xi, xs, __fadd_rn(z0f, dz), dz, ok);
+        return ok;
+      };
+      auto run = [&](int64_t a, int c, bool tay) {  // the loads of 4 events in flight at once
+        for (int k = 0; k < c; k += 4) {
+          double xv[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) xv[j] = k + j < c ? __ldg(xcol + a + k + j) : 0.0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (k + j < c) {
+              const F2 xs = df_split(xv[j]);
+              const float dz = dzof(xs);
+              if (tay) {
+                one(a + k + j, xv[j], xs, __fadd_rn(z0f, dz), dz, true);
+              } else {
+                const float zr =
+                    kmul(__fadd_rn(__fsub_rn(xs.hi, mu2.hi), __fsub_rn(xs.lo, mu2.lo)), c1p);
+                one(a + k + j, xv[j], xs, zr, 0.f, false);
+              }
+            }
+        }
+      };
+      for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
+        const int cnt = (int)(hi - c0 < kChunk ? hi - c0 : kChunk);
+        if (expand(c0, cnt)) {
+          run(c0, cnt, true);
+        } else {
+          for (int s0 = 0; s0 < cnt; s0 += kSBSub32) {
+            const int sc = cnt - s0 < kSBSub32 ? cnt - s0 : kSBSub32;
+            run(c0 + s0, sc, expand(c0 + s0, sc));
+          }
         }
         flush();
       }
@@ -562,7 +628,7 @@ __device__ __forceinline__ void sigbkg_block(
 }
 
 template <bool G, bool MIXED, bool STORE>
-__global__ void __launch_bounds__(kSBThreads) k_sigbkg(
+__global__ void __launch_bounds__(kSBThreads, 4) k_sigbkg(
     const __grid_constant__ SigBkgDesc D, const __grid_constant__ WeidCoef W,
     const Program* __restrict__ prog, const double* __restrict__ xcol, const int64_t n,
     const double* __restrict__ der, double* __restrict__ partials,
@@ -578,7 +644,7 @@ __global__ void __launch_bounds__(kSBThreads) k_sigbkg(
 // launch; item it of the work list is virtual block it - item0 of its fit, which processes
 // the events of the fit's standalone block of that index (the same bits alone or batched).
 template <bool MIXED>
-__global__ void __launch_bounds__(kSBThreads) k_tick_sigbkg(const TickItem* __restrict__ items,
+__global__ void __launch_bounds__(kSBThreads, 4) k_tick_sigbkg(const TickItem* __restrict__ items,
                                                             int nfits, int total,
                                                             const __grid_constant__ WeidCoef W) {
   __shared__ SBShared sh;
