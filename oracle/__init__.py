@@ -367,7 +367,9 @@ class Dalitz:
 
 
 class OrcTpar(C.Structure):
-    _fields_ = [("p_tau", C.c_int32), ("p_x", C.c_int32), ("p_y", C.c_int32), ("p_s", C.c_int32)]
+    _fields_ = [("p_tau", C.c_int32), ("p_x", C.c_int32), ("p_y", C.c_int32), ("p_s", C.c_int32),
+                ("dens", C.c_int32), ("p_b0", C.c_int32), ("p_b1", C.c_int32),
+                ("p_b2", C.c_int32), ("slo", C.c_double), ("shi", C.c_double)]
 
 
 def _tddp_lib():
@@ -380,6 +382,8 @@ def _tddp_lib():
         so.orc_tddp_norm.argtypes = args + [C.c_int, C.c_int, _D]
         so.orc_tddp_norm.restype = C.c_double
         so.orc_tddp_nll.argtypes = args + [C.c_int, C.c_int, C.c_int64, _D, _D, _D, _D, _D, _D]
+        so.orc_sigt_logd_many.argtypes = [C.POINTER(OrcDkin), C.POINTER(OrcTpar), _D, C.c_int64,
+                                          _D, _D, _D, _D, _D]
         so._tddp_ready = True
     return so
 
@@ -402,8 +406,25 @@ class Tddp(Dalitz):
         super().__init__(M, m1, m2, m3, R, nbx, nby)
         self.tp = None
 
-    def time_params(self, tau, x, y, scale):
-        self.tp = OrcTpar(tau, x, y, scale)
+    def time_params(self, tau, x, y, scale, density=None, sigt_range=(0.0, 1.0)):
+        """density: (b0, b1, b2) parameter indices of the sigma_t density (a Gamma(2)
+        distribution on sigt_range with rate exp(b0 + b1 (s12 - sc) + b2 (s13 - sc))),
+        or None for the likelihood conditional on sigma_t."""
+        if density is None:
+            self.tp = OrcTpar(tau, x, y, scale, 0, 0, 0, 0, *sigt_range)
+        else:
+            self.tp = OrcTpar(tau, x, y, scale, 1, *density, *sigt_range)
+
+    def sigt_logd(self, s12, s13, sigt, p=None, grad=False):
+        """log of the sigma_t density at each event (and its gradient in b0, b1, b2)."""
+        p = self.p if p is None else _f64(p)
+        s12, s13, sigt = (_f64(v) for v in (s12, s13, sigt))
+        out = np.empty_like(s12)
+        g = np.empty(3 * len(s12)) if grad else None
+        _tddp_lib().orc_sigt_logd_many(C.byref(self.kin), C.byref(self.tp), _dp(p), len(s12),
+                                        _dp(s12), _dp(s13), _dp(sigt), _dp(out),
+                                        _dp(g) if grad else None)
+        return (out, g.reshape(-1, 3)) if grad else out
 
     def _args(self, p):
         p = self.p if p is None else _f64(p)

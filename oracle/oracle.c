@@ -1077,7 +1077,47 @@ double orc_zemach_at(const orc_dkin* k, int ch, int L, double s12, double s13) {
 
 typedef struct {
   int32_t p_tau, p_x, p_y, p_s;
+  int32_t dens;            /* 1: the sigma_t density below is part of the PDF          */
+  int32_t p_b0, p_b1, p_b2; /* its parameters                                           */
+  double slo, shi;         /* the sigma_t range                                        */
 } orc_tpar;
+
+/* ------------------------------------------------------------------------------ */
+/* The decay-time uncertainty's density (Sec. 4: the sigma_t distribution of the    */
+/* mixing fit varies across the Dalitz plot; the paper gives no form).  Reading: a  */
+/* Gamma distribution of shape 2 truncated to [slo, shi], whose rate varies         */
+/* log-linearly over the plot:                                                       */
+/*   D(st | s12, s13) = lam^2 st e^{-lam st} / Z(lam),                               */
+/*   lam = exp(b0 + b1 (s12 - sc) + b2 (s13 - sc)),  sc = (M^2 + m1^2 + m2^2 + m3^2)/3, */
+/*   Z = g(lam slo) - g(lam shi),  g(a) = e^{-a} (1 + a)  (the integral of the shape). */
+/* The full PDF is I/N times D: D integrates to one over st at every point, so the  */
+/* product is normalised over (s12, s13, t, st).                                     */
+/* ------------------------------------------------------------------------------ */
+static double sigt_logd(const orc_dkin* k, const orc_tpar* tp, const double* p, double s12,
+                        double s13, double st, double* g3) {
+  double sc = (k->M * k->M + k->m1 * k->m1 + k->m2 * k->m2 + k->m3 * k->m3) / 3.0;
+  double u = s12 - sc, v = s13 - sc;
+  double ll = p[tp->p_b0] + p[tp->p_b1] * u + p[tp->p_b2] * v;
+  double lam = exp(ll);
+  double el = exp(-lam * tp->slo), eh = exp(-lam * tp->shi);
+  double Z = el * (1.0 + lam * tp->slo) - eh * (1.0 + lam * tp->shi);
+  if (g3) {
+    /* dZ/dlam = -lam slo^2 e^{-lam slo} + lam shi^2 e^{-lam shi} */
+    double dZ = -lam * tp->slo * tp->slo * el + lam * tp->shi * tp->shi * eh;
+    double dl = 2.0 / lam - st - dZ / Z; /* d log D / d lam */
+    g3[0] = dl * lam;
+    g3[1] = dl * lam * u;
+    g3[2] = dl * lam * v;
+  }
+  return 2.0 * ll + log(st) - lam * st - log(Z);
+}
+
+void orc_sigt_logd_many(const orc_dkin* k, const orc_tpar* tp, const double* p, int64_t n,
+                        const double* s12, const double* s13, const double* st, double* out,
+                        double* g /* n x 3 or NULL */) {
+  for (int64_t i = 0; i < n; ++i)
+    out[i] = sigt_logd(k, tp, p, s12[i], s13[i], st[i], g ? g + 3 * i : NULL);
+}
 
 /* w(z) for any z: the Im z > 0 routine, w(z) = 2 e^{-z^2} - w(-z) below the axis. */
 static double complex faddeeva_any(double complex z) {
@@ -1121,29 +1161,49 @@ void orc_smeared_exp_many(int64_t n, double lr, double li, const double* t, doub
  * a[r], b[r] the per-resonance amplitudes (A = 1 + sum c_r a_r). */
 static void tddp_amps(const orc_dkin* k, int nres, const orc_res* res, const double* p,
                       double s12, double s13, double complex* A, double complex* B,
-                      double complex* a, double complex* b) {
+                      double complex* a, double complex* b, double complex (*da)[2],
+                      double complex (*db)[2]) {
   double s23 = k->M * k->M + k->m1 * k->m1 + k->m2 * k->m2 + k->m3 * k->m3 - s12 - s13;
   *A = 1.0;
   *B = 1.0;
   for (int r = 0; r < nres; ++r) {
-    double re, im;
+    double re, im, d[4];
     orc_dalitz_amp(k, res[r].channel, res[r].spin, p[res[r].p_m0], p[res[r].p_g0], s12, s13,
-                   &re, &im, NULL);
+                   &re, &im, da ? d : NULL);
     a[r] = re + I * im;
+    if (da) {
+      da[r][0] = d[0] + I * d[1];
+      da[r][1] = d[2] + I * d[3];
+    }
     orc_dalitz_amp(k, res[r].channel, res[r].spin, p[res[r].p_m0], p[res[r].p_g0], s12, s23,
-                   &re, &im, NULL);
+                   &re, &im, db ? d : NULL);
     b[r] = re + I * im;
+    if (db) {
+      db[r][0] = d[0] + I * d[1];
+      db[r][1] = d[2] + I * d[3];
+    }
     double complex c = p[res[r].p_re] + I * p[res[r].p_im];
     *A += c * a[r];
     *B += c * b[r];
   }
 }
 
+/* Change of h(A, B) below for a change (dA, dB) of the amplitudes. */
+static double tddp_dh(double complex A, double complex B, double complex dA, double complex dB,
+                      const double* kk) {
+  double daa = 2 * creal(conj(A) * dA), dbb = 2 * creal(conj(B) * dB);
+  double complex dx = conj(dA) * B + conj(A) * dB;
+  return 0.5 * (daa + dbb) * kk[0] + 0.5 * (daa - dbb) * kk[1] + creal(dx) * kk[2] -
+         cimag(dx) * kk[3];
+}
+
 /* The four time coefficients and the combination h(A, B) = 1/2 (|A|^2 + |B|^2) k0 +
  * 1/2 (|A|^2 - |B|^2) k1 + Re(A* B) k2 - Im(A* B) k3, with its derivatives in the
- * coefficients c_r (added to g scaled by w) and in the k's (returned in dk[4]). */
-static double tddp_comb(int nres, const orc_res* res, double complex A, double complex B,
-                        const double complex* a, const double complex* b, const double* kk,
+ * coefficients c_r and (da, db not NULL) in the resonance masses and widths (added to g
+ * scaled by w) and in the k's (returned in dk[4]). */
+static double tddp_comb(int nres, const orc_res* res, const double* p, double complex A,
+                        double complex B, const double complex* a, const double complex* b,
+                        double complex (*da)[2], double complex (*db)[2], const double* kk,
                         double w, double* g, double* dk) {
   double aa = creal(A) * creal(A) + cimag(A) * cimag(A);
   double bb = creal(B) * creal(B) + cimag(B) * cimag(B);
@@ -1155,15 +1215,18 @@ static double tddp_comb(int nres, const orc_res* res, double complex A, double c
     dk[3] = -cimag(x);
   }
   if (g)
-    for (int r = 0; r < nres; ++r)
+    for (int r = 0; r < nres; ++r) {
       for (int part = 0; part < 2; ++part) {
         double complex dA = part ? I * a[r] : a[r], dB = part ? I * b[r] : b[r];
-        double daa = 2 * creal(conj(A) * dA), dbb = 2 * creal(conj(B) * dB);
-        double complex dx = conj(dA) * B + conj(A) * dB;
-        double d = 0.5 * (daa + dbb) * kk[0] + 0.5 * (daa - dbb) * kk[1] + creal(dx) * kk[2] -
-                   cimag(dx) * kk[3];
-        g[part ? res[r].p_im : res[r].p_re] += w * d;
+        g[part ? res[r].p_im : res[r].p_re] += w * tddp_dh(A, B, dA, dB, kk);
       }
+      if (da && db) {
+        /* dA = c_r da_r/dm0 (dGamma0), dB likewise */
+        double complex c = p[res[r].p_re] + I * p[res[r].p_im];
+        g[res[r].p_m0] += w * tddp_dh(A, B, c * da[r][0], c * db[r][0], kk);
+        g[res[r].p_g0] += w * tddp_dh(A, B, c * da[r][1], c * db[r][1], kk);
+      }
+    }
   return 0.5 * (aa + bb) * kk[0] + 0.5 * (aa - bb) * kk[1] + creal(x) * kk[2] - cimag(x) * kk[3];
 }
 
@@ -1217,15 +1280,16 @@ static double tddp_norm(const orc_dkin* k, int nres, const orc_res* res, const o
   orc_acc* gs = (orc_acc*)calloc(np, sizeof(orc_acc));
   orc_acc sk[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
   double* g = (double*)malloc(sizeof(double) * np);
-  double complex a[64], b[64], A, B;
+  double complex a[64], b[64], da[64][2], db[64][2], A, B;
   for (int i = 0; i < nbx; ++i)
     for (int j = 0; j < nby; ++j) {
       double s12 = x0 + (i + 0.5) * hx, s13 = y0 + (j + 0.5) * hy;
       if (!orc_dalitz_inside(k, s12, s13)) continue;
-      tddp_amps(k, nres, res, p, s12, s13, &A, &B, a, b);
+      tddp_amps(k, nres, res, p, s12, s13, &A, &B, a, b, dN ? da : NULL, dN ? db : NULL);
       double dk[4];
       memset(g, 0, sizeof(double) * np);
-      acc_add(&s, tddp_comb(nres, res, A, B, a, b, kk, 1.0, dN ? g : NULL, dk));
+      acc_add(&s, tddp_comb(nres, res, p, A, B, a, b, dN ? da : NULL, dN ? db : NULL, kk, 1.0,
+                            dN ? g : NULL, dk));
       if (dN) {
         for (int q = 0; q < np; ++q) acc_add(&gs[q], g[q]);
         for (int j = 0; j < 4; ++j) acc_add(&sk[j], dk[j]);
@@ -1248,10 +1312,10 @@ static double tddp_event(const orc_dkin* k, int nres, const orc_res* res, const 
                          double* g) {
   double kk[4], dkk[4][4], dk[4];
   tddp_time(p, tp, t, sigt, 0, kk, dkk);
-  double complex a[64], b[64], A, B;
-  tddp_amps(k, nres, res, p, s12, s13, &A, &B, a, b);
+  double complex a[64], b[64], da[64][2], db[64][2], A, B;
+  tddp_amps(k, nres, res, p, s12, s13, &A, &B, a, b, g ? da : NULL, g ? db : NULL);
   if (g) memset(g, 0, sizeof(double) * np);
-  double v = tddp_comb(nres, res, A, B, a, b, kk, 1.0, g, dk);
+  double v = tddp_comb(nres, res, p, A, B, a, b, g ? da : NULL, g ? db : NULL, kk, 1.0, g, dk);
   if (g) {
     int ip[4] = {tp->p_tau, tp->p_x, tp->p_y, tp->p_s};
     for (int q = 0; q < 4; ++q)
@@ -1287,6 +1351,15 @@ int orc_tddp_nll(const orc_dkin* k, int nres, const orc_res* res, const orc_tpar
     double v = tddp_event(k, nres, res, tp, p, np, s12[i], s13[i], t[i], sigt[i], grad ? g : NULL);
     acc_add(&s, -log(v));
     if (grad) for (int q = 0; q < np; ++q) acc_add(&gs[q], -g[q] / v);
+    if (tp->dens) {
+      double g3[3];
+      acc_add(&s, -sigt_logd(k, tp, p, s12[i], s13[i], sigt[i], grad ? g3 : NULL));
+      if (grad) {
+        acc_add(&gs[tp->p_b0], -g3[0]);
+        acc_add(&gs[tp->p_b1], -g3[1]);
+        acc_add(&gs[tp->p_b2], -g3[2]);
+      }
+    }
   }
   *nll = acc_get(&s) + (double)n * log(N);
   if (grad) for (int q = 0; q < np; ++q) grad[q] = acc_get(&gs[q]) + (double)n * dN[q] / N;

@@ -1072,6 +1072,60 @@ def test_tddp_gradient_fd():
     _fd_check(lambda q: d.nll_t(s12, s13, t, sigt, p=q, grad=True), p, free, rel=2e-6)
 
 
+def _tddp_dens_model(nbx=24, nby=24, b=(2.3, 0.4, -0.3), rng_=(0.02, 0.5)):
+    d, spec = _tddp_model(nbx, nby)
+    tp = d.tp
+    d.time_params(tp.p_tau, tp.p_x, tp.p_y, tp.p_s,
+                  density=tuple(d.param(v) for v in b), sigt_range=rng_)
+    return d, spec
+
+
+def test_sigt_density_integrates_to_one_at_every_dalitz_point():
+    """The sigma_t density is normalised on its range at any (s12, s13) and parameters:
+    adaptive quadrature of exp(log D) over [slo, shi]."""
+    d, spec = _tddp_dens_model()
+    lo, hi = 0.02, 0.5
+    x0, x1, y0, y1 = d.box()
+    for b in ((2.3, 0.4, -0.3), (0.5, -1.0, 2.0), (4.0, 0.0, 0.0)):
+        p = d.p.copy()
+        p[-3:] = b
+        for s12, s13 in ((0.9, 1.1), (0.3, 2.5), (2.6, 0.2)):
+            f = lambda st: math.exp(d.sigt_logd([s12], [s13], [st], p)[0])
+            val = integrate.quad(f, lo, hi, epsabs=0, epsrel=1e-13, limit=200)[0]
+            assert abs(val - 1) < 1e-11, (b, s12, s13, val)
+
+
+def test_sigt_density_is_a_truncated_gamma():
+    """At a point where the rate is exp(b0) (the plot's centre, or b1 = b2 = 0) the density
+    is scipy's Gamma(2, scale 1/rate) renormalised on [slo, shi]."""
+    lo, hi = 0.02, 0.5
+    d, spec = _tddp_dens_model(b=(2.1, 0.0, 0.0), rng_=(lo, hi))
+    lam = math.exp(2.1)
+    st = np.linspace(lo, hi, 57)
+    g = stats.gamma(2.0, scale=1.0 / lam)
+    ref = g.pdf(st) / (g.cdf(hi) - g.cdf(lo))
+    got = np.exp(d.sigt_logd(np.full_like(st, 1.0), np.full_like(st, 1.2), st))
+    assert np.max(np.abs(got / ref - 1)) < 1e-12
+    # and with slopes, at the centre of the plot
+    k = spec["kin"]
+    sc = (k["M"] ** 2 + k["m1"] ** 2 + k["m2"] ** 2 + k["m3"] ** 2) / 3
+    p = d.p.copy()
+    p[-2:] = (0.7, -0.4)
+    got = np.exp(d.sigt_logd(np.full_like(st, sc), np.full_like(st, sc), st, p))
+    assert np.max(np.abs(got / ref - 1)) < 1e-12
+
+
+def test_tddp_shape_and_density_gradient_fd():
+    """The mixing likelihood with free resonance masses and widths and the sigma_t density
+    (38 parameters here): analytic gradient against central differences."""
+    d, spec = _tddp_dens_model(nbx=20, nby=20)
+    s12, s13, t, sigt = _tddp_events(d, spec, 150)
+    sigt = np.clip(sigt, 0.021, 0.49)
+    p = d.p
+    _fd_check(lambda q: d.nll_t(s12, s13, t, sigt, p=q, grad=True), p, list(range(len(p))),
+              rel=3e-6)
+
+
 def test_tddp_norm_is_grid_sum_of_time_integrals():
     """N(theta) = sum over the inside cell centres of dA x the integral over all t of the
     intensity: per cell the integral of the unsmeared mixing formula over t >= 0 by
