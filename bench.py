@@ -193,7 +193,9 @@ def dalitz_events_gpu(gf, spec, n, seed):
             out[idx] = u[idx] * spec["envelope"] < np.exp(lp) * N
         return out
 
-    s12, s13 = synth.dalitz_events(n, accept, seed, batch=1 << 22)
+    # candidates per batch: about what n events need (acceptance ~ 6 %), at most 2^22
+    s12, s13 = synth.dalitz_events(n, accept, seed,
+                                   batch=int(min(1 << 22, max(1 << 16, 24 * n))))
     gctx.close()
     return s12, s13
 

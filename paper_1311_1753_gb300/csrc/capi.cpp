@@ -1569,7 +1569,9 @@ static int finish_set_data(gf_ctx* ctx) {
                                      ctx->prog.mix > 0);
   }
   per_sm = std::max(1, std::min(per_sm, 8));
-  const int64_t items = ctx->is_dalitz ? d.n : (d.n + 1) / 2;
+  // signal + background form: 16 events per thread at least, so that sorted data reach the
+  // expanded (chunked) event loop at every size
+  const int64_t items = ctx->is_dalitz ? d.n : ctx->use_sb ? (d.n + 15) / 16 : (d.n + 1) / 2;
   const int tpb = ctx->is_dalitz ? kThreads : kThreads1D;
   const int64_t want = (items + tpb - 1) / tpb;
   d.nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->sm_count * per_sm));

@@ -87,6 +87,16 @@ struct gf_server {
   int64_t unfinished = 0;
 };
 
+// The root is an AddPdf of one Voigtian and one threshold leaf (the form k_sigbkg.cu
+// evaluates; the compiler makes the final decision).
+static bool sigbkg_form(const gf_ctx* ctx, int root) {
+  if (root < 0 || root >= (int)ctx->nodes.size()) return false;
+  const NodeDef& nd = ctx->nodes[root];
+  if (nd.type != N_ADD || nd.children.size() != 2) return false;
+  const int a = ctx->nodes[nd.children[0]].type, b = ctx->nodes[nd.children[1]].type;
+  return (a == N_VOIGT && b == N_THRESH) || (a == N_THRESH && b == N_VOIGT);
+}
+
 static void fit_thread(gf_server* S, std::shared_ptr<Req> R) {
   const size_t n = R->ctx->free_ids.size();
   std::vector<double> x0(n), step(n), lo(n), hi(n);
@@ -275,8 +285,10 @@ static void scheduler(gf_server* S) {
       if (S->used_bytes + R->bytes > S->opts.mem_budget && !S->active.empty()) break;
       S->pending.pop_front();
       lk.unlock();
-      // batched ticks walk the events strided: a sorted copy would not pay for itself
-      R->ctx->event_sort = false;
+      // the batched 1D tick walks the events strided (a sorted copy would not pay for
+      // itself), except for the signal + background form, whose tick takes each thread's
+      // contiguous share of sorted events like the standalone kernel
+      R->ctx->event_sort = sigbkg_form(R->ctx, R->root);
       int rc = gf_set_data(R->ctx, R->root, R->ds);
       lk.lock();
       if (rc != GF_OK) {

@@ -127,7 +127,9 @@ def test_mixed_fit_within_a_hundredth_sigma(gf):
     for k, pid in enumerate(ctx.free_params()):
         ctx.set_value(pid, start[k])
     ctx.set_data(root, obs, [x])
-    r = ctx.fit(tol=1e-9)
+    # EDM 1e-7 (deviation ~ sqrt(2 EDM) = 4.5e-4 sigma): at 10^6 events the NLL's own FP64
+    # rounding (ulp of 4e6 ~ 1e-9) bounds the decrease a line search can still see
+    r = ctx.fit(tol=1e-7)
     assert r["status"] == gf.GF_OK, r
     assert 0 < r["n_calls_fast"] < r["n_calls"]
 
