@@ -181,11 +181,9 @@ __device__ __forceinline__ void faddeeva_f32(float x, float y, const WeidCoef& W
   wi = __fmaf_rn(0.56418958354775628695f, ii, 2.f * __fmaf_rn(pr, qi, pi * qr));
 }
 
-// Direct evaluations out of line: after the sub-chunking below they are the rare path, and
-// inline their code would be repeated in every unrolled copy of the event body.
-__device__ __noinline__ void w_direct_f2(F2 x, F2 y, const WeidCoef& W, F2& wr, F2& wi) {
-  faddeeva_f2(x, y, W, wr, wi);
-}
+// The mixed plan's direct evaluation out of line: inline, its code would be repeated in
+// every unrolled copy of the event body.  (The FP64 plan keeps its direct path inline: its
+// event loop is not unrolled, and a call would save and restore the live pairs.)
 __device__ __noinline__ void w_direct_f32(float x, float y, const WeidCoef& W, float& wr,
                                           float& wi) {
   faddeeva_f32(x, y, W, wr, wi);
@@ -297,6 +295,7 @@ __device__ void sb_finish(const SigBkgDesc& D, const double* __restrict__ der, c
 // Shared scratch of one block.
 struct SBShared {
   SBConst K;
+  WeidCoef W;  // the series coefficients, read by every thread (and the out-of-line paths)
   double red[(kSBThreads / 32) * kSBMom];
   double fin[kSBMom];
   int last;
@@ -306,14 +305,20 @@ struct SBShared {
 // block to arrive finishes the reduction.  sorted: the events are sorted ascending by x.
 template <bool G, bool MIXED, bool STORE>
 __device__ __forceinline__ void sigbkg_block(
-    const SigBkgDesc& D, const WeidCoef& W, const int sorted, const double* __restrict__ xcol,
+    const SigBkgDesc& D, const WeidCoef& Wg, const int sorted, const double* __restrict__ xcol,
     const int64_t n, const double* __restrict__ der, double* __restrict__ partials,
     unsigned* __restrict__ counter, double* __restrict__ result, double* __restrict__ out_logp,
     const int32_t* __restrict__ perm, const int vb, const int vgrid, SBShared& sh) {
   const int tid = threadIdx.x;
   if (tid == 0) sb_consts(D, der, G, sh.K);
+  {
+    const float* src = reinterpret_cast<const float*>(&Wg);
+    float* dst = reinterpret_cast<float*>(&sh.W);
+    for (int k = tid; k < (int)(sizeof(WeidCoef) / sizeof(float)); k += blockDim.x) dst[k] = src[k];
+  }
   __syncthreads();
   const SBConst& K = sh.K;
+  const WeidCoef& W = sh.W;
 
   Lazy acc;            // sum log P
   Lazy m[kSBMom - 1];  // moments SB_S .. SB_BL
@@ -352,7 +357,7 @@ __device__ __forceinline__ void sigbkg_block(
       const F2 zr = df_mul(df_split(xi - K.mu), c1);
       F2 wr, wi;
       if (tay) tayp_eval(T, zr, wr, wi);
-      else w_direct_f2(zr, y, W, wr, wi);
+      else faddeeva_f2(zr, y, W, wr, wi);
       const double td = xi - K.x0;
       F2 B = {0.f, 0.f}, t = {0.f, 0.f}, lt = {0.f, 0.f};
       if (td > 0.0) {
@@ -417,14 +422,12 @@ __device__ __forceinline__ void sigbkg_block(
         if (ok) tayp_build(T, df_mul(df_split(xm - K.mu), c1), y, W);
         return ok;
       };
-      auto run = [&](int64_t a, int c, bool tay) {  // the loads of 4 events in flight at once
-        for (int k = 0; k < c; k += 4) {
-          double xv[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) xv[j] = k + j < c ? __ldg(xcol + a + k + j) : 0.0;
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (k + j < c) one(a + k + j, xv[j], tay);
+      auto run = [&](int64_t a, int c, bool tay) {  // the next event's load in flight
+        double xn = __ldg(xcol + a);
+        for (int k = 0; k < c; ++k) {
+          const double xi = xn;
+          if (k + 1 < c) xn = __ldg(xcol + a + k + 1);
+          one(a + k, xi, tay);
         }
       };
       for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
