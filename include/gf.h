@@ -163,21 +163,35 @@ typedef struct {
 int gf_pdf_dalitz(gf_ctx* ctx, int obs12, int obs13, const gf_dalitz_kin* kin, int nres,
                   const gf_resonance* res, int* node);
 /* Time-dependent Dalitz model (Sec. 4: the D0 -> pi+ pi- pi0 mixing fit): the amplitude
- * model of gf_pdf_dalitz (resonance shapes fixed; particles 1 and 2 CP conjugates, m1 =
- * m2) for D0 (A at (s12, s13)) and D0bar (B, the same sum at (s12, s23)), with the decay
+ * model of gf_pdf_dalitz (particles 1 and 2 CP conjugates, m1 = m2) for D0 (A at
+ * (s12, s13)) and D0bar (B, the same sum at (s12, s23)), with the decay
  * time t and its per-event uncertainty sigma_t:
  *   I = 1/2 (|A|^2 + |B|^2) Tch + 1/2 (|A|^2 - |B|^2) Tc + Re(A* B) Tsh - Im(A* B) Ts,
  * the time factors e^{-t/tau} {cosh(y t/tau), cos(x t/tau), sinh(y t/tau),
  * sin(x t/tau)} (t >= 0) each convolved with a Gaussian of width scale * sigma_t.
  * Normalised over the Dalitz grid (gf_set_norm_grid; default 256 x 256 cells) and all t;
- * conditional on sigma_t.  tau, x, y, scale are parameter ids.  The data set holds the
- * columns s12, s13, t, sigma_t in this order (sigma_t > 0; every event inside the
+ * conditional on sigma_t unless gf_tddp_sigt_density adds its density.  tau, x, y, scale
+ * are parameter ids.  Resonance masses and widths may be free: the per-event amplitudes and
+ * their derivatives are then recomputed when a shape changes and N by a direct pass over
+ * the cells at each evaluation (fixed shapes: once per data load, N from grid sums).
+ * The data set holds the columns s12, s13, t, sigma_t in this order (sigma_t > 0; every
+ * event inside the
  * kinematic region, else GF_EINVAL from gf_set_data / gf_update_data).  FP64-accurate in
  * both precision modes: the time dependence in FP64, the amplitude algebra in
  * double-float pairs. */
 int gf_pdf_tddp(gf_ctx* ctx, int obs12, int obs13, int obs_t, int obs_sigt,
                 const gf_dalitz_kin* kin, int nres, const gf_resonance* res, int tau, int x,
                 int y, int scale, int* node);
+/* The decay-time uncertainty's density of a time-dependent Dalitz node (Sec. 4: the
+ * mixing fit's sigma_t distribution varies across the Dalitz plot): the PDF becomes
+ * I/N x D(sigma_t | s12, s13) with
+ *   D = lam^2 sigma_t e^{-lam sigma_t} / Z,  Z = g(lam lo) - g(lam hi),  g(a) = e^{-a}(1 + a),
+ *   lam = exp(b0 + b1 (s12 - sc) + b2 (s13 - sc)),  sc = (M^2 + m1^2 + m2^2 + m3^2)/3,
+ * a Gamma distribution of shape 2 truncated to the sigma_t observable's range [lo, hi]
+ * (lo > 0) whose rate varies over the plot; b0, b1, b2 are parameter ids.  D integrates
+ * to one over sigma_t at every point, so the product is normalised.  Without this call the
+ * likelihood is conditional on sigma_t. */
+int gf_tddp_sigt_density(gf_ctx* ctx, int node, int b0, int b1, int b2);
 /* Grid of the node's numerical normalisation: nbins_x bins for a 1D leaf, the lattice
  * of a convolution, or nbins_x x nbins_y cells for a Dalitz node. */
 int gf_set_norm_grid(gf_ctx* ctx, int node, int nbins_x, int nbins_y);

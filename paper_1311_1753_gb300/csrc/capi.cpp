@@ -142,6 +142,8 @@ static void free_dev(gf_ctx* ctx) {
   cudaFree(d.tddp_cache);
   cudaFree(d.tddp_gcols);
   cudaFree(d.tddp_gram);
+  cudaFree(d.tddp_dcache);
+  cudaFree(d.tddp_normd);
   for (void* p : d.conv_bufs) cudaFree(p);
   for (void* p : d.gn_bufs) cudaFree(p);
   for (auto& g : d.graph)
@@ -467,6 +469,22 @@ int gf_pdf_tddp(gf_ctx* ctx, int obs12, int obs13, int obs_t, int obs_sigt,
   nd.pars = {tau, x, y, scale};
   nd.nbx = nd.nby = 256;
   *node = id;
+  return GF_OK;
+}
+
+int gf_tddp_sigt_density(gf_ctx* ctx, int node, int b0, int b1, int b2) {
+  if (!ctx || !valid_node(ctx, node)) return GF_EINVAL;
+  NodeDef& nd = ctx->nodes[node];
+  if (nd.type != N_TDDP)
+    return set_error(ctx, GF_EINVAL, "sigma_t density: not a time-dependent Dalitz node");
+  for (int p : {b0, b1, b2})
+    if (!valid_par(ctx, p)) return set_error(ctx, GF_EINVAL, "sigma_t density: unknown parameter id");
+  if (!(ctx->obs[nd.obs4].lo > 0.0))
+    return set_error(ctx, GF_EINVAL, "sigma_t density: the sigma_t range must be positive");
+  nd.pars.resize(4);
+  nd.pars.insert(nd.pars.end(), {b0, b1, b2});
+  nd.aux = 1;
+  ctx->compiled = false;
   return GF_OK;
 }
 
@@ -1235,10 +1253,9 @@ int ensure_compiled(gf_ctx* ctx) {
     T.D.nres = (int)root.res.size();
     T.D.nfree = nf;
     T.nfree = nf;
+    T.shape_free = 0;
     for (int r = 0; r < T.D.nres; ++r) {
       const gf_resonance& R = root.res[r];
-      if (ctx->free_pos[R.mass] >= 0 || ctx->free_pos[R.width] >= 0)
-        return set_error(ctx, GF_EINVAL, "time-dependent Dalitz: resonance shapes must be fixed");
       DalitzRes& X = T.D.res[r];
       X.channel = R.channel;
       X.spin = R.spin;
@@ -1246,7 +1263,9 @@ int ensure_compiled(gf_ctx* ctx) {
       X.p_g0 = R.width;
       X.p_re = R.re;
       X.p_im = R.im;
-      X.g_m0 = X.g_g0 = -1;
+      X.g_m0 = ctx->free_pos[R.mass];
+      X.g_g0 = ctx->free_pos[R.width];
+      if (X.g_m0 >= 0 || X.g_g0 >= 0) T.shape_free = 1;
       X.g_re = ctx->free_pos[R.re];
       X.g_im = ctx->free_pos[R.im];
       X.ev_cached = r;
@@ -1260,6 +1279,21 @@ int ensure_compiled(gf_ctx* ctx) {
     T.g_x = ctx->free_pos[T.p_x];
     T.g_y = ctx->free_pos[T.p_y];
     T.g_s = ctx->free_pos[T.p_s];
+    T.dens = (root.aux == 1 && root.pars.size() == 7) ? 1 : 0;
+    if (T.dens) {
+      T.p_b0 = root.pars[4];
+      T.p_b1 = root.pars[5];
+      T.p_b2 = root.pars[6];
+      T.g_b0 = ctx->free_pos[T.p_b0];
+      T.g_b1 = ctx->free_pos[T.p_b1];
+      T.g_b2 = ctx->free_pos[T.p_b2];
+      T.slo = ctx->obs[root.obs4].lo;
+      T.shi = ctx->obs[root.obs4].hi;
+      const gf_dalitz_kin& K = root.kin;
+      T.sc = (K.M * K.M + K.m1 * K.m1 + K.m2 * K.m2 + K.m3 * K.m3) / 3.0;
+    } else {
+      T.p_b0 = T.p_b1 = T.p_b2 = T.g_b0 = T.g_b1 = T.g_b2 = -1;
+    }
     ctx->compiled = true;
     return GF_OK;
   }
@@ -1551,6 +1585,18 @@ static int finish_set_data(gf_ctx* ctx) {
     CK(cudaMalloc(&d.tddp_cache, sizeof(float4) * 2 * std::max(T.D.nres, 1) * (size_t)std::max<int64_t>(d.n, 1)));
     CK(cudaMalloc(&d.tddp_gcols, sizeof(double2) * 2 * std::max(T.D.nres, 1) * ncell));
     CK(cudaMalloc(&d.tddp_gram, sizeof(double2) * 3 * (kMaxRes + 1) * (kMaxRes + 1)));
+    cudaFree(d.tddp_dcache);
+    cudaFree(d.tddp_normd);
+    d.tddp_dcache = nullptr;
+    d.tddp_normd = nullptr;
+    if (T.shape_free) {
+      CK(cudaMalloc(&d.tddp_dcache, sizeof(float4) * 4 * std::max(T.D.nres, 1) *
+                                        (size_t)std::max<int64_t>(d.n, 1)));
+      CK(cudaMalloc(&d.tddp_normd, sizeof(double) * 64));
+      rc = grow(ctx, &d.partials2, &d.partials2_cap, (size_t)4096 * 64);
+      if (rc) return rc;
+    }
+    d.tddp_shape.clear();
     d.tddp_ready = false;
     return GF_OK;
   }
@@ -2020,17 +2066,45 @@ static int tddp_enqueue(gf_ctx* ctx, bool grad, double* out_logp, int* launches)
   int rc = enqueue_uploads(ctx);
   if (rc) return rc;
   CK(cudaEventRecord(d.ev0, ctx->stream));
-  if (!d.tddp_ready) {
-    CK(launch_dalitz_mask(T.D, d.inside, ctx->stream));
-    CK(launch_tddp_cache(T, d.theta, d.cols[0], d.cols[1], d.n, d.tddp_cache, ctx->stream));
-    CK(launch_tddp_gram(T, d.theta, d.inside, d.tddp_gcols, d.tddp_gram, ctx->stream));
-    *launches += 4;
-    d.tddp_ready = true;
+  if (!T.shape_free) {
+    if (!d.tddp_ready) {
+      CK(launch_dalitz_mask(T.D, d.inside, ctx->stream));
+      CK(launch_tddp_cache(T, d.theta, d.cols[0], d.cols[1], d.n, d.tddp_cache, ctx->stream));
+      CK(launch_tddp_gram(T, d.theta, d.inside, d.tddp_gcols, d.tddp_gram, ctx->stream));
+      *launches += 4;
+      d.tddp_ready = true;
+    }
+  } else {
+    // free shapes: the per-event amplitudes and their derivatives whenever a mass or
+    // width changed, and N with its gradient by a direct cell pass at every evaluation
+    std::vector<double> shape;
+    for (int r = 0; r < T.D.nres; ++r) {
+      shape.push_back(d.h_theta[T.D.res[r].p_m0]);
+      shape.push_back(d.h_theta[T.D.res[r].p_g0]);
+    }
+    if (!d.tddp_ready) {
+      CK(launch_dalitz_mask(T.D, d.inside, ctx->stream));
+      (*launches)++;
+    }
+    if (!d.tddp_ready || shape != d.tddp_shape) {
+      CK(launch_tddp_cache_free(T, d.theta, d.cols[0], d.cols[1], d.n, d.tddp_cache,
+                                d.tddp_dcache, ctx->stream));
+      (*launches)++;
+      d.tddp_shape = shape;
+      d.tddp_ready = true;
+    }
+    const int64_t ncell = (int64_t)T.D.nbx * T.D.nby;
+    const int nb = (int)std::max<int64_t>(
+        1, std::min<int64_t>((ncell + kThreads - 1) / kThreads, (int64_t)ctx->sm_count * 2));
+    CK(launch_tddp_norm_direct(T, d.theta, d.inside, d.partials2, d.counters + 1, d.tddp_normd,
+                               nb, ctx->stream));
+    (*launches)++;
   }
   CK(cudaEventRecord(d.evm, ctx->stream));
   const double* cols[4] = {d.cols[0], d.cols[1], d.cols[2], d.cols[3]};
-  CK(launch_tddp_events(T, grad, d.theta, cols, d.n, d.tddp_cache, d.tddp_gram, d.partials,
-                        d.counters, d.result, out_logp, d.nblocks, weideman(), ctx->stream));
+  CK(launch_tddp_events(T, grad, d.theta, cols, d.n, d.tddp_cache, d.tddp_dcache, d.tddp_gram,
+                        T.shape_free ? d.tddp_normd : nullptr, d.partials, d.counters,
+                        d.result, out_logp, d.nblocks, weideman(), ctx->stream));
   (*launches)++;
   CK(cudaEventRecord(d.ev1, ctx->stream));
   if (!out_logp) {

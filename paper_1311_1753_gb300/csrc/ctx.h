@@ -99,6 +99,9 @@ struct DevState {
   double2* tddp_gcols = nullptr;
   double2* tddp_gram = nullptr;
   bool tddp_ready = false;             // caches built for the loaded events
+  float4* tddp_dcache = nullptr;       // free shapes: per-event shape derivatives
+  double* tddp_normd = nullptr;        // free shapes: N and dN from the direct cell pass
+  std::vector<double> tddp_shape;      // (m0, Gamma0) per resonance the cache was built with
   // binned data: bin contents and chi-squared variances (device), N x bin volume
   bool binned = false;
   double* bw = nullptr;

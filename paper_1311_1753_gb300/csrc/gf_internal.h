@@ -193,7 +193,15 @@ struct TddpPlan {
   DalitzPlan D;
   int32_t p_tau, p_x, p_y, p_s;
   int32_t g_tau, g_x, g_y, g_s;
-  int32_t nfree, pad;
+  int32_t nfree;
+  int32_t shape_free;        // some resonance mass or width is free: amplitudes and their
+                             // shape derivatives per evaluation, N by a direct cell pass
+  // the sigma_t density (dens = 1): Gamma(2) truncated to [slo, shi] with rate
+  // exp(b0 + b1 (s12 - sc) + b2 (s13 - sc))
+  int32_t dens;
+  int32_t p_b0, p_b1, p_b2, g_b0, g_b1, g_b2;
+  int32_t pad;
+  double slo, shi, sc;
 };
 
 // ---- batched evaluation of many fits (one fit-server tick) ----------------------------

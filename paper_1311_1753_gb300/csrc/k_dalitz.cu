@@ -1019,6 +1019,8 @@ cudaError_t launch_tick_dalitz(bool mixed, const TickItem* items, int nfits, int
 
 // Opt the gradient kernels in to > 48 KB of dynamic shared memory on the current device.
 // Called once per device when a context is created: never inside a stream capture.
+static cudaError_t prepare_kernels_tddp();  // after the mixing kernels, below
+
 cudaError_t prepare_kernels_dalitz() {
   cudaError_t e = upload_df_tables();
   const int lim = 160 * 1024;
@@ -1033,6 +1035,7 @@ cudaError_t prepare_kernels_dalitz() {
   attr((const void*)k_dalitz_stream<DF, true, METRIC_NLL, true>);
   attr((const void*)k_tick_dalitz<float>);
   attr((const void*)k_tick_dalitz<DF>);
+  if (e == cudaSuccess) e = prepare_kernels_tddp();
   return e;
 }
 
@@ -1106,6 +1109,63 @@ __global__ void __launch_bounds__(kThreads) k_tddp_cache(const __grid_constant__
       chan_kin_c<double>(C, R.channel, x, z, y, k);  // (s12, s23): the CP-conjugate point
       res_amp_c<double>(R, C, r, k, A, FS, BW, Gm);
       cache[(size_t)(D.nres + r) * n + i] = pair4(A.r, A.i);
+    }
+  }
+}
+
+// Free resonance shapes: a_r, b_r and their derivatives in m0 and Gamma0, recomputed when
+// a shape changes, in double-float pairs (the Dalitz pass's resonance code):
+//   dA_r/dm0 = FS (hF BW - BW^2 dD), dD = 2 m0 - i Gamma (1 + m0 dlog K/dm0),
+//   dA_r/dGamma0 = FS i m0 (Gamma/Gamma0) BW^2  (FS = F_L S_L).
+__device__ __forceinline__ float4 pair4f(DF re, DF im) {
+  return make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+__device__ __forceinline__ void res_deriv_c(const DzC<DF>& C, int r, const DF& FS,
+                                            const C2<DF>& BW, const DF& Gm, C2<DF>& dm,
+                                            C2<DF>& dg) {
+  const DF b2r = BW.r * BW.r - BW.i * BW.i, b2i = DF(2.f) * BW.r * BW.i;
+  const DF dDr = C.twom0[r], dDi = -(Gm * C.dDfac[r]);
+  dm.r = FS * (C.hF[r] * BW.r - (b2r * dDr - b2i * dDi));
+  dm.i = FS * (C.hF[r] * BW.i - (b2r * dDi + b2i * dDr));
+  const DF f = FS * C.m0[r] * Gm * C.invg0[r];
+  dg.r = -(f * b2i);
+  dg.i = f * b2r;
+}
+
+// cache[r n + i] = a_r, cache[(nres + r) n + i] = b_r; dcache[(4 r + j) n + i], j = 0..3:
+// da_r/dm0, da_r/dGamma0, db_r/dm0, db_r/dGamma0 (float pairs).
+__global__ void __launch_bounds__(kThreads) k_tddp_cache_free(const __grid_constant__ TddpPlan T,
+                                                             const double* __restrict__ theta,
+                                                             const double* __restrict__ s12,
+                                                             const double* __restrict__ s13,
+                                                             int64_t n, float4* __restrict__ cache,
+                                                             float4* __restrict__ dcache) {
+  const DalitzPlan& D = T.D;
+  __shared__ ResK rk[kMaxRes];
+  __shared__ DzC<DF> C;
+  load_df_tables();
+  if (threadIdx.x < D.nres) res_constants(D, D.res[threadIdx.x], theta, rk[threadIdx.x]);
+  __syncthreads();
+  fill_dzc<DF>(D, rk, C);
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = s12[i], y = s13[i];
+    const DF a = DF::from(x), b = DF::from(y), c = DF::from(D.sum_m2 - x - y);
+    for (int r = 0; r < D.nres; ++r) {
+      const DalitzRes& R = D.res[r];
+      for (int side = 0; side < 2; ++side) {  // (s12, s13), then the CP-conjugate (s12, s23)
+        ChanK<DF> k;
+        C2<DF> A, BW, dm, dg;
+        DF FS, Gm;
+        if (side == 0) chan_kin_c<DF>(C, R.channel, a, b, c, k);
+        else chan_kin_c<DF>(C, R.channel, a, c, b, k);
+        res_amp_c<DF>(R, C, r, k, A, FS, BW, Gm);
+        res_deriv_c(C, r, FS, BW, Gm, dm, dg);
+        cache[(size_t)(side * D.nres + r) * n + i] = pair4f(A.r, A.i);
+        dcache[(size_t)(4 * r + 2 * side) * n + i] = pair4f(dm.r, dm.i);
+        dcache[(size_t)(4 * r + 2 * side + 1) * n + i] = pair4f(dg.r, dg.i);
+      }
     }
   }
 }
@@ -1352,6 +1412,129 @@ __device__ void tddp_norm_block(const TddpPlan& T, const double* th, const doubl
   __syncthreads();
 }
 
+// Free resonance shapes: N(theta) and dN/dtheta_free by a direct pass over the cells
+// inside the region (the Gram sums would change with every shape).  Per cell, in pairs,
+// with the time integrals k = (Ich, Ic, Ish, Is) of the rates l_j (1/l_j):
+//   I_c = p |A|^2 + q |B|^2 + Re(conj(A) B z),  p, q = (k0 +- k1)/2,  z = k2 + i k3,
+//   dI/dRe c_r + i dI/dIm c_r = 2 (conj(a_r) E + conj(b_r) F),  E = p A + z B/2,
+//   F = q B + conj(z) A/2,  dI/dshape_r = 2 Re(conj(E) c_r da_r + conj(F) c_r db_r),
+// and for tau, x, y the sums of (|A|^2 + |B|^2)/2, (|A|^2 - |B|^2)/2, Re(conj(A) B),
+// -Im(conj(A) B) times the derivatives of the k's.  The amplitudes are computed twice per
+// cell (for A and B first, then with their derivatives for the gradient) rather than
+// held.  Per-thread gradient sums in shared memory (nfree x blockDim pairs); the last
+// block writes out[0] = N, out[1 + k] = dN/dtheta_k.
+constexpr int kTddpNormStride = 5 + 4 * kMaxRes + 8;
+__global__ void __launch_bounds__(kThreads) k_tddp_norm_direct(
+    const __grid_constant__ TddpPlan T, const double* __restrict__ theta,
+    const uint8_t* __restrict__ inside, double* __restrict__ partials,
+    unsigned* __restrict__ counter, double* __restrict__ out) {
+  const DalitzPlan& D = T.D;
+  extern __shared__ F2 gsh[];  // nfree x blockDim
+  __shared__ ResK rk[kMaxRes];
+  __shared__ DzC<DF> C;
+  __shared__ double red[(kThreads / 32) * kTddpNormStride];
+  __shared__ double tot[kTddpNormStride];
+  __shared__ int last;
+  const int tid = threadIdx.x, bd = blockDim.x, nf = T.nfree, nres = D.nres;
+  if (tid < nres) res_constants(D, D.res[tid], theta, rk[tid]);
+  for (int k = 0; k < nf; ++k) gsh[k * bd + tid] = F2{0.f, 0.f};
+  __syncthreads();
+  fill_dzc<DF>(D, rk, C);
+  __syncthreads();
+  Cx l[3], dl[3][3];
+  tddp_rates(theta[T.p_tau], theta[T.p_x], theta[T.p_y], l, dl);
+  const Cx i1 = cinv(l[0]), i2 = cinv(l[1]), i3 = cinv(l[2]);
+  const double k0 = 0.5 * (i1.r + i2.r), k1 = i3.r, k2 = 0.5 * (i1.r - i2.r), k3 = i3.i;
+  const DF p = DF::from(0.5 * (k0 + k1)), q = DF::from(0.5 * (k0 - k1));
+  const DF zr = DF::from(k2), zi = DF::from(k3), half = DF(0.5f), two = DF(2.f);
+  DF sI = DF(0.f), sd[4] = {DF(0.f), DF(0.f), DF(0.f), DF(0.f)};
+  const int64_t ncell = (int64_t)D.nbx * D.nby;
+  for (int64_t i = (int64_t)blockIdx.x * bd + tid; i < ncell; i += (int64_t)gridDim.x * bd) {
+    if (!inside[i]) continue;
+    const int ix = (int)(i / D.nby), iy = (int)(i % D.nby);
+    const double xd = D.x0 + (ix + 0.5) * D.hx, yd = D.y0 + (iy + 0.5) * D.hy;
+    const DF a = DF::from(xd), b = DF::from(yd), c = DF::from(D.sum_m2 - xd - yd);
+    ChanK<DF> ka[3], kb[3];
+    for (int ch = 0; ch < 3; ++ch) {
+      chan_kin_c<DF>(C, ch, a, b, c, ka[ch]);
+      chan_kin_c<DF>(C, ch, a, c, b, kb[ch]);  // the CP-conjugate point (s12, s23)
+    }
+    C2<DF> A = {DF(1.f), DF(0.f)}, B = A;
+    for (int r = 0; r < nres; ++r) {
+      const DalitzRes& R = D.res[r];
+      C2<DF> Ar, Br, BW;
+      DF FS, Gm;
+      res_amp_c<DF>(R, C, r, ka[R.channel], Ar, FS, BW, Gm);
+      res_amp_c<DF>(R, C, r, kb[R.channel], Br, FS, BW, Gm);
+      A.r += C.cr[r] * Ar.r - C.ci[r] * Ar.i;
+      A.i += C.cr[r] * Ar.i + C.ci[r] * Ar.r;
+      B.r += C.cr[r] * Br.r - C.ci[r] * Br.i;
+      B.i += C.cr[r] * Br.i + C.ci[r] * Br.r;
+    }
+    const DF aa = A.r * A.r + A.i * A.i, bb = B.r * B.r + B.i * B.i;
+    const DF xr = A.r * B.r + A.i * B.i, xi = A.r * B.i - A.i * B.r;  // conj(A) B
+    sI += p * aa + q * bb + (xr * zr - xi * zi);
+    sd[0] += half * (aa + bb);
+    sd[1] += half * (aa - bb);
+    sd[2] += xr;
+    sd[3] += -xi;
+    // E = p A + z B/2, F = q B + conj(z) A/2
+    const C2<DF> E = {p * A.r + half * (zr * B.r - zi * B.i), p * A.i + half * (zr * B.i + zi * B.r)};
+    const C2<DF> F = {q * B.r + half * (zr * A.r + zi * A.i), q * B.i + half * (zr * A.i - zi * A.r)};
+    for (int r = 0; r < nres; ++r) {
+      const DalitzRes& R = D.res[r];
+      C2<DF> Ar, Br, BWa, BWb;
+      DF FSa, Gma, FSb, Gmb;
+      res_amp_c<DF>(R, C, r, ka[R.channel], Ar, FSa, BWa, Gma);
+      res_amp_c<DF>(R, C, r, kb[R.channel], Br, FSb, BWb, Gmb);
+      // conj(a) E + conj(b) F
+      const DF ur = Ar.r * E.r + Ar.i * E.i + Br.r * F.r + Br.i * F.i;
+      const DF ui = Ar.r * E.i - Ar.i * E.r + Br.r * F.i - Br.i * F.r;
+      if (R.g_re >= 0) gsh[R.g_re * bd + tid] = df_add(gsh[R.g_re * bd + tid], two * ur);
+      if (R.g_im >= 0) gsh[R.g_im * bd + tid] = df_add(gsh[R.g_im * bd + tid], two * ui);
+      if (R.g_m0 >= 0 || R.g_g0 >= 0) {
+        C2<DF> dma, dga, dmb, dgb;
+        res_deriv_c(C, r, FSa, BWa, Gma, dma, dga);
+        res_deriv_c(C, r, FSb, BWb, Gmb, dmb, dgb);
+        // 2 Re(conj(E) c w_a + conj(F) c w_b) = 2 Re(c (conj(E) w_a + conj(F) w_b))
+        auto term = [&](const C2<DF>& wa, const C2<DF>& wb) {
+          const DF vr = E.r * wa.r + E.i * wa.i + F.r * wb.r + F.i * wb.i;
+          const DF vi = E.r * wa.i - E.i * wa.r + F.r * wb.i - F.i * wb.r;
+          return two * (C.cr[r] * vr - C.ci[r] * vi);
+        };
+        if (R.g_m0 >= 0) gsh[R.g_m0 * bd + tid] = df_add(gsh[R.g_m0 * bd + tid], term(dma, dmb));
+        if (R.g_g0 >= 0) gsh[R.g_g0 * bd + tid] = df_add(gsh[R.g_g0 * bd + tid], term(dga, dgb));
+      }
+    }
+  }
+  const int m = 5 + nf;
+  block_sum_pairs([&](int k) -> F2 {
+                    return k == 0 ? F2(sI) : k < 5 ? F2(sd[k - 1]) : gsh[(k - 5) * bd + tid];
+                  },
+                  m, red, partials + (size_t)blockIdx.x * kTddpNormStride);
+  if (!arrive_last_of(counter, gridDim.x, &last)) return;
+  reduce_partials(partials, gridDim.x, kTddpNormStride, m, tot);
+  const double dA = D.hx * D.hy;
+  if (tid == 0) out[0] = dA * tot[0];
+  for (int k = tid; k < nf; k += bd) {
+    double v = tot[5 + k];
+    // tau, x, y: sum_k sd_k dk_k/dq, d(1/l)/dq = -(1/l^2) dl/dq
+    const int gp[3] = {T.g_tau, T.g_x, T.g_y};
+    for (int qq = 0; qq < 3; ++qq)
+      if (gp[qq] == k) {
+        Cx d[3];
+        for (int j = 0; j < 3; ++j) {
+          const Cx ij = cinv(l[j]);
+          d[j] = cmul(cmul(ij, ij), dl[j][qq]);
+        }
+        v += tot[1] * (-0.5 * (d[0].r + d[1].r)) + tot[2] * (-d[2].r) +
+             tot[3] * (-0.5 * (d[0].r - d[1].r)) + tot[4] * (-d[2].i);
+      }
+    out[1 + k] = dA * v;
+  }
+  if (tid == 0) *counter = 0u;
+}
+
 // The event pass: -log(I/N) summed (or stored per event) with the gradient; per-thread
 // gradient sums in shared memory (nfree x blockDim pairs).  The amplitude sums A, B and
 // the coefficient gradient (multiply-adds of cached amplitudes) run in double-float pairs
@@ -1363,13 +1546,15 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
     const __grid_constant__ TddpPlan T, const __grid_constant__ WeidCoef W,
     const double* __restrict__ theta, const double* __restrict__ ct,
     const double* __restrict__ csig, int64_t n, const float4* __restrict__ cache,
-    const double2* __restrict__ gram, double* __restrict__ partials,
+    const float4* __restrict__ dcache, const double2* __restrict__ gram,
+    const double* __restrict__ normd, const double* __restrict__ c12,
+    const double* __restrict__ c13, double* __restrict__ partials,
     unsigned* __restrict__ counter, double* __restrict__ result, double* __restrict__ out_logp) {
   const DalitzPlan& D = T.D;
   extern __shared__ F2 gsh[];  // G: nfree x blockDim
   __shared__ double th[4 * kMaxRes + 8];
   __shared__ double Nsh[1 + 4 * kMaxRes + 8];
-  __shared__ double red[(kThreads / 32) * (1 + 4 * kMaxRes + 4)];
+  __shared__ double red[(kThreads / 32) * (1 + 4 * kMaxRes + 8)];
   __shared__ Cx vec[4 * (kMaxRes + 1)];
   __shared__ double part[2 * kMaxRes + 3], kd[8];
   __shared__ F2 cp[2 * kMaxRes];  // c_r as pairs (re, im)
@@ -1384,8 +1569,12 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   __syncthreads();
   double logN = 0.0;
   if (STORE) {
-    tddp_norm_block(T, th, gram, Nsh, vec, part, kd, false);
-    logN = log(Nsh[0]);
+    if (normd) {
+      logN = log(normd[0]);
+    } else {
+      tddp_norm_block(T, th, gram, Nsh, vec, part, kd, false);
+      logN = log(Nsh[0]);
+    }
   }
   const double tau = th[T.p_tau], mx = th[T.p_x], my = th[T.p_y], sc = th[T.p_s];
   Cx l[3], dl[3][3];
@@ -1422,11 +1611,27 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
     const Cx X = cmul({A.r, -A.i}, B);
     const double dI[4] = {0.5 * (aa + bb), 0.5 * (aa - bb), X.r, -X.i};
     const double I = dI[0] * kk[0] + dI[1] * kk[1] + dI[2] * kk[2] + dI[3] * kk[3];
+    // the sigma_t density: log D = 2 ll + log st - lam st - log Z, lam = e^ll,
+    // ll = b0 + b1 u + b2 v, Z = e^{-lam slo} (1 + lam slo) - e^{-lam shi} (1 + lam shi)
+    double logD = 0.0, dlam = 0.0, du = 0.0, dv = 0.0;
+    if (T.dens) {
+      du = c12[i] - T.sc;
+      dv = c13[i] - T.sc;
+      const double ll = th[T.p_b0] + th[T.p_b1] * du + th[T.p_b2] * dv;
+      const double lam = df_exp(ll);
+      const double el = df_exp(-lam * T.slo), eh = df_exp(-lam * T.shi);
+      const double Z = el * (1.0 + lam * T.slo) - eh * (1.0 + lam * T.shi);
+      logD = 2.0 * ll + df_log(sigt) - lam * sigt - df_log(Z);
+      if (G) {
+        const double dZ = lam * (T.shi * T.shi * eh - T.slo * T.slo * el);
+        dlam = (2.0 / lam - sigt - dZ / Z) * lam;  // d log D / d ll
+      }
+    }
     if (STORE) {
-      out_logp[i] = df_log(I) - logN;
+      out_logp[i] = df_log(I) - logN + logD;
       continue;
     }
-    acc.add(-df_log(I));
+    acc.add(-df_log(I) - logD);
     if (G) {
       const double iI = -1.0 / I;
       // I = p |A|^2 + q |B|^2 + Re(z conj(A) B), p, q = (kk0 +- kk1)/2, z = kk2 + i kk3, so
@@ -1452,6 +1657,34 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
                                df_sub(df_mul(bre, Fi), df_mul(bim, Fr))));
         }
       }
+      // resonance shapes: Re(conj(E) c_r da_r + conj(F) c_r db_r) with the scaled E, F
+      if (dcache)
+        for (int r = 0; r < D.nres; ++r) {
+          const DalitzRes& R = D.res[r];
+          if (R.g_m0 < 0 && R.g_g0 < 0) continue;
+          const F2 cr = cp[2 * r], ci = cp[2 * r + 1];
+          for (int j = 0; j < 2; ++j) {
+            const int gi = j ? R.g_g0 : R.g_m0;
+            if (gi < 0) continue;
+            const float4 da = dcache[(size_t)(4 * r + j) * n + i];
+            const float4 db = dcache[(size_t)(4 * r + 2 + j) * n + i];
+            const F2 dar = {da.x, da.y}, dai = {da.z, da.w}, dbr = {db.x, db.y}, dbi = {db.z, db.w};
+            // w = c d (complex), then Re(conj(E) w_a) + Re(conj(F) w_b)
+            const F2 war = df_sub(df_mul(cr, dar), df_mul(ci, dai));
+            const F2 wai = df_add(df_mul(cr, dai), df_mul(ci, dar));
+            const F2 wbr = df_sub(df_mul(cr, dbr), df_mul(ci, dbi));
+            const F2 wbi = df_add(df_mul(cr, dbi), df_mul(ci, dbr));
+            F2& sacc = gsh[gi * bd + tid];
+            sacc = df_add(sacc, df_add(df_add(df_mul(Er, war), df_mul(Ei, wai)),
+                                       df_add(df_mul(Fr, wbr), df_mul(Fi, wbi))));
+          }
+        }
+      // the sigma_t density's parameters: d(-log D)/db = -(d log D/d ll) (1, u, v)
+      if (T.dens) {
+        if (T.g_b0 >= 0) gsh[T.g_b0 * bd + tid] = df_add(gsh[T.g_b0 * bd + tid], df_split(-dlam));
+        if (T.g_b1 >= 0) gsh[T.g_b1 * bd + tid] = df_add(gsh[T.g_b1 * bd + tid], df_split(-dlam * du));
+        if (T.g_b2 >= 0) gsh[T.g_b2 * bd + tid] = df_add(gsh[T.g_b2 * bd + tid], df_split(-dlam * dv));
+      }
       // time parameters: dI = sum_k dI_k dkk_k with dkk from dT_j = dT_j/dl_j dl_j:
       // dl_j/dtau = -G l_j, dl_2/dx = -i G, dl_0,1/dy = -+ G; dT_j/ds = dT_j/dsigma sigma_t
       auto add_time = [&](int gi, double d0, double d1, Cx d2) {
@@ -1470,12 +1703,17 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   }
   if (STORE) return;
   const int m = 1 + (G ? nf : 0);
-  const int stride = 1 + 4 * kMaxRes + 4;
+  const int stride = 1 + 4 * kMaxRes + 8;
   block_sum_pairs([&](int k) -> F2 { return k == 0 ? df_split(acc.get()) : gsh[(k - 1) * bd + tid]; },
                   m, red, partials + (size_t)blockIdx.x * stride);
   if (!arrive_last_of(counter, gridDim.x, &last)) return;
   reduce_partials(partials, gridDim.x, stride, m, result);
-  tddp_norm_block(T, th, gram, Nsh, vec, part, kd, G);
+  if (normd) {  // free shapes: N and dN from the direct cell pass
+    for (int k = tid; k < 1 + nf; k += bd) Nsh[k] = normd[k];
+    __syncthreads();
+  } else {
+    tddp_norm_block(T, th, gram, Nsh, vec, part, kd, G);
+  }
   if (tid == 0) {
     result[0] += (double)n * log(Nsh[0]);
     *counter = 0u;
@@ -1504,24 +1742,53 @@ cudaError_t launch_tddp_gram(const TddpPlan& T, const double* theta, const uint8
 
 cudaError_t launch_tddp_events(const TddpPlan& T, bool grad, const double* theta,
                                const double* const* cols, int64_t n, const float4* cache,
-                               const double2* gram, double* partials, unsigned* counter,
-                               double* result, double* out_logp, int nblocks,
-                               const WeidCoef& W, cudaStream_t st) {
+                               const float4* dcache, const double2* gram, const double* normd,
+                               double* partials, unsigned* counter, double* result,
+                               double* out_logp, int nblocks, const WeidCoef& W,
+                               cudaStream_t st) {
   const size_t smem = grad ? sizeof(F2) * T.nfree * kThreads : 0;
   if (out_logp) {
-    k_tddp_events<false, true><<<nblocks, kThreads, 0, st>>>(T, W, theta, cols[2], cols[3], n,
-                                                            cache, gram, partials, counter,
-                                                            result, out_logp);
+    k_tddp_events<false, true><<<nblocks, kThreads, 0, st>>>(
+        T, W, theta, cols[2], cols[3], n, cache, dcache, gram, normd, cols[0], cols[1], partials,
+        counter, result, out_logp);
   } else if (grad) {
-    k_tddp_events<true, false><<<nblocks, kThreads, smem, st>>>(T, W, theta, cols[2], cols[3], n,
-                                                               cache, gram, partials, counter,
-                                                               result, nullptr);
+    k_tddp_events<true, false><<<nblocks, kThreads, smem, st>>>(
+        T, W, theta, cols[2], cols[3], n, cache, dcache, gram, normd, cols[0], cols[1], partials,
+        counter, result, nullptr);
   } else {
-    k_tddp_events<false, false><<<nblocks, kThreads, 0, st>>>(T, W, theta, cols[2], cols[3], n,
-                                                             cache, gram, partials, counter,
-                                                             result, nullptr);
+    k_tddp_events<false, false><<<nblocks, kThreads, 0, st>>>(
+        T, W, theta, cols[2], cols[3], n, cache, dcache, gram, normd, cols[0], cols[1], partials,
+        counter, result, nullptr);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_tddp_cache_free(const TddpPlan& T, const double* theta, const double* s12,
+                                   const double* s13, int64_t n, float4* cache, float4* dcache,
+                                   cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_tddp_cache_free<<<grid_for(n, kThreads, 152 * 8), kThreads, 0, st>>>(T, theta, s12, s13, n,
+                                                                         cache, dcache);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tddp_norm_direct(const TddpPlan& T, const double* theta,
+                                    const uint8_t* inside, double* partials, unsigned* counter,
+                                    double* out, int nblocks, cudaStream_t st) {
+  const size_t smem = sizeof(F2) * (size_t)(T.nfree > 0 ? T.nfree : 1) * kThreads;
+  k_tddp_norm_direct<<<nblocks, kThreads, smem, st>>>(T, theta, inside, partials, counter, out);
+  return cudaGetLastError();
+}
+
+// The mixing kernels whose gradient sums in shared memory may exceed 48 KB (nfree x 256
+// pairs, up to 56 parameters).
+static cudaError_t prepare_kernels_tddp() {
+  const int lim = 120 * 1024;
+  cudaError_t e = cudaFuncSetAttribute(k_tddp_events<true, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tddp_norm_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return e;
 }
 
 }  // namespace gfi

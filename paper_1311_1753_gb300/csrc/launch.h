@@ -127,8 +127,17 @@ cudaError_t launch_tddp_gram(const TddpPlan& T, const double* theta, const uint8
 constexpr int kTddpBlocksPerSm = 3;
 cudaError_t launch_tddp_events(const TddpPlan& T, bool grad, const double* theta,
                                const double* const* cols, int64_t n, const float4* cache,
-                               const double2* gram, double* partials, unsigned* counter,
-                               double* result, double* out_logp, int nblocks,
-                               const WeidCoef& W, cudaStream_t st);
+                               const float4* dcache, const double2* gram, const double* normd,
+                               double* partials, unsigned* counter, double* result,
+                               double* out_logp, int nblocks, const WeidCoef& W,
+                               cudaStream_t st);
+// free resonance shapes: amplitudes and shape derivatives per event (dcache: 4 nres n), and
+// N with dN/dtheta by a direct pass over the cells (out[0], out[1 + k])
+cudaError_t launch_tddp_cache_free(const TddpPlan& T, const double* theta, const double* s12,
+                                   const double* s13, int64_t n, float4* cache, float4* dcache,
+                                   cudaStream_t st);
+cudaError_t launch_tddp_norm_direct(const TddpPlan& T, const double* theta,
+                                    const uint8_t* inside, double* partials, unsigned* counter,
+                                    double* out, int nblocks, cudaStream_t st);
 
 }  // namespace gfi

@@ -116,6 +116,7 @@ def _load():
         "gf_set_mixture_path": ([vp, C.c_int], C.c_int),
         "gf_update_data": ([vp, C.c_int64, C.POINTER(_D)], C.c_int),
         "gf_nll_noalloc": ([vp, C.c_int, C.c_int, _I, C.c_int64, C.POINTER(vp), _D, vp], C.c_int),
+        "gf_tddp_sigt_density": ([vp, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -275,6 +276,11 @@ class Context:
               for r in resonances])
         return self._id(lib.gf_pdf_tddp, obs12, obs13, obs_t, obs_sigt, C.byref(k),
                         len(resonances), rs, tau, x, y, scale)
+
+    def tddp_sigt_density(self, node, b0, b1, b2):
+        """gf_tddp_sigt_density: the sigma_t density (truncated Gamma(2), rate
+        exp(b0 + b1 (s12 - sc) + b2 (s13 - sc))) of a time-dependent Dalitz node."""
+        self._ck(lib.gf_tddp_sigt_density(self.h, node, b0, b1, b2), "gf_tddp_sigt_density")
 
     def set_norm_grid(self, node, nbx, nby=0):
         self._ck(lib.gf_set_norm_grid(self.h, node, nbx, nby), "gf_set_norm_grid")

@@ -67,3 +67,19 @@ def dalitz_accept(d, envelope):
             out[idx] = u[idx] * envelope < P
         return out
     return acc
+
+
+def tddp_from_spec(spec, nb, time, dens=None, sigt_range=(0.02, 0.5)):
+    """Oracle time-dependent Dalitz model: per resonance r the parameters m0_r, g0_r, re_r,
+    im_r (index 4 r + k), then tau, x, y, scale, then (with dens) b0, b1, b2."""
+    k = spec["kin"]
+    d = oracle.Tddp(k["M"], k["m1"], k["m2"], k["m3"], k["R"], nb, nb)
+    for r in spec["resonances"]:
+        idx = [d.param(r[f]) for f in ("m0", "g0", "re", "im")]
+        d.resonance(r["channel"], r["spin"], *idx)
+    tp = [d.param(v) for v in (time["tau"], time["x"], time["y"], time["scale"])]
+    if dens is None:
+        d.time_params(*tp)
+    else:
+        d.time_params(*tp, density=tuple(d.param(v) for v in dens), sigt_range=sigt_range)
+    return d

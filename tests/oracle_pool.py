@@ -79,3 +79,20 @@ def dalitz_accept(spec):
             out[idx] = u[idx] * env < P
         return out
     return acc
+
+
+def _w_tddp(args):
+    from tests import oracle_models as om
+    spec, nb, time, dens, p, cols, grad = args
+    d = om.tddp_from_spec(spec, nb, time, dens)
+    return d.nll_t(*cols, p=p, grad=grad)
+
+
+def tddp_nll(spec, nb, time, dens, p, cols, grad=False):
+    """The mixing model's NLL (and gradient) summed over slices of the events."""
+    parts = _slices(len(cols[0]), min(16, cores()))
+    res = pool().map(_w_tddp, [(spec, nb, time, dens, p, [c[a:b] for c in cols], grad)
+                               for a, b in parts])
+    if grad:
+        return sum(r[0] for r in res), np.sum([r[1] for r in res], axis=0)
+    return sum(res)
