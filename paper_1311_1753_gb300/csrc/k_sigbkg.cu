@@ -25,7 +25,7 @@
 //              [2^-80, 2^125) are re-evaluated in FP64.
 //  mixed plan  per-event arithmetic in FP32 (GF_MIXED): data enter by a bit split and exact
 //              float differences; w expanded to degree 4 in float around the middle event
-//              of each chunk of 96 (the expansion's coefficients from the FP64-accurate
+//              of each chunk of 64 (the expansion's coefficients from the FP64-accurate
 //              series), or the Weideman series in float for unsorted data or wide chunks;
 //              the chunk's moment sums in float, folded into pairs at the chunk's end; the
 //              log-sum, the block and cross-block sums, the normalisation integrals
@@ -44,8 +44,8 @@ constexpr int kSBThreads = 128;
 constexpr int kSBChunk64 = 24;     // FP64 plan: events per expansion of w
 constexpr int kSBSub64 = 6;        // ... and per sub-chunk of a chunk too wide for one
 constexpr float kSBLim64 = 3e-4f;  // largest |Re z - Re z0| of an expanded chunk (FP64 plan)
-constexpr int kSBChunk32 = 96;     // mixed plan
-constexpr int kSBSub32 = 24;
+constexpr int kSBChunk32 = 64;     // mixed plan
+constexpr int kSBSub32 = 16;
 // mixed plan: largest |Re z - Re z0| at |Re z0| < 0.6 (the Cauchy bound |t_k| <= 6 on the
 // unit circle around z0: degree-4 truncation below 6 d^5 ~ 1.5e-12), and a wider one,
 // 0.005 |Re z0|, for |z0| >= 2, where |w| <= 1.2/|z0| on the circle of radius |z0|/2
@@ -318,7 +318,10 @@ __device__ __forceinline__ void sigbkg_block(
   }
   __syncthreads();
   const SBConst& K = sh.K;
-  const WeidCoef& W = sh.W;
+  // the series coefficients: the kernel parameter (constant bank) for the inline paths, the
+  // shared copy for the mixed plan's out-of-line direct path
+  const WeidCoef& W = Wg;
+  const WeidCoef& Ws = sh.W;
 
   Lazy acc;            // sum log P
   Lazy m[kSBMom - 1];  // moments SB_S .. SB_BL
@@ -329,7 +332,7 @@ __device__ __forceinline__ void sigbkg_block(
   // FP64 fallback for one event (P outside the float-safe range or not positive)
   auto fallback = [&](int64_t i, double xi) {
     double o[kSBMom];
-    sb_event_fp64(xi, &K, W, o);
+    sb_event_fp64(xi, &K, Ws, o);
     if (STORE) {
       out_logp[perm ? perm[i] : i] = o[SB_LOGP];
       return;
@@ -345,6 +348,7 @@ __device__ __forceinline__ void sigbkg_block(
   constexpr int kChunk = MIXED ? kSBChunk32 : kSBChunk64;
   // sorted events and at least 8 per thread: one expansion of w per chunk pays
   const bool chunked = sorted && n >= 8 * nthreads;
+  (void)g;
 
   if constexpr (!MIXED) {
     // ---------------- FP64 plan: pairs ----------------
@@ -408,12 +412,14 @@ __device__ __forceinline__ void sigbkg_block(
         for (int k = 0; k < kSBMom - 1; ++k) m[k].norm();
     };
     if (chunked) {
-      // thread g: the contiguous share [n g / T, n (g + 1) / T) of the sorted events, in
-      // chunks of kChunk with one expansion of w per chunk
-      // (a chunk too wide for one expansion is taken as sub-chunks of kSBSub64 with one
-      // each, and only a sub-chunk still too wide -- the sparsest edge of the data --
-      // evaluates w per event: the threads' shares then cost about the same)
-      const int64_t lo = n * g / nthreads, hi = n * (g + 1) / nthreads;
+      // the sorted events in chunks of kChunk with one expansion of w per chunk; chunk c
+      // goes to the thread of index c mod T in block-cyclic order (thread t of block b
+      // takes c = j T + t B + b), so that the consecutive chunks of a region that costs
+      // more -- a sparse edge of the data, where a chunk too wide for one expansion is
+      // taken as sub-chunks of kSBSub64 and a sub-chunk still too wide evaluates w per
+      // event -- spread over all blocks instead of loading a few SMs
+      const int64_t nch = (n + kChunk - 1) / kChunk;
+      const int64_t gc = (int64_t)tid * vgrid + vb;
       auto expand = [&](int64_t a, int c) {  // expansion for events a .. a + c - 1, if narrow
         const double xm = __ldg(xcol + a + (c - 1) / 2);
         const float da = fabsf(__fmul_rn((float)(__ldg(xcol + a) - xm), c1.hi));
@@ -430,8 +436,9 @@ __device__ __forceinline__ void sigbkg_block(
           one(a + k, xi, tay);
         }
       };
-      for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
-        const int cnt = (int)(hi - c0 < kChunk ? hi - c0 : kChunk);
+      for (int64_t ci = gc; ci < nch; ci += nthreads) {
+        const int64_t c0 = ci * kChunk;
+        const int cnt = (int)(n - c0 < kChunk ? n - c0 : kChunk);
         if (expand(c0, cnt)) {
           run(c0, cnt, true);
         } else {
@@ -477,7 +484,7 @@ __device__ __forceinline__ void sigbkg_block(
         wr = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(T[4], dz, T[3]), dz, T[2]), dz, T[1]), dz, T[0]);
         wi = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(T[9], dz, T[8]), dz, T[7]), dz, T[6]), dz, T[5]);
       } else {
-        w_direct_f32(zr, y, W, wr, wi);
+        w_direct_f32(zr, y, Ws, wr, wi);
       }
       const float t = __fadd_rn(__fsub_rn(xs.hi, x02.hi), __fsub_rn(xs.lo, x02.lo));
       float B = 0.f, lt = 0.f;
@@ -536,7 +543,9 @@ __device__ __forceinline__ void sigbkg_block(
         }
     };
     if (chunked) {
-      const int64_t lo = n * g / nthreads, hi = n * (g + 1) / nthreads;
+      // chunks distributed over the threads as in the FP64 plan
+      const int64_t nch = (n + kChunk - 1) / kChunk;
+      const int64_t gc = (int64_t)tid * vgrid + vb;
       F2 xms = {0.f, 0.f};
       float z0f = 0.f;
       auto dzof = [&](F2 xs) {
@@ -584,8 +593,9 @@ __device__ __forceinline__ void sigbkg_block(
             }
         }
       };
-      for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
-        const int cnt = (int)(hi - c0 < kChunk ? hi - c0 : kChunk);
+      for (int64_t ci = gc; ci < nch; ci += nthreads) {
+        const int64_t c0 = ci * kChunk;
+        const int cnt = (int)(n - c0 < kChunk ? n - c0 : kChunk);
         if (expand(c0, cnt)) {
           run(c0, cnt, true);
         } else {
