@@ -1609,7 +1609,7 @@ static int finish_set_data(gf_ctx* ctx) {
   } else if (ctx->prog.logsum) {
     per_sm = events_logsum_blocks_per_sm(ctx->prog);
   } else if (ctx->use_sb) {
-    per_sm = std::min(sigbkg_blocks_per_sm(false), sigbkg_blocks_per_sm(true));
+    per_sm = sigbkg_blocks_per_sm(false);
   } else {
     per_sm = events_1d_blocks_per_sm(true, events_1d_smem(ctx->prog, true, kThreads1D),
                                      ctx->prog.mix > 0);
@@ -1621,7 +1621,14 @@ static int finish_set_data(gf_ctx* ctx) {
   const int tpb = ctx->is_dalitz ? kThreads : kThreads1D;
   const int64_t want = (items + tpb - 1) / tpb;
   d.nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->sm_count * per_sm));
-  rc = grow(ctx, &d.partials, &d.partials_cap, (size_t)std::max(d.nblocks, 2048) * 64);
+  d.nblocks_mixed = d.nblocks;
+  if (ctx->use_sb) {  // the mixed plan holds fewer registers: more resident blocks
+    const int pm = std::max(1, std::min(sigbkg_blocks_per_sm(true), 8));
+    d.nblocks_mixed =
+        (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->sm_count * pm));
+  }
+  rc = grow(ctx, &d.partials, &d.partials_cap,
+            (size_t)std::max(std::max(d.nblocks, d.nblocks_mixed), 2048) * 64);
   if (rc) return rc;
   // norm-side partials: 1D grid blocks x 4, Gram chunks x groups x 16, cell blocks x 49
   size_t need2 = (size_t)4096 * 64;
@@ -2039,7 +2046,7 @@ static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool capt
       const bool mixed = ctx->precision == GF_MIXED && !fp64;
       CK(launch_sigbkg(ctx->sb, W, d.prog, d.cols[ctx->prog.ins[ctx->prog.mix_leaf[0]].obs], d.n,
                        d.derived, d.partials, d.counters, d.result, nullptr, nullptr, grad, mixed,
-                       d.nblocks, ctx->stream));
+                       mixed ? d.nblocks_mixed : d.nblocks, ctx->stream));
     } else {
       CK(launch_events_1d(ctx->prog, d.prog, W, cols, d.n, d.theta, d.derived, d.partials,
                           d.counters, d.result, nullptr, nullptr, grad, false,
@@ -2396,7 +2403,9 @@ static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host)
                                     d.cols[ctx->prog.ins[ctx->prog.mix_leaf[0]].obs], d.n,
                                     d.derived, d.partials, d.counters, d.result, dst,
                                     d.sorted ? d.perm : nullptr, false,
-                                    ctx->precision == GF_MIXED, d.nblocks, ctx->stream);
+                                    ctx->precision == GF_MIXED,
+                                    ctx->precision == GF_MIXED ? d.nblocks_mixed : d.nblocks,
+                                    ctx->stream);
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "launch_sigbkg");
     } else if (rc == GF_OK) {
       cudaError_t e = launch_events_1d(ctx->prog, d.prog, W, cols, d.n, d.theta, d.derived, d.partials,

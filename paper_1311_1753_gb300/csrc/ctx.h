@@ -56,6 +56,7 @@ struct DevState {
   double* h_result = nullptr;         // pinned
   size_t partials_cap = 0, partials2_cap = 0;
   int nblocks = 0;
+  int nblocks_mixed = 0;              // signal + background form: the mixed plan's grid
   // Dalitz
   uint8_t* inside = nullptr;
   double* grid_cols = nullptr;

@@ -25,7 +25,7 @@
 //              [2^-80, 2^125) are re-evaluated in FP64.
 //  mixed plan  per-event arithmetic in FP32 (GF_MIXED): data enter by a bit split and exact
 //              float differences; w expanded to degree 4 in float around the middle event
-//              of each chunk of 64 (the expansion's coefficients from the FP64-accurate
+//              of each chunk of 96 (the expansion's coefficients from the FP64-accurate
 //              series), or the Weideman series in float for unsorted data or wide chunks;
 //              the chunk's moment sums in float, folded into pairs at the chunk's end; the
 //              log-sum, the block and cross-block sums, the normalisation integrals
@@ -44,8 +44,8 @@ constexpr int kSBThreads = 128;
 constexpr int kSBChunk64 = 24;     // FP64 plan: events per expansion of w
 constexpr int kSBSub64 = 6;        // ... and per sub-chunk of a chunk too wide for one
 constexpr float kSBLim64 = 3e-4f;  // largest |Re z - Re z0| of an expanded chunk (FP64 plan)
-constexpr int kSBChunk32 = 64;     // mixed plan
-constexpr int kSBSub32 = 16;
+constexpr int kSBChunk32 = 96;     // mixed plan
+constexpr int kSBSub32 = 24;
 // mixed plan: largest |Re z - Re z0| at |Re z0| < 0.6 (the Cauchy bound |t_k| <= 6 on the
 // unit circle around z0: degree-4 truncation below 6 d^5 ~ 1.5e-12), and a wider one,
 // 0.005 |Re z0|, for |z0| >= 2, where |w| <= 1.2/|z0| on the circle of radius |z0|/2
@@ -295,6 +295,10 @@ __device__ void sb_finish(const SigBkgDesc& D, const double* __restrict__ der, c
 // Shared scratch of one block.
 struct SBShared {
   SBConst K;
+  // mixed plan: the per-thread pair sums of the moments (touched once per chunk) and the
+  // constants used only at chunk boundaries, as pairs, out of the registers
+  float mh[kSBMom - 1][kSBThreads], ml[kSBMom - 1][kSBThreads];
+  F2 mu2, yp, sv, st, lref;
   WeidCoef W;  // the series coefficients, read by every thread (and the out-of-line paths)
   double red[(kSBThreads / 32) * kSBMom];
   double fin[kSBMom];
@@ -310,7 +314,19 @@ __device__ __forceinline__ void sigbkg_block(
     unsigned* __restrict__ counter, double* __restrict__ result, double* __restrict__ out_logp,
     const int32_t* __restrict__ perm, const int vb, const int vgrid, SBShared& sh) {
   const int tid = threadIdx.x;
-  if (tid == 0) sb_consts(D, der, G, sh.K);
+  if (tid == 0) {
+    sb_consts(D, der, G, sh.K);
+    if (MIXED) {
+      SBConst& k = sh.K;
+      sh.mu2 = df_split(k.mu);
+      sh.yp = df_from(k.y);
+      sh.sv = df_from(1.0 / k.ref);
+      sh.st = df_from(k.c3t / k.ref);
+      sh.lref = df_from(k.lref);
+    }
+  }
+  if (MIXED && G)
+    for (int k = 0; k < kSBMom - 1; ++k) sh.mh[k][tid] = sh.ml[k][tid] = 0.f;
   {
     const float* src = reinterpret_cast<const float*>(&Wg);
     float* dst = reinterpret_cast<float*>(&sh.W);
@@ -462,13 +478,12 @@ __device__ __forceinline__ void sigbkg_block(
     }
   } else {
     // ---------------- mixed plan: FP32 per event ----------------
-    const F2 mu2 = df_split(K.mu), x02 = df_split(K.x0);
+    const F2 x02 = df_split(K.x0);
     const float y = (float)K.y;
     // constants that multiply per-event values as pairs (one extra FMA each): the float
     // result then carries per-event rounding only
-    const F2 c1p = df_from(K.c1), yp = df_from(K.y), ccp = df_from(K.cc), pwp = df_from(K.pw);
+    const F2 c1p = df_from(K.c1), ccp = df_from(K.cc), pwp = df_from(K.pw);
     const F2 cap = df_from(K.ca), cbp = df_from(K.cb);
-    const F2 sv = df_from(1.0 / K.ref), st = df_from(K.c3t / K.ref), lref = df_from(K.lref);
     auto kmul = [](float a, F2 c) { return __fmaf_rn(a, c.hi, __fmul_rn(a, c.lo)); };
     ProdF prod;
     int pcount = 0;  // events in the running product
@@ -490,7 +505,7 @@ __device__ __forceinline__ void sigbkg_block(
       float B = 0.f, lt = 0.f;
       if (t > 0.f) {
         if (half) {
-          B = __fmul_rn(__fsqrt_rn(t), __expf(-kmul(t, ccp)));
+          B = __fmul_rn(__fmul_rn(t, rsqrtf(t)), __expf(-kmul(t, ccp)));
         } else {
           lt = __logf(t);
           B = __expf(kmul(lt, pwp) - kmul(t, ccp));
@@ -508,7 +523,7 @@ __device__ __forceinline__ void sigbkg_block(
       prod.mul(P);
       ++pcount;
       if (G) {
-        const float s = __frcp_rn(P);
+        const float s = __fdividef(1.f, P);
         const float a = s * wr, b = s * wi, za = zr * a;
         cm[SB_S - 1] += s;
         cm[SB_R - 1] += a;
@@ -530,17 +545,23 @@ __device__ __forceinline__ void sigbkg_block(
     auto flush = [&]() {
       if (STORE) return;
       acc.add(prod.log());
-      if (pcount) acc.add(df_mul_f(lref, (float)pcount));
+      if (pcount) acc.add(df_mul_f(sh.lref, (float)pcount));
       prod = ProdF();
       pcount = 0;
       acc.norm();
-      if (G)
+      if (G) {
+        const F2 sv = sh.sv, st = sh.st;
 #pragma unroll
         for (int k = 0; k < kSBMom - 1; ++k) {
-          m[k].add(df_mul_f(k + 1 < SB_B ? sv : st, cm[k]));
-          m[k].norm();
+          const F2 v = df_mul_f(k + 1 < SB_B ? sv : st, cm[k]);
+          const F2 a = two_sum(sh.mh[k][tid], v.hi);
+          sh.mh[k][tid] = a.hi;
+          const F2 b = fast_two_sum(a.hi, __fadd_rn(sh.ml[k][tid], __fadd_rn(a.lo, v.lo)));
+          sh.mh[k][tid] = b.hi;
+          sh.ml[k][tid] = b.lo;
           cm[k] = 0.f;
         }
+      }
     };
     if (chunked) {
       // chunks distributed over the threads as in the FP64 plan
@@ -556,7 +577,7 @@ __device__ __forceinline__ void sigbkg_block(
       auto expand = [&](int64_t a, int c) {
         const double xm = __ldg(xcol + a + (c - 1) / 2);
         xms = df_split(xm);
-        const F2 z0 = df_mul(df_split(xm - K.mu), c1p);
+        const F2 z0 = df_mul(df_split(xm - K.mu), c1p);  // (Re z0 in pairs)
         z0f = __fadd_rn(z0.hi, z0.lo);
         const float da = fabsf(dzof(df_split(__ldg(xcol + a))));
         const float db = fabsf(dzof(df_split(__ldg(xcol + a + c - 1))));
@@ -564,7 +585,7 @@ __device__ __forceinline__ void sigbkg_block(
         const bool ok = fmaxf(da, db) <= (az >= 2.f ? fmaxf(kSBLim32, kSBLim32Rel * az) : kSBLim32);
         if (ok) {
           F2 tr[5], ti[5];
-          tay_coefs<4>(z0, yp, W, tr, ti);
+          tay_coefs<4>(z0, sh.yp, W, tr, ti);
 #pragma unroll
           for (int k = 0; k < 5; ++k) {
             T[k] = __fadd_rn(tr[k].hi, tr[k].lo);
@@ -586,6 +607,7 @@ __device__ __forceinline__ void sigbkg_block(
               if (tay) {
                 one(a + k + j, xv[j], xs, __fadd_rn(z0f, dz), dz, true);
               } else {
+                const F2 mu2 = sh.mu2;
                 const float zr =
                     kmul(__fadd_rn(__fsub_rn(xs.hi, mu2.hi), __fsub_rn(xs.lo, mu2.lo)), c1p);
                 one(a + k + j, xv[j], xs, zr, 0.f, false);
@@ -611,6 +633,7 @@ __device__ __forceinline__ void sigbkg_block(
       for (int64_t i = g; i < n; i += nthreads) {
         const double xi = __ldcs(xcol + i);
         const F2 xs = df_split(xi);
+        const F2 mu2 = sh.mu2;
         const float zr = kmul(__fadd_rn(__fsub_rn(xs.hi, mu2.hi), __fsub_rn(xs.lo, mu2.lo)), c1p);
         one(i, xi, xs, zr, 0.f, false);
         if (++since == kSBChunk32) {
@@ -626,10 +649,11 @@ __device__ __forceinline__ void sigbkg_block(
   // block sums (fixed order), then the last block's cross-block sums and the gradient
   const int mm = G ? kSBMom : 1;
   constexpr int stride = 1 + kMaxFree1D;
-  F2 vals[kSBMom];  // the register sums, copied once for the indexed reduction
+  F2 vals[kSBMom];  // the register (FP64 plan) or shared (mixed plan) sums, copied once
   vals[0] = acc.get();
 #pragma unroll
-  for (int k = 1; k < kSBMom; ++k) vals[k] = m[k - 1].get();
+  for (int k = 1; k < kSBMom; ++k)
+    vals[k] = MIXED ? F2{sh.mh[k - 1][tid], sh.ml[k - 1][tid]} : m[k - 1].get();
   block_sum_pairs([&](int k) -> F2 { return vals[k]; }, mm, sh.red,
                   partials + (size_t)vb * stride);
   if (!arrive_last_of(counter, (unsigned)vgrid, &sh.last)) return;
@@ -641,7 +665,7 @@ __device__ __forceinline__ void sigbkg_block(
 }
 
 template <bool G, bool MIXED, bool STORE>
-__global__ void __launch_bounds__(kSBThreads, 4) k_sigbkg(
+__global__ void __launch_bounds__(kSBThreads, MIXED ? 6 : 4) k_sigbkg(
     const __grid_constant__ SigBkgDesc D, const __grid_constant__ WeidCoef W,
     const Program* __restrict__ prog, const double* __restrict__ xcol, const int64_t n,
     const double* __restrict__ der, double* __restrict__ partials,

@@ -198,8 +198,10 @@ static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
       if (c->dev.tick_kind == 3) {
         const void* fsb = static_cast<const char*>(c->dev.tick_desc) +
                           ((sizeof(Fit1D) + 255) / 256) * 256;
-        it_sb[n_sb++] = TickItem{fsb, th, res, tot_sb, c->dev.nblocks};
-        tot_sb += c->dev.nblocks;
+        // the grid of the plan the tick runs (the fit's standalone launches use the same)
+        const int nb = S->opts.precision == GF_MIXED ? c->dev.nblocks_mixed : c->dev.nblocks;
+        it_sb[n_sb++] = TickItem{fsb, th, res, tot_sb, nb};
+        tot_sb += nb;
       } else {
         it_ev1[n_ev1++] = TickItem{c->dev.tick_desc, th, res, tot_ev1, c->dev.nblocks};
         tot_ev1 += c->dev.nblocks;
