@@ -573,6 +573,98 @@ __device__ __forceinline__ void gram_apply(const double* __restrict__ gram, cons
   }
 }
 
+// FP64 plans with every resonance cached (fixed shapes): an event's cached amplitudes, the
+// coefficients and the per-resonance gradient sums s conj(A) a_r (s = -2/|A|^2) held in
+// registers (NR >= nres slots), A = 1 + sum c_r a_r accumulated as a lazily renormalised
+// pair (each product's rounding error and each sum's carried in a float), the gradient
+// sums renormalised every 16 events and added to the shared gradient slots once per
+// thread.  Fewer operations and no shared-memory traffic per event than the general path.
+__device__ __forceinline__ void lazy_prod(float& h, float& l, F2 a, F2 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const F2 t = two_sum(h, p);
+  h = t.hi;
+  l = __fadd_rn(l, __fadd_rn(t.lo, e));
+}
+template <int NR, bool G>
+__device__ __forceinline__ void cached_pairs_loop(const DalitzPlan& D, const DzC<DF>& C,
+                                                  const void* __restrict__ cache,
+                                                  int64_t stride, int64_t n, int vb, int vgrid,
+                                                  Acc<DF>& acc, Acc<DF>* gacc, int bd) {
+  const int nres = D.nres;
+  F2 cr[NR], ci[NR], gr[NR], gi[NR];
+  int slot[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    cr[r] = r < nres ? F2(C.cr[r]) : F2{0.f, 0.f};
+    ci[r] = r < nres ? F2(C.ci[r]) : F2{0.f, 0.f};
+    slot[r] = r < nres ? D.res[r].ev_cached : 0;
+    gr[r] = gi[r] = F2{0.f, 0.f};
+  }
+  const float4* cq = reinterpret_cast<const float4*>(cache);
+  int since = 0;
+  for (int64_t i = (int64_t)vb * bd + threadIdx.x; i < n; i += (int64_t)vgrid * bd) {
+    F2 ar[NR], ai[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (r < nres) {
+        const float4 v = __ldg(cq + (size_t)slot[r] * stride + i);
+        ar[r] = F2{v.x, v.y};
+        ai[r] = F2{v.z, v.w};
+      } else {
+        ar[r] = ai[r] = F2{0.f, 0.f};
+      }
+    }
+    float hr = 1.f, lr = 0.f, hi = 0.f, li = 0.f;  // A = a_NR + sum c_r a_r
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (r < nres) {
+        lazy_prod(hr, lr, cr[r], ar[r]);
+        lazy_prod(hr, lr, df_neg(ci[r]), ai[r]);
+        lazy_prod(hi, li, cr[r], ai[r]);
+        lazy_prod(hi, li, ci[r], ar[r]);
+      }
+    }
+    const F2 Ar = fast_two_sum(hr, lr), Ai = fast_two_sum(hi, li);
+    const F2 P = df_add(df_mul(Ar, Ar), df_mul(Ai, Ai));
+    acc.add(df_neg(df_log_tab(P, s_log_tab)));
+    if (G) {
+      const F2 sc = df_mul_f(df_rcp(P), -2.f);
+      const F2 Sr = df_mul(sc, Ar), Si = df_mul(sc, Ai);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (r < nres) {
+          // s conj(A) a_r: real part to d/dRe c_r, Si ar - Sr ai to d/dIm c_r
+          lazy_prod(gr[r].hi, gr[r].lo, Sr, ar[r]);
+          lazy_prod(gr[r].hi, gr[r].lo, Si, ai[r]);
+          lazy_prod(gi[r].hi, gi[r].lo, Si, ar[r]);
+          lazy_prod(gi[r].hi, gi[r].lo, df_neg(Sr), ai[r]);
+        }
+      }
+      if (++since == 16) {
+        since = 0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          gr[r] = fast_two_sum(gr[r].hi, gr[r].lo);
+          gi[r] = fast_two_sum(gi[r].hi, gi[r].lo);
+        }
+      }
+    }
+  }
+  if (G) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (r < nres) {
+        const DalitzRes& R = D.res[r];
+        if (R.g_re >= 0) gacc[R.g_re * bd].add(DF(fast_two_sum(gr[r].hi, gr[r].lo)));
+        if (R.g_im >= 0) gacc[R.g_im * bd].add(DF(fast_two_sum(gi[r].hi, gi[r].lo)));
+      }
+    }
+  }
+}
+
 // Body of one (virtual) block vb of the vgrid blocks of a stream launch.  T = float (FP32
 // plans: amplitudes in float with the hi/lo constants of ResKf) or DF (FP64 plans: every
 // step in double-float pairs; only the event coordinates' differences enter in FP64).
@@ -629,7 +721,14 @@ __device__ __forceinline__ void dalitz_stream_block(
   __syncthreads();
   const bool need0 = sh.need_ch[0] != 0, need1 = sh.need_ch[1] != 0, need2 = sh.need_ch[2] != 0;
   Acc<T> acc;
-  const int64_t nitems = (METRIC == METRIC_NORM) ? (int64_t)D.nbx * D.nby : n;
+  // FP64 plans with every resonance cached: the register path above
+  // (up to 8 resonances; larger models take the general path)
+  constexpr bool kFastCached = CO && !kF && METRIC == METRIC_NLL;
+  const bool fast = kFastCached && nres <= 8;
+  if constexpr (kFastCached) {
+    if (fast) cached_pairs_loop<8, G>(D, sh.C, cache, cache_stride, n, vb, vgrid, acc, gacc, bd);
+  }
+  const int64_t nitems = fast ? 0 : (METRIC == METRIC_NORM) ? (int64_t)D.nbx * D.nby : n;
 
   for (int64_t i = (int64_t)vb * bd + tid; i < nitems; i += (int64_t)vgrid * bd) {
     if constexpr (CO) {
@@ -816,12 +915,15 @@ __device__ __forceinline__ void dalitz_stream_block(
 // Registers per variant (measured): pair (DF) event passes are held to 85 (3 blocks of
 // 256 per SM) -- their dependent pair chains need the warps more than the registers --,
 // FP32 ones to 128 (2 blocks); the pair cell pass keeps its registers (1 block).
-template <typename T, bool G, int METRIC>
+// The cached-only FP64 event pass holds its amplitudes and gradient sums in registers
+// (2 blocks).
+template <typename T, bool G, int METRIC, bool CO>
 constexpr int dz_min_blocks() {
-  return std::is_same<T, DF>::value ? (METRIC == METRIC_NORM ? 1 : 3) : 2;
+  return std::is_same<T, DF>::value ? (METRIC == METRIC_NORM ? 1 : (CO && METRIC == METRIC_NLL ? 2 : 3))
+                                    : 2;
 }
 template <typename T, bool G, int METRIC, bool CO>
-__global__ void __launch_bounds__(kThreads, dz_min_blocks<T, G, METRIC>()) k_dalitz_stream(
+__global__ void __launch_bounds__(kThreads, dz_min_blocks<T, G, METRIC, CO>()) k_dalitz_stream(
     const DalitzPlan D, const double* __restrict__ theta, const double* __restrict__ s12d,
     const double* __restrict__ s13d, const float* __restrict__ sf, int64_t n,
     const void* __restrict__ cache, int64_t cache_stride, int cache_wide,
