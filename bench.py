@@ -42,8 +42,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # traffic of one launch are ncu counters of the 10^7-event launch of this build (the
 # profile summary of k_sigbkg under profiles/); None where no capture of the current
 # kernel exists.
-FP32_FLOPS_PER_EVENT = {}
-TRAFFIC_PER_LAUNCH = {}
+FP32_FLOPS_PER_EVENT = {"voigt_grad": 640.2}   # FADD 359.2 + FMUL 48.4 + 2 x FFMA 116.3
+TRAFFIC_PER_LAUNCH = {"voigt_grad": 81.53e6,        # 80.24 MB read + 1.29 MB written
+                      "voigt_grad_mixed": 82.50e6}  # 80.46 MB read + 2.04 MB written
 # the headline workload's name, shared by both arms' JSON lines
 VOIGT_WORKLOAD = ("1D composite: Voigtian (mu,sigma,Gamma) + threshold (c) with fraction f, "
                   "10^7 FP64 events, 2 x 10,000-bin grid normalisation")
@@ -221,6 +222,8 @@ def time_steps(torch, ctx, thetas, steps, warmup, grad=True, flush=True):
         (ctx.nll_grad if grad else ctx.nll)(thetas[k % len(thetas)])
     torch.cuda.synchronize()
     kern, launches, vals = [], 0, []
+    # the timed region is the profiler range (ncu --profile-from-start off lists only it)
+    torch.cuda.profiler.start()
     t0 = time.perf_counter()
     for k in range(steps):
         if flush:
@@ -235,6 +238,7 @@ def time_steps(torch, ctx, thetas, steps, warmup, grad=True, flush=True):
         launches += ctx.last_eval_stats()[1]
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    torch.cuda.profiler.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
     ctx.set_stream(0)
     return dict(step_ms=ms, kernel_ms=kern, launches=launches, wall_s=wall, values=vals)
@@ -368,7 +372,7 @@ def measured_fp64_tflops(torch, n=4096, reps=3):
     return 2.0 * n ** 3 / best / 1e12
 
 
-def voigt_roofline(torch, n, kern_s, hbm_peak):
+def voigt_roofline(torch, n, kern_s, hbm_peak, mixed=False):
     """Roofline of the headline event kernel (k_sigbkg<grad>, FP64 plan).  Headline: the
     method's work, FP64_FLOPS_PER_EVENT per event, against the FP64 unit peak (the pass
     computes FP64-accurate results on the FP32 pipe, so it can exceed the FP64 pipe's
@@ -377,8 +381,10 @@ def voigt_roofline(torch, n, kern_s, hbm_peak):
     ach64 = FP64_FLOPS_PER_EVENT["voigt_grad"] * n / kern_s / 1e12
     hb = 8 * n / kern_s / 1e9
     rf = {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-          "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get("voigt_grad"),
-          "kernel": "k_sigbkg<grad, FP64 plan> (double-float on the FP32 pipe)",
+          "frac": ach64 / FP64_PEAK_TFLOPS,
+          "traffic": TRAFFIC_PER_LAUNCH.get("voigt_grad_mixed" if mixed else "voigt_grad"),
+          "kernel": ("k_sigbkg<grad, mixed plan> (FP32 per event, FP64 sums)" if mixed else
+                     "k_sigbkg<grad, FP64 plan> (double-float on the FP32 pipe)"),
           "kernel_ms": kern_s * 1e3,
           "algorithmic_flops_per_event": FP64_FLOPS_PER_EVENT["voigt_grad"],
           "peak_source": "FP64 unit count: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
@@ -388,7 +394,7 @@ def voigt_roofline(torch, n, kern_s, hbm_peak):
         rf["fp64_dgemm_measured_tflops"] = measured_fp64_tflops(torch)
     except Exception as e:  # context only
         rf["fp64_dgemm_measured_tflops"] = repr(e)[:100]
-    f32 = FP32_FLOPS_PER_EVENT.get("voigt_grad")
+    f32 = None if mixed else FP32_FLOPS_PER_EVENT.get("voigt_grad")
     if f32:
         a32 = f32 * n / kern_s / 1e12
         rf["fp32_issue"] = {"flops_per_event": f32, "achieved_tflops": a32,
@@ -405,8 +411,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="voigt",
-                    choices=["voigt", "exp", "dalitz", "dalitz-mixed", "exp-sweep", "binned",
-                             "conv", "tddp"])
+                    choices=["voigt", "voigt-mixed", "exp", "dalitz", "dalitz-mixed", "exp-sweep",
+                             "binned", "conv", "tddp"])
     ap.add_argument("--sweep-sizes", default="1000000,10000000,100000000,1000000000",
                     help="event counts of --workload exp-sweep")
     ap.add_argument("--no-extra", action="store_true")
@@ -495,11 +501,15 @@ def main():
     # arithmetic of the timed event pass: double-float pairs of f32 (FP64-accurate: 1e-12
     # per event against the FP64 oracle, f64 in and out) for the 1D and Dalitz FP64 paths,
     # f32 amplitudes for the mixed Dalitz path
-    dtype = {"dalitz-mixed": "f32"}.get(args.workload, "df64")
-    if args.workload == "voigt":
+    dtype = {"dalitz-mixed": "f32", "voigt-mixed": "f32"}.get(args.workload, "df64")
+    if args.workload in ("voigt", "voigt-mixed"):
         n = 10_000_000
-        ctx, root, obs, cols, th0 = voigt_workload(gf, n, seed, gf.GF_FP64)
+        mixed = args.workload == "voigt-mixed"
+        ctx, root, obs, cols, th0 = voigt_workload(gf, n, seed,
+                                                   gf.GF_MIXED if mixed else gf.GF_FP64)
         wl = VOIGT_WORKLOAD
+        if mixed:
+            metric = "NLL+gradient evaluations: events x evals/s (1D composite, mixed precision)"
     elif args.workload == "exp":
         n = 100_000
         ctx, root, obs, cols, th0 = exp_workload(gf, n, synth.SEED_EXP + rank, gf.GF_FP64)
@@ -535,8 +545,8 @@ def main():
     kern_s = float(np.mean(res["kernel_ms"])) / 1e3
 
     roofline = None
-    if args.workload == "voigt":
-        roofline = voigt_roofline(torch, n, kern_s, hbm_peak)
+    if args.workload in ("voigt", "voigt-mixed"):
+        roofline = voigt_roofline(torch, n, kern_s, hbm_peak, mixed=mixed)
 
     # end-to-end through the C ABI with host buffers
     e2e = None

@@ -119,7 +119,6 @@ static void free_dev(gf_ctx* ctx) {
   cudaFree(d.partials);
   cudaFree(d.partials2);
   cudaFree(d.counters);
-  cudaFree(d.result);
   cudaFree(d.norm_out);
   cudaFree(d.inside);
   cudaFree(d.grid_cols);
@@ -133,7 +132,6 @@ static void free_dev(gf_ctx* ctx) {
   if (d.ev0) cudaEventDestroy(d.ev0);
   if (d.ev1) cudaEventDestroy(d.ev1);
   if (d.evm) cudaEventDestroy(d.evm);
-  cudaFree(d.flag);
   cudaFree(d.tick_desc);
   cudaFree(d.prog);
   cudaFree(d.perm);
@@ -1534,17 +1532,22 @@ static int alloc_work(gf_ctx* ctx) {
     CK(cudaMalloc(&d.counters, sizeof(unsigned) * 4));
     CK(cudaMemset(d.counters, 0, sizeof(unsigned) * 4));
   }
-  if (!d.result) CK(cudaMalloc(&d.result, sizeof(double) * 64));
   if (!d.norm_out) CK(cudaMalloc(&d.norm_out, sizeof(double) * 64));
   if (!d.h_theta) CK(cudaMallocHost(&d.h_theta, sizeof(double) * 64 * ((npar + 63) / 64)));
-  if (!d.h_result) CK(cudaMallocHost(&d.h_result, sizeof(double) * 64));
+  if (!d.h_result) {
+    // NLL and gradient (slots 0 .. nfree) and the data-check flag (slot 63) are written by
+    // the kernels straight into this pinned buffer through its device mapping: no copy
+    // back per evaluation
+    CK(cudaMallocHost(&d.h_result, sizeof(double) * 64));
+    std::memset(d.h_result, 0, sizeof(double) * 64);
+    void* p = nullptr;
+    CK(cudaHostGetDevicePointer(&p, d.h_result, 0));
+    d.result = static_cast<double*>(p);
+    d.flag = reinterpret_cast<int*>(d.result + 63);
+  }
   if (!d.ev0) CK(cudaEventCreate(&d.ev0));
   if (!d.ev1) CK(cudaEventCreate(&d.ev1));
   if (!d.evm) CK(cudaEventCreate(&d.evm));
-  if (!d.flag) {
-    CK(cudaMalloc(&d.flag, sizeof(int)));
-    CK(cudaMemset(d.flag, 0, sizeof(int)));
-  }
   return GF_OK;
 }
 
@@ -1618,14 +1621,15 @@ static int finish_set_data(gf_ctx* ctx) {
   // signal + background form: 16 events per thread at least, so that sorted data reach the
   // expanded (chunked) event loop at every size
   const int64_t items = ctx->is_dalitz ? d.n : ctx->use_sb ? (d.n + 15) / 16 : (d.n + 1) / 2;
-  const int tpb = ctx->is_dalitz ? kThreads : kThreads1D;
+  const int tpb = ctx->is_dalitz ? kThreads : ctx->use_sb ? sigbkg_threads(false) : kThreads1D;
   const int64_t want = (items + tpb - 1) / tpb;
   d.nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->sm_count * per_sm));
   d.nblocks_mixed = d.nblocks;
-  if (ctx->use_sb) {  // the mixed plan holds fewer registers: more resident blocks
+  if (ctx->use_sb) {  // the mixed plan: its own block size and resident blocks per SM
     const int pm = std::max(1, std::min(sigbkg_blocks_per_sm(true), 8));
-    d.nblocks_mixed =
-        (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)ctx->sm_count * pm));
+    const int tm = sigbkg_threads(true);
+    d.nblocks_mixed = (int)std::max<int64_t>(
+        1, std::min<int64_t>((items + tm - 1) / tm, (int64_t)ctx->sm_count * pm));
   }
   rc = grow(ctx, &d.partials, &d.partials_cap,
             (size_t)std::max(std::max(d.nblocks, d.nblocks_mixed), 2048) * 64);
@@ -2055,11 +2059,7 @@ static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool capt
     (*launches)++;
   }
   CK(cudaEventRecordWithFlags(d.ev1, ctx->stream, evf));
-  CK(cudaMemcpyAsync(d.h_result, d.result, sizeof(double) * (1 + (grad ? nf : 0)),
-                     cudaMemcpyDeviceToHost, ctx->stream));
-  // data-check flag rides along in the last pinned slot
-  CK(cudaMemcpyAsync(reinterpret_cast<int*>(d.h_result + 63), d.flag, sizeof(int),
-                     cudaMemcpyDeviceToHost, ctx->stream));
+  (void)nf;  // the result and the data-check flag are already in d.h_result (mapped)
   return GF_OK;
 }
 
@@ -2114,13 +2114,7 @@ static int tddp_enqueue(gf_ctx* ctx, bool grad, double* out_logp, int* launches)
                         d.result, out_logp, d.nblocks, weideman(), ctx->stream));
   (*launches)++;
   CK(cudaEventRecord(d.ev1, ctx->stream));
-  if (!out_logp) {
-    CK(cudaMemcpyAsync(d.h_result, d.result, sizeof(double) * (1 + (grad ? T.nfree : 0)),
-                       cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(reinterpret_cast<int*>(d.h_result + 63), d.flag, sizeof(int),
-                       cudaMemcpyDeviceToHost, ctx->stream));
-  }
-  return GF_OK;
+  return GF_OK;  // result and data-check flag: written into d.h_result (mapped)
 }
 
 int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64) {
@@ -2215,8 +2209,7 @@ int evaluate_finish(gf_ctx* ctx, double* nll, double* grad, bool grad_wanted) {
   else cudaGetLastError();
   const int bad = *reinterpret_cast<const int*>(d.h_result + 63);
   if (bad) {
-    *reinterpret_cast<int*>(d.h_result + 63) = 0;
-    CK(cudaMemset(d.flag, 0, sizeof(int)));
+    *reinterpret_cast<volatile int*>(d.h_result + 63) = 0;
     *nll = INFINITY;
     return set_error(ctx, GF_EINVAL, "gf_update_data: an event lies outside its range/region");
   }

@@ -50,7 +50,7 @@ struct DevState {
   double* partials = nullptr;
   double* partials2 = nullptr;
   unsigned* counters = nullptr;       // [0] events, [1] norm
-  double* result = nullptr;           // [1 + nfree]
+  double* result = nullptr;           // [1 + nfree]: device mapping of h_result
   double* norm_out = nullptr;
   double* h_theta = nullptr;          // pinned
   double* h_result = nullptr;         // pinned
@@ -79,7 +79,7 @@ struct DevState {
                                       // 3: 1D signal + background (FitSB after the Fit1D,
                                       // 256-byte aligned)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;  // eval start, stream kernel, end
-  int* flag = nullptr;                // device-side data check (0 = ok)
+  int* flag = nullptr;                // data check (0 = ok): slot 63 of h_result, mapped
   // sorted layout of owned 1D columns (ascending by the first Voigtian's observable)
   bool sorted = false;
   int sort_obs = -1;                  // the column the events are sorted by

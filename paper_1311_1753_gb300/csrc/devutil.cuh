@@ -86,10 +86,15 @@ struct Neu {
 // red[warp * m + k], one barrier, then thread k adds the warps' k-th sums in FP64.
 // red: (blockDim / 32) * m doubles.  Replaces m separate FP64 block sums (2 barriers and
 // 5 FP64 shuffle-adds per value and thread).
-template <class Val>
-__device__ __forceinline__ void block_sum_pairs(Val val, int m, double* red, double* out) {
+// M >= 0: the count m known at compile time (the loop unrolls, val's index is a constant,
+// so a caller's per-thread array stays in registers).
+template <int M = -1, class Val>
+__device__ __forceinline__ void block_sum_pairs(Val val, int m, double* red, double* out,
+                                                int ostride = 1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int k = 0; k < m; ++k) {
+  if (M >= 0) m = M;
+#pragma unroll
+  for (int k = 0; k < (M >= 0 ? M : m); ++k) {
     F2 v = val(k);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -102,31 +107,40 @@ __device__ __forceinline__ void block_sum_pairs(Val val, int m, double* red, dou
   for (int k = threadIdx.x; k < m; k += blockDim.x) {
     double r = 0.0;
     for (int w = 0; w < nw; ++w) r += red[w * m + k];
-    out[k] = r;
+    out[(size_t)k * ostride] = r;
   }
 }
 
-// Cross-block sums by the last block: out[k] = sum over b < nblk of partials[b stride + k],
-// k < m, in a fixed order.  Warp w takes k = w, w + nwarps, ...; its lanes stride over the
-// blocks with all their loads in flight (16 per lane and pass), summing as pairs (partials
-// enter by the bit split: no FP64 conversions; the padding zeros add exactly), then a
-// fixed shuffle tree.  Called by every thread of one block; ends with a barrier.
+// Cross-block sums by the last block: out[k] = sum over b < nblk of
+// partials[b stride + k kstride], k < m, in a fixed order.  Warp w takes k = w, w + nwarps,
+// ...; its lanes stride over the blocks with all their loads in flight (kPer per lane and
+// pass), summing as pairs in two interleaved chains (partials enter by the bit split: no
+// FP64 conversions; the padding zeros add exactly), then a fixed shuffle tree.  The
+// value-major layout (stride 1, kstride >= nblk) makes each warp load one contiguous run
+// of 256 bytes; the block-major one (kstride 1) touches a line per lane.  Called by every
+// thread of one block; ends with a barrier.
+template <int kPer = 16>
 __device__ inline void reduce_partials(const double* partials, int nblk, int stride, int m,
-                                       double* out) {
-  constexpr int kPer = 16;
+                                       double* out, int kstride = 1) {
+  static_assert(kPer % 2 == 0, "two chains");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int k = warp; k < m; k += nw) {
-    F2 a = {0.f, 0.f};
+    const double* p = partials + (size_t)k * kstride;
+    F2 a = {0.f, 0.f}, a2 = {0.f, 0.f};
     for (int b0 = 0; b0 < nblk; b0 += 32 * kPer) {
       double v[kPer];
 #pragma unroll
       for (int j = 0; j < kPer; ++j) {
         const int b = b0 + lane + 32 * j;
-        v[j] = b < nblk ? __ldcg(partials + (size_t)b * stride + k) : 0.0;
+        v[j] = b < nblk ? __ldcg(p + (size_t)b * stride) : 0.0;
       }
 #pragma unroll
-      for (int j = 0; j < kPer; ++j) a = df_add(a, df_split(v[j]));
+      for (int j = 0; j < kPer; j += 2) {
+        a = df_add(a, df_split(v[j]));
+        a2 = df_add(a2, df_split(v[j + 1]));
+      }
     }
+    a = df_add(a, a2);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const F2 u = {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};

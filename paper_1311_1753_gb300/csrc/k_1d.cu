@@ -401,17 +401,33 @@ __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& 
     if (threadIdx.x == 0) partials[(size_t)vb * 4 + k] = r;
   }
   if (!arrive_last_of(counter, (unsigned)vgrid, last)) return;
-  // last block: per leaf, fixed-order sum over its chunks, then every leaf record
-  for (int l = 0; l < P.nleaf; ++l) {
-    const LeafDesc& L = P.leaf[l];
-    if (L.nbins <= 0) continue;
-    for (int k = 0; k < 4; ++k) {
-      Neu a;
-      for (int b = threadIdx.x; b < L.grid_nblocks; b += blockDim.x)
-        a.add(__ldcg(partials + (size_t)(L.grid_first_block + b) * 4 + k));
-      const double r = block_sum(a.get(), red);
-      if (threadIdx.x == 0) sums[l][k] = r * (L.hi - L.lo) / L.nbins;
-      __syncthreads();
+  // last block: one warp per (leaf, value), its lanes' loads of the leaf's chunk partials
+  // all in flight, fixed-order pair sums; then every leaf record
+  {
+    constexpr int kPer = 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int q = warp; q < 4 * P.nleaf; q += nw) {
+      const LeafDesc& L = P.leaf[q >> 2];
+      const int k = q & 3;
+      if (L.nbins <= 0) continue;  // uniform over the warp
+      F2 a = {0.f, 0.f};
+      for (int b0 = 0; b0 < L.grid_nblocks; b0 += 32 * kPer) {
+        double t[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+          const int b = b0 + lane + 32 * j;
+          t[j] = b < L.grid_nblocks ? __ldcg(partials + (size_t)(L.grid_first_block + b) * 4 + k)
+                                    : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) a = df_add(a, df_split(t[j]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const F2 u = {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+        a = df_add(a, u);
+      }
+      if (lane == 0) sums[q >> 2][k] = df_to(a) * (L.hi - L.lo) / L.nbins;
     }
   }
   __syncthreads();
@@ -1591,7 +1607,8 @@ __global__ void k_check_range(const Cols cols, int nobs, int64_t n, const Range 
       const double v = cols.c[o][i];
       bad |= !(v >= R.lo[o] && v <= R.hi[o]);
     }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+  // the flag lives in mapped pinned host memory: a plain store (every writer stores 1)
+  if (__syncthreads_or(bad) && threadIdx.x == 0) *reinterpret_cast<volatile int*>(flag) = 1;
 }
 
 cudaError_t launch_check_range(const Cols& cols, int nobs, int64_t n, const double* lo,

@@ -373,7 +373,8 @@ __global__ void k_dalitz_check(const DalitzPlan D, const double* __restrict__ s1
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     bad |= !inside_region(D, s12[i], s13[i]);
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(flag, 1);
+  // the flag lives in mapped pinned host memory: a plain store (every writer stores 1)
+  if (__syncthreads_or(bad) && threadIdx.x == 0) *reinterpret_cast<volatile int*>(flag) = 1;
 }
 
 __global__ void k_dalitz_fcols(const DalitzPlan D, const double* __restrict__ s12,
@@ -865,12 +866,12 @@ __device__ __forceinline__ void dalitz_stream_block(
   if (METRIC == METRIC_STORE) return;
 
   const int m = 1 + (G ? nf : 0);
-  const int stride_p = 1 + 2 * kMaxRes * 2;
+  // partials value-major: value k of block b at partials[k vgrid + b]
   block_sum_pairs([&](int k) { return k == 0 ? acc.pair() : gacc[(k - 1) * bd].pair(); }, m, red,
-                  partials + (size_t)vb * stride_p);
+                  partials + vb, vgrid);
   if (!arrive_last_of(counter, (unsigned)vgrid, &sh.last)) return;
   double* tot = sh.tot;
-  reduce_partials(partials, vgrid, stride_p, m, tot);
+  reduce_partials(partials, vgrid, 1, m, tot, vgrid);
   __syncthreads();
   if (METRIC == METRIC_NORM) {
     const double dA = D.hx * D.hy;
@@ -1613,9 +1614,9 @@ __global__ void __launch_bounds__(kThreads) k_tddp_norm_direct(
   block_sum_pairs([&](int k) -> F2 {
                     return k == 0 ? F2(sI) : k < 5 ? F2(sd[k - 1]) : gsh[(k - 5) * bd + tid];
                   },
-                  m, red, partials + (size_t)blockIdx.x * kTddpNormStride);
+                  m, red, partials + blockIdx.x, gridDim.x);  // value-major
   if (!arrive_last_of(counter, gridDim.x, &last)) return;
-  reduce_partials(partials, gridDim.x, kTddpNormStride, m, tot);
+  reduce_partials(partials, gridDim.x, 1, m, tot, gridDim.x);
   const double dA = D.hx * D.hy;
   if (tid == 0) out[0] = dA * tot[0];
   for (int k = tid; k < nf; k += bd) {
@@ -1805,11 +1806,10 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   }
   if (STORE) return;
   const int m = 1 + (G ? nf : 0);
-  const int stride = 1 + 4 * kMaxRes + 8;
   block_sum_pairs([&](int k) -> F2 { return k == 0 ? df_split(acc.get()) : gsh[(k - 1) * bd + tid]; },
-                  m, red, partials + (size_t)blockIdx.x * stride);
+                  m, red, partials + blockIdx.x, gridDim.x);  // value-major
   if (!arrive_last_of(counter, gridDim.x, &last)) return;
-  reduce_partials(partials, gridDim.x, stride, m, result);
+  reduce_partials(partials, gridDim.x, 1, m, result, gridDim.x);
   if (normd) {  // free shapes: N and dN from the direct cell pass
     for (int k = tid; k < 1 + nf; k += bd) Nsh[k] = normd[k];
     __syncthreads();

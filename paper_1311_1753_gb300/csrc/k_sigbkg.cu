@@ -30,6 +30,7 @@
 //              the chunk's moment sums in float, folded into pairs at the chunk's end; the
 //              log-sum, the block and cross-block sums, the normalisation integrals
 //              (k_norm_1d) and the gradient's combination in FP64-accurate arithmetic.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -40,10 +41,30 @@
 namespace gfi {
 namespace {
 
-constexpr int kSBThreads = 128;
-constexpr int kSBChunk64 = 24;     // FP64 plan: events per expansion of w
-constexpr int kSBSub64 = 6;        // ... and per sub-chunk of a chunk too wide for one
-constexpr float kSBLim64 = 3e-4f;  // largest |Re z - Re z0| of an expanded chunk (FP64 plan)
+// Threads per block: the FP64 plan one block of 512 per SM (128 registers a thread), the
+// mixed plan two of 384 (80 registers); few blocks leave the last block one pass of loads
+// for the cross-block sums (one value per warp).
+template <bool MIXED>
+__host__ __device__ constexpr int sb_threads() { return MIXED ? 384 : 512; }
+template <bool MIXED>
+__host__ __device__ constexpr int sb_min_blocks() { return MIXED ? 2 : 1; }
+constexpr int kSBChunk64 = 48;     // FP64 plan: events per expansion of w, at most
+constexpr int kSBSub64 = 8;        // ... and per sub-chunk of a chunk too wide for one
+// FP64 plan: largest |Re z - Re z0| of an expanded chunk.  The float coefficients t2..t5
+// set the error, 6e-8 |t2| d^2 relative; measured against a 30-digit w over |Re z0| <= 6:
+// at d = 3e-4 below 1.1e-13 of Re w for every y in 1e-4 .. 1, at d = 6e-4 below 1.7e-13
+// for y >= 0.03 (4.4e-13 at y = 1e-3, where the Gaussian part's steep derivatives set
+// |t2/t0| up to ~20 near |Re z| = 2.5)
+constexpr float kSBLim64 = 3e-4f;
+constexpr float kSBLim64W = 6e-4f;
+constexpr double kSBLim64WY = 0.03;
+// FP64 plan, |Re z0| >= 6 and y >= 1e-6: the limit kSBLim64Rel |Re z0|.  There Re w is the
+// Lorentzian tail (the Gaussian part exp(-x^2) <= 2.3e-16 is below 1e-8 of it), whose
+// Taylor coefficients on the real line fall as |Re t_k| ~ (k + 1) Re w / |x|^k: with
+// d = rho |x| the float coefficients t2..t5 carry a relative error of 6e-8 x 3 rho^2
+// (9.5e-14 measured at rho = 5e-4 against a 30-digit w, y = 1e-3 .. 1, |x| = 6 .. 40) and
+// the truncation 7 rho^6 (1e-19)
+constexpr float kSBLim64Rel = 5e-4f;
 constexpr int kSBChunk32 = 96;     // mixed plan
 constexpr int kSBSub32 = 24;
 // mixed plan: largest |Re z - Re z0| at |Re z0| < 0.6 (the Cauchy bound |t_k| <= 6 on the
@@ -130,8 +151,8 @@ __device__ __forceinline__ void tay_coefs(F2 zr, F2 y, const WeidCoef& W, F2* tr
   }
 }
 
-// FP64 plan: t_0, t_1 as pairs, t_2 .. t_5 in float (their terms are below 3 d^2 <= 3e-7
-// of w, so float rounding there adds < 2e-14 of |w|).
+// FP64 plan: t_0, t_1 as pairs, t_2 .. t_5 in float (the chunk width limits kSBLim64* keep
+// their rounding below 2e-13 of Re w).
 struct TayP {
   F2 z0, t0r, t0i, t1r, t1i;
   float qr[4], qi[4];
@@ -293,16 +314,34 @@ __device__ void sb_finish(const SigBkgDesc& D, const double* __restrict__ der, c
 // ---- the kernel -------------------------------------------------------------------------------
 // STORE: log P_i into out_logp[perm ? perm[i] : i] instead of the sums.
 // Shared scratch of one block.
+template <bool MIXED>
 struct SBShared {
+  static constexpr int NT = sb_threads<MIXED>();
+  static constexpr int NM = MIXED ? kSBMom - 1 : 1;
   SBConst K;
   // mixed plan: the per-thread pair sums of the moments (touched once per chunk) and the
   // constants used only at chunk boundaries, as pairs, out of the registers
-  float mh[kSBMom - 1][kSBThreads], ml[kSBMom - 1][kSBThreads];
+  float mh[NM][MIXED ? NT : 1], ml[NM][MIXED ? NT : 1];
   F2 mu2, yp, sv, st, lref;
   WeidCoef W;  // the series coefficients, read by every thread (and the out-of-line paths)
-  double red[(kSBThreads / 32) * kSBMom];
+  double red[(NT / 32) * kSBMom];
   double fin[kSBMom];
   int last;
+};
+
+// The sorted events cut into nch = J T chunks (T threads, J = ceil(n / (T cmax))) of
+// floor(n / nch) or that plus one events, so that every thread walks exactly J chunks and
+// the same number of events to within J; chunk c starts at q c + floor(r c / nch) for
+// n = q nch + r (r c < nch^2: no overflow below 3 x 10^9 chunks).
+struct ChunkSplit {
+  int64_t nch, q, r;
+  __device__ ChunkSplit(int64_t n, int64_t nthreads, int cmax) {
+    const int64_t per = nthreads * cmax;
+    nch = (n + per - 1) / per * nthreads;
+    q = n / nch;
+    r = n - q * nch;
+  }
+  __device__ int64_t start(int64_t c) const { return q * c + r * c / nch; }
 };
 
 // Body of one (virtual) block vb of a launch of vgrid blocks over one data set; the last
@@ -312,7 +351,7 @@ __device__ __forceinline__ void sigbkg_block(
     const SigBkgDesc& D, const WeidCoef& Wg, const int sorted, const double* __restrict__ xcol,
     const int64_t n, const double* __restrict__ der, double* __restrict__ partials,
     unsigned* __restrict__ counter, double* __restrict__ result, double* __restrict__ out_logp,
-    const int32_t* __restrict__ perm, const int vb, const int vgrid, SBShared& sh) {
+    const int32_t* __restrict__ perm, const int vb, const int vgrid, SBShared<MIXED>& sh) {
   const int tid = threadIdx.x;
   if (tid == 0) {
     sb_consts(D, der, G, sh.K);
@@ -325,7 +364,7 @@ __device__ __forceinline__ void sigbkg_block(
       sh.lref = df_from(k.lref);
     }
   }
-  if (MIXED && G)
+  if constexpr (MIXED && G)
     for (int k = 0; k < kSBMom - 1; ++k) sh.mh[k][tid] = sh.ml[k][tid] = 0.f;
   {
     const float* src = reinterpret_cast<const float*>(&Wg);
@@ -359,8 +398,9 @@ __device__ __forceinline__ void sigbkg_block(
       for (int k = 1; k < kSBMom; ++k) m[k - 1].add(df_from(o[k]));
   };
 
-  const int64_t nthreads = (int64_t)vgrid * kSBThreads;
-  const int64_t g = (int64_t)vb * kSBThreads + tid;
+  constexpr int NT = sb_threads<MIXED>();
+  const int64_t nthreads = (int64_t)vgrid * NT;
+  const int64_t g = (int64_t)vb * NT + tid;
   constexpr int kChunk = MIXED ? kSBChunk32 : kSBChunk64;
   // sorted events and at least 8 per thread: one expansion of w per chunk pays
   const bool chunked = sorted && n >= 8 * nthreads;
@@ -428,19 +468,23 @@ __device__ __forceinline__ void sigbkg_block(
         for (int k = 0; k < kSBMom - 1; ++k) m[k].norm();
     };
     if (chunked) {
-      // the sorted events in chunks of kChunk with one expansion of w per chunk; chunk c
+      // the sorted events in chunks of at most kChunk (ChunkSplit) with one expansion of w
+      // per chunk; chunk c
       // goes to the thread of index c mod T in block-cyclic order (thread t of block b
       // takes c = j T + t B + b), so that the consecutive chunks of a region that costs
       // more -- a sparse edge of the data, where a chunk too wide for one expansion is
       // taken as sub-chunks of kSBSub64 and a sub-chunk still too wide evaluates w per
       // event -- spread over all blocks instead of loading a few SMs
-      const int64_t nch = (n + kChunk - 1) / kChunk;
       const int64_t gc = (int64_t)tid * vgrid + vb;
+      const bool wide_ok = K.y >= 1e-6;
+      const float lim0 = K.y >= kSBLim64WY ? kSBLim64W : kSBLim64;
       auto expand = [&](int64_t a, int c) {  // expansion for events a .. a + c - 1, if narrow
         const double xm = __ldg(xcol + a + (c - 1) / 2);
         const float da = fabsf(__fmul_rn((float)(__ldg(xcol + a) - xm), c1.hi));
         const float db = fabsf(__fmul_rn((float)(__ldg(xcol + a + c - 1) - xm), c1.hi));
-        const bool ok = fmaxf(da, db) <= kSBLim64;
+        const float az = fabsf(__fmul_rn((float)(xm - K.mu), c1.hi));
+        const float lim = wide_ok && az >= 6.f ? fmaxf(lim0, kSBLim64Rel * az) : lim0;
+        const bool ok = fmaxf(da, db) <= lim;
         if (ok) tayp_build(T, df_mul(df_split(xm - K.mu), c1), y, W);
         return ok;
       };
@@ -452,9 +496,10 @@ __device__ __forceinline__ void sigbkg_block(
           one(a + k, xi, tay);
         }
       };
-      for (int64_t ci = gc; ci < nch; ci += nthreads) {
-        const int64_t c0 = ci * kChunk;
-        const int cnt = (int)(n - c0 < kChunk ? n - c0 : kChunk);
+      const ChunkSplit cs(n, nthreads, kChunk);
+      for (int64_t ci = gc; ci < cs.nch; ci += nthreads) {
+        const int64_t c0 = cs.start(ci);
+        const int cnt = (int)(cs.start(ci + 1) - c0);
         if (expand(c0, cnt)) {
           run(c0, cnt, true);
         } else {
@@ -565,7 +610,6 @@ __device__ __forceinline__ void sigbkg_block(
     };
     if (chunked) {
       // chunks distributed over the threads as in the FP64 plan
-      const int64_t nch = (n + kChunk - 1) / kChunk;
       const int64_t gc = (int64_t)tid * vgrid + vb;
       F2 xms = {0.f, 0.f};
       float z0f = 0.f;
@@ -615,9 +659,10 @@ __device__ __forceinline__ void sigbkg_block(
             }
         }
       };
-      for (int64_t ci = gc; ci < nch; ci += nthreads) {
-        const int64_t c0 = ci * kChunk;
-        const int cnt = (int)(n - c0 < kChunk ? n - c0 : kChunk);
+      const ChunkSplit cs(n, nthreads, kChunk);
+      for (int64_t ci = gc; ci < cs.nch; ci += nthreads) {
+        const int64_t c0 = cs.start(ci);
+        const int cnt = (int)(cs.start(ci + 1) - c0);
         if (expand(c0, cnt)) {
           run(c0, cnt, true);
         } else {
@@ -648,16 +693,17 @@ __device__ __forceinline__ void sigbkg_block(
 
   // block sums (fixed order), then the last block's cross-block sums and the gradient
   const int mm = G ? kSBMom : 1;
-  constexpr int stride = 1 + kMaxFree1D;
   F2 vals[kSBMom];  // the register (FP64 plan) or shared (mixed plan) sums, copied once
   vals[0] = acc.get();
 #pragma unroll
   for (int k = 1; k < kSBMom; ++k)
-    vals[k] = MIXED ? F2{sh.mh[k - 1][tid], sh.ml[k - 1][tid]} : m[k - 1].get();
-  block_sum_pairs([&](int k) -> F2 { return vals[k]; }, mm, sh.red,
-                  partials + (size_t)vb * stride);
+    if constexpr (MIXED) vals[k] = F2{sh.mh[k - 1][tid], sh.ml[k - 1][tid]};
+    else vals[k] = m[k - 1].get();
+  // partials value-major: value k of block b at partials[k vgrid + b]
+  block_sum_pairs<G ? kSBMom : 1>([&](int k) -> F2 { return vals[k]; }, mm, sh.red, partials + vb,
+                                  vgrid);
   if (!arrive_last_of(counter, (unsigned)vgrid, &sh.last)) return;
-  reduce_partials(partials, vgrid, stride, mm, sh.fin);
+  reduce_partials(partials, vgrid, 1, mm, sh.fin, vgrid);
   if (tid == 0) {
     sb_finish(D, der, sh.fin, G, result);
     *counter = 0u;
@@ -665,13 +711,13 @@ __device__ __forceinline__ void sigbkg_block(
 }
 
 template <bool G, bool MIXED, bool STORE>
-__global__ void __launch_bounds__(kSBThreads, MIXED ? 6 : 4) k_sigbkg(
+__global__ void __launch_bounds__(sb_threads<MIXED>(), sb_min_blocks<MIXED>()) k_sigbkg(
     const __grid_constant__ SigBkgDesc D, const __grid_constant__ WeidCoef W,
     const Program* __restrict__ prog, const double* __restrict__ xcol, const int64_t n,
     const double* __restrict__ der, double* __restrict__ partials,
     unsigned* __restrict__ counter, double* __restrict__ result, double* __restrict__ out_logp,
     const int32_t* __restrict__ perm) {
-  __shared__ SBShared sh;
+  __shared__ SBShared<MIXED> sh;
   load_df_tables();  // visible after the block body's first barrier
   sigbkg_block<G, MIXED, STORE>(D, W, prog->sorted, xcol, n, der, partials, counter, result,
                                 out_logp, perm, blockIdx.x, gridDim.x, sh);
@@ -681,10 +727,10 @@ __global__ void __launch_bounds__(kSBThreads, MIXED ? 6 : 4) k_sigbkg(
 // launch; item it of the work list is virtual block it - item0 of its fit, which processes
 // the events of the fit's standalone block of that index (the same bits alone or batched).
 template <bool MIXED>
-__global__ void __launch_bounds__(kSBThreads, 4) k_tick_sigbkg(const TickItem* __restrict__ items,
-                                                            int nfits, int total,
-                                                            const __grid_constant__ WeidCoef W) {
-  __shared__ SBShared sh;
+__global__ void __launch_bounds__(sb_threads<MIXED>(), sb_min_blocks<MIXED>())
+    k_tick_sigbkg(const TickItem* __restrict__ items, int nfits, int total,
+                  const __grid_constant__ WeidCoef W) {
+  __shared__ SBShared<MIXED> sh;
   load_df_tables();
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     int f = 0;
@@ -703,18 +749,21 @@ __global__ void __launch_bounds__(kSBThreads, 4) k_tick_sigbkg(const TickItem* _
 int sigbkg_blocks_per_sm(bool mixed) {
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &nb, mixed ? k_sigbkg<true, true, false> : k_sigbkg<true, false, false>, kSBThreads, 0);
+      &nb, mixed ? k_sigbkg<true, true, false> : k_sigbkg<true, false, false>,
+      sigbkg_threads(mixed), 0);
   cudaGetLastError();
   return nb > 0 ? nb : 1;
 }
 
-int sigbkg_threads() { return kSBThreads; }
+int sigbkg_threads(bool mixed) { return mixed ? sb_threads<true>() : sb_threads<false>(); }
 
 cudaError_t launch_tick_sigbkg(bool mixed, const TickItem* items, int nfits, int total,
-                               const WeidCoef& W, int grid, cudaStream_t st) {
+                               const WeidCoef& W, int sm_count, cudaStream_t st) {
   if (total <= 0) return cudaSuccess;
-  if (mixed) k_tick_sigbkg<true><<<grid, kSBThreads, 0, st>>>(items, nfits, total, W);
-  else k_tick_sigbkg<false><<<grid, kSBThreads, 0, st>>>(items, nfits, total, W);
+  const int grid = std::max(1, std::min(total, sm_count * (mixed ? sb_min_blocks<true>()
+                                                                : sb_min_blocks<false>())));
+  if (mixed) k_tick_sigbkg<true><<<grid, sb_threads<true>(), 0, st>>>(items, nfits, total, W);
+  else k_tick_sigbkg<false><<<grid, sb_threads<false>(), 0, st>>>(items, nfits, total, W);
   return cudaGetLastError();
 }
 
@@ -724,26 +773,27 @@ cudaError_t launch_sigbkg(const SigBkgDesc& D, const WeidCoef& W, const Program*
                           double* result, double* out_logp, const int32_t* perm, bool grad,
                           bool mixed, int nblocks, cudaStream_t st) {
   if (nblocks < 1) nblocks = 1;
+  const int NT = sigbkg_threads(mixed);
   if (out_logp) {
     if (mixed)
-      k_sigbkg<false, true, true><<<nblocks, kSBThreads, 0, st>>>(D, W, prog, x, n, derived, partials,
+      k_sigbkg<false, true, true><<<nblocks, NT, 0, st>>>(D, W, prog, x, n, derived, partials,
                                                                   counter, result, out_logp, perm);
     else
-      k_sigbkg<false, false, true><<<nblocks, kSBThreads, 0, st>>>(D, W, prog, x, n, derived, partials,
+      k_sigbkg<false, false, true><<<nblocks, NT, 0, st>>>(D, W, prog, x, n, derived, partials,
                                                                    counter, result, out_logp, perm);
   } else if (mixed) {
     if (grad)
-      k_sigbkg<true, true, false><<<nblocks, kSBThreads, 0, st>>>(D, W, prog, x, n, derived, partials,
+      k_sigbkg<true, true, false><<<nblocks, NT, 0, st>>>(D, W, prog, x, n, derived, partials,
                                                                   counter, result, nullptr, nullptr);
     else
-      k_sigbkg<false, true, false><<<nblocks, kSBThreads, 0, st>>>(D, W, prog, x, n, derived, partials,
+      k_sigbkg<false, true, false><<<nblocks, NT, 0, st>>>(D, W, prog, x, n, derived, partials,
                                                                    counter, result, nullptr, nullptr);
   } else {
     if (grad)
-      k_sigbkg<true, false, false><<<nblocks, kSBThreads, 0, st>>>(D, W, prog, x, n, derived, partials,
+      k_sigbkg<true, false, false><<<nblocks, NT, 0, st>>>(D, W, prog, x, n, derived, partials,
                                                                    counter, result, nullptr, nullptr);
     else
-      k_sigbkg<false, false, false><<<nblocks, kSBThreads, 0, st>>>(D, W, prog, x, n, derived, partials,
+      k_sigbkg<false, false, false><<<nblocks, NT, 0, st>>>(D, W, prog, x, n, derived, partials,
                                                                     counter, result, nullptr, nullptr);
   }
   return cudaGetLastError();

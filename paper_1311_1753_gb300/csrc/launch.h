@@ -54,9 +54,10 @@ cudaError_t launch_sigbkg(const SigBkgDesc& D, const WeidCoef& W, const Program*
                           bool mixed, int nblocks, cudaStream_t st);
 int sigbkg_blocks_per_sm(bool mixed);
 // batched tick of signal + background fits (TickItem.fit -> FitSB)
+// (grid: sm_count times the plan's resident blocks per SM)
 cudaError_t launch_tick_sigbkg(bool mixed, const TickItem* items, int nfits, int total,
-                               const WeidCoef& W, int grid, cudaStream_t st);
-int sigbkg_threads();
+                               const WeidCoef& W, int sm_count, cudaStream_t st);
+int sigbkg_threads(bool mixed);  // threads per block of the FP64 or the mixed plan
 cudaError_t prepare_kernels_sigbkg();
 // loads the allocation-free entry point's module (its static scratch array)
 cudaError_t noalloc_preload();

@@ -231,7 +231,7 @@ static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
   }
   if (e == cudaSuccess && n_sb) {
     e = launch_tick_sigbkg(S->opts.precision == GF_MIXED, d_items + 3 * T.cap_fits, n_sb, tot_sb,
-                           W, grid, st);
+                           W, S->sm_count, st);
     ++nl;
   }
   if (e == cudaSuccess && n_dz) {

@@ -85,6 +85,25 @@ def test_fp64_plan_parity(gf, order, n, sort):
         assert abs(ctx.nll(th[free]) - fg) <= 1e-12 * max(1.0, abs(fg))
 
 
+@pytest.mark.parametrize("width", [2e-6, 1e-5, 3e-5, 2.5e-4, 9e-4])
+def test_fp64_plan_parity_across_line_widths(gf, width):
+    """Sorted events of lines of natural width 2e-6 .. 9e-4 (y = width / (2 sqrt(2) sigma)
+    from 2.4e-3 to 1.06): the expansion's narrow (y < 0.03) and wide chunk limits and the
+    relative one in the tails, per event within 1e-12 of the oracle."""
+    t = dict(synth.VOIGT_TRUTH, width=width)
+    lo, hi = synth.VOIGT_RANGE
+    x = synth.voigt_threshold_events(200_001, **t, lo=lo, hi=hi, seed=synth.SEED_VOIGT + 5)
+    m, free = om.voigt_model(truth=t, nbins=3000)
+    ctx, root, obs = pm.voigt_model(gf, truth=t, nbins=3000)
+    ctx.set_data(root, obs, [x])
+    th = m.p[free]
+    per_event(f"sigbkg fp64 sorted width={width:g}", ctx.logpdf(th), m.logpdf([x], m.p))
+    fg, gg = ctx.nll_grad(th)
+    fo, go = m.nll([x], m.p, grad=True)
+    assert abs(fg - fo) <= 1e-9 * max(1.0, abs(fo)), (fg, fo)
+    _grad_close(gg, go[free], len(x))
+
+
 def test_mixed_plan_errors_full_size(gf):
     """10^7 events (config 2) in GF_MIXED: per-event relative error percentiles, NLL and
     gradient against the FP64 oracle, stated and bounded."""
