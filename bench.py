@@ -42,18 +42,18 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # traffic of one launch are ncu counters of the 10^7-event launch of this build (the
 # profile summary of k_sigbkg under profiles/); None where no capture of the current
 # kernel exists.
-FP32_FLOPS_PER_EVENT = {"voigt_grad": 640.2}   # FADD 359.2 + FMUL 48.4 + 2 x FFMA 116.3
-TRAFFIC_PER_LAUNCH = {"voigt_grad": 81.53e6,        # 80.24 MB read + 1.29 MB written
-                      "voigt_grad_mixed": 82.50e6}  # 80.46 MB read + 2.04 MB written
+FP32_FLOPS_PER_EVENT = {"voigt_grad": 593.1}   # FADD 334.4 + FMUL 45.1 + 2 x FFMA 106.8
+TRAFFIC_PER_LAUNCH = {"voigt_grad": 81.72e6,        # 80.14 MB read + 1.58 MB written
+                      "voigt_grad_mixed": 83.28e6}  # 80.39 MB read + 2.89 MB written
 # the headline workload's name, shared by both arms' JSON lines
 VOIGT_WORKLOAD = ("1D composite: Voigtian (mu,sigma,Gamma) + threshold (c) with fraction f, "
                   "10^7 FP64 events, 2 x 10,000-bin grid normalisation")
 # The method's work: the same pass in FP64 operations (FMA = 2, add/mul = 1, each exp,
-# log, sqrt or division = 1), counted from the source: w(z) by one Weideman series
-# (N = 40: 305) and its degree-5 expansion per chunk of 24 events (recurrence ~40 per
-# chunk, evaluation 20, argument 3) = 37 per event; Voigt value and 3 partials 31;
-# threshold value and partial 9; the mixture (2 products, 1 sum) and its gradient terms
-# (6 products, 6 sums) 15; log P and 1/P 2.
+# log, sqrt or division = 1), a fixed count (it does not follow the kernel's chunk length):
+# w(z) by one Weideman series (N = 40: 305) and a degree-5 expansion amortised over 24
+# events (recurrence ~40 per expansion, evaluation 20, argument 3) = 37 per event; Voigt
+# value and 3 partials 31; threshold value and partial 9; the mixture (2 products, 1 sum)
+# and its gradient terms (6 products, 6 sums) 15; log P and 1/P 2.
 FP64_FLOPS_PER_EVENT = {"voigt_grad": 94}
 
 
