@@ -1592,10 +1592,12 @@ static int finish_set_data(gf_ctx* ctx) {
     cudaFree(d.tddp_normd);
     d.tddp_dcache = nullptr;
     d.tddp_normd = nullptr;
+    // N and dN/dtheta: from the direct cell pass (free shapes) or published by the event
+    // pass's first block to finish (fixed shapes)
+    CK(cudaMalloc(&d.tddp_normd, sizeof(double) * 64));
     if (T.shape_free) {
       CK(cudaMalloc(&d.tddp_dcache, sizeof(float4) * 4 * std::max(T.D.nres, 1) *
                                         (size_t)std::max<int64_t>(d.n, 1)));
-      CK(cudaMalloc(&d.tddp_normd, sizeof(double) * 64));
       rc = grow(ctx, &d.partials2, &d.partials2_cap, (size_t)4096 * 64);
       if (rc) return rc;
     }
@@ -2110,7 +2112,8 @@ static int tddp_enqueue(gf_ctx* ctx, bool grad, double* out_logp, int* launches)
   CK(cudaEventRecord(d.evm, ctx->stream));
   const double* cols[4] = {d.cols[0], d.cols[1], d.cols[2], d.cols[3]};
   CK(launch_tddp_events(T, grad, d.theta, cols, d.n, d.tddp_cache, d.tddp_dcache, d.tddp_gram,
-                        T.shape_free ? d.tddp_normd : nullptr, d.partials, d.counters,
+                        T.shape_free ? d.tddp_normd : nullptr, d.tddp_normd, d.partials,
+                        d.counters,
                         d.result, out_logp, d.nblocks, weideman(), ctx->stream));
   (*launches)++;
   CK(cudaEventRecord(d.ev1, ctx->stream));

@@ -1650,7 +1650,7 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
     const double* __restrict__ theta, const double* __restrict__ ct,
     const double* __restrict__ csig, int64_t n, const float4* __restrict__ cache,
     const float4* __restrict__ dcache, const double2* __restrict__ gram,
-    const double* __restrict__ normd, const double* __restrict__ c12,
+    const double* __restrict__ normd, double* __restrict__ nscratch, const double* __restrict__ c12,
     const double* __restrict__ c13, double* __restrict__ partials,
     unsigned* __restrict__ counter, double* __restrict__ result, double* __restrict__ out_logp) {
   const DalitzPlan& D = T.D;
@@ -1684,11 +1684,13 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   tddp_rates(tau, mx, my, l, dl);
   const double gam = 1.0 / tau;
   Neu acc;
-  // a contiguous share of ceil(n / gridDim) events per block: with every block resident
-  // (kTddpBlocksPerSm per SM) each SM gets the same number of events
-  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t i_end = min(n, (int64_t)blockIdx.x * per + per);
-  for (int64_t i = (int64_t)blockIdx.x * per + tid; i < i_end; i += bd) {
+  // a contiguous share of floor(n / gridDim) or one more events per block (block b from
+  // q b + floor(r b / gridDim), n = q gridDim + r): with every block resident
+  // (kTddpBlocksPerSm per SM) each SM gets the same number of events to within 3
+  const int64_t qb = n / gridDim.x, rb = n - qb * gridDim.x;
+  const int64_t i_beg = qb * blockIdx.x + rb * blockIdx.x / gridDim.x;
+  const int64_t i_end = qb * (blockIdx.x + 1) + rb * (blockIdx.x + 1) / gridDim.x;
+  for (int64_t i = i_beg + tid; i < i_end; i += bd) {
     // A = 1 + sum_r c_r a_r, B = 1 + sum_r c_r b_r in pairs
     F2 Ar = {1.f, 0.f}, Ai = {0.f, 0.f}, Br = Ar, Bi = Ai;
     for (int r = 0; r < D.nres; ++r) {
@@ -1808,17 +1810,26 @@ __global__ void __launch_bounds__(kThreads, kTddpBlocksPerSm) k_tddp_events(
   const int m = 1 + (G ? nf : 0);
   block_sum_pairs([&](int k) -> F2 { return k == 0 ? df_split(acc.get()) : gsh[(k - 1) * bd + tid]; },
                   m, red, partials + blockIdx.x, gridDim.x);  // value-major
+  if (!normd) {
+    // fixed shapes: the first block done with its events forms N and dN from the Gram sums
+    // (a serial FP64 stretch of ~13 us) and publishes them in nscratch before it arrives,
+    // off the last block's path: the last block to arrive finds them there
+    if (tid == 0) last = atomicAdd(counter + 2, 1u) == 0u;
+    __syncthreads();
+    if (last) {
+      tddp_norm_block(T, th, gram, Nsh, vec, part, kd, G);
+      for (int k = tid; k < 1 + nf; k += bd) nscratch[k] = Nsh[k];
+    }
+  }
   if (!arrive_last_of(counter, gridDim.x, &last)) return;
   reduce_partials(partials, gridDim.x, 1, m, result, gridDim.x);
-  if (normd) {  // free shapes: N and dN from the direct cell pass
-    for (int k = tid; k < 1 + nf; k += bd) Nsh[k] = normd[k];
-    __syncthreads();
-  } else {
-    tddp_norm_block(T, th, gram, Nsh, vec, part, kd, G);
-  }
+  const double* nsrc = normd ? normd : nscratch;  // direct cell pass (free shapes) or above
+  for (int k = tid; k < 1 + nf; k += bd) Nsh[k] = __ldcg(nsrc + k);
+  __syncthreads();
   if (tid == 0) {
     result[0] += (double)n * log(Nsh[0]);
-    *counter = 0u;
+    counter[0] = 0u;
+    counter[2] = 0u;
   }
   if (G)
     for (int k = tid; k < nf; k += bd) result[1 + k] += (double)n * Nsh[1 + k] / Nsh[0];
@@ -1845,21 +1856,21 @@ cudaError_t launch_tddp_gram(const TddpPlan& T, const double* theta, const uint8
 cudaError_t launch_tddp_events(const TddpPlan& T, bool grad, const double* theta,
                                const double* const* cols, int64_t n, const float4* cache,
                                const float4* dcache, const double2* gram, const double* normd,
-                               double* partials, unsigned* counter, double* result,
-                               double* out_logp, int nblocks, const WeidCoef& W,
+                               double* nscratch, double* partials, unsigned* counter,
+                               double* result, double* out_logp, int nblocks, const WeidCoef& W,
                                cudaStream_t st) {
   const size_t smem = grad ? sizeof(F2) * T.nfree * kThreads : 0;
   if (out_logp) {
     k_tddp_events<false, true><<<nblocks, kThreads, 0, st>>>(
-        T, W, theta, cols[2], cols[3], n, cache, dcache, gram, normd, cols[0], cols[1], partials,
+        T, W, theta, cols[2], cols[3], n, cache, dcache, gram, normd, nscratch, cols[0], cols[1], partials,
         counter, result, out_logp);
   } else if (grad) {
     k_tddp_events<true, false><<<nblocks, kThreads, smem, st>>>(
-        T, W, theta, cols[2], cols[3], n, cache, dcache, gram, normd, cols[0], cols[1], partials,
+        T, W, theta, cols[2], cols[3], n, cache, dcache, gram, normd, nscratch, cols[0], cols[1], partials,
         counter, result, nullptr);
   } else {
     k_tddp_events<false, false><<<nblocks, kThreads, 0, st>>>(
-        T, W, theta, cols[2], cols[3], n, cache, dcache, gram, normd, cols[0], cols[1], partials,
+        T, W, theta, cols[2], cols[3], n, cache, dcache, gram, normd, nscratch, cols[0], cols[1], partials,
         counter, result, nullptr);
   }
   return cudaGetLastError();

@@ -129,8 +129,8 @@ constexpr int kTddpBlocksPerSm = 3;
 cudaError_t launch_tddp_events(const TddpPlan& T, bool grad, const double* theta,
                                const double* const* cols, int64_t n, const float4* cache,
                                const float4* dcache, const double2* gram, const double* normd,
-                               double* partials, unsigned* counter, double* result,
-                               double* out_logp, int nblocks, const WeidCoef& W,
+                               double* nscratch, double* partials, unsigned* counter,
+                               double* result, double* out_logp, int nblocks, const WeidCoef& W,
                                cudaStream_t st);
 // free resonance shapes: amplitudes and shape derivatives per event (dcache: 4 nres n), and
 // N with dN/dtheta by a direct pass over the cells (out[0], out[1 + k])
