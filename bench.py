@@ -411,8 +411,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="voigt",
-                    choices=["voigt", "voigt-mixed", "exp", "dalitz", "dalitz-mixed", "exp-sweep",
-                             "binned", "conv", "tddp"])
+                    choices=["voigt", "voigt-mixed", "exp", "dalitz", "dalitz-mixed", "dalitz-free",
+                             "exp-sweep", "binned", "conv", "tddp"])
     ap.add_argument("--sweep-sizes", default="1000000,10000000,100000000,1000000000",
                     help="event counts of --workload exp-sweep")
     ap.add_argument("--no-extra", action="store_true")
@@ -516,13 +516,18 @@ def main():
         wl = "truncated exponential, 10^5 FP64 events, analytic normalisation"
         metric = "NLL+gradient evaluations: events x evals/s (exponential, FP64-accurate)"
     else:
+        # config 3 (dalitz: fixed shapes, cached amplitudes) or config 4 (free masses and
+        # widths: amplitudes recomputed per event) in mixed precision or FP64
         mixed = args.workload == "dalitz-mixed"
-        n = 5_000_000 if mixed else 1_000_000
+        big = args.workload in ("dalitz-mixed", "dalitz-free")
+        n = 5_000_000 if big else 1_000_000
         ctx, root, obs, cols, th0 = dalitz_workload(
-            gf, n, synth.SEED_DALITZ_BIG if mixed else synth.SEED_DALITZ_EVENTS,
-            gf.GF_MIXED if mixed else gf.GF_FP64, mixed)
+            gf, n, synth.SEED_DALITZ_BIG if big else synth.SEED_DALITZ_EVENTS,
+            gf.GF_MIXED if mixed else gf.GF_FP64, big)
         wl = ("Dalitz 8 BW resonances, 5x10^6 events, 30 free, FP32 amplitudes + FP64 sums"
-              if mixed else "Dalitz 8 BW resonances, 10^6 FP64 events, 16 free coefficients")
+              if mixed else
+              "Dalitz 8 BW resonances, 5x10^6 FP64 events, 30 free (masses, widths recomputed)"
+              if big else "Dalitz 8 BW resonances, 10^6 FP64 events, 16 free coefficients")
         metric = f"NLL+gradient evaluations: events x evals/s ({args.workload})"
 
     rng = np.random.default_rng(5)
@@ -589,7 +594,8 @@ def main():
                           "l2": "flushed between steps (256 MB write)",
                           "parallelism": f"replicas x{world} (independent data sets)"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-               "gpu_launches": res["launches"], "wall_s_timed_loop": res["wall_s"]}
+               "gpu_launches": res["launches"], "wall_s_timed_loop": res["wall_s"],
+               "event_kernel_ms": 1e3 * kern_s}
         if extra:
             out["extra"] = extra
         if fit_metrics:
