@@ -255,6 +255,22 @@ int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols);
 /* (Binned data sets are replaced with gf_set_data; gf_update_data rejects them.  For the
  * time-dependent Dalitz model the kinematic region and sigma_t > 0 are checked on the
  * host, as gf_set_data does, and GF_EINVAL is returned with no event replaced.) */
+/* Start loading the NEXT events of a 1D unbinned data set owned by the context (same n and
+ * observables; cols[k] n doubles in host memory, pinned for an asynchronous copy) while
+ * the current events are still being evaluated: the columns are copied on an internal
+ * copy stream into a second device buffer set and checked against the observable ranges
+ * there.  Returns at once.  A later gf_update_data with the same column pointers (cols[k]
+ * identical) makes them the context's events by swapping the two buffer sets: no copy at
+ * that call.  The new events are in the caller's order, as after gf_update_data (a data
+ * set evaluated repeatedly is sorted again from its second evaluation).  The host columns
+ * must stay unchanged until that gf_update_data returns.  A range error is reported by
+ * that gf_update_data (GF_EINVAL; the prefetched set is not loaded, the loaded one stays).
+ * A gf_update_data with other pointers, a second gf_prefetch_data or gf_set_data waits for
+ * the prefetch and drops it.  The evaluation graphs of both buffer sets are kept, so
+ * alternating sets does not re-capture them.  Device memory: one more copy of the columns.
+ * Dalitz, time-dependent Dalitz and binned data sets: GF_EINVAL; no data set owned:
+ * GF_ESTATE. */
+int gf_prefetch_data(gf_ctx* ctx, int64_t n, const double* const* cols);
 
 /* ---- evaluation (Sec. 2: evaluate and metric, summed over events) ------------------ */
 /* NLL(theta) = -sum_i log P(x_i; theta) with P normalised (or the context's binned

@@ -110,6 +110,13 @@ static int leaf(gf_ctx* ctx, int type, int obs, std::vector<int> pars, int* node
 // ---- device memory ------------------------------------------------------------------------------
 static void free_dev(gf_ctx* ctx) {
   DevState& d = ctx->dev;
+  if (d.copy_stream) {  // a prefetch may still be copying into the staging buffers
+    cudaStreamSynchronize(d.copy_stream);
+    cudaStreamDestroy(d.copy_stream);
+  }
+  if (d.ev_staged) cudaEventDestroy(d.ev_staged);
+  if (d.ev_free) cudaEventDestroy(d.ev_free);
+  for (double* p : d.stage) cudaFree(p);
   if (d.owns_cols)
     for (double* p : d.cols) cudaFree(p);
   d.cols.clear();
@@ -2140,7 +2147,7 @@ int evaluate_async(gf_ctx* ctx, const double* theta, bool grad, bool fp64) {
   const bool mixed = ctx->precision == GF_MIXED && !fp64;
   const bool steady = !ctx->is_dalitz || dalitz_is_steady(ctx, mixed, &direct);
   if (steady && ctx->graphs && !d.graph_off) {
-    const int key = (grad ? 1 : 0) | (fp64 ? 2 : 0) | (direct ? 4 : 0);
+    const int key = (grad ? 1 : 0) | (fp64 ? 2 : 0) | (direct ? 4 : 0) | (d.cur_set << 3);
     int launches = 0;
     if (!d.graph[key]) {
       // capture once; if the capture or instantiation fails for any reason the context
@@ -2472,12 +2479,109 @@ int gf_last_eval_times(gf_ctx* ctx, double* total_ms, double* stream_ms) {
   return GF_OK;
 }
 
+// Wait for a prefetch still in flight and forget it (its buffers stay allocated).
+static int drop_staged(gf_ctx* ctx) {
+  DevState& d = ctx->dev;
+  if (d.stage_src.empty()) return GF_OK;
+  d.stage_src.clear();
+  CK(cudaEventSynchronize(d.ev_staged));
+  return GF_OK;
+}
+
+// The prefetched set becomes the context's data: its copy and range check ran on the copy
+// stream during earlier work, so this is a swap of the two buffer sets.  The new events
+// are in the caller's order (the strided event loop; a set evaluated repeatedly is sorted
+// again from its second evaluation, as after gf_update_data).
+static int swap_staged(gf_ctx* ctx) {
+  DevState& d = ctx->dev;
+  d.stage_src.clear();
+  CK(cudaEventSynchronize(d.ev_staged));
+  volatile int* sflag = reinterpret_cast<volatile int*>(d.h_result + 62);
+  if (*sflag) {
+    *sflag = 0;
+    return set_error(ctx, GF_EINVAL, "gf_update_data: an event of the prefetched set lies outside "
+                                     "its range (the set was not loaded)");
+  }
+  std::swap(d.cols, d.stage);
+  d.cur_set ^= 1;
+  const int rc = mark_unsorted(ctx);  // the kernels read the flag from the device program
+  if (rc) return rc;
+  if (d.tick_desc) {  // the serving descriptor holds the old column pointers
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(d.tick_desc);
+    d.tick_desc = nullptr;
+    d.tick_kind = 0;
+  }
+  return GF_OK;
+}
+
+int gf_prefetch_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
+  if (!ctx || !cols) return GF_EINVAL;
+  DevState& d = ctx->dev;
+  if (!d.owns_cols || !d.theta) return set_error(ctx, GF_ESTATE, "no data set owned by the context");
+  if (n != d.n) return set_error(ctx, GF_EINVAL, "gf_prefetch_data: n must equal the loaded size");
+  if (d.binned || ctx->is_dalitz || ctx->is_tddp)
+    return set_error(ctx, GF_EINVAL, "gf_prefetch_data: 1D unbinned data sets only");
+  for (int k = 0; k < d.nobs; ++k)
+    if (!cols[k]) return GF_EINVAL;
+  int rc = ensure_compiled(ctx);
+  if (rc) return rc;
+  CK(cudaSetDevice(ctx->device));
+  rc = drop_staged(ctx);  // an earlier prefetch that was never loaded
+  if (rc) return rc;
+  if (!d.copy_stream) {
+    CK(cudaStreamCreateWithFlags(&d.copy_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&d.ev_staged, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&d.ev_free, cudaEventDisableTiming));
+  }
+  const size_t bytes = round_up((size_t)std::max<int64_t>(n + 2, 2) * 8, 256);
+  while ((int)d.stage.size() < d.nobs) {
+    double* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(ctx, GF_ENOMEM, "gf_prefetch_data: device allocation of the staging buffers failed");
+    }
+    d.stage.push_back(p);
+    CK(cudaMemsetAsync(p, 0, bytes, d.copy_stream));
+  }
+  // the staging buffers may still be read by work queued on the compute stream
+  CK(cudaEventRecord(d.ev_free, ctx->stream));
+  CK(cudaStreamWaitEvent(d.copy_stream, d.ev_free, 0));
+  *reinterpret_cast<volatile int*>(d.h_result + 62) = 0;
+  for (int k = 0; k < d.nobs; ++k)
+    if (n > 0)
+      CK(cudaMemcpyAsync(d.stage[k], cols[k], sizeof(double) * n, cudaMemcpyHostToDevice,
+                         d.copy_stream));
+  Cols c{};
+  double lo[kMaxObs], hi[kMaxObs];
+  for (int k = 0; k < d.nobs; ++k) {
+    c.c[k] = d.stage[k];
+    lo[k] = ctx->obs[d.obs_ids[k]].lo;
+    hi[k] = ctx->obs[d.obs_ids[k]].hi;
+  }
+  CK(launch_check_range(c, d.nobs, n, lo, hi, reinterpret_cast<int*>(d.result + 62),
+                        d.copy_stream));
+  CK(cudaEventRecord(d.ev_staged, d.copy_stream));
+  d.stage_src.assign(cols, cols + d.nobs);
+  return GF_OK;
+}
+
 int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
   if (!ctx || !cols) return GF_EINVAL;
   DevState& d = ctx->dev;
   if (!d.owns_cols || !d.theta) return set_error(ctx, GF_ESTATE, "no data set owned by the context");
   if (n != d.n) return set_error(ctx, GF_EINVAL, "gf_update_data: n must equal the loaded size");
   if (d.binned) return set_error(ctx, GF_EINVAL, "gf_update_data: binned data go through gf_set_data");
+  if (!d.stage_src.empty()) {
+    bool same = true;
+    for (int k = 0; k < d.nobs; ++k) same = same && d.stage_src[k] == cols[k];
+    if (same) {
+      CK(cudaSetDevice(ctx->device));
+      return swap_staged(ctx);
+    }
+    const int rd = drop_staged(ctx);  // another set: the prefetched one is not used
+    if (rd) return rd;
+  }
   d.tddp_ready = false;  // per-event amplitudes of the new events
   int rc = ensure_compiled(ctx);
   if (rc) return rc;

@@ -115,6 +115,7 @@ def _load():
         "gf_set_event_sort": ([vp, C.c_int], C.c_int),
         "gf_set_mixture_path": ([vp, C.c_int], C.c_int),
         "gf_update_data": ([vp, C.c_int64, C.POINTER(_D)], C.c_int),
+        "gf_prefetch_data": ([vp, C.c_int64, C.POINTER(_D)], C.c_int),
         "gf_nll_noalloc": ([vp, C.c_int, C.c_int, _I, C.c_int64, C.POINTER(vp), _D, vp], C.c_int),
         "gf_tddp_sigt_density": ([vp, C.c_int, C.c_int, C.c_int, C.c_int], C.c_int),
     }
@@ -404,6 +405,12 @@ class Context:
     def update_data_ptrs(self, n, host_ptrs):
         ptrs = (_D * len(host_ptrs))(*[C.cast(C.c_void_p(p), _D) for p in host_ptrs])
         self._ck(lib.gf_update_data(self.h, n, ptrs), "gf_update_data")
+
+    def prefetch_data_ptrs(self, n, host_ptrs):
+        """gf_prefetch_data with raw host pointers (pinned buffers the caller keeps alive
+        and unchanged until the gf_update_data that loads them)."""
+        ptrs = (_D * len(host_ptrs))(*[C.cast(C.c_void_p(p), _D) for p in host_ptrs])
+        self._ck(lib.gf_prefetch_data(self.h, n, ptrs), "gf_prefetch_data")
 
     def nll_noalloc(self, root, obs, n, dev_ptrs, theta, out_dev_ptr):
         """gf_nll_noalloc: NLL over caller-owned device columns into a caller-owned device
