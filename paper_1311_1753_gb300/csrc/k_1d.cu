@@ -1558,6 +1558,11 @@ __global__ void __launch_bounds__(kThreads) k_tick_norm_1d(const TickItem* __res
 }
 
 // event passes (NLL + gradient) of every batched fit (kThreads1D threads, as standalone)
+// One instantiation per event-kernel mode, as the standalone launches (binned: MODE 2;
+// unbinned: the AddPdf-of-leaves path MX = 1 or the stack machine MX = 0), so that a fit's
+// blocks run the same code alone and batched and no instantiation carries every mode's
+// registers.
+template <int MODE, int MX>
 __global__ void __launch_bounds__(kThreads1D) k_tick_events_1d(const TickItem* __restrict__ items,
                                                                int nfits, int total,
                                                                const __grid_constant__ WeidCoef W) {
@@ -1572,25 +1577,28 @@ __global__ void __launch_bounds__(kThreads1D) k_tick_events_1d(const TickItem* _
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const TickItem& ti = tick_item(items, nfits, it, cur, Ps);
     const Fit1D* F = static_cast<const Fit1D*>(ti.fit);
-    if (Ps.binned)
-      events_1d_block<true, 2>(Ps, W, F->cols, F->n, ti.theta, F->derived, F->partials,
-                               F->counter_ev, ti.result, nullptr, nullptr, F->analytic_only,
-                               it - ti.item0, ti.nitems, dyn, rec, rf, red, &last, nullptr);
-    else
-      events_1d_block<true, 0>(Ps, W, F->cols, F->n, ti.theta, F->derived, F->partials,
-                               F->counter_ev, ti.result, nullptr, nullptr, F->analytic_only,
-                               it - ti.item0, ti.nitems, dyn, rec, rf, red, &last, nullptr);
+    events_1d_block<true, MODE, MX>(Ps, W, F->cols, F->n, ti.theta, F->derived, F->partials,
+                                    F->counter_ev, ti.result, nullptr, nullptr, F->analytic_only,
+                                    it - ti.item0, ti.nitems, dyn, rec, rf, red, &last, nullptr);
     __syncthreads();
   }
 }
 
-cudaError_t launch_tick_1d(bool norm, const TickItem* items, int nfits, int total,
+cudaError_t launch_tick_1d(int kind, const TickItem* items, int nfits, int total,
                            const WeidCoef& W, size_t smem, int grid, cudaStream_t st) {
   if (total <= 0) return cudaSuccess;
-  if (norm) {
-    k_tick_norm_1d<<<grid, kThreads, 0, st>>>(items, nfits, total, W);
-  } else {
-    k_tick_events_1d<<<grid, kThreads1D, smem, st>>>(items, nfits, total, W);
+  switch (kind) {
+    case kTick1DNorm: k_tick_norm_1d<<<grid, kThreads, 0, st>>>(items, nfits, total, W); break;
+    case kTick1DStack:
+      k_tick_events_1d<0, 0><<<grid, kThreads1D, smem, st>>>(items, nfits, total, W);
+      break;
+    case kTick1DMixture:
+      k_tick_events_1d<0, 1><<<grid, kThreads1D, smem, st>>>(items, nfits, total, W);
+      break;
+    case kTick1DBinned:
+      k_tick_events_1d<2, -1><<<grid, kThreads1D, smem, st>>>(items, nfits, total, W);
+      break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
@@ -1692,7 +1700,9 @@ cudaError_t prepare_kernels_1d() {
   attr((const void*)k_events_1d<true, 0, 0>);
   attr((const void*)k_events_1d<true, 0, 1>);
   attr((const void*)k_events_1d<true, 2>);
-  attr((const void*)k_tick_events_1d);
+  attr((const void*)k_tick_events_1d<0, 0>);
+  attr((const void*)k_tick_events_1d<0, 1>);
+  attr((const void*)k_tick_events_1d<2, -1>);
   return e;
 }
 

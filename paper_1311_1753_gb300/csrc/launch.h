@@ -62,7 +62,10 @@ cudaError_t prepare_kernels_sigbkg();
 // loads the allocation-free entry point's module (its static scratch array)
 cudaError_t noalloc_preload();
 // batched fit-server tick (persistent launches over a work list of TickItems)
-cudaError_t launch_tick_1d(bool norm, const TickItem* items, int nfits, int total,
+// batched 1D ticks: the normalisation grids, or the event passes of one mode (the
+// standalone kernel's: stack machine, AddPdf of leaves, binned)
+constexpr int kTick1DNorm = 0, kTick1DStack = 1, kTick1DMixture = 2, kTick1DBinned = 3;
+cudaError_t launch_tick_1d(int kind, const TickItem* items, int nfits, int total,
                            const WeidCoef& W, size_t smem, int grid, cudaStream_t st);
 // flag := 1 if any event lies outside [lo[k], hi[k]] of its column
 cudaError_t launch_check_range(const Cols& cols, int nobs, int64_t n, const double* lo,

@@ -58,14 +58,18 @@ struct Req {
 // every batched fit's theta_all, and their results.
 struct TickBufs {
   int cap_fits = 0, cap_par = 0;
-  TickItem* h_items = nullptr;  // [4][cap_fits]: 1D norm, 1D events, Dalitz events,
-                                //   signal + background events
+  TickItem* h_items = nullptr;  // [kLists][cap_fits]: 1D norm, 1D events (stack machine),
+                                //   Dalitz events, signal + background events (the server's
+                                //   precision), 1D events (AddPdf of leaves), 1D binned
+                                //   events, signal + background events in FP64 (the
+                                //   refinement steps of mixed fits)
   double* h_theta = nullptr;    // [cap_fits][cap_par]
   double* h_res = nullptr;      // [cap_fits][64]
   void* d_block = nullptr;      // device mirror of items + theta
   double* d_res = nullptr;
   cudaStream_t st = nullptr;
-  size_t bytes_items() const { return sizeof(TickItem) * 4 * cap_fits; }
+  static constexpr int kLists = 7;
+  size_t bytes_items() const { return sizeof(TickItem) * kLists * cap_fits; }
   size_t bytes_theta() const { return sizeof(double) * (size_t)cap_fits * cap_par; }
 };
 
@@ -176,15 +180,19 @@ static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
   }
   if (!T.st) cudaStreamCreateWithFlags(&T.st, cudaStreamNonBlocking);
   TickItem* it_norm = T.h_items;
-  TickItem* it_ev1 = T.h_items + T.cap_fits;
   TickItem* it_dz = T.h_items + 2 * T.cap_fits;
   TickItem* it_sb = T.h_items + 3 * T.cap_fits;
+  TickItem* it_sb64 = T.h_items + 6 * T.cap_fits;
+  int n_sb64 = 0, tot_sb64 = 0;
+  // 1D event passes by mode (list 1: stack machine, 4: AddPdf of leaves, 5: binned)
+  const int list1d[3] = {1, 4, 5};
+  const int kind1d[3] = {kTick1DStack, kTick1DMixture, kTick1DBinned};
+  int n1[3] = {0, 0, 0}, tot1[3] = {0, 0, 0};
+  size_t smem1[3] = {0, 0, 0};  // the largest per-block scratch of each list's programs
   TickItem* d_items = static_cast<TickItem*>(T.d_block);
   double* d_theta = reinterpret_cast<double*>(static_cast<char*>(T.d_block) + T.bytes_items());
-  int n_norm = 0, n_ev1 = 0, n_dz = 0, n_sb = 0, tot_norm = 0, tot_ev1 = 0, tot_dz = 0,
-      tot_sb = 0;
+  int n_norm = 0, n_dz = 0, n_sb = 0, tot_norm = 0, tot_dz = 0, tot_sb = 0;
   int nfd = 0;
-  size_t smem1 = 0;  // the largest per-block scratch of the batched 1D programs
   for (int j = 0; j < nfit; ++j) {
     gf_ctx* c = fits[j]->ctx;
     fill_theta_all(c, fits[j]->theta.data(), T.h_theta + (size_t)j * T.cap_par);
@@ -198,14 +206,22 @@ static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
       if (c->dev.tick_kind == 3) {
         const void* fsb = static_cast<const char*>(c->dev.tick_desc) +
                           ((sizeof(Fit1D) + 255) / 256) * 256;
-        // the grid of the plan the tick runs (the fit's standalone launches use the same)
-        const int nb = S->opts.precision == GF_MIXED ? c->dev.nblocks_mixed : c->dev.nblocks;
-        it_sb[n_sb++] = TickItem{fsb, th, res, tot_sb, nb};
-        tot_sb += nb;
+        // the grid of the plan the tick runs (the fit's standalone launches use the same);
+        // a mixed fit's FP64 refinement steps run the FP64 plan in a list of their own
+        const bool mixed = S->opts.precision == GF_MIXED && !fits[j]->want64;
+        if (mixed) {
+          it_sb[n_sb++] = TickItem{fsb, th, res, tot_sb, c->dev.nblocks_mixed};
+          tot_sb += c->dev.nblocks_mixed;
+        } else {
+          it_sb64[n_sb64++] = TickItem{fsb, th, res, tot_sb64, c->dev.nblocks};
+          tot_sb64 += c->dev.nblocks;
+        }
       } else {
-        it_ev1[n_ev1++] = TickItem{c->dev.tick_desc, th, res, tot_ev1, c->dev.nblocks};
-        tot_ev1 += c->dev.nblocks;
-        smem1 = std::max(smem1, events_1d_smem(c->prog, true, kThreads1D));
+        const int m = c->prog.binned ? 2 : c->prog.mix ? 1 : 0;
+        TickItem* it = T.h_items + (size_t)list1d[m] * T.cap_fits;
+        it[n1[m]++] = TickItem{c->dev.tick_desc, th, res, tot1[m], c->dev.nblocks};
+        tot1[m] += c->dev.nblocks;
+        smem1[m] = std::max(smem1[m], events_1d_smem(c->prog, true, kThreads1D));
       }
     } else {
       it_dz[n_dz++] = TickItem{c->dev.tick_desc, th, res, tot_dz, c->dev.nblocks};
@@ -222,16 +238,22 @@ static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
   const WeidCoef& W = weideman();
   const int grid = S->sm_count * 4;
   if (e == cudaSuccess && n_norm) {
-    e = launch_tick_1d(true, d_items, n_norm, tot_norm, W, 0, grid, st);
+    e = launch_tick_1d(kTick1DNorm, d_items, n_norm, tot_norm, W, 0, grid, st);
     ++nl;
   }
-  if (e == cudaSuccess && n_ev1) {
-    e = launch_tick_1d(false, d_items + T.cap_fits, n_ev1, tot_ev1, W, smem1, grid, st);
-    ++nl;
-  }
+  for (int m = 0; m < 3; ++m)
+    if (e == cudaSuccess && n1[m]) {
+      e = launch_tick_1d(kind1d[m], d_items + (size_t)list1d[m] * T.cap_fits, n1[m], tot1[m], W,
+                         smem1[m], grid, st);
+      ++nl;
+    }
   if (e == cudaSuccess && n_sb) {
-    e = launch_tick_sigbkg(S->opts.precision == GF_MIXED, d_items + 3 * T.cap_fits, n_sb, tot_sb,
-                           W, S->sm_count, st);
+    e = launch_tick_sigbkg(true, d_items + 3 * T.cap_fits, n_sb, tot_sb, W, S->sm_count, st);
+    ++nl;
+  }
+  if (e == cudaSuccess && n_sb64) {
+    e = launch_tick_sigbkg(false, d_items + 6 * T.cap_fits, n_sb64, tot_sb64, W, S->sm_count,
+                           st);
     ++nl;
   }
   if (e == cudaSuccess && n_dz) {
@@ -292,6 +314,11 @@ static void scheduler(gf_server* S) {
       // contiguous share of sorted events like the standalone kernel
       R->ctx->event_sort = sigbkg_form(R->ctx, R->root);
       int rc = gf_set_data(R->ctx, R->root, R->ds);
+      // 1D fits: compiled and their tick descriptor prepared now, so that the first
+      // evaluation joins the batched launches too
+      if (rc == GF_OK && !R->ctx->is_dalitz && !R->ctx->is_tddp &&
+          ensure_compiled(R->ctx) == GF_OK)
+        tick_prepare(R->ctx);
       lk.lock();
       if (rc != GF_OK) {
         R->result.status = rc;
@@ -317,11 +344,14 @@ static void scheduler(gf_server* S) {
     for (auto& R : batch) R->want = false;
     lk.unlock();
     int64_t nl = 0;
-    // fits whose evaluation can join the batched launches: prepared, not an FP64
-    // refinement step, and their first evaluation done (it builds the caches)
+    // fits whose evaluation can join the batched launches: prepared (1D fits at
+    // admission; Dalitz fits after their first evaluation, which builds the caches), and
+    // not an FP64 refinement step unless the signal + background tick runs it
     std::vector<std::shared_ptr<Req>> batched, single;
     for (auto& R : batch) {
-      if (!R->want64 && R->evals > 0 && R->ctx->dev.tick_desc) batched.push_back(R);
+      const bool ready = R->ctx->dev.tick_desc && (R->evals > 0 || !R->ctx->is_dalitz);
+      const bool plan = !R->want64 || R->ctx->dev.tick_kind == 3;
+      if (ready && plan) batched.push_back(R);
       else single.push_back(R);
     }
     for (auto& R : single) {

@@ -75,9 +75,9 @@ def test_server_alone_equals_mix(gf, precision):
     srv.drain()
     st = srv.stats()
     assert 1 <= st["peak_slots"] <= 4 and st["ticks"] > 0
-    # after its first evaluation every fit joins the batched tick: at most four
-    # persistent launches (1D normalisation, 1D events, signal + background events,
-    # Dalitz events) per tick
+    # every 1D evaluation and a Dalitz fit's after its first join the batched tick: at
+    # most four persistent launches here (1D normalisation, signal + background events in
+    # the server's precision and in FP64 for refinement steps, Dalitz events) per tick
     assert st["launches"] <= 4 * st["ticks"] + 2 * len(reqs) * 4, st
     for a, t in zip(alone, tickets):
         r = srv.poll(t)
@@ -102,4 +102,67 @@ def test_server_memory_budget_limits_slots(gf):
     srv.drain()
     assert srv.stats()["peak_slots"] == 1
     assert all(srv.poll(t)["status"] == gf.GF_OK for t in tickets)
+    srv.close()
+
+
+def _tree_model(gf, kind):
+    """1D trees outside the signal + background form: an AddPdf of three leaves (the
+    AddPdf-of-leaves event path) and a nested sum (the stack machine)."""
+    ctx = gf.Context()
+    x = ctx.observable("x", -1.0, 2.0)
+    names = ["mu", "s", "ax", "a0", "a1", "f1", "f2"]
+    vals = [0.4, 0.3, -0.7, 1.0, 0.3, 0.5, 0.2]
+    P = [ctx.parameter(nm, v, 0.01, *((0.0, 1.0) if nm[0] == "f" else (0.0, 0.0)))
+         for nm, v in zip(names, vals)]
+    g, e, q = ctx.gauss(x, P[0], P[1]), ctx.exp(x, P[2]), ctx.poly(x, [P[3], P[4]])
+    ctx.set_fixed(P[3], True)
+    if kind == "mix3":
+        root = ctx.add([g, e, q], [P[5], P[6]])
+    else:
+        root = ctx.add([g, ctx.add([e, q], [P[6]])], [P[5]])
+    return ctx, root, [x]
+
+
+def test_server_1d_tree_kinds_alone_equals_mix(gf):
+    """Fits of the two general 1D event paths (their own tick kernels) beside each other
+    and beside signal + background fits: FP64 results are the same bits alone and in the
+    mix, and every evaluation, the first included, runs in the batched tick."""
+    rng = np.random.default_rng(31)
+    jobs = []
+    for j in range(6):
+        n = 40_000 + 10_000 * j
+        x = np.where(rng.random(n) < 0.5, rng.normal(0.4, 0.3, n), rng.uniform(-1.0, 2.0, n))
+        x = np.clip(x, -0.999, 1.999)
+        jobs.append((["mix3", "nested"][j % 2], x))
+    lo, hi = synth.VOIGT_RANGE
+    jobs.append(("voigt", synth.voigt_threshold_events(30_000, **synth.VOIGT_TRUTH, lo=lo, hi=hi,
+                                                       seed=77)))
+
+    def build(kind):
+        if kind == "voigt":
+            ctx, root, obs = pm.voigt_model(gf, nbins=2000)
+            for k, pid in enumerate(ctx.free_params()):
+                ctx.set_value(pid, [0.14551, 3.2e-4, 7e-5, 21.0, 0.29][k])
+            return ctx, root, obs
+        return _tree_model(gf, kind)
+
+    alone = []
+    for kind, x in jobs:
+        ctx, root, obs = build(kind)
+        ctx.set_data(root, obs, [x])
+        alone.append(ctx.fit(tol=1e-8))
+        ctx.close()
+    srv = gf.Server(precision=gf.GF_FP64, mem_budget=8 << 30, max_slots=8)
+    tickets = []
+    for kind, x in jobs:
+        ctx, root, obs = build(kind)
+        tickets.append(srv.submit(ctx, ctx.make_dataset(obs, [x]), root, tol=1e-8))
+    srv.drain()
+    st = srv.stats()
+    # per tick at most: 1D normalisation, stack machine, AddPdf of leaves, signal + background
+    assert st["launches"] <= 4 * st["ticks"], st
+    for a, t in zip(alone, tickets):
+        r = srv.poll(t)
+        assert r["status"] == a["status"]
+        assert np.array_equal(r["theta"], a["theta"]) and r["nll"] == a["nll"]
     srv.close()
