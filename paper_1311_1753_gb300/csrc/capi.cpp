@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "leafrec.h"
 
 using namespace gfi;
 
@@ -1383,6 +1384,7 @@ int ensure_compiled(gf_ctx* ctx) {
     P.bw = d.bw;
     P.bs2 = d.bs2;
     if (ctx->mixture_path && !d.binned) detect_logsum(P);
+    P.rec_off = 64 * (int)((std::max<size_t>(ctx->pars.size(), 1) + 63) / 64);
     ctx->use_sb = ctx->mixture_path && !d.binned && P.ngrid_blocks > 0 && C.convs.empty() &&
                   C.gns.empty() && detect_sigbkg(P, ctx->sb);
     // the kernels read the program from device memory (it is too large for parameters);
@@ -1533,14 +1535,16 @@ size_t device_bytes_for(const gf_ctx* ctx, int root, int64_t n) {
 static int alloc_work(gf_ctx* ctx) {
   DevState& d = ctx->dev;
   const int npar = (int)std::max<size_t>(ctx->pars.size(), 1);
-  if (!d.theta) CK(cudaMalloc(&d.theta, sizeof(double) * 64 * ((npar + 63) / 64)));
+  // theta, then room for the host-computed leaf records of log-sum programs
+  const size_t nth = 64 * (size_t)((npar + 63) / 64) + 2 * kLogLeaf * kLeafRec;
+  if (!d.theta) CK(cudaMalloc(&d.theta, sizeof(double) * nth));
   if (!d.derived) CK(cudaMalloc(&d.derived, sizeof(double) * (kMaxLeaf * kLeafRec + kMaxCoef)));
   if (!d.counters) {
     CK(cudaMalloc(&d.counters, sizeof(unsigned) * 4));
     CK(cudaMemset(d.counters, 0, sizeof(unsigned) * 4));
   }
   if (!d.norm_out) CK(cudaMalloc(&d.norm_out, sizeof(double) * 64));
-  if (!d.h_theta) CK(cudaMallocHost(&d.h_theta, sizeof(double) * 64 * ((npar + 63) / 64)));
+  if (!d.h_theta) CK(cudaMallocHost(&d.h_theta, sizeof(double) * nth));
   if (!d.h_result) {
     // NLL and gradient (slots 0 .. nfree) and the data-check flag (slot 63) are written by
     // the kernels straight into this pinned buffer through its device mapping: no copy
@@ -1866,13 +1870,32 @@ static int fill_theta_host(gf_ctx* ctx, const double* theta) {
     if (!std::isfinite(theta[k])) return set_error(ctx, GF_EINVAL, "non-finite theta");
     d.h_theta[ctx->free_ids[k]] = theta[k];
   }
+  if (ctx->compiled && ctx->prog.logsum) {
+    // the log-sum kernel's leaf records (analytic leaves: leafrec.h), here once instead of
+    // in FP64 in every block; doubles, then float pairs (hi rounded, lo the rest rounded)
+    const Program& P = ctx->prog;
+    double* rec = d.h_theta + P.rec_off;
+    float* pf = reinterpret_cast<float*>(rec + kLogLeaf * kLeafRec);
+    for (int l = 0; l < P.nleaf; ++l) {
+      double* r = rec + l * kLeafRec;
+      for (int k = 0; k < kLeafRec; ++k) r[k] = 0.0;
+      analytic_leaf_record(P.leaf[l], d.h_theta, (P.leaf[l].aux & kRawLeaf) != 0, r);
+      for (int k = 0; k < kLeafRec; ++k) {
+        const float hi = (float)r[k];
+        pf[2 * (l * kLeafRec + k)] = hi;
+        pf[2 * (l * kLeafRec + k) + 1] = (float)(r[k] - (double)hi);
+      }
+    }
+  }
   return GF_OK;
 }
 
 // Queue the upload of theta on the context's stream.
 static int enqueue_uploads(gf_ctx* ctx) {
   DevState& d = ctx->dev;
-  const int np = (int)ctx->pars.size();
+  int np = (int)ctx->pars.size();
+  if (ctx->compiled && ctx->prog.logsum)
+    np = ctx->prog.rec_off + 2 * kLogLeaf * kLeafRec;  // with the leaf records
   if (np > 0)
     CK(cudaMemcpyAsync(d.theta, d.h_theta, sizeof(double) * np, cudaMemcpyHostToDevice,
                        ctx->stream));

@@ -134,10 +134,12 @@ __device__ inline void reduce_partials(const double* partials, int nblk, int str
         const int b = b0 + lane + 32 * j;
         v[j] = b < nblk ? __ldcg(p + (size_t)b * stride) : 0.0;
       }
+      // only the loaded values: the padding is skipped, not split (df_split takes a
+      // zero down its out-of-line conversion path)
 #pragma unroll
       for (int j = 0; j < kPer; j += 2) {
-        a = df_add(a, df_split(v[j]));
-        a2 = df_add(a2, df_split(v[j + 1]));
+        if (b0 + lane + 32 * j < nblk) a = df_add(a, df_split(v[j]));
+        if (b0 + lane + 32 * (j + 1) < nblk) a2 = df_add(a2, df_split(v[j + 1]));
       }
     }
     a = df_add(a, a2);

@@ -93,6 +93,9 @@ struct Program {
   // K - 1 x [LEAF, LMUL], K <= kLogLeaf, at most 2 observables): log P = sum_k l_k is
   // evaluated directly, without the stack machine.  1: this form, 0: not.
   int32_t logsum;
+  // log-sum programs: the leaves' records (kLogLeaf x kLeafRec doubles), then the same as
+  // float pairs, computed on the host with theta and uploaded behind it at theta + rec_off
+  int32_t rec_off;
   // binned data (the events are bin centres): the metric over bins and its inputs.
   // binned = 0: unbinned events, metric -sum log P.
   int32_t binned, metric;  // metric: GF_METRIC_NLL / _BINNED_NLL / _CHISQ (gf.h)

@@ -15,6 +15,7 @@
 #include "devutil.cuh"
 #include "gf_internal.h"
 #include "launch.h"
+#include "leafrec.h"
 
 namespace gfi {
 
@@ -206,10 +207,10 @@ __device__ __forceinline__ double thresh_r(double x, const ShapeK& K, double* dr
 // rec[0] = 1/N, rec[1] = log N, rec[2 + k] = d log N / d par_k, rec[10 + j] = constants.
 // A leaf flagged kRawLeaf (the core and shell of a CompositePdf) keeps its unnormalised
 // shape: N = 1 and dN = 0.
-__device__ void make_leaf_record(const LeafDesc& L, const double* th, double N, const double* dN,
+__device__ __noinline__ void make_leaf_record(const LeafDesc& L, const double* th, double N, const double* dN,
                                  double* rec) {
   for (int k = 0; k < kLeafRec; ++k) rec[k] = 0.0;
-  const double lo = L.lo, hi = L.hi, D = hi - lo;
+  const double lo = L.lo, hi = L.hi;
   double* c = rec + 10;
   const bool raw = (L.aux & kRawLeaf) != 0;
   const double zero3[3] = {0.0, 0.0, 0.0};
@@ -218,51 +219,10 @@ __device__ void make_leaf_record(const LeafDesc& L, const double* th, double N, 
     dN = zero3;
   }
   switch (L.kind) {
-    case L_EXP: {
-      // N = e^{a lo} expm1(a D)/a;  d log N/da = lo + D phi(aD),
-      // phi(u) = 1/(1 - e^{-u}) - 1/u  (series 1/2 + u/12 - u^3/720 + u^5/30240 - u^7/1209600
-      // for |u| < 0.1, Bernoulli numbers).
-      const double a = th[L.par[0]];
-      const double u = a * D;
-      double logN, phi;
-      if (a == 0.0) {
-        logN = log(D);
-        phi = 0.5;
-      } else {
-        logN = a * lo + log(expm1(u) / a);
-        if (fabs(u) < 0.1) {
-          const double u2 = u * u;
-          phi = 0.5 + u * (1.0 / 12 + u2 * (-1.0 / 720 + u2 * (1.0 / 30240 - u2 / 1209600)));
-        } else {
-          phi = -1.0 / expm1(-u) - 1.0 / u;
-        }
-      }
-      if (raw) logN = 0.0;
-      rec[0] = exp(-logN);
-      rec[1] = logN;
-      rec[2] = raw ? 0.0 : lo + D * phi;
-      c[0] = a;
-      c[1] = -logN;
+    case L_EXP:
+    case L_GAUSS:
+      analytic_leaf_record(L, th, raw, rec);  // leafrec.h (also computed on the host)
       break;
-    }
-    case L_GAUSS: {
-      const double mu = th[L.par[0]], s = th[L.par[1]];
-      const double a = (lo - mu) / s, b = (hi - mu) / s;
-      double diff;  // Phi(b) - Phi(a)
-      if (a > 0.0) diff = 0.5 * (erfc(a / kSqrt2) - erfc(b / kSqrt2));
-      else if (b < 0.0) diff = 0.5 * (erfc(-b / kSqrt2) - erfc(-a / kSqrt2));
-      else diff = 0.5 * (erf(b / kSqrt2) - erf(a / kSqrt2));
-      const double n = raw ? 1.0 : s * kSqrt2Pi * diff;
-      const double ea = exp(-0.5 * a * a), eb = exp(-0.5 * b * b);
-      rec[0] = 1.0 / n;
-      rec[1] = log(n);
-      rec[2] = raw ? 0.0 : (ea - eb) / n;
-      rec[3] = raw ? 0.0 : (a * ea - b * eb) / n + 1.0 / s;
-      c[0] = mu;
-      c[1] = 1.0 / s;
-      c[2] = -rec[1];
-      break;
-    }
     case L_VOIGT: {
       const double mu = th[L.par[0]], s = th[L.par[1]], G = th[L.par[2]];
       rec[0] = 1.0 / N;
@@ -1183,9 +1143,16 @@ __global__ void __launch_bounds__(kThreads1D) k_events_logsum(
   extern __shared__ F2 gsh[];  // G: nfree x blockDim pairs (the per-thread gradient sums)
   const int tid = threadIdx.x, bd = blockDim.x;
   load_program(Pg, P);
-  if (tid < P.nleaf) make_leaf_record(P.leaf[tid], theta, 1.0, nullptr, rec + tid * kLeafRec);
-  __syncthreads();
-  for (int k = tid; k < kMaxLeaf * kLeafRec; k += bd) rf[k] = df_from(rec[k]);
+  // the leaf records and their float pairs, computed on the host with theta (leafrec.h)
+  // and uploaded behind it
+  {
+    const double* hr = theta + P.rec_off;
+    const F2* hp = reinterpret_cast<const F2*>(hr + kLogLeaf * kLeafRec);
+    for (int k = tid; k < P.nleaf * kLeafRec; k += bd) {
+      rec[k] = hr[k];
+      rf[k] = hp[k];
+    }
+  }
   __syncthreads();
 
   const int K = KM == 1 ? 1 : P.nleaf;
