@@ -55,6 +55,16 @@ VOIGT_WORKLOAD = ("1D composite: Voigtian (mu,sigma,Gamma) + threshold (c) with 
 # value and 3 partials 31; threshold value and partial 9; the mixture (2 products, 1 sum)
 # and its gradient terms (6 products, 6 sums) 15; log P and 1/P 2.
 FP64_FLOPS_PER_EVENT = {"voigt_grad": 94}
+# Config 4 (8 resonances, 7 with free mass and width, 30 free parameters), the method's
+# FP64 operations per event counted the same way from the amplitude code: the kinematics of
+# the 3 channels 95 (1/sqrt(s), break-up momentum, Blatt-Weisskopf factors, Zemach terms),
+# 7 Breit-Wigner amplitudes 105 (running width, complex reciprocal, barrier and angular
+# factors), 8 coefficient multiply-adds 64, |A|^2 and log 5; the gradient: 16 coefficient
+# terms 82, 14 mass and width derivatives 273: 624.
+FP64_FLOPS_PER_EVENT["dalitz_free"] = 624
+# Config 3 (every shape fixed): the pass reads each event's 8 cached amplitudes, FP64-
+# accurate as float pairs (16 B each): 128 B/event from HBM.
+BYTES_PER_EVENT = {"dalitz_cached": 128}
 
 
 def _peaks():
@@ -577,6 +587,26 @@ def main():
     roofline = None
     if args.workload in ("voigt", "voigt-mixed"):
         roofline = voigt_roofline(torch, n, kern_s, hbm_peak, mixed=mixed)
+    elif args.workload == "dalitz":
+        gbs = BYTES_PER_EVENT["dalitz_cached"] * n / kern_s / 1e9
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": gbs / hbm_peak, "traffic": None,
+                    "kernel": "k_dalitz_stream<DF, grad, NLL, cached-only>",
+                    "kernel_ms": kern_s * 1e3,
+                    "algorithmic_bytes_per_event": BYTES_PER_EVENT["dalitz_cached"]}
+    elif args.workload in ("dalitz-free", "dalitz-mixed"):
+        # the method's FP64 operations per event against the FP64 unit peak (FP64 plan:
+        # double-float on the FP32 pipe) or, executed in FP32, the FP32 peak (mixed plan)
+        ops = FP64_FLOPS_PER_EVENT["dalitz_free"] * n / kern_s / 1e12
+        pk = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
+        roofline = {"bound": "alu", "achieved": ops, "peak": pk, "unit": "TFLOP/s",
+                    "frac": ops / pk, "traffic": None,
+                    "kernel": ("k_dalitz_stream<float, grad, NLL> (FP32 amplitudes)" if mixed
+                               else "k_dalitz_stream<DF, grad, NLL> (double-float pairs)"),
+                    "kernel_ms": kern_s * 1e3,
+                    "algorithmic_flops_per_event": FP64_FLOPS_PER_EVENT["dalitz_free"],
+                    "peak_source": ("152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz" if mixed
+                                    else "FP64 unit count: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz")}
 
     # end-to-end through the C ABI with host buffers
     e2e = None

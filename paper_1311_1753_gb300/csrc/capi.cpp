@@ -2325,6 +2325,7 @@ int tick_prepare(gf_ctx* ctx) {
   F.gram = d.gram;
   F.partials = d.partials;
   F.counter = d.counters;
+  F.norm_scratch = d.norm_out;
   F.cache_wide = mixed ? 0 : 2;  // float2, or FP64 amplitudes as float pairs
   CK(cudaMalloc(&d.tick_desc, sizeof(F)));
   CK(cudaMemcpyAsync(d.tick_desc, &F, sizeof(F), cudaMemcpyHostToDevice, ctx->stream));

@@ -92,16 +92,39 @@ template <int M = -1, class Val>
 __device__ __forceinline__ void block_sum_pairs(Val val, int m, double* red, double* out,
                                                 int ostride = 1) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (M >= 0) m = M;
+  if (M >= 0) {
+    m = M;
 #pragma unroll
-  for (int k = 0; k < (M >= 0 ? M : m); ++k) {
-    F2 v = val(k);
+    for (int k = 0; k < M; ++k) {
+      F2 v = val(k);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const F2 u = {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
-      v = df_add(v, u);
+      for (int o = 16; o > 0; o >>= 1) {
+        const F2 u = {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+        v = df_add(v, u);
+      }
+      if (lane == 0) red[warp * m + k] = df_to(v);
     }
-    if (lane == 0) red[warp * m + k] = df_to(v);
+  } else {
+    // values four at a time, their shuffle trees interleaved (the same tree per value)
+    for (int k0 = 0; k0 < m; k0 += 4) {
+      F2 v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = k0 + j < m ? val(k0 + j) : F2{0.f, 0.f};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const F2 u = {__shfl_down_sync(0xffffffffu, v[j].hi, o),
+                        __shfl_down_sync(0xffffffffu, v[j].lo, o)};
+          v[j] = df_add(v[j], u);
+        }
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (k0 + j < m) red[warp * m + k0 + j] = df_to(v[j]);
+      }
+    }
   }
   __syncthreads();
   for (int k = threadIdx.x; k < m; k += blockDim.x) {

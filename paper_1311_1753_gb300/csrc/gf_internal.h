@@ -234,7 +234,8 @@ struct FitDz {
   const void* ev_cache;
   const double* gram;
   double* partials;
-  unsigned* counter;
+  unsigned* counter;      // [0] arrivals, [2] the first block done (it forms N)
+  double* norm_scratch;   // 1 + nfree doubles: N and dN/dtheta from that block
   int cache_wide;
   int pad;
 };

@@ -678,7 +678,7 @@ __device__ __forceinline__ void dalitz_stream_block(
     const void* __restrict__ cache, int64_t cache_stride, int cache_wide,
     const uint8_t* __restrict__ inside,
     double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
-    double* __restrict__ out_logp, const double* __restrict__ norm_in, int norm_mode,
+    double* __restrict__ out_logp, double* __restrict__ norm_io, int norm_mode,
     const double* __restrict__ gram, const int vb, const int vgrid, double* dyn,
     DzShared<T>& sh) {
   constexpr bool kF = std::is_same<T, float>::value;
@@ -715,7 +715,7 @@ __device__ __forceinline__ void dalitz_stream_block(
         N += cr * sh.gv[2 * k] + ci * sh.gv[2 * k + 1];
       }
     } else {
-      N = norm_in[0];
+      N = norm_io[0];
     }
     sh.logN = log(N);
   }
@@ -869,6 +869,36 @@ __device__ __forceinline__ void dalitz_stream_block(
   // partials value-major: value k of block b at partials[k vgrid + b]
   block_sum_pairs([&](int k) { return k == 0 ? acc.pair() : gacc[(k - 1) * bd].pair(); }, m, red,
                   partials + vb, vgrid);
+  // Gram normalisation: the first block done with its events forms N = c^H G c and dN
+  // (serial FP64 work) and leaves them in norm_io before it arrives, off the last block's
+  // path; the last block to arrive finds them there
+  const bool gram_nll = METRIC == METRIC_NLL && norm_mode == DN_GRAM;
+  if (gram_nll) {
+    if (tid == 0) sh.last = atomicAdd(counter + 2, 1u) == 0u;
+    __syncthreads();
+    if (sh.last) {
+      gram_apply(gram, rk, nres + 1, sh.gv);
+      __syncthreads();
+      if (tid == 0) {
+        // N = c^H G c, c_0 = a_NR = 1;  v_k = sum_s G_ks c_s;  dN/dRe c_k = 2 Re v_k,
+        // dN/dIm c_k = 2 Im v_k
+        double N = 0.0;
+        for (int k = 0; k < nf; ++k) norm_io[1 + k] = 0.0;
+        for (int k = 0; k <= nres; ++k) {
+          double cr, ci;
+          gram_coef(rk, k, cr, ci);
+          const double vr = sh.gv[2 * k], vi = sh.gv[2 * k + 1];
+          N += cr * vr + ci * vi;  // Re(conj(c_k) v_k)
+          if (k > 0 && G) {
+            const DalitzRes& R = D.res[k - 1];
+            if (R.g_re >= 0) norm_io[1 + R.g_re] += 2.0 * vr;
+            if (R.g_im >= 0) norm_io[1 + R.g_im] += 2.0 * vi;
+          }
+        }
+        norm_io[0] = N;
+      }
+    }
+  }
   if (!arrive_last_of(counter, (unsigned)vgrid, &sh.last)) return;
   double* tot = sh.tot;
   reduce_partials(partials, vgrid, 1, m, tot, vgrid);
@@ -877,40 +907,18 @@ __device__ __forceinline__ void dalitz_stream_block(
     const double dA = D.hx * D.hy;
     if (tid < m) result[tid] = tot[tid] * dA;
   } else {
-    if (norm_mode == DN_GRAM) gram_apply(gram, rk, nres + 1, sh.gv);
-    __syncthreads();
-  }
-  if (METRIC != METRIC_NORM && tid == 0) {
-    // combine with the normalisation: + n log N, + n dN/N
-    double N;
-    double dN[4 * kMaxRes];
-    for (int k = 0; k < nf; ++k) dN[k] = 0.0;
-    if (norm_mode == DN_GRAM) {
-      // N = c^H G c, c_0 = a_NR = 1;  v_k = sum_s G_ks c_s;  dN/dRe c_k = 2 Re v_k,
-      // dN/dIm c_k = 2 Im v_k
-      N = 0.0;
-      for (int k = 0; k <= nres; ++k) {
-        double cr, ci;
-        gram_coef(rk, k, cr, ci);
-        const double vr = sh.gv[2 * k], vi = sh.gv[2 * k + 1];
-        N += cr * vr + ci * vi;  // Re(conj(c_k) v_k)
-        if (k > 0 && G) {
-          const DalitzRes& R = D.res[k - 1];
-          if (R.g_re >= 0) dN[R.g_re] += 2.0 * vr;
-          if (R.g_im >= 0) dN[R.g_im] += 2.0 * vi;
-        }
-      }
-    } else {
-      N = norm_in[0];
-      if (G)
-        for (int k = 0; k < nf; ++k) dN[k] = norm_in[1 + k];
-    }
+    // combine with the normalisation (the Gram form's from the first block above, the
+    // direct cell pass's otherwise): + n log N, + n dN/N, one value per thread
+    const double N = __ldcg(norm_io);
     const double nn = (double)n;
-    result[0] = tot[0] + nn * log(N);
+    if (tid == 0) result[0] = tot[0] + nn * log(N);
     if (G)
-      for (int k = 0; k < nf; ++k) result[1 + k] = tot[1 + k] + nn * dN[k] / N;
+      for (int k = tid; k < nf; k += bd) result[1 + k] = tot[1 + k] + nn * __ldcg(norm_io + 1 + k) / N;
   }
-  if (tid == 0) *counter = 0u;
+  if (tid == 0) {
+    counter[0] = 0u;
+    if (gram_nll) counter[2] = 0u;
+  }
 }
 
 // Registers per variant (measured): pair (DF) event passes are held to 85 (3 blocks of
@@ -930,14 +938,14 @@ __global__ void __launch_bounds__(kThreads, dz_min_blocks<T, G, METRIC, CO>()) k
     const void* __restrict__ cache, int64_t cache_stride, int cache_wide,
     const uint8_t* __restrict__ inside,
     double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ result,
-    double* __restrict__ out_logp, const double* __restrict__ norm_in, int norm_mode,
+    double* __restrict__ out_logp, double* __restrict__ norm_io, int norm_mode,
     const double* __restrict__ gram) {
   extern __shared__ double dyn[];
   __shared__ DzShared<T> sh;
   load_df_tables();
   dalitz_stream_block<T, G, METRIC, CO>(D, theta, s12d, s13d, sf, n, cache, cache_stride,
                                         cache_wide, inside, partials, counter, result, out_logp,
-                                        norm_in, norm_mode, gram, blockIdx.x, gridDim.x, dyn, sh);
+                                        norm_io, norm_mode, gram, blockIdx.x, gridDim.x, dyn, sh);
 }
 
 // ---- batched tick: every waiting Dalitz fit (Gram normalisation) in one persistent launch
@@ -964,8 +972,9 @@ __global__ void __launch_bounds__(kThreads) k_tick_dalitz(const TickItem* __rest
     }
     dalitz_stream_block<T, true, METRIC_NLL, true>(Ds, ti.theta, F->s12, F->s13, F->sf, F->n,
                                              F->ev_cache, F->n, F->cache_wide, nullptr,
-                                             F->partials, F->counter, ti.result, nullptr, nullptr,
-                                             DN_GRAM, F->gram, it - ti.item0, ti.nitems, dyn, sh);
+                                             F->partials, F->counter, ti.result, nullptr,
+                                             F->norm_scratch, DN_GRAM, F->gram, it - ti.item0,
+                                             ti.nitems, dyn, sh);
     __syncthreads();
   }
 }
