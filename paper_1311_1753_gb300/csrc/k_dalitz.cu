@@ -690,8 +690,18 @@ __device__ __forceinline__ void dalitz_stream_block(
   const int nf = D.nfree;
   const int nres = D.nres;
   if (tid < nres) {
-    res_constants(D, D.res[tid], theta, rk[tid]);
-    make_resf(rk[tid], rkf[tid]);
+    if constexpr (CO) {
+      // every amplitude cached: only the coefficients enter (no running-width, barrier or
+      // mass constants, whose FP64 square roots and divisions cost the prologue ~8 us)
+      ResK& k = rk[tid];
+      k.cr = theta[D.res[tid].p_re];
+      k.ci = theta[D.res[tid].p_im];
+      split_const(k.cr, rkf[tid].crh, rkf[tid].crl);
+      split_const(k.ci, rkf[tid].cih, rkf[tid].cil);
+    } else {
+      res_constants(D, D.res[tid], theta, rk[tid]);
+      make_resf(rk[tid], rkf[tid]);
+    }
   }
   if (tid < 3) {
     int need = 0;
@@ -702,7 +712,14 @@ __device__ __forceinline__ void dalitz_stream_block(
   if (G)
     for (int k = 0; k < nf; ++k) gacc[k * bd] = Acc<T>();
   __syncthreads();
-  fill_dzc<T>(D, rk, sh.C);
+  if constexpr (CO) {
+    if (tid < nres) {
+      sh.C.cr[tid] = conv<T>(rk[tid].cr);
+      sh.C.ci[tid] = conv<T>(rk[tid].ci);
+    }
+  } else {
+    fill_dzc<T>(D, rk, sh.C);
+  }
   if (METRIC == METRIC_STORE && norm_mode == DN_GRAM) gram_apply(gram, rk, nres + 1, sh.gv);
   __syncthreads();
   if (METRIC == METRIC_STORE && tid == 0) {
