@@ -224,15 +224,17 @@ __device__ __noinline__ void make_leaf_record(const LeafDesc& L, const double* t
       analytic_leaf_record(L, th, raw, rec);  // leafrec.h (also computed on the host)
       break;
     case L_VOIGT: {
+      // two FP64 reciprocals (GB300's FP64 divisions are long serial sequences)
       const double mu = th[L.par[0]], s = th[L.par[1]], G = th[L.par[2]];
-      rec[0] = 1.0 / N;
+      const double iN = 1.0 / N, is = 1.0 / s;
+      rec[0] = iN;
       rec[1] = log(N);
-      for (int k = 0; k < 3; ++k) rec[2 + k] = dN[k] / N;
+      for (int k = 0; k < 3; ++k) rec[2 + k] = dN[k] * iN;
       c[0] = mu;
-      c[1] = 1.0 / (s * kSqrt2);
+      c[1] = is * (1.0 / kSqrt2);
       c[2] = 0.5 * G * c[1];
-      c[3] = 1.0 / (s * kSqrt2Pi * N);
-      c[4] = 1.0 / s;
+      c[3] = is * iN * (1.0 / kSqrt2Pi);
+      c[4] = is;
       // products the event-side gradient uses
       c[5] = c[3] * c[1];
       c[6] = c[3] * c[4];
@@ -241,13 +243,14 @@ __device__ __noinline__ void make_leaf_record(const LeafDesc& L, const double* t
       break;
     }
     case L_THRESH: {
-      rec[0] = 1.0 / N;
+      const double iN = 1.0 / N;
+      rec[0] = iN;
       rec[1] = log(N);
-      for (int k = 0; k < 3; ++k) rec[2 + k] = dN[k] / N;
+      for (int k = 0; k < 3; ++k) rec[2 + k] = dN[k] * iN;
       c[0] = th[L.par[0]];
       c[1] = th[L.par[1]];
       c[2] = th[L.par[2]];
-      c[3] = 1.0 / N;
+      c[3] = iN;
       break;
     }
     case L_RELBW: {
@@ -356,10 +359,9 @@ __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& 
       v[3] = dr[2];
     }
   }
-  for (int k = 0; k < 4; ++k) {
-    const double r = block_sum(v[k], red);
-    if (threadIdx.x == 0) partials[(size_t)vb * 4 + k] = r;
-  }
+  // the four block sums in one pass (pairs, their shuffle trees interleaved)
+  block_sum_pairs<4>([&](int k) -> F2 { return df_from(v[k]); }, 4, red,
+                     partials + (size_t)vb * 4);
   if (!arrive_last_of(counter, (unsigned)vgrid, last)) return;
   // last block: one warp per (leaf, value), its lanes' loads of the leaf's chunk partials
   // all in flight, fixed-order pair sums; then every leaf record
@@ -380,7 +382,8 @@ __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& 
                                     : 0.0;
         }
 #pragma unroll
-        for (int j = 0; j < kPer; ++j) a = df_add(a, df_split(t[j]));
+        for (int j = 0; j < kPer; ++j)  // the padding skipped (df_split's zero path is a call)
+          if (b0 + lane + 32 * j < L.grid_nblocks) a = df_add(a, df_split(t[j]));
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -391,10 +394,11 @@ __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& 
     }
   }
   __syncthreads();
-  if (threadIdx.x < P.nleaf) {
-    const int l = threadIdx.x;
-    make_leaf_record(P.leaf[l], theta, sums[l][0], &sums[l][1], derived + l * kLeafRec);
-  }
+  // one leaf per warp (lane 0): the leaves' FP64 records run side by side, not as
+  // divergent branches of one warp
+  if ((threadIdx.x & 31) == 0)
+    for (int l = threadIdx.x >> 5; l < P.nleaf; l += blockDim.x >> 5)
+      make_leaf_record(P.leaf[l], theta, sums[l][0], &sums[l][1], derived + l * kLeafRec);
   if (threadIdx.x == 0) {
     make_coefs(P, theta, derived + kMaxLeaf * kLeafRec);
     *counter = 0u;
@@ -1505,7 +1509,7 @@ __device__ __forceinline__ const TickItem& tick_item(const TickItem* __restrict_
 }
 
 // normalisation grids of every batched fit (kThreads threads: one bin per thread)
-__global__ void __launch_bounds__(kThreads) k_tick_norm_1d(const TickItem* __restrict__ items,
+__global__ void __launch_bounds__(kThreads, 1) k_tick_norm_1d(const TickItem* __restrict__ items,
                                                            int nfits, int total,
                                                            const __grid_constant__ WeidCoef W) {
   __shared__ Program Ps;
