@@ -36,15 +36,22 @@ from paper_1311_1753_gb300 import synth  # noqa: E402
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# The config-2 event pass (k_sigbkg, FP64 plan) computes FP64-accurate results in
-# double-float arithmetic (pairs of floats) on the FP32 pipe.  Its implementation's FP32
-# flops per event (FADD + FMUL + 2 FFMA executed per event, predicated-on) and the DRAM
-# traffic of one launch are ncu counters of the 10^7-event launch of this build (the
-# profile summary of k_sigbkg under profiles/); None where no capture of the current
-# kernel exists.
-FP32_FLOPS_PER_EVENT = {"voigt_grad": 593.1}   # FADD 334.4 + FMUL 45.1 + 2 x FFMA 106.8
-TRAFFIC_PER_LAUNCH = {"voigt_grad": 81.72e6,        # 80.14 MB read + 1.58 MB written
-                      "voigt_grad_mixed": 83.28e6}  # 80.39 MB read + 2.89 MB written
+# The FP64 plans compute FP64-accurate results in double-float arithmetic (pairs of
+# floats) on the FP32 pipe.  Each timed event kernel's FP32 flops per event (FADD + FMUL
+# + 2 FFMA executed per event, predicated-on) and the DRAM traffic of one launch are ncu
+# counters of one launch of this build at the bench's own size (the profile summaries
+# of k_sigbkg and k_dalitz_stream under profiles/).
+FP32_FLOPS_PER_EVENT = {"voigt_grad": 593.1,      # FADD 334.4 + FMUL 45.1 + 2 x FFMA 106.8
+                        "voigt_grad_mixed": 100.5,  # FADD 38.2 + FMUL 18.2 + 2 x FFMA 22.1
+                        "dalitz_cached": 1349.8,  # FADD 781.8 + FMUL 82.0 + 2 x FFMA 243.0
+                        "dalitz_free": 7446.0,    # FADD 3933.4 + FMUL 531.0 + 2 x FFMA 1491.0
+                        "dalitz_mixed": 902.4}    # FADD 204.0 + FMUL 280.0 + 2 x FFMA 209.0
+TRAFFIC_PER_LAUNCH = {"voigt_grad": 81.79e6,        # 80.15 MB read + 1.64 MB written
+                      "voigt_grad_mixed": 83.61e6,  # 80.45 MB read + 3.16 MB written
+                      "dalitz_cached": 131.34e6,    # 128.12 MB read + 3.22 MB written (10^6)
+                      "dalitz_free": 865.82e6,      # 164.01 MB read + 701.81 MB written (5 x 10^6;
+                                                    # the writes are register spills)
+                      "dalitz_mixed": 103.01e6}     # 100.13 MB read + 2.88 MB written (5 x 10^6)
 # the headline workload's name, shared by both arms' JSON lines
 VOIGT_WORKLOAD = ("1D composite: Voigtian (mu,sigma,Gamma) + threshold (c) with fraction f, "
                   "10^7 FP64 events, 2 x 10,000-bin grid normalisation")
@@ -407,6 +414,15 @@ def measured_fp64_tflops(torch, n=4096, reps=3):
     return 2.0 * n ** 3 / best / 1e12
 
 
+def fp32_issue(flops_per_event, n, kern_s):
+    """The implementation's FP32 flops (ncu's predicated-on FADD + FMUL + 2 x FFMA per
+    event) per second against the FP32 unit peak: how busy the FP32 pipe was kept."""
+    a32 = flops_per_event * n / kern_s / 1e12
+    return {"flops_per_event": flops_per_event, "achieved_tflops": a32,
+            "peak_tflops": FP32_PEAK_TFLOPS, "frac": a32 / FP32_PEAK_TFLOPS,
+            "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"}
+
+
 def voigt_roofline(torch, n, kern_s, hbm_peak, mixed=False):
     """Roofline of the headline event kernel (k_sigbkg<grad>, FP64 plan).  Headline: the
     method's work, FP64_FLOPS_PER_EVENT per event, against the FP64 unit peak (the pass
@@ -429,12 +445,8 @@ def voigt_roofline(torch, n, kern_s, hbm_peak, mixed=False):
         rf["fp64_dgemm_measured_tflops"] = measured_fp64_tflops(torch)
     except Exception as e:  # context only
         rf["fp64_dgemm_measured_tflops"] = repr(e)[:100]
-    f32 = None if mixed else FP32_FLOPS_PER_EVENT.get("voigt_grad")
-    if f32:
-        a32 = f32 * n / kern_s / 1e12
-        rf["fp32_issue"] = {"flops_per_event": f32, "achieved_tflops": a32,
-                            "peak_tflops": FP32_PEAK_TFLOPS, "frac": a32 / FP32_PEAK_TFLOPS,
-                            "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"}
+    rf["fp32_issue"] = fp32_issue(
+        FP32_FLOPS_PER_EVENT["voigt_grad_mixed" if mixed else "voigt_grad"], n, kern_s)
     return rf
 
 
@@ -551,8 +563,8 @@ def main():
         wl = "truncated exponential, 10^5 FP64 events, analytic normalisation"
         metric = "NLL+gradient evaluations: events x evals/s (exponential, FP64-accurate)"
     else:
-        # config 3 (dalitz: fixed shapes, cached amplitudes) or config 4 (free masses and
-        # widths: amplitudes recomputed per event) in mixed precision or FP64
+        # fixed-shape Dalitz (cached amplitudes, 10^6 events) or free-shape Dalitz (masses and
+        # widths free: amplitudes recomputed per event, 5 x 10^6 events) in mixed precision or FP64
         mixed = args.workload == "dalitz-mixed"
         big = args.workload in ("dalitz-mixed", "dalitz-free")
         n = 5_000_000 if big else 1_000_000
@@ -590,17 +602,21 @@ def main():
     elif args.workload == "dalitz":
         gbs = BYTES_PER_EVENT["dalitz_cached"] * n / kern_s / 1e9
         roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": gbs / hbm_peak, "traffic": None,
+                    "frac": gbs / hbm_peak, "traffic": TRAFFIC_PER_LAUNCH["dalitz_cached"],
                     "kernel": "k_dalitz_stream<DF, grad, NLL, cached-only>",
                     "kernel_ms": kern_s * 1e3,
-                    "algorithmic_bytes_per_event": BYTES_PER_EVENT["dalitz_cached"]}
+                    "algorithmic_bytes_per_event": BYTES_PER_EVENT["dalitz_cached"],
+                    "fp32_issue": fp32_issue(FP32_FLOPS_PER_EVENT["dalitz_cached"], n, kern_s)}
     elif args.workload in ("dalitz-free", "dalitz-mixed"):
         # the method's FP64 operations per event against the FP64 unit peak (FP64 plan:
         # double-float on the FP32 pipe) or, executed in FP32, the FP32 peak (mixed plan)
         ops = FP64_FLOPS_PER_EVENT["dalitz_free"] * n / kern_s / 1e12
         pk = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
         roofline = {"bound": "alu", "achieved": ops, "peak": pk, "unit": "TFLOP/s",
-                    "frac": ops / pk, "traffic": None,
+                    "frac": ops / pk,
+                    "traffic": TRAFFIC_PER_LAUNCH["dalitz_mixed" if mixed else "dalitz_free"],
+                    "fp32_issue": fp32_issue(FP32_FLOPS_PER_EVENT["dalitz_mixed" if mixed
+                                                                  else "dalitz_free"], n, kern_s),
                     "kernel": ("k_dalitz_stream<float, grad, NLL> (FP32 amplitudes)" if mixed
                                else "k_dalitz_stream<DF, grad, NLL> (double-float pairs)"),
                     "kernel_ms": kern_s * 1e3,
@@ -696,7 +712,7 @@ def run_fits(torch, gf, args):
 
     ctx, root, obs, cols, th = exp_workload(gf, 100_000, synth.SEED_EXP, gf.GF_FP64)
     r = timed_fit(ctx, np.array([-2.0]), 1e-8)
-    out["config1_exp_1e5"] = {"seconds": r["seconds"], "calls": r["n_calls"], "status": r["status"],
+    out["exp_1e5"] = {"seconds": r["seconds"], "calls": r["n_calls"], "status": r["status"],
                               "alpha": float(r["theta"][0]), "err": float(r["err"][0])}
     ctx.close()
     res = {}
@@ -704,15 +720,15 @@ def run_fits(torch, gf, args):
         ctx, root, obs, cols, th = voigt_workload(gf, 10_000_000, synth.SEED_VOIGT, prec)
         res[name] = timed_fit(ctx, th * np.array([1.0002, 1.1, 0.85, 1.1, 0.93]), 1e-6)
         ctx.close()
-    out["config2_voigt_1e7"] = pair(res["fp64"], res["mixed"], 10_000_000)
-    out["config2_voigt_1e7"]["pull_vs_truth_fp64"] = (
+    out["voigt_1e7"] = pair(res["fp64"], res["mixed"], 10_000_000)
+    out["voigt_1e7"]["pull_vs_truth_fp64"] = (
         (res["fp64"]["theta"] - th) / res["fp64"]["err"]).tolist()
     spec = dalitz_spec()
     data = dalitz_events_gpu(gf, spec, 1_000_000, synth.SEED_DALITZ_EVENTS)
     ctx, root, obs, cols, th = dalitz_workload(gf, 1_000_000, 0, gf.GF_FP64, False, data)
     rng = np.random.default_rng(8)
     r = timed_fit(ctx, th + 0.02 * rng.standard_normal(len(th)), 1e-6)
-    out["config3_dalitz_1e6"] = {"seconds": r["seconds"], "calls": r["n_calls"],
+    out["dalitz_fixed_1e6"] = {"seconds": r["seconds"], "calls": r["n_calls"],
                                  "status": r["status"]}
     ctx.close()
     data5 = dalitz_events_gpu(gf, spec, 5_000_000, synth.SEED_DALITZ_BIG)
@@ -722,7 +738,7 @@ def run_fits(torch, gf, args):
         start = th * (1 + 0.01 * np.random.default_rng(9).standard_normal(len(th)))
         res[name] = timed_fit(ctx, start, 1e-8)
         ctx.close()
-    out["config4_dalitz_5e6"] = pair(res["fp64"], res["mixed"], 5_000_000)
+    out["dalitz_free_5e6"] = pair(res["fp64"], res["mixed"], 5_000_000)
     return out
 
 
@@ -980,45 +996,45 @@ def run_tddp(torch, gf, n=100_000, steps=30):
 
 
 def run_extra(torch, gf, args):
-    """Secondary measurements: configs 1, 3, 4 evaluation rates (and, on request, fit
+    """Secondary measurements: exponential, binned, mixing and Dalitz evaluation rates (and, on request, fit
     times and the serving study)."""
     out = {}
     K = max(5, args.steps)
-    # config 1
+    # truncated exponential, 10^5 events
     ctx, root, obs, cols, th = exp_workload(gf, 100_000, synth.SEED_EXP, gf.GF_FP64)
     r = time_steps(torch, ctx, [th * (1 + 1e-3 * k) for k in range(4)], 50, 5, flush=False)
-    out["config1_exp_1e5"] = {"events_x_evals_per_s": 1e5 * 50 / (sum(r["step_ms"]) / 1e3),
+    out["exp_1e5"] = {"events_x_evals_per_s": 1e5 * 50 / (sum(r["step_ms"]) / 1e3),
                               "us_per_eval": 1e3 * float(np.mean(r["step_ms"])),
                               "kernel_us": 1e3 * float(np.mean(r["kernel_ms"]))}
     ctx.close()
-    out["config1_exp_hbm_sweep"] = run_exp_sweep(torch, gf)
+    out["exp_hbm_sweep"] = run_exp_sweep(torch, gf)
     out["binned_voigt_4000"] = run_binned(torch, gf)
     out["binned_relbw_conv_4000"] = run_zach(torch, gf)
     out["tddp_mixing_1e5"] = run_tddp(torch, gf)
-    # config 3 (FP64, 1e6 events, cached per-event amplitudes, Gram normalisation)
+    # fixed-shape Dalitz (FP64, 1e6 events, cached per-event amplitudes, Gram normalisation)
     spec = dalitz_spec()
     data = dalitz_events_gpu(gf, spec, 1_000_000, synth.SEED_DALITZ_EVENTS)
     ctx, root, obs, cols, th = dalitz_workload(gf, 1_000_000, 0, gf.GF_FP64, False, data)
     rng = np.random.default_rng(2)
     ths = [th * (1 + 1e-3 * rng.standard_normal(len(th))) for _ in range(4)]
     r = time_steps(torch, ctx, ths, K, 3)
-    out["config3_dalitz_fp64_1e6"] = {
+    out["dalitz_fixed_fp64_1e6"] = {
         "events_x_evals_per_s": 1e6 * K / (sum(r["step_ms"]) / 1e3),
         "ms_per_eval": float(np.mean(r["step_ms"])), "kernel_ms": float(np.mean(r["kernel_ms"]))}
     ctx.close()
-    # config 4 data: 5e6 events; mixed vs FP64 on the same data, 30 free parameters
+    # free-shape Dalitz data: 5e6 events; mixed vs FP64 on the same data, 30 free parameters
     data5 = dalitz_events_gpu(gf, spec, 5_000_000, synth.SEED_DALITZ_BIG)
     for prec, name in ((gf.GF_MIXED, "mixed"), (gf.GF_FP64, "fp64")):
         ctx, root, obs, cols, th = dalitz_workload(gf, 5_000_000, 0, prec, True, data5)
         ths = [th * (1 + 1e-3 * rng.standard_normal(len(th))) for _ in range(4)]
         r = time_steps(torch, ctx, ths, K, 3)
-        out[f"config4_dalitz_{name}_5e6"] = {
+        out[f"dalitz_free_{name}_5e6"] = {
             "events_x_evals_per_s": 5e6 * K / (sum(r["step_ms"]) / 1e3),
             "ms_per_eval": float(np.mean(r["step_ms"])),
             "kernel_ms": float(np.mean(r["kernel_ms"])), "free_params": len(th)}
         ctx.close()
-    m, f = out["config4_dalitz_mixed_5e6"], out["config4_dalitz_fp64_5e6"]
-    out["config4_mixed_over_fp64_speedup"] = f["ms_per_eval"] / m["ms_per_eval"]
+    m, f = out["dalitz_free_mixed_5e6"], out["dalitz_free_fp64_5e6"]
+    out["dalitz_free_mixed_over_fp64_speedup"] = f["ms_per_eval"] / m["ms_per_eval"]
     return out
 
 

@@ -1,4 +1,4 @@
-"""Parity of the sm_103a 1D path with the FP64 oracle (configs 1 and 2, generic trees).
+"""Parity of the sm_103a 1D path with the FP64 oracle (truncated exponential, Voigtian + threshold, generic trees).
 
 Tolerances: 1e-12 relative per event on P (|log P_gpu - log P_orc| <= 1e-12 for every
 event), 1e-9 relative on the total NLL, gradients 1e-9 relative to the gradient's scale."""
@@ -31,9 +31,9 @@ def _grad_close(g_gpu, g_orc, n, rel=1e-9):
     assert np.all(np.abs(g_gpu - g_orc) <= rel * scale + 1e-9 * np.abs(g_orc).max()), (g_gpu, g_orc)
 
 
-# ---- config 1: exponential ------------------------------------------------------------------------
+# ---- truncated exponential ------------------------------------------------------------------------
 @pytest.mark.parametrize("n", [0, 1, 2, 31, 33, 257, 100_000, 1_000_003])
-def test_config1_exponential_parity(gf, n):
+def test_exponential_parity(gf, n):
     x = synth.exp_events(max(n, 1), -1.0)[:n]
     ctx, root, obs = pm.exp_model(gf, -2.0)
     ctx.set_data(root, obs, [x])
@@ -53,7 +53,7 @@ def test_config1_exponential_parity(gf, n):
             assert abs(g[0] - go[0]) <= 1e-9 * max(abs(go[0]), n * 1e-6)
 
 
-def test_config1_deterministic_bitwise(gf):
+def test_exponential_deterministic_bitwise(gf):
     x = synth.exp_events(100_000, -1.0)
     ctx, root, obs = pm.exp_model(gf)
     ctx.set_data(root, obs, [x])
@@ -61,14 +61,14 @@ def test_config1_deterministic_bitwise(gf):
     assert len(vals) == 1
 
 
-# ---- config 2: Voigtian + threshold --------------------------------------------------------------------
+# ---- Voigtian + threshold --------------------------------------------------------------------
 def _voigt_data(n, seed=synth.SEED_VOIGT):
     lo, hi = synth.VOIGT_RANGE
     return synth.voigt_threshold_events(n, **synth.VOIGT_TRUTH, lo=lo, hi=hi, seed=seed)
 
 
 @pytest.mark.parametrize("n", [1, 33, 4099, 200_000])
-def test_config2_voigt_parity(gf, n):
+def test_voigt_parity(gf, n):
     x = _voigt_data(n)
     ctx, root, obs = pm.voigt_model(gf)
     ctx.set_data(root, obs, [x])
@@ -87,7 +87,7 @@ def test_config2_voigt_parity(gf, n):
         _grad_close(g, go[free], n)
 
 
-def test_config2_free_shape_parameters(gf):
+def test_voigt_free_shape_parameters(gf):
     # x0 and power free as well (fixed in the workload, free in general)
     x = _voigt_data(20_000)
     ctx, root, obs = pm.voigt_model(gf, free_shape=True, nbins=2000)
@@ -103,7 +103,7 @@ def test_config2_free_shape_parameters(gf):
     _grad_close(g, go, len(x), rel=1e-8)
 
 
-def test_config2_full_size(gf):
+def test_voigt_full_size(gf):
     """10^7 events in the benchmark's launch shape (sorted layout, chunked w): total NLL
     against the oracle's full sum, and log P of every event against the oracle's."""
     x = _voigt_data(10_000_000)

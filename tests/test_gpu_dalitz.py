@@ -1,10 +1,10 @@
-"""Parity of the sm_103a Dalitz path with the FP64 oracle (configs 3 and 4).
+"""Parity of the sm_103a Dalitz path with the FP64 oracle (fixed-shape and free-shape eight-resonance models).
 
 Per event: |log P_gpu - log P_orc| <= 1e-12 max(1, kappa_i) for every event, with the
 interference condition number kappa_i = (|a_NR| + sum_r |c_r A_r|)^2 / |A|^2.  Total NLL
 1e-9 relative; gradients 1e-9 relative to their scale.  FP32 (mixed) results: errors are
 measured and bounded (per event: median 1e-5, 99th percentile 1e-3 relative; NLL 1e-6
-relative).  The full-size cases (10^6 events of config 3, 5 x 10^6 of config 4) compare
+relative).  The full-size cases (10^6 events with fixed shapes, 5 x 10^6 with free masses and widths) compare
 every event; the oracle runs over the host cores there (tests/oracle_pool.py)."""
 from __future__ import annotations
 
@@ -105,7 +105,7 @@ def test_dalitz_gram_matches_oracle_norm(gf):
 
 
 def test_dalitz_full_size(gf):
-    """10^6 events (config 3) in the benchmark's launch shape: NLL against the oracle's
+    """10^6 events (fixed shapes) in the benchmark's launch shape: NLL against the oracle's
     full sum, and log P of every event within 1e-12 max(1, kappa_i)."""
     nres = len(SPEC["resonances"])
     s12, s13 = _events(1_000_000)
@@ -123,7 +123,7 @@ def test_dalitz_full_size(gf):
     WORST["config3 full 1e6: events with kappa > 1e3"] = float((kap > 1e3).sum())
 
 
-def test_config4_full_size_fp64_and_mixed(gf):
+def test_free_shape_full_size_fp64_and_mixed(gf):
     """5 x 10^6 events, 30 free parameters (masses and widths of 7 resonances free), the
     512 x 512 grid: the FP64 plan against the oracle on every event, NLL and gradient;
     the mixed plan (FP32 amplitudes) with its error percentiles stated and bounded."""

@@ -35,7 +35,7 @@ def _oracle_fit(m, free, cols, x0, step, lo, hi, fun=None):
 
 
 @pytest.mark.parametrize("use_grad", [True, False])
-def test_config1_fit(gf, use_grad):
+def test_exponential_fit(gf, use_grad):
     x = synth.exp_events(100_000, -1.0)
     ctx, root, obs = pm.exp_model(gf, -2.0)
     ctx.set_data(root, obs, [x])
@@ -55,7 +55,7 @@ def test_config1_fit(gf, use_grad):
     assert abs(r["theta"][0] - root_) <= 0.01 * o.err[0]
 
 
-def test_config2_fit(gf):
+def test_voigt_fit(gf):
     lo, hi = synth.VOIGT_RANGE
     x = synth.voigt_threshold_events(200_000, **synth.VOIGT_TRUTH, lo=lo, hi=hi, seed=99)
     m, free = om.voigt_model(nbins=2000)
@@ -76,7 +76,7 @@ def test_config2_fit(gf):
     assert np.all(np.abs(r["err"] / o.err - 1) < 0.01)
 
 
-def test_config3_fit_small_grid(gf):
+def test_dalitz_fixed_shape_fit_small_grid(gf):
     nres = len(SPEC["resonances"])
     d = om.dalitz_from_spec(SPEC, 128, 128)
     d_full = om.dalitz_from_spec(SPEC)
@@ -113,7 +113,7 @@ def test_autograd_wrapper(gf):
     assert abs(th.grad.item() - go[0]) <= 1e-9 * abs(go[0])
 
 
-def test_config4_mixed_fit_small(gf):
+def test_dalitz_free_shape_mixed_fit_small(gf):
     """Config 4's shape: 30 free parameters (7 masses and widths free), FP32 amplitudes with
     FP64 sums and normalisation, fused gradient; against the oracle's FP64 fit."""
     nres = len(SPEC["resonances"])

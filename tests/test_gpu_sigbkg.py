@@ -1,8 +1,8 @@
 """The signal + background form (an AddPdf of a Voigtian and a threshold leaf over one
-observable: Sec. 4's line shape, config 2) on its own kernel, in both precision modes.
+observable: Sec. 4's line shape, 10^7 events) on its own kernel, in both precision modes.
 
 FP64 mode: per event |log P_gpu - log P_orc| <= 1e-12, NLL 1e-9 relative, gradient 1e-9 of
-its scale (the general tests of config 2 run this kernel too).  Mixed mode (FP32 per-event
+its scale (the general Voigtian + threshold tests run this kernel too).  Mixed mode (FP32 per-event
 arithmetic, FP64 sums and normalisation): its errors against the FP64 oracle are measured
 at the workload's size, stated (tests/parity.py summary) and bounded; a mixed fit
 (FP32 BFGS, then the FP64 refinement) lands within 0.01 sigma of the oracle's fit."""
@@ -105,7 +105,7 @@ def test_fp64_plan_parity_across_line_widths(gf, width):
 
 
 def test_mixed_plan_errors_full_size(gf):
-    """10^7 events (config 2) in GF_MIXED: per-event relative error percentiles, NLL and
+    """10^7 events in GF_MIXED: per-event relative error percentiles, NLL and
     gradient against the FP64 oracle, stated and bounded."""
     x = _data(10_000_000)
     m, free = om.voigt_model()

@@ -181,7 +181,7 @@ SIGT = (0.02, 0.5)
 
 
 def _full_models(gf, nb=48, time=TIME, dens=DENS):
-    """Masses and widths of resonances 0..6 free (resonance 7 fixed, as in config 4), the 16
+    """Masses and widths of resonances 0..6 free (resonance 7 fixed, as in the free-shape Dalitz fit), the 16
     coefficients, tau, x, y, scale and the sigma_t density's b0, b1, b2: 37 free."""
     k = SPEC["kin"]
     d = om.tddp_from_spec(SPEC, nb, time, dens, SIGT)

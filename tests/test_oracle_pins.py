@@ -27,7 +27,7 @@ def _w_mp(z):
     return complex(mpmath.exp(-zz * zz) * mpmath.erfc(-1j * zz))
 
 
-def test_faddeeva_vs_mpmath_config2_region():
+def test_faddeeva_vs_mpmath_voigt_region():
     # Config 2: y = Gamma/(2 sqrt2 sigma) ~ 0.094, Re z in [-14.2, 36.6]; widen both.
     x = RNG.uniform(-16, 40, 300)
     y = RNG.uniform(0.01, 0.3, 300)
@@ -273,13 +273,13 @@ def _fd_check(fun, p, idx, rel=1e-6):
         assert abs(fd - g[k]) <= rel * scale + 1e-7, (k, fd, g[k])
 
 
-def test_gradient_config1_fd():
+def test_gradient_exponential_fd():
     m, free = om.exp_model(-1.3)
     x = synth.exp_events(5000, -1.0)
     _fd_check(lambda p: m.nll([x], p, grad=True), m.p, free)
 
 
-def test_gradient_config2_fd():
+def test_gradient_voigt_fd():
     m, free = om.voigt_model(nbins=2000)
     lo, hi = synth.VOIGT_RANGE
     x = synth.voigt_threshold_events(3000, **synth.VOIGT_TRUTH, lo=lo, hi=hi)
@@ -602,7 +602,7 @@ def test_minimiser_rosenbrock_with_bounds():
     assert r.converged and np.max(np.abs(r.x - 1)) < 1e-5
 
 
-def test_config1_fit_matches_mle_root_and_error():
+def test_exponential_fit_matches_mle_root_and_error():
     m, (a,) = om.exp_model(-2.0)
     x = synth.exp_events(100_000, -1.0)
     mean = x.mean()
