@@ -124,6 +124,7 @@ static void free_dev(gf_ctx* ctx) {
   d.owns_cols = false;
   cudaFree(d.theta);
   cudaFree(d.derived);
+  cudaFree(d.sbtab);
   cudaFree(d.partials);
   cudaFree(d.partials2);
   cudaFree(d.counters);
@@ -1390,6 +1391,8 @@ int ensure_compiled(gf_ctx* ctx) {
     // the kernels read the program from device memory (it is too large for parameters);
     // stream-ordered copy, then wait: the next launch may go to another stream
     DevState& dv = ctx->dev;
+    if (ctx->use_sb && !dv.sbtab)
+      CK(cudaMalloc(&dv.sbtab, sizeof(float4) * kSBTabF4 * (size_t)kSBTabCap));
     if (!dv.prog) CK(cudaMalloc(&dv.prog, sizeof(Program)));
     CK(cudaMemcpyAsync(dv.prog, &P, sizeof(Program), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1527,6 +1530,7 @@ size_t device_bytes_for(const gf_ctx* ctx, int root, int64_t n) {
     if (ctx->precision == GF_MIXED) b += 3 * (size_t)n * 4;
   } else {
     b += col * 4;  // observables (typically 1-2), or centres + contents + variances
+    b += sizeof(float4) * kSBTabF4 * (size_t)kSBTabCap;  // a Voigtian's table of expansions
   }
   return b + (4u << 20);  // work buffers
 }
@@ -1862,6 +1866,16 @@ extern "C" int gf_set_data_device(gf_ctx* ctx, int root, int nobs, const int* ob
 }
 
 // ---- evaluation ----------------------------------------------------------------------------------------------
+// The device copy of this evaluation's table layout (uploaded with theta).
+static const SBTabHdr* sbtab_hdr(gf_ctx* ctx) {
+  return reinterpret_cast<const SBTabHdr*>(ctx->dev.theta + ctx->prog.rec_off);
+}
+// Blocks of the normalisation launch that build the table: the SMs the grids leave, at
+// least 64 (16 k threads: one entry each for most lines)
+static int sbtab_blocks(const gf_ctx* ctx) {
+  return std::max(64, ctx->sm_count - ctx->prog.ngrid_blocks);
+}
+
 static int fill_theta_host(gf_ctx* ctx, const double* theta) {
   DevState& d = ctx->dev;
   const int np = (int)ctx->pars.size();
@@ -1870,6 +1884,7 @@ static int fill_theta_host(gf_ctx* ctx, const double* theta) {
     if (!std::isfinite(theta[k])) return set_error(ctx, GF_EINVAL, "non-finite theta");
     d.h_theta[ctx->free_ids[k]] = theta[k];
   }
+  sbtab_fill(ctx, d.h_theta);
   if (ctx->compiled && ctx->prog.logsum) {
     // the log-sum kernel's leaf records (analytic leaves: leafrec.h), here once instead of
     // in FP64 in every block; doubles, then float pairs (hi rounded, lo the rest rounded)
@@ -1896,6 +1911,8 @@ static int enqueue_uploads(gf_ctx* ctx) {
   int np = (int)ctx->pars.size();
   if (ctx->compiled && ctx->prog.logsum)
     np = ctx->prog.rec_off + 2 * kLogLeaf * kLeafRec;  // with the leaf records
+  else
+    np = theta_all_size(ctx);  // with the table's layout (signal + background form)
   if (np > 0)
     CK(cudaMemcpyAsync(d.theta, d.h_theta, sizeof(double) * np, cudaMemcpyHostToDevice,
                        ctx->stream));
@@ -2069,8 +2086,10 @@ static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool capt
   } else {
     const WeidCoef& W = weideman();
     if (ctx->has_grid) {
+      const bool tab = ctx->use_sb && d.sbtab;
       CK(launch_norm_1d(ctx->prog, d.prog, W, d.theta, d.partials2, d.counters + 1, d.derived,
-                        ctx->stream));
+                        tab ? sbtab_hdr(ctx) : nullptr, tab ? d.sbtab : nullptr,
+                        sbtab_blocks(ctx), ctx->stream));
       (*launches)++;
       const int rc = enqueue_convs(ctx, launches);
       if (rc) return rc;
@@ -2082,7 +2101,8 @@ static int enqueue_steady(gf_ctx* ctx, bool grad, bool fp64, int mode, bool capt
       const bool mixed = ctx->precision == GF_MIXED && !fp64;
       CK(launch_sigbkg(ctx->sb, W, d.prog, d.cols[ctx->prog.ins[ctx->prog.mix_leaf[0]].obs], d.n,
                        d.derived, d.partials, d.counters, d.result, nullptr, nullptr, grad, mixed,
-                       mixed ? d.nblocks_mixed : d.nblocks, ctx->stream));
+                       mixed ? d.nblocks_mixed : d.nblocks, sbtab_hdr(ctx), d.sbtab,
+                       ctx->stream));
     } else {
       CK(launch_events_1d(ctx->prog, d.prog, W, cols, d.n, d.theta, d.derived, d.partials,
                           d.counters, d.result, nullptr, nullptr, grad, false,
@@ -2262,6 +2282,29 @@ int evaluate_finish(gf_ctx* ctx, double* nll, double* grad, bool grad_wanted) {
   return GF_OK;
 }
 
+void sbtab_fill(const gf_ctx* ctx, double* theta_all) {
+  if (!ctx->compiled || !ctx->use_sb) return;
+  const Program& P = ctx->prog;
+  const DevState& d = ctx->dev;
+  SBTabHdr H{};
+  // sorted events with at least 8 per thread of both plans' launches go in chunks that
+  // expand w themselves: no table then
+  const int64_t t_max = std::max<int64_t>((int64_t)d.nblocks * sigbkg_threads(false),
+                                          (int64_t)d.nblocks_mixed * sigbkg_threads(true));
+  if (!(P.sorted && d.n >= 8 * t_max)) {
+    const LeafDesc& L = P.leaf[ctx->sb.slot_v];
+    sbtab_layout(theta_all[L.par[0]], theta_all[L.par[1]], theta_all[L.par[2]], L.lo, L.hi, H);
+  }
+  std::memcpy(theta_all + P.rec_off, &H, sizeof(H));
+}
+
+int theta_all_size(const gf_ctx* ctx) {
+  const int np = (int)ctx->pars.size();
+  if (ctx->compiled && ctx->use_sb)
+    return std::max(np, ctx->prog.rec_off + (int)((sizeof(SBTabHdr) + 7) / 8));
+  return np;
+}
+
 void fill_theta_all(const gf_ctx* ctx, const double* theta, double* out) {
   const int np = (int)ctx->pars.size();
   for (int i = 0; i < np; ++i) out[i] = ctx->pars[i].value;
@@ -2286,6 +2329,7 @@ int tick_prepare(gf_ctx* ctx) {
     F.counter_ev = d.counters;
     F.counter_norm = d.counters + 1;
     F.analytic_only = ctx->has_grid ? 0 : 1;
+    F.sbtab = ctx->use_sb ? d.sbtab : nullptr;
     // the signal + background form also gets its own event descriptor, after the Fit1D
     // (whose program the normalisation tick uses)
     const size_t off = round_up(sizeof(F), 256);
@@ -2300,6 +2344,8 @@ int tick_prepare(gf_ctx* ctx) {
       S.partials = d.partials;
       S.counter = d.counters;
       S.sorted = ctx->prog.sorted;
+      S.sbtab = d.sbtab;
+      S.rec_off = ctx->prog.rec_off;
       CK(cudaMemcpyAsync(static_cast<char*>(d.tick_desc) + off, &S, sizeof(S),
                          cudaMemcpyHostToDevice, ctx->stream));
     }
@@ -2418,8 +2464,10 @@ static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host)
   } else {
     const WeidCoef& W = weideman();
     if (ctx->has_grid) {
+      const bool tab = ctx->use_sb && d.sbtab;
       cudaError_t e = launch_norm_1d(ctx->prog, d.prog, W, d.theta, d.partials2, d.counters + 1,
-                                     d.derived, ctx->stream);
+                                     d.derived, tab ? sbtab_hdr(ctx) : nullptr,
+                                     tab ? d.sbtab : nullptr, sbtab_blocks(ctx), ctx->stream);
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "launch_norm_1d");
       if (rc == GF_OK) rc = enqueue_convs(ctx, nullptr);
     }
@@ -2432,7 +2480,7 @@ static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host)
                                     d.sorted ? d.perm : nullptr, false,
                                     ctx->precision == GF_MIXED,
                                     ctx->precision == GF_MIXED ? d.nblocks_mixed : d.nblocks,
-                                    ctx->stream);
+                                    sbtab_hdr(ctx), d.sbtab, ctx->stream);
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "launch_sigbkg");
     } else if (rc == GF_OK) {
       cudaError_t e = launch_events_1d(ctx->prog, d.prog, W, cols, d.n, d.theta, d.derived, d.partials,

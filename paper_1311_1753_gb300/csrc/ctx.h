@@ -47,6 +47,7 @@ struct DevState {
   double* theta = nullptr;            // all parameters (device)
   Program* prog = nullptr;            // compiled 1D program (device)
   double* derived = nullptr;
+  float4* sbtab = nullptr;            // signal + background form: the table of w expansions
   double* partials = nullptr;
   double* partials2 = nullptr;
   unsigned* counters = nullptr;       // [0] events, [1] norm
@@ -185,6 +186,10 @@ size_t device_bytes_for(const gf_ctx* ctx, int root, int64_t n);
 // evaluate_finish.
 int tick_prepare(gf_ctx* ctx);
 void fill_theta_all(const gf_ctx* ctx, const double* theta, double* out);
+// the signal + background form: this theta_all's table layout (SBTabHdr) at
+// theta_all + prog.rec_off; theta_all_size: the doubles a theta_all buffer then needs
+void sbtab_fill(const gf_ctx* ctx, double* theta_all);
+int theta_all_size(const gf_ctx* ctx);
 int tick_finish(gf_ctx* ctx, const double* res, double* nll, double* grad);
 int nfree(const gf_ctx* ctx);
 const WeidCoef& weideman();

@@ -94,7 +94,8 @@ struct Program {
   // evaluated directly, without the stack machine.  1: this form, 0: not.
   int32_t logsum;
   // log-sum programs: the leaves' records (kLogLeaf x kLeafRec doubles), then the same as
-  // float pairs, computed on the host with theta and uploaded behind it at theta + rec_off
+  // float pairs, computed on the host with theta and uploaded behind it at theta + rec_off;
+  // the signal + background form: its table layout (SBTabHdr) there
   int32_t rec_off;
   // binned data (the events are bin centres): the metric over bins and its inputs.
   // binned = 0: unbinned events, metric -sum log P.
@@ -123,6 +124,21 @@ struct SigBkgDesc {
   int32_t fsgn_v, fsgn_t;    // +1: coefficient = f; -1: 1 - f
   int32_t nfree;
 };
+
+// The table of expansions of w along the line Im z = y of one evaluation (the signal +
+// background kernel's Voigtian): entry j holds the degree-5 Taylor coefficients of w
+// around z_j + i y, z_j the middle of cell j of Re z.  Cells: nneg logarithmic cells below
+// -zc, ncore cells of width h from a, then logarithmic cells above zc (ratio e^lr), so
+// that every cell's half-width stays within the expansion's validated limit.  The host
+// lays the table out from theta (ntab = 0: no table this evaluation) and uploads this
+// header with theta; the normalisation launch builds the entries.
+struct SBTabHdr {
+  int32_t ntab, nneg, ncore, pad0;
+  float a, ih, h, zc, izc, ilr, lr, pad1;
+  double mu, c1, ic1, y;  // Re z = (x - mu) c1, ic1 = 1/c1
+};
+constexpr int kSBTabCap = 1 << 15;  // entries, at most (2.6 MB)
+constexpr int kSBTabF4 = 5;         // float4 per entry
 
 // One grid-normalised node (MappedPdf, CompositePdf): N = h sum_b F(lo + (b + 1/2) h) over
 // nbins midpoints of the observable, F the node's body (sub-program), with dN over the
@@ -221,6 +237,7 @@ struct Fit1D {
   double* partials_norm;
   unsigned* counter_ev;
   unsigned* counter_norm;
+  float4* sbtab;  // signal + background form: its table of w expansions (else nullptr)
   int analytic_only;
   int pad;
 };
@@ -248,8 +265,9 @@ struct FitSB {
   double* derived;
   double* partials;
   unsigned* counter;
+  const float4* sbtab;  // the table of w expansions (layout at theta + rec_off)
   int32_t sorted;
-  int32_t pad;
+  int32_t rec_off;
 };
 
 struct TickItem {

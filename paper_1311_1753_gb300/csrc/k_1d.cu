@@ -16,6 +16,7 @@
 #include "gf_internal.h"
 #include "launch.h"
 #include "leafrec.h"
+#include "sbtab.cuh"
 
 namespace gfi {
 
@@ -413,12 +414,23 @@ __device__ __forceinline__ void load_program(const Program* __restrict__ src, Pr
   __syncthreads();
 }
 
+// The normalisation launch: blocks 0 .. nnorm - 1 the grids, the rest (if tab) the entries
+// of the signal + background kernel's table of w expansions (independent of the grids).
 __global__ void __launch_bounds__(kThreads) k_norm_1d(const Program* __restrict__ Pg,
                                                       const __grid_constant__ WeidCoef W,
                                                       const double* __restrict__ theta,
                                                       double* __restrict__ partials,
                                                       unsigned* __restrict__ counter,
-                                                      double* __restrict__ derived) {
+                                                      double* __restrict__ derived, int nnorm,
+                                                      const SBTabHdr* __restrict__ hdr,
+                                                      float4* __restrict__ tab) {
+  if ((int)blockIdx.x >= nnorm) {
+    const int nt = ((int)gridDim.x - nnorm) * blockDim.x;
+    const int ntab = hdr->ntab;
+    for (int j = ((int)blockIdx.x - nnorm) * blockDim.x + threadIdx.x; j < ntab; j += nt)
+      sbtab_build(j, *hdr, W, tab);
+    return;
+  }
   __shared__ Program P;
   __shared__ double red[32];
   __shared__ int last;
@@ -426,7 +438,7 @@ __global__ void __launch_bounds__(kThreads) k_norm_1d(const Program* __restrict_
   __shared__ ShapeK shk;
   load_df_tables();
   load_program(Pg, P);
-  norm_1d_block(P, W, theta, partials, counter, derived, blockIdx.x, gridDim.x, red, &last, sums,
+  norm_1d_block(P, W, theta, partials, counter, derived, blockIdx.x, nnorm, red, &last, sums,
                 &shk);
 }
 
@@ -1522,8 +1534,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_tick_norm_1d(const TickItem* __
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const TickItem& ti = tick_item(items, nfits, it, cur, Ps);
     const Fit1D* F = static_cast<const Fit1D*>(ti.fit);
-    norm_1d_block(Ps, W, ti.theta, F->partials_norm, F->counter_norm, F->derived,
-                  it - ti.item0, ti.nitems, red, &last, sums, &shk);
+    const int vb = it - ti.item0, ng = Ps.ngrid_blocks;
+    if (vb >= ng) {  // the fit's table of w expansions (items beyond its grid blocks)
+      const SBTabHdr& H = *reinterpret_cast<const SBTabHdr*>(ti.theta + Ps.rec_off);
+      const int nt = (ti.nitems - ng) * blockDim.x;
+      for (int j = (vb - ng) * blockDim.x + threadIdx.x; j < H.ntab; j += nt)
+        sbtab_build(j, H, W, F->sbtab);
+    } else {
+      norm_1d_block(Ps, W, ti.theta, F->partials_norm, F->counter_norm, F->derived, vb, ng, red,
+                    &last, sums, &shk);
+    }
     __syncthreads();
   }
 }
@@ -1607,9 +1627,12 @@ cudaError_t launch_check_range(const Cols& cols, int nobs, int64_t n, const doub
 // ---- host launchers ---------------------------------------------------------------------------
 cudaError_t launch_norm_1d(const Program& P, const Program* prog, const WeidCoef& W,
                            const double* theta, double* partials, unsigned* counter,
-                           double* derived, cudaStream_t st) {
+                           double* derived, const SBTabHdr* tab_hdr, float4* tab,
+                           int tab_blocks, cudaStream_t st) {
   const int nb = P.ngrid_blocks > 0 ? P.ngrid_blocks : 1;
-  k_norm_1d<<<nb, kThreads, 0, st>>>(prog, W, theta, partials, counter, derived);
+  const int nt = tab ? tab_blocks : 0;
+  k_norm_1d<<<nb + nt, kThreads, 0, st>>>(prog, W, theta, partials, counter, derived, nb,
+                                           tab_hdr, tab);
   return cudaGetLastError();
 }
 

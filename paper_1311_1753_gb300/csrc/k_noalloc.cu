@@ -329,7 +329,8 @@ extern "C" int gf_nll_noalloc(gf_ctx* ctx, int root, int nobs, const int* obs, i
   }
   const WeidCoef& W = weideman();
   cudaError_t e = cudaSuccess;
-  if (has_grid) e = launch_norm_1d(P, d_prog, W, d_theta, d_pnorm, d_cnt_norm, d_derived, st);
+  if (has_grid) e = launch_norm_1d(P, d_prog, W, d_theta, d_pnorm, d_cnt_norm, d_derived, nullptr, nullptr, 0,
+                                 st);
   Cols cols{};
   for (int k = 0; k < nobs; ++k) cols.c[k] = dev_cols[k];
   if (e == cudaSuccess)

@@ -17,19 +17,24 @@
 // of the P_i with its binary exponent split off after every factor, whose logarithm is
 // taken once per chunk of events.
 //
+// w(z) along the line Im z = y: every event reads its degree-5 Taylor expansion from the
+// evaluation's table (sbtab.cuh), built by the normalisation launch at the middles of
+// cells of Re z narrow enough for the expansion's validated limits, in any event order;
+// the entry is reloaded only when an event's cell differs from the previous one's (sorted
+// events in chunks mostly share one).  Without a table (a line too narrow for its cells
+// to fit, y < 1e-6) w is expanded once per chunk of sorted events around the chunk's
+// middle event, or evaluated per event by the Weideman series.
+//
 // Two arithmetics:
 //  FP64 plan   double-float pairs on the FP32 pipe (as k_1d.cu): exact FP64 differences
-//              x - mu, x - x0; w by the Weideman series, or (events sorted by x) once per
-//              chunk of 24 events and expanded to degree 5 around the chunk's middle event
-//              (the tail of the expansion, k >= 2, in float); events whose P leaves
-//              [2^-80, 2^125) are re-evaluated in FP64.
+//              x - mu, x - x0; the expansion's t_0, t_1 as pairs, t_2 .. t_5 in float;
+//              events whose P leaves [2^-80, 2^125) are re-evaluated in FP64.
 //  mixed plan  per-event arithmetic in FP32 (GF_MIXED): data enter by a bit split and exact
-//              float differences; w expanded to degree 4 in float around the middle event
-//              of each chunk of 96 (the expansion's coefficients from the FP64-accurate
-//              series), or the Weideman series in float for unsorted data or wide chunks;
-//              the chunk's moment sums in float, folded into pairs at the chunk's end; the
-//              log-sum, the block and cross-block sums, the normalisation integrals
-//              (k_norm_1d) and the gradient's combination in FP64-accurate arithmetic.
+//              float differences (d = (x - x0) c1 from the cell middle's x0); the expansion
+//              in float (its coefficients rounded from the FP64-accurate ones); the chunk's
+//              moment sums in float, folded into pairs at the chunk's end; the log-sum, the
+//              block and cross-block sums, the normalisation integrals (k_norm_1d) and the
+//              gradient's combination in FP64-accurate arithmetic.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -37,6 +42,7 @@
 #include "devutil.cuh"
 #include "gf_internal.h"
 #include "launch.h"
+#include "sbtab.cuh"
 
 namespace gfi {
 namespace {
@@ -128,58 +134,6 @@ struct Lazy {
   __device__ __forceinline__ F2 get() const { return fast_two_sum(hi, lo); }
 };
 
-// ---- expansion of w around a chunk's middle event ------------------------------------------
-// t_k = w^(k)(z0)/k! from w' = -2 z w + 2i/sqrt(pi): t_1 = -2 z0 t_0 + 2i/sqrt(pi),
-// t_{k+1} = -2 (z0 t_k + t_{k-1})/(k + 1), in pairs (the recurrence cancels at large |z0|).
-// For real d = Re z - Re z0 the real and imaginary parts of sum t_k d^k separate.
-template <int DEG>
-__device__ __forceinline__ void tay_coefs(F2 zr, F2 y, const WeidCoef& W, F2* tr, F2* ti) {
-  faddeeva_f2(zr, y, W, tr[0], ti[0]);
-  F2 ar = df_sub(df_mul(zr, tr[0]), df_mul(y, ti[0]));
-  F2 ai = df_add(df_mul(zr, ti[0]), df_mul(y, tr[0]));
-  tr[1] = df_mul_f(ar, -2.f);
-  ti[1] = df_add(df_mul_f(ai, -2.f), DFC(kTwoInvSqrtPi));
-#pragma unroll
-  for (int k = 1; k < DEG; ++k) {
-    ar = df_sub(df_mul(zr, tr[k]), df_mul(y, ti[k]));
-    ai = df_add(df_mul(zr, ti[k]), df_mul(y, tr[k]));
-    const float s = -2.f / (float)(k + 1);  // exact for k + 1 in {2, 4}; else one rounding
-    const F2 sc = (k + 1 == 3) ? F2(DFC(-2.0 / 3)) : (k + 1 == 5) ? F2(DFC(-2.0 / 5))
-                                                                  : F2{s, 0.f};
-    tr[k + 1] = df_mul(df_add(ar, tr[k - 1]), sc);
-    ti[k + 1] = df_mul(df_add(ai, ti[k - 1]), sc);
-  }
-}
-
-// FP64 plan: t_0, t_1 as pairs, t_2 .. t_5 in float (the chunk width limits kSBLim64* keep
-// their rounding below 2e-13 of Re w).
-struct TayP {
-  F2 z0, t0r, t0i, t1r, t1i;
-  float qr[4], qi[4];
-};
-__device__ __forceinline__ void tayp_build(TayP& T, F2 zr, F2 y, const WeidCoef& W) {
-  F2 tr[6], ti[6];
-  tay_coefs<5>(zr, y, W, tr, ti);
-  T.z0 = zr;
-  T.t0r = tr[0];
-  T.t0i = ti[0];
-  T.t1r = tr[1];
-  T.t1i = ti[1];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    T.qr[k] = __fadd_rn(tr[k + 2].hi, tr[k + 2].lo);
-    T.qi[k] = __fadd_rn(ti[k + 2].hi, ti[k + 2].lo);
-  }
-}
-__device__ __forceinline__ void tayp_eval(const TayP& T, F2 zr, F2& wr, F2& wi) {
-  const F2 dd = df_sub(zr, T.z0);
-  const float d = dd.hi;
-  const float qr = __fmaf_rn(__fmaf_rn(__fmaf_rn(T.qr[3], d, T.qr[2]), d, T.qr[1]), d, T.qr[0]);
-  const float qi = __fmaf_rn(__fmaf_rn(__fmaf_rn(T.qi[3], d, T.qi[2]), d, T.qi[1]), d, T.qi[0]);
-  wr = df_add(T.t0r, df_mul(dd, df_add_f(T.t1r, __fmul_rn(d, qr))));
-  wi = df_add(T.t0i, df_mul(dd, df_add_f(T.t1i, __fmul_rn(d, qi))));
-}
-
 // Weideman's series in float (the mixed plan's unsorted events and wide chunks): the same
 // coefficients and rational map as faddeeva_f2, every step in FP32.
 __device__ __forceinline__ void faddeeva_f32(float x, float y, const WeidCoef& W, float& wr,
@@ -222,6 +176,7 @@ struct SBConst {
   double ref, lref, ca, cb;
   int half;  // p == 1/2 and no gradient in p: sqrt(t) instead of exp(p log t)
 };
+template <bool MIXED>
 __device__ __forceinline__ void sb_consts(const SigBkgDesc& D, const double* __restrict__ der,
                                           bool grad, SBConst& K) {
   const double* rv = der + D.slot_v * kLeafRec;
@@ -237,6 +192,7 @@ __device__ __forceinline__ void sb_consts(const SigBkgDesc& D, const double* __r
   K.cv = der[kMaxLeaf * kLeafRec + D.cslot_v];
   K.ct = der[kMaxLeaf * kLeafRec + D.cslot_t];
   K.half = (K.pw == 0.5 && !(grad && D.gt[1] >= 0)) ? 1 : 0;
+  if (!MIXED) return;  // the split below is the mixed plan's
   const double kv = K.cv * K.c3v, kt = K.ct * K.c3t;
   double ref = fabs(kv) >= fabs(kt) ? kv : kt;
   K.ca = ref != 0.0 ? kv / ref : 0.0;
@@ -323,6 +279,8 @@ struct SBShared {
   // constants used only at chunk boundaries, as pairs, out of the registers
   float mh[NM][MIXED ? NT : 1], ml[NM][MIXED ? NT : 1];
   F2 mu2, yp, sv, st, lref;
+  F2 kp[8];    // the per-event constants as pairs (warp 0 converts them, one per lane)
+  SBTabF tf;   // the table of w expansions (tf.ntab = 0: none)
   WeidCoef W;  // the series coefficients, read by every thread (and the out-of-line paths)
   double red[(NT / 32) * kSBMom];
   double fin[kSBMom];
@@ -351,17 +309,39 @@ __device__ __forceinline__ void sigbkg_block(
     const SigBkgDesc& D, const WeidCoef& Wg, const int sorted, const double* __restrict__ xcol,
     const int64_t n, const double* __restrict__ der, double* __restrict__ partials,
     unsigned* __restrict__ counter, double* __restrict__ result, double* __restrict__ out_logp,
-    const int32_t* __restrict__ perm, const int vb, const int vgrid, SBShared<MIXED>& sh) {
+    const int32_t* __restrict__ perm, const SBTabHdr* __restrict__ tabh,
+    const float4* __restrict__ tab, const int vb, const int vgrid, SBShared<MIXED>& sh) {
   const int tid = threadIdx.x;
   if (tid == 0) {
-    sb_consts(D, der, G, sh.K);
-    if (MIXED) {
-      SBConst& k = sh.K;
-      sh.mu2 = df_split(k.mu);
-      sh.yp = df_from(k.y);
-      sh.sv = df_from(1.0 / k.ref);
-      sh.st = df_from(k.c3t / k.ref);
-      sh.lref = df_from(k.lref);
+    sb_consts<MIXED>(D, der, G, sh.K);
+    sh.tf = tab ? sbtab_f(*tabh) : SBTabF{0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f};
+  }
+  // the constants as pairs, one per lane of warp 0 (their FP64 conversions and divisions
+  // side by side instead of in a chain on one thread or repeated by every thread)
+  if (tid < 32) {
+    __syncwarp();
+    const SBConst& k = sh.K;
+    if constexpr (!MIXED) {
+      if (tid < 8) {
+        const double v = tid == 0 ? k.c1 : tid == 1 ? k.y : tid == 2 ? k.c3v : tid == 3 ? k.pw
+                       : tid == 4 ? k.cc : tid == 5 ? k.c3t : tid == 6 ? k.cv : k.ct;
+        sh.kp[tid] = df_from(v);
+      }
+    } else {
+      switch (tid) {
+        case 0: sh.mu2 = df_split(k.mu); break;
+        case 1: sh.yp = df_from(k.y); break;
+        case 2: sh.sv = df_from(1.0 / k.ref); break;
+        case 3: sh.st = df_from(k.c3t / k.ref); break;
+        case 4: sh.lref = df_from(k.lref); break;
+        case 5: sh.kp[0] = df_from(k.c1); break;
+        case 6: sh.kp[1] = df_from(k.cc); break;
+        case 7: sh.kp[2] = df_from(k.pw); break;
+        case 8: sh.kp[3] = df_from(k.ca); break;
+        case 9: sh.kp[4] = df_from(k.cb); break;
+        case 10: sh.kp[5] = df_split(k.x0); break;
+        default: break;
+      }
     }
   }
   if constexpr (MIXED && G)
@@ -406,18 +386,34 @@ __device__ __forceinline__ void sigbkg_block(
   const bool chunked = sorted && n >= 8 * nthreads;
   (void)g;
 
+  // the table of w expansions for events in any order: each event's expansion by its cell
+  // of Re z, reloaded when the cell changes.  Sorted chunks expand w themselves (one
+  // Weideman series and recurrence per chunk costs less than a cell lookup per event).
+  const bool use_tab = sh.tf.ntab > 0 && !chunked;
+  int kcur = -1;
+
   if constexpr (!MIXED) {
     // ---------------- FP64 plan: pairs ----------------
-    const F2 c1 = df_from(K.c1), y = df_from(K.y), c3v = df_from(K.c3v);
-    const F2 pw = df_from(K.pw), cc = df_from(K.cc), c3t = df_from(K.c3t);
-    const F2 cv = df_from(K.cv), ct = df_from(K.ct);
+    const F2 c1 = sh.kp[0], y = sh.kp[1], c3v = sh.kp[2];
+    const F2 pw = sh.kp[3], cc = sh.kp[4], c3t = sh.kp[5];
+    const F2 cv = sh.kp[6], ct = sh.kp[7];
     ProdF2 prod;
     TayP T;
     auto one = [&](int64_t i, double xi, bool tay) {
       const F2 zr = df_mul(df_split(xi - K.mu), c1);
       F2 wr, wi;
-      if (tay) tayp_eval(T, zr, wr, wi);
-      else faddeeva_f2(zr, y, W, wr, wi);
+      if (use_tab) {
+        const int kc = sbtab_index(zr.hi, sh.tf);
+        if (kc != kcur) {
+          sbtab_load(tab, kc, T);
+          kcur = kc;
+        }
+        tayp_eval(T, zr, wr, wi);
+      } else if (tay) {
+        tayp_eval(T, zr, wr, wi);
+      } else {
+        faddeeva_f2(zr, y, W, wr, wi);
+      }
       const double td = xi - K.x0;
       F2 B = {0.f, 0.f}, t = {0.f, 0.f}, lt = {0.f, 0.f};
       if (td > 0.0) {
@@ -523,26 +519,29 @@ __device__ __forceinline__ void sigbkg_block(
     }
   } else {
     // ---------------- mixed plan: FP32 per event ----------------
-    const F2 x02 = df_split(K.x0);
-    const float y = (float)K.y;
+    const F2 x02 = sh.kp[5];
+    const float y = sh.yp.hi;
     // constants that multiply per-event values as pairs (one extra FMA each): the float
     // result then carries per-event rounding only
-    const F2 c1p = df_from(K.c1), ccp = df_from(K.cc), pwp = df_from(K.pw);
-    const F2 cap = df_from(K.ca), cbp = df_from(K.cb);
+    const F2 c1p = sh.kp[0], ccp = sh.kp[1], pwp = sh.kp[2];
+    const F2 cap = sh.kp[3], cbp = sh.kp[4];
     auto kmul = [](float a, F2 c) { return __fmaf_rn(a, c.hi, __fmul_rn(a, c.lo)); };
     ProdF prod;
     int pcount = 0;  // events in the running product
     float cm[kSBMom - 1];
 #pragma unroll
     for (int k = 0; k < kSBMom - 1; ++k) cm[k] = 0.f;
-    // one event: x as a pair, zr = Re z, dz = Re z - Re z0 (tay: T holds the degree-4
-    // expansion's coefficients, re then im; otherwise the float series)
-    float T[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // one event: x as a pair, zr = Re z, dz = Re z - Re z0 (tay: T holds the expansion's
+    // coefficients to degree 5, re then im (a chunk's own expansion: degree 4, the table's:
+    // 5); otherwise the float series)
+    float T[12] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     auto one = [&](int64_t i, double xi, F2 xs, float zr, float dz, bool tay) {
       float wr, wi;
       if (tay) {
-        wr = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(T[4], dz, T[3]), dz, T[2]), dz, T[1]), dz, T[0]);
-        wi = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(T[9], dz, T[8]), dz, T[7]), dz, T[6]), dz, T[5]);
+        wr = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(T[5], dz, T[4]), dz, T[3]), dz, T[2]), dz,
+                                 T[1]), dz, T[0]);
+        wi = __fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(__fmaf_rn(T[11], dz, T[10]), dz, T[9]), dz, T[8]),
+                                 dz, T[7]), dz, T[6]);
       } else {
         w_direct_f32(zr, y, Ws, wr, wi);
       }
@@ -608,14 +607,48 @@ __device__ __forceinline__ void sigbkg_block(
         }
       }
     };
+    // the current expansion's middle: x as a pair, Re z in float
+    F2 xms = {0.f, 0.f};
+    float z0f = 0.f;
+    auto dzof = [&](F2 xs) {
+      return kmul(__fadd_rn(__fsub_rn(xs.hi, xms.hi), __fsub_rn(xs.lo, xms.lo)), c1p);
+    };
+    // table entry kc as the float expansion around its cell's middle
+    auto mload = [&](int kc) {
+      const float4* e = tab + (size_t)kc * kSBTabF4;
+      const float4 a = __ldg(e), b = __ldg(e + 1), c = __ldg(e + 2), d = __ldg(e + 3),
+                   f = __ldg(e + 4);
+      z0f = __fadd_rn(a.x, a.y);
+      T[0] = __fadd_rn(a.z, a.w);
+      T[1] = __fadd_rn(b.z, b.w);
+      T[2] = c.z;
+      T[3] = c.w;
+      T[4] = d.x;
+      T[5] = d.y;
+      T[6] = __fadd_rn(b.x, b.y);
+      T[7] = __fadd_rn(c.x, c.y);
+      T[8] = d.z;
+      T[9] = d.w;
+      T[10] = f.x;
+      T[11] = f.y;
+      xms = F2{f.z, f.w};
+      kcur = kc;
+    };
+    if (use_tab) mload(0);
+    // an event's dz in the table: z0f + dz approximates Re z from any entry, and picks the
+    // cell whose entry then serves the event
+    auto tdz = [&](F2 xs) {
+      float dz = dzof(xs);
+      const int kc = sbtab_index(__fadd_rn(z0f, dz), sh.tf);
+      if (kc != kcur) {
+        mload(kc);
+        dz = dzof(xs);
+      }
+      return dz;
+    };
     if (chunked) {
       // chunks distributed over the threads as in the FP64 plan
       const int64_t gc = (int64_t)tid * vgrid + vb;
-      F2 xms = {0.f, 0.f};
-      float z0f = 0.f;
-      auto dzof = [&](F2 xs) {
-        return kmul(__fadd_rn(__fsub_rn(xs.hi, xms.hi), __fsub_rn(xs.lo, xms.lo)), c1p);
-      };
       // expansion (degree 4, float coefficients from the pair series) for events a ..
       // a + c - 1 when they lie close enough to the middle one
       auto expand = [&](int64_t a, int c) {
@@ -633,7 +666,7 @@ __device__ __forceinline__ void sigbkg_block(
 #pragma unroll
           for (int k = 0; k < 5; ++k) {
             T[k] = __fadd_rn(tr[k].hi, tr[k].lo);
-            T[5 + k] = __fadd_rn(ti[k].hi, ti[k].lo);
+            T[6 + k] = __fadd_rn(ti[k].hi, ti[k].lo);
           }
         }
         return ok;
@@ -647,8 +680,8 @@ __device__ __forceinline__ void sigbkg_block(
           for (int j = 0; j < 4; ++j)
             if (k + j < c) {
               const F2 xs = df_split(xv[j]);
-              const float dz = dzof(xs);
               if (tay) {
+                const float dz = dzof(xs);
                 one(a + k + j, xv[j], xs, __fadd_rn(z0f, dz), dz, true);
               } else {
                 const F2 mu2 = sh.mu2;
@@ -678,9 +711,15 @@ __device__ __forceinline__ void sigbkg_block(
       for (int64_t i = g; i < n; i += nthreads) {
         const double xi = __ldcs(xcol + i);
         const F2 xs = df_split(xi);
-        const F2 mu2 = sh.mu2;
-        const float zr = kmul(__fadd_rn(__fsub_rn(xs.hi, mu2.hi), __fsub_rn(xs.lo, mu2.lo)), c1p);
-        one(i, xi, xs, zr, 0.f, false);
+        if (use_tab) {
+          const float dz = tdz(xs);
+          one(i, xi, xs, __fadd_rn(z0f, dz), dz, true);
+        } else {
+          const F2 mu2 = sh.mu2;
+          const float zr =
+              kmul(__fadd_rn(__fsub_rn(xs.hi, mu2.hi), __fsub_rn(xs.lo, mu2.lo)), c1p);
+          one(i, xi, xs, zr, 0.f, false);
+        }
         if (++since == kSBChunk32) {
           flush();
           since = 0;
@@ -716,11 +755,12 @@ __global__ void __launch_bounds__(sb_threads<MIXED>(), sb_min_blocks<MIXED>()) k
     const Program* __restrict__ prog, const double* __restrict__ xcol, const int64_t n,
     const double* __restrict__ der, double* __restrict__ partials,
     unsigned* __restrict__ counter, double* __restrict__ result, double* __restrict__ out_logp,
-    const int32_t* __restrict__ perm) {
+    const int32_t* __restrict__ perm, const SBTabHdr* __restrict__ tabh,
+    const float4* __restrict__ tab) {
   __shared__ SBShared<MIXED> sh;
   load_df_tables();  // visible after the block body's first barrier
   sigbkg_block<G, MIXED, STORE>(D, W, prog->sorted, xcol, n, der, partials, counter, result,
-                                out_logp, perm, blockIdx.x, gridDim.x, sh);
+                                out_logp, perm, tabh, tab, blockIdx.x, gridDim.x, sh);
 }
 
 // The fit server's batched tick: every waiting signal + background fit in one persistent
@@ -738,8 +778,9 @@ __global__ void __launch_bounds__(sb_threads<MIXED>(), sb_min_blocks<MIXED>())
     const TickItem& ti = items[f];
     const FitSB* F = static_cast<const FitSB*>(ti.fit);
     sigbkg_block<true, MIXED, false>(F->D, W, F->sorted, F->x, F->n, F->derived, F->partials,
-                                     F->counter, ti.result, nullptr, nullptr, it - ti.item0,
-                                     ti.nitems, sh);
+                                     F->counter, ti.result, nullptr, nullptr,
+                                     reinterpret_cast<const SBTabHdr*>(ti.theta + F->rec_off),
+                                     F->sbtab, it - ti.item0, ti.nitems, sh);
     __syncthreads();
   }
 }
@@ -771,32 +812,68 @@ cudaError_t launch_sigbkg(const SigBkgDesc& D, const WeidCoef& W, const Program*
                           const double* x, int64_t n,
                           const double* derived, double* partials, unsigned* counter,
                           double* result, double* out_logp, const int32_t* perm, bool grad,
-                          bool mixed, int nblocks, cudaStream_t st) {
+                          bool mixed, int nblocks, const SBTabHdr* tab_hdr, const float4* tab,
+                          cudaStream_t st) {
   if (nblocks < 1) nblocks = 1;
   const int NT = sigbkg_threads(mixed);
+  auto go = [&](auto kern, double* lp, const int32_t* pm) {
+    kern<<<nblocks, NT, 0, st>>>(D, W, prog, x, n, derived, partials, counter, result, lp, pm,
+                                 tab_hdr, tab);
+  };
   if (out_logp) {
-    if (mixed)
-      k_sigbkg<false, true, true><<<nblocks, NT, 0, st>>>(D, W, prog, x, n, derived, partials,
-                                                                  counter, result, out_logp, perm);
-    else
-      k_sigbkg<false, false, true><<<nblocks, NT, 0, st>>>(D, W, prog, x, n, derived, partials,
-                                                                   counter, result, out_logp, perm);
+    if (mixed) go(k_sigbkg<false, true, true>, out_logp, perm);
+    else go(k_sigbkg<false, false, true>, out_logp, perm);
   } else if (mixed) {
-    if (grad)
-      k_sigbkg<true, true, false><<<nblocks, NT, 0, st>>>(D, W, prog, x, n, derived, partials,
-                                                                  counter, result, nullptr, nullptr);
-    else
-      k_sigbkg<false, true, false><<<nblocks, NT, 0, st>>>(D, W, prog, x, n, derived, partials,
-                                                                   counter, result, nullptr, nullptr);
+    if (grad) go(k_sigbkg<true, true, false>, nullptr, nullptr);
+    else go(k_sigbkg<false, true, false>, nullptr, nullptr);
   } else {
-    if (grad)
-      k_sigbkg<true, false, false><<<nblocks, NT, 0, st>>>(D, W, prog, x, n, derived, partials,
-                                                                   counter, result, nullptr, nullptr);
-    else
-      k_sigbkg<false, false, false><<<nblocks, NT, 0, st>>>(D, W, prog, x, n, derived, partials,
-                                                                    counter, result, nullptr, nullptr);
+    if (grad) go(k_sigbkg<true, false, false>, nullptr, nullptr);
+    else go(k_sigbkg<false, false, false>, nullptr, nullptr);
   }
   return cudaGetLastError();
+}
+
+// Layout of the table of w expansions for a Voigtian (mu, sigma, Gamma) over [lo, hi]:
+// Re z = (x - mu) c1 with c1 = 1/(sigma sqrt2) and Im z = y = Gamma c1 / 2 as the leaf
+// record forms them.  Core cells of width 2 x 0.96 of the FP64 plan's absolute limit
+// (kSBLim64 or, y >= kSBLim64WY, kSBLim64W); for y >= 1e-6 logarithmic cells beyond
+// |Re z| = 6 with half-widths 0.96 kSBLim64Rel |Re z|: the 4 % margin covers a rounded Re z
+// or logarithm in the cell lookup.
+void sbtab_layout(double mu, double sigma, double gamma, double lo, double hi, SBTabHdr& H) {
+  H = SBTabHdr{};
+  const double c1 = (1.0 / sigma) * (1.0 / kSqrt2);
+  const double y = 0.5 * gamma * c1;
+  if (!(sigma > 0.0) || !(gamma >= 0.0) || !std::isfinite(c1) || !std::isfinite(y) ||
+      !(hi > lo))
+    return;
+  double zlo = (lo - mu) * c1, zhi = (hi - mu) * c1;
+  const double pad = 1e-6 * (1.0 + std::max(std::fabs(zlo), std::fabs(zhi)));
+  zlo -= pad;
+  zhi += pad;
+  const double h = 2.0 * 0.96 * (y >= kSBLim64WY ? (double)kSBLim64W : (double)kSBLim64);
+  const bool wide = y >= 1e-6;
+  const double zc = wide ? 6.0 : INFINITY;
+  const double lr = std::log1p(2.0 * 0.96 * (double)kSBLim64Rel);
+  const double a = std::max(-zc, zlo), b = std::min(zc, zhi);
+  const double ncore = b > a ? std::ceil((b - a) / h) : 0.0;
+  const double nneg = zlo < -zc ? std::ceil(std::log(-zlo / zc) / lr) : 0.0;
+  const double npos = zhi > zc ? std::ceil(std::log(zhi / zc) / lr) : 0.0;
+  const double nt = nneg + ncore + npos;
+  if (!(nt >= 1.0 && nt <= (double)kSBTabCap)) return;
+  H.ntab = (int32_t)nt;
+  H.nneg = (int32_t)nneg;
+  H.ncore = (int32_t)ncore;
+  H.a = (float)a;
+  H.ih = (float)(1.0 / h);
+  H.h = (float)h;
+  H.zc = (float)zc;
+  H.izc = wide ? (float)(1.0 / zc) : 0.f;
+  H.ilr = (float)(1.0 / lr);
+  H.lr = (float)lr;
+  H.mu = mu;
+  H.c1 = c1;
+  H.ic1 = sigma * kSqrt2;
+  H.y = y;
 }
 
 // This unit's copy of the exp/log tables, once per device (that device current).

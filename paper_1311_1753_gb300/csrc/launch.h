@@ -10,9 +10,12 @@ namespace gfi {
 // k_1d.cu
 // P: the host copy (grid sizes); prog: the same program in device memory (read by the
 // kernels, copied to shared memory per block)
+// tab (or nullptr): the signal + background kernel's table of w expansions, built by
+// tab_blocks extra blocks of the same launch from the header tab_hdr (device memory)
 cudaError_t launch_norm_1d(const Program& P, const Program* prog, const WeidCoef& W,
                            const double* theta, double* partials, unsigned* counter,
-                           double* derived, cudaStream_t st);
+                           double* derived, const SBTabHdr* tab_hdr, float4* tab,
+                           int tab_blocks, cudaStream_t st);
 size_t events_1d_smem(const Program& P, bool grad, int threads);
 // store: out_logp[perm ? perm[i] : i] = log P_i (perm: the sort permutation of the
 // data set, or nullptr); otherwise the NLL (and gradient) into result.
@@ -46,12 +49,17 @@ cudaError_t launch_gather(const double* in, const int32_t* perm, double* out, in
 cudaError_t prepare_kernels_dalitz();
 // signal + background form (k_sigbkg.cu): NLL (+ gradient) into result[0 .. nfree], or
 // with out_logp the per-event log P (through perm if sorted); mixed: the FP32 plan.  The
-// kernel reads the sorted flag from the device copy of the program.
+// kernel reads the sorted flag from the device copy of the program.  tab (or nullptr):
+// the table of w expansions of this evaluation (header tab_hdr, ntab = 0: none), built
+// by the normalisation launch before it.
 cudaError_t launch_sigbkg(const SigBkgDesc& D, const WeidCoef& W, const Program* prog,
                           const double* x, int64_t n,
                           const double* derived, double* partials, unsigned* counter,
                           double* result, double* out_logp, const int32_t* perm, bool grad,
-                          bool mixed, int nblocks, cudaStream_t st);
+                          bool mixed, int nblocks, const SBTabHdr* tab_hdr, const float4* tab,
+                          cudaStream_t st);
+// host layout of the table (ntab = 0 when the line's cells would exceed kSBTabCap)
+void sbtab_layout(double mu, double sigma, double gamma, double lo, double hi, SBTabHdr& H);
 int sigbkg_blocks_per_sm(bool mixed);
 // batched tick of signal + background fits (TickItem.fit -> FitSB)
 // (grid: sm_count times the plan's resident blocks per SM)

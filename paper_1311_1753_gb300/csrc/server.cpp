@@ -29,6 +29,10 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
+// normalisation-tick items (of kThreads threads) that build a signal + background fit's
+// table of w expansions (its entries do not depend on how many threads build them)
+constexpr int kTickTabItems = 64;
+
 struct Req {
   uint64_t ticket = 0;
   gf_ctx* ctx = nullptr;
@@ -156,7 +160,7 @@ static void fit_thread(gf_server* S, std::shared_ptr<Req> R) {
 static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
   TickBufs& T = S->tb;
   int maxpar = 1;
-  for (auto& R : fits) maxpar = std::max(maxpar, (int)R->ctx->pars.size());
+  for (auto& R : fits) maxpar = std::max(maxpar, theta_all_size(R->ctx));
   const int nfit = (int)fits.size();
   if (nfit > T.cap_fits || maxpar > T.cap_par) {  // (re)size the buffers
     if (T.st) cudaStreamSynchronize(T.st);
@@ -196,12 +200,15 @@ static int64_t run_tick(gf_server* S, std::vector<std::shared_ptr<Req>>& fits) {
   for (int j = 0; j < nfit; ++j) {
     gf_ctx* c = fits[j]->ctx;
     fill_theta_all(c, fits[j]->theta.data(), T.h_theta + (size_t)j * T.cap_par);
+    sbtab_fill(c, T.h_theta + (size_t)j * T.cap_par);
     const double* th = d_theta + (size_t)j * T.cap_par;
     double* res = T.d_res + 64 * j;
     if (c->dev.tick_kind == 1 || c->dev.tick_kind == 3) {
       if (c->has_grid) {
-        it_norm[n_norm++] = TickItem{c->dev.tick_desc, th, res, tot_norm, c->prog.ngrid_blocks};
-        tot_norm += c->prog.ngrid_blocks;
+        // the signal + background form: kTickTabItems more items build its table
+        const int ni = c->prog.ngrid_blocks + (c->dev.tick_kind == 3 ? kTickTabItems : 0);
+        it_norm[n_norm++] = TickItem{c->dev.tick_desc, th, res, tot_norm, ni};
+        tot_norm += ni;
       }
       if (c->dev.tick_kind == 3) {
         const void* fsb = static_cast<const char*>(c->dev.tick_desc) +

@@ -13,7 +13,7 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def exp_model(alpha=-1.0, lo=0.0, hi=10.0):
-    """Config 1: e^{alpha x} on [0, 10] (Listing 1)."""
+    """The truncated exponential e^{alpha x} on [0, 10] (Listing 1)."""
     m = oracle.Model1D([(lo, hi)])
     a = m.param(alpha)
     m.exp(0, a)
@@ -21,7 +21,7 @@ def exp_model(alpha=-1.0, lo=0.0, hi=10.0):
 
 
 def voigt_model(truth=None, nbins=10000):
-    """Config 2: frac * Voigt(mu, sigma, width) + (1-frac) * threshold(x0, power, c).
+    """The line-shape fit: frac * Voigt(mu, sigma, width) + (1-frac) * threshold(x0, power, c).
     Returns (model, free parameter indices in the order mu, sigma, width, c, frac)."""
     t = dict(synth.VOIGT_TRUTH if truth is None else truth)
     m = oracle.Model1D([synth.VOIGT_RANGE], nbins=nbins)

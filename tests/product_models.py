@@ -6,7 +6,7 @@ from paper_1311_1753_gb300 import synth
 
 
 def exp_model(gf, alpha=-2.0, precision=None, lo=0.0, hi=10.0):
-    """Config 1 (Listing 1): alpha in [-10, 10], step 0.1."""
+    """The truncated exponential of Listing 1: alpha in [-10, 10], step 0.1."""
     ctx = gf.Context(0, gf.GF_FP64 if precision is None else precision)
     x = ctx.observable("x", lo, hi)
     a = ctx.parameter("alpha", alpha, 0.1, -10.0, 10.0)
@@ -14,15 +14,16 @@ def exp_model(gf, alpha=-2.0, precision=None, lo=0.0, hi=10.0):
     return ctx, root, [x]
 
 
-def voigt_model(gf, truth=None, precision=None, nbins=10000, free_shape=False):
-    """Config 2: Voigtian + threshold background; free mu, sigma, width, c, frac."""
+def voigt_model(gf, truth=None, precision=None, nbins=10000, free_shape=False, width_lo=1e-6):
+    """Voigtian + threshold background (the line-shape fit); free mu, sigma, width, c,
+    frac."""
     t = dict(synth.VOIGT_TRUTH if truth is None else truth)
     lo, hi = synth.VOIGT_RANGE
     ctx = gf.Context(0, gf.GF_FP64 if precision is None else precision)
     x = ctx.observable("dm", lo, hi)
     mu = ctx.parameter("mu", t["mu"], 1e-5, 0.143, 0.148)
     s = ctx.parameter("sigma", t["sigma"], 1e-5, 1e-5, 2e-3)
-    w = ctx.parameter("width", t["width"], 1e-5, 1e-6, 1e-3)
+    w = ctx.parameter("width", t["width"], 1e-5, width_lo, 1e-3)
     x0 = ctx.parameter("x0", t["x0"], 1e-4, fixed=not free_shape)
     pw = ctx.parameter("power", t["power"], 0.01, fixed=not free_shape)
     c = ctx.parameter("c", t["c"], 0.5, 0.0, 200.0)
@@ -37,7 +38,7 @@ def voigt_model(gf, truth=None, precision=None, nbins=10000, free_shape=False):
 
 
 def dalitz_model(gf, spec, precision=None, free_shapes=False, nbx=512, nby=512, fixed_last=True):
-    """Configs 3/4: resonance r has parameters m0_r, g0_r, re_r, im_r (index 4r + k).
+    """The eight-resonance Dalitz models: resonance r has parameters m0_r, g0_r, re_r, im_r (index 4r + k).
     free_shapes: masses and widths free (except the last resonance if fixed_last)."""
     k = spec["kin"]
     ctx = gf.Context(0, gf.GF_FP64 if precision is None else precision)

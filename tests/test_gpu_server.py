@@ -92,8 +92,9 @@ def test_server_alone_equals_mix(gf, precision):
 
 def test_server_memory_budget_limits_slots(gf):
     reqs = _requests(gf, gf.GF_MIXED, k=4)
-    # each request needs > 4 MB of work buffers: a 6 MB budget admits one at a time
-    srv = gf.Server(precision=gf.GF_MIXED, mem_budget=6 << 20, max_slots=8)
+    # each request needs > 5 MB (4 MB of work buffers, a Voigtian fit also its 2.6 MB table
+    # of w expansions) and at most 8.5 MB: a 10 MB budget admits one at a time
+    srv = gf.Server(precision=gf.GF_MIXED, mem_budget=10 << 20, max_slots=8)
     tickets = []
     for kind, cols, opts in reqs:
         ctx, root, obs = _build(gf, kind, gf.GF_MIXED, opts)

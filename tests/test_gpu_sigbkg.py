@@ -85,19 +85,24 @@ def test_fp64_plan_parity(gf, order, n, sort):
         assert abs(ctx.nll(th[free]) - fg) <= 1e-12 * max(1.0, abs(fg))
 
 
-@pytest.mark.parametrize("width", [2e-6, 1e-5, 3e-5, 2.5e-4, 9e-4])
-def test_fp64_plan_parity_across_line_widths(gf, width):
-    """Sorted events of lines of natural width 2e-6 .. 9e-4 (y = width / (2 sqrt(2) sigma)
-    from 2.4e-3 to 1.06): the expansion's narrow (y < 0.03) and wide chunk limits and the
-    relative one in the tails, per event within 1e-12 of the oracle."""
+@pytest.mark.parametrize("sort", [True, False])
+@pytest.mark.parametrize("width", [1e-10, 2e-6, 1e-5, 3e-5, 2.5e-4, 9e-4])
+def test_fp64_plan_parity_across_line_widths(gf, width, sort):
+    """Lines of natural width 2e-6 .. 9e-4 (y = width / (2 sqrt(2) sigma) from 2.4e-3 to
+    1.06), sorted and caller-ordered events: the table of w expansions with its narrow
+    (y < 0.03) and wide core cells and the logarithmic cells of the tails; width 1e-10
+    (y = 1.2e-7: no logarithmic cells, more core cells than the table holds) runs without
+    the table (per-chunk expansions, or the series per event).  Per event within 1e-12
+    of the oracle."""
     t = dict(synth.VOIGT_TRUTH, width=width)
     lo, hi = synth.VOIGT_RANGE
     x = synth.voigt_threshold_events(200_001, **t, lo=lo, hi=hi, seed=synth.SEED_VOIGT + 5)
     m, free = om.voigt_model(truth=t, nbins=3000)
-    ctx, root, obs = pm.voigt_model(gf, truth=t, nbins=3000)
+    ctx, root, obs = pm.voigt_model(gf, truth=t, nbins=3000, width_lo=min(1e-6, width / 10))
+    ctx.set_event_sort(sort)
     ctx.set_data(root, obs, [x])
     th = m.p[free]
-    per_event(f"sigbkg fp64 sorted width={width:g}", ctx.logpdf(th), m.logpdf([x], m.p))
+    per_event(f"sigbkg fp64 sort={sort} width={width:g}", ctx.logpdf(th), m.logpdf([x], m.p))
     fg, gg = ctx.nll_grad(th)
     fo, go = m.nll([x], m.p, grad=True)
     assert abs(fg - fo) <= 1e-9 * max(1.0, abs(fo)), (fg, fo)
@@ -120,10 +125,10 @@ def test_mixed_plan_errors_full_size(gf):
     pct = {q: float(np.quantile(rel, q)) for q in (0.5, 0.9, 0.99, 0.999)}
     pct[1.0] = float(rel.max())
     for q, v in pct.items():
-        WORST[f"config2 mixed full 1e7: per-event |P/P_orc - 1| quantile {q}"] = v
+        WORST[f"voigt mixed full 1e7: per-event |P/P_orc - 1| quantile {q}"] = v
     f, g = ctx.nll_grad(th)
-    WORST["config2 mixed full 1e7: NLL relative error"] = abs(f / fo - 1)
-    WORST["config2 mixed full 1e7: max |dgrad_k / grad_k|"] = float(np.max(np.abs(g / go[free] - 1)))
+    WORST["voigt mixed full 1e7: NLL relative error"] = abs(f / fo - 1)
+    WORST["voigt mixed full 1e7: max |dgrad_k / grad_k|"] = float(np.max(np.abs(g / go[free] - 1)))
     assert pct[0.5] < 1e-6 and pct[0.99] < 1e-5 and pct[1.0] < 1e-3
     assert abs(f / fo - 1) < 1e-8
     assert np.all(np.abs(g - go[free]) <= 1e-4 * np.abs(go[free]) + 1e-6 * np.abs(go[free]).max())
@@ -135,8 +140,29 @@ def test_mixed_plan_errors_full_size(gf):
     _grad_close(g64, go[free], len(x))
 
 
+def test_mixed_plan_errors_caller_order(gf):
+    """10^6 events in the caller's (unsorted) order in GF_MIXED: every event's expansion
+    looked up in the table by its cell; the same bounds as the sorted full-size case."""
+    x = _data(1_000_000, seed=synth.SEED_VOIGT + 9)
+    m, free = om.voigt_model()
+    p = m.p.copy()
+    p[free] *= np.array([0.99999, 0.98, 1.03, 0.97, 1.02])
+    th = p[free]
+    lo_ = m.logpdf([x], p)
+    fo, go = m.nll([x], p, grad=True)
+    ctx, root, obs = pm.voigt_model(gf, precision=gf.GF_MIXED)
+    ctx.set_event_sort(False)
+    ctx.set_data(root, obs, [x])
+    rel = np.abs(np.expm1(ctx.logpdf(th) - lo_))
+    WORST["voigt mixed caller order 1e6: per-event max |P/P_orc - 1|"] = float(rel.max())
+    assert np.median(rel) < 1e-6 and np.quantile(rel, 0.99) < 1e-5 and rel.max() < 1e-3
+    f, g = ctx.nll_grad(th)
+    assert abs(f / fo - 1) < 1e-8
+    assert np.all(np.abs(g - go[free]) <= 1e-4 * np.abs(go[free]) + 1e-6 * np.abs(go[free]).max())
+
+
 def test_mixed_fit_within_a_hundredth_sigma(gf):
-    """Config 2's form at 10^6 events: the mixed fit (FP32 BFGS, then FP64 from the FP32
+    """The Voigtian + threshold form at 10^6 events: the mixed fit (FP32 BFGS, then FP64 from the FP32
     inverse Hessian) against the oracle's BFGS on the FP64 likelihood."""
     x = _data(1_000_000, seed=123)
     m, free = om.voigt_model(nbins=2000)
@@ -162,6 +188,6 @@ def test_mixed_fit_within_a_hundredth_sigma(gf):
                      np.array([0.148, 2e-3, 1e-3, 200.0, 1.0]), tol=1e-10)
     assert o.converged
     dev = (r["theta"] - o.x) / o.err
-    WORST["config2 mixed fit 1e6: max |theta - theta_orc| / sigma"] = float(np.abs(dev).max())
+    WORST["voigt mixed fit 1e6: max |theta - theta_orc| / sigma"] = float(np.abs(dev).max())
     assert np.all(np.abs(dev) <= 0.01), dev
     assert np.all(np.abs(r["err"] / o.err - 1) < 0.02)
