@@ -75,6 +75,7 @@ struct ArD {
 struct ShapeK {
   double x0;        // mu (Voigtian) or x0 (threshold)
   F2 a, b, c, d, e;
+  F2 t0, hh;        // grid: lo - x0 and the bin width (midpoint b at t0 + (b + 1/2) hh)
   double rb[10];    // relativistic Breit-Wigner constants (relbw_consts)
   double rb_dm0;    // and its dm0
 };
@@ -155,20 +156,28 @@ __device__ __forceinline__ typename A::T relbw_f(double x, const double* cd,
   return f;
 }
 
-// Voigtian: r = Re w(z)/(sigma sqrt(2 pi)), z = (x - mu)/(sigma sqrt 2) + i Gamma/(2 sigma sqrt 2).
-// a = 1/(sigma sqrt2), b = Im z, c = 1/(sigma sqrt(2 pi)), d = 1/sigma, e = a/2.
-__device__ __forceinline__ void voigt_consts(double mu, double s, double G, ShapeK& K) {
-  const double c1 = 1.0 / (s * kSqrt2);
-  K.x0 = mu;
-  K.a = df_from(c1);
-  K.b = df_from(0.5 * G * c1);
-  K.c = df_from(1.0 / (s * kSqrt2Pi));
-  K.d = df_from(1.0 / s);
-  K.e = df_from(0.5 * c1);
+// The grid of a leaf over [lo, hi] relative to x0, in pairs: t0 = lo - x0, hh = (hi - lo)/nbins.
+__device__ __forceinline__ void grid_consts(const LeafDesc& L, double x0, ShapeK& K) {
+  K.t0 = df_from(L.lo - x0);
+  K.hh = df_mul(df_from(L.hi - L.lo), df_rcp(F2{(float)L.nbins, 0.f}));
 }
-__device__ __forceinline__ double voigt_r(double x, const ShapeK& K, const WeidCoef& W,
-                                          double* dr) {
-  const F2 zr = df_mul(df_split(x - K.x0), K.a);
+
+// Voigtian: r = Re w(z)/(sigma sqrt(2 pi)), z = (x - mu)/(sigma sqrt 2) + i Gamma/(2 sigma sqrt 2).
+// a = 1/(sigma sqrt2), b = Im z, c = 1/(sigma sqrt(2 pi)), d = 1/sigma, e = a/2: in pairs on
+// the FP32 pipe (one thread forms them; FP64 divisions on it would be a long chain).
+__device__ __forceinline__ void voigt_consts(double mu, double s, double G, ShapeK& K) {
+  const F2 is = df_rcp(df_from(s));
+  const F2 a = df_mul(is, F2(DFC(1.0 / kSqrt2)));
+  K.x0 = mu;
+  K.a = a;
+  K.b = df_mul(df_mul_f(df_from(G), 0.5f), a);
+  K.c = df_mul(is, F2(DFC(1.0 / kSqrt2Pi)));
+  K.d = is;
+  K.e = df_mul_f(a, 0.5f);
+}
+// r and dr/d(mu, sigma, Gamma) at t = x - mu, as pairs (out[0] = r).
+__device__ __forceinline__ void voigt_r2(F2 t, const ShapeK& K, const WeidCoef& W, F2* out) {
+  const F2 zr = df_mul(t, K.a);
   F2 wr, wi;
   faddeeva_f2(zr, K.b, W, wr, wi);
   const F2 r = df_mul(wr, K.c);
@@ -176,11 +185,11 @@ __device__ __forceinline__ double voigt_r(double x, const ShapeK& K, const WeidC
   const F2 dre = df_mul_f(df_sub(df_mul(zr, wr), df_mul(K.b, wi)), -2.f);
   const F2 dim = df_add(df_mul_f(df_add(df_mul(zr, wi), df_mul(K.b, wr)), -2.f),
                         F2(DFC(kTwoInvSqrtPi)));
-  dr[0] = -df_to(df_mul(df_mul(K.c, K.a), dre));                                 // d/dmu
-  dr[1] = -df_to(df_add(df_mul(df_mul(K.c, K.d), df_sub(df_mul(dre, zr), df_mul(dim, K.b))),
-                        df_mul(r, K.d)));                                           // d/dsigma
-  dr[2] = -df_to(df_mul(df_mul(K.c, K.e), dim));                                 // d/dGamma
-  return df_to(r);
+  out[0] = r;
+  out[1] = df_neg(df_mul(df_mul(K.c, K.a), dre));                                 // d/dmu
+  out[2] = df_neg(df_add(df_mul(df_mul(K.c, K.d), df_sub(df_mul(dre, zr), df_mul(dim, K.b))),
+                         df_mul(r, K.d)));                                           // d/dsigma
+  out[3] = df_neg(df_mul(df_mul(K.c, K.e), dim));                                 // d/dGamma
 }
 
 // Threshold: r = (x - x0)^p e^{-c (x - x0)} for x > x0.  a = p, b = c.
@@ -189,19 +198,18 @@ __device__ __forceinline__ void thresh_consts(double x0, double p, double c, Sha
   K.a = df_from(p);
   K.b = df_from(c);
 }
-__device__ __forceinline__ double thresh_r(double x, const ShapeK& K, double* dr) {
-  const double t = x - K.x0;
-  if (!(t > 0.0)) {
-    dr[0] = dr[1] = dr[2] = 0.0;
-    return 0.0;
+// r and dr/d(x0, p, c) at t = x - x0, as pairs.
+__device__ __forceinline__ void thresh_r2(F2 T, const ShapeK& K, F2* out) {
+  if (!(T.hi > 0.f)) {
+    out[0] = out[1] = out[2] = out[3] = F2{0.f, 0.f};
+    return;
   }
-  const F2 T = df_split(t);
   const F2 lt = df_log_tab(T, s_log_tab);
   const F2 r = df_exp_tab(df_sub(df_mul(K.a, lt), df_mul(K.b, T)), s_exp_tab);
-  dr[0] = df_to(df_mul(r, df_sub(K.b, df_mul(K.a, df_rcp(T)))));
-  dr[1] = df_to(df_mul(r, lt));
-  dr[2] = -df_to(df_mul(T, r));
-  return df_to(r);
+  out[0] = r;
+  out[1] = df_mul(r, df_sub(K.b, df_mul(K.a, df_rcp(T))));
+  out[2] = df_mul(r, lt);
+  out[3] = df_neg(df_mul(T, r));
 }
 
 // ---- leaf records ------------------------------------------------------------------------
@@ -310,17 +318,63 @@ __device__ inline void make_coefs(const Program& P, const double* th, double* co
   }
 }
 
+// The Voigtian's and the threshold's leaf records from the pair sums S = (N, dN/dpar_k)
+// of their grids, formed in pairs on the FP32 pipe by a whole warp: every lane takes the
+// same steps, then lane k converts value k to FP64 and stores it (one conversion per lane
+// instead of a chain of FP64 divisions, logarithm and conversions on one thread).  The
+// parameters the events subtract (mu, x0) and the threshold's (p, c) are copied exactly.
+// Same layout as make_leaf_record.
+__device__ __forceinline__ void leaf_record_warp(const LeafDesc& L, const double* th,
+                                                 const F2* S, double* rec) {
+  const int lane = threadIdx.x & 31;
+  const bool raw = (L.aux & kRawLeaf) != 0;
+  const F2 z = {0.f, 0.f};
+  const F2 N = raw ? F2{1.f, 0.f} : S[0];
+  const F2 iN = df_rcp(N);
+  const F2 lN = raw ? z : df_log_tab(N, s_log_tab);
+  const F2 r2 = raw ? z : df_mul(S[1], iN), r3 = raw ? z : df_mul(S[2], iN),
+           r4 = raw ? z : df_mul(S[3], iN);
+  F2 v = z;
+  bool exact = false;  // this lane copies a parameter
+  if (lane == 0) v = iN;
+  if (lane == 1) v = lN;
+  if (lane == 2) v = r2;
+  if (lane == 3) v = r3;
+  if (lane == 4) v = r4;
+  if (L.kind == L_VOIGT) {
+    const F2 is = df_rcp(df_from(th[L.par[1]]));
+    const F2 c1 = df_mul(is, F2(DFC(1.0 / kSqrt2)));
+    const F2 c3 = df_mul(df_mul(is, iN), F2(DFC(1.0 / kSqrt2Pi)));
+    const F2 c31 = df_mul(c3, c1);
+    exact = lane == 10;  // mu
+    if (lane == 11) v = c1;
+    if (lane == 12) v = df_mul(df_mul_f(df_from(th[L.par[2]]), 0.5f), c1);
+    if (lane == 13) v = c3;
+    if (lane == 14) v = is;
+    if (lane == 15) v = c31;
+    if (lane == 16) v = df_mul(c3, is);
+    if (lane == 17) v = df_mul_f(c31, 0.5f);
+    if (lane == 18) v = df_add(is, r3);
+  } else {  // L_THRESH: x0, p, c, then 1/N
+    exact = lane >= 10 && lane < 13;
+    if (lane == 13) v = iN;
+  }
+  if (lane < kLeafRec) rec[lane] = exact ? th[L.par[lane - 10]] : df_to(v);
+}
+
 // ---- normalisation grid -----------------------------------------------------------------
 // One block per (grid leaf, chunk of kThreads bins): each thread takes one midpoint.
-// partials: [block][4] = (sum r, sum dr/dp0, dr/dp1, dr/dp2).
+// partials (value-major within a block): [block][4] = (sum r, sum dr/dp0, dr/dp1, dr/dp2).
 // Body of one (virtual) block vb of the vgrid blocks of a normalisation launch; the last
-// block to arrive finishes.  Shared scratch: red[32], *last, sums[kMaxLeaf][4].
+// block to arrive finishes.  Shared scratch: red[32], *last, sums[kMaxLeaf][4] (pairs).
+// The Voigtian and threshold grids run in pairs end to end (bin positions, values, block
+// and cross-block sums, records); other leaves evaluate in FP64 and enter the pair sums.
 __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& W,
                                               const double* __restrict__ theta,
                                               double* __restrict__ partials,
                                               unsigned* __restrict__ counter,
                                               double* __restrict__ derived, int vb, int vgrid,
-                                              double* red, int* last, double (*sums)[4],
+                                              double* red, int* last, F2 (*sums)[4],
                                               ShapeK* shk) {
   // locate this block's leaf
   int li = -1;
@@ -331,41 +385,42 @@ __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& 
   }
   if (li >= 0 && threadIdx.x == 0) {
     const LeafDesc& L = P.leaf[li];
-    if (L.kind == L_VOIGT) voigt_consts(theta[L.par[0]], theta[L.par[1]], theta[L.par[2]], *shk);
-    else if (L.kind == L_RELBW) {
+    if (L.kind == L_VOIGT) {
+      voigt_consts(theta[L.par[0]], theta[L.par[1]], theta[L.par[2]], *shk);
+      grid_consts(L, shk->x0, *shk);
+    } else if (L.kind == L_RELBW) {
       relbw_consts(L, theta, shk->rb);
       shk->rb_dm0 = theta[L.par[0]];
+    } else {
+      thresh_consts(theta[L.par[0]], theta[L.par[1]], theta[L.par[2]], *shk);
+      grid_consts(L, shk->x0, *shk);
     }
-    else thresh_consts(theta[L.par[0]], theta[L.par[1]], theta[L.par[2]], *shk);
   }
   __syncthreads();
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  F2 v[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   if (li >= 0) {
     const LeafDesc& L = P.leaf[li];
     const int b = (vb - L.grid_first_block) * blockDim.x + threadIdx.x;
     if (b < L.nbins) {
-      const double h = (L.hi - L.lo) / L.nbins;
-      const double x = L.lo + (b + 0.5) * h;
-      double dr[3];
-      if (L.kind == L_VOIGT) {
-        v[0] = voigt_r(x, *shk, W, dr);
-      } else if (L.kind == L_RELBW) {
-        v[0] = relbw_f<ArD, true>(x, shk->rb, shk->rb, L.aux & 0xff, shk->rb_dm0, dr[0], dr[1]);
-        dr[2] = 0.0;
+      if (L.kind == L_RELBW) {
+        const double h = (L.hi - L.lo) / L.nbins;
+        const double x = L.lo + (b + 0.5) * h;
+        double d0, d1;
+        v[0] = df_from(relbw_f<ArD, true>(x, shk->rb, shk->rb, L.aux & 0xff, shk->rb_dm0, d0, d1));
+        v[1] = df_from(d0);
+        v[2] = df_from(d1);
       } else {
-        v[0] = thresh_r(x, *shk, dr);
+        const F2 t = df_add(shk->t0, df_mul_f(shk->hh, (float)b + 0.5f));
+        if (L.kind == L_VOIGT) voigt_r2(t, *shk, W, v);
+        else thresh_r2(t, *shk, v);
       }
-      v[1] = dr[0];
-      v[2] = dr[1];
-      v[3] = dr[2];
     }
   }
   // the four block sums in one pass (pairs, their shuffle trees interleaved)
-  block_sum_pairs<4>([&](int k) -> F2 { return df_from(v[k]); }, 4, red,
-                     partials + (size_t)vb * 4);
+  block_sum_pairs<4>([&](int k) -> F2 { return v[k]; }, 4, red, partials + (size_t)vb * 4);
   if (!arrive_last_of(counter, (unsigned)vgrid, last)) return;
   // last block: one warp per (leaf, value), its lanes' loads of the leaf's chunk partials
-  // all in flight, fixed-order pair sums; then every leaf record
+  // all in flight, fixed-order pair sums times the bin width; then every leaf record
   {
     constexpr int kPer = 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -391,15 +446,26 @@ __device__ __forceinline__ void norm_1d_block(const Program& P, const WeidCoef& 
         const F2 u = {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
         a = df_add(a, u);
       }
-      if (lane == 0) sums[q >> 2][k] = df_to(a) * (L.hi - L.lo) / L.nbins;
+      if (lane == 0)
+        sums[q >> 2][k] = df_mul(a, df_mul(df_from(L.hi - L.lo), df_rcp(F2{(float)L.nbins, 0.f})));
     }
   }
   __syncthreads();
-  // one leaf per warp (lane 0): the leaves' FP64 records run side by side, not as
-  // divergent branches of one warp
-  if ((threadIdx.x & 31) == 0)
-    for (int l = threadIdx.x >> 5; l < P.nleaf; l += blockDim.x >> 5)
-      make_leaf_record(P.leaf[l], theta, sums[l][0], &sums[l][1], derived + l * kLeafRec);
+  // one leaf per warp: the Voigtian's and threshold's records by the whole warp in pairs,
+  // the others by its lane 0 in FP64 (the leaves' records side by side, not as divergent
+  // branches of one warp)
+  {
+    const int lane = threadIdx.x & 31;
+    for (int l = threadIdx.x >> 5; l < P.nleaf; l += blockDim.x >> 5) {
+      const LeafDesc& L = P.leaf[l];
+      if (L.nbins > 0 && (L.kind == L_VOIGT || L.kind == L_THRESH)) {
+        leaf_record_warp(L, theta, sums[l], derived + l * kLeafRec);
+      } else if (lane == 0) {
+        const double dN[3] = {df_to(sums[l][1]), df_to(sums[l][2]), df_to(sums[l][3])};
+        make_leaf_record(L, theta, df_to(sums[l][0]), dN, derived + l * kLeafRec);
+      }
+    }
+  }
   if (threadIdx.x == 0) {
     make_coefs(P, theta, derived + kMaxLeaf * kLeafRec);
     *counter = 0u;
@@ -434,7 +500,7 @@ __global__ void __launch_bounds__(kThreads) k_norm_1d(const Program* __restrict_
   __shared__ Program P;
   __shared__ double red[32];
   __shared__ int last;
-  __shared__ double sums[kMaxLeaf][4];
+  __shared__ F2 sums[kMaxLeaf][4];
   __shared__ ShapeK shk;
   load_df_tables();
   load_program(Pg, P);
@@ -1527,7 +1593,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tick_norm_1d(const TickItem* __
   __shared__ Program Ps;
   __shared__ double red[32];
   __shared__ int last;
-  __shared__ double sums[kMaxLeaf][4];
+  __shared__ F2 sums[kMaxLeaf][4];
   __shared__ ShapeK shk;
   load_df_tables();  // visible after tick_item's first barrier
   int cur = -1;
