@@ -264,18 +264,19 @@ def time_steps(torch, ctx, thetas, steps, warmup, grad=True, flush=True):
 def e2e_steps(torch, ctx, cols, thetas, steps, warmup, pipelined=True):
     """Public-API step with host buffers, pipelined for 1D data sets: step k evaluates its
     events (NLL + gradient back to the host) while the library copies and range-checks
-    step k+1's events from pinned host memory on its copy stream (gf_prefetch_data);
-    gf_update_data then loads them (a swap of two device buffer sets; events in the
-    caller's order).  Each timed step completes one copy of a step's events.  Wall clock
-    per step."""
+    the events of steps k+1 and k+2 from pinned host memory, one after the other on its
+    copy stream (gf_prefetch_data, two sets ahead); gf_update_data then loads step k+1's
+    (a swap of device buffer sets; events in the caller's order) and step k+3's copy is
+    queued.  Each timed step completes one copy of a step's events.  Wall clock per
+    step."""
     pinned = []
-    for shift in (0, 1):
+    for shift in (0, 1, 2):
         p = [torch.from_numpy(np.ascontiguousarray(np.roll(c, shift))).pin_memory() for c in cols]
         pinned.append(p)
     n = len(cols[0])
 
     def ptrs(k):
-        return [t.data_ptr() for t in pinned[k % 2]]
+        return [t.data_ptr() for t in pinned[k % 3]]
 
     if not pipelined:  # Dalitz data sets: copy, check and evaluate in turn
         for k in range(warmup):
@@ -289,18 +290,19 @@ def e2e_steps(torch, ctx, cols, thetas, steps, warmup, pipelined=True):
         return time.perf_counter() - t0, 8 * n * len(cols)
     ctx.update_data_ptrs(n, ptrs(0))
     ctx.prefetch_data_ptrs(n, ptrs(1))
+    ctx.prefetch_data_ptrs(n, ptrs(2))
     k = 0
     for _ in range(warmup):
         ctx.nll_grad(thetas[k % len(thetas)])
         ctx.update_data_ptrs(n, ptrs(k + 1))
-        ctx.prefetch_data_ptrs(n, ptrs(k + 2))
+        ctx.prefetch_data_ptrs(n, ptrs(k + 3))
         k += 1
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
         ctx.nll_grad(thetas[k % len(thetas)])
         ctx.update_data_ptrs(n, ptrs(k + 1))
-        ctx.prefetch_data_ptrs(n, ptrs(k + 2))
+        ctx.prefetch_data_ptrs(n, ptrs(k + 3))
         k += 1
     wall = time.perf_counter() - t0
     return wall, 8 * n * len(cols)
@@ -634,10 +636,11 @@ def main():
                "h2d_bytes_per_step": h2d + 8 * len(th0),
                "d2h_bytes_per_step": 8 * (1 + len(th0)) + 4,
                "note": ("pipelined through the C ABI: step k's NLL + gradient (back to the "
-                        "host) while step k+1's events are copied from pinned host memory "
-                        "and range-checked on the library's copy stream "
-                        "(gf_prefetch_data), then loaded by gf_update_data; wall clock per "
-                        "step" if pipe else
+                        "host) while the events of steps k+1 and k+2 are copied from pinned "
+                        "host memory and range-checked, one after the other, on the "
+                        "library's copy stream (gf_prefetch_data, two sets ahead); step "
+                        "k+1's are then loaded by gf_update_data; wall clock per step"
+                        if pipe else
                         "gf_update_data from pinned host memory + gf_nll_grad in turn, wall "
                         "clock per step")}
     except Exception as e:  # report, do not hide

@@ -265,9 +265,12 @@ int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols);
  * set evaluated repeatedly is sorted again from its second evaluation).  The host columns
  * must stay unchanged until that gf_update_data returns.  A range error is reported by
  * that gf_update_data (GF_EINVAL; the prefetched set is not loaded, the loaded one stays).
- * A gf_update_data with other pointers, a second gf_prefetch_data or gf_set_data waits for
- * the prefetch and drops it.  The evaluation graphs of both buffer sets are kept, so
- * alternating sets does not re-capture them.  Device memory: one more copy of the columns.
+ * Up to two prefetches may wait, copied one after the other: gf_update_data with the
+ * columns of one of them loads it and drops the ones staged before it; a third
+ * gf_prefetch_data drops the oldest; gf_update_data with other pointers or gf_set_data
+ * waits for them and drops them all.  The evaluation graphs of the three buffer sets are
+ * kept, so rotating sets does not re-capture them.  Device memory: up to two more copies
+ * of the columns.
  * Dalitz, time-dependent Dalitz and binned data sets: GF_EINVAL; no data set owned:
  * GF_ESTATE. */
 int gf_prefetch_data(gf_ctx* ctx, int64_t n, const double* const* cols);

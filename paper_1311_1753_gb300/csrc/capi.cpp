@@ -115,9 +115,11 @@ static void free_dev(gf_ctx* ctx) {
     cudaStreamSynchronize(d.copy_stream);
     cudaStreamDestroy(d.copy_stream);
   }
-  if (d.ev_staged) cudaEventDestroy(d.ev_staged);
+  for (int q = 0; q < DevState::kStage; ++q) {
+    if (d.ev_staged[q]) cudaEventDestroy(d.ev_staged[q]);
+    for (double* p : d.stage[q]) cudaFree(p);
+  }
   if (d.ev_free) cudaEventDestroy(d.ev_free);
-  for (double* p : d.stage) cudaFree(p);
   if (d.owns_cols)
     for (double* p : d.cols) cudaFree(p);
   d.cols.clear();
@@ -2551,31 +2553,51 @@ int gf_last_eval_times(gf_ctx* ctx, double* total_ms, double* stream_ms) {
   return GF_OK;
 }
 
-// Wait for a prefetch still in flight and forget it (its buffers stay allocated).
-static int drop_staged(gf_ctx* ctx) {
+// The range-check flag of spare set q (slots 61, 62 of the mapped result block).
+static volatile int* stage_flag_host(DevState& d, int q) {
+  return reinterpret_cast<volatile int*>(d.h_result + 61 + q);
+}
+
+// Wait for the oldest prefetch still in flight and forget it (its buffers stay allocated).
+static int drop_oldest(gf_ctx* ctx) {
   DevState& d = ctx->dev;
-  if (d.stage_src.empty()) return GF_OK;
-  d.stage_src.clear();
-  CK(cudaEventSynchronize(d.ev_staged));
+  if (d.npend == 0) return GF_OK;
+  const int q = d.pend[0];
+  d.stage_src[q].clear();
+  for (int k = 1; k < d.npend; ++k) d.pend[k - 1] = d.pend[k];
+  d.npend--;
+  CK(cudaEventSynchronize(d.ev_staged[q]));
   return GF_OK;
 }
 
-// The prefetched set becomes the context's data: its copy and range check ran on the copy
-// stream during earlier work, so this is a swap of the two buffer sets.  The new events
-// are in the caller's order (the strided event loop; a set evaluated repeatedly is sorted
-// again from its second evaluation, as after gf_update_data).
+// ... and every one of them.
+static int drop_staged(gf_ctx* ctx) {
+  while (ctx->dev.npend > 0) {
+    const int rc = drop_oldest(ctx);
+    if (rc) return rc;
+  }
+  return GF_OK;
+}
+
+// The oldest prefetched set becomes the context's data: its copy and range check ran on
+// the copy stream during earlier work, so this is a swap of two buffer sets.  The new
+// events are in the caller's order (the strided event loop; a set evaluated repeatedly is
+// sorted again from its second evaluation, as after gf_update_data).
 static int swap_staged(gf_ctx* ctx) {
   DevState& d = ctx->dev;
-  d.stage_src.clear();
-  CK(cudaEventSynchronize(d.ev_staged));
-  volatile int* sflag = reinterpret_cast<volatile int*>(d.h_result + 62);
+  const int q = d.pend[0];
+  d.stage_src[q].clear();
+  for (int k = 1; k < d.npend; ++k) d.pend[k - 1] = d.pend[k];
+  d.npend--;
+  CK(cudaEventSynchronize(d.ev_staged[q]));
+  volatile int* sflag = stage_flag_host(d, q);
   if (*sflag) {
     *sflag = 0;
     return set_error(ctx, GF_EINVAL, "gf_update_data: an event of the prefetched set lies outside "
                                      "its range (the set was not loaded)");
   }
-  std::swap(d.cols, d.stage);
-  d.cur_set ^= 1;
+  std::swap(d.cols, d.stage[q]);
+  std::swap(d.cur_set, d.stage_id[q]);
   const int rc = mark_unsorted(ctx);  // the kernels read the flag from the device program
   if (rc) return rc;
   if (d.tick_desc) {  // the serving descriptor holds the old column pointers
@@ -2599,42 +2621,48 @@ int gf_prefetch_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
   int rc = ensure_compiled(ctx);
   if (rc) return rc;
   CK(cudaSetDevice(ctx->device));
-  rc = drop_staged(ctx);  // an earlier prefetch that was never loaded
-  if (rc) return rc;
+  if (d.npend == DevState::kStage) {  // the queue is full: the oldest is never loaded
+    rc = drop_oldest(ctx);
+    if (rc) return rc;
+  }
   if (!d.copy_stream) {
     CK(cudaStreamCreateWithFlags(&d.copy_stream, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&d.ev_staged, cudaEventDisableTiming));
+    for (int q = 0; q < DevState::kStage; ++q)
+      CK(cudaEventCreateWithFlags(&d.ev_staged[q], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&d.ev_free, cudaEventDisableTiming));
   }
+  int q = 0;  // a spare set holding no prefetch
+  while (!d.stage_src[q].empty()) ++q;
   const size_t bytes = round_up((size_t)std::max<int64_t>(n + 2, 2) * 8, 256);
-  while ((int)d.stage.size() < d.nobs) {
+  while ((int)d.stage[q].size() < d.nobs) {
     double* p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
       cudaGetLastError();
       return set_error(ctx, GF_ENOMEM, "gf_prefetch_data: device allocation of the staging buffers failed");
     }
-    d.stage.push_back(p);
+    d.stage[q].push_back(p);
     CK(cudaMemsetAsync(p, 0, bytes, d.copy_stream));
   }
-  // the staging buffers may still be read by work queued on the compute stream
+  // the spare buffers may still be read by work queued on the compute stream
   CK(cudaEventRecord(d.ev_free, ctx->stream));
   CK(cudaStreamWaitEvent(d.copy_stream, d.ev_free, 0));
-  *reinterpret_cast<volatile int*>(d.h_result + 62) = 0;
+  *stage_flag_host(d, q) = 0;
   for (int k = 0; k < d.nobs; ++k)
     if (n > 0)
-      CK(cudaMemcpyAsync(d.stage[k], cols[k], sizeof(double) * n, cudaMemcpyHostToDevice,
+      CK(cudaMemcpyAsync(d.stage[q][k], cols[k], sizeof(double) * n, cudaMemcpyHostToDevice,
                          d.copy_stream));
   Cols c{};
   double lo[kMaxObs], hi[kMaxObs];
   for (int k = 0; k < d.nobs; ++k) {
-    c.c[k] = d.stage[k];
+    c.c[k] = d.stage[q][k];
     lo[k] = ctx->obs[d.obs_ids[k]].lo;
     hi[k] = ctx->obs[d.obs_ids[k]].hi;
   }
-  CK(launch_check_range(c, d.nobs, n, lo, hi, reinterpret_cast<int*>(d.result + 62),
+  CK(launch_check_range(c, d.nobs, n, lo, hi, reinterpret_cast<int*>(d.result + 61 + q),
                         d.copy_stream));
-  CK(cudaEventRecord(d.ev_staged, d.copy_stream));
-  d.stage_src.assign(cols, cols + d.nobs);
+  CK(cudaEventRecord(d.ev_staged[q], d.copy_stream));
+  d.stage_src[q].assign(cols, cols + d.nobs);
+  d.pend[d.npend++] = q;
   return GF_OK;
 }
 
@@ -2644,14 +2672,21 @@ int gf_update_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
   if (!d.owns_cols || !d.theta) return set_error(ctx, GF_ESTATE, "no data set owned by the context");
   if (n != d.n) return set_error(ctx, GF_EINVAL, "gf_update_data: n must equal the loaded size");
   if (d.binned) return set_error(ctx, GF_EINVAL, "gf_update_data: binned data go through gf_set_data");
-  if (!d.stage_src.empty()) {
-    bool same = true;
-    for (int k = 0; k < d.nobs; ++k) same = same && d.stage_src[k] == cols[k];
-    if (same) {
-      CK(cudaSetDevice(ctx->device));
-      return swap_staged(ctx);
+  if (d.npend > 0) {
+    // the columns of a pending prefetch: the ones staged before it are never loaded
+    int at = -1;
+    for (int j = 0; j < d.npend && at < 0; ++j) {
+      bool same = true;
+      for (int k = 0; k < d.nobs; ++k) same = same && d.stage_src[d.pend[j]][k] == cols[k];
+      if (same) at = j;
     }
-    const int rd = drop_staged(ctx);  // another set: the prefetched one is not used
+    CK(cudaSetDevice(ctx->device));
+    for (int j = 0; j < at; ++j) {
+      const int rd = drop_oldest(ctx);
+      if (rd) return rd;
+    }
+    if (at >= 0) return swap_staged(ctx);
+    const int rd = drop_staged(ctx);  // another set: the prefetched ones are not used
     if (rd) return rd;
   }
   d.tddp_ready = false;  // per-event amplitudes of the new events

@@ -72,7 +72,7 @@ struct DevState {
   bool gram_valid = false;
   bool mask_built = false;
   // timing
-  cudaGraphExec_t graph[16] = {};     // steady-state evaluation graphs: grad | fp64 << 1 |
+  cudaGraphExec_t graph[24] = {};     // steady-state evaluation graphs: grad | fp64 << 1 |
                                       // direct << 2 | cur_set << 3
   bool graph_off = false;             // a capture failed: launch directly from then on
   std::string graph_why;              // why (for gf_last_eval_graph)
@@ -87,14 +87,18 @@ struct DevState {
   int sort_obs = -1;                  // the column the events are sorted by
   int32_t* perm = nullptr;            // sorted position -> original event index
   int evals_since_load = 0;           // evaluations since the columns were (re)loaded
-  // the next data set prefetched by gf_prefetch_data: copied and range-checked on
-  // copy_stream into the inactive buffer set `stage`, swapped in by gf_update_data; the
-  // graphs of each buffer set are kept (key bit cur_set)
-  std::vector<double*> stage;         // the inactive buffer set (same sizes as cols)
+  // the next data sets prefetched by gf_prefetch_data (up to kStage in flight): copied and
+  // range-checked in order on copy_stream into the spare buffer sets, swapped in by
+  // gf_update_data; the graphs of each of the 1 + kStage buffer sets are kept (key cur_set)
+  static constexpr int kStage = 2;
+  std::vector<double*> stage[kStage];   // spare buffer sets (same sizes as cols)
+  int stage_id[kStage] = {1, 2};        // their buffer-set numbers (cols has cur_set)
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_staged = nullptr;    // recorded after the staged set's copy and check
-  cudaEvent_t ev_free = nullptr;      // the compute stream's work before the copy
-  std::vector<const double*> stage_src;  // host columns of the staged set (empty: none)
+  cudaEvent_t ev_staged[kStage] = {};   // recorded after each spare set's copy and check
+  cudaEvent_t ev_free = nullptr;        // the compute stream's work before a copy
+  std::vector<const double*> stage_src[kStage];  // host columns staged there (empty: none)
+  int pend[kStage] = {0, 0};            // the spare sets holding prefetches, oldest first
+  int npend = 0;
   int cur_set = 0;
   // convolution nodes: device descriptors and their tables (allocated at compile)
   std::vector<void*> conv_bufs;        // every allocation of the conv tables

@@ -38,6 +38,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "devutil.cuh"
 #include "gf_internal.h"
@@ -312,9 +313,13 @@ __device__ __forceinline__ void sigbkg_block(
     const int32_t* __restrict__ perm, const SBTabHdr* __restrict__ tabh,
     const float4* __restrict__ tab, const int vb, const int vgrid, SBShared<MIXED>& sh) {
   const int tid = threadIdx.x;
+  constexpr int NT = sb_threads<MIXED>();
+  const int64_t nthreads = (int64_t)vgrid * NT;
+  // sorted events and at least 8 per thread: one expansion of w per chunk pays
+  const bool chunked = sorted && n >= 8 * nthreads;
   if (tid == 0) {
     sb_consts<MIXED>(D, der, G, sh.K);
-    sh.tf = tab ? sbtab_f(*tabh) : SBTabF{0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f};
+    sh.tf = tab && !chunked ? sbtab_f(*tabh) : SBTabF{0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f};
   }
   // the constants as pairs, one per lane of warp 0 (their FP64 conversions and divisions
   // side by side instead of in a chain on one thread or repeated by every thread)
@@ -378,18 +383,14 @@ __device__ __forceinline__ void sigbkg_block(
       for (int k = 1; k < kSBMom; ++k) m[k - 1].add(df_from(o[k]));
   };
 
-  constexpr int NT = sb_threads<MIXED>();
-  const int64_t nthreads = (int64_t)vgrid * NT;
   const int64_t g = (int64_t)vb * NT + tid;
   constexpr int kChunk = MIXED ? kSBChunk32 : kSBChunk64;
-  // sorted events and at least 8 per thread: one expansion of w per chunk pays
-  const bool chunked = sorted && n >= 8 * nthreads;
   (void)g;
 
   // the table of w expansions for events in any order: each event's expansion by its cell
   // of Re z, reloaded when the cell changes.  Sorted chunks expand w themselves (one
   // Weideman series and recurrence per chunk costs less than a cell lookup per event).
-  const bool use_tab = sh.tf.ntab > 0 && !chunked;
+  const bool use_tab = sh.tf.ntab > 0;  // (never in chunks)
   int kcur = -1;
 
   if constexpr (!MIXED) {
@@ -399,10 +400,12 @@ __device__ __forceinline__ void sigbkg_block(
     const F2 cv = sh.kp[6], ct = sh.kp[7];
     ProdF2 prod;
     TayP T;
-    auto one = [&](int64_t i, double xi, bool tay) {
+    // tabc: std::true_type for the table's lookups, std::false_type for the chunk's own
+    // expansion (tay) or the series (the two loops get their own code)
+    auto one = [&](int64_t i, double xi, bool tay, auto tabc) {
       const F2 zr = df_mul(df_split(xi - K.mu), c1);
       F2 wr, wi;
-      if (use_tab) {
+      if constexpr (decltype(tabc)::value) {
         const int kc = sbtab_index(zr.hi, sh.tf);
         if (kc != kcur) {
           sbtab_load(tab, kc, T);
@@ -489,7 +492,7 @@ __device__ __forceinline__ void sigbkg_block(
         for (int k = 0; k < c; ++k) {
           const double xi = xn;
           if (k + 1 < c) xn = __ldg(xcol + a + k + 1);
-          one(a + k, xi, tay);
+          one(a + k, xi, tay, std::false_type{});
         }
       };
       const ChunkSplit cs(n, nthreads, kChunk);
@@ -507,15 +510,19 @@ __device__ __forceinline__ void sigbkg_block(
         flush();
       }
     } else {
-      int since = 0;
-      for (int64_t i = g; i < n; i += nthreads) {
-        one(i, __ldcs(xcol + i), false);
-        if (++since == kSBFlush) {
-          flush();
-          since = 0;
+      auto loop = [&](auto tabc) {
+        int since = 0;
+        for (int64_t i = g; i < n; i += nthreads) {
+          one(i, __ldcs(xcol + i), false, tabc);
+          if (++since == kSBFlush) {
+            flush();
+            since = 0;
+          }
         }
-      }
-      flush();
+        flush();
+      };
+      if (use_tab) loop(std::true_type{});
+      else loop(std::false_type{});
     }
   } else {
     // ---------------- mixed plan: FP32 per event ----------------

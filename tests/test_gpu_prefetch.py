@@ -1,6 +1,6 @@
-"""gf_prefetch_data: the next events copied and range-checked on the library's copy stream
-while the current ones are evaluated, then loaded by gf_update_data as a swap of two
-device buffer sets (Sec. 2's data loading, pipelined with the evaluation).
+"""gf_prefetch_data: the next events (up to two sets ahead) copied and range-checked on the
+library's copy stream while the current ones are evaluated, then loaded by gf_update_data
+as a swap of device buffer sets (Sec. 2's data loading, pipelined with the evaluation).
 
 The loaded set must give exactly what a fresh gf_set_data of the same events in the
 caller's order gives (the same kernels: bitwise), per event against the oracle, in both
@@ -69,6 +69,45 @@ def test_prefetched_sets_match_a_fresh_load(gf):
     per_event("prefetched set", ctx.logpdf(th), m.logpdf([xs[2]], p))
     fo, go = m.nll([xs[2]], p, grad=True)
     assert abs(ref[2][0] - fo) <= 1e-9 * abs(fo)
+    ctx.close()
+
+
+def test_two_prefetches_in_flight(gf):
+    """Two sets staged ahead (three device buffer sets in rotation), loaded in order, each
+    equal to a fresh load; a third prefetch while two wait drops the oldest, and loading
+    the newer of two pending sets drops the older one."""
+    n = 200_001
+    xs = [np.ascontiguousarray(_voigt_data(n, synth.SEED_VOIGT + 400 + k)) for k in range(6)]
+    m, free = om.voigt_model(nbins=2000)
+    th = m.p[free] * np.array([1.0, 0.99, 1.03, 0.98, 1.01])
+    ref = {}
+    for k in range(6):
+        f = _fresh(gf, xs[k], sort=False)
+        ref[k] = f.nll_grad(th)
+        f.close()
+    ctx, root, obs = pm.voigt_model(gf, nbins=2000)
+    ctx.set_data(root, obs, [xs[0]])
+    ctx.prefetch_data_ptrs(n, _ptrs([xs[1]]))
+    ctx.prefetch_data_ptrs(n, _ptrs([xs[2]]))
+    order = [1, 2, 3, 4, 5, 1, 2, 3]
+    for step, k in enumerate(order):
+        f, g = ctx.nll_grad(th)  # the loaded set, while the next two are copied
+        ctx.update_data_ptrs(n, _ptrs([xs[k]]))
+        if step + 2 < len(order):
+            ctx.prefetch_data_ptrs(n, _ptrs([xs[order[step + 2]]]))
+        f, g = ctx.nll_grad(th)
+        assert f == ref[k][0] and np.array_equal(g, ref[k][1]), (step, k)
+    # a full queue (2 and 3 wait): staging 4 drops 2; loading 4 then drops 3
+    ctx.prefetch_data_ptrs(n, _ptrs([xs[2]]))
+    ctx.prefetch_data_ptrs(n, _ptrs([xs[3]]))
+    ctx.prefetch_data_ptrs(n, _ptrs([xs[4]]))
+    ctx.update_data_ptrs(n, _ptrs([xs[4]]))
+    f, g = ctx.nll_grad(th)
+    assert f == ref[4][0] and np.array_equal(g, ref[4][1])
+    # 3 was dropped: loading it copies it on the spot
+    ctx.update_data_ptrs(n, _ptrs([xs[3]]))
+    f, g = ctx.nll_grad(th)
+    assert f == ref[3][0] and np.array_equal(g, ref[3][1])
     ctx.close()
 
 
