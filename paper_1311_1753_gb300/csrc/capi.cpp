@@ -113,9 +113,12 @@ static void free_dev(gf_ctx* ctx) {
   DevState& d = ctx->dev;
   if (d.copy_stream) {  // a prefetch may still be copying into the staging buffers
     cudaStreamSynchronize(d.copy_stream);
+    cudaStreamSynchronize(d.check_stream);
     cudaStreamDestroy(d.copy_stream);
+    cudaStreamDestroy(d.check_stream);
   }
   for (int q = 0; q < DevState::kStage; ++q) {
+    if (d.ev_copied[q]) cudaEventDestroy(d.ev_copied[q]);
     if (d.ev_staged[q]) cudaEventDestroy(d.ev_staged[q]);
     for (double* p : d.stage[q]) cudaFree(p);
   }
@@ -2627,8 +2630,11 @@ int gf_prefetch_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
   }
   if (!d.copy_stream) {
     CK(cudaStreamCreateWithFlags(&d.copy_stream, cudaStreamNonBlocking));
-    for (int q = 0; q < DevState::kStage; ++q)
+    CK(cudaStreamCreateWithFlags(&d.check_stream, cudaStreamNonBlocking));
+    for (int q = 0; q < DevState::kStage; ++q) {
+      CK(cudaEventCreateWithFlags(&d.ev_copied[q], cudaEventDisableTiming));
       CK(cudaEventCreateWithFlags(&d.ev_staged[q], cudaEventDisableTiming));
+    }
     CK(cudaEventCreateWithFlags(&d.ev_free, cudaEventDisableTiming));
   }
   int q = 0;  // a spare set holding no prefetch
@@ -2658,9 +2664,13 @@ int gf_prefetch_data(gf_ctx* ctx, int64_t n, const double* const* cols) {
     lo[k] = ctx->obs[d.obs_ids[k]].lo;
     hi[k] = ctx->obs[d.obs_ids[k]].hi;
   }
+  // the check on its own stream behind the copy: the copy stream goes on to the next
+  // set's copy while the check waits for SMs the evaluation holds
+  CK(cudaEventRecord(d.ev_copied[q], d.copy_stream));
+  CK(cudaStreamWaitEvent(d.check_stream, d.ev_copied[q], 0));
   CK(launch_check_range(c, d.nobs, n, lo, hi, reinterpret_cast<int*>(d.result + 61 + q),
-                        d.copy_stream));
-  CK(cudaEventRecord(d.ev_staged[q], d.copy_stream));
+                        d.check_stream));
+  CK(cudaEventRecord(d.ev_staged[q], d.check_stream));
   d.stage_src[q].assign(cols, cols + d.nobs);
   d.pend[d.npend++] = q;
   return GF_OK;

@@ -94,7 +94,10 @@ struct DevState {
   std::vector<double*> stage[kStage];   // spare buffer sets (same sizes as cols)
   int stage_id[kStage] = {1, 2};        // their buffer-set numbers (cols has cur_set)
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_staged[kStage] = {};   // recorded after each spare set's copy and check
+  cudaStream_t check_stream = nullptr;  // the range checks (off the copy stream: a check
+                                        // waits for free SMs, the next copy need not)
+  cudaEvent_t ev_copied[kStage] = {};   // recorded after each spare set's copy
+  cudaEvent_t ev_staged[kStage] = {};   // ... and after its range check
   cudaEvent_t ev_free = nullptr;        // the compute stream's work before a copy
   std::vector<const double*> stage_src[kStage];  // host columns staged there (empty: none)
   int pend[kStage] = {0, 0};            // the spare sets holding prefetches, oldest first
