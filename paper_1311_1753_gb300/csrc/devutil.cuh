@@ -82,10 +82,12 @@ struct Neu {
 
 // Sum m per-thread values (pairs, from val(k)) over the block in a fixed order and write
 // the block's sums to out[0 .. m-1] (global memory): each warp folds its 32 lanes with
-// pair shuffles (lane order fixed), lane 0 stores the warp's m sums as doubles in
-// red[warp * m + k], one barrier, then thread k adds the warps' k-th sums in FP64.
-// red: (blockDim / 32) * m doubles.  Replaces m separate FP64 block sums (2 barriers and
-// 5 FP64 shuffle-adds per value and thread).
+// pair shuffles (lane order fixed), lane 0 stores the warp's m sums as pairs in
+// red[warp * m + k], one barrier, then thread k adds the warps' k-th sums as pairs and
+// converts the total to FP64 once.  Every step stays on the FP32 pipe until that one
+// conversion per value (an FP64 instruction occupies an SM sub-partition for many cycles
+// on this part, so per-warp conversions of every value were the slow part).
+// red: (blockDim / 32) * m doubles (each slot holds one pair).
 // M >= 0: the count m known at compile time (the loop unrolls, val's index is a constant,
 // so a caller's per-thread array stays in registers).
 template <int M = -1, class Val>
@@ -102,7 +104,7 @@ __device__ __forceinline__ void block_sum_pairs(Val val, int m, double* red, dou
         const F2 u = {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
         v = df_add(v, u);
       }
-      if (lane == 0) red[warp * m + k] = df_to(v);
+      if (lane == 0) reinterpret_cast<F2*>(red)[warp * m + k] = v;
     }
   } else {
     // values four at a time, their shuffle trees interleaved (the same tree per value)
@@ -122,15 +124,16 @@ __device__ __forceinline__ void block_sum_pairs(Val val, int m, double* red, dou
       if (lane == 0) {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          if (k0 + j < m) red[warp * m + k0 + j] = df_to(v[j]);
+          if (k0 + j < m) reinterpret_cast<F2*>(red)[warp * m + k0 + j] = v[j];
       }
     }
   }
   __syncthreads();
+  const F2* rp = reinterpret_cast<const F2*>(red);
   for (int k = threadIdx.x; k < m; k += blockDim.x) {
-    double r = 0.0;
-    for (int w = 0; w < nw; ++w) r += red[w * m + k];
-    out[(size_t)k * ostride] = r;
+    F2 r = rp[k];
+    for (int w = 1; w < nw; ++w) r = df_add(r, rp[w * m + k]);
+    out[(size_t)k * ostride] = df_to(r);
   }
 }
 
