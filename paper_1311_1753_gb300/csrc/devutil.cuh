@@ -179,6 +179,52 @@ __device__ inline void reduce_partials(const double* partials, int nblk, int str
   __syncthreads();
 }
 
+// Padded block-major partials: value k of block b at partials[b ps + k] with ps the
+// smallest multiple of 16 doubles >= m, so that every block writes its own 128-byte lines
+// (in the value-major layout 16 blocks' 8-byte stores share a line).
+__host__ __device__ constexpr int partial_stride(int m) { return (m + 15) / 16 * 16; }
+
+// Their cross-block sums by the last block: thread t sums the elements t, t + T, t + 2T, ...
+// of the flat array (value t mod ps for T a multiple of ps; consecutive threads load
+// consecutive doubles, kB loads in flight) as pairs, then thread k < m adds the T/ps sums of
+// value k in order and converts once.  Fixed order (bitwise reproducible).  scratch: T
+// pairs (shared memory); out: m doubles.  Called by every thread of one block; ends with a
+// barrier.
+template <int kB = 8>
+__device__ inline void reduce_partials_bm(const double* partials, int nblk, int m, double* out,
+                                          F2* scratch) {
+  const int T = blockDim.x, t = threadIdx.x, ps = partial_stride(m);
+  if (T % ps != 0) {  // a warp per value over the same layout
+    reduce_partials(partials, nblk, ps, m, out, 1);
+    return;
+  }
+  const int total = nblk * ps;
+  F2 a = {0.f, 0.f}, a2 = {0.f, 0.f};
+  if (t % ps < m) {
+    for (int f0 = t; f0 < total; f0 += kB * T) {
+      double v[kB];
+#pragma unroll
+      for (int j = 0; j < kB; ++j) {
+        const int f = f0 + j * T;
+        v[j] = f < total ? __ldcg(partials + f) : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < kB; j += 2) {  // only the loaded values (df_split's zero path is a call)
+        if (f0 + j * T < total) a = df_add(a, df_split(v[j]));
+        if (f0 + (j + 1) * T < total) a2 = df_add(a2, df_split(v[j + 1]));
+      }
+    }
+  }
+  scratch[t] = df_add(a, a2);
+  __syncthreads();
+  if (t < m) {
+    F2 r = scratch[t];
+    for (int j = t + ps; j < T; j += ps) r = df_add(r, scratch[j]);
+    out[t] = df_to(r);
+  }
+  __syncthreads();
+}
+
 // Last-block pattern: every block publishes its partial, then bumps a counter; the
 // block that takes the last ticket sees every partial and finishes the reduction.
 // The counter is reset by that block, so the next launch starts from zero.

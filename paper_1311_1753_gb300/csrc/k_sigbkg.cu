@@ -283,7 +283,8 @@ struct SBShared {
   F2 kp[8];    // the per-event constants as pairs (warp 0 converts them, one per lane)
   SBTabF tf;   // the table of w expansions (tf.ntab = 0: none)
   WeidCoef W;  // the series coefficients, read by every thread (and the out-of-line paths)
-  double red[(NT / 32) * kSBMom];
+  double red[(NT / 32) * kSBMom > NT ? (NT / 32) * kSBMom : NT];  // block sums; NT pairs for
+                                                                   // the cross-block sums
   double fin[kSBMom];
   int last;
 };
@@ -745,11 +746,11 @@ __device__ __forceinline__ void sigbkg_block(
   for (int k = 1; k < kSBMom; ++k)
     if constexpr (MIXED) vals[k] = F2{sh.mh[k - 1][tid], sh.ml[k - 1][tid]};
     else vals[k] = m[k - 1].get();
-  // partials value-major: value k of block b at partials[k vgrid + b]
-  block_sum_pairs<G ? kSBMom : 1>([&](int k) -> F2 { return vals[k]; }, mm, sh.red, partials + vb,
-                                  vgrid);
+  // partials padded block-major: value k of block b at partials[b partial_stride(mm) + k]
+  block_sum_pairs<G ? kSBMom : 1>([&](int k) -> F2 { return vals[k]; }, mm, sh.red,
+                                  partials + (size_t)vb * partial_stride(mm), 1);
   if (!arrive_last_of(counter, (unsigned)vgrid, &sh.last)) return;
-  reduce_partials(partials, vgrid, 1, mm, sh.fin, vgrid);
+  reduce_partials_bm(partials, vgrid, mm, sh.fin, reinterpret_cast<F2*>(sh.red));
   if (tid == 0) {
     sb_finish(D, der, sh.fin, G, result);
     *counter = 0u;
