@@ -324,7 +324,9 @@ MinResult minimise_refined(const FGFun* fg_fast, const FGFun& fg_exact,
   if (r1.x.empty() || (r1.status != GF_OK && r1.status != GF_ENOCONV)) return r1;
   MinOpts o2 = opt;
   o2.hesse = false;
-  o2.f_noise_rel = 0.0;
+  // the FP64-accurate sums' own rounding (pair accumulators: ~1e-15 of |f| for millions of
+  // events): below it a line search cannot tell a step's decrease from noise
+  o2.f_noise_rel = opt.f_noise_rel_exact;
   o2.max_calls = std::max(1, opt.max_calls - r1.calls);
   // curvature for the FP64 stage: the FP32 Hessian at the hand-over point, mapped to
   // internal coordinates (V = D^-1 H_ext^-1 D^-1, D = dext/du); BFGS's own estimate

@@ -14,6 +14,7 @@ struct MinOpts {
   double f_noise_rel = 0.0;       // noise of f relative to |f|: smaller differences count as
                                   // no change in the line search
   double f_noise_rel_fast = 3e-8; // the same for fg_fast of minimise_refined (FP32 sums)
+  double f_noise_rel_exact = 2e-15;  // ... and for its FP64-accurate stage
 };
 
 struct MinResult {
