@@ -41,17 +41,17 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # + 2 FFMA executed per event, predicated-on) and the DRAM traffic of one launch are ncu
 # counters of one launch of this build at the bench's own size (the profile summaries
 # of k_sigbkg and k_dalitz_stream under profiles/).
-FP32_FLOPS_PER_EVENT = {"voigt_grad": 593.1,      # FADD 334.4 + FMUL 45.1 + 2 x FFMA 106.8
-                        "voigt_grad_mixed": 104.5,  # FADD 38.3 + FMUL 18.2 + 2 x FFMA 24.0
-                        "dalitz_cached": 1349.8,  # FADD 781.8 + FMUL 82.0 + 2 x FFMA 243.0
-                        "dalitz_free": 7446.0,    # FADD 3933.4 + FMUL 531.0 + 2 x FFMA 1491.0
-                        "dalitz_mixed": 902.4}    # FADD 204.0 + FMUL 280.0 + 2 x FFMA 209.0
-TRAFFIC_PER_LAUNCH = {"voigt_grad": 81.97e6,        # 80.14 MB read + 1.83 MB written
-                      "voigt_grad_mixed": 83.65e6,  # 80.44 MB read + 3.21 MB written
-                      "dalitz_cached": 131.34e6,    # 128.12 MB read + 3.22 MB written (10^6)
-                      "dalitz_free": 865.82e6,      # 164.01 MB read + 701.81 MB written (5 x 10^6;
+FP32_FLOPS_PER_EVENT = {"voigt_grad": 593.1,      # FADD 334.5 + FMUL 45.1 + 2 x FFMA 106.8
+                        "voigt_grad_mixed": 104.6,  # FADD 38.3 + FMUL 18.2 + 2 x FFMA 24.0
+                        "dalitz_cached": 1350.2,  # FADD 782.2 + FMUL 82.0 + 2 x FFMA 243.0
+                        "dalitz_free": 7446.6,    # FADD 3933.6 + FMUL 531.0 + 2 x FFMA 1491.0
+                        "dalitz_mixed": 902.1}    # FADD 204.1 + FMUL 280.0 + 2 x FFMA 209.0
+TRAFFIC_PER_LAUNCH = {"voigt_grad": 81.85e6,        # 80.15 MB read + 1.70 MB written
+                      "voigt_grad_mixed": 83.61e6,  # 80.47 MB read + 3.14 MB written
+                      "dalitz_cached": 131.37e6,    # 128.14 MB read + 3.23 MB written (10^6)
+                      "dalitz_free": 864.78e6,      # 164.37 MB read + 700.41 MB written (5 x 10^6;
                                                     # the writes are register spills)
-                      "dalitz_mixed": 103.01e6}     # 100.13 MB read + 2.88 MB written (5 x 10^6)
+                      "dalitz_mixed": 103.00e6}     # 100.10 MB read + 2.90 MB written (5 x 10^6)
 # the headline workload's name, shared by both arms' JSON lines
 VOIGT_WORKLOAD = ("1D composite: Voigtian (mu,sigma,Gamma) + threshold (c) with fraction f, "
                   "10^7 FP64 events, 2 x 10,000-bin grid normalisation")
