@@ -62,14 +62,15 @@ VOIGT_WORKLOAD = ("1D composite: Voigtian (mu,sigma,Gamma) + threshold (c) with 
 # value and 3 partials 31; threshold value and partial 9; the mixture (2 products, 1 sum)
 # and its gradient terms (6 products, 6 sums) 15; log P and 1/P 2.
 FP64_FLOPS_PER_EVENT = {"voigt_grad": 94}
-# Config 4 (8 resonances, 7 with free mass and width, 30 free parameters), the method's
-# FP64 operations per event counted the same way from the amplitude code: the kinematics of
+# The free-shape Dalitz model (8 resonances, 7 with free mass and width, 30 free
+# parameters), the method's FP64 operations per event counted the same way from the
+# amplitude code: the kinematics of
 # the 3 channels 95 (1/sqrt(s), break-up momentum, Blatt-Weisskopf factors, Zemach terms),
 # 7 Breit-Wigner amplitudes 105 (running width, complex reciprocal, barrier and angular
 # factors), 8 coefficient multiply-adds 64, |A|^2 and log 5; the gradient: 16 coefficient
 # terms 82, 14 mass and width derivatives 273: 624.
 FP64_FLOPS_PER_EVENT["dalitz_free"] = 624
-# Config 3 (every shape fixed): the pass reads each event's 8 cached amplitudes, FP64-
+# The fixed-shape Dalitz model: the pass reads each event's 8 cached amplitudes, FP64-
 # accurate as float pairs (16 B each): 128 B/event from HBM.
 BYTES_PER_EVENT = {"dalitz_cached": 128}
 
@@ -687,8 +688,8 @@ def main():
 
 
 def run_fits(torch, gf, args):
-    """Time-to-fit (gf_fit: BFGS + fused gradient + Hessian errors) per workload.  Configs 2
-    and 4 in FP64 and in mixed precision (FP32 per-event arithmetic, FP64 sums, then the
+    """Time-to-fit (gf_fit: BFGS + fused gradient + Hessian errors) per workload.  The line
+    shape (10^7 events) and the free-shape Dalitz model (5 x 10^6) in FP64 and in mixed precision (FP32 per-event arithmetic, FP64 sums, then the
     FP64 refinement) on the same data from the same start, with the mixed fit's largest
     deviation from the FP64 fit in sigma units."""
     out = {}

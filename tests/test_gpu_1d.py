@@ -44,7 +44,7 @@ def test_exponential_parity(gf, n):
         lg = ctx.logpdf(th)
         if n:
             lo = m.logpdf([x], p)
-            per_event(f"config1 n={n} alpha={alpha}", lg, lo)
+            per_event(f"exponential n={n} alpha={alpha}", lg, lo)
         f, g = ctx.nll_grad(th)
         fo, go = m.nll([x], p, grad=True)
         assert abs(f - fo) <= 1e-9 * max(1.0, abs(fo))
@@ -80,7 +80,7 @@ def test_voigt_parity(gf, n):
         th = p[free]
         lo_ = m.logpdf([x], p)
         lg = ctx.logpdf(th)
-        per_event(f"config2 n={n}", lg, lo_)
+        per_event(f"voigt n={n}", lg, lo_)
         f, g = ctx.nll_grad(th)
         fo, go = m.nll([x], p, grad=True)
         assert abs(f - fo) <= 1e-9 * abs(fo)
@@ -114,7 +114,7 @@ def test_voigt_full_size(gf):
     f = ctx.nll(th)
     fo = m.nll([x], m.p)
     assert abs(f - fo) <= 1e-9 * abs(fo)
-    per_event("config2 full 1e7", ctx.logpdf(th), m.logpdf([x], m.p))
+    per_event("voigt full 1e7", ctx.logpdf(th), m.logpdf([x], m.p))
 
 
 def test_sorted_layout_matches_strided_loop(gf):

@@ -119,8 +119,8 @@ def test_dalitz_full_size(gf):
     assert abs(f - fo) <= 1e-9 * abs(fo)
     P, kap = op.dalitz_intensity(SPEC, p, s12, s13, kappa=True)
     N, _ = d.norm(p)
-    per_event("config3 full 1e6", ctx.logpdf(th), np.log(P / N), kap)
-    WORST["config3 full 1e6: events with kappa > 1e3"] = float((kap > 1e3).sum())
+    per_event("dalitz fixed full 1e6", ctx.logpdf(th), np.log(P / N), kap)
+    WORST["dalitz fixed full 1e6: events with kappa > 1e3"] = float((kap > 1e3).sum())
 
 
 def test_free_shape_full_size_fp64_and_mixed(gf):
@@ -142,7 +142,7 @@ def test_free_shape_full_size_fp64_and_mixed(gf):
     go = go[free]
     ctx, root, obs = pm.dalitz_model(gf, SPEC, free_shapes=True)
     ctx.set_data(root, obs, [s12, s13])
-    per_event("config4 fp64 full 5e6", ctx.logpdf(th), lo_, kap)
+    per_event("dalitz free fp64 full 5e6", ctx.logpdf(th), lo_, kap)
     f, g = ctx.nll_grad(th)
     assert abs(f - fo) <= 1e-9 * abs(fo), (f, fo)
     scale = np.maximum(np.abs(go), 1e-6 * len(s12))
@@ -154,11 +154,11 @@ def test_free_shape_full_size_fp64_and_mixed(gf):
     pct = {q_: float(np.quantile(rel, q_)) for q_ in (0.5, 0.9, 0.99, 0.999)}
     pct[1.0] = float(rel.max())
     for q_, v in pct.items():
-        WORST[f"config4 mixed full 5e6: per-event |P/P_orc - 1| quantile {q_}"] = v
+        WORST[f"dalitz free mixed full 5e6: per-event |P/P_orc - 1| quantile {q_}"] = v
     assert pct[0.5] < 1e-5 and pct[0.99] < 1e-3
     fm, gm = mctx.nll_grad(th)
-    WORST["config4 mixed full 5e6: NLL relative error"] = abs(fm / fo - 1)
-    WORST["config4 mixed full 5e6: max |dgrad| / max |grad|"] = float(
+    WORST["dalitz free mixed full 5e6: NLL relative error"] = abs(fm / fo - 1)
+    WORST["dalitz free mixed full 5e6: max |dgrad| / max |grad|"] = float(
         np.max(np.abs(gm - go)) / np.abs(go).max())
     assert abs(fm - fo) <= 1e-6 * abs(fo)
     assert np.max(np.abs(gm - go)) <= 1e-3 * np.abs(go).max()

@@ -114,7 +114,7 @@ def test_autograd_wrapper(gf):
 
 
 def test_dalitz_free_shape_mixed_fit_small(gf):
-    """Config 4's shape: 30 free parameters (7 masses and widths free), FP32 amplitudes with
+    """The free-shape Dalitz model: 30 free parameters (7 masses and widths free), FP32 amplitudes with
     FP64 sums and normalisation, fused gradient; against the oracle's FP64 fit."""
     nres = len(SPEC["resonances"])
     d = om.dalitz_from_spec(SPEC, 128, 128)

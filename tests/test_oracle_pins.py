@@ -28,7 +28,7 @@ def _w_mp(z):
 
 
 def test_faddeeva_vs_mpmath_voigt_region():
-    # Config 2: y = Gamma/(2 sqrt2 sigma) ~ 0.094, Re z in [-14.2, 36.6]; widen both.
+    # The line-shape workload: y = Gamma/(2 sqrt2 sigma) ~ 0.094, Re z in [-14.2, 36.6]; widen both.
     x = RNG.uniform(-16, 40, 300)
     y = RNG.uniform(0.01, 0.3, 300)
     z = x + 1j * y
