@@ -263,13 +263,13 @@ def time_steps(torch, ctx, thetas, steps, warmup, grad=True, flush=True):
 
 
 def e2e_steps(torch, ctx, cols, thetas, steps, warmup, pipelined=True):
-    """Public-API step with host buffers, pipelined for 1D data sets: step k evaluates its
-    events (NLL + gradient back to the host) while the library copies and range-checks
-    the events of steps k+1 and k+2 from pinned host memory, one after the other on its
-    copy stream (gf_prefetch_data, two sets ahead); gf_update_data then loads step k+1's
-    (a swap of device buffer sets; events in the caller's order) and step k+3's copy is
-    queued.  Each timed step completes one copy of a step's events.  Wall clock per
-    step."""
+    """Public-API step with host buffers, pipelined for 1D data sets: step k queues the
+    evaluation of its events (gf_nll_grad_start), then, while it runs, loads step k+1's
+    events (gf_update_data: a swap of device buffer sets, their copy and range check done
+    earlier on the library's copy stream) and queues step k+3's copy from pinned host
+    memory (gf_prefetch_data, two sets ahead), then takes the NLL + gradient back to the
+    host (gf_nll_grad_finish).  Events in the caller's order.  Each timed step completes
+    one copy of a step's events.  Wall clock per step."""
     pinned = []
     for shift in (0, 1, 2):
         p = [torch.from_numpy(np.ascontiguousarray(np.roll(c, shift))).pin_memory() for c in cols]
@@ -293,17 +293,21 @@ def e2e_steps(torch, ctx, cols, thetas, steps, warmup, pipelined=True):
     ctx.prefetch_data_ptrs(n, ptrs(1))
     ctx.prefetch_data_ptrs(n, ptrs(2))
     k = 0
-    for _ in range(warmup):
-        ctx.nll_grad(thetas[k % len(thetas)])
+
+    def step(k):
+        # the evaluation queued, the next set loaded and a later one queued while it runs
+        ctx.nll_grad_start(thetas[k % len(thetas)])
         ctx.update_data_ptrs(n, ptrs(k + 1))
         ctx.prefetch_data_ptrs(n, ptrs(k + 3))
+        return ctx.nll_grad_finish()
+
+    for _ in range(warmup):
+        step(k)
         k += 1
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        ctx.nll_grad(thetas[k % len(thetas)])
-        ctx.update_data_ptrs(n, ptrs(k + 1))
-        ctx.prefetch_data_ptrs(n, ptrs(k + 3))
+        step(k)
         k += 1
     wall = time.perf_counter() - t0
     return wall, 8 * n * len(cols)
@@ -636,11 +640,13 @@ def main():
         e2e = {"value": n * ksteps / wall, "unit": unit,
                "h2d_bytes_per_step": h2d + 8 * len(th0),
                "d2h_bytes_per_step": 8 * (1 + len(th0)) + 4,
-               "note": ("pipelined through the C ABI: step k's NLL + gradient (back to the "
-                        "host) while the events of steps k+1 and k+2 are copied from pinned "
-                        "host memory and range-checked, one after the other, on the "
-                        "library's copy stream (gf_prefetch_data, two sets ahead); step "
-                        "k+1's are then loaded by gf_update_data; wall clock per step"
+               "note": ("pipelined through the C ABI: step k's NLL + gradient queued "
+                        "(gf_nll_grad_start) and taken back to the host (gf_nll_grad_finish) "
+                        "while the events of steps k+1 and k+2 are copied from pinned host "
+                        "memory and range-checked, one after the other, on the library's "
+                        "copy stream (gf_prefetch_data, two sets ahead); step k+1's are "
+                        "loaded by gf_update_data during step k's evaluation; wall clock "
+                        "per step"
                         if pipe else
                         "gf_update_data from pinned host memory + gf_nll_grad in turn, wall "
                         "clock per step")}

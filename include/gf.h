@@ -283,6 +283,19 @@ int gf_prefetch_data(gf_ctx* ctx, int64_t n, const double* const* cols);
 int gf_nll(gf_ctx* ctx, const double* theta, double* nll);
 /* NLL and its gradient over theta from the same event pass. */
 int gf_nll_grad(gf_ctx* ctx, const double* theta, double* nll, double* grad);
+/* The same evaluation in two halves, so that the host can work while the GPU computes
+ * (Sec. 2's evaluation, pipelined with data loading).  gf_nll_grad_start queues the
+ * evaluation at theta on the context's stream and returns; gf_nll_grad_finish waits for
+ * it and returns what gf_nll_grad would have returned (the same bits).  Between the two
+ * the caller may load the next events with gf_update_data (a swap with a prefetched set,
+ * or a copy queued behind the evaluation) and queue more with gf_prefetch_data (its copy
+ * waits for the queued evaluation before overwriting a buffer set it reads): the queued
+ * evaluation keeps the events it started with.  One evaluation per context at a time:
+ * until gf_nll_grad_finish, a second start and every call that evaluates or sets new
+ * parameters or a new data set (gf_nll, gf_nll_grad, gf_logpdf, gf_fit, gf_set_data,
+ * ...) returns GF_ESTATE; gf_nll_grad_finish without a start returns GF_ESTATE. */
+int gf_nll_grad_start(gf_ctx* ctx, const double* theta);
+int gf_nll_grad_finish(gf_ctx* ctx, double* nll, double* grad);
 /* Per-event log P_i at theta into out (host array of n doubles, event order). */
 int gf_logpdf(gf_ctx* ctx, const double* theta, double* out);
 /* Same into a device array of n doubles. */

@@ -1781,6 +1781,8 @@ static int mark_unsorted(gf_ctx* ctx) {
 
 extern "C" int gf_set_data(gf_ctx* ctx, int root, const gf_dataset* ds) {
   if (!ctx || !ds || ds->ctx != ctx || !valid_node(ctx, root)) return GF_EINVAL;
+  if (ctx->eval_in_flight)
+    return set_error(ctx, GF_ESTATE, "an evaluation started by gf_nll_grad_start is not finished");
   CK(cudaSetDevice(ctx->device));
   const NodeDef& nd = ctx->nodes[root];
   if (nd.type == N_DALITZ || nd.type == N_TDDP) {
@@ -1851,6 +1853,8 @@ extern "C" int gf_set_data_device(gf_ctx* ctx, int root, int nobs, const int* ob
   if (!ctx || !valid_node(ctx, root) || nobs < 1 || nobs > kMaxObs || !obs || n < 0 ||
       !dev_cols)
     return GF_EINVAL;
+  if (ctx->eval_in_flight)
+    return set_error(ctx, GF_ESTATE, "an evaluation started by gf_nll_grad_start is not finished");
   for (int k = 0; k < nobs; ++k) {
     if (!valid_obs(ctx, obs[k]) || !dev_cols[k]) return GF_EINVAL;
     if (reinterpret_cast<uintptr_t>(dev_cols[k]) % 16 != 0)
@@ -1883,6 +1887,9 @@ static int sbtab_blocks(const gf_ctx* ctx) {
 
 static int fill_theta_host(gf_ctx* ctx, const double* theta) {
   DevState& d = ctx->dev;
+  // the queued evaluation's graph reads the pinned theta when the stream reaches it
+  if (ctx->eval_in_flight)
+    return set_error(ctx, GF_ESTATE, "an evaluation started by gf_nll_grad_start is not finished");
   const int np = (int)ctx->pars.size();
   for (int i = 0; i < np; ++i) d.h_theta[i] = ctx->pars[i].value;
   for (size_t k = 0; k < ctx->free_ids.size(); ++k) {
@@ -2400,15 +2407,22 @@ int tick_finish(gf_ctx* ctx, const double* res, double* nll, double* grad) {
   return GF_OK;
 }
 
-int evaluate(gf_ctx* ctx, const double* theta, double* nll, double* grad, bool fp64) {
-  // a data set evaluated repeatedly (a fit) after gf_update_data gets sorted again
+// A data set evaluated repeatedly (a fit) after gf_update_data gets sorted again.
+static int resort_if_repeated(gf_ctx* ctx) {
   DevState& d = ctx->dev;
   if (!d.sorted && d.owns_cols && ++d.evals_since_load >= 2 && sort_eligible(ctx)) {
     CK(cudaSetDevice(ctx->device));
-    const int rs = sort_events(ctx);
-    if (rs) return rs;
+    return sort_events(ctx);
   }
-  int rc = evaluate_async(ctx, theta, grad != nullptr, fp64);
+  return GF_OK;
+}
+
+int evaluate(gf_ctx* ctx, const double* theta, double* nll, double* grad, bool fp64) {
+  if (ctx->eval_in_flight)
+    return set_error(ctx, GF_ESTATE, "an evaluation started by gf_nll_grad_start is not finished");
+  int rc = resort_if_repeated(ctx);
+  if (rc) return rc;
+  rc = evaluate_async(ctx, theta, grad != nullptr, fp64);
   if (rc) return rc;
   return evaluate_finish(ctx, nll, grad, grad != nullptr);
 }
@@ -2431,6 +2445,30 @@ int gf_nll_grad(gf_ctx* ctx, const double* theta, double* nll, double* grad) {
   if (rc) return rc;
   if (!ctx->free_ids.empty() && (!theta || !grad)) return GF_EINVAL;
   return evaluate(ctx, theta, nll, grad);
+}
+
+int gf_nll_grad_start(gf_ctx* ctx, const double* theta) {
+  if (!ctx) return GF_EINVAL;
+  if (ctx->eval_in_flight)
+    return set_error(ctx, GF_ESTATE, "gf_nll_grad_start: an evaluation is already in flight");
+  int rc = ensure_compiled(ctx);
+  if (rc) return rc;
+  if (!ctx->free_ids.empty() && !theta) return GF_EINVAL;
+  rc = resort_if_repeated(ctx);
+  if (rc) return rc;
+  rc = evaluate_async(ctx, theta, true, false);
+  if (rc) return rc;
+  ctx->eval_in_flight = true;
+  return GF_OK;
+}
+
+int gf_nll_grad_finish(gf_ctx* ctx, double* nll, double* grad) {
+  if (!ctx || !nll) return GF_EINVAL;
+  if (!ctx->eval_in_flight)
+    return set_error(ctx, GF_ESTATE, "gf_nll_grad_finish: no evaluation in flight");
+  if (!ctx->free_ids.empty() && !grad) return GF_EINVAL;
+  ctx->eval_in_flight = false;
+  return evaluate_finish(ctx, nll, grad, true);
 }
 
 static int logpdf_impl(gf_ctx* ctx, const double* theta, double* out, bool host) {

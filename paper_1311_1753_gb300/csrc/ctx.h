@@ -169,6 +169,8 @@ struct gf_ctx {
   double last_ms = 0.0;
   double last_stream_ms = 0.0;
   int last_launches = 0;
+  bool eval_in_flight = false;  // gf_nll_grad_start queued an evaluation, not yet finished
+  bool eval_grad = false;       // ... with its gradient
   bool last_graph = false;  // the last evaluation replayed a captured graph
   bool graphs = true;       // replay captured graphs of steady evaluations
   bool event_sort = true;   // keep owned 1D columns sorted for the chunked event loop

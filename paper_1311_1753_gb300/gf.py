@@ -96,6 +96,8 @@ def _load():
         "gf_set_data_device": ([vp, C.c_int, C.c_int, _I, C.c_int64, C.POINTER(vp)], C.c_int),
         "gf_nll": ([vp, _D, _D], C.c_int),
         "gf_nll_grad": ([vp, _D, _D, _D], C.c_int),
+        "gf_nll_grad_start": ([vp, _D], C.c_int),
+        "gf_nll_grad_finish": ([vp, _D, _D], C.c_int),
         "gf_logpdf": ([vp, _D, _D], C.c_int),
         "gf_logpdf_device": ([vp, _D, vp], C.c_int),
         "gf_dalitz_gram": ([vp, _D, _D], C.c_int),
@@ -375,6 +377,22 @@ class Context:
         if rc == GF_ENONFINITE:
             return float("inf"), g
         self._ck(rc, "gf_nll_grad")
+        return out.value, g
+
+    def nll_grad_start(self, theta):
+        """gf_nll_grad_start: queue NLL + gradient at theta and return at once."""
+        th = _f64(theta)
+        self._ck(lib.gf_nll_grad_start(self.h, _dp(th)), "gf_nll_grad_start")
+        self._nf_started = len(th)
+
+    def nll_grad_finish(self):
+        """gf_nll_grad_finish: wait for the started evaluation; (nll, gradient)."""
+        out = C.c_double()
+        g = np.zeros(getattr(self, "_nf_started", 0))
+        rc = lib.gf_nll_grad_finish(self.h, C.byref(out), _dp(g))
+        if rc == GF_ENONFINITE:
+            return float("inf"), g
+        self._ck(rc, "gf_nll_grad_finish")
         return out.value, g
 
     def logpdf(self, theta):

@@ -111,6 +111,48 @@ def test_two_prefetches_in_flight(gf):
     ctx.close()
 
 
+def test_started_evaluation_with_loads_in_between(gf):
+    """gf_nll_grad_start / gf_nll_grad_finish: the same bits as gf_nll_grad, also with the
+    next set loaded and a later one prefetched while the started evaluation runs (it keeps
+    the events it started with); a second start, an evaluation or a new data set while
+    one is in flight, and a finish without a start, are refused."""
+    n = 150_001
+    xs = [np.ascontiguousarray(_voigt_data(n, synth.SEED_VOIGT + 500 + k)) for k in range(5)]
+    m, free = om.voigt_model(nbins=2000)
+    th = m.p[free] * np.array([1.0, 1.01, 0.98, 1.02, 0.99])
+    ref = {}
+    for k in range(5):
+        f = _fresh(gf, xs[k], sort=False)
+        ref[k] = f.nll_grad(th)
+        f.close()
+    ctx, root, obs = pm.voigt_model(gf, nbins=2000)
+    ctx.set_event_sort(False)
+    ctx.set_data(root, obs, [xs[0]])
+    ctx.nll_grad_start(th)
+    with pytest.raises(gf.GFError):
+        ctx.nll_grad_start(th)
+    with pytest.raises(gf.GFError):
+        ctx.nll(th)
+    with pytest.raises(gf.GFError):
+        ctx.set_data(root, obs, [xs[1]])
+    f, g = ctx.nll_grad_finish()
+    assert f == ref[0][0] and np.array_equal(g, ref[0][1])
+    with pytest.raises(gf.GFError):
+        ctx.nll_grad_finish()
+    ctx.prefetch_data_ptrs(n, _ptrs([xs[1]]))
+    ctx.prefetch_data_ptrs(n, _ptrs([xs[2]]))
+    for k in range(4):
+        ctx.nll_grad_start(th)
+        ctx.update_data_ptrs(n, _ptrs([xs[k + 1]]))
+        if k + 3 < 5:
+            ctx.prefetch_data_ptrs(n, _ptrs([xs[k + 3]]))
+        f, g = ctx.nll_grad_finish()
+        assert f == ref[k][0] and np.array_equal(g, ref[k][1]), k
+    f, g = ctx.nll_grad(th)
+    assert f == ref[4][0] and np.array_equal(g, ref[4][1])
+    ctx.close()
+
+
 def test_prefetch_range_error_keeps_the_loaded_set(gf):
     n = 50_001
     x = np.ascontiguousarray(_voigt_data(n, synth.SEED_VOIGT + 300))
