@@ -45,6 +45,9 @@ def test_status_text_and_no_device_behaviour():
     assert rc in (gf.GF_ECUDA, gf.GF_EINVAL) and not h.value
     assert gf.lib.gf_destroy(None) == gf.GF_OK
     assert gf.lib.gf_nll(None, None, None) == gf.GF_EINVAL
+    assert gf.lib.gf_nll_grad_start(None, None) == gf.GF_EINVAL
+    assert gf.lib.gf_nll_grad_finish(None, None, None) == gf.GF_EINVAL
+    assert gf.lib.gf_prefetch_data(None, 0, None) == gf.GF_EINVAL
 
 
 def test_oracle_builds():
